@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the f(R) field solve on GB300.
+
+One step = one full solve of the synthetic workload to ||f - L(u)|| <= 1e-8 ||f||
+from a zero start with the mixed-precision form (FP32 smoothing, FP64
+residual and defect correction), inputs resident in HBM.  The plain FP64
+solve of the same input is timed beside it (time-to-tolerance).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank solves its own replica of the workload (the
+solves are independent, no collective on the data path); the timing is the
+max over ranks and `value` counts the updates of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("cell-updates/s & time-to-residual 1e-8 per f(R) solve "
+          "(plain FP64 vs mixed+learned), HBM %")
+UNIT = "cell-updates/s"
+
+WORKLOAD = dict(name="grid256", N=256, box=100.0, a=1.0, fr0=1e-5, sigma_g=1.5, seed=2002)
+
+# Algorithmic bytes per cell of one launch, per profiled kernel family
+# ("Kernels and rooflines"):
+#  0 FP32 NGS half-sweep: read u (4) + f of the active colour (2) + write the
+#    active u (2)                                   = 8 B per cell of the level
+#  1 FP32 linear GS half-sweep: read u32 (4) + e (4) + r active (2) + write e
+#    active (2)                                     = 12 B per cell
+#  2 FP64 residual: read u, E, f (24) + write r32, u32, e32 (12) = 36 B per cell
+#  (FP64 NGS half-sweep, plain path: read u, E (16) + f active (4) + write u, E
+#   active (8) = 28 B per cell)
+ALG_BYTES = {0: 8.0, 1: 12.0, 2: 36.0}
+KERNEL_NAMES = {0: "k_sweep32 (FP32 NGS half-sweep, base level)",
+                1: "k_lin_sweep (FP32 linear GS half-sweep, base level)",
+                2: "k_resid64 (FP64 residual, base level)"}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline_sample(max_seconds: float = 20.0) -> dict:
+    """The CPU oracle (single thread, FP64) on a bounded sample of the workload:
+    a full solve of a 64^3 lognormal field with the workload's cell size,
+    sigma_g and |fR0|, repeated while time remains."""
+    import oracle
+    from paper_1305_2418_gb300 import synth
+    w = WORKLOAD
+    N = 64
+    box = w["box"] * N / w["N"]
+    delta = synth.lognormal_delta(N, box, w["sigma_g"], w["seed"])
+    t0 = time.perf_counter()
+    upd = 0.0
+    n = 0
+    while True:
+        _, st = oracle.solve_dense(delta, box, w["fr0"], a=w["a"], tol=1e-8)
+        upd += st["updates"]
+        n += 1
+        if time.perf_counter() - t0 > max_seconds / 2 or n >= 8:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} full FP64 oracle solve(s) of a 64^3 lognormal field "
+                      f"(box {box:g} Mpc/h, same cell size, sigma_g {w['sigma_g']}, "
+                      f"|fR0| {w['fr0']:g}) to 1e-8, {dt:.1f} s"}
+
+
+def run_reference(args, rank: int) -> None:
+    if rank != 0:
+        return
+    import oracle
+    from paper_1305_2418_gb300 import synth
+    w = WORKLOAD
+    N = 64
+    box = w["box"] * N / w["N"]
+    delta = synth.lognormal_delta(N, box, w["sigma_g"], w["seed"])
+    for _ in range(args.warmup):
+        oracle.solve_dense(delta, box, w["fr0"], a=w["a"], tol=1e-8)
+    upd = 0.0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, st = oracle.solve_dense(delta, box, w["fr0"], a=w["a"], tol=1e-8)
+        upd += st["updates"]
+    dt = time.perf_counter() - t0
+    val = upd / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"] + " (64^3 sample per step, same cell size)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one full FP64 oracle solve of a 64^3 sample per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1305_2418_gb300 import build, mgfr, synth
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = WORKLOAD
+    delta_h = synth.lognormal_delta(w["N"], w["box"], w["sigma_g"], w["seed"])
+    delta = torch.from_numpy(delta_h).to(dev)
+    n = delta.numel()
+
+    def solver(prec, profile=1):
+        return mgfr.Solver(local, fr0_abs=w["fr0"], precision=prec, profile=profile)
+
+    # ---- plain FP64 solve, time to tolerance (reported beside) ----
+    s64 = solver(mgfr.PREC_FP64)
+    s64.solve_density(delta, w["box"], w["a"])
+    torch.cuda.synchronize()
+    t64 = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        o64 = s64.solve_density(delta, w["box"], w["a"])
+        e1.record()
+        torch.cuda.synchronize()
+        t64.append(e0.elapsed_time(e1))
+    st64 = o64["stats"]
+    s64.close()
+
+    # ---- mixed-precision form: the timed steps ----
+    sm = solver(mgfr.PREC_MIXED)
+    for _ in range(args.warmup):
+        sm.solve_density(delta, w["box"], w["a"])
+    torch.cuda.synchronize()
+    barrier()
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern_ms = [0.0] * 4
+    kern_n = [0] * 4
+    launches = 0
+    upd = 0
+    e0.record()
+    for _ in range(args.steps):
+        out = sm.solve_density(delta, w["box"], w["a"])
+        st = out["stats"]
+        for q in range(4):
+            kern_ms[q] += st["kern_ms"][q]
+            kern_n[q] += st["kern_launches"][q]
+        launches += st["gpu_launches"]
+        upd += st["cell_updates"] + st["linear_updates"]
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * upd / (ms_max / 1e3)
+    last = st
+
+    # ---- end to end through the public API: host buffers, copies timed ----
+    host_in = torch.from_numpy(delta_h).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    for _ in range(1):
+        d_in = host_in.to(dev, non_blocking=True)
+        r = sm.solve_density(d_in, w["box"], w["a"], want_acc=False)
+        host_out.copy_(r["fr"], non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    e2e_upd = 0
+    for _ in range(args.steps):
+        d_in = host_in.to(dev, non_blocking=True)
+        r = sm.solve_density(d_in, w["box"], w["a"], want_acc=False)
+        host_out.copy_(r["fr"], non_blocking=True)
+        e2e_upd += r["stats"]["cell_updates"] + r["stats"]["linear_updates"]
+    f1.record()
+    torch.cuda.synchronize()
+    te = torch.tensor([f0.elapsed_time(f1)], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * e2e_upd / (float(te.item()) / 1e3)
+    sm.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant profiled kernel ----
+    fam = max(range(3), key=lambda q: kern_ms[q])
+    avg_ms = kern_ms[fam] / max(kern_n[fam], 1)
+    bytes_per_launch = ALG_BYTES[fam] * n
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    roof = {"bound": "hbm", "kernel": KERNEL_NAMES[fam], "achieved": achieved, "peak": peak,
+            "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "launches": kern_n[fam], "avg_launch_us": 1e3 * avg_ms,
+            "kernel_share_of_step": kern_ms[fam] / ms,
+            "per_family_ms": {KERNEL_NAMES[q]: kern_ms[q] / args.steps for q in range(3)}}
+
+    cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline_sample()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{w['name']}: 256^3 periodic lognormal delta (sigma_g 1.5, "
+                               f"P(k)~k^-1.5), box 100 Mpc/h, |fR0| 1e-5, n 1, a 1; base-level "
+                               f"solve to 1e-8, zero start",
+                   "precision": "mixed (FP32 smoothing, FP64 residual/defect correction)",
+                   "l2": "working set (u, E, f FP64 + FP32 levels, ~700 MB) larger than L2",
+                   "parallelism": f"replicas x{world}"},
+        "time_to_tol_ms": {"mixed": ms_max / args.steps, "fp64": min(t64)},
+        "vcycles": {"mixed_fp32": last["vcycles"], "mixed_outer_fp64": last["outer_iters"],
+                    "fp64": st64["vcycles"]},
+        "cell_updates_per_step": {"nonlinear": last["cell_updates"],
+                                  "linear": last["linear_updates"],
+                                  "fp64_path": st64["cell_updates"]},
+        "res_rel_final": last["res_l2_final"] / last["f_l2"],
+        "roofline": roof,
+        "clocks": ck,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * n},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

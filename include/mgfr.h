@@ -1,0 +1,151 @@
+/*
+ * mgfr.h -- C ABI of the GB300 f(R) modified-gravity field solver.
+ *
+ * The library solves the quasi-static scalar-field equation of Hu-Sawicki
+ * f(R) gravity in the log variable u = ln(f_R / fR_bar(a)) (Puchwein, Baldi &
+ * Springel, arXiv:1305.2418, Sec. 3.2, eqs. fR_u and u_field_eq) with
+ * red-black Newton-Gauss-Seidel relaxation accelerated by FAS multigrid
+ * (Sec. 3.3, eqs. iterative_correction, u_coarse_grid, fine_correction), on a
+ * periodic base grid or on a hierarchy refined where particle counts are high
+ * (Sec. 3.1), and returns f_R = fR_bar e^u and the extra acceleration
+ * a_MG = (c^2/2) grad f_R (Sec. 2, eq. modgrav_accel).
+ *
+ * Conventions shared by every entry point:
+ *  - Lengths are comoving Mpc/h; positions are wrapped periodically into
+ *    [0, box).  The model is flat LCDM background (Omega_L = 1 - Omega_m)
+ *    with fR_bar0 = -fr0_abs < 0.
+ *  - The discrete equation, in comoving units, is
+ *      L_i(u) = (1/h^2) sum_{6 nbrs j} (e^{u_j} + e^{u_i})/2 (u_j - u_i)
+ *               + alpha Rt (1 - e^{-u_i/(n+1)})  =  f_i = -alpha Om a^-3 delta_i,
+ *    Rt = Om a^-3 + 4 OL, fR_bar(a) = -fr0_abs (Rt(1)/Rt(a))^{n+1},
+ *    alpha = a^2 (H0/c)^2 / fR_bar(a)  (Sec. 3.2 divided by a^-2).
+ *  - A solve stops when ||f - L(u)||_2 <= tol_rel ||f||_2 on the level being
+ *    solved (||f - L(0)||_2 = ||f||_2 is the zero-start residual).
+ *  - Output force unit: acc = a_MG / c^2 = grad_x f_R / (2a), in h/Mpc;
+ *    multiply by c^2 for physical units.
+ *  - Dense grids are C order a[i][j][k] with i along x (slowest), k along z.
+ *    Grid force arrays are component-major [3][N^3]; particle arrays are
+ *    [Np][3].
+ *  - Memory: every pointer named *_dev is device memory owned by the caller;
+ *    it must stay valid until the call returns.  The library allocates its
+ *    own workspaces inside the context (freed by mgfr_destroy).  Work runs on
+ *    the context's stream (given at mgfr_create; 0 = legacy default stream)
+ *    and every solve call returns only after its results are written.
+ *  - Errors: every call returns an mgfr_status and never aborts; the text of
+ *    the last error is available from mgfr_last_error.  Kernel waits are
+ *    bounded; no call traps the GPU.
+ */
+#ifndef MGFR_H
+#define MGFR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mgfr_ctx mgfr_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  MGFR_OK = 0,
+  MGFR_E_INVALID = 1,     /* bad argument (size, NaN, pointer, parameter) */
+  MGFR_E_CUDA = 2,        /* a CUDA runtime call failed                   */
+  MGFR_E_OOM = 3,         /* device workspace allocation failed           */
+  MGFR_E_NOCONVERGE = 4,  /* max_vcycles reached; outputs hold last iterate */
+  MGFR_E_TIMEOUT = 5,     /* a bounded device wait gave up                */
+  MGFR_E_UNSUPPORTED = 6  /* feature not available in this build           */
+} mgfr_status;
+
+typedef enum { MGFR_PREC_FP64 = 0, MGFR_PREC_MIXED = 1 } mgfr_precision;
+
+typedef struct {
+  /* model (Sec. 2) */
+  double omega_m;      /* matter density parameter; Omega_L = 1 - omega_m  */
+  double fr0_abs;      /* |fR_bar0| > 0                                     */
+  int n;               /* Hu-Sawicki exponent n >= 1                        */
+  /* solver (Sec. 3.3) */
+  int precision;       /* mgfr_precision                                    */
+  double tol_rel;      /* stopping test, default 1e-8                       */
+  int n_pre, n_post;   /* red-black sweeps before/after the coarse grid     */
+  int max_vcycles;     /* per level solve, default 100                      */
+  int prolong_linear;  /* 1: linear reconstruction, 0: straight injection   */
+  double step_cap;     /* clamp on a Newton step |du| (default 2)           */
+  /* refinement (Sec. 3.1) */
+  int max_level;       /* number of refinement levels above the base       */
+  int refine_count;    /* a cell is refined when it holds > refine_count    */
+  /* mixed precision: FP32 nonlinear V-cycles until the relative residual is
+   * below mixed_switch, then FP64 defect-correction iterations, each with
+   * mixed_inner FP32 linear V-cycles on the Jacobian system.               */
+  double mixed_switch; /* default 1e-5                                      */
+  int mixed_inner;     /* default 1                                         */
+  long long max_spins; /* bound on any device-side wait (default 1<<26)     */
+  int profile;         /* 1: time the base-level sweep kernels with CUDA
+                          events recorded around each launch (see stats)   */
+} mgfr_config;
+
+typedef struct {
+  int vcycles;               /* nonlinear V-cycles (all precisions), base level */
+  int outer_iters;           /* FP64 defect-correction iterations (mixed)  */
+  long long cell_updates;    /* nonlinear NGS updates, all levels          */
+  long long linear_updates;  /* FP32 linear Gauss-Seidel updates (mixed)   */
+  double res_l2_init;        /* ||f - L(u0)||_2 on the base level          */
+  double res_l2_final;       /* ||f - L(u)||_2 on the base level           */
+  double res_max_final;      /* max |f - L(u)| on the base level           */
+  double f_l2;               /* ||f||_2 on the base level                  */
+  double t_total_ms;         /* wall time of the call                      */
+  double t_solve_ms;         /* time of the base-level solve               */
+  int n_levels;              /* levels of the hierarchy (1 = base only)    */
+  long long cells_per_level[16];
+  long long octs_per_level[16];
+  int level_iters[16];       /* V-cycles (or sweeps) per refined level     */
+  double level_res[16];      /* final relative residual per level          */
+  /* per-kernel device time with cfg.profile = 1 (0 otherwise):
+   * [0] nonlinear NGS half-sweeps on the base level (FP64 or FP32),
+   * [1] FP32 linear Gauss-Seidel half-sweeps on the base level (mixed),
+   * [2] FP64 residual on the base level (mixed, phase B),
+   * [3] refined-level relaxation sweeps.                                   */
+  double kern_ms[4];
+  long long kern_launches[4];
+  long long gpu_launches;    /* kernels this call launched (graph nodes included) */
+} mgfr_stats;
+
+/* Fill *cfg with the defaults above (omega_m 0.3, fr0_abs 1e-5, n 1, FP64,
+ * tol 1e-8, 2+2 sweeps, 100 V-cycles, linear prolongation, step cap 2,
+ * max_level 0, refine_count 8, mixed_switch 1e-5, mixed_inner 1). */
+void mgfr_config_default(mgfr_config* cfg);
+
+/* Create a context on CUDA device `device`, working on `cuda_stream`
+ * (a cudaStream_t; NULL = default stream).  Validates cfg. */
+mgfr_status mgfr_create(mgfr_ctx** out, const mgfr_config* cfg, int device, void* cuda_stream);
+
+/* Replace the configuration of an existing context (validated). */
+mgfr_status mgfr_set_config(mgfr_ctx* ctx, const mgfr_config* cfg);
+
+/*
+ * Solve on a periodic N^3 grid given the density contrast (Sec. 3.2-3.3).
+ *   delta_dev   [N^3] FP64 density contrast rho/rho_bar - 1 (C order).
+ *   N           power of two, 8 <= N <= 1024.   box > 0, a > 0.
+ *   u_init_dev  [N^3] FP64 initial guess for u, or NULL for u = 0
+ *               (the previous-step warm start of Sec. 3.3, step 2).
+ *   fr_out_dev  [N^3] FP64 f_R (required).
+ *   acc_out_dev [3][N^3] FP64 a_MG / c^2, or NULL.
+ *   u_out_dev   [N^3] FP64 solution u, or NULL.
+ *   st          statistics, or NULL.
+ * Returns MGFR_E_NOCONVERGE (outputs filled from the last iterate) when the
+ * stopping test fails within max_vcycles.
+ */
+mgfr_status mgfr_solve_density(mgfr_ctx* ctx, const double* delta_dev, int N, double box, double a,
+                               const double* u_init_dev, double* fr_out_dev, double* acc_out_dev,
+                               double* u_out_dev, mgfr_stats* st);
+
+/* Text of the last error seen by this context ("" if none). */
+const char* mgfr_last_error(const mgfr_ctx* ctx);
+
+/* Release the context and its device workspaces (NULL is accepted). */
+void mgfr_destroy(mgfr_ctx* ctx);
+
+/* Library version string. */
+const char* mgfr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGFR_H */

@@ -1,0 +1,505 @@
+// dense_f32.cu -- mixed-precision kernels for dense periodic levels.
+//
+// Phase A (FP32 nonlinear FAS): the same Newton-Gauss-Seidel update, FAS
+// restriction/right-hand side/correction as the FP64 path (Puchwein, Baldi &
+// Springel 2013, Sec. 3.3), in FP32, with e^u recomputed on the fly by the
+// SFU instead of stored.  These are HBM-bound: a half-sweep streams u and f
+// once and writes u once.
+//
+// Phase B (defect correction): r = f - L(u) in FP64 on the FP64 iterate, then
+// the linearised system J(u) e = r (J the Jacobian of the discrete L) is
+// relaxed by an FP32 linear multigrid V-cycle and u += e in FP64.  Solving
+// the linearised correction in FP32 avoids the ~1e-7 cancellation floor of a
+// nonlinear FP32 correction.
+#include <algorithm>
+
+#include "mgfr_internal.cuh"
+
+namespace {
+
+constexpr int BS = 256;
+
+__device__ __forceinline__ long long cidx(int i, int j, int k, int lg) {
+  return ((((long long)i << lg) + j) << lg) + k;
+}
+
+struct ModelF {
+  float aRt, aRt_np1, inv_np1;
+};
+
+__host__ __device__ inline ModelF to_f(const Model& m) {
+  return ModelF{(float)m.aRt, (float)m.aRt_np1, (float)m.inv_np1};
+}
+
+// Loads the float pair (k0 = 2kp, k1 = 2kp+1) of row (i,j) and the two
+// z-neighbours outside the pair (k0-1 and k1+1), using warp shuffles inside a
+// row and direct loads at warp and row edges (periodic in k).
+struct Pair {
+  float2 c;
+  float km, kp;  // u[k0-1], u[k1+1]
+};
+
+__device__ __forceinline__ Pair load_pair(const float* __restrict__ u, long long rowbase, int kp,
+                                          int np, int lane) {
+  const float2* u2 = reinterpret_cast<const float2*>(u + rowbase);
+  Pair p;
+  p.c = u2[kp];
+  float up = __shfl_up_sync(0xffffffffu, p.c.y, 1);
+  float dn = __shfl_down_sync(0xffffffffu, p.c.x, 1);
+  const int N = 2 * np;
+  p.km = (kp == 0 || lane == 0) ? u[rowbase + ((2 * kp - 1 + N) & (N - 1))] : up;
+  p.kp = (kp == np - 1 || lane == 31) ? u[rowbase + ((2 * kp + 2) & (N - 1))] : dn;
+  return p;
+}
+
+// ---- Phase A: nonlinear FP32 Newton-Gauss-Seidel half-sweep ----------------
+// Thread = one z-pair (2kp, 2kp+1) of one (i,j) row; it updates the pair's
+// cell of the active colour and writes the whole pair back (full sectors).
+__global__ void __launch_bounds__(BS) k_sweep32(float* __restrict__ u, const float* __restrict__ f,
+                                                int lg, int colour, ModelF m, float ih2,
+                                                float cap) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int N = 1 << lg, M = N - 1, np = N >> 1;
+  const bool live = t < (1LL << (3 * lg - 1));
+  const long long tt = live ? t : 0;
+  const int kp = (int)(tt & (np - 1));
+  const long long rr = tt >> (lg - 1);
+  const int j = (int)(rr & M), i = (int)(rr >> lg);
+  const long long row = cidx(i, j, 0, lg);
+  const int lane = threadIdx.x & 31;
+  Pair p = load_pair(u, row, kp, np, lane);
+  if (!live) return;
+  const int odd = (i + j + colour) & 1;  // active cell is k0 + odd
+  const float2* u2 = reinterpret_cast<const float2*>(u);
+  const long long q = row / 2 + kp;
+  const float2 a = u2[cidx((i - 1) & M, j, 0, lg) / 2 + kp];
+  const float2 b = u2[cidx((i + 1) & M, j, 0, lg) / 2 + kp];
+  const float2 c = u2[cidx(i, (j - 1) & M, 0, lg) / 2 + kp];
+  const float2 d = u2[cidx(i, (j + 1) & M, 0, lg) / 2 + kp];
+  float uc, nb[6];
+  if (odd) {
+    uc = p.c.y;
+    nb[0] = a.y; nb[1] = b.y; nb[2] = c.y; nb[3] = d.y; nb[4] = p.c.x; nb[5] = p.kp;
+  } else {
+    uc = p.c.x;
+    nb[0] = a.x; nb[1] = b.x; nb[2] = c.x; nb[3] = d.x; nb[4] = p.km; nb[5] = p.c.y;
+  }
+  const float Ec = __expf(uc);
+  float sbd = 0.f, sd = 0.f, sb = 0.f;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const float bb = 0.5f * (__expf(nb[e]) + Ec), du = nb[e] - uc;
+    sbd = fmaf(bb, du, sbd);
+    sd += du;
+    sb += bb;
+  }
+  const float s = __expf(-uc * m.inv_np1);
+  const float L = sbd * ih2 + m.aRt * (1.f - s);
+  const float dL = (0.5f * Ec * sd - sb) * ih2 + m.aRt_np1 * s;
+  float step = __fdividef(L - f[row + 2 * kp + odd], dL);
+  step = fminf(fmaxf(step, -cap), cap);
+  float2 out = p.c;
+  if (odd) out.y = uc - step; else out.x = uc - step;
+  reinterpret_cast<float2*>(u)[q] = out;
+}
+
+__device__ __forceinline__ float Lpoint32(const float* __restrict__ u, int i, int j, int k, int lg,
+                                          const ModelF& m, float ih2) {
+  const int M = (1 << lg) - 1;
+  const float uc = u[cidx(i, j, k, lg)], Ec = __expf(uc);
+  const float nb[6] = {u[cidx((i - 1) & M, j, k, lg)], u[cidx((i + 1) & M, j, k, lg)],
+                       u[cidx(i, (j - 1) & M, k, lg)], u[cidx(i, (j + 1) & M, k, lg)],
+                       u[cidx(i, j, (k - 1) & M, lg)], u[cidx(i, j, (k + 1) & M, lg)]};
+  float sbd = 0.f;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) sbd = fmaf(0.5f * (__expf(nb[e]) + Ec), nb[e] - uc, sbd);
+  return sbd * ih2 + m.aRt * (1.f - __expf(-uc * m.inv_np1));
+}
+
+__device__ __forceinline__ void block_partial(double ss, double mx, double* __restrict__ partials) {
+  __shared__ double s1[BS / 32], s2[BS / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s1[threadIdx.x >> 5] = ss;
+    s2[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) {
+      a += s1[w];
+      b = fmax(b, s2[w]);
+    }
+    partials[2 * blockIdx.x] = a;
+    partials[2 * blockIdx.x + 1] = b;
+  }
+}
+
+// Restrict u and the FP32 residual (8-daughter average); the residual norm of
+// the fine level is accumulated too (used on the finest level only).
+__global__ void __launch_bounds__(BS) k_restrict32(const float* __restrict__ u,
+                                                   const float* __restrict__ f, int lgf,
+                                                   float* __restrict__ uc, float* __restrict__ ucold,
+                                                   float* __restrict__ fc, ModelF m, float ih2) {
+  const int lgc = lgf - 1, Nc = 1 << lgc;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (1LL << (3 * lgc))) return;
+  const int K = (int)(t & (Nc - 1)), J = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
+  float su = 0.f, sr = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int i = 2 * I + (q >> 2), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q & 1);
+    const long long c = cidx(i, j, k, lgf);
+    su += u[c];
+    sr += f[c] - Lpoint32(u, i, j, k, lgf, m, ih2);
+  }
+  uc[t] = 0.125f * su;
+  ucold[t] = 0.125f * su;
+  fc[t] = 0.125f * sr;
+}
+
+__global__ void __launch_bounds__(BS) k_fas_rhs32(const float* __restrict__ u, float* __restrict__ f,
+                                                  int lg, ModelF m, float ih2) {
+  const int N = 1 << lg;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (1LL << (3 * lg))) return;
+  const int k = (int)(t & (N - 1)), j = (int)((t >> lg) & (N - 1)), i = (int)(t >> (2 * lg));
+  f[t] += Lpoint32(u, i, j, k, lg, m, ih2);
+}
+
+// fine += P(coarse - coarse_old) (linear or injection); `sub` selects whether
+// coarse_old is subtracted (nonlinear FAS) or not (linear correction scheme).
+__global__ void __launch_bounds__(BS) k_prolong32(float* __restrict__ u, const float* __restrict__ uc,
+                                                  const float* __restrict__ ucold, int lgf,
+                                                  int linear) {
+  const int N = 1 << lgf, lgc = lgf - 1, Mc = (N >> 1) - 1;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (1LL << (3 * lgf))) return;
+  const int k = (int)(t & (N - 1)), j = (int)((t >> lgf) & (N - 1)), i = (int)(t >> (2 * lgf));
+  const int I = i >> 1, J = j >> 1, K = k >> 1;
+  auto corr = [&](int a, int b, int c) {
+    const long long q = cidx(a & Mc, b & Mc, c & Mc, lgc);
+    return ucold ? uc[q] - ucold[q] : uc[q];
+  };
+  float v = corr(I, J, K);
+  if (linear) {
+    const float sx = (i & 1) ? 0.125f : -0.125f, sy = (j & 1) ? 0.125f : -0.125f,
+                sz = (k & 1) ? 0.125f : -0.125f;
+    v += sx * (corr(I + 1, J, K) - corr(I - 1, J, K));
+    v += sy * (corr(I, J + 1, K) - corr(I, J - 1, K));
+    v += sz * (corr(I, J, K + 1) - corr(I, J, K - 1));
+  }
+  u[t] += v;
+}
+
+__global__ void __launch_bounds__(64) k_coarse32(float* __restrict__ ug, const float* __restrict__ fg,
+                                                 ModelF m, float ih2, float cap, int sweeps) {
+  __shared__ float u[64];
+  const int t = threadIdx.x;
+  u[t] = ug[t];
+  const float fc = fg[t];
+  const int i = t >> 4, j = (t >> 2) & 3, k = t & 3, colour = (i + j + k) & 1;
+  const int nb[6] = {(((i + 3) & 3) << 4) | (j << 2) | k, (((i + 1) & 3) << 4) | (j << 2) | k,
+                     (i << 4) | (((j + 3) & 3) << 2) | k, (i << 4) | (((j + 1) & 3) << 2) | k,
+                     (i << 4) | (j << 2) | ((k + 3) & 3), (i << 4) | (j << 2) | ((k + 1) & 3)};
+  __syncthreads();
+  for (int s = 0; s < sweeps; ++s)
+    for (int c = 0; c < 2; ++c) {
+      if (colour == c) {
+        const float uc = u[t], Ec = __expf(uc);
+        float sbd = 0.f, sd = 0.f, sb = 0.f;
+        for (int q = 0; q < 6; ++q) {
+          const float un = u[nb[q]], b = 0.5f * (__expf(un) + Ec), du = un - uc;
+          sbd = fmaf(b, du, sbd);
+          sd += du;
+          sb += b;
+        }
+        const float sN = __expf(-uc * m.inv_np1);
+        const float L = sbd * ih2 + m.aRt * (1.f - sN);
+        const float dL = (0.5f * Ec * sd - sb) * ih2 + m.aRt_np1 * sN;
+        float step = (L - fc) / dL;
+        step = fminf(fmaxf(step, -cap), cap);
+        u[t] = uc - step;
+      }
+      __syncthreads();
+    }
+  ug[t] = u[t];
+}
+
+// FP32 residual norm on the finest level (phase A stopping test).
+__global__ void __launch_bounds__(BS) k_norm32(const float* __restrict__ u, const float* __restrict__ f,
+                                               int lg, long long n, ModelF m, float ih2,
+                                               double* __restrict__ partials) {
+  double ss = 0.0, mx = 0.0;
+  const int N = 1 << lg;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(t & (N - 1)), j = (int)((t >> lg) & (N - 1)), i = (int)(t >> (2 * lg));
+    const double r = (double)(f[t] - Lpoint32(u, i, j, k, lg, m, ih2));
+    ss = fma(r, r, ss);
+    mx = fmax(mx, fabs(r));
+  }
+  block_partial(ss, mx, partials);
+}
+
+__global__ void k_from64(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < n) y[t] = (float)x[t];
+}
+
+__global__ void k_to64(const float* __restrict__ u32, double* __restrict__ u, double* __restrict__ E,
+                       long long n) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double v = (double)u32[t];
+  u[t] = v;
+  E[t] = exp(v);
+}
+
+// ---- Phase B ---------------------------------------------------------------
+__device__ __forceinline__ double nl_s64(double u, double E, int n, double inv_np1) {
+  return n == 1 ? rsqrt(E) : exp(-u * inv_np1);
+}
+
+// r = f - L(u) in FP64 on the FP64 iterate; stores r and u rounded to FP32,
+// zeroes the correction e, and accumulates the norms.
+__global__ void __launch_bounds__(BS) k_resid64(const double* __restrict__ u,
+                                                const double* __restrict__ E,
+                                                const double* __restrict__ f, int lg, Model m,
+                                                double ih2, float* __restrict__ r32,
+                                                float* __restrict__ u32, float* __restrict__ e32,
+                                                double* __restrict__ partials) {
+  const int N = 1 << lg, M = N - 1;
+  const long long n = 1LL << (3 * lg);
+  double ss = 0.0, mx = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(t & M), j = (int)((t >> lg) & M), i = (int)(t >> (2 * lg));
+    const long long nb[6] = {cidx((i - 1) & M, j, k, lg), cidx((i + 1) & M, j, k, lg),
+                             cidx(i, (j - 1) & M, k, lg), cidx(i, (j + 1) & M, k, lg),
+                             cidx(i, j, (k - 1) & M, lg), cidx(i, j, (k + 1) & M, lg)};
+    const double uc = u[t], Ec = E[t];
+    double sbd = 0.0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sbd = fma(0.5 * (E[nb[q]] + Ec), u[nb[q]] - uc, sbd);
+    const double r = f[t] - (sbd * ih2 + m.aRt * (1.0 - nl_s64(uc, Ec, m.n, m.inv_np1)));
+    r32[t] = (float)r;
+    u32[t] = (float)uc;
+    e32[t] = 0.f;
+    ss = fma(r, r, ss);
+    mx = fmax(mx, fabs(r));
+  }
+  block_partial(ss, mx, partials);
+}
+
+// Jacobian of L at u (neighbours j of cell i):
+//   dL_i/du_j = (E_j (u_j - u_i) + E_i + E_j) / (2 h^2),
+//   dL_i/du_i = sum_j (E_i (u_j - u_i) - E_i - E_j) / (2 h^2)
+//               + alpha Rt/(n+1) e^{-u_i/(n+1)}.
+struct Jrow {
+  float off[6], diag;
+};
+
+__device__ __forceinline__ Jrow jac_row(float uc, const float* nb, const ModelF& m, float ih2) {
+  Jrow J;
+  const float Ec = __expf(uc);
+  float d = 0.f;
+  const float h2 = 0.5f * ih2;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const float En = __expf(nb[q]), du = nb[q] - uc;
+    J.off[q] = h2 * fmaf(En, du, Ec + En);
+    d += fmaf(Ec, du, -Ec - En);
+  }
+  J.diag = d * h2 + m.aRt_np1 * __expf(-uc * m.inv_np1);
+  return J;
+}
+
+__device__ __forceinline__ void nb6(const float* __restrict__ x, int i, int j, int k, int lg,
+                                    float* out) {
+  const int M = (1 << lg) - 1;
+  out[0] = x[cidx((i - 1) & M, j, k, lg)];
+  out[1] = x[cidx((i + 1) & M, j, k, lg)];
+  out[2] = x[cidx(i, (j - 1) & M, k, lg)];
+  out[3] = x[cidx(i, (j + 1) & M, k, lg)];
+  out[4] = x[cidx(i, j, (k - 1) & M, lg)];
+  out[5] = x[cidx(i, j, (k + 1) & M, lg)];
+}
+
+// Gauss-Seidel half-sweep on J e = r: e_i = (r_i - sum_j J_ij e_j) / J_ii.
+__global__ void __launch_bounds__(BS) k_lin_sweep(float* __restrict__ e, const float* __restrict__ r,
+                                                  const float* __restrict__ u, int lg, int colour,
+                                                  ModelF m, float ih2) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int N = 1 << lg, M = N - 1;
+  if (t >= (1LL << (3 * lg - 1))) return;
+  const int k2 = (int)(t & ((N >> 1) - 1));
+  const long long rr = t >> (lg - 1);
+  const int j = (int)(rr & M), i = (int)(rr >> lg);
+  const int k = 2 * k2 + ((i + j + colour) & 1);
+  const long long c = cidx(i, j, k, lg);
+  float un[6], en[6];
+  nb6(u, i, j, k, lg, un);
+  nb6(e, i, j, k, lg, en);
+  const Jrow J = jac_row(u[c], un, m, ih2);
+  float s = r[c];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) s = fmaf(-J.off[q], en[q], s);
+  e[c] = __fdividef(s, J.diag);
+}
+
+// Coarse linear problem: r_c = R(r - J e), u_c = R(u), e_c = 0.
+__global__ void __launch_bounds__(BS) k_lin_restrict(const float* __restrict__ e,
+                                                     const float* __restrict__ r,
+                                                     const float* __restrict__ u, int lgf,
+                                                     float* __restrict__ ec, float* __restrict__ rc,
+                                                     float* __restrict__ uc, ModelF m, float ih2) {
+  const int lgc = lgf - 1, Nc = 1 << lgc;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (1LL << (3 * lgc))) return;
+  const int K = (int)(t & (Nc - 1)), J = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
+  float su = 0.f, sr = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int i = 2 * I + (q >> 2), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q & 1);
+    const long long c = cidx(i, j, k, lgf);
+    float un[6], en[6];
+    nb6(u, i, j, k, lgf, un);
+    nb6(e, i, j, k, lgf, en);
+    const Jrow Jr = jac_row(u[c], un, m, ih2);
+    float Je = Jr.diag * e[c];
+    for (int p = 0; p < 6; ++p) Je = fmaf(Jr.off[p], en[p], Je);
+    sr += r[c] - Je;
+    su += u[c];
+  }
+  uc[t] = 0.125f * su;
+  rc[t] = 0.125f * sr;
+  ec[t] = 0.f;
+}
+
+__global__ void __launch_bounds__(64) k_lin_coarse(float* __restrict__ eg, const float* __restrict__ rg,
+                                                   const float* __restrict__ ug, ModelF m, float ih2,
+                                                   int sweeps) {
+  __shared__ float e[64];
+  const int t = threadIdx.x;
+  const int i = t >> 4, j = (t >> 2) & 3, k = t & 3, colour = (i + j + k) & 1;
+  const int nb[6] = {(((i + 3) & 3) << 4) | (j << 2) | k, (((i + 1) & 3) << 4) | (j << 2) | k,
+                     (i << 4) | (((j + 3) & 3) << 2) | k, (i << 4) | (((j + 1) & 3) << 2) | k,
+                     (i << 4) | (j << 2) | ((k + 3) & 3), (i << 4) | (j << 2) | ((k + 1) & 3)};
+  float un[6];
+  for (int q = 0; q < 6; ++q) un[q] = ug[nb[q]];
+  const Jrow J = jac_row(ug[t], un, m, ih2);
+  const float rc = rg[t];
+  e[t] = eg[t];
+  __syncthreads();
+  for (int s = 0; s < sweeps; ++s)
+    for (int c = 0; c < 2; ++c) {
+      if (colour == c) {
+        float acc = rc;
+        for (int q = 0; q < 6; ++q) acc = fmaf(-J.off[q], e[nb[q]], acc);
+        e[t] = acc / J.diag;
+      }
+      __syncthreads();
+    }
+  eg[t] = e[t];
+}
+
+__global__ void k_apply_corr(double* __restrict__ u, double* __restrict__ E,
+                             const float* __restrict__ e, long long n, double cap) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double d = fmin(fmax((double)e[t], -cap), cap);
+  const double v = u[t] + d;
+  u[t] = v;
+  E[t] = exp(v);
+}
+
+__global__ void k_zero(float* __restrict__ x, long long n) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < n) x[t] = 0.f;
+}
+
+__global__ void k_finish32(const double* __restrict__ partials, int nparts, double* __restrict__ out) {
+  __shared__ double s1[256], s2[256];
+  double a = 0.0, b = 0.0;
+  for (int q = threadIdx.x; q < nparts; q += blockDim.x) {
+    a += partials[2 * q];
+    b = fmax(b, partials[2 * q + 1]);
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      s1[threadIdx.x] += s1[threadIdx.x + w];
+      s2[threadIdx.x] = fmax(s2[threadIdx.x], s2[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = s1[0];
+    out[1] = s2[0];
+  }
+}
+
+}  // namespace
+
+namespace f32 {
+
+void from64(const double* x, float* y, long long n, cudaStream_t s) {
+  k_from64<<<nblocks(n, BS), BS, 0, s>>>(x, y, n);
+}
+void to64(DenseLevel& L, cudaStream_t s) { k_to64<<<nblocks(L.n, BS), BS, 0, s>>>(L.u32, L.u, L.E, L.n); }
+
+void sweep(DenseLevel& L, const Model& m, int colour, float cap, cudaStream_t s) {
+  k_sweep32<<<nblocks(L.n / 2, BS), BS, 0, s>>>(L.u32, L.f32, L.lg, colour, to_f(m), (float)L.ih2,
+                                                cap);
+}
+void restrict_resid(DenseLevel& F, DenseLevel& C, const Model& m, double*, int, cudaStream_t s) {
+  k_restrict32<<<nblocks(C.n, BS), BS, 0, s>>>(F.u32, F.f32, F.lg, C.u32, C.uold32, C.f32, to_f(m),
+                                                (float)F.ih2);
+}
+void fas_rhs(DenseLevel& C, const Model& m, cudaStream_t s) {
+  k_fas_rhs32<<<nblocks(C.n, BS), BS, 0, s>>>(C.u32, C.f32, C.lg, to_f(m), (float)C.ih2);
+}
+void prolong_corr(DenseLevel& F, DenseLevel& C, int linear, cudaStream_t s) {
+  k_prolong32<<<nblocks(F.n, BS), BS, 0, s>>>(F.u32, C.u32, C.uold32, F.lg, linear);
+}
+void coarse_solve(DenseLevel& C, const Model& m, float cap, int sweeps, cudaStream_t s) {
+  k_coarse32<<<1, 64, 0, s>>>(C.u32, C.f32, to_f(m), (float)C.ih2, cap, sweeps);
+}
+void norm32(DenseLevel& L, const Model& m, double* partials, int nparts, double* out,
+            cudaStream_t s) {
+  int nb = (int)std::min<long long>(nparts, nblocks(L.n, BS));
+  k_norm32<<<nb, BS, 0, s>>>(L.u32, L.f32, L.lg, L.n, to_f(m), (float)L.ih2, partials);
+  k_finish32<<<1, 256, 0, s>>>(partials, nb, out);
+}
+void resid64(DenseLevel& L, const Model& m, double* partials, int nparts, double* out,
+             cudaStream_t s) {
+  int nb = (int)std::min<long long>(nparts, nblocks(L.n, BS));
+  k_resid64<<<nb, BS, 0, s>>>(L.u, L.E, L.f, L.lg, m, L.ih2, L.r32, L.u32, L.e32, partials);
+  k_finish32<<<1, 256, 0, s>>>(partials, nb, out);
+}
+void lin_sweep(DenseLevel& L, const Model& m, int colour, cudaStream_t s) {
+  k_lin_sweep<<<nblocks(L.n / 2, BS), BS, 0, s>>>(L.e32, L.r32, L.u32, L.lg, colour, to_f(m),
+                                                  (float)L.ih2);
+}
+void lin_restrict(DenseLevel& F, DenseLevel& C, const Model& m, cudaStream_t s) {
+  k_lin_restrict<<<nblocks(C.n, BS), BS, 0, s>>>(F.e32, F.r32, F.u32, F.lg, C.e32, C.r32, C.u32,
+                                                 to_f(m), (float)F.ih2);
+}
+void lin_prolong(DenseLevel& F, DenseLevel& C, int linear, cudaStream_t s) {
+  k_prolong32<<<nblocks(F.n, BS), BS, 0, s>>>(F.e32, C.e32, nullptr, F.lg, linear);
+}
+void lin_coarse(DenseLevel& C, const Model& m, int sweeps, cudaStream_t s) {
+  k_lin_coarse<<<1, 64, 0, s>>>(C.e32, C.r32, C.u32, to_f(m), (float)C.ih2, sweeps);
+}
+void zero(float* x, long long n, cudaStream_t s) { k_zero<<<nblocks(n, BS), BS, 0, s>>>(x, n); }
+void apply_corr(DenseLevel& L, double cap, cudaStream_t s) {
+  k_apply_corr<<<nblocks(L.n, BS), BS, 0, s>>>(L.u, L.E, L.e32, L.n, cap);
+}
+
+}  // namespace f32

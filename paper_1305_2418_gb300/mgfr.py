@@ -1,0 +1,163 @@
+"""Thin ctypes binding of libmgfr.so (the C ABI declared in include/mgfr.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  Inputs and outputs are torch CUDA tensors (FP64, contiguous); the
+work is ordered on torch's current stream.  There is no CPU fallback: if the
+library is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libmgfr.so")
+
+MGFR_OK, MGFR_E_INVALID, MGFR_E_CUDA, MGFR_E_OOM, MGFR_E_NOCONVERGE, MGFR_E_TIMEOUT, \
+    MGFR_E_UNSUPPORTED = range(7)
+STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "NOCONVERGE", "TIMEOUT", "UNSUPPORTED"]
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("omega_m", C.c_double), ("fr0_abs", C.c_double), ("n", C.c_int),
+        ("precision", C.c_int), ("tol_rel", C.c_double), ("n_pre", C.c_int),
+        ("n_post", C.c_int), ("max_vcycles", C.c_int), ("prolong_linear", C.c_int),
+        ("step_cap", C.c_double), ("max_level", C.c_int), ("refine_count", C.c_int),
+        ("mixed_switch", C.c_double), ("mixed_inner", C.c_int), ("max_spins", C.c_longlong),
+        ("profile", C.c_int),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("vcycles", C.c_int), ("outer_iters", C.c_int), ("cell_updates", C.c_longlong),
+        ("linear_updates", C.c_longlong), ("res_l2_init", C.c_double),
+        ("res_l2_final", C.c_double), ("res_max_final", C.c_double), ("f_l2", C.c_double),
+        ("t_total_ms", C.c_double), ("t_solve_ms", C.c_double), ("n_levels", C.c_int),
+        ("cells_per_level", C.c_longlong * 16), ("octs_per_level", C.c_longlong * 16),
+        ("level_iters", C.c_int * 16), ("level_res", C.c_double * 16),
+        ("kern_ms", C.c_double * 4), ("kern_launches", C.c_longlong * 4),
+        ("gpu_launches", C.c_longlong),
+    ]
+
+    def to_dict(self) -> dict:
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+
+class MGFRError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mgfr {STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+# name -> (restype, argtypes); every symbol that include/mgfr.h declares.
+SIGNATURES = {
+    "mgfr_version": (C.c_char_p, []),
+    "mgfr_config_default": (None, [C.c_void_p]),
+    "mgfr_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "mgfr_set_config": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mgfr_solve_density": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p]),
+    "mgfr_last_error": (C.c_char_p, [C.c_void_p]),
+    "mgfr_destroy": (None, [C.c_void_p]),
+}
+
+
+def lib():
+    """Load libmgfr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_1305_2418_gb300.build")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def default_config(**kw) -> Config:
+    cfg = Config()
+    lib().mgfr_config_default(C.byref(cfg))
+    for k, v in kw.items():
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous(), "need contiguous CUDA FP64"
+    return C.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """A library context bound to one device and torch's current stream."""
+
+    def __init__(self, device: int = 0, stream=None, **cfg):
+        import torch
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        self.cfg = default_config(**cfg)
+        h = C.c_void_p()
+        st = lib().mgfr_create(C.byref(h), C.byref(self.cfg), device, C.c_void_p(stream.cuda_stream))
+        if st != MGFR_OK:
+            raise MGFRError(st, "mgfr_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mgfr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return lib().mgfr_last_error(self.h).decode()
+
+    def set_config(self, **kw):
+        for k, v in kw.items():
+            setattr(self.cfg, k, v)
+        st = lib().mgfr_set_config(self.h, C.byref(self.cfg))
+        if st != MGFR_OK:
+            raise MGFRError(st, self.last_error())
+
+    def _check(self, st, allow_noconverge=False):
+        if st == MGFR_OK or (allow_noconverge and st == MGFR_E_NOCONVERGE):
+            return st
+        raise MGFRError(st, self.last_error())
+
+    def solve_density(self, delta, box: float, a: float = 1.0, u_init=None, want_acc=True,
+                      want_u=False, allow_noconverge=False):
+        """f_R (and force, u) on a periodic N^3 grid from delta (mgfr_solve_density)."""
+        import torch
+        N = delta.shape[0]
+        fr = torch.empty_like(delta)
+        acc = torch.empty((3,) + tuple(delta.shape), dtype=delta.dtype, device=delta.device) \
+            if want_acc else None
+        u = torch.empty_like(delta) if want_u else None
+        stats = Stats()
+        st = lib().mgfr_solve_density(self.h, _ptr(delta), N, box, a, _ptr(u_init), _ptr(fr),
+                                      _ptr(acc), _ptr(u), C.byref(stats))
+        self._check(st, allow_noconverge)
+        return {"fr": fr, "acc": acc, "u": u, "stats": stats.to_dict(), "status": st}

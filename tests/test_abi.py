@@ -1,0 +1,75 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/*.h declares; the ctypes mirrors of the public structs match the C
+layout; argument validation needs no GPU.  CPU only (no compute calls)."""
+import ctypes as C
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1305_2418_gb300 import build, mgfr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return mgfr.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(mgfr_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 6
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in mgfr.SIGNATURES, n
+
+
+def test_struct_layout_matches_header(tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "mgfr.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(mgfr_config), sizeof(mgfr_stats),
+         offsetof(mgfr_config, profile), offsetof(mgfr_stats, kern_ms),
+         offsetof(mgfr_stats, level_res));
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert vals == [C.sizeof(mgfr.Config), C.sizeof(mgfr.Stats), mgfr.Config.profile.offset,
+                    mgfr.Stats.kern_ms.offset, mgfr.Stats.level_res.offset]
+
+
+def test_default_config_and_validation(lib):
+    cfg = mgfr.default_config()
+    assert cfg.omega_m == 0.3 and cfg.fr0_abs == 1e-5 and cfg.n == 1
+    assert cfg.tol_rel == 1e-8 and cfg.n_pre == 2 and cfg.n_post == 2
+    assert lib.mgfr_version().decode().startswith("mgfr")
+    bad = [dict(fr0_abs=0.0), dict(n=0), dict(tol_rel=2.0), dict(n_pre=0, n_post=0),
+           dict(precision=7), dict(omega_m=-1.0), dict(step_cap=0.0)]
+    for kw in bad:
+        c = mgfr.default_config(**kw)
+        h = C.c_void_p()
+        st = lib.mgfr_create(C.byref(h), C.byref(c), 0, None)
+        assert st == mgfr.MGFR_E_INVALID, kw
+        assert not h.value
+    assert lib.mgfr_last_error(None) == b"NULL context"
+    lib.mgfr_destroy(None)
