@@ -66,14 +66,19 @@ void prof_end(mgfr_ctx* c) {
 }
 
 void prof_collect(mgfr_ctx* c, int g, mgfr_stats* st) {
-  if (!st || !c->cfg.profile) return;
+  if (!c->cfg.profile) return;
   for (auto& r : c->prof[g]) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
-      st->kern_ms[r.fam] += ms;
-      st->kern_launches[r.fam] += 1;
+      if (st) {
+        st->kern_ms[r.fam] += ms;
+        st->kern_launches[r.fam] += 1;
+      }
+    } else {
+      (void)cudaGetLastError();
     }
   }
+  prof_clear(c, g);
 }
 
 long long count_kernel_nodes(cudaGraph_t g) {
@@ -245,19 +250,33 @@ static void vcycle64(mgfr_ctx* c, const Model& m, int l, long long& updates) {
 template <class Fn>
 mgfr_status capture(mgfr_ctx* c, int gid, cudaGraphExec_t* out, Fn body) {
   cudaGraph_t g = nullptr;
-  prof_clear(c, gid);
-  if (c->cfg.profile)
-    prof_reserve(c, 4 + 2 * (size_t)(c->cfg.n_pre + c->cfg.n_post) * (size_t)c->cfg.mixed_inner);
   MG_CK(c, cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
-  c->capturing = gid;
-  body();
   c->capturing = -1;
+  body();
   cudaError_t e = cudaStreamEndCapture(c->s, &g);
   if (e != cudaSuccess) return set_err(c, MGFR_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   c->graph_kernels[gid] = count_kernel_nodes(g);
   e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return set_err(c, MGFR_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return MGFR_OK;
+}
+
+// Issue one cycle: replay its graph, or with cfg.profile run the same launch
+// sequence directly on the stream with timing events around the profiled
+// kernels (events are not recorded inside graphs).
+template <class Fn>
+mgfr_status issue(mgfr_ctx* c, int gid, cudaGraphExec_t gx, Fn body) {
+  if (c->cfg.profile) {
+    prof_clear(c, gid);
+    prof_reserve(c, 4 + 2 * (size_t)(c->cfg.n_pre + c->cfg.n_post) * (size_t)c->cfg.mixed_inner);
+    c->capturing = gid;
+    body();
+    c->capturing = -1;
+  } else {
+    MG_CK(c, cudaGraphLaunch(gx, c->s));
+  }
+  c->launches += c->graph_kernels[gid];
   return MGFR_OK;
 }
 
@@ -293,15 +312,16 @@ mgfr_status dense_solve64(mgfr_ctx* c, const Model& m, double box, mgfr_stats* s
   long long updates_per = 0;
   char key[256];
   make_key(key, sizeof(key), "v64", H.N, box, m, g);
+  auto body64 = [&]() {
+    updates_per = 0;
+    vcycle64(c, m, 0, updates_per);
+    f64::resid_norm(L0, m, H.partials, H.nparts, H.scal, c->s);
+    cudaMemcpyAsync(hs, H.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+  };
   if (!c->g_v64 || std::strcmp(key, c->graph_key) != 0) {
     if (c->g_v64) cudaGraphExecDestroy(c->g_v64);
     c->g_v64 = nullptr;
-    mgfr_status cs = capture(c, 0, &c->g_v64, [&]() {
-      updates_per = 0;
-      vcycle64(c, m, 0, updates_per);
-      f64::resid_norm(L0, m, H.partials, H.nparts, H.scal, c->s);
-      cudaMemcpyAsync(hs, H.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s);
-    });
+    mgfr_status cs = capture(c, 0, &c->g_v64, body64);
     if (cs != MGFR_OK) return cs;
     std::strcpy(c->graph_key, key);
     c->updates_v64 = updates_per;
@@ -309,8 +329,7 @@ mgfr_status dense_solve64(mgfr_ctx* c, const Model& m, double box, mgfr_stats* s
   double r = r0;
   int it = 0;
   while (r > target && it < g.max_vcycles) {
-    MG_CK(c, cudaGraphLaunch(c->g_v64, c->s));
-    c->launches += c->graph_kernels[0];
+    if ((rs = issue(c, 0, c->g_v64, body64)) != MGFR_OK) return rs;
     rs = sync_read(c);
     if (rs != MGFR_OK) return rs;
     prof_collect(c, 0, st);
@@ -421,32 +440,34 @@ mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stat
   char key[256];
   make_key(key, sizeof(key), "v32", H.N, box, m, g);
   long long upd = 0;
+  auto body32 = [&]() {
+    upd = 0;
+    vcycle32(c, m, 0, upd);
+    f32::norm32(L0, m, H.partials, H.nparts, H.scal, c->s);
+    cudaMemcpyAsync(hs, H.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+  };
   if (!c->g_v32 || std::strcmp(key, c->key32) != 0) {
     if (c->g_v32) cudaGraphExecDestroy(c->g_v32);
     c->g_v32 = nullptr;
-    rs = capture(c, 1, &c->g_v32, [&]() {
-      upd = 0;
-      vcycle32(c, m, 0, upd);
-      f32::norm32(L0, m, H.partials, H.nparts, H.scal, c->s);
-      cudaMemcpyAsync(hs, H.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s);
-    });
+    rs = capture(c, 1, &c->g_v32, body32);
     if (rs != MGFR_OK) return rs;
     std::strcpy(c->key32, key);
     c->updates_v32 = upd;
   }
   make_key(key, sizeof(key), "lin", H.N, box, m, g);
+  auto bodylin = [&]() {
+    upd = 0;
+    for (int q = 0; q < g.mixed_inner; ++q) vcycle_lin(c, m, 0, upd);
+    f32::apply_corr(L0, g.step_cap, c->s);
+    prof_begin(c, 2);
+    f32::resid64(L0, m, H.partials, H.nparts, H.scal, c->s);
+    prof_end(c);
+    cudaMemcpyAsync(hs, H.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s);
+  };
   if (!c->g_lin || std::strcmp(key, c->keylin) != 0) {
     if (c->g_lin) cudaGraphExecDestroy(c->g_lin);
     c->g_lin = nullptr;
-    rs = capture(c, 2, &c->g_lin, [&]() {
-      upd = 0;
-      for (int q = 0; q < g.mixed_inner; ++q) vcycle_lin(c, m, 0, upd);
-      f32::apply_corr(L0, g.step_cap, c->s);
-      prof_begin(c, 2);
-      f32::resid64(L0, m, H.partials, H.nparts, H.scal, c->s);
-      prof_end(c);
-      cudaMemcpyAsync(hs, H.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s);
-    });
+    rs = capture(c, 2, &c->g_lin, bodylin);
     if (rs != MGFR_OK) return rs;
     std::strcpy(c->keylin, key);
     c->updates_lin = upd;
@@ -461,8 +482,7 @@ mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stat
   for (int round = 0; round < 8 && r > target; ++round) {
     double prev = -1.0;
     while (vc < g.max_vcycles) {
-      MG_CK(c, cudaGraphLaunch(c->g_v32, c->s));
-      c->launches += c->graph_kernels[1];
+      if ((rs = issue(c, 1, c->g_v32, body32)) != MGFR_OK) return rs;
       if ((rs = sync_read(c)) != MGFR_OK) return rs;
       prof_collect(c, 1, st);
       ++vc;
@@ -480,8 +500,7 @@ mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stat
     r = std::sqrt(hs[0]);
     bool rose = false;
     while (r > target && outer < g.max_vcycles) {
-      MG_CK(c, cudaGraphLaunch(c->g_lin, c->s));
-      c->launches += c->graph_kernels[2];
+      if ((rs = issue(c, 2, c->g_lin, bodylin)) != MGFR_OK) return rs;
       if ((rs = sync_read(c)) != MGFR_OK) return rs;
       prof_collect(c, 2, st);
       ++outer;
