@@ -79,6 +79,8 @@ typedef struct {
   long long max_spins; /* bound on any device-side wait (default 1<<26)     */
   int profile;         /* 1: time the base-level sweep kernels with CUDA
                           events recorded around each launch (see stats)   */
+  double mask_thres;   /* refined-level multigrid: coarse cells are relaxed
+                          where the mask exceeds this (Sec. 3.3; 0.4)      */
 } mgfr_config;
 
 typedef struct {
@@ -109,7 +111,8 @@ typedef struct {
 
 /* Fill *cfg with the defaults above (omega_m 0.3, fr0_abs 1e-5, n 1, FP64,
  * tol 1e-8, 2+2 sweeps, 100 V-cycles, linear prolongation, step cap 2,
- * max_level 0, refine_count 8, mixed_switch 1e-5, mixed_inner 1). */
+ * max_level 0, refine_count 8, mixed_switch 1e-5, mixed_inner 1,
+ * mask_thres 0.4). */
 void mgfr_config_default(mgfr_config* cfg);
 
 /* Create a context on CUDA device `device`, working on `cuda_stream`
@@ -135,6 +138,54 @@ mgfr_status mgfr_set_config(mgfr_ctx* ctx, const mgfr_config* cfg);
 mgfr_status mgfr_solve_density(mgfr_ctx* ctx, const double* delta_dev, int N, double box, double a,
                                const double* u_init_dev, double* fr_out_dev, double* acc_out_dev,
                                double* u_out_dev, mgfr_stats* st);
+
+/*
+ * Solve on the refined hierarchy built from particles (Sec. 3.1 and 3.3).
+ *   pos_dev      [Np][3] FP64 comoving positions (Mpc/h), wrapped into [0, box).
+ *   N_base       base grid size (power of two, 8..1024); cfg.max_level
+ *                refinement levels are added where a cell holds more than
+ *                cfg.refine_count particles (nearest-grid-point count), the
+ *                flags dilated by one cell over the 26 neighbours, each
+ *                flagged cell refined into a full oct of 8 daughters.
+ *   Masses: adaptive cloud-in-cell (cube of the particle's leaf-cell side),
+ *   summed into every coarser cell; delta_l = m N_l^3 / Np - 1 per level.
+ *   Solve: base level as mgfr_solve_density, then each refined level in turn
+ *   with ghost cells and initial guess prolonged from the converged coarser
+ *   level (one-way interface); the coarser solutions are not modified.
+ *   u_init_dev   [N_base^3] initial guess of the base level or NULL.
+ *   fr_base_out_dev [N_base^3] f_R on the base level, or NULL.
+ *   acc_out_dev  [Np][3] a_MG / c^2 at the particles, gathered from the leaf
+ *                cells with the mass-assignment weights, or NULL.
+ * The hierarchy and the per-level fields stay in the context until the next
+ * solve (see mgfr_get_level_*).  Returns MGFR_E_NOCONVERGE if a level missed
+ * its tolerance (outputs filled), MGFR_E_INVALID on a non-finite position.
+ */
+mgfr_status mgfr_solve_particles(mgfr_ctx* ctx, const double* pos_dev, long long Np, int N_base,
+                                 double box, double a, const double* u_init_dev,
+                                 double* fr_base_out_dev, double* acc_out_dev, mgfr_stats* st);
+
+/* Size of level `level` of the last particle solve: octs (0 on the base)
+ * and cells (N_base^3 on the base, 8 per oct above). */
+mgfr_status mgfr_get_level_info(mgfr_ctx* ctx, int level, long long* n_oct, long long* ncell);
+
+/* Parent key of every oct of refined level `level` >= 1, in storage order:
+ * the parent's linear index (I N_{l-1} + J) N_{l-1} + K on level l-1.
+ * keys_host: host array of n_oct entries.  Cell c of oct o is its daughter
+ * (di, dj, dk) with c = 8 o + 4 di + 2 dj + dk. */
+mgfr_status mgfr_get_level_keys(mgfr_ctx* ctx, int level, long long* keys_host);
+
+typedef enum {
+  MGFR_FIELD_U = 0,      /* u, [ncell]                                   */
+  MGFR_FIELD_FR = 1,     /* f_R, [ncell]                                 */
+  MGFR_FIELD_SOURCE = 2, /* f = -alpha Om a^-3 delta, [ncell]            */
+  MGFR_FIELD_MASS = 3,   /* deposited mass in particle masses, [ncell]   */
+  MGFR_FIELD_ACC = 4,    /* a_MG / c^2: base [3][ncell], refined [ncell][3] */
+  MGFR_FIELD_COUNT = 5   /* particles per cell (nearest grid point)      */
+} mgfr_field;
+
+/* Copy a per-level field of the last particle solve to host memory
+ * (out_host: ncell doubles, 3 ncell for MGFR_FIELD_ACC). */
+mgfr_status mgfr_get_level_field(mgfr_ctx* ctx, int level, int what, double* out_host);
 
 /* Text of the last error seen by this context ("" if none). */
 const char* mgfr_last_error(const mgfr_ctx* ctx);

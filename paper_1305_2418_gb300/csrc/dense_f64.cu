@@ -61,7 +61,8 @@ __global__ void k_init(const double* __restrict__ u0, double* __restrict__ u,
 // is clamped to |du| <= cap.
 __global__ void __launch_bounds__(BS) k_sweep(double* __restrict__ u, double* __restrict__ E,
                                               const double* __restrict__ f, int lg, int colour,
-                                              Model m, double ih2, double cap) {
+                                              Model m, double ih2, double cap,
+                                              const float* __restrict__ mask, float mthr) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int N = 1 << lg, M = N - 1;
   if (t >= (1LL << (3 * lg - 1))) return;
@@ -70,6 +71,7 @@ __global__ void __launch_bounds__(BS) k_sweep(double* __restrict__ u, double* __
   const int j = (int)(r & M), i = (int)(r >> lg);
   const int k = 2 * k2 + ((i + j + colour) & 1);
   const long long c = cidx(i, j, k, lg);
+  if (mask && !(mask[c] > mthr)) return;
   const long long nb[6] = {cidx((i - 1) & M, j, k, lg), cidx((i + 1) & M, j, k, lg),
                            cidx(i, (j - 1) & M, k, lg), cidx(i, (j + 1) & M, k, lg),
                            cidx(i, j, (k - 1) & M, lg), cidx(i, j, (k + 1) & M, lg)};
@@ -102,7 +104,8 @@ __global__ void __launch_bounds__(BS) k_restrict_resid(const double* __restrict_
                                                        double* __restrict__ Ec,
                                                        double* __restrict__ ucold,
                                                        double* __restrict__ fc, Model m,
-                                                       double ih2) {
+                                                       double ih2, const float* __restrict__ mask,
+                                                       float mthr) {
   const int lgc = lgf - 1, Nc = 1 << lgc;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (1LL << (3 * lgc))) return;
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(BS) k_restrict_resid(const double* __restrict_
     const int i = 2 * I + (q >> 2), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q & 1);
     const long long c = cidx(i, j, k, lgf);
     su += u[c];
-    sr += f[c] - Lpoint(u, E, i, j, k, lgf, m, ih2);
+    if (!mask || mask[c] > mthr) sr += f[c] - Lpoint(u, E, i, j, k, lgf, m, ih2);
   }
   const double um = 0.125 * su;
   uc[t] = um;
@@ -126,10 +129,12 @@ __global__ void __launch_bounds__(BS) k_restrict_resid(const double* __restrict_
 __global__ void __launch_bounds__(BS) k_fas_rhs(const double* __restrict__ u,
                                                 const double* __restrict__ E,
                                                 double* __restrict__ f, int lg, Model m,
-                                                double ih2) {
+                                                double ih2, const float* __restrict__ mask,
+                                                float mthr) {
   const int N = 1 << lg;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (1LL << (3 * lg))) return;
+  if (mask && !(mask[t] > mthr)) return;
   const int k = (int)(t & (N - 1)), j = (int)((t >> lg) & (N - 1)), i = (int)(t >> (2 * lg));
   f[t] += Lpoint(u, E, i, j, k, lg, m, ih2);
 }
@@ -140,10 +145,12 @@ __global__ void __launch_bounds__(BS) k_prolong_corr(double* __restrict__ u,
                                                      double* __restrict__ E,
                                                      const double* __restrict__ uc,
                                                      const double* __restrict__ ucold, int lgf,
-                                                     int linear) {
+                                                     int linear, const float* __restrict__ mask,
+                                                     float mthr) {
   const int N = 1 << lgf, lgc = lgf - 1, Mc = (N >> 1) - 1;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (1LL << (3 * lgf))) return;
+  if (mask && !(mask[t] > mthr)) return;
   const int k = (int)(t & (N - 1)), j = (int)((t >> lgf) & (N - 1)), i = (int)(t >> (2 * lgf));
   const int I = i >> 1, J = j >> 1, K = k >> 1;
   auto corr = [&](int a, int b, int c) {
@@ -168,9 +175,11 @@ __global__ void __launch_bounds__(BS) k_prolong_corr(double* __restrict__ u,
 // max_sweeps is reached (bounded loop).
 __global__ void __launch_bounds__(64) k_coarse(double* __restrict__ ug, double* __restrict__ Eg,
                                                const double* __restrict__ fg, Model m, double ih2,
-                                               double cap, int max_sweeps, double rel) {
+                                               double cap, int max_sweeps, double rel,
+                                               const float* __restrict__ mask, float mthr) {
   __shared__ double u[64], E[64], f[64], red[64];
   const int t = threadIdx.x;
+  const bool active = !mask || mask[t] > mthr;
   u[t] = ug[t];
   E[t] = Eg[t];
   f[t] = fg[t];
@@ -186,7 +195,7 @@ __global__ void __launch_bounds__(64) k_coarse(double* __restrict__ ug, double* 
     double sbd = 0.0;
     for (int q = 0; q < 6; ++q) sbd = fma(0.5 * (E[nb[q]] + E[t]), u[nb[q]] - u[t], sbd);
     const double rr = fabs(f[t] - (sbd * ih2 + m.aRt * (1.0 - nl_s(u[t], E[t], m))));
-    red[t] = rr;
+    red[t] = active ? rr : 0.0;
     __syncthreads();
     for (int w = 32; w > 0; w >>= 1) {
       if (t < w) red[t] = fmax(red[t], red[t + w]);
@@ -197,7 +206,7 @@ __global__ void __launch_bounds__(64) k_coarse(double* __restrict__ ug, double* 
     if (r0 < 0.0) r0 = rmax;
     if (s == max_sweeps || rmax <= rel * r0) break;
     for (int c = 0; c < 2; ++c) {
-      if (colour == c) {
+      if (colour == c && active) {
         double sb = 0.0, sd = 0.0;
         sbd = 0.0;
         const double uc = u[t], Ec = E[t];
@@ -315,25 +324,27 @@ void init_u(const double* u0, double* u, double* E, long long n, cudaStream_t s)
 }
 
 void sweep(DenseLevel& L, const Model& m, int colour, double cap, cudaStream_t s) {
-  k_sweep<<<nblocks(L.n / 2, BS), BS, 0, s>>>(L.u, L.E, L.f, L.lg, colour, m, L.ih2, cap);
+  k_sweep<<<nblocks(L.n / 2, BS), BS, 0, s>>>(L.u, L.E, L.f, L.lg, colour, m, L.ih2, cap, L.mask,
+                                              L.mthr);
 }
 
 void restrict_resid(DenseLevel& F, DenseLevel& C, const Model& m, cudaStream_t s) {
   k_restrict_resid<<<nblocks(C.n, BS), BS, 0, s>>>(F.u, F.E, F.f, F.lg, C.u, C.E, C.uold, C.f, m,
-                                                   F.ih2);
+                                                   F.ih2, F.mask, F.mthr);
 }
 
 void fas_rhs(DenseLevel& C, const Model& m, cudaStream_t s) {
-  k_fas_rhs<<<nblocks(C.n, BS), BS, 0, s>>>(C.u, C.E, C.f, C.lg, m, C.ih2);
+  k_fas_rhs<<<nblocks(C.n, BS), BS, 0, s>>>(C.u, C.E, C.f, C.lg, m, C.ih2, C.mask, C.mthr);
 }
 
 void prolong_corr(DenseLevel& F, DenseLevel& C, int linear, cudaStream_t s) {
-  k_prolong_corr<<<nblocks(F.n, BS), BS, 0, s>>>(F.u, F.E, C.u, C.uold, F.lg, linear);
+  k_prolong_corr<<<nblocks(F.n, BS), BS, 0, s>>>(F.u, F.E, C.u, C.uold, F.lg, linear, F.mask,
+                                                 F.mthr);
 }
 
 void coarse_solve(DenseLevel& C, const Model& m, double cap, int max_sweeps, double rel,
                   cudaStream_t s) {
-  k_coarse<<<1, 64, 0, s>>>(C.u, C.E, C.f, m, C.ih2, cap, max_sweeps, rel);
+  k_coarse<<<1, 64, 0, s>>>(C.u, C.E, C.f, m, C.ih2, cap, max_sweeps, rel, C.mask, C.mthr);
 }
 
 void resid_norm(DenseLevel& L, const Model& m, double* partials, int nparts, double* out,

@@ -43,6 +43,10 @@ struct DenseLevel {
   float *u32 = nullptr, *f32 = nullptr, *uold32 = nullptr;
   // FP32 linear multigrid on the Jacobian system (mixed precision, phase B)
   float *e32 = nullptr, *r32 = nullptr, *w32 = nullptr;
+  // multigrid mask of partial-level solves (Sec. 3.3): only cells with
+  // mask > mthr are relaxed; nullptr = all cells.
+  const float* mask = nullptr;
+  float mthr = 0.4f;
 };
 
 struct DenseHier {

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <chrono>
+#include <vector>
 
 #include "mgfr_internal.cuh"
 #include "amr.cuh"
@@ -121,6 +122,7 @@ void mgfr_config_default(mgfr_config* c) {
   c->mixed_switch = 1e-5;
   c->mixed_inner = 1;
   c->max_spins = 1LL << 26;
+  c->mask_thres = 0.4;
 }
 
 }  // extern "C"
@@ -147,6 +149,7 @@ static bool validate_cfg(const mgfr_config* c, std::string& why) {
   if (!(c->mixed_switch > 0.0 && c->mixed_switch < 1.0)) return bad("mixed_switch in (0,1)");
   if (c->mixed_inner < 1 || c->mixed_inner > 16) return bad("mixed_inner in [1, 16]");
   if (c->max_spins < 0) return bad("max_spins must be >= 0");
+  if (!(c->mask_thres >= 0.0 && c->mask_thres < 1.0)) return bad("mask_thres in [0, 1)");
   return true;
 }
 
@@ -213,6 +216,13 @@ static void set_spacing(DenseHier& H, double box) {
     H.L[l].h = box / H.L[l].N;
     H.L[l].ih2 = 1.0 / (H.L[l].h * H.L[l].h);
   }
+}
+
+mgfr_status ensure_dense_public(mgfr_ctx* c, int N, bool mixed, double box) {
+  mgfr_status rs = ensure_dense(c, N, mixed);
+  if (rs != MGFR_OK) return rs;
+  set_spacing(c->dh, box);
+  return MGFR_OK;
 }
 
 // ---- FP64 V-cycle (Sec. 3.3, steps 3-7) ------------------------------------

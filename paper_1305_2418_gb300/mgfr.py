@@ -17,6 +17,7 @@ MGFR_OK, MGFR_E_INVALID, MGFR_E_CUDA, MGFR_E_OOM, MGFR_E_NOCONVERGE, MGFR_E_TIME
     MGFR_E_UNSUPPORTED = range(7)
 STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "NOCONVERGE", "TIMEOUT", "UNSUPPORTED"]
 PREC_FP64, PREC_MIXED = 0, 1
+FIELD_U, FIELD_FR, FIELD_SOURCE, FIELD_MASS, FIELD_ACC, FIELD_COUNT = range(6)
 
 
 class Config(C.Structure):
@@ -26,7 +27,7 @@ class Config(C.Structure):
         ("n_post", C.c_int), ("max_vcycles", C.c_int), ("prolong_linear", C.c_int),
         ("step_cap", C.c_double), ("max_level", C.c_int), ("refine_count", C.c_int),
         ("mixed_switch", C.c_double), ("mixed_inner", C.c_int), ("max_spins", C.c_longlong),
-        ("profile", C.c_int),
+        ("profile", C.c_int), ("mask_thres", C.c_double),
     ]
 
 
@@ -67,6 +68,12 @@ SIGNATURES = {
     "mgfr_solve_density": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
+    "mgfr_solve_particles": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_int, C.c_double,
+                                       C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p]),
+    "mgfr_get_level_info": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "mgfr_get_level_keys": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "mgfr_get_level_field": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "mgfr_last_error": (C.c_char_p, [C.c_void_p]),
     "mgfr_destroy": (None, [C.c_void_p]),
 }
@@ -161,3 +168,35 @@ class Solver:
                                       _ptr(acc), _ptr(u), C.byref(stats))
         self._check(st, allow_noconverge)
         return {"fr": fr, "acc": acc, "u": u, "stats": stats.to_dict(), "status": st}
+
+    def solve_particles(self, pos, N_base: int, box: float, a: float = 1.0, u_init=None,
+                        want_fr=True, want_acc=True, allow_noconverge=False):
+        """f_R on the base grid and the force at the particles (mgfr_solve_particles)."""
+        import torch
+        assert pos.ndim == 2 and pos.shape[1] == 3
+        fr = torch.empty((N_base,) * 3, dtype=torch.float64, device=pos.device) if want_fr else None
+        acc = torch.empty_like(pos) if want_acc else None
+        stats = Stats()
+        st = lib().mgfr_solve_particles(self.h, _ptr(pos), pos.shape[0], N_base, box, a,
+                                        _ptr(u_init), _ptr(fr), _ptr(acc), C.byref(stats))
+        self._check(st, allow_noconverge)
+        return {"fr": fr, "acc": acc, "stats": stats.to_dict(), "status": st}
+
+    def level_info(self, level: int):
+        no, nc = C.c_longlong(), C.c_longlong()
+        self._check(lib().mgfr_get_level_info(self.h, level, C.byref(no), C.byref(nc)))
+        return no.value, nc.value
+
+    def level_keys(self, level: int):
+        import numpy as np
+        no, _ = self.level_info(level)
+        out = np.empty(no, dtype=np.int64)
+        self._check(lib().mgfr_get_level_keys(self.h, level, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def level_field(self, level: int, what: int):
+        import numpy as np
+        _, nc = self.level_info(level)
+        out = np.empty(3 * nc if what == FIELD_ACC else nc)
+        self._check(lib().mgfr_get_level_field(self.h, level, what, out.ctypes.data_as(C.c_void_p)))
+        return out
