@@ -80,7 +80,9 @@ typedef struct {
   int profile;         /* 1: time the base-level sweep kernels with CUDA
                           events recorded around each launch (see stats)   */
   double mask_thres;   /* refined-level multigrid: coarse cells are relaxed
-                          where the mask exceeds this (Sec. 3.3; 0.4)      */
+                          where the mask exceeds this (Sec. 3.3 uses 0.4;
+                          default 0.99 relaxes only fully covered cells,
+                          which converges also for weak screening)        */
 } mgfr_config;
 
 typedef struct {
@@ -112,7 +114,7 @@ typedef struct {
 /* Fill *cfg with the defaults above (omega_m 0.3, fr0_abs 1e-5, n 1, FP64,
  * tol 1e-8, 2+2 sweeps, 100 V-cycles, linear prolongation, step cap 2,
  * max_level 0, refine_count 8, mixed_switch 1e-5, mixed_inner 1,
- * mask_thres 0.4). */
+ * mask_thres 0.99). */
 void mgfr_config_default(mgfr_config* cfg);
 
 /* Create a context on CUDA device `device`, working on `cuda_stream`

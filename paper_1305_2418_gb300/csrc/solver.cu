@@ -122,7 +122,7 @@ void mgfr_config_default(mgfr_config* c) {
   c->mixed_switch = 1e-5;
   c->mixed_inner = 1;
   c->max_spins = 1LL << 26;
-  c->mask_thres = 0.4;
+  c->mask_thres = 0.99;
 }
 
 }  // extern "C"
