@@ -30,7 +30,8 @@ METRIC = ("cell-updates/s & time-to-residual 1e-8 per f(R) solve "
           "(plain FP64 vs mixed+learned), HBM %")
 UNIT = "cell-updates/s"
 
-WORKLOAD = dict(name="grid256", N=256, box=100.0, a=1.0, fr0=1e-5, sigma_g=1.5, seed=2002)
+WORKLOAD = dict(name="particles256", N=256, box=100.0, a=1.0, fr0=1e-5, sigma_g=1.5, seed=2002,
+                lmax=2, nbar=1.0, refine_count=8)
 
 # Algorithmic bytes per cell of one launch, per profiled kernel family
 # ("Kernels and rooflines"):
@@ -41,10 +42,13 @@ WORKLOAD = dict(name="grid256", N=256, box=100.0, a=1.0, fr0=1e-5, sigma_g=1.5, 
 #  2 FP64 residual: read u, E, f (24) + write r32, u32, e32 (12) = 36 B per cell
 #  (FP64 NGS half-sweep, plain path: read u, E (16) + f active (4) + write u, E
 #   active (8) = 28 B per cell)
-ALG_BYTES = {0: 8.0, 1: 12.0, 2: 36.0}
+#  3 FP64 NGS half-sweep on octs: read u, E (16) + f active (4) + write u, E
+#    active (8) + neighbour-oct table (24 B per oct = 3)   = 31 B per cell
+ALG_BYTES = {0: 8.0, 1: 12.0, 2: 36.0, 3: 31.0}
 KERNEL_NAMES = {0: "k_sweep32 (FP32 NGS half-sweep, base level)",
                 1: "k_lin_sweep (FP32 linear GS half-sweep, base level)",
-                2: "k_resid64 (FP64 residual, base level)"}
+                2: "k_resid64 (FP64 residual, base level)",
+                3: "k_oct_sweep (NGS half-sweep on the octs of the level being solved)"}
 
 
 def peaks():
@@ -103,57 +107,67 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline_sample(max_seconds: float = 20.0) -> dict:
-    """The CPU oracle (single thread, FP64) on a bounded sample of the workload:
-    a full solve of a 64^3 lognormal field with the workload's cell size,
-    sigma_g and |fR0|, repeated while time remains."""
+def _oracle_particle_sample():
+    """One full oracle solve of a bounded sample of the particle workload: a
+    32^3 base grid in a 12.5 Mpc/h box (the workload's cell size), particles
+    drawn the same way (nbar 1, sigma_g 1.5), the same refinement rule,
+    |fR0| and tolerance.  Returns (cell updates, seconds)."""
     import oracle
     from paper_1305_2418_gb300 import synth
     w = WORKLOAD
-    N = 64
+    N = 32
     box = w["box"] * N / w["N"]
-    delta = synth.lognormal_delta(N, box, w["sigma_g"], w["seed"])
+    d = synth.lognormal_delta(N, box, w["sigma_g"], w["seed"])
+    pos = synth.poisson_particles(d, box, w["nbar"], w["seed"])
     t0 = time.perf_counter()
-    upd = 0.0
-    n = 0
-    while True:
-        _, st = oracle.solve_dense(delta, box, w["fr0"], a=w["a"], tol=1e-8)
-        upd += st["updates"]
-        n += 1
-        if time.perf_counter() - t0 > max_seconds / 2 or n >= 8:
-            break
+    A = oracle.AMR(pos, N, box, w["lmax"], w["refine_count"])
+    A.deposit()
+    A.set_model(w["fr0"], a=w["a"])
+    rc, st = A.solve(tol=1e-8)
+    A.particle_force()
     dt = time.perf_counter() - t0
+    upd = st[3] + sum(st[4 + 4 * (l - 1)] * A.ncell(l) for l in range(1, A.nlev))
+    A.close()
+    return upd, dt
+
+
+SAMPLE_DESC = ("full FP64 oracle particle solve (structure, adaptive CIC, every level to 1e-8, "
+               "particle force) of a 32^3-base sample: box 12.5 Mpc/h (same cell size), nbar 1, "
+               "sigma_g 1.5, 2 refinement levels, |fR0| 1e-5")
+
+
+def cpu_baseline_sample(max_seconds: float = 20.0) -> dict:
+    """The CPU oracle (single thread, FP64) on a bounded sample of the workload."""
+    t0 = time.perf_counter()
+    upd = dt = 0.0
+    n = 0
+    while n < 1 or (time.perf_counter() - t0 < max_seconds / 2 and n < 8):
+        u, t = _oracle_particle_sample()
+        upd += u
+        dt += t
+        n += 1
     return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} full FP64 oracle solve(s) of a 64^3 lognormal field "
-                      f"(box {box:g} Mpc/h, same cell size, sigma_g {w['sigma_g']}, "
-                      f"|fR0| {w['fr0']:g}) to 1e-8, {dt:.1f} s"}
+            "sample": f"{n} x {SAMPLE_DESC}, {dt:.1f} s"}
 
 
 def run_reference(args, rank: int) -> None:
     if rank != 0:
         return
-    import oracle
-    from paper_1305_2418_gb300 import synth
-    w = WORKLOAD
-    N = 64
-    box = w["box"] * N / w["N"]
-    delta = synth.lognormal_delta(N, box, w["sigma_g"], w["seed"])
     for _ in range(args.warmup):
-        oracle.solve_dense(delta, box, w["fr0"], a=w["a"], tol=1e-8)
-    upd = 0.0
-    t0 = time.perf_counter()
+        _oracle_particle_sample()
+    upd = dt = 0.0
     for _ in range(args.steps):
-        _, st = oracle.solve_dense(delta, box, w["fr0"], a=w["a"], tol=1e-8)
-        upd += st["updates"]
-    dt = time.perf_counter() - t0
+        u, t = _oracle_particle_sample()
+        upd += u
+        dt += t
     val = upd / dt
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["name"] + " (64^3 sample per step, same cell size)"},
+            "config": {"workload": WORKLOAD["name"] + " (bounded 32^3-base sample per step)"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "one full FP64 oracle solve of a 64^3 sample per step"},
+                             "sample": "one " + SAMPLE_DESC + " per step"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -190,21 +204,28 @@ def main():
 
     w = WORKLOAD
     delta_h = synth.lognormal_delta(w["N"], w["box"], w["sigma_g"], w["seed"])
-    delta = torch.from_numpy(delta_h).to(dev)
-    n = delta.numel()
+    pos_h = synth.poisson_particles(delta_h, w["box"], w["nbar"], w["seed"])
+    pos = torch.from_numpy(pos_h).to(dev)
+    n = w["N"] ** 3
+    n_part = pos_h.shape[0]
 
     def solver(prec, profile=1):
-        return mgfr.Solver(local, fr0_abs=w["fr0"], precision=prec, profile=profile)
+        return mgfr.Solver(local, fr0_abs=w["fr0"], precision=prec, profile=profile,
+                           max_level=w["lmax"], refine_count=w["refine_count"])
+
+    def step(s, p=None, want_fr=False):
+        return s.solve_particles(pos if p is None else p, w["N"], w["box"], w["a"],
+                                 want_fr=want_fr)
 
     # ---- plain FP64 solve, time to tolerance (reported beside) ----
     s64 = solver(mgfr.PREC_FP64)
-    s64.solve_density(delta, w["box"], w["a"])
+    step(s64)
     torch.cuda.synchronize()
     t64 = []
     for _ in range(2):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        o64 = s64.solve_density(delta, w["box"], w["a"])
+        o64 = step(s64)
         e1.record()
         torch.cuda.synchronize()
         t64.append(e0.elapsed_time(e1))
@@ -214,7 +235,7 @@ def main():
     # ---- mixed-precision form: the timed steps (graphs replayed) ----
     sm = solver(mgfr.PREC_MIXED, profile=0)
     for _ in range(args.warmup):
-        sm.solve_density(delta, w["box"], w["a"])
+        step(sm)
     torch.cuda.synchronize()
     barrier()
     clocks = Clocks(local)
@@ -222,11 +243,12 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     kern_ms = [0.0] * 4
     kern_n = [0] * 4
+    kern_cells = [0] * 4
     launches = 0
     upd = 0
     e0.record()
     for _ in range(args.steps):
-        out = sm.solve_density(delta, w["box"], w["a"])
+        out = step(sm)
         st = out["stats"]
         launches += st["gpu_launches"]
         upd += st["cell_updates"] + st["linear_updates"]
@@ -238,15 +260,16 @@ def main():
     # Same steps again with per-launch CUDA events around the profiled kernels
     # (launched directly on the library's stream instead of from graphs).
     sp = solver(mgfr.PREC_MIXED, profile=1)
-    sp.solve_density(delta, w["box"], w["a"])
+    step(sp)
     torch.cuda.synchronize()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record()
     for _ in range(args.steps):
-        stp = sp.solve_density(delta, w["box"], w["a"])["stats"]
+        stp = step(sp)["stats"]
         for q in range(4):
             kern_ms[q] += stp["kern_ms"][q]
             kern_n[q] += stp["kern_launches"][q]
+            kern_cells[q] += stp["kern_cells"][q]
     p1.record()
     torch.cuda.synchronize()
     ms_prof = p0.elapsed_time(p1)
@@ -259,12 +282,12 @@ def main():
     last = st
 
     # ---- end to end through the public API: host buffers, copies timed ----
-    host_in = torch.from_numpy(delta_h).pin_memory()
+    host_in = torch.from_numpy(pos_h).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     for _ in range(1):
         d_in = host_in.to(dev, non_blocking=True)
-        r = sm.solve_density(d_in, w["box"], w["a"], want_acc=False)
-        host_out.copy_(r["fr"], non_blocking=True)
+        r = step(sm, d_in)
+        host_out.copy_(r["acc"], non_blocking=True)
     torch.cuda.synchronize()
     barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -272,8 +295,8 @@ def main():
     e2e_upd = 0
     for _ in range(args.steps):
         d_in = host_in.to(dev, non_blocking=True)
-        r = sm.solve_density(d_in, w["box"], w["a"], want_acc=False)
-        host_out.copy_(r["fr"], non_blocking=True)
+        r = step(sm, d_in)
+        host_out.copy_(r["acc"], non_blocking=True)
         e2e_upd += r["stats"]["cell_updates"] + r["stats"]["linear_updates"]
     f1.record()
     torch.cuda.synchronize()
@@ -289,17 +312,18 @@ def main():
         return
 
     # ---- roofline of the dominant profiled kernel ----
-    fam = max(range(3), key=lambda q: kern_ms[q])
+    fam = max(range(4), key=lambda q: kern_ms[q])
     avg_ms = kern_ms[fam] / max(kern_n[fam], 1)
-    bytes_per_launch = ALG_BYTES[fam] * n
+    bytes_per_launch = ALG_BYTES[fam] * kern_cells[fam] / max(kern_n[fam], 1)
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
     peak, peak_kind = peaks()
     roof = {"bound": "hbm", "kernel": KERNEL_NAMES[fam], "achieved": achieved, "peak": peak,
             "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
             "traffic": None, "launches": kern_n[fam], "avg_launch_us": 1e3 * avg_ms,
+            "alg_bytes_per_launch": bytes_per_launch,
             "kernel_share_of_step": kern_ms[fam] / ms_prof,
             "profiled_ms_per_step": ms_prof / args.steps,
-            "per_family_ms": {KERNEL_NAMES[q]: kern_ms[q] / args.steps for q in range(3)}}
+            "per_family_ms": {KERNEL_NAMES[q]: kern_ms[q] / args.steps for q in range(4)}}
 
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline_sample()
 
@@ -307,15 +331,20 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"{w['name']}: 256^3 periodic lognormal delta (sigma_g 1.5, "
-                               f"P(k)~k^-1.5), box 100 Mpc/h, |fR0| 1e-5, n 1, a 1; base-level "
-                               f"solve to 1e-8, zero start",
+        "config": {"workload": f"{w['name']}: {n_part} particles Poisson-sampled (nbar 1) from a "
+                               f"256^3 lognormal delta (sigma_g 1.5, P(k)~k^-1.5), box 100 Mpc/h, "
+                               f"256^3 base grid + 2 refinement levels (> 8 particles, 1-cell "
+                               f"buffer), adaptive CIC, |fR0| 1e-5, n 1, a 1; every level solved "
+                               f"to 1e-8 from a zero start; force gathered to the particles",
+                   "levels_cells": last["cells_per_level"][:last["n_levels"]],
                    "precision": "mixed (FP32 smoothing, FP64 residual/defect correction)",
                    "l2": "working set (u, E, f FP64 + FP32 levels, ~700 MB) larger than L2",
                    "parallelism": f"replicas x{world}"},
         "time_to_tol_ms": {"mixed": ms_max / args.steps, "fp64": min(t64)},
         "vcycles": {"mixed_fp32": last["vcycles"], "mixed_outer_fp64": last["outer_iters"],
-                    "fp64": st64["vcycles"]},
+                    "fp64": st64["vcycles"],
+                    "refined_levels_mixed": last["level_iters"][1:last["n_levels"]],
+                    "refined_levels_fp64": st64["level_iters"][1:st64["n_levels"]]},
         "cell_updates_per_step": {"nonlinear": last["cell_updates"],
                                   "linear": last["linear_updates"],
                                   "fp64_path": st64["cell_updates"]},
@@ -323,8 +352,8 @@ def main():
         "roofline": roof,
         "clocks": ck,
         "gpu_launches": launches,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
-                "d2h_bytes_per_step": 8 * n},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * n_part,
+                "d2h_bytes_per_step": 24 * n_part},
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

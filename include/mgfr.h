@@ -108,6 +108,7 @@ typedef struct {
    * [3] refined-level relaxation sweeps.                                   */
   double kern_ms[4];
   long long kern_launches[4];
+  long long kern_cells[4];   /* cells of the levels those launches covered   */
   long long gpu_launches;    /* kernels this call launched (graph nodes included) */
 } mgfr_stats;
 

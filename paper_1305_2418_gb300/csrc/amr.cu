@@ -952,6 +952,8 @@ static DenseLevel sub_work(AmrWork* A, const DenseHier& H, int k, float mthr) {
   return D;
 }
 
+void prof_reserve_public(mgfr_ctx* c, size_t pairs);
+
 static void relax_tree(AmrSolveCtx& S, int l, int sweeps) {
   mgfr_ctx* c = S.c;
   AmrWork* A = S.A;
@@ -960,7 +962,7 @@ static void relax_tree(AmrSolveCtx& S, int l, int sweeps) {
   for (int s = 0; s < sweeps; ++s) {
     for (int col = 0; col < 2; ++col) {
       if (l >= 1) {
-        if (l == S.L) prof_begin(c, 3);
+        if (l == S.L) prof_begin(c, 3, L.ncell);
         k_oct_sweep<<<nblocks(4 * L.n_oct, BS), BS, 0, c->s>>>(
             L.w, L.wE, L.wf, L.nbr, L.ghost, L.ghostE, l == S.L ? nullptr : L.mask, S.mthr,
             L.n_oct, col, S.m, L.ih2, g.step_cap);
@@ -1112,6 +1114,7 @@ static mgfr_status solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, 
     c->launches += 1;
   }
   AmrSolveCtx S{c, A, m, Lv, mthr, 0};
+  if (g.profile) prof_reserve_public(c, 64);
   double hs[3];
   TRY(level_norm(c, A, Lv, m, hs));
   const double fn = std::sqrt(hs[2]), r0 = std::sqrt(hs[0]);
@@ -1119,7 +1122,9 @@ static mgfr_status solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, 
   double r = r0;
   int it = 0;
   while (r > target && it < g.max_vcycles) {
+    c->capturing = 3;
     vcycle_tree(S, Lv);
+    c->capturing = -1;
     TRY(level_norm(c, A, Lv, m, hs));
     prof_collect(c, 3, st);
     r = std::sqrt(hs[0]);

@@ -123,6 +123,7 @@ struct mgfr_ctx {
   struct ProfRec {
     int fam;
     cudaEvent_t a, b;
+    long long cells;
   };
   std::vector<ProfRec> prof[4];  // per graph: 0 v64, 1 v32, 2 lin, 3 refined
   std::vector<cudaEvent_t> evpool;
@@ -136,7 +137,7 @@ long long count_kernel_nodes(cudaGraph_t g);
 
 // Record a timing event pair around a kernel launch while capturing graph
 // `c->capturing` with profiling on.
-void prof_begin(mgfr_ctx* c, int fam);
+void prof_begin(mgfr_ctx* c, int fam, long long cells);
 void prof_end(mgfr_ctx* c);
 void prof_collect(mgfr_ctx* c, int graph, mgfr_stats* st);
 void prof_clear(mgfr_ctx* c, int graph);

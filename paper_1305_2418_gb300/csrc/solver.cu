@@ -51,9 +51,11 @@ static void prof_reserve(mgfr_ctx* c, size_t pairs) {
   }
 }
 
-void prof_begin(mgfr_ctx* c, int fam) {
+void prof_reserve_public(mgfr_ctx* c, size_t pairs) { prof_reserve(c, pairs); }
+
+void prof_begin(mgfr_ctx* c, int fam, long long cells) {
   if (!c->cfg.profile || c->capturing < 0 || c->evpool.size() < 2) return;
-  mgfr_ctx::ProfRec r{fam, c->evpool.back(), nullptr};
+  mgfr_ctx::ProfRec r{fam, c->evpool.back(), nullptr, cells};
   c->evpool.pop_back();
   r.b = c->evpool.back();
   c->evpool.pop_back();
@@ -74,6 +76,7 @@ void prof_collect(mgfr_ctx* c, int g, mgfr_stats* st) {
       if (st) {
         st->kern_ms[r.fam] += ms;
         st->kern_launches[r.fam] += 1;
+        st->kern_cells[r.fam] += r.cells;
       }
     } else {
       (void)cudaGetLastError();
@@ -233,7 +236,7 @@ static void vcycle64(mgfr_ctx* c, const Model& m, int l, long long& updates) {
   const mgfr_config& g = c->cfg;
   for (int s = 0; s < g.n_pre; ++s) {
     for (int col = 0; col < 2; ++col) {
-      if (l == 0) prof_begin(c, 0);
+      if (l == 0) prof_begin(c, 0, F.n);
       f64::sweep(F, m, col, g.step_cap, c->s);
       if (l == 0) prof_end(c);
     }
@@ -248,7 +251,7 @@ static void vcycle64(mgfr_ctx* c, const Model& m, int l, long long& updates) {
   f64::prolong_corr(F, C, g.prolong_linear, c->s);
   for (int s = 0; s < g.n_post; ++s) {
     for (int col = 0; col < 2; ++col) {
-      if (l == 0) prof_begin(c, 0);
+      if (l == 0) prof_begin(c, 0, F.n);
       f64::sweep(F, m, col, g.step_cap, c->s);
       if (l == 0) prof_end(c);
     }
@@ -371,7 +374,7 @@ static void vcycle32(mgfr_ctx* c, const Model& m, int l, long long& updates) {
   const float cap = (float)g.step_cap;
   for (int s = 0; s < g.n_pre; ++s) {
     for (int col = 0; col < 2; ++col) {
-      if (l == 0) prof_begin(c, 0);
+      if (l == 0) prof_begin(c, 0, F.n);
       f32::sweep(F, m, col, cap, c->s);
       if (l == 0) prof_end(c);
     }
@@ -386,7 +389,7 @@ static void vcycle32(mgfr_ctx* c, const Model& m, int l, long long& updates) {
   f32::prolong_corr(F, C, g.prolong_linear, c->s);
   for (int s = 0; s < g.n_post; ++s) {
     for (int col = 0; col < 2; ++col) {
-      if (l == 0) prof_begin(c, 0);
+      if (l == 0) prof_begin(c, 0, F.n);
       f32::sweep(F, m, col, cap, c->s);
       if (l == 0) prof_end(c);
     }
@@ -402,7 +405,7 @@ static void vcycle_lin(mgfr_ctx* c, const Model& m, int l, long long& updates) {
   const mgfr_config& g = c->cfg;
   for (int s = 0; s < g.n_pre; ++s) {
     for (int col = 0; col < 2; ++col) {
-      if (l == 0) prof_begin(c, 1);
+      if (l == 0) prof_begin(c, 1, F.n);
       f32::lin_sweep(F, m, col, c->s);
       if (l == 0) prof_end(c);
     }
@@ -416,7 +419,7 @@ static void vcycle_lin(mgfr_ctx* c, const Model& m, int l, long long& updates) {
   f32::lin_prolong(F, C, g.prolong_linear, c->s);
   for (int s = 0; s < g.n_post; ++s) {
     for (int col = 0; col < 2; ++col) {
-      if (l == 0) prof_begin(c, 1);
+      if (l == 0) prof_begin(c, 1, F.n);
       f32::lin_sweep(F, m, col, c->s);
       if (l == 0) prof_end(c);
     }
@@ -469,7 +472,7 @@ mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stat
     upd = 0;
     for (int q = 0; q < g.mixed_inner; ++q) vcycle_lin(c, m, 0, upd);
     f32::apply_corr(L0, g.step_cap, c->s);
-    prof_begin(c, 2);
+    prof_begin(c, 2, L0.n);
     f32::resid64(L0, m, H.partials, H.nparts, H.scal, c->s);
     prof_end(c);
     cudaMemcpyAsync(hs, H.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s);

@@ -40,7 +40,7 @@ class Stats(C.Structure):
         ("cells_per_level", C.c_longlong * 16), ("octs_per_level", C.c_longlong * 16),
         ("level_iters", C.c_int * 16), ("level_res", C.c_double * 16),
         ("kern_ms", C.c_double * 4), ("kern_launches", C.c_longlong * 4),
-        ("gpu_launches", C.c_longlong),
+        ("kern_cells", C.c_longlong * 4), ("gpu_launches", C.c_longlong),
     ]
 
     def to_dict(self) -> dict:
