@@ -50,45 +50,6 @@ __device__ __forceinline__ P3 particle_t(const double* __restrict__ pos, long lo
             wrap_coord(pos[3 * p + 2], inv, N0)};
 }
 
-// ---- tree lookups ----------------------------------------------------------
-// Cell at level l with level-l coordinates (I,J,K) (wrapped).  Returns the
-// cell index at the deepest level m <= l that exists on the path, m in *lev.
-__device__ __forceinline__ long long find_cell(const TreeView& T, int l, long long I, long long J,
-                                               long long K, int* lev) {
-  const long long Nl = 1LL << (T.lg0 + l);
-  I &= Nl - 1;
-  J &= Nl - 1;
-  K &= Nl - 1;
-  long long c = (((I >> l) << T.lg0) + (J >> l) << T.lg0) + (K >> l);
-  for (int m = 1; m <= l; ++m) {
-    const int o = T.son[m - 1][c];
-    if (o < 0) {
-      *lev = m - 1;
-      return c;
-    }
-    const int sh = l - m;
-    c = 8LL * o + (((I >> sh) & 1) << 2) + (((J >> sh) & 1) << 1) + ((K >> sh) & 1);
-  }
-  *lev = l;
-  return c;
-}
-
-__device__ __forceinline__ void cell_coords(const TreeView& T, int l, long long c, long long* I,
-                                            long long* J, long long* K) {
-  if (l == 0) {
-    const long long M = (1LL << T.lg0) - 1;
-    *K = c & M;
-    *J = (c >> T.lg0) & M;
-    *I = c >> (2 * T.lg0);
-    return;
-  }
-  const int4 p = T.opos[l][c >> 3];
-  const int ch = (int)(c & 7);
-  *I = 2LL * p.x + ((ch >> 2) & 1);
-  *J = 2LL * p.y + ((ch >> 1) & 1);
-  *K = 2LL * p.z + (ch & 1);
-}
-
 // ---- structure kernels -----------------------------------------------------
 __global__ void k_count(const double* __restrict__ pos, long long Np, double inv, double N0, int l,
                         TreeView T, int* __restrict__ count) {
@@ -398,324 +359,38 @@ __global__ void k_nan_check(const double* __restrict__ x, long long n,
   if (i < n && !isfinite(x[i])) atomicOr(err, 2ULL);
 }
 
-// ---- refined-level operators -----------------------------------------------
-__device__ __forceinline__ double nl_s(double u, double E, const Model& m) {
-  return m.n == 1 ? rsqrt(E) : exp(-u * m.inv_np1);
-}
-
-// value of the neighbour of cell (o, ch) in direction d: same oct, the
-// neighbouring oct, or the ghost slot (ghost != nullptr).
-struct OctNb {
-  double u, E;
+// ---- refined-level force --------------------------------------------------
+struct OctNbE {
+  double E;
 };
 
-__device__ __forceinline__ OctNb oct_nb(const double* __restrict__ u, const double* __restrict__ E,
-                                        const int* __restrict__ nbr,
-                                        const double* __restrict__ ghost,
-                                        const double* __restrict__ ghostE, long long o, int ch,
-                                        int d) {
+// E of the neighbour of cell (o, ch) in direction d (same oct, neighbouring
+// oct, or the ghost slot of the face).
+__device__ __forceinline__ double oct_nbE(const double* __restrict__ E,
+                                         const int* __restrict__ nbr,
+                                         const double* __restrict__ ghostE, long long o, int ch,
+                                         int d) {
   const int ax = d >> 1, plus = d & 1;
   const int bit = (ch >> (2 - ax)) & 1;
   const int chn = ch ^ (1 << (2 - ax));
-  if (bit != plus) {  // inside the oct
-    const long long q = 8 * o + chn;
-    return OctNb{u[q], E[q]};
-  }
+  if (bit != plus) return E[8 * o + chn];
   const int no = nbr[6 * o + d];
-  if (no >= 0) {
-    const long long q = 8LL * no + chn;
-    return OctNb{u[q], E[q]};
-  }
-  // ghost slot: face d, index from the two tangential bits
+  if (no >= 0) return E[8LL * no + chn];
   const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
   const int qi = (((ch >> (2 - t1)) & 1) << 1) | ((ch >> (2 - t2)) & 1);
-  const long long g = 24 * o + 4 * d + qi;
-  return OctNb{ghost[g], ghostE[g]};
+  return ghostE[24 * o + 4 * d + qi];
 }
 
-// red (colour 0) cells of an oct: children with even di+dj+dk
-__constant__ int kColourChild[2][4] = {{0, 3, 5, 6}, {1, 2, 4, 7}};
-
-__global__ void __launch_bounds__(BS) k_oct_sweep(double* __restrict__ u, double* __restrict__ E,
-                                                  const double* __restrict__ f,
-                                                  const int* __restrict__ nbr,
-                                                  const double* __restrict__ ghost,
-                                                  const double* __restrict__ ghostE,
-                                                  const float* __restrict__ mask, float mthr,
-                                                  long long n_oct, int colour, Model m, double ih2,
-                                                  double cap) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= 4 * n_oct) return;
-  const long long o = t >> 2;
-  const int ch = kColourChild[colour][t & 3];
-  const long long c = 8 * o + ch;
-  if (mask && !(mask[c] > mthr)) return;
-  const double uc = u[c], Ec = E[c];
-  double sbd = 0.0, sd = 0.0, sb = 0.0;
-#pragma unroll
-  for (int d = 0; d < 6; ++d) {
-    const OctNb nb = oct_nb(u, E, nbr, ghost, ghostE, o, ch, d);
-    const double b = 0.5 * (nb.E + Ec), du = nb.u - uc;
-    sbd = fma(b, du, sbd);
-    sd += du;
-    sb += b;
-  }
-  const double s = nl_s(uc, Ec, m);
-  const double L = sbd * ih2 + m.aRt * (1.0 - s);
-  const double dL = (0.5 * Ec * sd - sb) * ih2 + m.aRt_np1 * s;
-  double step = (L - f[c]) / dL;
-  step = fmin(fmax(step, -cap), cap);
-  const double un = uc - step;
-  u[c] = un;
-  E[c] = exp(un);
-}
-
-__device__ __forceinline__ double oct_L(const double* __restrict__ u, const double* __restrict__ E,
-                                        const int* __restrict__ nbr,
-                                        const double* __restrict__ ghost,
-                                        const double* __restrict__ ghostE, long long o, int ch,
-                                        const Model& m, double ih2) {
-  const long long c = 8 * o + ch;
-  const double uc = u[c], Ec = E[c];
-  double sbd = 0.0;
-#pragma unroll
-  for (int d = 0; d < 6; ++d) {
-    const OctNb nb = oct_nb(u, E, nbr, ghost, ghostE, o, ch, d);
-    sbd = fma(0.5 * (nb.E + Ec), nb.u - uc, sbd);
-  }
-  return sbd * ih2 + m.aRt * (1.0 - nl_s(uc, Ec, m));
-}
-
-// residual norm over all cells of a level (ghost layer fixed)
-__global__ void __launch_bounds__(BS) k_oct_norm(const double* __restrict__ u,
-                                                 const double* __restrict__ E,
-                                                 const double* __restrict__ f,
-                                                 const int* __restrict__ nbr,
-                                                 const double* __restrict__ ghost,
-                                                 const double* __restrict__ ghostE,
-                                                 long long ncell, Model m, double ih2,
-                                                 double* __restrict__ partials) {
-  double ss = 0.0, mx = 0.0, fs = 0.0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
-       c += (long long)gridDim.x * blockDim.x) {
-    const double r = f[c] - oct_L(u, E, nbr, ghost, ghostE, c >> 3, (int)(c & 7), m, ih2);
-    ss = fma(r, r, ss);
-    mx = fmax(mx, fabs(r));
-    fs = fma(f[c], f[c], fs);
-  }
-  __shared__ double s1[BS / 32], s2[BS / 32], s3[BS / 32];
-  for (int q = 16; q > 0; q >>= 1) {
-    ss += __shfl_xor_sync(0xffffffffu, ss, q);
-    fs += __shfl_xor_sync(0xffffffffu, fs, q);
-    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, q));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    s1[threadIdx.x >> 5] = ss;
-    s2[threadIdx.x >> 5] = mx;
-    s3[threadIdx.x >> 5] = fs;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0, e = 0.0;
-    for (int w = 0; w < BS / 32; ++w) {
-      a += s1[w];
-      b = fmax(b, s2[w]);
-      e += s3[w];
-    }
-    partials[3 * blockIdx.x] = a;
-    partials[3 * blockIdx.x + 1] = b;
-    partials[3 * blockIdx.x + 2] = e;
-  }
-}
-
-__global__ void k_finish3(const double* __restrict__ partials, int nparts, double* __restrict__ out) {
-  __shared__ double s1[256], s2[256], s3[256];
-  double a = 0.0, b = 0.0, e = 0.0;
-  for (int q = threadIdx.x; q < nparts; q += blockDim.x) {
-    a += partials[3 * q];
-    b = fmax(b, partials[3 * q + 1]);
-    e += partials[3 * q + 2];
-  }
-  s1[threadIdx.x] = a;
-  s2[threadIdx.x] = b;
-  s3[threadIdx.x] = e;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) {
-      s1[threadIdx.x] += s1[threadIdx.x + w];
-      s2[threadIdx.x] = fmax(s2[threadIdx.x], s2[threadIdx.x + w]);
-      s3[threadIdx.x] += s3[threadIdx.x + w];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    out[0] = s1[0];
-    out[1] = s2[0];
-    out[2] = s3[0];
-  }
-}
-
-// Restrict oct level k to its parents on level k-1: u average, masked
-// residual average (cells with mask <= mthr contribute 0), saved old value.
-__global__ void __launch_bounds__(BS) k_oct_restrict(
-    const double* __restrict__ u, const double* __restrict__ E, const double* __restrict__ f,
-    const int* __restrict__ nbr, const double* __restrict__ ghost,
-    const double* __restrict__ ghostE, const float* __restrict__ mask, float mthr,
-    long long n_oct, const int* __restrict__ pcell, Model m, double ih2, double* __restrict__ uc,
-    double* __restrict__ Ec, double* __restrict__ ucold, double* __restrict__ fc) {
+__global__ void k_oct_pnbrs(long long n_oct, int l, TreeView T, int* __restrict__ pnbr) {
   const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (o >= n_oct) return;
-  double su = 0.0, sr = 0.0;
-  for (int ch = 0; ch < 8; ++ch) {
-    const long long c = 8 * o + ch;
-    su += u[c];
-    if (!mask || mask[c] > mthr) sr += f[c] - oct_L(u, E, nbr, ghost, ghostE, o, ch, m, ih2);
-  }
-  const int p = pcell[o];
-  const double um = 0.125 * su;
-  uc[p] = um;
-  ucold[p] = um;
-  Ec[p] = exp(um);
-  fc[p] = 0.125 * sr;
-}
-
-// FAS right-hand side on a coarse oct level: f += L(u) at relaxed cells.
-__global__ void __launch_bounds__(BS) k_oct_fas(const double* __restrict__ u,
-                                                const double* __restrict__ E,
-                                                double* __restrict__ f,
-                                                const int* __restrict__ nbr,
-                                                const float* __restrict__ mask, float mthr,
-                                                long long ncell, Model m, double ih2) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= ncell || !(mask[c] > mthr)) return;
-  f[c] += oct_L(u, E, nbr, nullptr, nullptr, c >> 3, (int)(c & 7), m, ih2);
-}
-
-// parent value of level-l cell (I,J,K) with the linear reconstruction from
-// the parent's neighbours (a component is 0 where a neighbour is missing);
-// `val` reads the parent level's field (a difference of two arrays for
-// corrections).
-template <class F>
-__device__ __forceinline__ double prolong_value(const TreeView& T, int l, long long I, long long J,
-                                                long long K, long long pc, int linear, F val) {
-  double v = val(pc);
-  if (!linear) return v;
-  const long long P[3] = {I >> 1, J >> 1, K >> 1};
-  const long long C[3] = {I, J, K};
-  for (int ax = 0; ax < 3; ++ax) {
-    long long Qp[3] = {P[0], P[1], P[2]}, Qm[3] = {P[0], P[1], P[2]};
-    Qp[ax] += 1;
-    Qm[ax] -= 1;
-    int lp, lm;
-    const long long cp = find_cell(T, l - 1, Qp[0], Qp[1], Qp[2], &lp);
-    const long long cm = find_cell(T, l - 1, Qm[0], Qm[1], Qm[2], &lm);
-    if (lp != l - 1 || lm != l - 1) continue;
-    const double s = (C[ax] & 1) ? 0.125 : -0.125;
-    v += s * (val(cp) - val(cm));
-  }
-  return v;
-}
-
-// Initial guess of level l from the converged level l-1 (Sec. 3.3, step 9).
-__global__ void k_oct_init(long long ncell, int l, TreeView T, const int* __restrict__ pcell,
-                           const double* __restrict__ up, int linear, double* __restrict__ u,
-                           double* __restrict__ E) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  long long I, J, K;
-  cell_coords(T, l, c, &I, &J, &K);
-  const double v = prolong_value(T, l, I, J, K, pcell[c >> 3], linear,
-                                 [&](long long q) { return up[q]; });
-  u[c] = v;
-  E[c] = exp(v);
-}
-
-// Ghost values of level l: for every oct face without a neighbouring oct, the
-// 4 level-l cells across it take the linear reconstruction of their parent
-// (level l-1, converged) -- fixed during the level solve.
-__global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restrict__ nbr,
-                         const double* __restrict__ up, int linear, double* __restrict__ ghost,
-                         double* __restrict__ ghostE) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= 24 * n_oct) return;
-  const long long o = t / 24;
-  const int d = (int)((t % 24) >> 2), qi = (int)(t & 3);
-  if (nbr[6 * o + d] >= 0) return;
-  const int ax = d >> 1, plus = d & 1;
-  const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
-  int b[3];
-  b[ax] = plus;  // the oct's cell on that face has this bit
-  b[t1] = (qi >> 1) & 1;
-  b[t2] = qi & 1;
   const int4 p = T.opos[l][o];
-  long long C[3] = {2LL * p.x + b[0], 2LL * p.y + b[1], 2LL * p.z + b[2]};
-  C[ax] += plus ? 1 : -1;
-  const long long Nl = 1LL << (T.lg0 + l);
-  for (int a = 0; a < 3; ++a) C[a] &= Nl - 1;
-  int lev;
-  const long long pc = find_cell(T, l - 1, C[0] >> 1, C[1] >> 1, C[2] >> 1, &lev);
-  double v = 0.0;
-  if (lev == l - 1)
-    v = prolong_value(T, l, C[0], C[1], C[2], pc, linear, [&](long long q) { return up[q]; });
-  ghost[t] = v;
-  ghostE[t] = exp(v);
-}
-
-// Correction of relaxed level-l cells from the coarse level l-1:
-// u += P(uc - ucold) (eq. fine_correction).
-__global__ void k_oct_prolong(long long ncell, int l, TreeView T, const int* __restrict__ pcell,
-                              const double* __restrict__ uc, const double* __restrict__ ucold,
-                              const float* __restrict__ mask, float mthr, int linear,
-                              double* __restrict__ u, double* __restrict__ E) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  if (mask && !(mask[c] > mthr)) return;
-  long long I, J, K;
-  cell_coords(T, l, c, &I, &J, &K);
-  const double v = prolong_value(T, l, I, J, K, pcell[c >> 3], linear,
-                                 [&](long long q) { return uc[q] - ucold[q]; });
-  const double un = u[c] + v;
-  u[c] = un;
-  E[c] = exp(un);
-}
-
-// mask of level l-1 cells from their daughters: average of the 8 masks for
-// cells with daughters (cells without daughters keep 0).
-__global__ void k_mask_up(const float* __restrict__ mchild, long long n_oct,
-                          const int* __restrict__ pcell, float* __restrict__ mparent) {
-  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (o >= n_oct) return;
-  float s = 0.f;
-  for (int q = 0; q < 8; ++q) s += mchild[8 * o + q];
-  mparent[pcell[o]] = 0.125f * s;
-}
-
-__global__ void k_mask_dense(const float* __restrict__ mf, int lgf, float* __restrict__ mc) {
-  const int lgc = lgf - 1, Nc = 1 << lgc;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (1LL << (3 * lgc))) return;
-  const int K = (int)(t & (Nc - 1)), J = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
-  float s = 0.f;
-  for (int q = 0; q < 8; ++q) {
-    const int i = 2 * I + (q >> 2), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q & 1);
-    s += mf[((((long long)i << lgf) + j) << lgf) + k];
+  const int dd[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+  for (int d = 0; d < 6; ++d) {
+    int lev;
+    const long long q = find_cell(T, l - 1, p.x + dd[d][0], p.y + dd[d][1], p.z + dd[d][2], &lev);
+    pnbr[6 * o + d] = lev == l - 1 ? (int)q : -1;
   }
-  mc[t] = 0.125f * s;
-}
-
-__global__ void k_fill_f(float* __restrict__ x, long long n, float v) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n) x[i] = v;
-}
-
-__global__ void k_count_relaxed(const float* __restrict__ mask, long long n, float mthr,
-                                long long* __restrict__ out) {
-  long long cnt = 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    cnt += mask[i] > mthr;
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd((unsigned long long*)out, (unsigned long long)cnt);
 }
 
 // f_R and a_MG/c^2 on a refined level (central differences, ghosts at edges)
@@ -728,9 +403,9 @@ __global__ void k_oct_force(const double* __restrict__ E, const int* __restrict_
   const int ch = (int)(c & 7);
   fr[c] = fbar * E[c];
   for (int ax = 0; ax < 3; ++ax) {
-    const OctNb m = oct_nb(E, E, nbr, ghostE, ghostE, o, ch, 2 * ax);
-    const OctNb p = oct_nb(E, E, nbr, ghostE, ghostE, o, ch, 2 * ax + 1);
-    acc[3 * c + ax] = g_scale * (p.E - m.E);
+    const double em = oct_nbE(E, nbr, ghostE, o, ch, 2 * ax);
+    const double ep = oct_nbE(E, nbr, ghostE, o, ch, 2 * ax + 1);
+    acc[3 * c + ax] = g_scale * (ep - em);
   }
 }
 
@@ -743,8 +418,10 @@ __global__ void k_oct_force(const double* __restrict__ E, const int* __restrict_
 static AmrWork* W(mgfr_ctx* c) { return (AmrWork*)c->amr; }
 
 static void free_level(AmrLevel& L) {
-  void* ps[] = {L.son, L.refined, L.count, L.opos, L.pcell, L.nbr, L.mass, L.w, L.wE, L.wf,
-                L.wold, L.mask, L.ghost, L.ghostE, L.acc};
+  void* ps[] = {L.son,  L.refined, L.count,  L.opos, L.pcell,   L.nbr,     L.mass,
+                L.w,    L.wE,      L.wf,     L.wold, L.mask,    L.ghost,   L.ghostE,
+                L.acc,  L.pnbr,    L.w32,    L.wE32, L.wf32,    L.wold32,  L.ghost32,
+                L.ghostE32};
   for (void* p : ps)
     if (p) cudaFree(p);
   // u, E, f of level >= 1 are owned here too
@@ -771,7 +448,7 @@ void amr_free(mgfr_ctx* c) {
   c->amr = nullptr;
 }
 
-static TreeView tree_view(const AmrWork* A) {
+TreeView tree_view(const AmrWork* A) {
   TreeView T{};
   T.nlev = A->nlev;
   T.lg0 = A->lg0;
@@ -814,6 +491,8 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
   L.son = nullptr; L.refined = nullptr; L.count = nullptr; L.opos = nullptr; L.pcell = nullptr;
   L.nbr = nullptr; L.mass = nullptr; L.w = nullptr; L.wE = nullptr; L.wf = nullptr;
   L.wold = nullptr; L.mask = nullptr; L.ghost = nullptr; L.ghostE = nullptr; L.acc = nullptr;
+  L.pnbr = nullptr; L.w32 = nullptr; L.wE32 = nullptr; L.wf32 = nullptr; L.wold32 = nullptr;
+  L.ghost32 = nullptr; L.ghostE32 = nullptr;
   TRY(grow(c, &L.son, n));
   TRY(grow(c, &L.refined, n));
   TRY(grow(c, &L.count, n));
@@ -823,7 +502,14 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
   TRY(grow(c, &L.wf, n));
   TRY(grow(c, &L.wold, n));
   TRY(grow(c, &L.mask, n));
+  TRY(grow(c, &L.w32, n));
+  TRY(grow(c, &L.wE32, n));
+  TRY(grow(c, &L.wf32, n));
+  TRY(grow(c, &L.wold32, n));
   if (l > 0) {
+    TRY(grow(c, &L.pnbr, 6 * no));
+    TRY(grow(c, &L.ghost32, 24 * no));
+    TRY(grow(c, &L.ghostE32, 24 * no));
     TRY(grow(c, &L.opos, no));
     TRY(grow(c, &L.pcell, no));
     TRY(grow(c, &L.nbr, 6 * no));
@@ -895,7 +581,8 @@ static mgfr_status build_structure(mgfr_ctx* c, AmrWork* A, const double* pos) {
     k_make_octs<<<nblocks(L.ncell, BS), BS, 0, c->s>>>(L.son, L.ncell, l, T, N.pcell, N.opos);
     T = tree_view(A);
     k_oct_nbrs<<<nblocks(N.n_oct, BS), BS, 0, c->s>>>(N.n_oct, l + 1, T, N.nbr);
-    c->launches += 2;
+    k_oct_pnbrs<<<nblocks(N.n_oct, BS), BS, 0, c->s>>>(N.n_oct, l + 1, T, N.pnbr);
+    c->launches += 3;
   }
   // the deepest level has no sons
   AmrLevel& D = A->L[A->nlev - 1];
@@ -920,225 +607,6 @@ static mgfr_status deposit(mgfr_ctx* c, AmrWork* A, const double* pos) {
                                                            A->L[l].pcell, A->L[l - 1].mass);
     c->launches += 1;
   }
-  return MGFR_OK;
-}
-
-// ---- level solves -------------------------------------------------------------
-struct AmrSolveCtx {
-  mgfr_ctx* c;
-  AmrWork* A;
-  Model m;
-  int L;          // level being solved
-  float mthr;
-  long long updates;
-};
-
-// Dense view of the base level's work arrays (mask included).
-static DenseLevel base_work(AmrWork* A, const DenseHier& H) {
-  DenseLevel D = H.L[0];
-  AmrLevel& B = A->L[0];
-  D.u = B.w;
-  D.E = B.wE;
-  D.f = B.wf;
-  D.uold = B.wold;
-  D.mask = B.mask;
-  return D;
-}
-
-static DenseLevel sub_work(AmrWork* A, const DenseHier& H, int k, float mthr) {
-  DenseLevel D = H.L[k];
-  D.mask = A->dmask[k];
-  D.mthr = mthr;
-  return D;
-}
-
-void prof_reserve_public(mgfr_ctx* c, size_t pairs);
-
-static void relax_tree(AmrSolveCtx& S, int l, int sweeps) {
-  mgfr_ctx* c = S.c;
-  AmrWork* A = S.A;
-  const mgfr_config& g = c->cfg;
-  AmrLevel& L = A->L[l];
-  for (int s = 0; s < sweeps; ++s) {
-    for (int col = 0; col < 2; ++col) {
-      if (l >= 1) {
-        if (l == S.L) prof_begin(c, 3, L.ncell);
-        k_oct_sweep<<<nblocks(4 * L.n_oct, BS), BS, 0, c->s>>>(
-            L.w, L.wE, L.wf, L.nbr, L.ghost, L.ghostE, l == S.L ? nullptr : L.mask, S.mthr,
-            L.n_oct, col, S.m, L.ih2, g.step_cap);
-        if (l == S.L) prof_end(c);
-      } else {
-        DenseLevel D = base_work(A, c->dh);
-        D.mthr = S.mthr;
-        f64::sweep(D, S.m, col, g.step_cap, c->s);
-      }
-      c->launches += 1;
-    }
-    S.updates += L.relaxed;
-  }
-}
-
-static void vcycle_dense_masked(AmrSolveCtx& S, int k);
-
-// Masked FAS V-cycle of the level-S.L solve, entered at tree level l >= 0.
-static void vcycle_tree(AmrSolveCtx& S, int l) {
-  mgfr_ctx* c = S.c;
-  AmrWork* A = S.A;
-  const mgfr_config& g = c->cfg;
-  AmrLevel& F = A->L[l];
-  relax_tree(S, l, g.n_pre);
-  if (l >= 1) {
-    AmrLevel& P = A->L[l - 1];
-    k_oct_restrict<<<nblocks(F.n_oct, BS), BS, 0, c->s>>>(
-        F.w, F.wE, F.wf, F.nbr, F.ghost, F.ghostE, l == S.L ? nullptr : F.mask, S.mthr, F.n_oct,
-        F.pcell, S.m, F.ih2, P.w, P.wE, P.wold, P.wf);
-    if (l - 1 >= 1) {
-      k_oct_fas<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(P.w, P.wE, P.wf, P.nbr, P.mask, S.mthr,
-                                                       P.ncell, S.m, P.ih2);
-    } else {
-      DenseLevel D = base_work(A, c->dh);
-      D.mthr = S.mthr;
-      f64::fas_rhs(D, S.m, c->s);
-    }
-    c->launches += 2;
-    vcycle_tree(S, l - 1);
-    TreeView T = tree_view(A);
-    k_oct_prolong<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(
-        F.ncell, l, T, F.pcell, P.w, P.wold, l == S.L ? nullptr : F.mask, S.mthr,
-        g.prolong_linear, F.w, F.wE);
-    c->launches += 1;
-  } else {
-    // base level -> dense levels below it
-    DenseHier& H = c->dh;
-    DenseLevel B = base_work(A, H);
-    B.mthr = S.mthr;
-    DenseLevel C1 = sub_work(A, H, 1, S.mthr);
-    f64::restrict_resid(B, C1, S.m, c->s);
-    f64::fas_rhs(C1, S.m, c->s);
-    c->launches += 2;
-    vcycle_dense_masked(S, 1);
-    f64::prolong_corr(B, C1, g.prolong_linear, c->s);
-    c->launches += 1;
-  }
-  relax_tree(S, l, g.n_post);
-}
-
-static void vcycle_dense_masked(AmrSolveCtx& S, int k) {
-  mgfr_ctx* c = S.c;
-  DenseHier& H = c->dh;
-  const mgfr_config& g = c->cfg;
-  DenseLevel F = sub_work(S.A, H, k, S.mthr);
-  if (F.N <= 4) {
-    f64::coarse_solve(F, S.m, g.step_cap, 60, 1e-12, c->s);
-    c->launches += 1;
-    return;
-  }
-  for (int s = 0; s < g.n_pre; ++s) {
-    f64::sweep(F, S.m, 0, g.step_cap, c->s);
-    f64::sweep(F, S.m, 1, g.step_cap, c->s);
-    c->launches += 2;
-  }
-  DenseLevel C = sub_work(S.A, H, k + 1, S.mthr);
-  f64::restrict_resid(F, C, S.m, c->s);
-  f64::fas_rhs(C, S.m, c->s);
-  c->launches += 2;
-  vcycle_dense_masked(S, k + 1);
-  f64::prolong_corr(F, C, g.prolong_linear, c->s);
-  c->launches += 1;
-  for (int s = 0; s < g.n_post; ++s) {
-    f64::sweep(F, S.m, 0, g.step_cap, c->s);
-    f64::sweep(F, S.m, 1, g.step_cap, c->s);
-    c->launches += 2;
-  }
-}
-
-// residual norm of level l (sum r^2, max |r|, sum f^2) -> host hs[0..2]
-static mgfr_status level_norm(mgfr_ctx* c, AmrWork* A, int l, const Model& m, double* hs) {
-  AmrLevel& L = A->L[l];
-  DenseHier& H = c->dh;
-  const int nparts = std::min<long long>(H.nparts / 2, nblocks(L.ncell, BS));
-  k_oct_norm<<<nparts, BS, 0, c->s>>>(L.w, L.wE, L.wf, L.nbr, L.ghost, L.ghostE, L.ncell, m,
-                                      L.ih2, H.partials);
-  k_finish3<<<1, 256, 0, c->s>>>(H.partials, nparts, H.scal + 8);
-  c->launches += 2;
-  MG_CK(c, cudaMemcpyAsync(hs, H.scal + 8, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
-  MG_CK(c, cudaStreamSynchronize(c->s));
-  return MGFR_OK;
-}
-
-static mgfr_status count_relaxed(mgfr_ctx* c, AmrWork* A, const float* mask, long long n,
-                                 float mthr, long long* out) {
-  MG_CK(c, cudaMemsetAsync(A->d_small + 2, 0, sizeof(long long), c->s));
-  k_count_relaxed<<<std::min<long long>(1024, nblocks(n, BS)), BS, 0, c->s>>>(mask, n, mthr,
-                                                                              A->d_small + 2);
-  c->launches += 1;
-  MG_CK(c, cudaMemcpyAsync(out, A->d_small + 2, sizeof(long long), cudaMemcpyDeviceToHost, c->s));
-  MG_CK(c, cudaStreamSynchronize(c->s));
-  return MGFR_OK;
-}
-
-// One-way solve of refined level L (Sec. 3.3, steps 9-10).
-static mgfr_status solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgfr_stats* st) {
-  const mgfr_config& g = c->cfg;
-  DenseHier& H = c->dh;
-  AmrLevel& F = A->L[Lv];
-  const float mthr = (float)g.mask_thres;
-  TreeView T = tree_view(A);
-  const double* up = Lv - 1 == 0 ? H.L[0].u : A->L[Lv - 1].u;
-  // ghosts and initial guess from the converged parent level
-  k_ghosts<<<nblocks(24 * F.n_oct, BS), BS, 0, c->s>>>(F.n_oct, Lv, T, F.nbr, up, g.prolong_linear,
-                                                       F.ghost, F.ghostE);
-  k_oct_init<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.ncell, Lv, T, F.pcell, up,
-                                                    g.prolong_linear, F.w, F.wE);
-  MG_CK(c, cudaMemcpyAsync(F.wf, F.f, sizeof(double) * (size_t)F.ncell, cudaMemcpyDeviceToDevice, c->s));
-  k_fill_f<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.mask, F.ncell, 1.f);
-  c->launches += 3;
-  F.relaxed = F.ncell;
-  // coarse tree levels: work = converged solution; masks averaged down
-  for (int l = Lv - 1; l >= 0; --l) {
-    AmrLevel& P = A->L[l];
-    const double* uu = l == 0 ? H.L[0].u : P.u;
-    const double* EE = l == 0 ? H.L[0].E : P.E;
-    MG_CK(c, cudaMemcpyAsync(P.w, uu, sizeof(double) * (size_t)P.ncell, cudaMemcpyDeviceToDevice, c->s));
-    MG_CK(c, cudaMemcpyAsync(P.wE, EE, sizeof(double) * (size_t)P.ncell, cudaMemcpyDeviceToDevice, c->s));
-    MG_CK(c, cudaMemcpyAsync(P.wold, uu, sizeof(double) * (size_t)P.ncell, cudaMemcpyDeviceToDevice, c->s));
-    MG_CK(c, cudaMemsetAsync(P.mask, 0, sizeof(float) * (size_t)P.ncell, c->s));
-    AmrLevel& Ch = A->L[l + 1];
-    k_mask_up<<<nblocks(Ch.n_oct, BS), BS, 0, c->s>>>(Ch.mask, Ch.n_oct, Ch.pcell, P.mask);
-    c->launches += 1;
-    TRY(count_relaxed(c, A, P.mask, P.ncell, mthr, &P.relaxed));
-  }
-  for (int k = 1; k < H.nlev; ++k) {
-    const float* mf = k == 1 ? A->L[0].mask : A->dmask[k - 1];
-    k_mask_dense<<<nblocks(H.L[k].n, BS), BS, 0, c->s>>>(mf, H.L[k - 1].lg, A->dmask[k]);
-    c->launches += 1;
-  }
-  AmrSolveCtx S{c, A, m, Lv, mthr, 0};
-  if (g.profile) prof_reserve_public(c, 64);
-  double hs[3];
-  TRY(level_norm(c, A, Lv, m, hs));
-  const double fn = std::sqrt(hs[2]), r0 = std::sqrt(hs[0]);
-  const double target = g.tol_rel * (fn > 0.0 ? fn : r0);
-  double r = r0;
-  int it = 0;
-  while (r > target && it < g.max_vcycles) {
-    c->capturing = 3;
-    vcycle_tree(S, Lv);
-    c->capturing = -1;
-    TRY(level_norm(c, A, Lv, m, hs));
-    prof_collect(c, 3, st);
-    r = std::sqrt(hs[0]);
-    ++it;
-    if (!std::isfinite(r)) break;
-  }
-  MG_CK(c, cudaMemcpyAsync(F.u, F.w, sizeof(double) * (size_t)F.ncell, cudaMemcpyDeviceToDevice, c->s));
-  MG_CK(c, cudaMemcpyAsync(F.E, F.wE, sizeof(double) * (size_t)F.ncell, cudaMemcpyDeviceToDevice, c->s));
-  if (st) {
-    st->level_iters[Lv] = it;
-    st->level_res[Lv] = fn > 0.0 ? r / fn : r;
-    st->cell_updates += S.updates;
-  }
-  if (!(r <= target)) return set_err(c, MGFR_E_NOCONVERGE, "refined level did not converge");
   return MGFR_OK;
 }
 
@@ -1219,7 +687,7 @@ mgfr_status mgfr_solve_particles(mgfr_ctx* c, const double* pos, long long Np, i
   if (rs != MGFR_OK && rs != MGFR_E_NOCONVERGE) return rs;
   mgfr_status worst = rs;
   for (int l = 1; l < A->nlev; ++l) {
-    mgfr_status ls = solve_level(c, A, l, m, st);
+    mgfr_status ls = amr_solve_level(c, A, l, m, st);
     if (ls != MGFR_OK && ls != MGFR_E_NOCONVERGE) return ls;
     if (ls != MGFR_OK) worst = ls;
   }

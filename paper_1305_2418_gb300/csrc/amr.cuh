@@ -30,6 +30,10 @@ struct AmrLevel {
   float* mask = nullptr;              // [ncell] multigrid mask
   double *ghost = nullptr, *ghostE = nullptr;  // [n_oct*24]
   double* acc = nullptr;              // [ncell*3] (level >= 1)
+  int* pnbr = nullptr;                // [n_oct*6] parent's face-neighbour cells (-1: none)
+  // FP32 work arrays (mixed precision phase of the level solves)
+  float *w32 = nullptr, *wE32 = nullptr, *wf32 = nullptr, *wold32 = nullptr;
+  float *ghost32 = nullptr, *ghostE32 = nullptr;
   long long relaxed = 0;              // cells relaxed in the current level solve
 };
 
@@ -39,6 +43,46 @@ struct TreeView {
   const int4* opos[AMR_MAXL];
   const int* nbr[AMR_MAXL];
 };
+
+// ---- tree lookups ----------------------------------------------------------
+// Cell at level l with level-l coordinates (I,J,K) (wrapped).  Returns the
+// cell index at the deepest level m <= l that exists on the path, m in *lev.
+static __device__ __forceinline__ long long find_cell(const TreeView& T, int l, long long I, long long J,
+                                               long long K, int* lev) {
+  const long long Nl = 1LL << (T.lg0 + l);
+  I &= Nl - 1;
+  J &= Nl - 1;
+  K &= Nl - 1;
+  long long c = (((I >> l) << T.lg0) + (J >> l) << T.lg0) + (K >> l);
+  for (int m = 1; m <= l; ++m) {
+    const int o = T.son[m - 1][c];
+    if (o < 0) {
+      *lev = m - 1;
+      return c;
+    }
+    const int sh = l - m;
+    c = 8LL * o + (((I >> sh) & 1) << 2) + (((J >> sh) & 1) << 1) + ((K >> sh) & 1);
+  }
+  *lev = l;
+  return c;
+}
+
+static __device__ __forceinline__ void cell_coords(const TreeView& T, int l, long long c, long long* I,
+                                            long long* J, long long* K) {
+  if (l == 0) {
+    const long long M = (1LL << T.lg0) - 1;
+    *K = c & M;
+    *J = (c >> T.lg0) & M;
+    *I = c >> (2 * T.lg0);
+    return;
+  }
+  const int4 p = T.opos[l][c >> 3];
+  const int ch = (int)(c & 7);
+  *I = 2LL * p.x + ((ch >> 2) & 1);
+  *J = 2LL * p.y + ((ch >> 1) & 1);
+  *K = 2LL * p.z + (ch & 1);
+}
+
 
 struct AmrWork {
   int N0 = 0, lg0 = 0, nlev = 0;
@@ -56,3 +100,7 @@ struct AmrWork {
 };
 
 void amr_free(mgfr_ctx* c);
+TreeView tree_view(const AmrWork* A);
+// One-way solve of refined level L >= 1 (amr_solve.cu).
+mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int L, const Model& m, mgfr_stats* st);
+void prof_reserve_public(mgfr_ctx* c, size_t pairs);

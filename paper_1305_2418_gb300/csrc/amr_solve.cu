@@ -1,0 +1,832 @@
+// amr_solve.cu -- one-way solve of a refined level (Puchwein, Baldi & Springel
+// 2013, Sec. 3.3, steps 9-12 and the mask function of the multigrid on
+// partial levels).
+//
+// Level L is relaxed with red-black Newton-Gauss-Seidel on its octs, its ghost
+// layer fixed from the converged level L-1.  The FAS coarse grids are the
+// coarser tree levels and then the dense levels below the base; a coarse cell
+// is relaxed only where its mask (1 on level L, the daughters' average below,
+// 0 without daughters) exceeds mask_thres.  Unrelaxed coarse cells keep the
+// converged coarse solution (or the restriction of their daughters), so the
+// coarse solutions themselves are never modified.
+//
+// Kernels are templated on the working precision T.  The FP64 form runs FP64
+// V-cycles to the tolerance.  The mixed form first runs FP32 V-cycles (e^u
+// stored in FP32, SFU exponentials) until the FP32 residual reaches
+// mixed_switch or stalls, then finishes with FP64 V-cycles from that iterate;
+// the stopping test is always the FP64 residual.
+#include <algorithm>
+#include <cmath>
+
+#include "amr.cuh"
+
+namespace {
+
+constexpr int BS = 256;
+
+template <class T>
+struct MT {
+  T aRt, aRt_np1, inv_np1;
+  int n;
+};
+
+template <class T>
+MT<T> mt(const Model& m) {
+  return MT<T>{(T)m.aRt, (T)m.aRt_np1, (T)m.inv_np1, m.n};
+}
+
+__device__ __forceinline__ double ex(double x) { return exp(x); }
+__device__ __forceinline__ float ex(float x) { return __expf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+
+// e^{-u/(n+1)} (1/sqrt(E) for n = 1)
+template <class T>
+__device__ __forceinline__ T nls(T u, T E, const MT<T>& m) {
+  return m.n == 1 ? rsq(E) : ex(-u * m.inv_np1);
+}
+
+template <class T>
+struct NB {
+  T u, E;
+};
+
+// neighbour of cell (o, ch) in direction d: same oct, neighbouring oct, or
+// the ghost slot of that face.
+template <class T>
+__device__ __forceinline__ NB<T> onb(const T* __restrict__ u, const T* __restrict__ E,
+                                     const int* __restrict__ nbr, const T* __restrict__ gh,
+                                     const T* __restrict__ ghE, long long o, int ch, int d) {
+  const int ax = d >> 1, plus = d & 1;
+  const int bit = (ch >> (2 - ax)) & 1;
+  const int chn = ch ^ (1 << (2 - ax));
+  if (bit != plus) {
+    const long long q = 8 * o + chn;
+    return NB<T>{u[q], E[q]};
+  }
+  const int no = nbr[6 * o + d];
+  if (no >= 0) {
+    const long long q = 8LL * no + chn;
+    return NB<T>{u[q], E[q]};
+  }
+  const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+  const int qi = (((ch >> (2 - t1)) & 1) << 1) | ((ch >> (2 - t2)) & 1);
+  const long long g = 24 * o + 4 * d + qi;
+  return NB<T>{gh[g], ghE[g]};
+}
+
+// L_i (Sec. 3.2) from the centre and its six neighbours
+template <class T>
+__device__ __forceinline__ T Lval(T uc, T Ec, const NB<T>* nb, const MT<T>& m, T ih2) {
+  T sbd = 0;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) sbd = fma((T)0.5 * (nb[q].E + Ec), nb[q].u - uc, sbd);
+  return sbd * ih2 + m.aRt * ((T)1 - nls(uc, Ec, m));
+}
+
+// Newton step (L - f)/(dL/du), clamped (Sec. 3.3, eq. iterative_correction)
+template <class T>
+__device__ __forceinline__ T newton(T uc, T Ec, const NB<T>* nb, T f, const MT<T>& m, T ih2, T cap) {
+  T sbd = 0, sd = 0, sb = 0;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const T b = (T)0.5 * (nb[q].E + Ec), du = nb[q].u - uc;
+    sbd = fma(b, du, sbd);
+    sd += du;
+    sb += b;
+  }
+  const T s = nls(uc, Ec, m);
+  const T L = sbd * ih2 + m.aRt * ((T)1 - s);
+  const T dL = ((T)0.5 * Ec * sd - sb) * ih2 + m.aRt_np1 * s;
+  T step = (L - f) / dL;
+  return fmin(fmax(step, -cap), cap);
+}
+
+__constant__ int kColourChild[2][4] = {{0, 3, 5, 6}, {1, 2, 4, 7}};
+
+template <class T>
+__global__ void __launch_bounds__(BS) k_osweep(T* __restrict__ u, T* __restrict__ E,
+                                               const T* __restrict__ f, const int* __restrict__ nbr,
+                                               const T* __restrict__ gh, const T* __restrict__ ghE,
+                                               const float* __restrict__ mask, float mthr,
+                                               long long n_oct, int colour, MT<T> m, T ih2, T cap) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= 4 * n_oct) return;
+  const long long o = t >> 2;
+  const int ch = kColourChild[colour][t & 3];
+  const long long c = 8 * o + ch;
+  if (mask && !(mask[c] > mthr)) return;
+  NB<T> nb[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
+  const T uc = u[c];
+  const T un = uc - newton(uc, E[c], nb, f[c], m, ih2, cap);
+  u[c] = un;
+  E[c] = ex(un);
+}
+
+// restrict oct level to its parents: u average, masked residual average
+template <class T>
+__global__ void __launch_bounds__(BS) k_orestrict(
+    const T* __restrict__ u, const T* __restrict__ E, const T* __restrict__ f,
+    const int* __restrict__ nbr, const T* __restrict__ gh, const T* __restrict__ ghE,
+    const float* __restrict__ mask, float mthr, long long n_oct, const int* __restrict__ pcell,
+    MT<T> m, T ih2, T* __restrict__ uc, T* __restrict__ Ec, T* __restrict__ ucold,
+    T* __restrict__ fc) {
+  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (o >= n_oct) return;
+  T su = 0, sr = 0;
+  for (int ch = 0; ch < 8; ++ch) {
+    const long long c = 8 * o + ch;
+    su += u[c];
+    if (!mask || mask[c] > mthr) {
+      NB<T> nb[6];
+#pragma unroll
+      for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
+      sr += f[c] - Lval(u[c], E[c], nb, m, ih2);
+    }
+  }
+  const int p = pcell[o];
+  const T um = (T)0.125 * su;
+  uc[p] = um;
+  ucold[p] = um;
+  Ec[p] = ex(um);
+  fc[p] = (T)0.125 * sr;
+}
+
+// FAS right-hand side on a coarse oct level: f += L(u) at relaxed cells
+template <class T>
+__global__ void __launch_bounds__(BS) k_ofas(const T* __restrict__ u, const T* __restrict__ E,
+                                             T* __restrict__ f, const int* __restrict__ nbr,
+                                             const T* __restrict__ gh, const T* __restrict__ ghE,
+                                             const float* __restrict__ mask, float mthr,
+                                             long long ncell, MT<T> m, T ih2) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= ncell || !(mask[c] > mthr)) return;
+  const long long o = c >> 3;
+  const int ch = (int)(c & 7);
+  NB<T> nb[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
+  f[c] += Lval(u[c], E[c], nb, m, ih2);
+}
+
+// u += P(uc - ucold) on relaxed cells (eq. fine_correction), the parent's
+// neighbours from the pnbr table (a gradient component is 0 where one is
+// missing).
+template <class T>
+__global__ void __launch_bounds__(BS) k_oprolong(long long ncell, const int* __restrict__ pcell,
+                                                 const int* __restrict__ pnbr,
+                                                 const T* __restrict__ uc,
+                                                 const T* __restrict__ ucold,
+                                                 const float* __restrict__ mask, float mthr,
+                                                 int linear, T* __restrict__ u, T* __restrict__ E) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  if (mask && !(mask[c] > mthr)) return;
+  const long long o = c >> 3;
+  const int ch = (int)(c & 7);
+  const int p = pcell[o];
+  T v = uc[p] - ucold[p];
+  if (linear) {
+    for (int ax = 0; ax < 3; ++ax) {
+      const int pm = pnbr[6 * o + 2 * ax], pp = pnbr[6 * o + 2 * ax + 1];
+      if (pm < 0 || pp < 0) continue;
+      const T s = ((ch >> (2 - ax)) & 1) ? (T)0.125 : (T)-0.125;
+      v += s * ((uc[pp] - ucold[pp]) - (uc[pm] - ucold[pm]));
+    }
+  }
+  const T un = u[c] + v;
+  u[c] = un;
+  E[c] = ex(un);
+}
+
+// residual norms of level L (sum r^2, max |r|, sum f^2), accumulated in FP64
+template <class T>
+__global__ void __launch_bounds__(BS) k_onorm(const T* __restrict__ u, const T* __restrict__ E,
+                                              const T* __restrict__ f, const int* __restrict__ nbr,
+                                              const T* __restrict__ gh, const T* __restrict__ ghE,
+                                              long long ncell, MT<T> m, T ih2,
+                                              double* __restrict__ partials) {
+  double ss = 0.0, mx = 0.0, fs = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    const long long o = c >> 3;
+    const int ch = (int)(c & 7);
+    NB<T> nb[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
+    const double r = (double)(f[c] - Lval(u[c], E[c], nb, m, ih2));
+    ss = fma(r, r, ss);
+    mx = fmax(mx, fabs(r));
+    fs = fma((double)f[c], (double)f[c], fs);
+  }
+  __shared__ double s1[BS / 32], s2[BS / 32], s3[BS / 32];
+  for (int q = 16; q > 0; q >>= 1) {
+    ss += __shfl_xor_sync(0xffffffffu, ss, q);
+    fs += __shfl_xor_sync(0xffffffffu, fs, q);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, q));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s1[threadIdx.x >> 5] = ss;
+    s2[threadIdx.x >> 5] = mx;
+    s3[threadIdx.x >> 5] = fs;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, e = 0.0;
+    for (int w = 0; w < BS / 32; ++w) {
+      a += s1[w];
+      b = fmax(b, s2[w]);
+      e += s3[w];
+    }
+    partials[3 * blockIdx.x] = a;
+    partials[3 * blockIdx.x + 1] = b;
+    partials[3 * blockIdx.x + 2] = e;
+  }
+}
+
+__global__ void k_finish3(const double* __restrict__ partials, int nparts, double* __restrict__ out) {
+  __shared__ double s1[256], s2[256], s3[256];
+  double a = 0.0, b = 0.0, e = 0.0;
+  for (int q = threadIdx.x; q < nparts; q += blockDim.x) {
+    a += partials[3 * q];
+    b = fmax(b, partials[3 * q + 1]);
+    e += partials[3 * q + 2];
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  s3[threadIdx.x] = e;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      s1[threadIdx.x] += s1[threadIdx.x + w];
+      s2[threadIdx.x] = fmax(s2[threadIdx.x], s2[threadIdx.x + w]);
+      s3[threadIdx.x] += s3[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = s1[0];
+    out[1] = s2[0];
+    out[2] = s3[0];
+  }
+}
+
+// ---- dense levels (base and below) with masks, u and E stored ------------
+__device__ __forceinline__ long long cidx(int i, int j, int k, int lg) {
+  return ((((long long)i << lg) + j) << lg) + k;
+}
+
+template <class T>
+__device__ __forceinline__ void dnb(const T* __restrict__ u, const T* __restrict__ E, int i, int j,
+                                    int k, int lg, NB<T>* nb) {
+  const int M = (1 << lg) - 1;
+  const long long q[6] = {cidx((i - 1) & M, j, k, lg), cidx((i + 1) & M, j, k, lg),
+                          cidx(i, (j - 1) & M, k, lg), cidx(i, (j + 1) & M, k, lg),
+                          cidx(i, j, (k - 1) & M, lg), cidx(i, j, (k + 1) & M, lg)};
+#pragma unroll
+  for (int d = 0; d < 6; ++d) nb[d] = NB<T>{u[q[d]], E[q[d]]};
+}
+
+template <class T>
+__global__ void __launch_bounds__(BS) k_dsweep(T* __restrict__ u, T* __restrict__ E,
+                                               const T* __restrict__ f, int lg, int colour, MT<T> m,
+                                               T ih2, T cap, const float* __restrict__ mask,
+                                               float mthr) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int N = 1 << lg, M = N - 1;
+  if (t >= (1LL << (3 * lg - 1))) return;
+  const int k2 = (int)(t & ((N >> 1) - 1));
+  const long long r = t >> (lg - 1);
+  const int j = (int)(r & M), i = (int)(r >> lg);
+  const int k = 2 * k2 + ((i + j + colour) & 1);
+  const long long c = cidx(i, j, k, lg);
+  if (mask && !(mask[c] > mthr)) return;
+  NB<T> nb[6];
+  dnb(u, E, i, j, k, lg, nb);
+  const T uc = u[c];
+  const T un = uc - newton(uc, E[c], nb, f[c], m, ih2, cap);
+  u[c] = un;
+  E[c] = ex(un);
+}
+
+template <class T>
+__global__ void __launch_bounds__(BS) k_drestrict(const T* __restrict__ u, const T* __restrict__ E,
+                                                  const T* __restrict__ f, int lgf,
+                                                  T* __restrict__ uc, T* __restrict__ Ec,
+                                                  T* __restrict__ ucold, T* __restrict__ fc, MT<T> m,
+                                                  T ih2, const float* __restrict__ mask, float mthr) {
+  const int lgc = lgf - 1, Nc = 1 << lgc;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (1LL << (3 * lgc))) return;
+  const int K = (int)(t & (Nc - 1)), J = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
+  T su = 0, sr = 0;
+  for (int q = 0; q < 8; ++q) {
+    const int i = 2 * I + (q >> 2), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q & 1);
+    const long long c = cidx(i, j, k, lgf);
+    su += u[c];
+    if (!mask || mask[c] > mthr) {
+      NB<T> nb[6];
+      dnb(u, E, i, j, k, lgf, nb);
+      sr += f[c] - Lval(u[c], E[c], nb, m, ih2);
+    }
+  }
+  const T um = (T)0.125 * su;
+  uc[t] = um;
+  ucold[t] = um;
+  Ec[t] = ex(um);
+  fc[t] = (T)0.125 * sr;
+}
+
+template <class T>
+__global__ void __launch_bounds__(BS) k_dfas(const T* __restrict__ u, const T* __restrict__ E,
+                                             T* __restrict__ f, int lg, MT<T> m, T ih2,
+                                             const float* __restrict__ mask, float mthr) {
+  const int N = 1 << lg;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (1LL << (3 * lg))) return;
+  if (mask && !(mask[t] > mthr)) return;
+  const int k = (int)(t & (N - 1)), j = (int)((t >> lg) & (N - 1)), i = (int)(t >> (2 * lg));
+  NB<T> nb[6];
+  dnb(u, E, i, j, k, lg, nb);
+  f[t] += Lval(u[t], E[t], nb, m, ih2);
+}
+
+template <class T>
+__global__ void __launch_bounds__(BS) k_dprolong(T* __restrict__ u, T* __restrict__ E,
+                                                 const T* __restrict__ uc, const T* __restrict__ ucold,
+                                                 int lgf, int linear, const float* __restrict__ mask,
+                                                 float mthr) {
+  const int N = 1 << lgf, lgc = lgf - 1, Mc = (N >> 1) - 1;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (1LL << (3 * lgf))) return;
+  if (mask && !(mask[t] > mthr)) return;
+  const int k = (int)(t & (N - 1)), j = (int)((t >> lgf) & (N - 1)), i = (int)(t >> (2 * lgf));
+  const int I = i >> 1, J = j >> 1, K = k >> 1;
+  auto corr = [&](int a, int b, int c) {
+    const long long q = cidx(a & Mc, b & Mc, c & Mc, lgc);
+    return uc[q] - ucold[q];
+  };
+  T v = corr(I, J, K);
+  if (linear) {
+    v += ((i & 1) ? (T)0.125 : (T)-0.125) * (corr(I + 1, J, K) - corr(I - 1, J, K));
+    v += ((j & 1) ? (T)0.125 : (T)-0.125) * (corr(I, J + 1, K) - corr(I, J - 1, K));
+    v += ((k & 1) ? (T)0.125 : (T)-0.125) * (corr(I, J, K + 1) - corr(I, J, K - 1));
+  }
+  const T un = u[t] + v;
+  u[t] = un;
+  E[t] = ex(un);
+}
+
+// masked NGS on the 4^3 grid, fixed sweep count (one block of 64 threads)
+template <class T>
+__global__ void __launch_bounds__(64) k_dcoarse(T* __restrict__ ug, T* __restrict__ Eg,
+                                                const T* __restrict__ fg, MT<T> m, T ih2, T cap,
+                                                int sweeps, const float* __restrict__ mask,
+                                                float mthr) {
+  __shared__ T u[64], E[64];
+  const int t = threadIdx.x;
+  u[t] = ug[t];
+  E[t] = Eg[t];
+  const T f = fg[t];
+  const bool active = !mask || mask[t] > mthr;
+  const int i = t >> 4, j = (t >> 2) & 3, k = t & 3, colour = (i + j + k) & 1;
+  const int q[6] = {(((i + 3) & 3) << 4) | (j << 2) | k, (((i + 1) & 3) << 4) | (j << 2) | k,
+                    (i << 4) | (((j + 3) & 3) << 2) | k, (i << 4) | (((j + 1) & 3) << 2) | k,
+                    (i << 4) | (j << 2) | ((k + 3) & 3), (i << 4) | (j << 2) | ((k + 1) & 3)};
+  __syncthreads();
+  for (int s = 0; s < sweeps; ++s)
+    for (int col = 0; col < 2; ++col) {
+      if (colour == col && active) {
+        NB<T> nb[6];
+        for (int d = 0; d < 6; ++d) nb[d] = NB<T>{u[q[d]], E[q[d]]};
+        const T un = u[t] - newton(u[t], E[t], nb, f, m, ih2, cap);
+        u[t] = un;
+        E[t] = ex(un);
+      }
+      __syncthreads();
+    }
+  ug[t] = u[t];
+  Eg[t] = E[t];
+}
+
+// ---- set-up kernels --------------------------------------------------------
+// initial guess of level L from the converged level L-1 (linear
+// reconstruction with the parent's neighbours), FP64 and FP32 copies
+__global__ void k_init_level(long long ncell, const int* __restrict__ pcell,
+                             const int* __restrict__ pnbr, const double* __restrict__ up,
+                             int linear, double* __restrict__ w, double* __restrict__ wE,
+                             float* __restrict__ w32, float* __restrict__ wE32) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const long long o = c >> 3;
+  const int ch = (int)(c & 7);
+  double v = up[pcell[o]];
+  if (linear) {
+    for (int ax = 0; ax < 3; ++ax) {
+      const int pm = pnbr[6 * o + 2 * ax], pp = pnbr[6 * o + 2 * ax + 1];
+      if (pm < 0 || pp < 0) continue;
+      v += (((ch >> (2 - ax)) & 1) ? 0.125 : -0.125) * (up[pp] - up[pm]);
+    }
+  }
+  w[c] = v;
+  wE[c] = exp(v);
+  if (w32) {
+    w32[c] = (float)v;
+    wE32[c] = __expf((float)v);
+  }
+}
+
+// Ghost layer of level l: the level-l cells across every oct face without a
+// neighbouring oct take the linear reconstruction of their (converged)
+// parent on level l-1; fixed during the level solve.
+__global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restrict__ nbr,
+                         const double* __restrict__ up, int linear, double* __restrict__ ghost,
+                         double* __restrict__ ghostE, float* __restrict__ g32,
+                         float* __restrict__ gE32) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= 24 * n_oct) return;
+  const long long o = t / 24;
+  const int d = (int)((t % 24) >> 2), qi = (int)(t & 3);
+  if (nbr[6 * o + d] >= 0) return;
+  const int ax = d >> 1, plus = d & 1;
+  const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+  int b[3];
+  b[ax] = plus;
+  b[t1] = (qi >> 1) & 1;
+  b[t2] = qi & 1;
+  const int4 p = T.opos[l][o];
+  long long C[3] = {2LL * p.x + b[0], 2LL * p.y + b[1], 2LL * p.z + b[2]};
+  C[ax] += plus ? 1 : -1;
+  const long long Nl = 1LL << (T.lg0 + l);
+  for (int a = 0; a < 3; ++a) C[a] &= Nl - 1;
+  int lev;
+  const long long P[3] = {C[0] >> 1, C[1] >> 1, C[2] >> 1};
+  const long long pc = find_cell(T, l - 1, P[0], P[1], P[2], &lev);
+  double v = 0.0;
+  if (lev == l - 1) {
+    v = up[pc];
+    if (linear) {
+      for (int a = 0; a < 3; ++a) {
+        long long Qp[3] = {P[0], P[1], P[2]}, Qm[3] = {P[0], P[1], P[2]};
+        Qp[a] += 1;
+        Qm[a] -= 1;
+        int lp, lm;
+        const long long cp = find_cell(T, l - 1, Qp[0], Qp[1], Qp[2], &lp);
+        const long long cm = find_cell(T, l - 1, Qm[0], Qm[1], Qm[2], &lm);
+        if (lp != l - 1 || lm != l - 1) continue;
+        v += ((C[a] & 1) ? 0.125 : -0.125) * (up[cp] - up[cm]);
+      }
+    }
+  }
+  ghost[t] = v;
+  ghostE[t] = exp(v);
+  g32[t] = (float)v;
+  gE32[t] = __expf((float)v);
+}
+
+__global__ void k_d2f(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+
+// FP64 iterate from the FP32 one: w = w32, wE = e^w
+__global__ void k_f2d_exp(const float* __restrict__ w32, double* __restrict__ w,
+                          double* __restrict__ wE, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = (double)w32[i];
+  w[i] = v;
+  wE[i] = exp(v);
+}
+
+__global__ void k_mask_up(const float* __restrict__ mchild, long long n_oct,
+                          const int* __restrict__ pcell, float* __restrict__ mparent) {
+  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (o >= n_oct) return;
+  float s = 0.f;
+  for (int q = 0; q < 8; ++q) s += mchild[8 * o + q];
+  mparent[pcell[o]] = 0.125f * s;
+}
+
+__global__ void k_mask_dense(const float* __restrict__ mf, int lgf, float* __restrict__ mc) {
+  const int lgc = lgf - 1, Nc = 1 << lgc;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (1LL << (3 * lgc))) return;
+  const int K = (int)(t & (Nc - 1)), J = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
+  float s = 0.f;
+  for (int q = 0; q < 8; ++q)
+    s += mf[cidx(2 * I + (q >> 2), 2 * J + ((q >> 1) & 1), 2 * K + (q & 1), lgf)];
+  mc[t] = 0.125f * s;
+}
+
+__global__ void k_fill_f(float* __restrict__ x, long long n, float v) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+
+__global__ void k_count_relaxed(const float* __restrict__ mask, long long n, float mthr,
+                                long long* __restrict__ out) {
+  long long cnt = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    cnt += mask[i] > mthr;
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd((unsigned long long*)out, (unsigned long long)cnt);
+}
+
+}  // namespace
+
+// ============================================================================
+// host orchestration
+// ============================================================================
+namespace {
+
+// work arrays of one tree level in precision T
+template <class T>
+struct TA {
+  T *w, *wE, *wf, *wold, *gh, *ghE;
+};
+
+template <class T>
+TA<T> tarr(AmrLevel& L);
+template <>
+TA<double> tarr<double>(AmrLevel& L) {
+  return TA<double>{L.w, L.wE, L.wf, L.wold, L.ghost, L.ghostE};
+}
+template <>
+TA<float> tarr<float>(AmrLevel& L) {
+  return TA<float>{L.w32, L.wE32, L.wf32, L.wold32, L.ghost32, L.ghostE32};
+}
+
+// work arrays of dense level k of the hierarchy below the base (k >= 1)
+template <class T>
+TA<T> darr(DenseLevel& D);
+template <>
+TA<double> darr<double>(DenseLevel& D) {
+  return TA<double>{D.u, D.E, D.f, D.uold, nullptr, nullptr};
+}
+template <>
+TA<float> darr<float>(DenseLevel& D) {
+  return TA<float>{D.u32, D.e32, D.f32, D.uold32, nullptr, nullptr};
+}
+
+struct SolveCtx {
+  mgfr_ctx* c;
+  AmrWork* A;
+  Model m;
+  int L;
+  float mthr;
+  long long updates;
+};
+
+template <class T>
+void relax(SolveCtx& S, int l, int sweeps) {
+  mgfr_ctx* c = S.c;
+  AmrLevel& L = S.A->L[l];
+  const mgfr_config& g = c->cfg;
+  const MT<T> m = mt<T>(S.m);
+  TA<T> a = tarr<T>(L);
+  for (int s = 0; s < sweeps; ++s) {
+    for (int col = 0; col < 2; ++col) {
+      if (l >= 1) {
+        if (l == S.L) prof_begin(c, 3, L.ncell);
+        k_osweep<T><<<nblocks(4 * L.n_oct, BS), BS, 0, c->s>>>(
+            a.w, a.wE, a.wf, L.nbr, a.gh, a.ghE, l == S.L ? nullptr : L.mask, S.mthr, L.n_oct,
+            col, m, (T)L.ih2, (T)g.step_cap);
+        if (l == S.L) prof_end(c);
+      } else {
+        const int lg = L.lgN;
+        k_dsweep<T><<<nblocks(L.ncell / 2, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, lg, col, m,
+                                                              (T)L.ih2, (T)g.step_cap, L.mask,
+                                                              S.mthr);
+      }
+      c->launches += 1;
+    }
+    S.updates += L.relaxed;
+  }
+}
+
+template <class T>
+void vcycle_dense(SolveCtx& S, int k) {
+  mgfr_ctx* c = S.c;
+  const mgfr_config& g = c->cfg;
+  DenseHier& H = c->dh;
+  DenseLevel& F = H.L[k];
+  const float* mk = S.A->dmask[k];
+  const MT<T> m = mt<T>(S.m);
+  TA<T> a = darr<T>(F);
+  if (F.N <= 4) {
+    k_dcoarse<T><<<1, 64, 0, c->s>>>(a.w, a.wE, a.wf, m, (T)F.ih2, (T)g.step_cap, 20, mk, S.mthr);
+    c->launches += 1;
+    return;
+  }
+  for (int s = 0; s < g.n_pre; ++s)
+    for (int col = 0; col < 2; ++col) {
+      k_dsweep<T><<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lg, col, m, (T)F.ih2,
+                                                         (T)g.step_cap, mk, S.mthr);
+      c->launches += 1;
+    }
+  DenseLevel& C = H.L[k + 1];
+  TA<T> b = darr<T>(C);
+  k_drestrict<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lg, b.w, b.wE, b.wold,
+                                                    b.wf, m, (T)F.ih2, mk, S.mthr);
+  k_dfas<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, C.lg, m, (T)C.ih2,
+                                               S.A->dmask[k + 1], S.mthr);
+  c->launches += 2;
+  vcycle_dense<T>(S, k + 1);
+  k_dprolong<T><<<nblocks(F.n, BS), BS, 0, c->s>>>(a.w, a.wE, b.w, b.wold, F.lg,
+                                                   g.prolong_linear, mk, S.mthr);
+  c->launches += 1;
+  for (int s = 0; s < g.n_post; ++s)
+    for (int col = 0; col < 2; ++col) {
+      k_dsweep<T><<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lg, col, m, (T)F.ih2,
+                                                         (T)g.step_cap, mk, S.mthr);
+      c->launches += 1;
+    }
+}
+
+// masked FAS V-cycle of the level-S.L solve at tree level l >= 0
+template <class T>
+void vcycle_tree(SolveCtx& S, int l) {
+  mgfr_ctx* c = S.c;
+  AmrWork* A = S.A;
+  const mgfr_config& g = c->cfg;
+  const MT<T> m = mt<T>(S.m);
+  AmrLevel& F = A->L[l];
+  TA<T> a = tarr<T>(F);
+  relax<T>(S, l, g.n_pre);
+  const float* fmask = l == S.L ? nullptr : F.mask;
+  if (l >= 1) {
+    AmrLevel& P = A->L[l - 1];
+    TA<T> b = tarr<T>(P);
+    k_orestrict<T><<<nblocks(F.n_oct, BS), BS, 0, c->s>>>(
+        a.w, a.wE, a.wf, F.nbr, a.gh, a.ghE, fmask, S.mthr, F.n_oct, F.pcell, m, (T)F.ih2, b.w,
+        b.wE, b.wold, b.wf);
+    if (l - 1 >= 1)
+      k_ofas<T><<<nblocks(P.ncell, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, P.nbr, b.gh, b.ghE,
+                                                       P.mask, S.mthr, P.ncell, m, (T)P.ih2);
+    else
+      k_dfas<T><<<nblocks(P.ncell, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, P.lgN, m, (T)P.ih2,
+                                                       P.mask, S.mthr);
+    c->launches += 2;
+    vcycle_tree<T>(S, l - 1);
+    k_oprolong<T><<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.ncell, F.pcell, F.pnbr, b.w, b.wold,
+                                                         fmask, S.mthr, g.prolong_linear, a.w,
+                                                         a.wE);
+    c->launches += 1;
+  } else {
+    DenseHier& H = c->dh;
+    DenseLevel& C = H.L[1];
+    TA<T> b = darr<T>(C);
+    k_drestrict<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lgN, b.w, b.wE, b.wold,
+                                                      b.wf, m, (T)F.ih2, F.mask, S.mthr);
+    k_dfas<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, C.lg, m, (T)C.ih2, A->dmask[1],
+                                                 S.mthr);
+    c->launches += 2;
+    vcycle_dense<T>(S, 1);
+    k_dprolong<T><<<nblocks(F.ncell, BS), BS, 0, c->s>>>(a.w, a.wE, b.w, b.wold, F.lgN,
+                                                         g.prolong_linear, F.mask, S.mthr);
+    c->launches += 1;
+  }
+  relax<T>(S, l, g.n_post);
+}
+
+// residual norms of level L in precision T -> hs[0..2] (sum r^2, max, sum f^2)
+template <class T>
+mgfr_status level_norm(SolveCtx& S, double* hs) {
+  mgfr_ctx* c = S.c;
+  AmrLevel& L = S.A->L[S.L];
+  DenseHier& H = c->dh;
+  TA<T> a = tarr<T>(L);
+  const int nparts = (int)std::min<long long>(H.nparts / 2, nblocks(L.ncell, BS));
+  k_onorm<T><<<nparts, BS, 0, c->s>>>(a.w, a.wE, a.wf, L.nbr, a.gh, a.ghE, L.ncell, mt<T>(S.m),
+                                      (T)L.ih2, H.partials);
+  k_finish3<<<1, 256, 0, c->s>>>(H.partials, nparts, H.scal + 8);
+  c->launches += 2;
+  MG_CK(c, cudaMemcpyAsync(hs, H.scal + 8, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+  MG_CK(c, cudaStreamSynchronize(c->s));
+  return MGFR_OK;
+}
+
+mgfr_status count_relaxed(mgfr_ctx* c, AmrWork* A, const float* mask, long long n, float mthr,
+                          long long* out) {
+  MG_CK(c, cudaMemsetAsync(A->d_small + 2, 0, sizeof(long long), c->s));
+  k_count_relaxed<<<(unsigned)std::min<long long>(1024, nblocks(n, BS)), BS, 0, c->s>>>(
+      mask, n, mthr, A->d_small + 2);
+  c->launches += 1;
+  MG_CK(c, cudaMemcpyAsync(out, A->d_small + 2, sizeof(long long), cudaMemcpyDeviceToHost, c->s));
+  MG_CK(c, cudaStreamSynchronize(c->s));
+  return MGFR_OK;
+}
+
+#define TRY(x)                    \
+  do {                            \
+    mgfr_status s_ = (x);         \
+    if (s_ != MGFR_OK) return s_; \
+  } while (0)
+
+template <class T>
+mgfr_status run_vcycle(SolveCtx& S, mgfr_stats* st, double* hs) {
+  S.c->capturing = 3;
+  vcycle_tree<T>(S, S.L);
+  S.c->capturing = -1;
+  TRY(level_norm<T>(S, hs));
+  prof_collect(S.c, 3, st);
+  return MGFR_OK;
+}
+
+}  // namespace
+
+mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgfr_stats* st) {
+  const mgfr_config& g = c->cfg;
+  DenseHier& H = c->dh;
+  AmrLevel& F = A->L[Lv];
+  const bool mixed = g.precision == MGFR_PREC_MIXED;
+  const float mthr = (float)g.mask_thres;
+  TreeView T = tree_view(A);
+  const double* up = Lv - 1 == 0 ? H.L[0].u : A->L[Lv - 1].u;
+  k_ghosts<<<nblocks(24 * F.n_oct, BS), BS, 0, c->s>>>(F.n_oct, Lv, T, F.nbr, up,
+                                                       g.prolong_linear, F.ghost, F.ghostE,
+                                                       F.ghost32, F.ghostE32);
+  k_init_level<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.ncell, F.pcell, F.pnbr, up,
+                                                      g.prolong_linear, F.w, F.wE,
+                                                      mixed ? F.w32 : nullptr, F.wE32);
+  MG_CK(c, cudaMemcpyAsync(F.wf, F.f, sizeof(double) * (size_t)F.ncell, cudaMemcpyDeviceToDevice,
+                           c->s));
+  k_fill_f<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.mask, F.ncell, 1.f);
+  c->launches += 3;
+  if (mixed) {
+    k_d2f<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.f, F.wf32, F.ncell);
+    c->launches += 1;
+  }
+  F.relaxed = F.ncell;
+  for (int l = Lv - 1; l >= 0; --l) {
+    AmrLevel& P = A->L[l];
+    const double* uu = l == 0 ? H.L[0].u : P.u;
+    const double* EE = l == 0 ? H.L[0].E : P.E;
+    const size_t b8 = sizeof(double) * (size_t)P.ncell;
+    MG_CK(c, cudaMemcpyAsync(P.w, uu, b8, cudaMemcpyDeviceToDevice, c->s));
+    MG_CK(c, cudaMemcpyAsync(P.wE, EE, b8, cudaMemcpyDeviceToDevice, c->s));
+    MG_CK(c, cudaMemcpyAsync(P.wold, uu, b8, cudaMemcpyDeviceToDevice, c->s));
+    if (mixed) {
+      k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(uu, P.w32, P.ncell);
+      k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(EE, P.wE32, P.ncell);
+      k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(uu, P.wold32, P.ncell);
+      c->launches += 3;
+    }
+    MG_CK(c, cudaMemsetAsync(P.mask, 0, sizeof(float) * (size_t)P.ncell, c->s));
+    AmrLevel& Ch = A->L[l + 1];
+    k_mask_up<<<nblocks(Ch.n_oct, BS), BS, 0, c->s>>>(Ch.mask, Ch.n_oct, Ch.pcell, P.mask);
+    c->launches += 1;
+    TRY(count_relaxed(c, A, P.mask, P.ncell, mthr, &P.relaxed));
+  }
+  for (int k = 1; k < H.nlev; ++k) {
+    const float* mf = k == 1 ? A->L[0].mask : A->dmask[k - 1];
+    k_mask_dense<<<nblocks(H.L[k].n, BS), BS, 0, c->s>>>(mf, H.L[k - 1].lg, A->dmask[k]);
+    c->launches += 1;
+  }
+  SolveCtx S{c, A, m, Lv, mthr, 0};
+  if (g.profile) prof_reserve_public(c, 64);
+  double hs[3];
+  TRY(level_norm<double>(S, hs));
+  const double fn = std::sqrt(hs[2]), r0 = std::sqrt(hs[0]);
+  const double ref = fn > 0.0 ? fn : r0;
+  const double target = g.tol_rel * ref;
+  double r = r0;
+  int it = 0, it32 = 0;
+  if (mixed && r > target) {
+    // FP32 V-cycles until mixed_switch or a stall
+    double prev = -1.0;
+    while (it32 < g.max_vcycles) {
+      TRY(run_vcycle<float>(S, st, hs));
+      ++it32;
+      const double r32 = std::sqrt(hs[0]);
+      if (!std::isfinite(r32) || r32 <= g.mixed_switch * ref || (prev > 0.0 && r32 > 0.7 * prev))
+        break;
+      prev = r32;
+    }
+    k_f2d_exp<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.w32, F.w, F.wE, F.ncell);
+    c->launches += 1;
+    TRY(level_norm<double>(S, hs));
+    r = std::sqrt(hs[0]);
+  }
+  while (r > target && it < g.max_vcycles) {
+    TRY(run_vcycle<double>(S, st, hs));
+    r = std::sqrt(hs[0]);
+    ++it;
+    if (!std::isfinite(r)) break;
+  }
+  MG_CK(c, cudaMemcpyAsync(F.u, F.w, sizeof(double) * (size_t)F.ncell, cudaMemcpyDeviceToDevice,
+                           c->s));
+  MG_CK(c, cudaMemcpyAsync(F.E, F.wE, sizeof(double) * (size_t)F.ncell, cudaMemcpyDeviceToDevice,
+                           c->s));
+  if (st) {
+    st->level_iters[Lv] = it + it32;
+    st->level_res[Lv] = r / ref;
+    st->cell_updates += S.updates;
+  }
+  if (!(r <= target)) return set_err(c, MGFR_E_NOCONVERGE, "refined level did not converge");
+  return MGFR_OK;
+}
