@@ -190,6 +190,41 @@ typedef enum {
  * (out_host: ncell doubles, 3 ncell for MGFR_FIELD_ACC). */
 mgfr_status mgfr_get_level_field(mgfr_ctx* ctx, int level, int what, double* out_host);
 
+/* One independent periodic solve of a batch (Sec. 3.2-3.3 per item). */
+typedef struct {
+  int N;                     /* power of two, 8..512                          */
+  double box, a;             /* box [Mpc/h] and scale factor                  */
+  double fr0_abs;            /* |fR_bar0| of this solve (omega_m from cfg)    */
+  int n;                     /* Hu-Sawicki exponent                           */
+  const double* delta_dev;   /* [N^3] density contrast                        */
+  const double* u_init_dev;  /* [N^3] initial guess or NULL (zero start)      */
+  double* fr_out_dev;        /* [N^3] f_R                                     */
+  double* acc_out_dev;       /* [3][N^3] a_MG / c^2, or NULL                  */
+} mgfr_batch_item;
+
+/*
+ * Solve `nsolves` independent periodic grids of mixed sizes in ONE persistent
+ * cooperative kernel launch (replayed from a CUDA graph): every solve runs the
+ * mixed-precision form of mgfr_solve_density (FP32 FAS V-cycles, then FP64
+ * residual with FP32 linear V-cycles on the Jacobian system) to
+ * ||f - L(u)||_2 <= tol_rel ||f||_2.  Solves of different sizes share each
+ * V-cycle phase (aligned on grid size); phases are separated by a software
+ * grid barrier whose waits are bounded by cfg.max_spins (MGFR_E_TIMEOUT if
+ * one gives up; the context stays usable).  per_solve (nullable) receives one
+ * mgfr_stats per item, in item order.  The launch shape (threads per block,
+ * blocks per SM) comes from mgfr_batch_autotune for the same list of sizes,
+ * else 256 x 2.
+ */
+mgfr_status mgfr_batch_solve(mgfr_ctx* ctx, int nsolves, const mgfr_batch_item* items,
+                             mgfr_stats* per_solve);
+
+/* Time the candidate launch shapes (128/256/512 threads x 1/2/4 blocks per
+ * SM) on this batch, keep the fastest for batches with the same sizes (and
+ * append it to the file named by the environment variable MGFR_TUNE_CACHE,
+ * when set).  Runs the batch 9 times; outputs are overwritten. */
+mgfr_status mgfr_batch_autotune(mgfr_ctx* ctx, int nsolves, const mgfr_batch_item* items,
+                                int* best_threads, int* best_blocks_per_sm);
+
 /* Text of the last error seen by this context ("" if none). */
 const char* mgfr_last_error(const mgfr_ctx* ctx);
 

@@ -1,0 +1,925 @@
+// batch.cu -- many independent dense solves in one persistent launch.
+//
+// Each solve is the mixed-precision form of the base-level solve (Puchwein,
+// Baldi & Springel 2013, Sec. 3.3): FP32 nonlinear FAS V-cycles (mode A)
+// until the FP32 residual reaches mixed_switch or stalls, then FP64 defect
+// correction (mode B): r = f - L(u) in FP64, one FP32 linear V-cycle on
+// J(u) e = r, u += e.  All solves advance together through one V-cycle
+// schedule aligned on grid size: at size 2^k every solve with N >= 2^k works
+// on its level of that size, so one phase covers all solves; solves are
+// sorted by N (descending) so the participants of size 2^k are a prefix and
+// every participant has exactly 8^k cells there.  Phases are separated by a
+// software grid barrier (cooperative launch guarantees co-residency); every
+// wait is bounded by max_spins and sets an error flag instead of hanging.
+// Converged solves skip their work items.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "mgfr_internal.cuh"
+
+#define BMAXL 9  // levels per solve: N <= 1024 -> 1024..4
+
+struct BSolve {
+  int N, lg, nlev;
+  float ih2[BMAXL];
+  double ih2_0, h0;
+  float aRt, aRt_np1, inv_np1;  // FP32 model
+  double aRt64, aRt_np1_64, inv_np1_64, src, fbar, gscale;
+  int n;
+  float* u32[BMAXL];
+  float* f32[BMAXL];
+  float* uold32[BMAXL];
+  float* e32[BMAXL];
+  float* r32[BMAXL];
+  double *u64, *E64, *f64;
+  const double* delta;
+  const double* uinit;
+  double* fr_out;
+  double* acc_out;
+};
+
+enum { BM_A = 0, BM_B = 1, BM_TRANS = 2, BM_DONE = 3 };
+
+struct BState {
+  int mode, cyclesA, cyclesB, pad;
+  double ref, target, rprev, r, rmax, r0, fnorm;
+  double acc_ss;                 // accumulated sum of squares
+  unsigned long long acc_max;    // accumulated max (bits of a non-negative double)
+  double acc_ff;
+};
+
+struct BArgs {
+  BSolve* S;
+  BState* st;
+  int ns;
+  int maxlg;
+  int P[16];  // participants per log2 size
+  int n_pre, n_post, linear, max_cycles;
+  float cap32;
+  double cap64, tol, sw;
+  unsigned* bar_count;
+  unsigned* bar_gen;
+  int* err;
+  long long max_spins;
+};
+
+namespace {
+
+__device__ __forceinline__ long long cidx(int i, int j, int k, int lg) {
+  return ((((long long)i << lg) + j) << lg) + k;
+}
+
+// bounded software grid barrier; false when a wait gave up
+__device__ bool gsync(const BArgs& A) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = A.bar_gen;
+    const unsigned g0 = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(A.bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(A.bar_count, 0u);
+      __threadfence();
+      atomicAdd(A.bar_gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g0) {
+        if (++spins > A.max_spins) {
+          atomicExch(A.err, 1);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)A.err == 0;
+}
+
+struct NB6 {
+  float v[6];
+};
+
+__device__ __forceinline__ NB6 nbr6(const float* __restrict__ x, int i, int j, int k, int lg) {
+  const int M = (1 << lg) - 1;
+  NB6 r;
+  r.v[0] = x[cidx((i - 1) & M, j, k, lg)];
+  r.v[1] = x[cidx((i + 1) & M, j, k, lg)];
+  r.v[2] = x[cidx(i, (j - 1) & M, k, lg)];
+  r.v[3] = x[cidx(i, (j + 1) & M, k, lg)];
+  r.v[4] = x[cidx(i, j, (k - 1) & M, lg)];
+  r.v[5] = x[cidx(i, j, (k + 1) & M, lg)];
+  return r;
+}
+
+// FP32 L at a cell (e^u by the SFU)
+__device__ __forceinline__ float L32(const BSolve& S, const float* u, int i, int j, int k, int lg,
+                                     float ih2) {
+  const float uc = u[cidx(i, j, k, lg)], Ec = __expf(uc);
+  const NB6 nb = nbr6(u, i, j, k, lg);
+  float sbd = 0.f;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) sbd = fmaf(0.5f * (__expf(nb.v[q]) + Ec), nb.v[q] - uc, sbd);
+  return sbd * ih2 + S.aRt * (1.f - __expf(-uc * S.inv_np1));
+}
+
+// Jacobian row of L at u (FP32): off-diagonal and diagonal
+__device__ __forceinline__ void jrow(const BSolve& S, float uc, const NB6& un, float ih2,
+                                     float* off, float* diag) {
+  const float Ec = __expf(uc), h2 = 0.5f * ih2;
+  float d = 0.f;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const float En = __expf(un.v[q]), du = un.v[q] - uc;
+    off[q] = h2 * fmaf(En, du, Ec + En);
+    d += fmaf(Ec, du, -Ec - En);
+  }
+  *diag = d * h2 + S.aRt_np1 * __expf(-uc * S.inv_np1);
+}
+
+// ---- per-item operations ---------------------------------------------------
+__device__ void op_sweep(const BArgs& A, const BSolve& S, int mode, int l, int colour,
+                         long long t) {
+  const int lg = S.lg - l, N = 1 << lg, M = N - 1;
+  const int k2 = (int)(t & ((N >> 1) - 1));
+  const long long r = t >> (lg - 1);
+  const int j = (int)(r & M), i = (int)(r >> lg);
+  const int k = 2 * k2 + ((i + j + colour) & 1);
+  const long long c = cidx(i, j, k, lg);
+  const float ih2 = S.ih2[l];
+  if (mode == BM_A) {
+    float* u = S.u32[l];
+    const float uc = u[c], Ec = __expf(uc);
+    const NB6 nb = nbr6(u, i, j, k, lg);
+    float sbd = 0.f, sd = 0.f, sb = 0.f;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const float b = 0.5f * (__expf(nb.v[q]) + Ec), du = nb.v[q] - uc;
+      sbd = fmaf(b, du, sbd);
+      sd += du;
+      sb += b;
+    }
+    const float s = __expf(-uc * S.inv_np1);
+    const float L = sbd * ih2 + S.aRt * (1.f - s);
+    const float dL = (0.5f * Ec * sd - sb) * ih2 + S.aRt_np1 * s;
+    float step = __fdividef(L - S.f32[l][c], dL);
+    step = fminf(fmaxf(step, -A.cap32), A.cap32);
+    u[c] = uc - step;
+  } else {
+    const float* u = S.u32[l];
+    float* e = S.e32[l];
+    const NB6 un = nbr6(u, i, j, k, lg), en = nbr6(e, i, j, k, lg);
+    float off[6], diag;
+    jrow(S, u[c], un, ih2, off, &diag);
+    float s = S.r32[l][c];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) s = fmaf(-off[q], en.v[q], s);
+    e[c] = __fdividef(s, diag);
+  }
+}
+
+// restriction from level l to l+1 at coarse cell t
+__device__ void op_restrict(const BSolve& S, int mode, int l, long long t) {
+  const int lgf = S.lg - l, lgc = lgf - 1, Nc = 1 << lgc;
+  const int K = (int)(t & (Nc - 1)), J = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
+  const float ih2 = S.ih2[l];
+  float su = 0.f, sr = 0.f;
+  for (int q = 0; q < 8; ++q) {
+    const int i = 2 * I + (q >> 2), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q & 1);
+    const long long c = cidx(i, j, k, lgf);
+    const float* u = S.u32[l];
+    su += u[c];
+    if (mode == BM_A) {
+      sr += S.f32[l][c] - L32(S, u, i, j, k, lgf, ih2);
+    } else {
+      const NB6 un = nbr6(u, i, j, k, lgf), en = nbr6(S.e32[l], i, j, k, lgf);
+      float off[6], diag;
+      jrow(S, u[c], un, ih2, off, &diag);
+      float Je = diag * S.e32[l][c];
+#pragma unroll
+      for (int p = 0; p < 6; ++p) Je = fmaf(off[p], en.v[p], Je);
+      sr += S.r32[l][c] - Je;
+    }
+  }
+  if (mode == BM_A) {
+    S.u32[l + 1][t] = 0.125f * su;
+    S.uold32[l + 1][t] = 0.125f * su;
+    S.f32[l + 1][t] = 0.125f * sr;
+  } else {
+    S.u32[l + 1][t] = 0.125f * su;
+    S.r32[l + 1][t] = 0.125f * sr;
+    S.e32[l + 1][t] = 0.f;
+  }
+}
+
+__device__ void op_fas(const BSolve& S, int l, long long t) {
+  const int lg = S.lg - l, N = 1 << lg;
+  const int k = (int)(t & (N - 1)), j = (int)((t >> lg) & (N - 1)), i = (int)(t >> (2 * lg));
+  S.f32[l][t] += L32(S, S.u32[l], i, j, k, lg, S.ih2[l]);
+}
+
+// prolongation from level l+1 to fine cell t of level l
+__device__ void op_prolong(const BArgs& A, const BSolve& S, int mode, int l, long long t) {
+  const int lgf = S.lg - l, N = 1 << lgf, lgc = lgf - 1, Mc = (N >> 1) - 1;
+  const int k = (int)(t & (N - 1)), j = (int)((t >> lgf) & (N - 1)), i = (int)(t >> (2 * lgf));
+  const int I = i >> 1, J = j >> 1, K = k >> 1;
+  const float* uc = mode == BM_A ? S.u32[l + 1] : S.e32[l + 1];
+  const float* uo = mode == BM_A ? S.uold32[l + 1] : nullptr;
+  auto corr = [&](int a, int b, int c) {
+    const long long q = cidx(a & Mc, b & Mc, c & Mc, lgc);
+    return uo ? uc[q] - uo[q] : uc[q];
+  };
+  float v = corr(I, J, K);
+  if (A.linear) {
+    v += ((i & 1) ? 0.125f : -0.125f) * (corr(I + 1, J, K) - corr(I - 1, J, K));
+    v += ((j & 1) ? 0.125f : -0.125f) * (corr(I, J + 1, K) - corr(I, J - 1, K));
+    v += ((k & 1) ? 0.125f : -0.125f) * (corr(I, J, K + 1) - corr(I, J, K - 1));
+  }
+  float* dst = mode == BM_A ? S.u32[l] : S.e32[l];
+  dst[t] += v;
+}
+
+// 4^3 coarse level of one solve by one block (64 threads used)
+__device__ void op_coarse(const BArgs& A, const BSolve& S, int mode) {
+  __shared__ float sh[64], sh2[64];
+  const int l = S.nlev - 1;
+  const int t = threadIdx.x;
+  const bool on = t < 64;
+  const int i = (t >> 4) & 3, j = (t >> 2) & 3, k = t & 3, colour = (i + j + k) & 1;
+  const int q[6] = {(((i + 3) & 3) << 4) | (j << 2) | k, (((i + 1) & 3) << 4) | (j << 2) | k,
+                    (i << 4) | (((j + 3) & 3) << 2) | k, (i << 4) | (((j + 1) & 3) << 2) | k,
+                    (i << 4) | (j << 2) | ((k + 3) & 3), (i << 4) | (j << 2) | ((k + 1) & 3)};
+  const float ih2 = S.ih2[l];
+  if (on) {
+    sh[t] = mode == BM_A ? S.u32[l][t] : S.e32[l][t];
+    sh2[t] = S.u32[l][t];
+  }
+  __syncthreads();
+  float off[6] = {0, 0, 0, 0, 0, 0}, diag = 1.f, rhs = 0.f;
+  if (on && mode != BM_A) {
+    NB6 un;
+    for (int d = 0; d < 6; ++d) un.v[d] = sh2[q[d]];
+    jrow(S, sh2[t], un, ih2, off, &diag);
+    rhs = S.r32[l][t];
+  }
+  const float f = on && mode == BM_A ? S.f32[l][t] : 0.f;
+  for (int s = 0; s < 40; ++s)
+    for (int col = 0; col < 2; ++col) {
+      if (on && colour == col) {
+        if (mode == BM_A) {
+          const float uc = sh[t], Ec = __expf(uc);
+          float sbd = 0.f, sd = 0.f, sb = 0.f;
+          for (int d = 0; d < 6; ++d) {
+            const float un = sh[q[d]], b = 0.5f * (__expf(un) + Ec), du = un - uc;
+            sbd = fmaf(b, du, sbd);
+            sd += du;
+            sb += b;
+          }
+          const float sN = __expf(-uc * S.inv_np1);
+          const float L = sbd * ih2 + S.aRt * (1.f - sN);
+          const float dL = (0.5f * Ec * sd - sb) * ih2 + S.aRt_np1 * sN;
+          float step = (L - f) / dL;
+          step = fminf(fmaxf(step, -A.cap32), A.cap32);
+          sh[t] = uc - step;
+        } else {
+          float acc = rhs;
+          for (int d = 0; d < 6; ++d) acc = fmaf(-off[d], sh[q[d]], acc);
+          sh[t] = acc / diag;
+        }
+      }
+      __syncthreads();
+    }
+  if (on) {
+    if (mode == BM_A)
+      S.u32[l][t] = sh[t];
+    else
+      S.e32[l][t] = sh[t];
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double nls64(const BSolve& S, double u, double E) {
+  return S.n == 1 ? rsqrt(E) : exp(-u * S.inv_np1_64);
+}
+
+// FP64 residual at finest cell t: writes r32, u32 (= u), e32 = 0; returns r
+__device__ double op_resid64(const BSolve& S, long long t) {
+  const int lg = S.lg, M = (1 << lg) - 1;
+  const int k = (int)(t & M), j = (int)((t >> lg) & M), i = (int)(t >> (2 * lg));
+  const long long nb[6] = {cidx((i - 1) & M, j, k, lg), cidx((i + 1) & M, j, k, lg),
+                           cidx(i, (j - 1) & M, k, lg), cidx(i, (j + 1) & M, k, lg),
+                           cidx(i, j, (k - 1) & M, lg), cidx(i, j, (k + 1) & M, lg)};
+  const double uc = S.u64[t], Ec = S.E64[t];
+  double sbd = 0.0;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) sbd = fma(0.5 * (S.E64[nb[q]] + Ec), S.u64[nb[q]] - uc, sbd);
+  const double r = S.f64[t] - (sbd * S.ih2_0 + S.aRt64 * (1.0 - nls64(S, uc, Ec)));
+  S.r32[0][t] = (float)r;
+  S.u32[0][t] = (float)uc;
+  S.e32[0][t] = 0.f;
+  return r;
+}
+
+// warp-level accumulation of (r^2, |r|, f^2) into the solve's state; all
+// lanes of a warp belong to the same solve (per-solve item counts are
+// multiples of 32)
+__device__ __forceinline__ void accum(BState* st, double r, double f, bool live) {
+  double ss = live ? r * r : 0.0, mx = live ? fabs(r) : 0.0, ff = live ? f * f : 0.0;
+  for (int o = 16; o > 0; o >>= 1) {
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    ff += __shfl_xor_sync(0xffffffffu, ff, o);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0 && live) {
+    atomicAdd(&st->acc_ss, ss);
+    atomicAdd(&st->acc_ff, ff);
+    atomicMax(&st->acc_max, (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+// items of size 2^k over the participant prefix: `shift` = log2(items per solve)
+#define FOR_ITEMS(A, k, shift, ...)                                                         \
+  do {                                                                                     \
+    const long long tot_ = (long long)(A).P[k] << (shift);                                 \
+    for (long long g_ = blockIdx.x * (long long)blockDim.x + threadIdx.x; g_ < tot_;       \
+         g_ += (long long)gridDim.x * blockDim.x) {                                        \
+      const int s = (int)(g_ >> (shift));                                                  \
+      const long long t = g_ & ((1LL << (shift)) - 1);                                     \
+      const BSolve& S = (A).S[s];                                                          \
+      const int mode = *(volatile const int*)&(A).st[s].mode;                              \
+      __VA_ARGS__                                                                          \
+    }                                                                                      \
+  } while (0)
+
+// finest-level items of every solve (sizes differ): walk solves in turn
+#define FOR_FINEST(A, ...)                                                                \
+  do {                                                                                     \
+    long long base_ = 0;                                                                   \
+    for (int s = 0; s < (A).ns; ++s) {                                                     \
+      const BSolve& S = (A).S[s];                                                          \
+      const long long n_ = 1LL << (3 * S.lg);                                              \
+      const int mode = *(volatile const int*)&(A).st[s].mode;                              \
+      const long long gs_ = (long long)gridDim.x * blockDim.x;                             \
+      const long long g0_ = blockIdx.x * (long long)blockDim.x + threadIdx.x;              \
+      long long first_ = (g0_ - base_ % gs_ + gs_) % gs_;                                  \
+      for (long long t = first_; t < n_; t += gs_) {                                       \
+        __VA_ARGS__                                                                        \
+      }                                                                                    \
+      base_ += n_;                                                                         \
+    }                                                                                      \
+  } while (0)
+
+__global__ void __launch_bounds__(512) k_batch(BArgs A) {
+  // ---- set-up: f = src delta, u from the initial guess -----------------------
+  FOR_FINEST(A, {
+    (void)mode;
+    const double f = S.src * S.delta[t];
+    const double u0 = S.uinit ? S.uinit[t] : 0.0;
+    S.f64[t] = f;
+    S.f32[0][t] = (float)f;
+    S.u64[t] = u0;
+    S.E64[t] = exp(u0);
+    S.u32[0][t] = (float)u0;
+  });
+  if (!gsync(A)) return;
+  // initial FP64 residual and ||f||.  Lanes of a warp walk consecutive cells
+  // of one solve (cell counts and the grid stride are multiples of 32), so
+  // the warp reductions in accum() see whole warps.
+  {
+    const long long gs = (long long)gridDim.x * blockDim.x;
+    const long long g0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long base = 0;
+    for (int s = 0; s < A.ns; ++s) {
+      const BSolve& S = A.S[s];
+      const long long n = 1LL << (3 * S.lg);
+      const long long first = (g0 - base % gs + gs) % gs;
+      // all lanes of a warp iterate together: pad the loop to whole warps
+      const long long lane_first = first;
+      for (long long t = lane_first; t - (threadIdx.x & 31) < n; t += gs) {
+        const bool live = t < n;
+        double r = 0.0, f = 0.0;
+        if (live) {
+          r = op_resid64(S, t);
+          f = S.f64[t];
+        }
+        accum(&A.st[s], r, f, live);
+      }
+      base += n;
+    }
+  }
+  if (!gsync(A)) return;
+  if (blockIdx.x == 0) {
+    for (int s = threadIdx.x; s < A.ns; s += blockDim.x) {
+      BState& q = A.st[s];
+      q.fnorm = sqrt(q.acc_ff);
+      q.r0 = sqrt(q.acc_ss);
+      q.ref = q.fnorm > 0.0 ? q.fnorm : q.r0;
+      q.target = A.tol * q.ref;
+      q.r = q.r0;
+      q.rmax = __longlong_as_double((long long)q.acc_max);
+      q.rprev = -1.0;
+      q.mode = q.r0 <= q.target ? BM_DONE : BM_A;
+      q.acc_ss = q.acc_ff = 0.0;
+      q.acc_max = 0ULL;
+    }
+  }
+  if (!gsync(A)) return;
+
+  for (int cyc = 0; cyc < A.max_cycles; ++cyc) {
+    // ---- down ----------------------------------------------------------------
+    for (int k = A.maxlg; k >= 3; --k) {
+      for (int p = 0; p < A.n_pre; ++p)
+        for (int col = 0; col < 2; ++col) {
+          FOR_ITEMS(A, k, 3 * k - 1, {
+            if (mode == BM_A || mode == BM_B) op_sweep(A, S, mode, S.lg - k, col, t);
+          });
+          if (!gsync(A)) return;
+        }
+      FOR_ITEMS(A, k, 3 * (k - 1), {
+        if (mode == BM_A || mode == BM_B) op_restrict(S, mode, S.lg - k, t);
+      });
+      if (!gsync(A)) return;
+      FOR_ITEMS(A, k, 3 * (k - 1), {
+        if (mode == BM_A) op_fas(S, S.lg - k + 1, t);
+      });
+      if (!gsync(A)) return;
+    }
+    // ---- coarsest 4^3: one block per solve -------------------------------------
+    for (int s = blockIdx.x; s < A.ns; s += gridDim.x) {
+      const int mode = *(volatile const int*)&A.st[s].mode;
+      if (mode == BM_A || mode == BM_B) op_coarse(A, A.S[s], mode);
+    }
+    if (!gsync(A)) return;
+    // ---- up ------------------------------------------------------------------
+    for (int k = 3; k <= A.maxlg; ++k) {
+      FOR_ITEMS(A, k, 3 * k, {
+        if (mode == BM_A || mode == BM_B) op_prolong(A, S, mode, S.lg - k, t);
+      });
+      if (!gsync(A)) return;
+      for (int p = 0; p < A.n_post; ++p)
+        for (int col = 0; col < 2; ++col) {
+          FOR_ITEMS(A, k, 3 * k - 1, {
+            if (mode == BM_A || mode == BM_B) op_sweep(A, S, mode, S.lg - k, col, t);
+          });
+          if (!gsync(A)) return;
+        }
+    }
+    // ---- end of cycle: mode B applies the correction ---------------------------
+    FOR_FINEST(A, {
+      if (mode == BM_B) {
+        const double d = fmin(fmax((double)S.e32[0][t], -A.cap64), A.cap64);
+        const double v = S.u64[t] + d;
+        S.u64[t] = v;
+        S.E64[t] = exp(v);
+      }
+    });
+    if (!gsync(A)) return;
+    // residual norms: FP32 for mode A, FP64 (+ new linear system) for mode B
+    {
+      const long long gs = (long long)gridDim.x * blockDim.x;
+      const long long g0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+      long long base = 0;
+      for (int s = 0; s < A.ns; ++s) {
+        const BSolve& S = A.S[s];
+        const long long n = 1LL << (3 * S.lg);
+        const int mode = *(volatile const int*)&A.st[s].mode;
+        const long long first = (g0 - base % gs + gs) % gs;
+        base += n;
+        if (mode != BM_A && mode != BM_B) continue;
+        for (long long t = first; t - (threadIdx.x & 31) < n; t += gs) {
+          const bool live = t < n;
+          double r = 0.0;
+          if (live) {
+            if (mode == BM_B) {
+              r = op_resid64(S, t);
+            } else {
+              const int lg = S.lg, M = (1 << lg) - 1;
+              const int kk = (int)(t & M), jj = (int)((t >> lg) & M), ii = (int)(t >> (2 * lg));
+              r = (double)(S.f32[0][t] - L32(S, S.u32[0], ii, jj, kk, lg, S.ih2[0]));
+            }
+          }
+          accum(&A.st[s], r, 0.0, live);
+        }
+      }
+    }
+    if (!gsync(A)) return;
+    // decide
+    if (blockIdx.x == 0) {
+      for (int s = threadIdx.x; s < A.ns; s += blockDim.x) {
+        BState& q = A.st[s];
+        const double r = sqrt(q.acc_ss);
+        const double rm = __longlong_as_double((long long)q.acc_max);
+        q.acc_ss = 0.0;
+        q.acc_max = 0ULL;
+        if (q.mode == BM_A) {
+          q.cyclesA++;
+          if (!(r == r) || r <= A.sw * q.ref || (q.rprev > 0.0 && r > 0.7 * q.rprev))
+            q.mode = BM_TRANS;
+          q.rprev = r;
+        } else if (q.mode == BM_B) {
+          q.cyclesB++;
+          const bool rose = !(r < q.r);
+          q.r = r;
+          q.rmax = rm;
+          if (r <= q.target) {
+            q.mode = BM_DONE;
+          } else if (rose) {
+            q.mode = BM_A;  // back to nonlinear FP32 cycles from u32 = fp32(u)
+            q.rprev = -1.0;
+          }
+        }
+        if (q.mode != BM_DONE && q.cyclesA + q.cyclesB >= A.max_cycles) q.mode = BM_DONE;
+      }
+    }
+    if (!gsync(A)) return;
+    // transition A -> B: FP64 iterate from the FP32 one, FP64 residual
+    FOR_FINEST(A, {
+      if (mode == BM_TRANS) {
+        const double v = (double)S.u32[0][t];
+        S.u64[t] = v;
+        S.E64[t] = exp(v);
+      }
+    });
+    if (!gsync(A)) return;
+    {
+      const long long gs = (long long)gridDim.x * blockDim.x;
+      const long long g0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+      long long base = 0;
+      for (int s = 0; s < A.ns; ++s) {
+        const BSolve& S = A.S[s];
+        const long long n = 1LL << (3 * S.lg);
+        const int mode = *(volatile const int*)&A.st[s].mode;
+        const long long first = (g0 - base % gs + gs) % gs;
+        base += n;
+        if (mode != BM_TRANS) continue;
+        for (long long t = first; t - (threadIdx.x & 31) < n; t += gs) {
+          const bool live = t < n;
+          const double r = live ? op_resid64(S, t) : 0.0;
+          accum(&A.st[s], r, 0.0, live);
+        }
+      }
+    }
+    if (!gsync(A)) return;
+    int active = 0;
+    if (blockIdx.x == 0) {
+      __shared__ int cnt;
+      if (threadIdx.x == 0) cnt = 0;
+      __syncthreads();
+      for (int s = threadIdx.x; s < A.ns; s += blockDim.x) {
+        BState& q = A.st[s];
+        if (q.mode == BM_TRANS) {
+          const double r = sqrt(q.acc_ss);
+          q.r = r;
+          q.rmax = __longlong_as_double((long long)q.acc_max);
+          q.mode = r <= q.target ? BM_DONE : BM_B;
+          q.acc_ss = 0.0;
+          q.acc_max = 0ULL;
+        }
+        if (q.mode != BM_DONE) atomicAdd(&cnt, 1);
+      }
+      __syncthreads();
+      active = cnt;
+      if (threadIdx.x == 0) atomicExch(A.err + 1, active);
+    }
+    if (!gsync(A)) return;
+    if (*(volatile int*)(A.err + 1) == 0) break;
+  }
+  // ---- outputs: fR = fbar e^u and the force -----------------------------------
+  FOR_FINEST(A, {
+    (void)mode;
+    const int lg = S.lg, M = (1 << lg) - 1;
+    const long long n = 1LL << (3 * lg);
+    const int kk = (int)(t & M), jj = (int)((t >> lg) & M), ii = (int)(t >> (2 * lg));
+    S.fr_out[t] = S.fbar * S.E64[t];
+    if (S.acc_out) {
+      const double* E = S.E64;
+      S.acc_out[t] = S.gscale * (E[cidx((ii + 1) & M, jj, kk, lg)] - E[cidx((ii - 1) & M, jj, kk, lg)]);
+      S.acc_out[n + t] =
+          S.gscale * (E[cidx(ii, (jj + 1) & M, kk, lg)] - E[cidx(ii, (jj - 1) & M, kk, lg)]);
+      S.acc_out[2 * n + t] =
+          S.gscale * (E[cidx(ii, jj, (kk + 1) & M, lg)] - E[cidx(ii, jj, (kk - 1) & M, lg)]);
+    }
+  });
+}
+
+}  // namespace
+
+// ============================================================================
+// host side
+// ============================================================================
+struct BatchWork {
+  std::string sig;
+  std::vector<void*> bufs;
+  BSolve* dS = nullptr;
+  BState* dst = nullptr;
+  unsigned* bar = nullptr;  // [0] count, [1] generation
+  int* err = nullptr;
+  std::vector<int> order;
+  std::map<std::string, std::pair<int, int>> tuned;  // signature -> (threads, blocks/SM)
+  cudaGraphExec_t gx = nullptr;
+  std::string gkey;
+};
+
+static void batch_release(BatchWork* B) {
+  for (void* p : B->bufs) cudaFree(p);
+  B->bufs.clear();
+  if (B->dS) cudaFree(B->dS);
+  if (B->dst) cudaFree(B->dst);
+  if (B->bar) cudaFree(B->bar);
+  if (B->err) cudaFree(B->err);
+  B->dS = nullptr;
+  B->dst = nullptr;
+  B->bar = nullptr;
+  B->err = nullptr;
+  if (B->gx) cudaGraphExecDestroy(B->gx);
+  B->gx = nullptr;
+  B->gkey.clear();
+}
+
+void batch_free(mgfr_ctx* c) {
+  BatchWork* B = (BatchWork*)c->batch;
+  if (!B) return;
+  batch_release(B);
+  delete B;
+  c->batch = nullptr;
+}
+
+static mgfr_status launch_batch(mgfr_ctx* c, BatchWork* B, const BArgs& A, int threads, int bpsm,
+                                bool use_graph) {
+  int dev = c->device, nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int occ = 0;
+  MG_CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, threads, 0));
+  if (occ < 1) return set_err(c, MGFR_E_UNSUPPORTED, "batched kernel cannot be resident");
+  const int grid = nsm * std::min(bpsm, occ);
+  MG_CK(c, cudaMemsetAsync(B->bar, 0, 2 * sizeof(unsigned), c->s));
+  MG_CK(c, cudaMemsetAsync(B->err, 0, 2 * sizeof(int), c->s));
+  BArgs a = A;
+  void* args[] = {&a};
+  if (!use_graph) {
+    MG_CK(c, cudaLaunchCooperativeKernel((void*)k_batch, grid, threads, args, 0, c->s));
+    c->launches += 1;
+    return MGFR_OK;
+  }
+  char key[512];
+  std::snprintf(key, sizeof(key), "%s|%d|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%lld", B->sig.c_str(),
+                threads, grid, A.n_pre, A.n_post, A.linear, A.max_cycles, A.cap64, A.tol, A.sw,
+                A.max_spins);
+  if (!B->gx || B->gkey != key) {
+    if (B->gx) cudaGraphExecDestroy(B->gx);
+    B->gx = nullptr;
+    cudaGraph_t g = nullptr;
+    MG_CK(c, cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaLaunchCooperativeKernel((void*)k_batch, grid, threads, args, 0, c->s);
+    cudaError_t e2 = cudaStreamEndCapture(c->s, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      (void)cudaGetLastError();
+      // capture of a cooperative launch unsupported: launch directly
+      MG_CK(c, cudaLaunchCooperativeKernel((void*)k_batch, grid, threads, args, 0, c->s));
+      c->launches += 1;
+      return MGFR_OK;
+    }
+    e = cudaGraphInstantiate(&B->gx, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return set_err(c, MGFR_E_CUDA, "batched graph instantiate failed");
+    B->gkey = key;
+  }
+  MG_CK(c, cudaGraphLaunch(B->gx, c->s));
+  c->launches += 1;
+  return MGFR_OK;
+}
+
+extern "C" {
+
+mgfr_status mgfr_batch_solve(mgfr_ctx* c, int nsolves, const mgfr_batch_item* items,
+                             mgfr_stats* per_solve) {
+  if (!c) return MGFR_E_INVALID;
+  if (nsolves < 1 || nsolves > 4096 || !items)
+    return set_err(c, MGFR_E_INVALID, "need 1..4096 batch items");
+  const mgfr_config& g = c->cfg;
+  for (int i = 0; i < nsolves; ++i) {
+    const mgfr_batch_item& it = items[i];
+    if (it.N < 8 || it.N > 512 || (it.N & (it.N - 1)))
+      return set_err(c, MGFR_E_INVALID, "batch item N must be a power of two in [8, 512]");
+    if (!(it.box > 0.0) || !(it.a > 0.0) || !(it.fr0_abs > 0.0) || it.n < 1 || !it.delta_dev ||
+        !it.fr_out_dev)
+      return set_err(c, MGFR_E_INVALID, "invalid batch item");
+  }
+  auto w0 = std::chrono::steady_clock::now();
+  MG_CK(c, cudaSetDevice(c->device));
+  c->launches = 0;
+  if (!c->batch) c->batch = new BatchWork();
+  BatchWork* B = (BatchWork*)c->batch;
+  // solves sorted by N (descending): participants of a size form a prefix
+  std::vector<int> order(nsolves);
+  for (int i = 0; i < nsolves; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return items[x].N > items[y].N; });
+  std::string sig;
+  for (int i : order) sig += std::to_string(items[i].N) + ",";
+  if (sig != B->sig) {
+    batch_release(B);
+    B->sig = sig;
+  }
+  std::vector<BSolve> hs(nsolves);
+  int maxlg = 0;
+  size_t bi = 0;
+  auto buf = [&](size_t bytes) -> void* {
+    if (bi < B->bufs.size()) return B->bufs[bi++];
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    B->bufs.push_back(p);
+    ++bi;
+    return p;
+  };
+  for (int q = 0; q < nsolves; ++q) {
+    const mgfr_batch_item& it = items[order[q]];
+    BSolve& S = hs[q];
+    std::memset(&S, 0, sizeof(S));
+    S.N = it.N;
+    int lg = 0;
+    while ((1 << lg) < it.N) ++lg;
+    S.lg = lg;
+    S.nlev = lg - 1;
+    maxlg = std::max(maxlg, lg);
+    mgfr_config cf = g;
+    cf.fr0_abs = it.fr0_abs;
+    cf.n = it.n;
+    const Model m = make_model(cf, it.a);
+    S.h0 = it.box / it.N;
+    S.ih2_0 = 1.0 / (S.h0 * S.h0);
+    for (int l = 0; l < S.nlev; ++l) {
+      const double h = it.box / (it.N >> l);
+      S.ih2[l] = (float)(1.0 / (h * h));
+      const size_t n = (size_t)1 << (3 * (lg - l));
+      S.u32[l] = (float*)buf(4 * n);
+      S.f32[l] = (float*)buf(4 * n);
+      S.e32[l] = (float*)buf(4 * n);
+      S.r32[l] = (float*)buf(4 * n);
+      if (l > 0) S.uold32[l] = (float*)buf(4 * n);
+      if (!S.u32[l] || !S.f32[l] || !S.e32[l] || !S.r32[l] || (l > 0 && !S.uold32[l]))
+        return set_err(c, MGFR_E_OOM, "batch workspace allocation failed");
+    }
+    const size_t n0 = (size_t)1 << (3 * lg);
+    S.u64 = (double*)buf(8 * n0);
+    S.E64 = (double*)buf(8 * n0);
+    S.f64 = (double*)buf(8 * n0);
+    if (!S.u64 || !S.E64 || !S.f64) return set_err(c, MGFR_E_OOM, "batch workspace allocation failed");
+    S.aRt = (float)m.aRt;
+    S.aRt_np1 = (float)m.aRt_np1;
+    S.inv_np1 = (float)m.inv_np1;
+    S.aRt64 = m.aRt;
+    S.aRt_np1_64 = m.aRt_np1;
+    S.inv_np1_64 = m.inv_np1;
+    S.src = m.src;
+    S.fbar = m.fbar;
+    S.gscale = m.fbar / (2.0 * S.h0) / (2.0 * m.a);
+    S.n = m.n;
+    S.delta = it.delta_dev;
+    S.uinit = it.u_init_dev;
+    S.fr_out = it.fr_out_dev;
+    S.acc_out = it.acc_out_dev;
+  }
+  if (!B->dS) MG_CK(c, cudaMalloc(&B->dS, sizeof(BSolve) * nsolves));
+  if (!B->dst) MG_CK(c, cudaMalloc(&B->dst, sizeof(BState) * nsolves));
+  if (!B->bar) MG_CK(c, cudaMalloc(&B->bar, 2 * sizeof(unsigned)));
+  if (!B->err) MG_CK(c, cudaMalloc(&B->err, 2 * sizeof(int)));
+  MG_CK(c, cudaEventRecord(c->ev_in, c->user));
+  MG_CK(c, cudaStreamWaitEvent(c->s, c->ev_in, 0));
+  MG_CK(c, cudaMemcpyAsync(B->dS, hs.data(), sizeof(BSolve) * nsolves, cudaMemcpyHostToDevice, c->s));
+  MG_CK(c, cudaMemsetAsync(B->dst, 0, sizeof(BState) * nsolves, c->s));
+  BArgs A{};
+  A.S = B->dS;
+  A.st = B->dst;
+  A.ns = nsolves;
+  A.maxlg = maxlg;
+  for (int k = 0; k < 16; ++k) {
+    int p = 0;
+    for (int q = 0; q < nsolves; ++q) p += hs[q].lg >= k;
+    A.P[k] = p;
+  }
+  A.n_pre = g.n_pre;
+  A.n_post = g.n_post;
+  A.linear = g.prolong_linear;
+  A.max_cycles = g.max_vcycles;
+  A.cap32 = (float)g.step_cap;
+  A.cap64 = g.step_cap;
+  A.tol = g.tol_rel;
+  A.sw = g.mixed_switch;
+  A.bar_count = B->bar;
+  A.bar_gen = B->bar + 1;
+  A.err = B->err;
+  A.max_spins = g.max_spins;
+  // launch shape: tuned choice for this signature, else 256 threads x 2 per SM
+  int threads = 256, bpsm = 2;
+  auto itc = B->tuned.find(sig);
+  if (itc != B->tuned.end()) {
+    threads = itc->second.first;
+    bpsm = itc->second.second;
+  }
+  MG_CK(c, cudaEventRecord(c->t0, c->s));
+  mgfr_status rs = launch_batch(c, B, A, threads, bpsm, true);
+  if (rs != MGFR_OK) return rs;
+  MG_CK(c, cudaEventRecord(c->t1, c->s));
+  std::vector<BState> st(nsolves);
+  int err = 0;
+  MG_CK(c, cudaMemcpyAsync(st.data(), B->dst, sizeof(BState) * nsolves, cudaMemcpyDeviceToHost, c->s));
+  MG_CK(c, cudaMemcpyAsync(&err, B->err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+  MG_CK(c, cudaEventRecord(c->ev_out, c->s));
+  MG_CK(c, cudaStreamWaitEvent(c->user, c->ev_out, 0));
+  MG_CK(c, cudaStreamSynchronize(c->s));
+  MG_CK(c, cudaGetLastError());
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->t0, c->t1);
+  const double wall =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
+  bool allok = true;
+  for (int q = 0; q < nsolves; ++q) {
+    const BState& b = st[q];
+    const bool ok = b.r <= b.target;
+    allok = allok && ok;
+    if (per_solve) {
+      mgfr_stats& o = per_solve[order[q]];
+      std::memset(&o, 0, sizeof(o));
+      o.vcycles = b.cyclesA;
+      o.outer_iters = b.cyclesB;
+      o.res_l2_init = b.r0;
+      o.res_l2_final = b.r;
+      o.res_max_final = b.rmax;
+      o.f_l2 = b.fnorm;
+      o.t_solve_ms = ms;
+      o.t_total_ms = wall;
+      o.n_levels = 1;
+      o.cells_per_level[0] = 1LL << (3 * hs[q].lg);
+      o.gpu_launches = c->launches;
+      long long cells = 0;
+      for (int l = 0; l < hs[q].nlev; ++l) cells += 1LL << (3 * (hs[q].lg - l));
+      o.cell_updates = (long long)b.cyclesA * (g.n_pre + g.n_post) * cells;
+      o.linear_updates = (long long)b.cyclesB * (g.n_pre + g.n_post) * cells;
+    }
+  }
+  if (err) return set_err(c, MGFR_E_TIMEOUT, "a grid barrier wait in the batched kernel gave up");
+  if (!allok) return set_err(c, MGFR_E_NOCONVERGE, "a batched solve missed its tolerance");
+  return MGFR_OK;
+}
+
+// Time every candidate launch shape on this batch and keep the fastest for
+// batches of the same size signature (persisted in the file named by
+// MGFR_TUNE_CACHE when set).
+mgfr_status mgfr_batch_autotune(mgfr_ctx* c, int nsolves, const mgfr_batch_item* items,
+                                int* best_threads, int* best_blocks_per_sm) {
+  if (!c) return MGFR_E_INVALID;
+  const int cand_t[] = {128, 256, 512};
+  const int cand_b[] = {1, 2, 4};
+  float best = 1e30f;
+  int bt = 256, bb = 2;
+  mgfr_config saved = c->cfg;
+  for (int t : cand_t)
+    for (int b : cand_b) {
+      if (!c->batch) c->batch = new BatchWork();
+      BatchWork* B = (BatchWork*)c->batch;
+      // force this shape through the tuned map for the current signature
+      std::vector<int> order(nsolves);
+      for (int i = 0; i < nsolves; ++i) order[i] = i;
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int x, int y) { return items[x].N > items[y].N; });
+      std::string sig;
+      for (int i : order) sig += std::to_string(items[i].N) + ",";
+      B->tuned[sig] = {t, b};
+      mgfr_status rs = mgfr_batch_solve(c, nsolves, items, nullptr);
+      if (rs != MGFR_OK && rs != MGFR_E_NOCONVERGE) {
+        c->cfg = saved;
+        return rs;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c->t0, c->t1);
+      if (ms < best) {
+        best = ms;
+        bt = t;
+        bb = b;
+      }
+    }
+  c->cfg = saved;
+  BatchWork* B = (BatchWork*)c->batch;
+  B->tuned[B->sig] = {bt, bb};
+  if (const char* path = std::getenv("MGFR_TUNE_CACHE")) {
+    if (FILE* f = std::fopen(path, "a")) {
+      std::fprintf(f, "%s %d %d %.4f\n", B->sig.c_str(), bt, bb, best);
+      std::fclose(f);
+    }
+  }
+  if (best_threads) *best_threads = bt;
+  if (best_blocks_per_sm) *best_blocks_per_sm = bb;
+  return MGFR_OK;
+}
+
+}  // extern "C"

@@ -119,6 +119,7 @@ struct mgfr_ctx {
   char graph_key[256] = {0}, key32[256] = {0}, keylin[256] = {0};
   long long updates_v64 = 0, updates_v32 = 0, updates_lin = 0;
   void* amr = nullptr;    // refined hierarchy workspace (amr.cu)
+  void* batch = nullptr;  // batched-solve workspace (batch.cu)
   // profiling: events recorded around base-level kernels inside each graph
   struct ProfRec {
     int fam;
@@ -143,6 +144,7 @@ void prof_collect(mgfr_ctx* c, int graph, mgfr_stats* st);
 void prof_clear(mgfr_ctx* c, int graph);
 
 mgfr_status set_err(mgfr_ctx* c, mgfr_status st, const std::string& msg);
+void batch_free(mgfr_ctx* c);
 #define MG_CK(ctx, call)                                                                  \
   do {                                                                                    \
     cudaError_t e_ = (call);                                                              \

@@ -51,6 +51,14 @@ class Stats(C.Structure):
         return out
 
 
+class BatchItem(C.Structure):
+    _fields_ = [
+        ("N", C.c_int), ("box", C.c_double), ("a", C.c_double), ("fr0_abs", C.c_double),
+        ("n", C.c_int), ("delta_dev", C.c_void_p), ("u_init_dev", C.c_void_p),
+        ("fr_out_dev", C.c_void_p), ("acc_out_dev", C.c_void_p),
+    ]
+
+
 class MGFRError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"mgfr {STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
@@ -74,6 +82,8 @@ SIGNATURES = {
     "mgfr_get_level_info": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "mgfr_get_level_keys": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "mgfr_get_level_field": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "mgfr_batch_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "mgfr_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mgfr_last_error": (C.c_char_p, [C.c_void_p]),
     "mgfr_destroy": (None, [C.c_void_p]),
 }
@@ -200,3 +210,41 @@ class Solver:
         out = np.empty(3 * nc if what == FIELD_ACC else nc)
         self._check(lib().mgfr_get_level_field(self.h, level, what, out.ctypes.data_as(C.c_void_p)))
         return out
+
+    def _batch_items(self, deltas, boxes, a, fr0s, ns, u_inits, want_acc):
+        import torch
+        k = len(deltas)
+        items = (BatchItem * k)()
+        outs = []
+        for i, d in enumerate(deltas):
+            fr = torch.empty_like(d)
+            acc = torch.empty((3,) + tuple(d.shape), dtype=d.dtype, device=d.device) \
+                if want_acc else None
+            outs.append({"fr": fr, "acc": acc})
+            u0 = None if u_inits is None else u_inits[i]
+            items[i] = BatchItem(d.shape[0], boxes[i], a[i], fr0s[i], ns[i], _ptr(d), _ptr(u0),
+                                 _ptr(fr), _ptr(acc))
+        return items, outs
+
+    def batch_solve(self, deltas, boxes, fr0s, a=None, ns=None, u_inits=None, want_acc=False,
+                    allow_noconverge=False):
+        """Many independent periodic solves in one persistent launch (mgfr_batch_solve)."""
+        k = len(deltas)
+        a = [1.0] * k if a is None else a
+        ns = [1] * k if ns is None else ns
+        items, outs = self._batch_items(deltas, boxes, a, fr0s, ns, u_inits, want_acc)
+        stats = (Stats * k)()
+        st = lib().mgfr_batch_solve(self.h, k, items, stats)
+        self._check(st, allow_noconverge)
+        for i in range(k):
+            outs[i]["stats"] = stats[i].to_dict()
+        return outs, st
+
+    def batch_autotune(self, deltas, boxes, fr0s, a=None, ns=None):
+        k = len(deltas)
+        a = [1.0] * k if a is None else a
+        ns = [1] * k if ns is None else ns
+        items, _ = self._batch_items(deltas, boxes, a, fr0s, ns, None, False)
+        t, b = C.c_int(), C.c_int()
+        self._check(lib().mgfr_batch_autotune(self.h, k, items, C.byref(t), C.byref(b)), True)
+        return t.value, b.value
