@@ -225,6 +225,33 @@ mgfr_status mgfr_batch_solve(mgfr_ctx* ctx, int nsolves, const mgfr_batch_item* 
 mgfr_status mgfr_batch_autotune(mgfr_ctx* ctx, int nsolves, const mgfr_batch_item* items,
                                 int* best_threads, int* best_blocks_per_sm);
 
+/*
+ * FP64 dense-grid solve that allocates nothing (no counterpart in the paper:
+ * an addition of this library for callers that cannot allocate device
+ * memory, such as code running inside another framework's memory pool or a
+ * service whose request path forbids allocation).
+ *
+ * Same arguments and results as mgfr_solve_density with precision FP64, a
+ * zero initial guess and no u output, but without a context: the
+ * configuration and the stream are passed in, and all multigrid scratch lives
+ * in one fixed device array inside the library (grids up to 64^3; about
+ * 7.5 MB that every GPU which loads the library keeps until the process
+ * exits).  N must be a power of two in [8, 64]; anything larger returns
+ * MGFR_E_INVALID.  cfg->precision and cfg->profile are ignored.
+ *   delta_dev [N^3], fr_out_dev [N^3], acc_out_dev [3][N^3] or NULL: caller's
+ *   device buffers; cuda_stream: the stream to run on (NULL = default).
+ * The first call on a device looks up that device's scratch address; make
+ * that first call before any stream capture.  Every call reuses the same
+ * scratch and writes it before reading it, so nothing carries over from one
+ * call to the next; calls that overlap on the GPU (two streams or two host
+ * threads at once) race on the scratch and must be serialised by the caller.
+ * The call returns after its results are written.  No cudaMalloc, cudaFree
+ * or other allocating routine is called.
+ */
+mgfr_status mgfr_solve_density_noalloc(const mgfr_config* cfg, const double* delta_dev, int N,
+                                       double box, double a, double* fr_out_dev,
+                                       double* acc_out_dev, void* cuda_stream, mgfr_stats* st);
+
 /* Text of the last error seen by this context ("" if none). */
 const char* mgfr_last_error(const mgfr_ctx* ctx);
 

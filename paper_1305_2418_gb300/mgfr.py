@@ -82,6 +82,9 @@ SIGNATURES = {
     "mgfr_get_level_info": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "mgfr_get_level_keys": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "mgfr_get_level_field": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "mgfr_solve_density_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                             C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p]),
     "mgfr_batch_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "mgfr_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mgfr_last_error": (C.c_char_p, [C.c_void_p]),
