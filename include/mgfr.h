@@ -226,6 +226,45 @@ mgfr_status mgfr_batch_autotune(mgfr_ctx* ctx, int nsolves, const mgfr_batch_ite
                                 int* best_threads, int* best_blocks_per_sm);
 
 /*
+ * Learned initial guess (an addition to the paper's method: the paper starts
+ * from the previous step's u, Sec. 3.3 step 2).  A 4-level 3D U-Net
+ * (16/32/64/128 channels, 3^3 kernels, circular padding, BF16 weights and
+ * activations, FP32 accumulation) maps per-voxel features (ln(1+delta),
+ * log10|fR0| + 5, 1) to u; the multigrid then drives the residual to the same
+ * tolerance from that start (pass it as u_init).  Training and inference run
+ * on this library's own tensor-core kernels.  D (box cells per side) must be
+ * a power of two in [32, 512]; the network applies at the cell size it was
+ * trained at.
+ */
+/* (Re)create the network with He-normal weights from `seed`. */
+mgfr_status mgfr_unet_init(mgfr_ctx* ctx, unsigned long long seed);
+/* One Adam step (learning rate lr) on B samples of D^3: delta_dev [B][D^3],
+ * fr0_host [B] (|fR0| per sample, host), u_target_dev [B][D^3]; *loss_out =
+ * mean squared error before the step. */
+mgfr_status mgfr_unet_train_step(mgfr_ctx* ctx, int B, int D, const double* delta_dev,
+                                 const double* fr0_host, const double* u_target_dev, float lr,
+                                 double* loss_out);
+/* u_out_dev [D^3] = network(delta_dev [D^3], |fR0|). */
+mgfr_status mgfr_unet_predict(mgfr_ctx* ctx, int D, const double* delta_dev, double fr0_abs,
+                              double* u_out_dev);
+/* Copy the FP32 master parameters to (set = 0) or from (set = 1) host memory;
+ * *count receives their number (host may be NULL to query it). */
+mgfr_status mgfr_unet_params(mgfr_ctx* ctx, int set, float* host, long long* count);
+/* Gradients of the last training step (same layout as the parameters). */
+mgfr_status mgfr_unet_grads(mgfr_ctx* ctx, float* host);
+/* One convolution of the network on caller device buffers (NDHWC, channel
+ * counts multiples of 16, Cout <= 128, D a power of two >= 4; W [27][Cin][Cout]
+ * BF16 with tap = (dx+1)*9 + (dy+1)*3 + (dz+1) for input offset (dx,dy,dz)):
+ *   op 0: out (BF16 [B D^3][Cout]) = relu?(conv(x) + bias)   (bias nullable)
+ *   op 1: out (FP32 [B D^3][Cin])  = gradient w.r.t. x for output gradient g
+ *   op 2: out (FP32 [27][Cin][Cout]) = gradient w.r.t. W, db (FP32 [Cout],
+ *         nullable) = gradient w.r.t. the bias; allocates its own scratch.
+ * Runs on `stream` and returns when done. */
+mgfr_status mgfr_nn_conv3d(int op, int B, int D, int Cin, int Cout, const void* x_bf16,
+                           const void* w_bf16, const float* bias, int relu, const void* g_bf16,
+                           void* out, float* db, void* stream);
+
+/*
  * FP64 dense-grid solve that allocates nothing (no counterpart in the paper:
  * an addition of this library for callers that cannot allocate device
  * memory, such as code running inside another framework's memory pool or a

@@ -120,6 +120,7 @@ struct mgfr_ctx {
   long long updates_v64 = 0, updates_v32 = 0, updates_lin = 0;
   void* amr = nullptr;    // refined hierarchy workspace (amr.cu)
   void* batch = nullptr;  // batched-solve workspace (batch.cu)
+  void* unet = nullptr;   // learned initial guess network (unet.cu)
   // profiling: events recorded around base-level kernels inside each graph
   struct ProfRec {
     int fam;
@@ -145,6 +146,7 @@ void prof_clear(mgfr_ctx* c, int graph);
 
 mgfr_status set_err(mgfr_ctx* c, mgfr_status st, const std::string& msg);
 void batch_free(mgfr_ctx* c);
+void unet_free(mgfr_ctx* c);
 #define MG_CK(ctx, call)                                                                  \
   do {                                                                                    \
     cudaError_t e_ = (call);                                                              \

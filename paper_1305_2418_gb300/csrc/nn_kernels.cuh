@@ -1,0 +1,33 @@
+// nn_kernels.cuh -- BF16 tensor-core 3D convolution primitives (3^3 taps,
+// circular padding, NDHWC) with FP32 accumulation, for the learned initial
+// guess of the field solve.  Declarations shared by unet.cu.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "mgfr_internal.cuh"
+
+// Activation tensor view: element (voxel m, channel c) at p[m * ld + off + c].
+struct TView {
+  __nv_bfloat16* p;
+  int ld, off;
+};
+struct FView {
+  float* p;
+  int ld, off;
+};
+
+// y = conv(x, W) + b (+ReLU): x [B*D^3][Cin] bf16, W [27][Cin][Cout] bf16
+// (tap = (dx+1)*9 + (dy+1)*3 + (dz+1), x index i + dx), y bf16.
+// Cin, Cout multiples of 16 (Cout <= 128).
+void nn_conv_fwd(TView x, int Cin, const __nv_bfloat16* W, const float* bias, int relu, TView y,
+                 int Cout, int B, int lgD, cudaStream_t s);
+// gx (+)= conv^T(g, W): g [B*D^3][Cout] bf16 (gradient of the pre-activation),
+// gx FP32 [.][Cin] (accumulate if acc).
+void nn_conv_dgrad(TView g, int Cout, const __nv_bfloat16* W, FView gx, int Cin, int accumulate,
+                   int B, int lgD, cudaStream_t s);
+// dW[27][Cin][Cout] (FP32, overwritten) = sum_m x[nbr(m,tap)][ci] g[m][co];
+// db[Cout] = sum_m g[m][co].  `partials` is scratch of nn_wgrad_scratch()
+// floats.
+void nn_conv_wgrad(TView x, int Cin, TView g, int Cout, float* dW, float* db, float* partials,
+                   int B, int lgD, cudaStream_t s);
+long long nn_wgrad_scratch(int Cin, int Cout);

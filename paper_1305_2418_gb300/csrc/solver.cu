@@ -589,6 +589,7 @@ void mgfr_destroy(mgfr_ctx* c) {
   free_dense(c->dh);
   amr_free(c);
   batch_free(c);
+  unet_free(c);
   for (auto e : c->evpool) cudaEventDestroy(e);
   c->evpool.clear();
   if (c->host_scal) cudaFreeHost(c->host_scal);

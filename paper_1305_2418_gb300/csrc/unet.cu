@@ -1,0 +1,633 @@
+// unet.cu -- learned initial guess for the field solve: a 4-level 3D U-Net
+// (16/32/64/128 channels, 3^3 kernels, circular padding) with BF16 weights
+// and activations and FP32 accumulation, trained and evaluated on the GPU by
+// this library's own kernels (nn_conv.cu and the elementwise kernels here).
+//
+// Input features per voxel: ln(1 + delta), log10|fR0| + 5, 1 (padded to 16
+// channels).  Output: u (FP32).  Encoder: two conv+ReLU per level, 2^3
+// average pooling.  Decoder: nearest upsampling, concatenation with the
+// encoder output of the same level, two conv+ReLU.  Head: 1x1x1 conv to 1
+// channel.  Loss: mean squared error in u.  Optimiser: Adam on FP32 master
+// weights, BF16 copies used by the convolutions.
+//
+// The network is fully convolutional, so it applies to any power-of-two box
+// >= 8 cells at the cell size it was trained on.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "nn_kernels.cuh"
+
+namespace {
+
+constexpr int BS = 256;
+
+struct ConvSpec {
+  int cin, cout, lvl;  // level 0 = full resolution
+};
+
+// 14 convolutions in execution order
+const ConvSpec kConvs[14] = {
+    {16, 16, 0},  {16, 16, 0},                       // enc1
+    {16, 32, 1},  {32, 32, 1},                       // enc2
+    {32, 64, 2},  {64, 64, 2},                       // enc3
+    {64, 128, 3}, {128, 128, 3},                     // bottom
+    {192, 64, 2}, {64, 64, 2},                       // dec3 (up 128 + enc3 64)
+    {96, 32, 1},  {32, 32, 1},                       // dec2 (up 64 + enc2 32)
+    {48, 16, 0},  {16, 16, 0},                       // dec1 (up 32 + enc1 16)
+};
+
+__global__ void k_features(const double* __restrict__ delta, const double* __restrict__ fr0s,
+                           long long per, long long M, __nv_bfloat16* __restrict__ x) {
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const double d = delta[m];
+  const double fr0 = fr0s[m / per];
+  __nv_bfloat16* o = x + m * 16;
+  o[0] = __float2bfloat16((float)log(fmax(1.0 + d, 1e-3)));
+  o[1] = __float2bfloat16((float)(log10(fr0) + 5.0));
+  o[2] = __float2bfloat16(1.f);
+  for (int c = 3; c < 16; ++c) o[c] = __float2bfloat16(0.f);
+}
+
+// 2^3 average pooling: y[M'][c] from x (full res, view)
+__global__ void k_pool(TView x, TView y, int C, int lgDc, long long Mc) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= Mc * C) return;
+  const long long mc = t / C;
+  const int c = (int)(t % C);
+  const long long per = 1LL << (3 * lgDc);
+  const long long b = mc / per, r = mc % per;
+  const int Dc = 1 << lgDc, lgDf = lgDc + 1;
+  const int I = (int)(r >> (2 * lgDc)), J = (int)((r >> lgDc) & (Dc - 1)), K = (int)(r & (Dc - 1));
+  float s = 0.f;
+  for (int q = 0; q < 8; ++q) {
+    const long long mf = (b << (3 * lgDf)) +
+                         ((((long long)(2 * I + (q >> 2)) << lgDf) + (2 * J + ((q >> 1) & 1))) << lgDf) +
+                         (2 * K + (q & 1));
+    s += __bfloat162float(x.p[mf * x.ld + x.off + c]);
+  }
+  y.p[mc * y.ld + y.off + c] = __float2bfloat16(0.125f * s);
+}
+
+// g_fine[child][c] += g_coarse[parent][c] / 8
+__global__ void k_pool_bwd(FView gc, FView gf, int C, int lgDf, long long Mf) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= Mf * C) return;
+  const long long mf = t / C;
+  const int c = (int)(t % C);
+  const long long per = 1LL << (3 * lgDf);
+  const long long b = mf / per, r = mf % per;
+  const int Df = 1 << lgDf, lgDc = lgDf - 1;
+  const int i = (int)(r >> (2 * lgDf)), j = (int)((r >> lgDf) & (Df - 1)), k = (int)(r & (Df - 1));
+  const long long mc = (b << (3 * lgDc)) + ((((long long)(i >> 1) << lgDc) + (j >> 1)) << lgDc) + (k >> 1);
+  gf.p[mf * gf.ld + gf.off + c] += 0.125f * gc.p[mc * gc.ld + gc.off + c];
+}
+
+// nearest upsampling: y[fine][c] = x[parent][c]
+__global__ void k_up(TView x, TView y, int C, int lgDf, long long Mf) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= Mf * C) return;
+  const long long mf = t / C;
+  const int c = (int)(t % C);
+  const long long per = 1LL << (3 * lgDf);
+  const long long b = mf / per, r = mf % per;
+  const int Df = 1 << lgDf, lgDc = lgDf - 1;
+  const int i = (int)(r >> (2 * lgDf)), j = (int)((r >> lgDf) & (Df - 1)), k = (int)(r & (Df - 1));
+  const long long mc = (b << (3 * lgDc)) + ((((long long)(i >> 1) << lgDc) + (j >> 1)) << lgDc) + (k >> 1);
+  y.p[mf * y.ld + y.off + c] = x.p[mc * x.ld + x.off + c];
+}
+
+// g_coarse[parent][c] = sum of the 8 children's gradients
+__global__ void k_up_bwd(FView gf, FView gc, int C, int lgDc, long long Mc) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= Mc * C) return;
+  const long long mc = t / C;
+  const int c = (int)(t % C);
+  const long long per = 1LL << (3 * lgDc);
+  const long long b = mc / per, r = mc % per;
+  const int Dc = 1 << lgDc, lgDf = lgDc + 1;
+  const int I = (int)(r >> (2 * lgDc)), J = (int)((r >> lgDc) & (Dc - 1)), K = (int)(r & (Dc - 1));
+  float s = 0.f;
+  for (int q = 0; q < 8; ++q) {
+    const long long mf = (b << (3 * lgDf)) +
+                         ((((long long)(2 * I + (q >> 2)) << lgDf) + (2 * J + ((q >> 1) & 1))) << lgDf) +
+                         (2 * K + (q & 1));
+    s += gf.p[mf * gf.ld + gf.off + c];
+  }
+  gc.p[mc * gc.ld + gc.off + c] = s;
+}
+
+// gradient of the pre-activation: g * (y > 0), to BF16, contiguous [M][C]
+__global__ void k_relu_bwd(FView g, TView y, int C, long long M, __nv_bfloat16* __restrict__ out) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= M * C) return;
+  const long long m = t / C;
+  const int c = (int)(t % C);
+  const float yy = __bfloat162float(y.p[m * y.ld + y.off + c]);
+  out[t] = __float2bfloat16(yy > 0.f ? g.p[m * g.ld + g.off + c] : 0.f);
+}
+
+__global__ void k_head_fwd(TView x, const float* __restrict__ w, long long M, float* __restrict__ out) {
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  float s = w[16];
+  for (int c = 0; c < 16; ++c) s = fmaf(w[c], __bfloat162float(x.p[m * x.ld + x.off + c]), s);
+  out[m] = s;
+}
+
+// loss partials and d loss / d out = 2 (out - target) / M
+__global__ void k_mse(const float* __restrict__ out, const double* __restrict__ target, long long M,
+                      float* __restrict__ gout, double* __restrict__ partial) {
+  __shared__ double red[BS];
+  double s = 0.0;
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < M;
+       m += (long long)gridDim.x * blockDim.x) {
+    const double d = (double)out[m] - target[m];
+    s += d * d;
+    gout[m] = (float)(2.0 * d / (double)M);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = BS / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_head_bwd(TView x, const float* __restrict__ w, const float* __restrict__ gout,
+                           long long M, FView gx, float* __restrict__ gw_part) {
+  __shared__ float red[17][BS / 32];
+  float acc[17];
+  for (int c = 0; c < 17; ++c) acc[c] = 0.f;
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < M;
+       m += (long long)gridDim.x * blockDim.x) {
+    const float g = gout[m];
+    for (int c = 0; c < 16; ++c) {
+      acc[c] = fmaf(g, __bfloat162float(x.p[m * x.ld + x.off + c]), acc[c]);
+      gx.p[m * gx.ld + gx.off + c] = g * w[c];
+    }
+    acc[16] += g;
+  }
+  for (int c = 0; c < 17; ++c) {
+    float v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 17) {
+    float s = 0.f;
+    for (int q = 0; q < BS / 32; ++q) s += red[threadIdx.x][q];
+    gw_part[blockIdx.x * 17 + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_sum_parts(const float* __restrict__ part, int nparts, int n, float* __restrict__ out) {
+  const int i = threadIdx.x;
+  if (i >= n) return;
+  float s = 0.f;
+  for (int q = 0; q < nparts; ++q) s += part[q * n + i];
+  out[i] = s;
+}
+
+// Adam (bias-corrected), then refresh the BF16 copies of conv weights
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
+                       float* __restrict__ m2, long long n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float a = b1 * m1[i] + (1.f - b1) * gi;
+  const float b = b2 * m2[i] + (1.f - b2) * gi * gi;
+  m1[i] = a;
+  m2[i] = b;
+  p[i] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = __float2bfloat16(x[i]);
+}
+
+__global__ void k_out_to_double(const float* __restrict__ x, double* __restrict__ y, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (double)x[i];
+}
+
+__global__ void k_zero_f(float* __restrict__ x, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) x[i] = 0.f;
+}
+
+}  // namespace
+
+// ============================================================================
+struct UNet {
+  // parameter layout in one flat FP32 array: per conv W[27][cin][cout], b[cout]; head w[16], b
+  long long woff[14], boff[14], head_off = 0, nparam = 0;
+  long long wbf_off[14], nwbf = 0;
+  float *P = nullptr, *G = nullptr, *M1 = nullptr, *M2 = nullptr;  // device
+  __nv_bfloat16* Wbf = nullptr;
+  long long step = 0;
+  // activation buffers for one (B, lgD)
+  int B = 0, lgD = 0;
+  std::vector<void*> bufs;
+  __nv_bfloat16 *X0, *E1a, *CAT1, *P1, *E2a, *CAT2, *P2, *E3a, *CAT3, *P3, *Ba, *Bb, *D3a, *D3b,
+      *D2a, *D2b, *D1a, *D1b, *Gpre;
+  float *OUT, *GOUT, *G_E1a, *G_CAT1, *G_P1, *G_E2a, *G_CAT2, *G_P2, *G_E3a, *G_CAT3, *G_P3, *G_Ba,
+      *G_Bb, *G_D3a, *G_D3b, *G_D2a, *G_D2b, *G_D1a, *G_D1b, *wpart;
+  double* fr0d = nullptr;
+  double* lossp = nullptr;
+  long long wpart_n = 0;
+};
+
+static void unet_free_bufs(UNet* U) {
+  for (void* p : U->bufs) cudaFree(p);
+  U->bufs.clear();
+  U->B = U->lgD = 0;
+}
+
+void unet_free(mgfr_ctx* c) {
+  UNet* U = (UNet*)c->unet;
+  if (!U) return;
+  unet_free_bufs(U);
+  void* ps[] = {U->P, U->G, U->M1, U->M2, U->Wbf};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  delete U;
+  c->unet = nullptr;
+}
+
+static mgfr_status unet_alloc(mgfr_ctx* c, UNet* U, int B, int lgD) {
+  if (U->B == B && U->lgD == lgD) return MGFR_OK;
+  unet_free_bufs(U);
+  const long long M0 = (long long)B << (3 * lgD), M1 = M0 >> 3, M2 = M1 >> 3, M3 = M2 >> 3;
+  auto bf = [&](long long n) -> __nv_bfloat16* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(__nv_bfloat16) * (size_t)n) != cudaSuccess) return nullptr;
+    U->bufs.push_back(p);
+    return (__nv_bfloat16*)p;
+  };
+  auto f = [&](long long n) -> float* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(float) * (size_t)n) != cudaSuccess) return nullptr;
+    U->bufs.push_back(p);
+    return (float*)p;
+  };
+  U->X0 = bf(M0 * 16);
+  U->E1a = bf(M0 * 16);
+  U->CAT1 = bf(M0 * 48);
+  U->P1 = bf(M1 * 16);
+  U->E2a = bf(M1 * 32);
+  U->CAT2 = bf(M1 * 96);
+  U->P2 = bf(M2 * 32);
+  U->E3a = bf(M2 * 64);
+  U->CAT3 = bf(M2 * 192);
+  U->P3 = bf(M3 * 64);
+  U->Ba = bf(M3 * 128);
+  U->Bb = bf(M3 * 128);
+  U->D3a = bf(M2 * 64);
+  U->D3b = bf(M2 * 64);
+  U->D2a = bf(M1 * 32);
+  U->D2b = bf(M1 * 32);
+  U->D1a = bf(M0 * 16);
+  U->D1b = bf(M0 * 16);
+  U->Gpre = bf(M0 * 48);
+  U->OUT = f(M0);
+  U->GOUT = f(M0);
+  U->G_E1a = f(M0 * 16);
+  U->G_CAT1 = f(M0 * 48);
+  U->G_P1 = f(M1 * 16);
+  U->G_E2a = f(M1 * 32);
+  U->G_CAT2 = f(M1 * 96);
+  U->G_P2 = f(M2 * 32);
+  U->G_E3a = f(M2 * 64);
+  U->G_CAT3 = f(M2 * 192);
+  U->G_P3 = f(M3 * 64);
+  U->G_Ba = f(M3 * 128);
+  U->G_Bb = f(M3 * 128);
+  U->G_D3a = f(M2 * 64);
+  U->G_D3b = f(M2 * 64);
+  U->G_D2a = f(M1 * 32);
+  U->G_D2b = f(M1 * 32);
+  U->G_D1a = f(M0 * 16);
+  U->G_D1b = f(M0 * 16);
+  long long wn = 0;
+  for (const ConvSpec& cs : kConvs) wn = std::max(wn, nn_wgrad_scratch(cs.cin, cs.cout));
+  U->wpart_n = wn;
+  U->wpart = f(std::max(wn, 17LL * 1024));
+  void* p = nullptr;
+  if (cudaMalloc(&p, sizeof(double) * 1024) != cudaSuccess) return set_err(c, MGFR_E_OOM, "unet");
+  U->bufs.push_back(p);
+  U->lossp = (double*)p;
+  if (cudaMalloc(&p, sizeof(double) * 4096) != cudaSuccess) return set_err(c, MGFR_E_OOM, "unet");
+  U->bufs.push_back(p);
+  U->fr0d = (double*)p;
+  for (void* q : U->bufs)
+    if (!q) return set_err(c, MGFR_E_OOM, "U-Net activation allocation failed");
+  U->B = B;
+  U->lgD = lgD;
+  return MGFR_OK;
+}
+
+static TView tv(__nv_bfloat16* p, int ld, int off = 0) { return TView{p, ld, off}; }
+static FView fv(float* p, int ld, int off = 0) { return FView{p, ld, off}; }
+
+// conv layer i: input view, output view (post-ReLU)
+struct LayerIO {
+  TView x, y;
+  FView gx, gy;  // gradients w.r.t. input and output
+  int lgD;
+};
+
+static void layer_views(UNet* U, LayerIO* L) {
+  const int g = U->lgD;
+  L[0] = {tv(U->X0, 16), tv(U->E1a, 16), fv(nullptr, 0), fv(U->G_E1a, 16), g};
+  L[1] = {tv(U->E1a, 16), tv(U->CAT1, 48, 32), fv(U->G_E1a, 16), fv(U->G_CAT1, 48, 32), g};
+  L[2] = {tv(U->P1, 16), tv(U->E2a, 32), fv(U->G_P1, 16), fv(U->G_E2a, 32), g - 1};
+  L[3] = {tv(U->E2a, 32), tv(U->CAT2, 96, 64), fv(U->G_E2a, 32), fv(U->G_CAT2, 96, 64), g - 1};
+  L[4] = {tv(U->P2, 32), tv(U->E3a, 64), fv(U->G_P2, 32), fv(U->G_E3a, 64), g - 2};
+  L[5] = {tv(U->E3a, 64), tv(U->CAT3, 192, 128), fv(U->G_E3a, 64), fv(U->G_CAT3, 192, 128), g - 2};
+  L[6] = {tv(U->P3, 64), tv(U->Ba, 128), fv(U->G_P3, 64), fv(U->G_Ba, 128), g - 3};
+  L[7] = {tv(U->Ba, 128), tv(U->Bb, 128), fv(U->G_Ba, 128), fv(U->G_Bb, 128), g - 3};
+  L[8] = {tv(U->CAT3, 192), tv(U->D3a, 64), fv(U->G_CAT3, 192), fv(U->G_D3a, 64), g - 2};
+  L[9] = {tv(U->D3a, 64), tv(U->D3b, 64), fv(U->G_D3a, 64), fv(U->G_D3b, 64), g - 2};
+  L[10] = {tv(U->CAT2, 96), tv(U->D2a, 32), fv(U->G_CAT2, 96), fv(U->G_D2a, 32), g - 1};
+  L[11] = {tv(U->D2a, 32), tv(U->D2b, 32), fv(U->G_D2a, 32), fv(U->G_D2b, 32), g - 1};
+  L[12] = {tv(U->CAT1, 48), tv(U->D1a, 16), fv(U->G_CAT1, 48), fv(U->G_D1a, 16), g};
+  L[13] = {tv(U->D1a, 16), tv(U->D1b, 16), fv(U->G_D1a, 16), fv(U->G_D1b, 16), g};
+}
+
+static void conv_fwd(mgfr_ctx* c, UNet* U, int i, const LayerIO& L) {
+  const ConvSpec& s = kConvs[i];
+  nn_conv_fwd(L.x, s.cin, U->Wbf + U->wbf_off[i], U->P + U->boff[i], 1, L.y, s.cout, U->B, L.lgD,
+              c->s);
+  c->launches += 1;
+}
+
+static void forward(mgfr_ctx* c, UNet* U) {
+  LayerIO L[14];
+  layer_views(U, L);
+  const int g = U->lgD, B = U->B;
+  const long long M0 = (long long)B << (3 * g);
+  auto launch_pool = [&](TView x, TView y, int C, int lgDc) {
+    const long long Mc = (long long)B << (3 * lgDc);
+    k_pool<<<nblocks(Mc * C, BS), BS, 0, c->s>>>(x, y, C, lgDc, Mc);
+    c->launches += 1;
+  };
+  auto launch_up = [&](TView x, TView y, int C, int lgDf) {
+    const long long Mf = (long long)B << (3 * lgDf);
+    k_up<<<nblocks(Mf * C, BS), BS, 0, c->s>>>(x, y, C, lgDf, Mf);
+    c->launches += 1;
+  };
+  conv_fwd(c, U, 0, L[0]);
+  conv_fwd(c, U, 1, L[1]);
+  launch_pool(tv(U->CAT1, 48, 32), tv(U->P1, 16), 16, g - 1);
+  conv_fwd(c, U, 2, L[2]);
+  conv_fwd(c, U, 3, L[3]);
+  launch_pool(tv(U->CAT2, 96, 64), tv(U->P2, 32), 32, g - 2);
+  conv_fwd(c, U, 4, L[4]);
+  conv_fwd(c, U, 5, L[5]);
+  launch_pool(tv(U->CAT3, 192, 128), tv(U->P3, 64), 64, g - 3);
+  conv_fwd(c, U, 6, L[6]);
+  conv_fwd(c, U, 7, L[7]);
+  launch_up(tv(U->Bb, 128), tv(U->CAT3, 192, 0), 128, g - 2);
+  conv_fwd(c, U, 8, L[8]);
+  conv_fwd(c, U, 9, L[9]);
+  launch_up(tv(U->D3b, 64), tv(U->CAT2, 96, 0), 64, g - 1);
+  conv_fwd(c, U, 10, L[10]);
+  conv_fwd(c, U, 11, L[11]);
+  launch_up(tv(U->D2b, 32), tv(U->CAT1, 48, 0), 32, g);
+  conv_fwd(c, U, 12, L[12]);
+  conv_fwd(c, U, 13, L[13]);
+  k_head_fwd<<<nblocks(M0, BS), BS, 0, c->s>>>(tv(U->D1b, 16), U->P + U->head_off, M0, U->OUT);
+  c->launches += 1;
+}
+
+static void conv_bwd(mgfr_ctx* c, UNet* U, int i, const LayerIO& L, int acc_in) {
+  const ConvSpec& s = kConvs[i];
+  const long long M = (long long)U->B << (3 * L.lgD);
+  k_relu_bwd<<<nblocks(M * s.cout, BS), BS, 0, c->s>>>(L.gy, L.y, s.cout, M, U->Gpre);
+  const TView g = tv(U->Gpre, s.cout);
+  nn_conv_wgrad(L.x, s.cin, g, s.cout, U->G + U->woff[i], U->G + U->boff[i], U->wpart, U->B, L.lgD,
+                c->s);
+  if (L.gx.p) nn_conv_dgrad(g, s.cout, U->Wbf + U->wbf_off[i], L.gx, s.cin, acc_in, U->B, L.lgD, c->s);
+  c->launches += 5;
+}
+
+static void backward(mgfr_ctx* c, UNet* U) {
+  LayerIO L[14];
+  layer_views(U, L);
+  const int g = U->lgD, B = U->B;
+  const long long M0 = (long long)B << (3 * g);
+  const int nb = 256;
+  k_head_bwd<<<nb, BS, 0, c->s>>>(tv(U->D1b, 16), U->P + U->head_off, U->GOUT, M0,
+                                   fv(U->G_D1b, 16), U->wpart);
+  k_sum_parts<<<1, 32, 0, c->s>>>(U->wpart, nb, 17, U->G + U->head_off);
+  c->launches += 2;
+  auto up_bwd = [&](FView gf, FView gc, int C, int lgDc) {
+    const long long Mc = (long long)B << (3 * lgDc);
+    k_up_bwd<<<nblocks(Mc * C, BS), BS, 0, c->s>>>(gf, gc, C, lgDc, Mc);
+    c->launches += 1;
+  };
+  auto pool_bwd = [&](FView gc, FView gf, int C, int lgDf) {
+    const long long Mf = (long long)B << (3 * lgDf);
+    k_pool_bwd<<<nblocks(Mf * C, BS), BS, 0, c->s>>>(gc, gf, C, lgDf, Mf);
+    c->launches += 1;
+  };
+  conv_bwd(c, U, 13, L[13], 0);                        // -> G_D1a
+  conv_bwd(c, U, 12, L[12], 0);                        // -> G_CAT1 (all 48)
+  up_bwd(fv(U->G_CAT1, 48, 0), fv(U->G_D2b, 32), 32, g - 1);
+  conv_bwd(c, U, 11, L[11], 0);                        // -> G_D2a
+  conv_bwd(c, U, 10, L[10], 0);                        // -> G_CAT2 (all 96)
+  up_bwd(fv(U->G_CAT2, 96, 0), fv(U->G_D3b, 64), 64, g - 2);
+  conv_bwd(c, U, 9, L[9], 0);                          // -> G_D3a
+  conv_bwd(c, U, 8, L[8], 0);                          // -> G_CAT3 (all 192)
+  up_bwd(fv(U->G_CAT3, 192, 0), fv(U->G_Bb, 128), 128, g - 3);
+  conv_bwd(c, U, 7, L[7], 0);                          // -> G_Ba
+  conv_bwd(c, U, 6, L[6], 0);                          // -> G_P3
+  pool_bwd(fv(U->G_P3, 64), fv(U->G_CAT3, 192, 128), 64, g - 2);
+  conv_bwd(c, U, 5, L[5], 0);                          // -> G_E3a
+  conv_bwd(c, U, 4, L[4], 0);                          // -> G_P2
+  pool_bwd(fv(U->G_P2, 32), fv(U->G_CAT2, 96, 64), 32, g - 1);
+  conv_bwd(c, U, 3, L[3], 0);                          // -> G_E2a
+  conv_bwd(c, U, 2, L[2], 0);                          // -> G_P1
+  pool_bwd(fv(U->G_P1, 16), fv(U->G_CAT1, 48, 32), 16, g);
+  conv_bwd(c, U, 1, L[1], 0);                          // -> G_E1a
+  conv_bwd(c, U, 0, L[0], 0);                          // no input gradient
+}
+
+static void refresh_bf16(mgfr_ctx* c, UNet* U) {
+  for (int i = 0; i < 14; ++i) {
+    const long long n = 27LL * kConvs[i].cin * kConvs[i].cout;
+    k_to_bf16<<<nblocks(n, BS), BS, 0, c->s>>>(U->P + U->woff[i], U->Wbf + U->wbf_off[i], n);
+    c->launches += 1;
+  }
+}
+
+static mgfr_status unet_make(mgfr_ctx* c, unsigned long long seed) {
+  unet_free(c);
+  UNet* U = new UNet();
+  c->unet = U;
+  long long off = 0, boff = 0;
+  for (int i = 0; i < 14; ++i) {
+    U->woff[i] = off;
+    off += 27LL * kConvs[i].cin * kConvs[i].cout;
+    U->boff[i] = off;
+    off += kConvs[i].cout;
+    U->wbf_off[i] = boff;
+    boff += 27LL * kConvs[i].cin * kConvs[i].cout;
+  }
+  U->head_off = off;
+  off += 17;
+  U->nparam = off;
+  U->nwbf = boff;
+  MG_CK(c, cudaMalloc(&U->P, sizeof(float) * off));
+  MG_CK(c, cudaMalloc(&U->G, sizeof(float) * off));
+  MG_CK(c, cudaMalloc(&U->M1, sizeof(float) * off));
+  MG_CK(c, cudaMalloc(&U->M2, sizeof(float) * off));
+  MG_CK(c, cudaMalloc(&U->Wbf, sizeof(__nv_bfloat16) * boff));
+  // He-normal initialisation from a seeded generator (host), zero biases
+  std::vector<float> h((size_t)off, 0.f);
+  std::mt19937_64 rng(seed);
+  for (int i = 0; i < 14; ++i) {
+    std::normal_distribution<float> nd(0.f, std::sqrt(2.f / (27.f * kConvs[i].cin)));
+    for (long long q = 0; q < 27LL * kConvs[i].cin * kConvs[i].cout; ++q) h[U->woff[i] + q] = nd(rng);
+  }
+  std::normal_distribution<float> nh(0.f, 0.25f);
+  for (int q = 0; q < 16; ++q) h[U->head_off + q] = nh(rng);
+  MG_CK(c, cudaMemcpy(U->P, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice));
+  MG_CK(c, cudaMemset(U->M1, 0, sizeof(float) * off));
+  MG_CK(c, cudaMemset(U->M2, 0, sizeof(float) * off));
+  refresh_bf16(c, U);
+  MG_CK(c, cudaStreamSynchronize(c->s));
+  return MGFR_OK;
+}
+
+static int lg_of(int D) {
+  int lg = 0;
+  while ((1 << lg) < D) ++lg;
+  return lg;
+}
+
+extern "C" {
+
+mgfr_status mgfr_unet_init(mgfr_ctx* c, unsigned long long seed) {
+  if (!c) return MGFR_E_INVALID;
+  MG_CK(c, cudaSetDevice(c->device));
+  return unet_make(c, seed);
+}
+
+mgfr_status mgfr_unet_train_step(mgfr_ctx* c, int B, int D, const double* delta_dev,
+                                 const double* fr0_host, const double* u_target_dev, float lr,
+                                 double* loss_out) {
+  if (!c || !c->unet) return c ? set_err(c, MGFR_E_INVALID, "call mgfr_unet_init first") : MGFR_E_INVALID;
+  if (B < 1 || B > 4096 || D < 32 || D > 512 || (D & (D - 1)) || !delta_dev || !fr0_host ||
+      !u_target_dev)
+    return set_err(c, MGFR_E_INVALID, "bad U-Net training batch");
+  UNet* U = (UNet*)c->unet;
+  MG_CK(c, cudaSetDevice(c->device));
+  mgfr_status rs = unet_alloc(c, U, B, lg_of(D));
+  if (rs != MGFR_OK) return rs;
+  const long long M0 = (long long)B * D * D * D;
+  MG_CK(c, cudaMemcpyAsync(U->fr0d, fr0_host, sizeof(double) * B, cudaMemcpyHostToDevice, c->s));
+  k_features<<<nblocks(M0, BS), BS, 0, c->s>>>(delta_dev, U->fr0d, (long long)D * D * D, M0, U->X0);
+  forward(c, U);
+  const int nb = 1024;
+  k_mse<<<nb, BS, 0, c->s>>>(U->OUT, u_target_dev, M0, U->GOUT, U->lossp);
+  backward(c, U);
+  U->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)U->step), c2 = 1.f - std::pow(b2, (float)U->step);
+  k_adam<<<nblocks(U->nparam, BS), BS, 0, c->s>>>(U->P, U->G, U->M1, U->M2, U->nparam, lr, b1, b2,
+                                                  1e-8f, c1, c2);
+  refresh_bf16(c, U);
+  std::vector<double> part(nb);
+  MG_CK(c, cudaMemcpyAsync(part.data(), U->lossp, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->s));
+  MG_CK(c, cudaStreamSynchronize(c->s));
+  MG_CK(c, cudaGetLastError());
+  double s = 0.0;
+  for (double v : part) s += v;
+  if (loss_out) *loss_out = s / (double)M0;
+  return MGFR_OK;
+}
+
+mgfr_status mgfr_unet_predict(mgfr_ctx* c, int D, const double* delta_dev, double fr0_abs,
+                              double* u_out_dev) {
+  if (!c || !c->unet) return c ? set_err(c, MGFR_E_INVALID, "call mgfr_unet_init first") : MGFR_E_INVALID;
+  if (D < 32 || D > 512 || (D & (D - 1)) || !delta_dev || !u_out_dev || !(fr0_abs > 0.0))
+    return set_err(c, MGFR_E_INVALID, "bad U-Net input");
+  UNet* U = (UNet*)c->unet;
+  MG_CK(c, cudaSetDevice(c->device));
+  mgfr_status rs = unet_alloc(c, U, 1, lg_of(D));
+  if (rs != MGFR_OK) return rs;
+  const long long M0 = (long long)D * D * D;
+  MG_CK(c, cudaMemcpyAsync(U->fr0d, &fr0_abs, sizeof(double), cudaMemcpyHostToDevice, c->s));
+  k_features<<<nblocks(M0, BS), BS, 0, c->s>>>(delta_dev, U->fr0d, M0, M0, U->X0);
+  forward(c, U);
+  k_out_to_double<<<nblocks(M0, BS), BS, 0, c->s>>>(U->OUT, u_out_dev, M0);
+  MG_CK(c, cudaStreamSynchronize(c->s));
+  MG_CK(c, cudaGetLastError());
+  return MGFR_OK;
+}
+
+mgfr_status mgfr_unet_params(mgfr_ctx* c, int set, float* host, long long* count) {
+  if (!c || !c->unet) return MGFR_E_INVALID;
+  UNet* U = (UNet*)c->unet;
+  if (count) *count = U->nparam;
+  if (!host) return MGFR_OK;
+  if (set) {
+    MG_CK(c, cudaMemcpy(U->P, host, sizeof(float) * U->nparam, cudaMemcpyHostToDevice));
+    refresh_bf16(c, U);
+    MG_CK(c, cudaStreamSynchronize(c->s));
+  } else {
+    MG_CK(c, cudaMemcpy(host, U->P, sizeof(float) * U->nparam, cudaMemcpyDeviceToHost));
+  }
+  return MGFR_OK;
+}
+
+mgfr_status mgfr_unet_grads(mgfr_ctx* c, float* host) {
+  if (!c || !c->unet || !host) return MGFR_E_INVALID;
+  UNet* U = (UNet*)c->unet;
+  MG_CK(c, cudaMemcpy(host, U->G, sizeof(float) * U->nparam, cudaMemcpyDeviceToHost));
+  return MGFR_OK;
+}
+
+// Convolution primitive on caller buffers (contiguous NDHWC, C multiples of 16):
+// op 0: y(bf16) = relu?(conv(x, W) + b); op 1: gx(FP32) = conv^T(g, W);
+// op 2: dW(FP32 [27][Cin][Cout]), db(FP32) from x and g.
+mgfr_status mgfr_nn_conv3d(int op, int B, int D, int Cin, int Cout, const void* x_bf16,
+                           const void* w_bf16, const float* bias, int relu, const void* g_bf16,
+                           void* out, float* db, void* stream) {
+  if (B < 1 || D < 4 || (D & (D - 1)) || Cin % 16 || Cout % 16 || Cin < 16 || Cout < 16 ||
+      Cout > 128 || Cin > 256)
+    return MGFR_E_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int lgD = lg_of(D);
+  if (op == 0) {
+    nn_conv_fwd(TView{(__nv_bfloat16*)x_bf16, Cin, 0}, Cin, (const __nv_bfloat16*)w_bf16, bias,
+                relu, TView{(__nv_bfloat16*)out, Cout, 0}, Cout, B, lgD, s);
+  } else if (op == 1) {
+    nn_conv_dgrad(TView{(__nv_bfloat16*)g_bf16, Cout, 0}, Cout, (const __nv_bfloat16*)w_bf16,
+                  FView{(float*)out, Cin, 0}, Cin, 0, B, lgD, s);
+  } else if (op == 2) {
+    float* part = nullptr;
+    if (cudaMalloc(&part, sizeof(float) * (size_t)nn_wgrad_scratch(Cin, Cout)) != cudaSuccess)
+      return MGFR_E_OOM;
+    nn_conv_wgrad(TView{(__nv_bfloat16*)x_bf16, Cin, 0}, Cin, TView{(__nv_bfloat16*)g_bf16, Cout, 0},
+                  Cout, (float*)out, db, part, B, lgD, s);
+    cudaStreamSynchronize(s);
+    cudaFree(part);
+  } else {
+    return MGFR_E_INVALID;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return MGFR_E_CUDA;
+  return MGFR_OK;
+}
+
+}  // extern "C"

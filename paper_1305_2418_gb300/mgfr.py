@@ -87,6 +87,15 @@ SIGNATURES = {
                                              C.c_void_p]),
     "mgfr_batch_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "mgfr_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mgfr_unet_init": (C.c_int, [C.c_void_p, C.c_ulonglong]),
+    "mgfr_unet_train_step": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_float, C.c_void_p]),
+    "mgfr_unet_predict": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_double, C.c_void_p]),
+    "mgfr_unet_params": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "mgfr_unet_grads": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mgfr_nn_conv3d": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p]),
     "mgfr_last_error": (C.c_char_p, [C.c_void_p]),
     "mgfr_destroy": (None, [C.c_void_p]),
 }
@@ -251,3 +260,66 @@ class Solver:
         t, b = C.c_int(), C.c_int()
         self._check(lib().mgfr_batch_autotune(self.h, k, items, C.byref(t), C.byref(b)), True)
         return t.value, b.value
+
+    # ---- learned initial guess (U-Net) ----
+    def unet_init(self, seed: int = 0):
+        self._check(lib().mgfr_unet_init(self.h, seed))
+
+    def unet_train_step(self, deltas, fr0s, targets, lr=1e-3):
+        """One Adam step on a batch: deltas/targets [B, D, D, D] CUDA FP64."""
+        import numpy as np
+        B, D = deltas.shape[0], deltas.shape[1]
+        fr = np.ascontiguousarray(fr0s, dtype=np.float64)
+        loss = C.c_double()
+        self._check(lib().mgfr_unet_train_step(self.h, B, D, _ptr(deltas.contiguous()),
+                                               fr.ctypes.data_as(C.c_void_p),
+                                               _ptr(targets.contiguous()), lr, C.byref(loss)))
+        return loss.value
+
+    def unet_predict(self, delta, fr0_abs):
+        import torch
+        u = torch.empty_like(delta)
+        self._check(lib().mgfr_unet_predict(self.h, delta.shape[0], _ptr(delta), fr0_abs, _ptr(u)))
+        return u
+
+    def unet_params(self):
+        import numpy as np
+        n = C.c_longlong()
+        self._check(lib().mgfr_unet_params(self.h, 0, None, C.byref(n)))
+        out = np.empty(n.value, dtype=np.float32)
+        self._check(lib().mgfr_unet_params(self.h, 0, out.ctypes.data_as(C.c_void_p), None))
+        return out
+
+    def unet_set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(lib().mgfr_unet_params(self.h, 1, p.ctypes.data_as(C.c_void_p), None))
+
+    def unet_grads(self):
+        import numpy as np
+        n = C.c_longlong()
+        self._check(lib().mgfr_unet_params(self.h, 0, None, C.byref(n)))
+        out = np.empty(n.value, dtype=np.float32)
+        self._check(lib().mgfr_unet_grads(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+
+def conv3d(op, x, w, bias=None, relu=False, g=None, db=None, stream=None):
+    """Convolution primitive of the network (mgfr_nn_conv3d) on torch tensors:
+    x [B, D, D, D, Cin] bf16, w [27, Cin, Cout] bf16, g [B, D, D, D, Cout] bf16."""
+    import torch
+    B, D = x.shape[0], x.shape[1]
+    Cin, Cout = w.shape[1], w.shape[2]
+    if op == 0:
+        out = torch.empty(x.shape[:-1] + (Cout,), dtype=torch.bfloat16, device=x.device)
+    elif op == 1:
+        out = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    else:
+        out = torch.empty((27, Cin, Cout), dtype=torch.float32, device=x.device)
+    s = torch.cuda.current_stream(x.device) if stream is None else stream
+    vp = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+    st = lib().mgfr_nn_conv3d(op, B, D, Cin, Cout, vp(x), vp(w), vp(bias), int(relu), vp(g),
+                              vp(out), vp(db), C.c_void_p(s.cuda_stream))
+    if st != MGFR_OK:
+        raise MGFRError(st, "mgfr_nn_conv3d failed")
+    return out

@@ -1,0 +1,79 @@
+"""GPU tests of the learned-start network: its BF16 tensor-core convolution
+kernels against the FP64 NumPy oracle (forward, input gradient, weight
+gradient), and the trained network's gain over a zero start.
+
+Tolerances: forward output is BF16, so |diff| <= 8e-3 max|ref|; the
+gradients are accumulated and returned in FP32: |diff| <= 2e-5 max|ref|.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import nn_oracle as nn
+from paper_1305_2418_gb300 import build, learned, mgfr, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available(), "GPU test run without a GPU"
+    build.build()
+    return torch.device("cuda:0")
+
+
+def bf(a, dev):
+    return torch.from_numpy(a).to(dev).to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("B,D,Cin,Cout", [(1, 8, 16, 16), (2, 8, 48, 16), (1, 8, 192, 64),
+                                          (1, 4, 64, 128), (1, 8, 96, 32), (2, 4, 128, 128)])
+def test_conv_kernels_match_oracle(dev, B, D, Cin, Cout):
+    rng = np.random.default_rng(B * 1000 + D * 10 + Cin + Cout)
+    x = rng.standard_normal((B, D, D, D, Cin)).astype(np.float32)
+    W = (rng.standard_normal((27, Cin, Cout)) / np.sqrt(27 * Cin)).astype(np.float32)
+    b = rng.standard_normal(Cout).astype(np.float32)
+    g = rng.standard_normal((B, D, D, D, Cout)).astype(np.float32)
+    xt, Wt, gt = bf(x, dev), bf(W, dev), bf(g, dev)
+    # the oracle sees exactly the BF16-rounded operands, in FP64
+    x64 = xt.float().cpu().numpy().astype(np.float64)
+    W64 = Wt.float().cpu().numpy().astype(np.float64)
+    g64 = gt.float().cpu().numpy().astype(np.float64)
+    bt = torch.from_numpy(b).to(dev)
+    y = mgfr.conv3d(0, xt, Wt, bias=bt, relu=True).float().cpu().numpy()
+    y_ref = nn.conv3d_fwd(x64, W64, b.astype(np.float64), relu=True)
+    assert np.abs(y - y_ref).max() <= 8e-3 * np.abs(y_ref).max()
+    gx = mgfr.conv3d(1, xt, Wt, g=gt).cpu().numpy()
+    gx_ref = nn.conv3d_dgrad(g64, W64)
+    assert np.abs(gx - gx_ref).max() <= 2e-5 * np.abs(gx_ref).max()
+    db = torch.empty(Cout, dtype=torch.float32, device=dev)
+    dW = mgfr.conv3d(2, xt, Wt, g=gt, db=db).cpu().numpy()
+    dW_ref, db_ref = nn.conv3d_wgrad(x64, g64)
+    assert np.abs(dW - dW_ref).max() <= 2e-5 * np.abs(dW_ref).max()
+    assert np.abs(db.cpu().numpy() - db_ref).max() <= 2e-5 * np.abs(db_ref).max()
+
+
+def test_unet_training_reduces_loss_and_cycles(dev):
+    """Train on solver-generated 32^3 pairs (12.5 Mpc/h boxes, the 0.39 Mpc/h
+    cell of the 256^3 / 100 Mpc/h fields), then start 64^3 solves at the same
+    cell size from the prediction: fewer V-cycles than from zero, same answer."""
+    s = mgfr.Solver(0, precision=mgfr.PREC_MIXED)
+    deltas, fr0s, us = learned.make_training_set(s, 64, 32, 12.5, seed=11)
+    s.unet_init(seed=3)
+    losses = learned.train(s, deltas, fr0s, us, steps=400, batch=4, lr=2e-3, seed=5)
+    first, last = float(np.mean(losses[:20])), float(np.mean(losses[-20:]))
+    assert np.isfinite(last) and last < 0.1 * first, (first, last)
+    fields = []
+    rng = np.random.default_rng(99)
+    for q in range(4):
+        fr0 = float(10 ** rng.uniform(-6, -4))
+        d = torch.from_numpy(synth.lognormal_delta(64, 25.0, float(rng.uniform(0.5, 2.0)),
+                                                   777 + q)).to(dev)
+        fields.append((d, fr0))
+    rows = learned.evaluate(s, fields, 25.0)
+    zero = sum(r["zero_cycles"] for r in rows)
+    lrn = sum(r["learned_cycles"] for r in rows)
+    assert lrn < zero, rows
+    for r in rows:
+        assert r["max_rel_diff_fr"] <= 1e-5, r
+    s.close()
