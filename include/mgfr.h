@@ -230,7 +230,8 @@ mgfr_status mgfr_batch_autotune(mgfr_ctx* ctx, int nsolves, const mgfr_batch_ite
  * from the previous step's u, Sec. 3.3 step 2).  A 4-level 3D U-Net
  * (16/32/64/128 channels, 3^3 kernels, circular padding, BF16 weights and
  * activations, FP32 accumulation) maps per-voxel features (ln(1+delta),
- * log10|fR0| + 5, 1) to u; the multigrid then drives the residual to the same
+ * log10|fR0| + 5, 1, and the local screening value -(n+1) ln(1 + Om delta/Rt)
+ * at a = 1) to u; the multigrid then drives the residual to the same
  * tolerance from that start (pass it as u_init).  Training and inference run
  * on this library's own tensor-core kernels.  D (box cells per side) must be
  * a power of two in [32, 512]; the network applies at the cell size it was

@@ -3,8 +3,9 @@
 // and activations and FP32 accumulation, trained and evaluated on the GPU by
 // this library's own kernels (nn_conv.cu and the elementwise kernels here).
 //
-// Input features per voxel: ln(1 + delta), log10|fR0| + 5, 1 (padded to 16
-// channels).  Output: u (FP32).  Encoder: two conv+ReLU per level, 2^3
+// Input features per voxel: ln(1 + delta), log10|fR0| + 5, 1 and the local
+// screening value -(n+1) ln(1 + Om delta / Rt) (padded to 16 channels; the
+// boxes are at a = 1).  Output: u (FP32).  Encoder: two conv+ReLU per level, 2^3
 // average pooling.  Decoder: nearest upsampling, concatenation with the
 // encoder output of the same level, two conv+ReLU.  Head: 1x1x1 conv to 1
 // channel.  Loss: mean squared error in u.  Optimiser: Adam on FP32 master
@@ -40,8 +41,12 @@ const ConvSpec kConvs[14] = {
     {48, 16, 0},  {16, 16, 0},                       // dec1 (up 32 + enc1 16)
 };
 
+// features: ln(1+delta), log10|fR0| + 5, 1, and the local screening value
+// -(n+1) ln(1 + Om a^-3 delta / Rt) (the solution where delta is uniform on
+// scales beyond the Compton length), clamped to [-20, 5].
 __global__ void k_features(const double* __restrict__ delta, const double* __restrict__ fr0s,
-                           long long per, long long M, __nv_bfloat16* __restrict__ x) {
+                           long long per, long long M, __nv_bfloat16* __restrict__ x,
+                           double scr, double np1) {
   const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (m >= M) return;
   const double d = delta[m];
@@ -50,7 +55,9 @@ __global__ void k_features(const double* __restrict__ delta, const double* __res
   o[0] = __float2bfloat16((float)log(fmax(1.0 + d, 1e-3)));
   o[1] = __float2bfloat16((float)(log10(fr0) + 5.0));
   o[2] = __float2bfloat16(1.f);
-  for (int c = 3; c < 16; ++c) o[c] = __float2bfloat16(0.f);
+  const double ul = -np1 * log(fmax(1.0 + scr * d, 1e-6));
+  o[3] = __float2bfloat16((float)fmin(fmax(ul, -20.0), 5.0));
+  for (int c = 4; c < 16; ++c) o[c] = __float2bfloat16(0.f);
 }
 
 // 2^3 average pooling: y[M'][c] from x (full res, view)
@@ -535,7 +542,9 @@ mgfr_status mgfr_unet_train_step(mgfr_ctx* c, int B, int D, const double* delta_
   if (rs != MGFR_OK) return rs;
   const long long M0 = (long long)B * D * D * D;
   MG_CK(c, cudaMemcpyAsync(U->fr0d, fr0_host, sizeof(double) * B, cudaMemcpyHostToDevice, c->s));
-  k_features<<<nblocks(M0, BS), BS, 0, c->s>>>(delta_dev, U->fr0d, (long long)D * D * D, M0, U->X0);
+  const Model mm = make_model(c->cfg, 1.0);
+  k_features<<<nblocks(M0, BS), BS, 0, c->s>>>(delta_dev, U->fr0d, (long long)D * D * D, M0, U->X0,
+                                               c->cfg.omega_m / mm.Rt, (double)(c->cfg.n + 1));
   forward(c, U);
   const int nb = 1024;
   k_mse<<<nb, BS, 0, c->s>>>(U->OUT, u_target_dev, M0, U->GOUT, U->lossp);
@@ -567,7 +576,9 @@ mgfr_status mgfr_unet_predict(mgfr_ctx* c, int D, const double* delta_dev, doubl
   if (rs != MGFR_OK) return rs;
   const long long M0 = (long long)D * D * D;
   MG_CK(c, cudaMemcpyAsync(U->fr0d, &fr0_abs, sizeof(double), cudaMemcpyHostToDevice, c->s));
-  k_features<<<nblocks(M0, BS), BS, 0, c->s>>>(delta_dev, U->fr0d, M0, M0, U->X0);
+  const Model mm = make_model(c->cfg, 1.0);
+  k_features<<<nblocks(M0, BS), BS, 0, c->s>>>(delta_dev, U->fr0d, M0, M0, U->X0,
+                                               c->cfg.omega_m / mm.Rt, (double)(c->cfg.n + 1));
   forward(c, U);
   k_out_to_double<<<nblocks(M0, BS), BS, 0, c->s>>>(U->OUT, u_out_dev, M0);
   MG_CK(c, cudaStreamSynchronize(c->s));
