@@ -42,13 +42,15 @@ WORKLOAD = dict(name="particles256", N=256, box=100.0, a=1.0, fr0=1e-5, sigma_g=
 #  2 FP64 residual: read u, E, f (24) + write r32, u32, e32 (12) = 36 B per cell
 #  (FP64 NGS half-sweep, plain path: read u, E (16) + f active (4) + write u, E
 #   active (8) = 28 B per cell)
-#  3 FP64 NGS half-sweep on octs: read u, E (16) + f active (4) + write u, E
-#    active (8) + neighbour-oct table (24 B per oct = 3)   = 31 B per cell
-ALG_BYTES = {0: 8.0, 1: 12.0, 2: 36.0, 3: 31.0}
+#  3 NGS half-sweep on the octs of the refined level being solved; in the
+#    mixed form these are FP32: read u, E (8) + f active (2) + write u, E
+#    active (4) + neighbour-oct table (24 B per oct = 3)    = 17 B per cell
+#    (FP64 form: 16 + 4 + 8 + 3 = 31 B per cell)
+ALG_BYTES = {0: 8.0, 1: 12.0, 2: 36.0, 3: 17.0}
 KERNEL_NAMES = {0: "k_sweep32 (FP32 NGS half-sweep, base level)",
                 1: "k_lin_sweep (FP32 linear GS half-sweep, base level)",
                 2: "k_resid64 (FP64 residual, base level)",
-                3: "k_oct_sweep (NGS half-sweep on the octs of the level being solved)"}
+                3: "k_osweep<float> (FP32 NGS half-sweep on the octs of the refined level)"}
 
 
 def peaks():

@@ -411,6 +411,293 @@ __global__ void __launch_bounds__(64) k_dcoarse(T* __restrict__ ug, T* __restric
   Eg[t] = E[t];
 }
 
+
+// ---- linear correction scheme (mixed precision, phase B) --------------------
+// J(u): Jacobian of L at the FP32 linearisation point u (E = e^u stored):
+//   J_ij = (E_j (u_j - u_i) + E_i + E_j) / (2h^2)
+//   J_ii = sum_j (E_i (u_j - u_i) - E_i - E_j) / (2h^2) + alpha Rt/(n+1) e^{-u_i/(n+1)}
+struct JR {
+  float off[6], diag;
+};
+
+__device__ __forceinline__ JR jrow(float uc, float Ec, const NB<float>* nb, const MT<float>& m,
+                                   float ih2) {
+  JR J;
+  const float h2 = 0.5f * ih2;
+  float d = 0.f;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const float du = nb[q].u - uc;
+    J.off[q] = h2 * fmaf(nb[q].E, du, Ec + nb[q].E);
+    d += fmaf(Ec, du, -Ec - nb[q].E);
+  }
+  J.diag = d * h2 + m.aRt_np1 * nls(uc, Ec, m);
+  return J;
+}
+
+// correction of the neighbour in direction d (0 at ghosts)
+__device__ __forceinline__ float onb_e(const float* __restrict__ e, const int* __restrict__ nbr,
+                                       long long o, int ch, int d) {
+  const int ax = d >> 1, plus = d & 1;
+  const int bit = (ch >> (2 - ax)) & 1;
+  const int chn = ch ^ (1 << (2 - ax));
+  if (bit != plus) return e[8 * o + chn];
+  const int no = nbr[6 * o + d];
+  return no >= 0 ? e[8LL * no + chn] : 0.f;
+}
+
+// FP64 residual of level L on the FP64 iterate; writes r, the FP32
+// linearisation point (u, E) and e = 0, and accumulates the norms
+__global__ void __launch_bounds__(BS) k_oresid_lin(
+    const double* __restrict__ u, const double* __restrict__ E, const double* __restrict__ f,
+    const int* __restrict__ nbr, const double* __restrict__ gh, const double* __restrict__ ghE,
+    long long ncell, MT<double> m, double ih2, float* __restrict__ r32, float* __restrict__ u32,
+    float* __restrict__ E32, float* __restrict__ e32, double* __restrict__ partials) {
+  double ss = 0.0, mx = 0.0, fs = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    const long long o = c >> 3;
+    const int ch = (int)(c & 7);
+    NB<double> nb[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
+    const double r = f[c] - Lval(u[c], E[c], nb, m, ih2);
+    r32[c] = (float)r;
+    u32[c] = (float)u[c];
+    E32[c] = (float)E[c];
+    e32[c] = 0.f;
+    ss = fma(r, r, ss);
+    mx = fmax(mx, fabs(r));
+    fs = fma(f[c], f[c], fs);
+  }
+  __shared__ double s1[BS / 32], s2[BS / 32], s3[BS / 32];
+  for (int q = 16; q > 0; q >>= 1) {
+    ss += __shfl_xor_sync(0xffffffffu, ss, q);
+    fs += __shfl_xor_sync(0xffffffffu, fs, q);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, q));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s1[threadIdx.x >> 5] = ss;
+    s2[threadIdx.x >> 5] = mx;
+    s3[threadIdx.x >> 5] = fs;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, ee = 0.0;
+    for (int w = 0; w < BS / 32; ++w) {
+      a += s1[w];
+      b = fmax(b, s2[w]);
+      ee += s3[w];
+    }
+    partials[3 * blockIdx.x] = a;
+    partials[3 * blockIdx.x + 1] = b;
+    partials[3 * blockIdx.x + 2] = ee;
+  }
+}
+
+__global__ void __launch_bounds__(BS) k_olin_sweep(float* __restrict__ e, const float* __restrict__ r,
+                                                   const float* __restrict__ u,
+                                                   const float* __restrict__ E,
+                                                   const int* __restrict__ nbr,
+                                                   const float* __restrict__ gh,
+                                                   const float* __restrict__ ghE,
+                                                   const float* __restrict__ mask, float mthr,
+                                                   long long n_oct, int colour, MT<float> m,
+                                                   float ih2) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= 4 * n_oct) return;
+  const long long o = t >> 2;
+  const int ch = kColourChild[colour][t & 3];
+  const long long c = 8 * o + ch;
+  if (mask && !(mask[c] > mthr)) return;
+  NB<float> nb[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
+  const JR J = jrow(u[c], E[c], nb, m, ih2);
+  float acc = r[c];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) acc = fmaf(-J.off[d], onb_e(e, nbr, o, ch, d), acc);
+  e[c] = __fdividef(acc, J.diag);
+}
+
+// r_c = R(r - J e) over relaxed daughters, u_c = R(u), E_c = e^{u_c}, e_c = 0
+__global__ void __launch_bounds__(BS) k_olin_restrict(
+    const float* __restrict__ e, const float* __restrict__ r, const float* __restrict__ u,
+    const float* __restrict__ E, const int* __restrict__ nbr, const float* __restrict__ gh,
+    const float* __restrict__ ghE, const float* __restrict__ mask, float mthr, long long n_oct,
+    const int* __restrict__ pcell, MT<float> m, float ih2, float* __restrict__ rc,
+    float* __restrict__ uc, float* __restrict__ Ec, float* __restrict__ ec) {
+  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (o >= n_oct) return;
+  float su = 0.f, sr = 0.f;
+  for (int ch = 0; ch < 8; ++ch) {
+    const long long c = 8 * o + ch;
+    su += u[c];
+    if (!mask || mask[c] > mthr) {
+      NB<float> nb[6];
+#pragma unroll
+      for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
+      const JR J = jrow(u[c], E[c], nb, m, ih2);
+      float Je = J.diag * e[c];
+#pragma unroll
+      for (int d = 0; d < 6; ++d) Je = fmaf(J.off[d], onb_e(e, nbr, o, ch, d), Je);
+      sr += r[c] - Je;
+    }
+  }
+  const int p = pcell[o];
+  const float um = 0.125f * su;
+  uc[p] = um;
+  Ec[p] = __expf(um);
+  rc[p] = 0.125f * sr;
+  ec[p] = 0.f;
+}
+
+// e += P(e_c) on relaxed cells (linear reconstruction from the parent)
+__global__ void __launch_bounds__(BS) k_olin_prolong(long long ncell, const int* __restrict__ pcell,
+                                                     const int* __restrict__ pnbr,
+                                                     const float* __restrict__ ec,
+                                                     const float* __restrict__ mask, float mthr,
+                                                     int linear, float* __restrict__ e) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  if (mask && !(mask[c] > mthr)) return;
+  const long long o = c >> 3;
+  const int ch = (int)(c & 7);
+  float v = ec[pcell[o]];
+  if (linear) {
+    for (int ax = 0; ax < 3; ++ax) {
+      const int pm = pnbr[6 * o + 2 * ax], pp = pnbr[6 * o + 2 * ax + 1];
+      if (pm < 0 || pp < 0) continue;
+      v += (((ch >> (2 - ax)) & 1) ? 0.125f : -0.125f) * (ec[pp] - ec[pm]);
+    }
+  }
+  e[c] += v;
+}
+
+__global__ void __launch_bounds__(BS) k_dlin_sweep(float* __restrict__ e, const float* __restrict__ r,
+                                                   const float* __restrict__ u,
+                                                   const float* __restrict__ E, int lg, int colour,
+                                                   MT<float> m, float ih2,
+                                                   const float* __restrict__ mask, float mthr) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int N = 1 << lg, M = N - 1;
+  if (t >= (1LL << (3 * lg - 1))) return;
+  const int k2 = (int)(t & ((N >> 1) - 1));
+  const long long rr = t >> (lg - 1);
+  const int j = (int)(rr & M), i = (int)(rr >> lg);
+  const int k = 2 * k2 + ((i + j + colour) & 1);
+  const long long c = cidx(i, j, k, lg);
+  if (mask && !(mask[c] > mthr)) return;
+  NB<float> nb[6];
+  dnb(u, E, i, j, k, lg, nb);
+  const JR J = jrow(u[c], E[c], nb, m, ih2);
+  NB<float> en[6];
+  dnb(e, e, i, j, k, lg, en);
+  float acc = r[c];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) acc = fmaf(-J.off[d], en[d].u, acc);
+  e[c] = __fdividef(acc, J.diag);
+}
+
+__global__ void __launch_bounds__(BS) k_dlin_restrict(const float* __restrict__ e,
+                                                      const float* __restrict__ r,
+                                                      const float* __restrict__ u,
+                                                      const float* __restrict__ E, int lgf,
+                                                      float* __restrict__ rc, float* __restrict__ uc,
+                                                      float* __restrict__ Ec, float* __restrict__ ec,
+                                                      MT<float> m, float ih2,
+                                                      const float* __restrict__ mask, float mthr) {
+  const int lgc = lgf - 1, Nc = 1 << lgc;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (1LL << (3 * lgc))) return;
+  const int K = (int)(t & (Nc - 1)), J0 = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
+  float su = 0.f, sr = 0.f;
+  for (int q = 0; q < 8; ++q) {
+    const int i = 2 * I + (q >> 2), j = 2 * J0 + ((q >> 1) & 1), k = 2 * K + (q & 1);
+    const long long c = cidx(i, j, k, lgf);
+    su += u[c];
+    if (!mask || mask[c] > mthr) {
+      NB<float> nb[6], en[6];
+      dnb(u, E, i, j, k, lgf, nb);
+      dnb(e, e, i, j, k, lgf, en);
+      const JR J = jrow(u[c], E[c], nb, m, ih2);
+      float Je = J.diag * e[c];
+#pragma unroll
+      for (int d = 0; d < 6; ++d) Je = fmaf(J.off[d], en[d].u, Je);
+      sr += r[c] - Je;
+    }
+  }
+  const float um = 0.125f * su;
+  uc[t] = um;
+  Ec[t] = __expf(um);
+  rc[t] = 0.125f * sr;
+  ec[t] = 0.f;
+}
+
+__global__ void __launch_bounds__(BS) k_dlin_prolong(float* __restrict__ e, const float* __restrict__ ec,
+                                                     int lgf, int linear,
+                                                     const float* __restrict__ mask, float mthr) {
+  const int N = 1 << lgf, lgc = lgf - 1, Mc = (N >> 1) - 1;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (1LL << (3 * lgf))) return;
+  if (mask && !(mask[t] > mthr)) return;
+  const int k = (int)(t & (N - 1)), j = (int)((t >> lgf) & (N - 1)), i = (int)(t >> (2 * lgf));
+  const int I = i >> 1, J = j >> 1, K = k >> 1;
+  auto cv = [&](int a, int b, int c) { return ec[cidx(a & Mc, b & Mc, c & Mc, lgc)]; };
+  float v = cv(I, J, K);
+  if (linear) {
+    v += ((i & 1) ? 0.125f : -0.125f) * (cv(I + 1, J, K) - cv(I - 1, J, K));
+    v += ((j & 1) ? 0.125f : -0.125f) * (cv(I, J + 1, K) - cv(I, J - 1, K));
+    v += ((k & 1) ? 0.125f : -0.125f) * (cv(I, J, K + 1) - cv(I, J, K - 1));
+  }
+  e[t] += v;
+}
+
+__global__ void __launch_bounds__(64) k_dlin_coarse(float* __restrict__ eg, const float* __restrict__ rg,
+                                                    const float* __restrict__ ug,
+                                                    const float* __restrict__ Eg, MT<float> m,
+                                                    float ih2, int sweeps,
+                                                    const float* __restrict__ mask, float mthr) {
+  __shared__ float e[64];
+  const int t = threadIdx.x;
+  const bool active = !mask || mask[t] > mthr;
+  const int i = t >> 4, j = (t >> 2) & 3, k = t & 3, colour = (i + j + k) & 1;
+  const int q[6] = {(((i + 3) & 3) << 4) | (j << 2) | k, (((i + 1) & 3) << 4) | (j << 2) | k,
+                    (i << 4) | (((j + 3) & 3) << 2) | k, (i << 4) | (((j + 1) & 3) << 2) | k,
+                    (i << 4) | (j << 2) | ((k + 3) & 3), (i << 4) | (j << 2) | ((k + 1) & 3)};
+  NB<float> nb[6];
+  for (int d = 0; d < 6; ++d) nb[d] = NB<float>{ug[q[d]], Eg[q[d]]};
+  const JR J = jrow(ug[t], Eg[t], nb, m, ih2);
+  const float rc = rg[t];
+  e[t] = eg[t];
+  __syncthreads();
+  for (int s = 0; s < sweeps; ++s)
+    for (int col = 0; col < 2; ++col) {
+      if (colour == col && active) {
+        float acc = rc;
+        for (int d = 0; d < 6; ++d) acc = fmaf(-J.off[d], e[q[d]], acc);
+        e[t] = acc / J.diag;
+      }
+      __syncthreads();
+    }
+  eg[t] = e[t];
+}
+
+// w += clamp(e), wE = e^w on level L (FP64)
+__global__ void k_apply_lin(double* __restrict__ w, double* __restrict__ wE,
+                            const float* __restrict__ e, long long n, double cap) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = w[i] + fmin(fmax((double)e[i], -cap), cap);
+  w[i] = v;
+  wE[i] = exp(v);
+}
+
+__global__ void k_zero32(float* __restrict__ x, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) x[i] = 0.f;
+}
+
 // ---- set-up kernels --------------------------------------------------------
 // initial guess of level L from the converged level L-1 (linear
 // reconstruction with the parent's neighbours), FP64 and FP32 copies
@@ -721,6 +1008,117 @@ mgfr_status count_relaxed(mgfr_ctx* c, AmrWork* A, const float* mask, long long 
   return MGFR_OK;
 }
 
+
+// ---- linear masked V-cycle (phase B of the mixed form) -------------------------
+// level arrays: u = w32 (linearisation point), E = wE32, r = wf32, e = wold32;
+// dense levels below the base: u = u32, E = e32, r = r32, e = uold32.
+void lin_relax(SolveCtx& S, int l, int sweeps) {
+  mgfr_ctx* c = S.c;
+  AmrLevel& L = S.A->L[l];
+  const MT<float> m = mt<float>(S.m);
+  for (int s = 0; s < sweeps; ++s) {
+    for (int col = 0; col < 2; ++col) {
+      if (l >= 1)
+        k_olin_sweep<<<nblocks(4 * L.n_oct, BS), BS, 0, c->s>>>(
+            L.wold32, L.wf32, L.w32, L.wE32, L.nbr, L.ghost32, L.ghostE32,
+            l == S.L ? nullptr : L.mask, S.mthr, L.n_oct, col, m, (float)L.ih2);
+      else
+        k_dlin_sweep<<<nblocks(L.ncell / 2, BS), BS, 0, c->s>>>(L.wold32, L.wf32, L.w32, L.wE32,
+                                                               L.lgN, col, m, (float)L.ih2,
+                                                               L.mask, S.mthr);
+      c->launches += 1;
+    }
+  }
+}
+
+void lin_vcycle_dense(SolveCtx& S, int k) {
+  mgfr_ctx* c = S.c;
+  const mgfr_config& g = c->cfg;
+  DenseHier& H = c->dh;
+  DenseLevel& F = H.L[k];
+  const float* mk = S.A->dmask[k];
+  const MT<float> m = mt<float>(S.m);
+  if (F.N <= 4) {
+    k_dlin_coarse<<<1, 64, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, m, (float)F.ih2, 20, mk, S.mthr);
+    c->launches += 1;
+    return;
+  }
+  for (int s = 0; s < g.n_pre; ++s)
+    for (int col = 0; col < 2; ++col) {
+      k_dlin_sweep<<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, F.lg, col,
+                                                         m, (float)F.ih2, mk, S.mthr);
+      c->launches += 1;
+    }
+  DenseLevel& C = H.L[k + 1];
+  k_dlin_restrict<<<nblocks(C.n, BS), BS, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, F.lg, C.r32,
+                                                     C.u32, C.e32, C.uold32, m, (float)F.ih2, mk,
+                                                     S.mthr);
+  c->launches += 1;
+  lin_vcycle_dense(S, k + 1);
+  k_dlin_prolong<<<nblocks(F.n, BS), BS, 0, c->s>>>(F.uold32, C.uold32, F.lg, g.prolong_linear, mk,
+                                                    S.mthr);
+  c->launches += 1;
+  for (int s = 0; s < g.n_post; ++s)
+    for (int col = 0; col < 2; ++col) {
+      k_dlin_sweep<<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, F.lg, col,
+                                                         m, (float)F.ih2, mk, S.mthr);
+      c->launches += 1;
+    }
+}
+
+void lin_vcycle_tree(SolveCtx& S, int l) {
+  mgfr_ctx* c = S.c;
+  AmrWork* A = S.A;
+  const mgfr_config& g = c->cfg;
+  const MT<float> m = mt<float>(S.m);
+  AmrLevel& F = A->L[l];
+  lin_relax(S, l, g.n_pre);
+  S.updates += (long long)g.n_pre * F.relaxed;
+  const float* fmask = l == S.L ? nullptr : F.mask;
+  if (l >= 1) {
+    AmrLevel& P = A->L[l - 1];
+    k_olin_restrict<<<nblocks(F.n_oct, BS), BS, 0, c->s>>>(
+        F.wold32, F.wf32, F.w32, F.wE32, F.nbr, F.ghost32, F.ghostE32, fmask, S.mthr, F.n_oct,
+        F.pcell, m, (float)F.ih2, P.wf32, P.w32, P.wE32, P.wold32);
+    c->launches += 1;
+    lin_vcycle_tree(S, l - 1);
+    k_olin_prolong<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.ncell, F.pcell, F.pnbr, P.wold32, fmask,
+                                                          S.mthr, g.prolong_linear, F.wold32);
+    c->launches += 1;
+  } else {
+    DenseHier& H = c->dh;
+    DenseLevel& C = H.L[1];
+    k_dlin_restrict<<<nblocks(C.n, BS), BS, 0, c->s>>>(F.wold32, F.wf32, F.w32, F.wE32, F.lgN,
+                                                       C.r32, C.u32, C.e32, C.uold32, m,
+                                                       (float)F.ih2, F.mask, S.mthr);
+    c->launches += 1;
+    lin_vcycle_dense(S, 1);
+    k_dlin_prolong<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.wold32, C.uold32, F.lgN,
+                                                          g.prolong_linear, F.mask, S.mthr);
+    c->launches += 1;
+  }
+  lin_relax(S, l, g.n_post);
+  S.updates += (long long)g.n_post * F.relaxed;
+}
+
+// FP64 residual of level L with the linear system set up for phase B
+mgfr_status lin_resid(SolveCtx& S, double* hs) {
+  mgfr_ctx* c = S.c;
+  AmrLevel& L = S.A->L[S.L];
+  DenseHier& H = c->dh;
+  const int nparts = (int)std::min<long long>(H.nparts / 2, nblocks(L.ncell, BS));
+  if (c->capturing >= 0) prof_begin(c, 2, L.ncell);
+  k_oresid_lin<<<nparts, BS, 0, c->s>>>(L.w, L.wE, L.wf, L.nbr, L.ghost, L.ghostE, L.ncell,
+                                        mt<double>(S.m), L.ih2, L.wf32, L.w32, L.wE32, L.wold32,
+                                        H.partials);
+  if (c->capturing >= 0) prof_end(c);
+  k_finish3<<<1, 256, 0, c->s>>>(H.partials, nparts, H.scal + 8);
+  c->launches += 2;
+  MG_CK(c, cudaMemcpyAsync(hs, H.scal + 8, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+  MG_CK(c, cudaStreamSynchronize(c->s));
+  return MGFR_OK;
+}
+
 #define TRY(x)                    \
   do {                            \
     mgfr_status s_ = (x);         \
@@ -809,8 +1207,34 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
     }
     k_f2d_exp<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.w32, F.w, F.wE, F.ncell);
     c->launches += 1;
-    TRY(level_norm<double>(S, hs));
+    // phase B: FP64 residual, FP32 linear masked V-cycle on J(u) e = r, u += e
+    for (int l = Lv - 1; l >= 0; --l) {
+      AmrLevel& P = A->L[l];
+      k_zero32<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(P.wold32, P.ncell);
+      c->launches += 1;
+    }
+    for (int k = 1; k < H.nlev; ++k) {
+      k_zero32<<<nblocks(H.L[k].n, BS), BS, 0, c->s>>>(H.L[k].uold32, H.L[k].n);
+      c->launches += 1;
+    }
+    c->capturing = 3;
+    TRY(lin_resid(S, hs));
+    c->capturing = -1;
     r = std::sqrt(hs[0]);
+    double rprev = r;
+    while (r > target && it < g.max_vcycles) {
+      c->capturing = 3;
+      for (int q = 0; q < g.mixed_inner; ++q) lin_vcycle_tree(S, Lv);
+      k_apply_lin<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.w, F.wE, F.wold32, F.ncell, g.step_cap);
+      c->launches += 1;
+      TRY(lin_resid(S, hs));
+      c->capturing = -1;
+      prof_collect(c, 3, st);
+      r = std::sqrt(hs[0]);
+      ++it;
+      if (!std::isfinite(r) || r > rprev) break;  // finish with FP64 V-cycles below
+      rprev = r;
+    }
   }
   while (r > target && it < g.max_vcycles) {
     TRY(run_vcycle<double>(S, st, hs));
