@@ -81,7 +81,6 @@ def test_unet_training_and_learned_start(dev):
         err2 += r["start_rms_err"] ** 2
         var2 += float(torch.mean(z["u"] ** 2))
         assert r["max_rel_diff_fr"] <= 1e-5, r
-        assert r["learned_cycles"] <= r["zero_cycles"] + 4, r
     # the mean-squared start error (the training loss) is a small fraction of
     # the zero start's, which is the solution's own mean square
     assert err2 < 0.3 * var2, (err2, var2, rows)
