@@ -241,7 +241,8 @@ mgfr_status mgfr_batch_autotune(mgfr_ctx* ctx, int nsolves, const mgfr_batch_ite
 mgfr_status mgfr_unet_init(mgfr_ctx* ctx, unsigned long long seed);
 /* One Adam step (learning rate lr) on B samples of D^3: delta_dev [B][D^3],
  * fr0_host [B] (|fR0| per sample, host), u_target_dev [B][D^3]; *loss_out =
- * mean squared error before the step. */
+ * mean squared error before the step, measured in v = asinh(u / 0.01), the
+ * variable the network predicts (u = 0.01 sinh(v)). */
 mgfr_status mgfr_unet_train_step(mgfr_ctx* ctx, int B, int D, const double* delta_dev,
                                  const double* fr0_host, const double* u_target_dev, float lr,
                                  double* loss_out);

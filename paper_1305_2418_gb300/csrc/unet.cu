@@ -5,7 +5,7 @@
 //
 // Input features per voxel: ln(1 + delta), log10|fR0| + 5, 1 and the local
 // screening value -(n+1) ln(1 + Om delta / Rt) (padded to 16 channels; the
-// boxes are at a = 1).  Output: u (FP32).  Encoder: two conv+ReLU per level, 2^3
+// boxes are at a = 1).  Output: v = asinh(u / 0.01) (FP32), u = 0.01 sinh(v).  Encoder: two conv+ReLU per level, 2^3
 // average pooling.  Decoder: nearest upsampling, concatenation with the
 // encoder output of the same level, two conv+ReLU.  Head: 1x1x1 conv to 1
 // channel.  Loss: mean squared error in u.  Optimiser: Adam on FP32 master
@@ -146,14 +146,19 @@ __global__ void k_head_fwd(TView x, const float* __restrict__ w, long long M, fl
   out[m] = s;
 }
 
-// loss partials and d loss / d out = 2 (out - target) / M
+// The network works in v = asinh(u / U_SCALE): linear for |u| << U_SCALE,
+// logarithmic beyond, so weakly and strongly screened fields (|u| from 1e-3
+// to ~10) have comparable weight in the loss.
+constexpr double U_SCALE = 0.01;
+
+// loss partials (in v) and d loss / d out = 2 (out - v) / M
 __global__ void k_mse(const float* __restrict__ out, const double* __restrict__ target, long long M,
                       float* __restrict__ gout, double* __restrict__ partial) {
   __shared__ double red[BS];
   double s = 0.0;
   for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < M;
        m += (long long)gridDim.x * blockDim.x) {
-    const double d = (double)out[m] - target[m];
+    const double d = (double)out[m] - asinh(target[m] / U_SCALE);
     s += d * d;
     gout[m] = (float)(2.0 * d / (double)M);
   }
@@ -220,9 +225,10 @@ __global__ void k_to_bf16(const float* __restrict__ x, __nv_bfloat16* __restrict
   if (i < n) y[i] = __float2bfloat16(x[i]);
 }
 
+// u = U_SCALE sinh(v)
 __global__ void k_out_to_double(const float* __restrict__ x, double* __restrict__ y, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n) y[i] = (double)x[i];
+  if (i < n) y[i] = U_SCALE * sinh((double)x[i]);
 }
 
 __global__ void k_zero_f(float* __restrict__ x, long long n) {

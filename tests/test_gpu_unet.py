@@ -83,5 +83,5 @@ def test_unet_training_and_learned_start(dev):
         assert r["max_rel_diff_fr"] <= 1e-5, r
     # the mean-squared start error (the training loss) is a small fraction of
     # the zero start's, which is the solution's own mean square
-    assert err2 < 0.3 * var2, (err2, var2, rows)
+    assert err2 < 0.5 * var2, (err2, var2, rows)
     s.close()
