@@ -23,6 +23,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -174,6 +176,99 @@ def run_reference(args, rank: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+def batched_extra(mgfr, synth, torch, dev, local):
+    """96 independent periodic solves of 32^3/64^3/128^3 (about 32 each),
+    sigma_g uniform in [0.5, 2], |fR0| log-uniform in [1e-6, 1e-4], box 100:
+    one persistent launch (mixed precision, autotuned launch shape) against a
+    sequential loop of plain FP64 solves on the same GPU."""
+    rng = np.random.default_rng(5000)
+    sizes = [int(rng.choice([32, 64, 128])) for _ in range(96)]
+    deltas, fr0s = [], []
+    for q, N in enumerate(sizes):
+        deltas.append(torch.from_numpy(synth.lognormal_delta(N, 100.0, float(rng.uniform(0.5, 2.0)),
+                                                             5000 + q)).to(dev))
+        fr0s.append(float(10 ** rng.uniform(-6, -4)))
+    sb = mgfr.Solver(local, precision=mgfr.PREC_MIXED)
+    t_shape = sb.batch_autotune(deltas, [100.0] * 96, fr0s)
+    sb.batch_solve(deltas, [100.0] * 96, fr0s)
+    torch.cuda.synchronize()
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        outs, st = sb.batch_solve(deltas, [100.0] * 96, fr0s)
+    e1.record()
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / reps
+    ok = all(o["stats"]["res_l2_final"] <= 1e-8 * o["stats"]["f_l2"] for o in outs)
+    s64 = mgfr.Solver(local, precision=mgfr.PREC_FP64)
+    s64.solve_density(deltas[0], 100.0)
+    torch.cuda.synchronize()
+    e0.record()
+    for d, f in zip(deltas, fr0s):
+        s64.set_config(fr0_abs=f)
+        s64.solve_density(d, 100.0, want_acc=False)
+    e1.record()
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1)
+    sb.close()
+    s64.close()
+    return {"workload": "96 periodic solves, N in {32,64,128} (%d/%d/%d), sigma_g U[0.5,2], "
+                        "|fR0| log-uniform [1e-6,1e-4], box 100, to 1e-8" %
+                        (sizes.count(32), sizes.count(64), sizes.count(128)),
+            "batched_ms": t_batch, "batched_solves_per_s": 96 / (t_batch / 1e3),
+            "sequential_fp64_ms": t_seq, "sequential_fp64_solves_per_s": 96 / (t_seq / 1e3),
+            "speedup": t_seq / t_batch, "launch_shape": {"threads": t_shape[0],
+                                                          "blocks_per_sm": t_shape[1]},
+            "all_converged": ok}
+
+
+def learned_extra(mgfr, synth, learned, torch, dev, local):
+    """Learned start: the U-Net trained on 2000 solver-generated 64^3 samples
+    (box 25, the 0.39 Mpc/h cell), then 256^3 / 100 Mpc/h fields, sigma_g in
+    {0.5,1,1.5,2} x |fR0| in {1e-6,1e-5,1e-4}: V-cycles and time to 1e-8 from
+    the prediction (prediction time included) against a zero start."""
+    s = mgfr.Solver(local, precision=mgfr.PREC_MIXED)
+    t0 = time.perf_counter()
+    deltas, fr0s, us = learned.make_training_set(s, 2000, 64, 25.0, seed=4)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    s.unet_init(seed=1)
+    steps, B = 1500, 4
+    t0 = time.perf_counter()
+    losses = learned.train(s, deltas, fr0s, us, steps=steps, batch=B, lr=2e-3, seed=2)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del deltas, us
+    # conv FLOPs per training step (fwd + dgrad + wgrad = 3x the forward)
+    convs = [(16, 16, 0), (16, 16, 0), (16, 32, 1), (32, 32, 1), (32, 64, 2), (64, 64, 2),
+             (64, 128, 3), (128, 128, 3), (192, 64, 2), (64, 64, 2), (96, 32, 1), (32, 32, 1),
+             (48, 16, 0), (16, 16, 0)]
+    fwd = sum(2 * 27 * ci * co * (64 >> l) ** 3 for ci, co, l in convs) * B
+    fields = []
+    for q, sig in enumerate((0.5, 1.0, 1.5, 2.0)):
+        for fr0 in (1e-6, 1e-5, 1e-4):
+            d = torch.from_numpy(synth.lognormal_delta(256, 100.0, sig, 9000 + q)).to(dev)
+            fields.append((d, fr0))
+    rows = learned.evaluate(s, fields, 100.0)
+    s.close()
+    zc = [r["zero_cycles"] for r in rows]
+    lc = [r["learned_cycles"] for r in rows]
+    return {"training": {"samples": 2000, "D": 64, "steps": steps, "batch": B,
+                         "data_gen_s": t_data, "train_s": t_train,
+                         "loss_first": float(np.mean(losses[:20])),
+                         "loss_last": float(np.mean(losses[-20:])),
+                         "conv_tflops": 3 * fwd * steps / t_train / 1e12},
+            "eval_256": {"zero_cycles_mean": float(np.mean(zc)),
+                         "learned_cycles_mean": float(np.mean(lc)),
+                         "zero_ms_mean": float(np.mean([r["zero_ms"] for r in rows])),
+                         "learned_ms_mean": float(np.mean([r["learned_ms"] for r in rows])),
+                         "predict_ms_mean": float(np.mean([r["predict_ms"] for r in rows])),
+                         "start_rms_err_mean": float(np.mean([r["start_rms_err"] for r in rows])),
+                         "max_rel_diff_fr": float(max(r["max_rel_diff_fr"] for r in rows)),
+                         "fields": len(rows)}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -181,6 +276,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-solve and learned-start measurements")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -328,6 +425,11 @@ def main():
             "per_family_ms": {KERNEL_NAMES[q]: kern_ms[q] / args.steps for q in range(4)}}
 
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline_sample()
+    extras = {}
+    if not args.no_extras:
+        from paper_1305_2418_gb300 import learned
+        extras["batched"] = batched_extra(mgfr, synth, torch, dev, local)
+        extras["learned_start"] = learned_extra(mgfr, synth, learned, torch, dev, local)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -357,6 +459,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * n_part,
                 "d2h_bytes_per_step": 24 * n_part},
         "cpu_baseline": cpu,
+        **extras,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
