@@ -278,6 +278,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-solve and learned-start measurements")
+    ap.add_argument("--only-mixed", action="store_true",
+                    help="run only the timed mixed-precision steps (for profiler captures)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -316,6 +318,13 @@ def main():
         return s.solve_particles(pos if p is None else p, w["N"], w["box"], w["a"],
                                  want_fr=want_fr)
 
+    if args.only_mixed:
+        sm = solver(mgfr.PREC_MIXED, profile=0)
+        for _ in range(args.warmup + args.steps):
+            step(sm)
+        torch.cuda.synchronize()
+        sm.close()
+        return
     # ---- plain FP64 solve, time to tolerance (reported beside) ----
     s64 = solver(mgfr.PREC_FP64)
     step(s64)
