@@ -280,6 +280,9 @@ def main():
                     help="skip the batched-solve and learned-start measurements")
     ap.add_argument("--only-mixed", action="store_true",
                     help="run only the timed mixed-precision steps (for profiler captures)")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="half the particle density (nbar 0.5): a smaller hierarchy for "
+                         "full-metric profiler captures (about 3 GB on the device)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -303,7 +306,9 @@ def main():
         if world > 1:
             dist.barrier()
 
-    w = WORKLOAD
+    w = dict(WORKLOAD)
+    if args.profile_case:
+        w["nbar"] = 0.5
     delta_h = synth.lognormal_delta(w["N"], w["box"], w["sigma_g"], w["seed"])
     pos_h = synth.poisson_particles(delta_h, w["box"], w["nbar"], w["seed"])
     pos = torch.from_numpy(pos_h).to(dev)
