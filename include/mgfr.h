@@ -75,7 +75,7 @@ typedef struct {
    * below mixed_switch, then FP64 defect-correction iterations, each with
    * mixed_inner FP32 linear V-cycles on the Jacobian system.               */
   double mixed_switch; /* default 1e-5                                      */
-  int mixed_inner;     /* default 1                                         */
+  int mixed_inner;     /* default 3                                         */
   long long max_spins; /* bound on any device-side wait (default 1<<26)     */
   int profile;         /* 1: time the base-level sweep kernels with CUDA
                           events recorded around each launch (see stats)   */
@@ -114,7 +114,7 @@ typedef struct {
 
 /* Fill *cfg with the defaults above (omega_m 0.3, fr0_abs 1e-5, n 1, FP64,
  * tol 1e-8, 2+2 sweeps, 100 V-cycles, linear prolongation, step cap 2,
- * max_level 0, refine_count 8, mixed_switch 1e-5, mixed_inner 1,
+ * max_level 0, refine_count 8, mixed_switch 1e-5, mixed_inner 3,
  * mask_thres 0.99). */
 void mgfr_config_default(mgfr_config* cfg);
 
