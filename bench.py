@@ -48,11 +48,16 @@ WORKLOAD = dict(name="particles256", N=256, box=100.0, a=1.0, fr0=1e-5, sigma_g=
 #    mixed form these are FP32: read u, E (8) + f active (2) + write u, E
 #    active (4) + neighbour-oct table (24 B per oct = 3)    = 17 B per cell
 #    (FP64 form: 16 + 4 + 8 + 3 = 31 B per cell)
-ALG_BYTES = {0: 8.0, 1: 12.0, 2: 36.0, 3: 17.0}
+#  4 FP32 linear Gauss-Seidel half-sweep on the octs of the refined level:
+#    read u, E, e (12) + r active (2) + write e active (2) + neighbour table (3)
+#    = 19 B per cell
+# (Ghost faces add bytes that depend on the patch geometry; not counted.)
+ALG_BYTES = {0: 8.0, 1: 12.0, 2: 36.0, 3: 17.0, 4: 19.0}
 KERNEL_NAMES = {0: "k_sweep32 (FP32 NGS half-sweep, base level)",
                 1: "k_lin_sweep (FP32 linear GS half-sweep, base level)",
                 2: "k_resid64 (FP64 residual, base level)",
-                3: "k_osweep<float> (FP32 NGS half-sweep on the octs of the refined level)"}
+                3: "k_oct_sweep32<false> (FP32 NGS half-sweep on the octs of the refined level)",
+                4: "k_oct_sweep32<true> (FP32 linear GS half-sweep on the octs of the refined level)"}
 
 
 def peaks():
@@ -354,9 +359,9 @@ def main():
     clocks = Clocks(local)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    kern_ms = [0.0] * 4
-    kern_n = [0] * 4
-    kern_cells = [0] * 4
+    kern_ms = [0.0] * 6
+    kern_n = [0] * 6
+    kern_cells = [0] * 6
     launches = 0
     upd = 0
     e0.record()
@@ -379,7 +384,7 @@ def main():
     p0.record()
     for _ in range(args.steps):
         stp = step(sp)["stats"]
-        for q in range(4):
+        for q in range(5):
             kern_ms[q] += stp["kern_ms"][q]
             kern_n[q] += stp["kern_launches"][q]
             kern_cells[q] += stp["kern_cells"][q]
@@ -425,7 +430,7 @@ def main():
         return
 
     # ---- roofline of the dominant profiled kernel ----
-    fam = max(range(4), key=lambda q: kern_ms[q])
+    fam = max(range(5), key=lambda q: kern_ms[q])
     avg_ms = kern_ms[fam] / max(kern_n[fam], 1)
     bytes_per_launch = ALG_BYTES[fam] * kern_cells[fam] / max(kern_n[fam], 1)
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
@@ -436,7 +441,7 @@ def main():
             "alg_bytes_per_launch": bytes_per_launch,
             "kernel_share_of_step": kern_ms[fam] / ms_prof,
             "profiled_ms_per_step": ms_prof / args.steps,
-            "per_family_ms": {KERNEL_NAMES[q]: kern_ms[q] / args.steps for q in range(4)}}
+            "per_family_ms": {KERNEL_NAMES[q]: kern_ms[q] / args.steps for q in range(5)}}
 
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline_sample()
     extras = {}

@@ -104,11 +104,13 @@ typedef struct {
   /* per-kernel device time with cfg.profile = 1 (0 otherwise):
    * [0] nonlinear NGS half-sweeps on the base level (FP64 or FP32),
    * [1] FP32 linear Gauss-Seidel half-sweeps on the base level (mixed),
-   * [2] FP64 residual on the base level (mixed, phase B),
-   * [3] refined-level relaxation sweeps.                                   */
-  double kern_ms[4];
-  long long kern_launches[4];
-  long long kern_cells[4];   /* cells of the levels those launches covered   */
+   * [2] FP64 residuals of the mixed form (base and refined levels),
+   * [3] nonlinear NGS half-sweeps on the refined level being solved,
+   * [4] FP32 linear Gauss-Seidel half-sweeps on the refined level being
+   *     solved (mixed), [5] reserved.                                      */
+  double kern_ms[6];
+  long long kern_launches[6];
+  long long kern_cells[6];   /* cells of the levels those launches covered   */
   long long gpu_launches;    /* kernels this call launched (graph nodes included) */
 } mgfr_stats;
 

@@ -34,6 +34,7 @@ struct AmrLevel {
   // FP32 work arrays (mixed precision phase of the level solves)
   float *w32 = nullptr, *wE32 = nullptr, *wf32 = nullptr, *wold32 = nullptr;
   float *ghost32 = nullptr, *ghostE32 = nullptr;
+  float2* ghostUE32 = nullptr;        // [n_oct*24] interleaved (u, E) ghost pairs
   long long relaxed = 0;              // cells relaxed in the current level solve
 };
 

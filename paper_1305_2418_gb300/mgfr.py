@@ -39,8 +39,8 @@ class Stats(C.Structure):
         ("t_total_ms", C.c_double), ("t_solve_ms", C.c_double), ("n_levels", C.c_int),
         ("cells_per_level", C.c_longlong * 16), ("octs_per_level", C.c_longlong * 16),
         ("level_iters", C.c_int * 16), ("level_res", C.c_double * 16),
-        ("kern_ms", C.c_double * 4), ("kern_launches", C.c_longlong * 4),
-        ("kern_cells", C.c_longlong * 4), ("gpu_launches", C.c_longlong),
+        ("kern_ms", C.c_double * 6), ("kern_launches", C.c_longlong * 6),
+        ("kern_cells", C.c_longlong * 6), ("gpu_launches", C.c_longlong),
     ]
 
     def to_dict(self) -> dict:
