@@ -937,6 +937,37 @@ double orc_amr_residual(void* h, int l, int prolong_linear, double* r) {
 }
 
 /*
+ * r = f - L(u) at the given cells of level l only (ghost values prolonged from
+ * the level l-1 field), for spot checks of large hierarchies [Sec. 3.2-3.3].
+ */
+void orc_amr_residual_at(void* h, int l, int prolong_linear, const long long* cells,
+                         long long ncells, double* r) {
+  orc_amr* A = (orc_amr*)h;
+  amr_make_sources(A);
+  const orc_model* m = &A->model;
+  double hl = A->box / (double)lev_dim(A, l), ih2 = 1.0 / (hl * hl);
+  for (long long q = 0; q < ncells; ++q) {
+    long long c = cells[q];
+    int64_t I, J, K;
+    cell_coords(A, l, c, &I, &J, &K);
+    double uc = A->u[l][c], Ec = exp(uc), lap = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+      double un[2];
+      for (int s = 0; s < 2; ++s) {
+        int d = 2 * ax + s;
+        int64_t In = I + DIRS[d][0], Jn = J + DIRS[d][1], Kn = K + DIRS[d][2];
+        long long nb = find_cell(A, l, In, Jn, Kn);
+        un[s] = nb >= 0 ? A->u[l][nb]
+                        : prolong_from_parent(A, l, A->u[l - 1], In, Jn, Kn, prolong_linear);
+      }
+      double bm = 0.5 * (exp(un[0]) + Ec), bp = 0.5 * (exp(un[1]) + Ec);
+      lap += bm * un[0] + bp * un[1] - (bm + bp) * uc;
+    }
+    r[q] = A->f[l][c] - (lap * ih2 + m->alpha * m->Rt * (1.0 - exp(-uc / (m->n + 1))));
+  }
+}
+
+/*
  * Solve refined level l >= 1 [Sec. 3.3, steps 9-10]: initial guess and ghost
  * values prolonged from level l-1; ghosts fixed; red-black NGS until
  * ||f - L(u)||_2 <= tol ||f||_2 over the level's cells.  If init_from_parent

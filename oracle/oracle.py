@@ -67,6 +67,7 @@ def lib():
                 "orc_amr_get_u": (None, [vp, i, vp]),
                 "orc_amr_ghosts": (None, [vp, i, i, vp]),
                 "orc_amr_residual": (d, [vp, i, i, vp]),
+                "orc_amr_residual_at": (None, [vp, i, i, vp, ll, vp]),
                 "orc_amr_solve_level": (i, [vp, i, d, ll, i, d, i, vp]),
                 "orc_amr_solve": (i, [vp, d, i, ll, i, i, i, d, vp, vp]),
                 "orc_amr_level_force": (None, [vp, i, i, vp, vp]),
@@ -247,6 +248,13 @@ class AMR:
     def residual(self, l, prolong_linear=True):
         r = np.empty(self.ncell(l))
         lib().orc_amr_residual(self.h, l, int(prolong_linear), _p(r))
+        return r
+
+    def residual_at(self, l, cells, prolong_linear=True):
+        """f - L(u) at the given cells of level l (current u of levels l, l-1)."""
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        r = np.empty(len(cells))
+        lib().orc_amr_residual_at(self.h, l, int(prolong_linear), _p(cells), len(cells), _p(r))
         return r
 
     def solve_level(self, l, tol=1e-8, max_sweeps=200000, prolong_linear=True, step_cap=2.0,
