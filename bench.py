@@ -300,6 +300,7 @@ def main():
     import torch
     import torch.distributed as dist
     from paper_1305_2418_gb300 import build, mgfr, synth
+    from paper_1305_2418_gb300 import dist as D
 
     build.build()
     torch.cuda.set_device(local)
@@ -418,10 +419,7 @@ def main():
         e2e_upd += r["stats"]["cell_updates"] + r["stats"]["linear_updates"]
     f1.record()
     torch.cuda.synchronize()
-    te = torch.tensor([f0.elapsed_time(f1)], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * e2e_upd / (float(te.item()) / 1e3)
+    e2e_value, _ = D.whole_job_rate(e2e_upd, f0.elapsed_time(f1), dev)
     sm.close()
 
     if rank != 0:
