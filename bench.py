@@ -393,11 +393,7 @@ def main():
     torch.cuda.synchronize()
     ms_prof = p0.elapsed_time(p1)
     sp.close()
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * upd / (ms_max / 1e3)
+    value, ms_max = D.whole_job_rate(upd, ms, dev)
     last = st
 
     # ---- end to end through the public API: host buffers, copies timed ----
