@@ -211,10 +211,65 @@ __device__ __forceinline__ void touch(int lev, long long c, double w, LevelPtrs&
 
 struct StackEnt {
   double lo[3], hi[3];  // interval in level-`l` units
+  double scale;         // level-l unit volume as a fraction of the particle's cube
   long long c;          // refined cell index at level l
   int l;
   int pad;
 };
+
+// Split a piece [lo, hi] (level-l units, inside refined cell c of level l)
+// among the daughters: per axis the two daughters' overlap lengths, then the
+// 8 products.  Daughters that are refined again are split the same way one
+// more level down; deeper pieces go to the explicit stack.
+template <bool GATHER>
+__device__ __forceinline__ void split_down(const TreeView& T, int l, long long c, const double* lo,
+                                           const double* hi, double scale, LevelPtrs& D,
+                                           const GatherPtrs& G, double* out, StackEnt* st,
+                                           int& sp, unsigned long long* err, bool allow_deeper) {
+  const int o = T.son[l][c];
+  const int lc = l + 1;
+  double len[3][2], clo[3][2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double base = 2.0 * floor(lo[a]);
+    const double l2 = 2.0 * lo[a], h2 = 2.0 * hi[a];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const double c0 = base + b;
+      const double x0 = fmax(l2, c0), x1 = fmin(h2, c0 + 1.0);
+      clo[a][b] = x0;
+      len[a][b] = x1 - x0;
+    }
+  }
+  const double sc = scale * 0.125;  // daughter-unit volume -> cube fraction
+  for (int ch = 0; ch < 8; ++ch) {
+    const int b0 = (ch >> 2) & 1, b1 = (ch >> 1) & 1, b2 = ch & 1;
+    if (!(len[0][b0] > 0.0) || !(len[1][b1] > 0.0) || !(len[2][b2] > 0.0)) continue;
+    const long long cc = 8LL * o + ch;
+    const bool ref = lc + 1 < T.nlev && T.son[lc][cc] >= 0;
+    if (!ref) {
+      touch<GATHER>(lc, cc, len[0][b0] * len[1][b1] * len[2][b2] * sc, D, G, out);
+      continue;
+    }
+    const double nlo[3] = {clo[0][b0], clo[1][b1], clo[2][b2]};
+    const double nhi[3] = {clo[0][b0] + len[0][b0], clo[1][b1] + len[1][b1],
+                           clo[2][b2] + len[2][b2]};
+    if (allow_deeper) {
+      split_down<GATHER>(T, lc, cc, nlo, nhi, sc, D, G, out, st, sp, err, false);
+    } else if (sp < 48) {
+      StackEnt& n = st[sp++];
+      for (int a = 0; a < 3; ++a) {
+        n.lo[a] = nlo[a];
+        n.hi[a] = nhi[a];
+      }
+      n.c = cc;
+      n.l = lc;
+      n.scale = sc;
+    } else {
+      atomicOr(err, 1ULL);
+    }
+  }
+}
 
 template <bool GATHER>
 __device__ void visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, const GatherPtrs& G,
@@ -254,63 +309,20 @@ __device__ void visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
       touch<GATHER>(lev, c, w, D, G, out);
       continue;
     }
-    if (sp >= 48) {
-      atomicOr(err, 1ULL);
-      continue;
-    }
-    StackEnt& e = st[sp++];
     const long long P[3] = {i0[0] + ba, i0[1] + bb, i0[2] + bc};
     const int bits[3] = {ba, bb, bc};
+    double lo[3], hi[3];
     for (int a = 0; a < 3; ++a) {
       // the cube is [tl, tl + 1] in level-lam units; clip to the cell [P, P+1]
-      e.lo[a] = bits[a] ? (double)P[a] : tl[a];
-      e.hi[a] = bits[a] ? tl[a] + 1.0 : (double)P[a] + 1.0;
+      lo[a] = bits[a] ? (double)P[a] : tl[a];
+      hi[a] = bits[a] ? tl[a] + 1.0 : (double)P[a] + 1.0;
     }
-    e.c = c;
-    e.l = lam;
+    split_down<GATHER>(T, lam, c, lo, hi, 1.0, D, G, out, st, sp, err, true);
   }
-  // split refined pieces among daughters (volumes in level-lam units)
+  // pieces refined three or more levels below the particle's leaf
   while (sp > 0) {
     const StackEnt e = st[--sp];
-    const int o = T.son[e.l][e.c];
-    const int lc = e.l + 1;
-    const double scale = ldexp(1.0, -3 * (lc - lam));  // daughter-unit volume -> cube fraction
-    long long I0[3];
-    double lo2[3], hi2[3];
-    for (int a = 0; a < 3; ++a) {
-      lo2[a] = 2.0 * e.lo[a];
-      hi2[a] = 2.0 * e.hi[a];
-      I0[a] = 2 * (long long)floor(e.lo[a] + 0.0);  // parent coordinate * 2
-    }
-    // parent cell coordinate: floor of the interval start (interval lies in it)
-    for (int ch = 0; ch < 8; ++ch) {
-      const int b[3] = {(ch >> 2) & 1, (ch >> 1) & 1, ch & 1};
-      double lo[3], hi[3];
-      bool empty = false;
-      for (int a = 0; a < 3; ++a) {
-        const double c0 = (double)(I0[a] + b[a]);
-        lo[a] = fmax(lo2[a], c0);
-        hi[a] = fmin(hi2[a], c0 + 1.0);
-        if (!(hi[a] > lo[a])) empty = true;
-      }
-      if (empty) continue;
-      const long long cc = 8LL * o + ch;
-      const bool ref = lc + 1 < T.nlev && T.son[lc][cc] >= 0;
-      if (!ref) {
-        const double vol = (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]) * scale;
-        touch<GATHER>(lc, cc, vol, D, G, out);
-      } else if (sp < 48) {
-        StackEnt& n = st[sp++];
-        for (int a = 0; a < 3; ++a) {
-          n.lo[a] = lo[a];
-          n.hi[a] = hi[a];
-        }
-        n.c = cc;
-        n.l = lc;
-      } else {
-        atomicOr(err, 1ULL);
-      }
-    }
+    split_down<GATHER>(T, e.l, e.c, e.lo, e.hi, e.scale, D, G, out, st, sp, err, false);
   }
 }
 
