@@ -219,16 +219,22 @@ struct StackEnt {
 
 // Split a piece [lo, hi] (level-l units, inside refined cell c of level l)
 // among the daughters: per axis the two daughters' overlap lengths, then the
-// 8 products.  Daughters that are refined again are split the same way one
-// more level down; deeper pieces go to the explicit stack.
-template <bool GATHER>
+// 8 products.  A daughter that is itself refined is handed to `deeper`
+// (DEPTH = 2: split again one level down in registers; DEPTH = 1: pushed on
+// the explicit stack).  No recursion, so the stack frame size is static.
+template <bool GATHER, int DEPTH>
 __device__ __forceinline__ void split_down(const TreeView& T, int l, long long c, const double* lo,
                                            const double* hi, double scale, LevelPtrs& D,
                                            const GatherPtrs& G, double* out, StackEnt* st,
-                                           int& sp, unsigned long long* err, bool allow_deeper) {
-  const int o = T.son[l][c];
-  const int lc = l + 1;
-  double len[3][2], clo[3][2];
+                                           int& sp, unsigned long long* err);
+
+template <bool GATHER>
+__device__ __forceinline__ void split_pieces(const TreeView& T, int l, long long c,
+                                             const double* lo, const double* hi, double scale,
+                                             double len[3][2], double clo[3][2], int& o) {
+  (void)T;
+  (void)scale;
+  o = T.son[l][c];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const double base = 2.0 * floor(lo[a]);
@@ -241,6 +247,17 @@ __device__ __forceinline__ void split_down(const TreeView& T, int l, long long c
       len[a][b] = x1 - x0;
     }
   }
+}
+
+template <bool GATHER, int DEPTH>
+__device__ __forceinline__ void split_down(const TreeView& T, int l, long long c, const double* lo,
+                                           const double* hi, double scale, LevelPtrs& D,
+                                           const GatherPtrs& G, double* out, StackEnt* st,
+                                           int& sp, unsigned long long* err) {
+  double len[3][2], clo[3][2];
+  int o;
+  split_pieces<GATHER>(T, l, c, lo, hi, scale, len, clo, o);
+  const int lc = l + 1;
   const double sc = scale * 0.125;  // daughter-unit volume -> cube fraction
   for (int ch = 0; ch < 8; ++ch) {
     const int b0 = (ch >> 2) & 1, b1 = (ch >> 1) & 1, b2 = ch & 1;
@@ -254,19 +271,21 @@ __device__ __forceinline__ void split_down(const TreeView& T, int l, long long c
     const double nlo[3] = {clo[0][b0], clo[1][b1], clo[2][b2]};
     const double nhi[3] = {clo[0][b0] + len[0][b0], clo[1][b1] + len[1][b1],
                            clo[2][b2] + len[2][b2]};
-    if (allow_deeper) {
-      split_down<GATHER>(T, lc, cc, nlo, nhi, sc, D, G, out, st, sp, err, false);
-    } else if (sp < 48) {
-      StackEnt& n = st[sp++];
-      for (int a = 0; a < 3; ++a) {
-        n.lo[a] = nlo[a];
-        n.hi[a] = nhi[a];
-      }
-      n.c = cc;
-      n.l = lc;
-      n.scale = sc;
+    if constexpr (DEPTH > 1) {
+      split_down<GATHER, DEPTH - 1>(T, lc, cc, nlo, nhi, sc, D, G, out, st, sp, err);
     } else {
-      atomicOr(err, 1ULL);
+      if (sp < 48) {
+        StackEnt& n = st[sp++];
+        for (int a = 0; a < 3; ++a) {
+          n.lo[a] = nlo[a];
+          n.hi[a] = nhi[a];
+        }
+        n.c = cc;
+        n.l = lc;
+        n.scale = sc;
+      } else {
+        atomicOr(err, 1ULL);
+      }
     }
   }
 }
@@ -317,12 +336,12 @@ __device__ void visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
       lo[a] = bits[a] ? (double)P[a] : tl[a];
       hi[a] = bits[a] ? tl[a] + 1.0 : (double)P[a] + 1.0;
     }
-    split_down<GATHER>(T, lam, c, lo, hi, 1.0, D, G, out, st, sp, err, true);
+    split_down<GATHER, 2>(T, lam, c, lo, hi, 1.0, D, G, out, st, sp, err);
   }
   // pieces refined three or more levels below the particle's leaf
   while (sp > 0) {
     const StackEnt e = st[--sp];
-    split_down<GATHER>(T, e.l, e.c, e.lo, e.hi, e.scale, D, G, out, st, sp, err, false);
+    split_down<GATHER, 1>(T, e.l, e.c, e.lo, e.hi, e.scale, D, G, out, st, sp, err);
   }
 }
 

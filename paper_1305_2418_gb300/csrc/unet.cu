@@ -231,11 +231,6 @@ __global__ void k_out_to_double(const float* __restrict__ x, double* __restrict_
   if (i < n) y[i] = U_SCALE * sinh((double)x[i]);
 }
 
-__global__ void k_zero_f(float* __restrict__ x, long long n) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n) x[i] = 0.f;
-}
-
 }  // namespace
 
 // ============================================================================
