@@ -56,8 +56,8 @@ ALG_BYTES = {0: 8.0, 1: 12.0, 2: 36.0, 3: 17.0, 4: 19.0}
 KERNEL_NAMES = {0: "k_sweep32 (FP32 NGS half-sweep, base level)",
                 1: "k_lin_sweep (FP32 linear GS half-sweep, base level)",
                 2: "k_resid64 (FP64 residual, base level)",
-                3: "k_osweep32 (FP32 NGS half-sweep on the octs of the refined level)",
-                4: "k_olin_sweep (FP32 linear GS half-sweep on the octs of the refined level)"}
+                3: "k_oct_sweep32<false> (FP32 NGS half-sweep on the octs of the refined level)",
+                4: "k_oct_sweep32<true> (FP32 linear GS half-sweep on the octs of the refined level)"}
 
 
 def peaks():

@@ -209,70 +209,65 @@ __device__ __forceinline__ void touch(int lev, long long c, double w, LevelPtrs&
   }
 }
 
+// Fixed point for the traversal: a coordinate is held as X = floor(t 2^52),
+// t in level-0 cell units (t < N0 <= 2^10, so X < 2^62).  For every level m,
+// X >> (52 - m) = floor(t 2^m) exactly (nested floors), so the cells chosen are
+// those of the floating-point definition; every overlap length is an integer,
+// exact in double, and a weight is rounded only by its two products.  All of
+// the traversal but those products runs on the integer pipes.
+constexpr int QB = 52;
+
+__device__ __forceinline__ long long qfix(double t) {
+  return (long long)__dmul_rn(t, 4503599627370496.0);  // exact scaling by 2^52, then floor
+}
+
 struct StackEnt {
-  double lo[3], hi[3];  // interval in level-`l` units
-  double scale;         // level-l unit volume as a fraction of the particle's cube
-  long long c;          // refined cell index at level l
+  long long lo[3], hi[3];  // piece [lo, hi) per axis, fixed-point units
+  long long c;             // refined cell index at level l holding the piece
   int l;
   int pad;
 };
 
-// Split a piece [lo, hi] (level-l units, inside refined cell c of level l)
-// among the daughters: per axis the two daughters' overlap lengths, then the
-// 8 products.  A daughter that is itself refined is handed to `deeper`
-// (DEPTH = 2: split again one level down in registers; DEPTH = 1: pushed on
-// the explicit stack).  No recursion, so the stack frame size is static.
+// Split the piece [lo, hi) of refined cell c at level l among its daughters:
+// per axis the daughter boundary is mid = (2P + 1) 2^(QB - l - 1) and the
+// two overlaps are [lo, min(hi, mid)) and [max(lo, mid), hi).  A daughter
+// that is refined again is split one more level in registers (DEPTH = 2) or
+// pushed on the explicit stack (DEPTH = 1).  No recursion: the stack frame
+// size is static.
 template <bool GATHER, int DEPTH>
-__device__ __forceinline__ void split_down(const TreeView& T, int l, long long c, const double* lo,
-                                           const double* hi, double scale, LevelPtrs& D,
-                                           const GatherPtrs& G, double* out, StackEnt* st,
-                                           int& sp, unsigned long long* err);
-
-template <bool GATHER>
-__device__ __forceinline__ void split_pieces(const TreeView& T, int l, long long c,
-                                             const double* lo, const double* hi, double scale,
-                                             double len[3][2], double clo[3][2], int& o) {
-  (void)T;
-  (void)scale;
-  o = T.son[l][c];
+__device__ __forceinline__ void split_q(const TreeView& T, int l, long long c, const long long* lo,
+                                        const long long* hi, double scale, LevelPtrs& D,
+                                        const GatherPtrs& G, double* out, StackEnt* st, int& sp,
+                                        unsigned long long* err) {
+  const int o = T.son[l][c];
+  const int lc = l + 1, sh = QB - lc;
+  long long clo[3][2], chi[3][2];
+  double len[3][2];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double base = 2.0 * floor(lo[a]);
-    const double l2 = 2.0 * lo[a], h2 = 2.0 * hi[a];
+    const long long mid = ((lo[a] >> sh) | 1LL) * (1LL << sh);
+    clo[a][0] = lo[a];
+    chi[a][0] = min(hi[a], mid);
+    clo[a][1] = max(lo[a], mid);
+    chi[a][1] = hi[a];
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const double c0 = base + b;
-      const double x0 = fmax(l2, c0), x1 = fmin(h2, c0 + 1.0);
-      clo[a][b] = x0;
-      len[a][b] = x1 - x0;
-    }
+    for (int b = 0; b < 2; ++b) len[a][b] = (double)(chi[a][b] - clo[a][b]);
   }
-}
-
-template <bool GATHER, int DEPTH>
-__device__ __forceinline__ void split_down(const TreeView& T, int l, long long c, const double* lo,
-                                           const double* hi, double scale, LevelPtrs& D,
-                                           const GatherPtrs& G, double* out, StackEnt* st,
-                                           int& sp, unsigned long long* err) {
-  double len[3][2], clo[3][2];
-  int o;
-  split_pieces<GATHER>(T, l, c, lo, hi, scale, len, clo, o);
-  const int lc = l + 1;
-  const double sc = scale * 0.125;  // daughter-unit volume -> cube fraction
+  len[0][0] *= scale;
+  len[0][1] *= scale;
   for (int ch = 0; ch < 8; ++ch) {
     const int b0 = (ch >> 2) & 1, b1 = (ch >> 1) & 1, b2 = ch & 1;
-    if (!(len[0][b0] > 0.0) || !(len[1][b1] > 0.0) || !(len[2][b2] > 0.0)) continue;
+    if (chi[0][b0] <= clo[0][b0] || chi[1][b1] <= clo[1][b1] || chi[2][b2] <= clo[2][b2]) continue;
     const long long cc = 8LL * o + ch;
     const bool ref = lc + 1 < T.nlev && T.son[lc][cc] >= 0;
     if (!ref) {
-      touch<GATHER>(lc, cc, len[0][b0] * len[1][b1] * len[2][b2] * sc, D, G, out);
+      touch<GATHER>(lc, cc, len[0][b0] * len[1][b1] * len[2][b2], D, G, out);
       continue;
     }
-    const double nlo[3] = {clo[0][b0], clo[1][b1], clo[2][b2]};
-    const double nhi[3] = {clo[0][b0] + len[0][b0], clo[1][b1] + len[1][b1],
-                           clo[2][b2] + len[2][b2]};
+    const long long nlo[3] = {clo[0][b0], clo[1][b1], clo[2][b2]};
+    const long long nhi[3] = {chi[0][b0], chi[1][b1], chi[2][b2]};
     if constexpr (DEPTH > 1) {
-      split_down<GATHER, DEPTH - 1>(T, lc, cc, nlo, nhi, sc, D, G, out, st, sp, err);
+      split_q<GATHER, DEPTH - 1>(T, lc, cc, nlo, nhi, scale, D, G, out, st, sp, err);
     } else {
       if (sp < 48) {
         StackEnt& n = st[sp++];
@@ -282,7 +277,6 @@ __device__ __forceinline__ void split_down(const TreeView& T, int l, long long c
         }
         n.c = cc;
         n.l = lc;
-        n.scale = sc;
       } else {
         atomicOr(err, 1ULL);
       }
@@ -293,55 +287,70 @@ __device__ __forceinline__ void split_down(const TreeView& T, int l, long long c
 template <bool GATHER>
 __device__ void visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, const GatherPtrs& G,
                                double* out, unsigned long long* err) {
-  // leaf level of the particle
-  int lam = 0;
-  {
-    long long c = (((long long)floor(t.x) << T.lg0) + (long long)floor(t.y) << T.lg0) +
-                  (long long)floor(t.z);
-    for (int m = 1; m < T.nlev; ++m) {
-      const int o = T.son[m - 1][c];
-      if (o < 0) break;
-      const long long I = (long long)floor(ldexp(t.x, m)), J = (long long)floor(ldexp(t.y, m)),
-                      K = (long long)floor(ldexp(t.z, m));
-      c = 8LL * o + ((I & 1) << 2) + ((J & 1) << 1) + (K & 1);
-      lam = m;
-    }
+  const long long X[3] = {qfix(t.x), qfix(t.y), qfix(t.z)};
+  // leaf level lam of the particle and the oct holding its leaf cell
+  int lam = 0, own = -1;
+  long long c = ((((X[0] >> QB) << T.lg0) + (X[1] >> QB)) << T.lg0) + (X[2] >> QB);
+  for (int m = 1; m < T.nlev; ++m) {
+    const int o = T.son[m - 1][c];
+    if (o < 0) break;
+    const int sh = QB - m;
+    c = 8LL * o + (((X[0] >> sh) & 1) << 2) + (((X[1] >> sh) & 1) << 1) + ((X[2] >> sh) & 1);
+    lam = m;
+    own = o;
   }
-  const double tl[3] = {ldexp(t.x, lam) - 0.5, ldexp(t.y, lam) - 0.5, ldexp(t.z, lam) - 0.5};
-  long long i0[3];
-  double w1[3];
+  // the cube: side one level-lam cell, centred on the particle: [cl, cl + 2^F)
+  const int F = QB - lam;
+  const long long one = 1LL << F;
+  long long cl[3], i0[3], edge[3];
+  double Lw[3][2];
+  // 2^(-3F): fixed-point volume -> fraction of the cube (a normal double)
+  const double scale = __longlong_as_double((long long)(1023 - 3 * F) << 52);
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
-    i0[a] = (long long)floor(tl[a]);
-    w1[a] = tl[a] - (double)i0[a];
+    cl[a] = X[a] - (one >> 1);
+    i0[a] = cl[a] >> F;
+    edge[a] = (i0[a] + 1) * one;  // boundary between the two cells the cube spans
+    Lw[a][0] = (double)(edge[a] - cl[a]);
+    Lw[a][1] = (double)(cl[a] + one - edge[a]);
   }
+  Lw[0][0] *= scale;
+  Lw[0][1] *= scale;
   StackEnt st[48];
   int sp = 0;
   for (int q = 0; q < 8; ++q) {
-    const int ba = (q >> 2) & 1, bb = (q >> 1) & 1, bc = q & 1;
-    const double w = (ba ? w1[0] : 1.0 - w1[0]) * (bb ? w1[1] : 1.0 - w1[1]) *
-                     (bc ? w1[2] : 1.0 - w1[2]);
-    if (!(w > 0.0)) continue;
+    const int bits[3] = {(q >> 2) & 1, (q >> 1) & 1, q & 1};
+    if ((bits[0] && edge[0] == cl[0] + one) || (bits[1] && edge[1] == cl[1] + one) ||
+        (bits[2] && edge[2] == cl[2] + one))
+      continue;  // zero-width piece
+    const long long K[3] = {i0[0] + bits[0], i0[1] + bits[1], i0[2] + bits[2]};
     int lev;
-    const long long c = find_cell(T, lam, i0[0] + ba, i0[1] + bb, i0[2] + bc, &lev);
-    const bool refined = lev == lam && lam + 1 < T.nlev && T.son[lam][c] >= 0;
+    long long cq;
+    if (lam > 0 && (K[0] >> 1) == (X[0] >> (F + 1)) && (K[1] >> 1) == (X[1] >> (F + 1)) &&
+        (K[2] >> 1) == (X[2] >> (F + 1))) {
+      // same oct as the particle's leaf cell
+      cq = 8LL * own + ((K[0] & 1) << 2) + ((K[1] & 1) << 1) + (K[2] & 1);
+      lev = lam;
+    } else {
+      cq = find_cell(T, lam, K[0], K[1], K[2], &lev);
+    }
+    const bool refined = lev == lam && lam + 1 < T.nlev && T.son[lam][cq] >= 0;
     if (!refined) {
-      touch<GATHER>(lev, c, w, D, G, out);
+      touch<GATHER>(lev, cq, Lw[0][bits[0]] * Lw[1][bits[1]] * Lw[2][bits[2]], D, G, out);
       continue;
     }
-    const long long P[3] = {i0[0] + ba, i0[1] + bb, i0[2] + bc};
-    const int bits[3] = {ba, bb, bc};
-    double lo[3], hi[3];
+    long long lo[3], hi[3];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-      // the cube is [tl, tl + 1] in level-lam units; clip to the cell [P, P+1]
-      lo[a] = bits[a] ? (double)P[a] : tl[a];
-      hi[a] = bits[a] ? tl[a] + 1.0 : (double)P[a] + 1.0;
+      lo[a] = bits[a] ? edge[a] : cl[a];
+      hi[a] = bits[a] ? cl[a] + one : edge[a];
     }
-    split_down<GATHER, 2>(T, lam, c, lo, hi, 1.0, D, G, out, st, sp, err);
+    split_q<GATHER, 2>(T, lam, cq, lo, hi, scale, D, G, out, st, sp, err);
   }
   // pieces refined three or more levels below the particle's leaf
   while (sp > 0) {
     const StackEnt e = st[--sp];
-    split_down<GATHER, 1>(T, e.l, e.c, e.lo, e.hi, e.scale, D, G, out, st, sp, err);
+    split_q<GATHER, 1>(T, e.l, e.c, e.lo, e.hi, scale, D, G, out, st, sp, err);
   }
 }
 

@@ -76,29 +76,6 @@ __device__ __forceinline__ NB<T> onb(const T* __restrict__ u, const T* __restric
   return NB<T>{gh[g], ghE[g]};
 }
 
-// FP32 variant reading the ghost face as interleaved (u, E) pairs
-__device__ __forceinline__ NB<float> onb2(const float* __restrict__ u, const float* __restrict__ E,
-                                          const int* __restrict__ nbr,
-                                          const float2* __restrict__ ghUE, long long o, int ch,
-                                          int d) {
-  const int ax = d >> 1, plus = d & 1;
-  const int bit = (ch >> (2 - ax)) & 1;
-  const int chn = ch ^ (1 << (2 - ax));
-  if (bit != plus) {
-    const long long q = 8 * o + chn;
-    return NB<float>{u[q], E[q]};
-  }
-  const int no = nbr[6 * o + d];
-  if (no >= 0) {
-    const long long q = 8LL * no + chn;
-    return NB<float>{u[q], E[q]};
-  }
-  const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
-  const int qi = (((ch >> (2 - t1)) & 1) << 1) | ((ch >> (2 - t2)) & 1);
-  const float2 g = ghUE[24 * o + 4 * d + qi];
-  return NB<float>{g.x, g.y};
-}
-
 // L_i (Sec. 3.2) from the centre and its six neighbours
 template <class T>
 __device__ __forceinline__ T Lval(T uc, T Ec, const NB<T>* nb, const MT<T>& m, T ih2) {
@@ -147,28 +124,6 @@ __global__ void __launch_bounds__(BS) k_osweep(T* __restrict__ u, T* __restrict_
   const T un = uc - newton(uc, E[c], nb, f[c], m, ih2, cap);
   u[c] = un;
   E[c] = ex(un);
-}
-
-__global__ void __launch_bounds__(BS) k_osweep32(float* __restrict__ u, float* __restrict__ E,
-                                                 const float* __restrict__ f,
-                                                 const int* __restrict__ nbr,
-                                                 const float2* __restrict__ ghUE,
-                                                 const float* __restrict__ mask, float mthr,
-                                                 long long n_oct, int colour, MT<float> m,
-                                                 float ih2, float cap) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= 4 * n_oct) return;
-  const long long o = t >> 2;
-  const int ch = kColourChild[colour][t & 3];
-  const long long c = 8 * o + ch;
-  if (mask && !(mask[c] > mthr)) return;
-  NB<float> nb[6];
-#pragma unroll
-  for (int d = 0; d < 6; ++d) nb[d] = onb2(u, E, nbr, ghUE, o, ch, d);
-  const float uc = u[c];
-  const float un = uc - newton(uc, E[c], nb, f[c], m, ih2, cap);
-  u[c] = un;
-  E[c] = __expf(un);
 }
 
 // restrict oct level to its parents: u average, masked residual average
@@ -545,7 +500,8 @@ __global__ void __launch_bounds__(BS) k_olin_sweep(float* __restrict__ e, const 
                                                    const float* __restrict__ u,
                                                    const float* __restrict__ E,
                                                    const int* __restrict__ nbr,
-                                                   const float2* __restrict__ ghUE,
+                                                   const float* __restrict__ gh,
+                                                   const float* __restrict__ ghE,
                                                    const float* __restrict__ mask, float mthr,
                                                    long long n_oct, int colour, MT<float> m,
                                                    float ih2) {
@@ -557,7 +513,7 @@ __global__ void __launch_bounds__(BS) k_olin_sweep(float* __restrict__ e, const 
   if (mask && !(mask[c] > mthr)) return;
   NB<float> nb[6];
 #pragma unroll
-  for (int d = 0; d < 6; ++d) nb[d] = onb2(u, E, nbr, ghUE, o, ch, d);
+  for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
   const JR J = jrow(u[c], E[c], nb, m, ih2);
   float acc = r[c];
 #pragma unroll
@@ -743,6 +699,143 @@ __global__ void k_zero32(float* __restrict__ x, long long n) {
   if (i < n) x[i] = 0.f;
 }
 
+
+// ---- thread-per-oct FP32 sweeps ------------------------------------------------
+// One thread updates the 4 cells of one colour in its oct: the oct's 8 values
+// are two float4 loads, each face is visited once (a neighbouring oct's cells
+// or the ghost face, stored as interleaved (u, E) pairs = one 32-byte sector),
+// and the oct is written back whole.  Consecutive threads own consecutive
+// octs, so the oct loads and stores are fully coalesced.
+struct Oct8 {
+  float v[8];
+};
+
+__device__ __forceinline__ Oct8 ld8(const float* __restrict__ p, long long o) {
+  const float4* q = reinterpret_cast<const float4*>(p + 8 * o);
+  const float4 a = q[0], b = q[1];
+  return Oct8{{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w}};
+}
+
+__device__ __forceinline__ void st8(float* __restrict__ p, long long o, const Oct8& x) {
+  float4* q = reinterpret_cast<float4*>(p + 8 * o);
+  q[0] = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
+  q[1] = make_float4(x.v[4], x.v[5], x.v[6], x.v[7]);
+}
+
+// tangential face index of cell ch on a face normal to axis ax
+__device__ __forceinline__ int face_q(int ch, int ax) {
+  const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+  return (((ch >> (2 - t1)) & 1) << 1) | ((ch >> (2 - t2)) & 1);
+}
+
+// LIN = true : Gauss-Seidel on J(u) e = r  (arrays u, E fixed; e updated)
+// LIN = false: Newton-Gauss-Seidel on L(u) = f (u, E updated)
+template <bool LIN, int COL>
+__global__ void __launch_bounds__(BS) k_oct_sweep32(
+    float* __restrict__ u, float* __restrict__ E, float* __restrict__ e,
+    const float* __restrict__ rf, const int* __restrict__ nbr, const float2* __restrict__ ghUE,
+    const float* __restrict__ mask, float mthr, long long n_oct, MT<float> m, float ih2,
+    float cap) {
+  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (o >= n_oct) return;
+  constexpr int CC[2][4] = {{0, 3, 5, 6}, {1, 2, 4, 7}};
+  const Oct8 U = ld8(u, o), EE = ld8(E, o), R = ld8(rf, o);
+  Oct8 X = LIN ? ld8(e, o) : U;  // LIN: correction; else unused copy
+  bool act[4];
+  float s1[4], s2[4], s3[4];  // LIN: (sum off*e, diag sum, -); NL: (sum b du, sum du, sum b)
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int ch = CC[COL][q];
+    act[q] = !mask || mask[8 * o + ch] > mthr;
+    s1[q] = s2[q] = s3[q] = 0.f;
+    // in-oct neighbours (other colour, unchanged in this half-sweep)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int cn = ch ^ (1 << (2 - a));
+      const float du = U.v[cn] - U.v[ch];
+      if (LIN) {
+        s1[q] = fmaf(0.5f * ih2 * fmaf(EE.v[cn], du, EE.v[ch] + EE.v[cn]), X.v[cn], s1[q]);
+        s2[q] += fmaf(EE.v[ch], du, -EE.v[ch] - EE.v[cn]);
+      } else {
+        const float b = 0.5f * (EE.v[cn] + EE.v[ch]);
+        s1[q] = fmaf(b, du, s1[q]);
+        s2[q] += du;
+        s3[q] += b;
+      }
+    }
+  }
+  // faces
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    const int a = d >> 1, plus = d & 1;
+    const int no = nbr[6 * o + d];
+    Oct8 NU, NE, NX;
+    float2 G[4];
+    if (no >= 0) {
+      NU = ld8(u, no);
+      NE = ld8(E, no);
+      if (LIN) NX = ld8(e, no);
+    } else {
+      const float4* gp = reinterpret_cast<const float4*>(ghUE + 24 * o + 4 * d);
+      const float4 g0 = gp[0], g1 = gp[1];
+      G[0] = make_float2(g0.x, g0.y);
+      G[1] = make_float2(g0.z, g0.w);
+      G[2] = make_float2(g1.x, g1.y);
+      G[3] = make_float2(g1.z, g1.w);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ch = CC[COL][q];
+      if (((ch >> (2 - a)) & 1) != plus) continue;  // not on this face
+      float un, En, xn;
+      if (no >= 0) {
+        const int cn = ch ^ (1 << (2 - a));
+        un = NU.v[cn];
+        En = NE.v[cn];
+        xn = LIN ? NX.v[cn] : 0.f;
+      } else {
+        const float2 g = G[face_q(ch, a)];
+        un = g.x;
+        En = g.y;
+        xn = 0.f;
+      }
+      const float du = un - U.v[ch];
+      if (LIN) {
+        s1[q] = fmaf(0.5f * ih2 * fmaf(En, du, EE.v[ch] + En), xn, s1[q]);
+        s2[q] += fmaf(EE.v[ch], du, -EE.v[ch] - En);
+      } else {
+        const float b = 0.5f * (En + EE.v[ch]);
+        s1[q] = fmaf(b, du, s1[q]);
+        s2[q] += du;
+        s3[q] += b;
+      }
+    }
+  }
+  Oct8 UO = U, EO = EE;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (!act[q]) continue;
+    const int ch = CC[COL][q];
+    const float sN = nls(U.v[ch], EE.v[ch], m);
+    if (LIN) {
+      const float diag = s2[q] * 0.5f * ih2 + m.aRt_np1 * sN;
+      X.v[ch] = __fdividef(R.v[ch] - s1[q], diag);
+    } else {
+      const float L = s1[q] * ih2 + m.aRt * (1.f - sN);
+      const float dL = (0.5f * EE.v[ch] * s2[q] - s3[q]) * ih2 + m.aRt_np1 * sN;
+      float step = __fdividef(L - R.v[ch], dL);
+      step = fminf(fmaxf(step, -cap), cap);
+      UO.v[ch] = U.v[ch] - step;
+      EO.v[ch] = __expf(UO.v[ch]);
+    }
+  }
+  if (LIN) {
+    st8(e, o, X);
+  } else {
+    st8(u, o, UO);
+    st8(E, o, EO);
+  }
+}
 
 // interleaved (u, E) FP32 copy of the ghost slots
 __global__ void k_ghost_pack(const double* __restrict__ g, const double* __restrict__ gE,
@@ -933,9 +1026,15 @@ void relax(SolveCtx& S, int l, int sweeps) {
       if (l >= 1) {
         if (l == S.L) prof_begin(c, 3, L.ncell);
         if constexpr (std::is_same<T, float>::value) {
-          k_osweep32<<<nblocks(4 * L.n_oct, BS), BS, 0, c->s>>>(
-              L.w32, L.wE32, L.wf32, L.nbr, L.ghostUE32, l == S.L ? nullptr : L.mask, S.mthr,
-              L.n_oct, col, m, (float)L.ih2, (float)g.step_cap);
+          const float* mk = l == S.L ? nullptr : L.mask;
+          if (col == 0)
+            k_oct_sweep32<false, 0><<<nblocks(L.n_oct, BS), BS, 0, c->s>>>(
+                L.w32, L.wE32, nullptr, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, L.n_oct, m,
+                (float)L.ih2, (float)g.step_cap);
+          else
+            k_oct_sweep32<false, 1><<<nblocks(L.n_oct, BS), BS, 0, c->s>>>(
+                L.w32, L.wE32, nullptr, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, L.n_oct, m,
+                (float)L.ih2, (float)g.step_cap);
         } else {
           k_osweep<T><<<nblocks(4 * L.n_oct, BS), BS, 0, c->s>>>(
               a.w, a.wE, a.wf, L.nbr, a.gh, a.ghE, l == S.L ? nullptr : L.mask, S.mthr, L.n_oct,
@@ -1080,9 +1179,14 @@ void lin_relax(SolveCtx& S, int l, int sweeps) {
       if (l >= 1) {
         const float* mk = l == S.L ? nullptr : L.mask;
         if (l == S.L) prof_begin(c, 4, L.ncell);
-        k_olin_sweep<<<nblocks(4 * L.n_oct, BS), BS, 0, c->s>>>(
-            L.wold32, L.wf32, L.w32, L.wE32, L.nbr, L.ghostUE32, mk, S.mthr, L.n_oct, col, m,
-            (float)L.ih2);
+        if (col == 0)
+          k_oct_sweep32<true, 0><<<nblocks(L.n_oct, BS), BS, 0, c->s>>>(
+              L.w32, L.wE32, L.wold32, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, L.n_oct, m,
+              (float)L.ih2, 0.f);
+        else
+          k_oct_sweep32<true, 1><<<nblocks(L.n_oct, BS), BS, 0, c->s>>>(
+              L.w32, L.wE32, L.wold32, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, L.n_oct, m,
+              (float)L.ih2, 0.f);
         if (l == S.L) prof_end(c);
       } else
         k_dlin_sweep<<<nblocks(L.ncell / 2, BS), BS, 0, c->s>>>(L.wold32, L.wf32, L.w32, L.wE32,
