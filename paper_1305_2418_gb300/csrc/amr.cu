@@ -461,7 +461,7 @@ static void free_level(AmrLevel& L) {
   void* ps[] = {L.son,  L.refined, L.count,  L.opos, L.pcell,   L.nbr,     L.mass,
                 L.w,    L.wE,      L.wf,     L.wold, L.mask,    L.ghost,   L.ghostE,
                 L.acc,  L.pnbr,    L.w32,    L.wE32, L.wf32,    L.wold32,  L.ghost32,
-                L.ghostE32, L.ghostUE32};
+                L.ghostE32, L.ghostUE32, L.olist};
   for (void* p : ps)
     if (p) cudaFree(p);
   // u, E, f of level >= 1 are owned here too
@@ -532,7 +532,7 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
   L.nbr = nullptr; L.mass = nullptr; L.w = nullptr; L.wE = nullptr; L.wf = nullptr;
   L.wold = nullptr; L.mask = nullptr; L.ghost = nullptr; L.ghostE = nullptr; L.acc = nullptr;
   L.pnbr = nullptr; L.w32 = nullptr; L.wE32 = nullptr; L.wf32 = nullptr; L.wold32 = nullptr;
-  L.ghost32 = nullptr; L.ghostE32 = nullptr; L.ghostUE32 = nullptr;
+  L.ghost32 = nullptr; L.ghostE32 = nullptr; L.ghostUE32 = nullptr; L.olist = nullptr;
   TRY(grow(c, &L.son, n));
   TRY(grow(c, &L.refined, n));
   TRY(grow(c, &L.count, n));
@@ -551,6 +551,7 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
     TRY(grow(c, &L.ghost32, 24 * no));
     TRY(grow(c, &L.ghostE32, 24 * no));
     TRY(grow(c, &L.ghostUE32, 24 * no));
+    TRY(grow(c, &L.olist, no));
     TRY(grow(c, &L.opos, no));
     TRY(grow(c, &L.pcell, no));
     TRY(grow(c, &L.nbr, 6 * no));

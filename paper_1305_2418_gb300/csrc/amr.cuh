@@ -36,6 +36,8 @@ struct AmrLevel {
   float *ghost32 = nullptr, *ghostE32 = nullptr;
   float2* ghostUE32 = nullptr;        // [n_oct*24] interleaved (u, E) ghost pairs
   long long relaxed = 0;              // cells relaxed in the current level solve
+  int* olist = nullptr;               // [n_oct] octs with a relaxed cell (coarse level of a solve)
+  long long n_list = 0;               // entries of olist in use
 };
 
 struct TreeView {

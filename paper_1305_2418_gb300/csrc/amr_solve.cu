@@ -110,10 +110,11 @@ __global__ void __launch_bounds__(BS) k_osweep(T* __restrict__ u, T* __restrict_
                                                const T* __restrict__ f, const int* __restrict__ nbr,
                                                const T* __restrict__ gh, const T* __restrict__ ghE,
                                                const float* __restrict__ mask, float mthr,
-                                               long long n_oct, int colour, MT<T> m, T ih2, T cap) {
+                                               long long n_oct, const int* __restrict__ olist,
+                                               int colour, MT<T> m, T ih2, T cap) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= 4 * n_oct) return;
-  const long long o = t >> 2;
+  const long long o = olist ? olist[t >> 2] : t >> 2;
   const int ch = kColourChild[colour][t & 3];
   const long long c = 8 * o + ch;
   if (mask && !(mask[c] > mthr)) return;
@@ -131,11 +132,12 @@ template <class T>
 __global__ void __launch_bounds__(BS) k_orestrict(
     const T* __restrict__ u, const T* __restrict__ E, const T* __restrict__ f,
     const int* __restrict__ nbr, const T* __restrict__ gh, const T* __restrict__ ghE,
-    const float* __restrict__ mask, float mthr, long long n_oct, const int* __restrict__ pcell,
-    MT<T> m, T ih2, T* __restrict__ uc, T* __restrict__ Ec, T* __restrict__ ucold,
-    T* __restrict__ fc) {
-  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (o >= n_oct) return;
+    const float* __restrict__ mask, float mthr, long long n_oct, const int* __restrict__ olist,
+    const int* __restrict__ pcell, MT<T> m, T ih2, T* __restrict__ uc, T* __restrict__ Ec,
+    T* __restrict__ ucold, T* __restrict__ fc) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n_oct) return;
+  const long long o = olist ? olist[t] : t;
   T su = 0, sr = 0;
   for (int ch = 0; ch < 8; ++ch) {
     const long long c = 8 * o + ch;
@@ -161,11 +163,14 @@ __global__ void __launch_bounds__(BS) k_ofas(const T* __restrict__ u, const T* _
                                              T* __restrict__ f, const int* __restrict__ nbr,
                                              const T* __restrict__ gh, const T* __restrict__ ghE,
                                              const float* __restrict__ mask, float mthr,
-                                             long long ncell, MT<T> m, T ih2) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= ncell || !(mask[c] > mthr)) return;
-  const long long o = c >> 3;
-  const int ch = (int)(c & 7);
+                                             long long ncell, const int* __restrict__ olist,
+                                             MT<T> m, T ih2) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= ncell) return;
+  const long long o = olist ? olist[t >> 3] : t >> 3;
+  const int ch = (int)(t & 7);
+  const long long c = 8 * o + ch;
+  if (!(mask[c] > mthr)) return;
   NB<T> nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
@@ -176,17 +181,19 @@ __global__ void __launch_bounds__(BS) k_ofas(const T* __restrict__ u, const T* _
 // neighbours from the pnbr table (a gradient component is 0 where one is
 // missing).
 template <class T>
-__global__ void __launch_bounds__(BS) k_oprolong(long long ncell, const int* __restrict__ pcell,
+__global__ void __launch_bounds__(BS) k_oprolong(long long ncell, const int* __restrict__ olist,
+                                                 const int* __restrict__ pcell,
                                                  const int* __restrict__ pnbr,
                                                  const T* __restrict__ uc,
                                                  const T* __restrict__ ucold,
                                                  const float* __restrict__ mask, float mthr,
                                                  int linear, T* __restrict__ u, T* __restrict__ E) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= ncell) return;
+  const long long o = olist ? olist[t >> 3] : t >> 3;
+  const int ch = (int)(t & 7);
+  const long long c = 8 * o + ch;
   if (mask && !(mask[c] > mthr)) return;
-  const long long o = c >> 3;
-  const int ch = (int)(c & 7);
   const int p = pcell[o];
   T v = uc[p] - ucold[p];
   if (linear) {
@@ -496,40 +503,17 @@ __global__ void __launch_bounds__(BS) k_oresid_lin(
   }
 }
 
-__global__ void __launch_bounds__(BS) k_olin_sweep(float* __restrict__ e, const float* __restrict__ r,
-                                                   const float* __restrict__ u,
-                                                   const float* __restrict__ E,
-                                                   const int* __restrict__ nbr,
-                                                   const float* __restrict__ gh,
-                                                   const float* __restrict__ ghE,
-                                                   const float* __restrict__ mask, float mthr,
-                                                   long long n_oct, int colour, MT<float> m,
-                                                   float ih2) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= 4 * n_oct) return;
-  const long long o = t >> 2;
-  const int ch = kColourChild[colour][t & 3];
-  const long long c = 8 * o + ch;
-  if (mask && !(mask[c] > mthr)) return;
-  NB<float> nb[6];
-#pragma unroll
-  for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
-  const JR J = jrow(u[c], E[c], nb, m, ih2);
-  float acc = r[c];
-#pragma unroll
-  for (int d = 0; d < 6; ++d) acc = fmaf(-J.off[d], onb_e(e, nbr, o, ch, d), acc);
-  e[c] = __fdividef(acc, J.diag);
-}
-
 // r_c = R(r - J e) over relaxed daughters, u_c = R(u), E_c = e^{u_c}, e_c = 0
 __global__ void __launch_bounds__(BS) k_olin_restrict(
     const float* __restrict__ e, const float* __restrict__ r, const float* __restrict__ u,
     const float* __restrict__ E, const int* __restrict__ nbr, const float* __restrict__ gh,
     const float* __restrict__ ghE, const float* __restrict__ mask, float mthr, long long n_oct,
-    const int* __restrict__ pcell, MT<float> m, float ih2, float* __restrict__ rc,
-    float* __restrict__ uc, float* __restrict__ Ec, float* __restrict__ ec) {
-  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (o >= n_oct) return;
+    const int* __restrict__ olist, const int* __restrict__ pcell, MT<float> m, float ih2,
+    float* __restrict__ rc, float* __restrict__ uc, float* __restrict__ Ec,
+    float* __restrict__ ec) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n_oct) return;
+  const long long o = olist ? olist[t] : t;
   float su = 0.f, sr = 0.f;
   for (int ch = 0; ch < 8; ++ch) {
     const long long c = 8 * o + ch;
@@ -554,16 +538,18 @@ __global__ void __launch_bounds__(BS) k_olin_restrict(
 }
 
 // e += P(e_c) on relaxed cells (linear reconstruction from the parent)
-__global__ void __launch_bounds__(BS) k_olin_prolong(long long ncell, const int* __restrict__ pcell,
+__global__ void __launch_bounds__(BS) k_olin_prolong(long long ncell, const int* __restrict__ olist,
+                                                     const int* __restrict__ pcell,
                                                      const int* __restrict__ pnbr,
                                                      const float* __restrict__ ec,
                                                      const float* __restrict__ mask, float mthr,
                                                      int linear, float* __restrict__ e) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= ncell) return;
+  const long long o = olist ? olist[t >> 3] : t >> 3;
+  const int ch = (int)(t & 7);
+  const long long c = 8 * o + ch;
   if (mask && !(mask[c] > mthr)) return;
-  const long long o = c >> 3;
-  const int ch = (int)(c & 7);
   float v = ec[pcell[o]];
   if (linear) {
     for (int ax = 0; ax < 3; ++ax) {
@@ -734,10 +720,11 @@ template <bool LIN, int COL>
 __global__ void __launch_bounds__(BS) k_oct_sweep32(
     float* __restrict__ u, float* __restrict__ E, float* __restrict__ e,
     const float* __restrict__ rf, const int* __restrict__ nbr, const float2* __restrict__ ghUE,
-    const float* __restrict__ mask, float mthr, long long n_oct, MT<float> m, float ih2,
-    float cap) {
-  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (o >= n_oct) return;
+    const float* __restrict__ mask, float mthr, long long n_oct, const int* __restrict__ olist,
+    MT<float> m, float ih2, float cap) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n_oct) return;
+  const long long o = olist ? olist[t] : t;
   constexpr int CC[2][4] = {{0, 3, 5, 6}, {1, 2, 4, 7}};
   const Oct8 U = ld8(u, o), EE = ld8(E, o), R = ld8(rf, o);
   Oct8 X = LIN ? ld8(e, o) : U;  // LIN: correction; else unused copy
@@ -969,6 +956,28 @@ __global__ void k_count_relaxed(const float* __restrict__ mask, long long n, flo
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd((unsigned long long*)out, (unsigned long long)cnt);
 }
 
+// Octs of a coarse level holding at least one relaxed cell, appended with one
+// atomic per warp (order within a warp kept; any order is valid, since each
+// kernel over the list updates cells independently of the visiting order).
+__global__ void k_oct_list(const float* __restrict__ mask, long long n_oct, float mthr,
+                           int* __restrict__ list, unsigned long long* __restrict__ count) {
+  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  bool act = false;
+  if (o < n_oct) {
+    const float4* m4 = reinterpret_cast<const float4*>(mask + 8 * o);
+    const float4 a = m4[0], b = m4[1];
+    act = a.x > mthr || a.y > mthr || a.z > mthr || a.w > mthr || b.x > mthr || b.y > mthr ||
+          b.z > mthr || b.w > mthr;
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, act);
+  if (!bal) return;
+  const int lane = threadIdx.x & 31, lead = __ffs(bal) - 1;
+  unsigned long long base = 0;
+  if (lane == lead) base = atomicAdd(count, (unsigned long long)__popc(bal));
+  base = __shfl_sync(0xffffffffu, base, lead);
+  if (act) list[base + __popc(bal & ((1u << lane) - 1u))] = (int)o;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -1014,6 +1023,16 @@ struct SolveCtx {
   long long updates;
 };
 
+// Octs visited on tree level l >= 1 of the level-S.L solve: every oct of the
+// solved level, the active-oct list on a coarser level.
+struct ORange {
+  const int* list;
+  long long n;
+};
+ORange orange(const SolveCtx& S, const AmrLevel& L, int l) {
+  return l == S.L ? ORange{nullptr, L.n_oct} : ORange{L.olist, L.n_list};
+}
+
 template <class T>
 void relax(SolveCtx& S, int l, int sweeps) {
   mgfr_ctx* c = S.c;
@@ -1024,21 +1043,23 @@ void relax(SolveCtx& S, int l, int sweeps) {
   for (int s = 0; s < sweeps; ++s) {
     for (int col = 0; col < 2; ++col) {
       if (l >= 1) {
+        const ORange R = orange(S, L, l);
+        if (R.n == 0) continue;
         if (l == S.L) prof_begin(c, 3, L.ncell);
         if constexpr (std::is_same<T, float>::value) {
           const float* mk = l == S.L ? nullptr : L.mask;
           if (col == 0)
-            k_oct_sweep32<false, 0><<<nblocks(L.n_oct, BS), BS, 0, c->s>>>(
-                L.w32, L.wE32, nullptr, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, L.n_oct, m,
+            k_oct_sweep32<false, 0><<<nblocks(R.n, BS), BS, 0, c->s>>>(
+                L.w32, L.wE32, nullptr, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, R.n, R.list, m,
                 (float)L.ih2, (float)g.step_cap);
           else
-            k_oct_sweep32<false, 1><<<nblocks(L.n_oct, BS), BS, 0, c->s>>>(
-                L.w32, L.wE32, nullptr, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, L.n_oct, m,
+            k_oct_sweep32<false, 1><<<nblocks(R.n, BS), BS, 0, c->s>>>(
+                L.w32, L.wE32, nullptr, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, R.n, R.list, m,
                 (float)L.ih2, (float)g.step_cap);
         } else {
-          k_osweep<T><<<nblocks(4 * L.n_oct, BS), BS, 0, c->s>>>(
-              a.w, a.wE, a.wf, L.nbr, a.gh, a.ghE, l == S.L ? nullptr : L.mask, S.mthr, L.n_oct,
-              col, m, (T)L.ih2, (T)g.step_cap);
+          k_osweep<T><<<nblocks(4 * R.n, BS), BS, 0, c->s>>>(
+              a.w, a.wE, a.wf, L.nbr, a.gh, a.ghE, l == S.L ? nullptr : L.mask, S.mthr, R.n,
+              R.list, col, m, (T)L.ih2, (T)g.step_cap);
         }
         if (l == S.L) prof_end(c);
       } else {
@@ -1106,20 +1127,27 @@ void vcycle_tree(SolveCtx& S, int l) {
   if (l >= 1) {
     AmrLevel& P = A->L[l - 1];
     TA<T> b = tarr<T>(P);
-    k_orestrict<T><<<nblocks(F.n_oct, BS), BS, 0, c->s>>>(
-        a.w, a.wE, a.wf, F.nbr, a.gh, a.ghE, fmask, S.mthr, F.n_oct, F.pcell, m, (T)F.ih2, b.w,
-        b.wE, b.wold, b.wf);
-    if (l - 1 >= 1)
-      k_ofas<T><<<nblocks(P.ncell, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, P.nbr, b.gh, b.ghE,
-                                                       P.mask, S.mthr, P.ncell, m, (T)P.ih2);
-    else
+    const ORange R = orange(S, F, l);
+    if (R.n > 0)
+      k_orestrict<T><<<nblocks(R.n, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.nbr, a.gh, a.ghE,
+                                                        fmask, S.mthr, R.n, R.list, F.pcell, m,
+                                                        (T)F.ih2, b.w, b.wE, b.wold, b.wf);
+    if (l - 1 >= 1) {
+      if (P.n_list > 0)
+        k_ofas<T><<<nblocks(8 * P.n_list, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, P.nbr, b.gh,
+                                                              b.ghE, P.mask, S.mthr,
+                                                              8 * P.n_list, P.olist, m,
+                                                              (T)P.ih2);
+    } else {
       k_dfas<T><<<nblocks(P.ncell, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, P.lgN, m, (T)P.ih2,
                                                        P.mask, S.mthr);
+    }
     c->launches += 2;
     vcycle_tree<T>(S, l - 1);
-    k_oprolong<T><<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.ncell, F.pcell, F.pnbr, b.w, b.wold,
-                                                         fmask, S.mthr, g.prolong_linear, a.w,
-                                                         a.wE);
+    if (R.n > 0)
+      k_oprolong<T><<<nblocks(8 * R.n, BS), BS, 0, c->s>>>(8 * R.n, R.list, F.pcell, F.pnbr,
+                                                           b.w, b.wold, fmask, S.mthr,
+                                                           g.prolong_linear, a.w, a.wE);
     c->launches += 1;
   } else {
     DenseHier& H = c->dh;
@@ -1167,6 +1195,19 @@ mgfr_status count_relaxed(mgfr_ctx* c, AmrWork* A, const float* mask, long long 
 }
 
 
+// active-oct list of coarse tree level P (octs with a relaxed cell) -> P.olist
+mgfr_status build_oct_list(mgfr_ctx* c, AmrWork* A, AmrLevel& P, float mthr) {
+  MG_CK(c, cudaMemsetAsync(A->d_small + 3, 0, sizeof(long long), c->s));
+  k_oct_list<<<nblocks(P.n_oct, BS), BS, 0, c->s>>>(P.mask, P.n_oct, mthr, P.olist,
+                                                    (unsigned long long*)(A->d_small + 3));
+  c->launches += 1;
+  long long n = 0;
+  MG_CK(c, cudaMemcpyAsync(&n, A->d_small + 3, sizeof(long long), cudaMemcpyDeviceToHost, c->s));
+  MG_CK(c, cudaStreamSynchronize(c->s));
+  P.n_list = n;
+  return MGFR_OK;
+}
+
 // ---- linear masked V-cycle (phase B of the mixed form) -------------------------
 // level arrays: u = w32 (linearisation point), E = wE32, r = wf32, e = wold32;
 // dense levels below the base: u = u32, E = e32, r = r32, e = uold32.
@@ -1178,14 +1219,16 @@ void lin_relax(SolveCtx& S, int l, int sweeps) {
     for (int col = 0; col < 2; ++col) {
       if (l >= 1) {
         const float* mk = l == S.L ? nullptr : L.mask;
+        const ORange R = orange(S, L, l);
+        if (R.n == 0) continue;
         if (l == S.L) prof_begin(c, 4, L.ncell);
         if (col == 0)
-          k_oct_sweep32<true, 0><<<nblocks(L.n_oct, BS), BS, 0, c->s>>>(
-              L.w32, L.wE32, L.wold32, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, L.n_oct, m,
+          k_oct_sweep32<true, 0><<<nblocks(R.n, BS), BS, 0, c->s>>>(
+              L.w32, L.wE32, L.wold32, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, R.n, R.list, m,
               (float)L.ih2, 0.f);
         else
-          k_oct_sweep32<true, 1><<<nblocks(L.n_oct, BS), BS, 0, c->s>>>(
-              L.w32, L.wE32, L.wold32, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, L.n_oct, m,
+          k_oct_sweep32<true, 1><<<nblocks(R.n, BS), BS, 0, c->s>>>(
+              L.w32, L.wE32, L.wold32, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, R.n, R.list, m,
               (float)L.ih2, 0.f);
         if (l == S.L) prof_end(c);
       } else
@@ -1243,13 +1286,17 @@ void lin_vcycle_tree(SolveCtx& S, int l) {
   const float* fmask = l == S.L ? nullptr : F.mask;
   if (l >= 1) {
     AmrLevel& P = A->L[l - 1];
-    k_olin_restrict<<<nblocks(F.n_oct, BS), BS, 0, c->s>>>(
-        F.wold32, F.wf32, F.w32, F.wE32, F.nbr, F.ghost32, F.ghostE32, fmask, S.mthr, F.n_oct,
-        F.pcell, m, (float)F.ih2, P.wf32, P.w32, P.wE32, P.wold32);
+    const ORange R = orange(S, F, l);
+    if (R.n > 0)
+      k_olin_restrict<<<nblocks(R.n, BS), BS, 0, c->s>>>(
+          F.wold32, F.wf32, F.w32, F.wE32, F.nbr, F.ghost32, F.ghostE32, fmask, S.mthr, R.n,
+          R.list, F.pcell, m, (float)F.ih2, P.wf32, P.w32, P.wE32, P.wold32);
     c->launches += 1;
     lin_vcycle_tree(S, l - 1);
-    k_olin_prolong<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.ncell, F.pcell, F.pnbr, P.wold32, fmask,
-                                                          S.mthr, g.prolong_linear, F.wold32);
+    if (R.n > 0)
+      k_olin_prolong<<<nblocks(8 * R.n, BS), BS, 0, c->s>>>(8 * R.n, R.list, F.pcell, F.pnbr,
+                                                            P.wold32, fmask, S.mthr,
+                                                            g.prolong_linear, F.wold32);
     c->launches += 1;
   } else {
     DenseHier& H = c->dh;
@@ -1348,6 +1395,7 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
     k_mask_up<<<nblocks(Ch.n_oct, BS), BS, 0, c->s>>>(Ch.mask, Ch.n_oct, Ch.pcell, P.mask);
     c->launches += 1;
     TRY(count_relaxed(c, A, P.mask, P.ncell, mthr, &P.relaxed));
+    if (l >= 1) TRY(build_oct_list(c, A, P, mthr));
   }
   for (int k = 1; k < H.nlev; ++k) {
     const float* mf = k == 1 ? A->L[0].mask : A->dmask[k - 1];
