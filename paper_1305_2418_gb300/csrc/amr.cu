@@ -80,16 +80,38 @@ __global__ void k_flag(const int* __restrict__ count, long long ncell, int thr, 
 }
 
 // Exclusive scan of the refinement flags -> son indices (three passes).
+// On the base level the scan runs in Morton (Z) order of the cells: scan
+// element i is the cell whose coordinates interleave the bits of i, so the
+// octs of level 1, and through their daughters every deeper level, are stored
+// along a Z curve and face-neighbouring octs lie close together in memory.
 constexpr int SCAN_BS = 1024, SCAN_ITEMS = 4, SCAN_TILE = SCAN_BS * SCAN_ITEMS;
 
+// every third bit of x (bits 0, 3, 6, ...) packed into the low bits
+__device__ __forceinline__ unsigned long long take3(unsigned long long x) {
+  unsigned long long r = 0;
+#pragma unroll
+  for (int b = 0; b < 21; ++b) r |= ((x >> (3 * b)) & 1ULL) << b;
+  return r;
+}
+
+// scan position -> cell index: identity, or Morton order on an N = 2^mlg base
+__device__ __forceinline__ long long scan_cell(long long i, int mlg) {
+  if (mlg == 0) return i;
+  const unsigned long long x = (unsigned long long)i;
+  const long long I = (long long)take3(x >> 2), J = (long long)take3(x >> 1),
+                  K = (long long)take3(x);
+  return (((I << mlg) + J) << mlg) + K;
+}
+
 __global__ void __launch_bounds__(SCAN_BS) k_scan_count(const unsigned char* __restrict__ flags,
-                                                        long long n, int* __restrict__ sums) {
+                                                        long long n, int mlg,
+                                                        int* __restrict__ sums) {
   __shared__ int red[SCAN_BS / 32];
   const long long base = (long long)blockIdx.x * SCAN_TILE;
   int cnt = 0;
   for (int q = 0; q < SCAN_ITEMS; ++q) {
     const long long i = base + (long long)q * SCAN_BS + threadIdx.x;
-    if (i < n) cnt += flags[i] != 0;
+    if (i < n) cnt += flags[scan_cell(i, mlg)] != 0;
   }
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
@@ -128,7 +150,7 @@ __global__ void __launch_bounds__(SCAN_BS) k_scan_sums(int* __restrict__ sums, l
 }
 
 __global__ void __launch_bounds__(SCAN_BS) k_scan_scatter(const unsigned char* __restrict__ flags,
-                                                          long long n,
+                                                          long long n, int mlg,
                                                           const int* __restrict__ offs,
                                                           int* __restrict__ son) {
   __shared__ int buf[SCAN_BS];
@@ -136,7 +158,8 @@ __global__ void __launch_bounds__(SCAN_BS) k_scan_scatter(const unsigned char* _
   int run = offs[blockIdx.x];
   for (int q = 0; q < SCAN_ITEMS; ++q) {
     const long long i = base + (long long)q * SCAN_BS + threadIdx.x;
-    const int v = (i < n && flags[i]) ? 1 : 0;
+    const long long c = i < n ? scan_cell(i, mlg) : 0;
+    const int v = (i < n && flags[c]) ? 1 : 0;
     buf[threadIdx.x] = v;
     __syncthreads();
     for (int off = 1; off < SCAN_BS; off <<= 1) {
@@ -145,7 +168,7 @@ __global__ void __launch_bounds__(SCAN_BS) k_scan_scatter(const unsigned char* _
       buf[threadIdx.x] += add;
       __syncthreads();
     }
-    if (i < n) son[i] = v ? run + buf[threadIdx.x] - 1 : -1;
+    if (i < n) son[c] = v ? run + buf[threadIdx.x] - 1 : -1;
     const int tot = buf[SCAN_BS - 1];
     __syncthreads();
     run += tot;
@@ -568,7 +591,7 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
 }
 
 static mgfr_status scan_flags(mgfr_ctx* c, AmrWork* A, const unsigned char* flags, long long n,
-                              int* son, long long* total) {
+                              int mlg, int* son, long long* total) {
   const long long nb = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (nb > A->blocksums_cap) {
     if (A->blocksums) cudaFree(A->blocksums);
@@ -576,9 +599,9 @@ static mgfr_status scan_flags(mgfr_ctx* c, AmrWork* A, const unsigned char* flag
     MG_CK(c, cudaMalloc(&A->blocksums, sizeof(int) * (size_t)nb));
     A->blocksums_cap = nb;
   }
-  k_scan_count<<<(unsigned)nb, SCAN_BS, 0, c->s>>>(flags, n, A->blocksums);
+  k_scan_count<<<(unsigned)nb, SCAN_BS, 0, c->s>>>(flags, n, mlg, A->blocksums);
   k_scan_sums<<<1, SCAN_BS, 0, c->s>>>(A->blocksums, nb, A->d_small);
-  k_scan_scatter<<<(unsigned)nb, SCAN_BS, 0, c->s>>>(flags, n, A->blocksums, son);
+  k_scan_scatter<<<(unsigned)nb, SCAN_BS, 0, c->s>>>(flags, n, mlg, A->blocksums, son);
   c->launches += 3;
   MG_CK(c, cudaMemcpyAsync(total, A->d_small, sizeof(long long), cudaMemcpyDeviceToHost, c->s));
   MG_CK(c, cudaStreamSynchronize(c->s));
@@ -612,7 +635,7 @@ static mgfr_status build_structure(mgfr_ctx* c, AmrWork* A, const double* pos) {
                                                   L.refined);
     c->launches += 1;
     long long nref = 0;
-    TRY(scan_flags(c, A, L.refined, L.ncell, L.son, &nref));
+    TRY(scan_flags(c, A, L.refined, L.ncell, l == 0 ? A->lg0 : 0, L.son, &nref));
     if (nref == 0) break;
     AmrLevel& N = A->L[l + 1];
     N.n_oct = nref;

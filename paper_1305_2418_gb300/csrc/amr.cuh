@@ -5,10 +5,12 @@
 // Levels: 0 is the dense periodic base grid (N0^3, C order).  Level l >= 1
 // is a list of octs (8 daughters of one refined level-(l-1) cell); cell
 // index 8*o + (4 di + 2 dj + dk).  son[l][cell] is the oct at l+1 of a
-// refined cell (-1 otherwise).  Octs of level l+1 are stored in the storage
-// order of their parents (a stream compaction of level l), so a parent's
-// position is given by opos (its level-(l-1)... coordinates) and keys are
-// reported as the parent's linear index (I N + J) N + K at level l.
+// refined cell (-1 otherwise).  Octs of level 1 are stored in Morton (Z)
+// order of their base-level parents, and octs of level l+1 >= 2 in the
+// storage order of their parents (a stream compaction of level l), which
+// continues the same Z curve; a parent's position is given by opos (its
+// level-(l-1) coordinates) and keys are reported as the parent's linear index
+// (I N + J) N + K at level l.
 #pragma once
 #include "mgfr_internal.cuh"
 

@@ -282,15 +282,16 @@ __global__ void k_finish3(const double* __restrict__ partials, int nparts, doubl
 }
 
 // ---- dense levels (base and below) with masks, u and E stored ------------
-__device__ __forceinline__ long long cidx(int i, int j, int k, int lg) {
-  return ((((long long)i << lg) + j) << lg) + k;
+// linear index of (i, j, k) on an N = 2^lg grid (N <= 1024: fits 32 bits)
+__device__ __forceinline__ unsigned cidx(int i, int j, int k, int lg) {
+  return ((((unsigned)i << lg) + (unsigned)j) << lg) + (unsigned)k;
 }
 
 template <class T>
 __device__ __forceinline__ void dnb(const T* __restrict__ u, const T* __restrict__ E, int i, int j,
                                     int k, int lg, NB<T>* nb) {
   const int M = (1 << lg) - 1;
-  const long long q[6] = {cidx((i - 1) & M, j, k, lg), cidx((i + 1) & M, j, k, lg),
+  const unsigned q[6] = {cidx((i - 1) & M, j, k, lg), cidx((i + 1) & M, j, k, lg),
                           cidx(i, (j - 1) & M, k, lg), cidx(i, (j + 1) & M, k, lg),
                           cidx(i, j, (k - 1) & M, lg), cidx(i, j, (k + 1) & M, lg)};
 #pragma unroll
@@ -302,14 +303,14 @@ __global__ void __launch_bounds__(BS) k_dsweep(T* __restrict__ u, T* __restrict_
                                                const T* __restrict__ f, int lg, int colour, MT<T> m,
                                                T ih2, T cap, const float* __restrict__ mask,
                                                float mthr) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = 1 << lg, M = N - 1;
-  if (t >= (1LL << (3 * lg - 1))) return;
+  if (t >= (1u << (3 * lg - 1))) return;
   const int k2 = (int)(t & ((N >> 1) - 1));
-  const long long r = t >> (lg - 1);
+  const unsigned r = t >> (lg - 1);
   const int j = (int)(r & M), i = (int)(r >> lg);
   const int k = 2 * k2 + ((i + j + colour) & 1);
-  const long long c = cidx(i, j, k, lg);
+  const unsigned c = cidx(i, j, k, lg);
   if (mask && !(mask[c] > mthr)) return;
   NB<T> nb[6];
   dnb(u, E, i, j, k, lg, nb);
@@ -326,13 +327,13 @@ __global__ void __launch_bounds__(BS) k_drestrict(const T* __restrict__ u, const
                                                   T* __restrict__ ucold, T* __restrict__ fc, MT<T> m,
                                                   T ih2, const float* __restrict__ mask, float mthr) {
   const int lgc = lgf - 1, Nc = 1 << lgc;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (1LL << (3 * lgc))) return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (1u << (3 * lgc))) return;
   const int K = (int)(t & (Nc - 1)), J = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
   T su = 0, sr = 0;
   for (int q = 0; q < 8; ++q) {
     const int i = 2 * I + (q >> 2), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q & 1);
-    const long long c = cidx(i, j, k, lgf);
+    const unsigned c = cidx(i, j, k, lgf);
     su += u[c];
     if (!mask || mask[c] > mthr) {
       NB<T> nb[6];
@@ -352,8 +353,8 @@ __global__ void __launch_bounds__(BS) k_dfas(const T* __restrict__ u, const T* _
                                              T* __restrict__ f, int lg, MT<T> m, T ih2,
                                              const float* __restrict__ mask, float mthr) {
   const int N = 1 << lg;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (1LL << (3 * lg))) return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (1u << (3 * lg))) return;
   if (mask && !(mask[t] > mthr)) return;
   const int k = (int)(t & (N - 1)), j = (int)((t >> lg) & (N - 1)), i = (int)(t >> (2 * lg));
   NB<T> nb[6];
@@ -367,13 +368,13 @@ __global__ void __launch_bounds__(BS) k_dprolong(T* __restrict__ u, T* __restric
                                                  int lgf, int linear, const float* __restrict__ mask,
                                                  float mthr) {
   const int N = 1 << lgf, lgc = lgf - 1, Mc = (N >> 1) - 1;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (1LL << (3 * lgf))) return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (1u << (3 * lgf))) return;
   if (mask && !(mask[t] > mthr)) return;
   const int k = (int)(t & (N - 1)), j = (int)((t >> lgf) & (N - 1)), i = (int)(t >> (2 * lgf));
   const int I = i >> 1, J = j >> 1, K = k >> 1;
   auto corr = [&](int a, int b, int c) {
-    const long long q = cidx(a & Mc, b & Mc, c & Mc, lgc);
+    const unsigned q = cidx(a & Mc, b & Mc, c & Mc, lgc);
     return uc[q] - ucold[q];
   };
   T v = corr(I, J, K);
@@ -566,14 +567,14 @@ __global__ void __launch_bounds__(BS) k_dlin_sweep(float* __restrict__ e, const 
                                                    const float* __restrict__ E, int lg, int colour,
                                                    MT<float> m, float ih2,
                                                    const float* __restrict__ mask, float mthr) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = 1 << lg, M = N - 1;
-  if (t >= (1LL << (3 * lg - 1))) return;
+  if (t >= (1u << (3 * lg - 1))) return;
   const int k2 = (int)(t & ((N >> 1) - 1));
-  const long long rr = t >> (lg - 1);
+  const unsigned rr = t >> (lg - 1);
   const int j = (int)(rr & M), i = (int)(rr >> lg);
   const int k = 2 * k2 + ((i + j + colour) & 1);
-  const long long c = cidx(i, j, k, lg);
+  const unsigned c = cidx(i, j, k, lg);
   if (mask && !(mask[c] > mthr)) return;
   NB<float> nb[6];
   dnb(u, E, i, j, k, lg, nb);
@@ -595,13 +596,13 @@ __global__ void __launch_bounds__(BS) k_dlin_restrict(const float* __restrict__ 
                                                       MT<float> m, float ih2,
                                                       const float* __restrict__ mask, float mthr) {
   const int lgc = lgf - 1, Nc = 1 << lgc;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (1LL << (3 * lgc))) return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (1u << (3 * lgc))) return;
   const int K = (int)(t & (Nc - 1)), J0 = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
   float su = 0.f, sr = 0.f;
   for (int q = 0; q < 8; ++q) {
     const int i = 2 * I + (q >> 2), j = 2 * J0 + ((q >> 1) & 1), k = 2 * K + (q & 1);
-    const long long c = cidx(i, j, k, lgf);
+    const unsigned c = cidx(i, j, k, lgf);
     su += u[c];
     if (!mask || mask[c] > mthr) {
       NB<float> nb[6], en[6];
@@ -625,8 +626,8 @@ __global__ void __launch_bounds__(BS) k_dlin_prolong(float* __restrict__ e, cons
                                                      int lgf, int linear,
                                                      const float* __restrict__ mask, float mthr) {
   const int N = 1 << lgf, lgc = lgf - 1, Mc = (N >> 1) - 1;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (1LL << (3 * lgf))) return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (1u << (3 * lgf))) return;
   if (mask && !(mask[t] > mthr)) return;
   const int k = (int)(t & (N - 1)), j = (int)((t >> lgf) & (N - 1)), i = (int)(t >> (2 * lgf));
   const int I = i >> 1, J = j >> 1, K = k >> 1;
@@ -824,13 +825,6 @@ __global__ void __launch_bounds__(BS) k_oct_sweep32(
   }
 }
 
-// interleaved (u, E) FP32 copy of the ghost slots
-__global__ void k_ghost_pack(const double* __restrict__ g, const double* __restrict__ gE,
-                             long long n, float2* __restrict__ out) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n) out[i] = make_float2((float)g[i], (float)gE[i]);
-}
-
 // ---- set-up kernels --------------------------------------------------------
 // initial guess of level L from the converged level L-1 (linear
 // reconstruction with the parent's neighbours), FP64 and FP32 copies
@@ -858,35 +852,34 @@ __global__ void k_init_level(long long ncell, const int* __restrict__ pcell,
   }
 }
 
-// Ghost layer of level l: the level-l cells across every oct face without a
-// neighbouring oct take the linear reconstruction of their (converged)
-// parent on level l-1; fixed during the level solve.
+// Ghost values on the faces of level-l octs that have no neighbouring oct
+// (Sec. 3.3), one thread per (oct, face).  The face's four outside cells are
+// daughters of one level-(l-1) cell P, the oct's parent shifted along the face
+// normal, so P and its six neighbours are looked up once per face.  A ghost is
+// P's value plus, per axis, s (c+ - c-)/8, s = +1 or -1 for the ghost's
+// high or low daughter position in P (a component is 0 where one of P's
+// neighbours does not exist).  Written as FP64 (u, e^u), FP32 copies and
+// interleaved FP32 (u, E) pairs.
 __global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restrict__ nbr,
                          const double* __restrict__ up, int linear, double* __restrict__ ghost,
                          double* __restrict__ ghostE, float* __restrict__ g32,
-                         float* __restrict__ gE32) {
+                         float* __restrict__ gE32, float2* __restrict__ ghUE) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= 24 * n_oct) return;
-  const long long o = t / 24;
-  const int d = (int)((t % 24) >> 2), qi = (int)(t & 3);
+  if (t >= 6 * n_oct) return;
+  const long long o = t / 6;
+  const int d = (int)(t - 6 * o);
   if (nbr[6 * o + d] >= 0) return;
   const int ax = d >> 1, plus = d & 1;
   const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
-  int b[3];
-  b[ax] = plus;
-  b[t1] = (qi >> 1) & 1;
-  b[t2] = qi & 1;
   const int4 p = T.opos[l][o];
-  long long C[3] = {2LL * p.x + b[0], 2LL * p.y + b[1], 2LL * p.z + b[2]};
-  C[ax] += plus ? 1 : -1;
-  const long long Nl = 1LL << (T.lg0 + l);
-  for (int a = 0; a < 3; ++a) C[a] &= Nl - 1;
+  long long P[3] = {p.x, p.y, p.z};
+  P[ax] += plus ? 1 : -1;
   int lev;
-  const long long P[3] = {C[0] >> 1, C[1] >> 1, C[2] >> 1};
   const long long pc = find_cell(T, l - 1, P[0], P[1], P[2], &lev);
-  double v = 0.0;
+  double v0 = 0.0, g[3] = {0.0, 0.0, 0.0};
+  bool have[3] = {false, false, false};
   if (lev == l - 1) {
-    v = up[pc];
+    v0 = up[pc];
     if (linear) {
       for (int a = 0; a < 3; ++a) {
         long long Qp[3] = {P[0], P[1], P[2]}, Qm[3] = {P[0], P[1], P[2]};
@@ -896,14 +889,29 @@ __global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restri
         const long long cp = find_cell(T, l - 1, Qp[0], Qp[1], Qp[2], &lp);
         const long long cm = find_cell(T, l - 1, Qm[0], Qm[1], Qm[2], &lm);
         if (lp != l - 1 || lm != l - 1) continue;
-        v += ((C[a] & 1) ? 0.125 : -0.125) * (up[cp] - up[cm]);
+        g[a] = up[cp] - up[cm];
+        have[a] = true;
       }
     }
   }
-  ghost[t] = v;
-  ghostE[t] = exp(v);
-  g32[t] = (float)v;
-  gE32[t] = __expf((float)v);
+  for (int qi = 0; qi < 4; ++qi) {
+    // daughter position of the ghost inside P: along the normal the side
+    // facing the oct, tangentially the oct cell's own bits
+    int hi[3];
+    hi[ax] = plus ? 0 : 1;
+    hi[t1] = (qi >> 1) & 1;
+    hi[t2] = qi & 1;
+    double v = v0;
+    for (int a = 0; a < 3; ++a)
+      if (have[a]) v += (hi[a] ? 0.125 : -0.125) * g[a];
+    const long long q = 24 * o + 4 * d + qi;
+    const double E = exp(v);
+    ghost[q] = v;
+    ghostE[q] = E;
+    g32[q] = (float)v;
+    gE32[q] = __expf((float)v);
+    ghUE[q] = make_float2((float)v, (float)E);
+  }
 }
 
 __global__ void k_d2f(const double* __restrict__ x, float* __restrict__ y, long long n) {
@@ -932,8 +940,8 @@ __global__ void k_mask_up(const float* __restrict__ mchild, long long n_oct,
 
 __global__ void k_mask_dense(const float* __restrict__ mf, int lgf, float* __restrict__ mc) {
   const int lgc = lgf - 1, Nc = 1 << lgc;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (1LL << (3 * lgc))) return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (1u << (3 * lgc))) return;
   const int K = (int)(t & (Nc - 1)), J = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
   float s = 0.f;
   for (int q = 0; q < 8; ++q)
@@ -1358,11 +1366,9 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
   const float mthr = (float)g.mask_thres;
   TreeView T = tree_view(A);
   const double* up = Lv - 1 == 0 ? H.L[0].u : A->L[Lv - 1].u;
-  k_ghosts<<<nblocks(24 * F.n_oct, BS), BS, 0, c->s>>>(F.n_oct, Lv, T, F.nbr, up,
-                                                       g.prolong_linear, F.ghost, F.ghostE,
-                                                       F.ghost32, F.ghostE32);
-  k_ghost_pack<<<nblocks(24 * F.n_oct, BS), BS, 0, c->s>>>(F.ghost, F.ghostE, 24 * F.n_oct,
-                                                          F.ghostUE32);
+  k_ghosts<<<nblocks(6 * F.n_oct, BS), BS, 0, c->s>>>(F.n_oct, Lv, T, F.nbr, up,
+                                                      g.prolong_linear, F.ghost, F.ghostE,
+                                                      F.ghost32, F.ghostE32, F.ghostUE32);
   c->launches += 1;
   k_init_level<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.ncell, F.pcell, F.pnbr, up,
                                                       g.prolong_linear, F.w, F.wE,
@@ -1405,7 +1411,12 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
   SolveCtx S{c, A, m, Lv, mthr, 0};
   if (g.profile) prof_reserve_public(c, 64);
   double hs[3];
-  TRY(level_norm<double>(S, hs));
+  // initial norms (the reference ||f|| and whether to iterate at all): FP32
+  // arrays in the mixed form, whose FP64 residual decides convergence below
+  if (mixed)
+    TRY(level_norm<float>(S, hs));
+  else
+    TRY(level_norm<double>(S, hs));
   const double fn = std::sqrt(hs[2]), r0 = std::sqrt(hs[0]);
   const double ref = fn > 0.0 ? fn : r0;
   const double target = g.tol_rel * ref;

@@ -72,8 +72,9 @@ struct BArgs {
 
 namespace {
 
-__device__ __forceinline__ long long cidx(int i, int j, int k, int lg) {
-  return ((((long long)i << lg) + j) << lg) + k;
+// linear index of (i, j, k) on an N = 2^lg grid (N <= 1024: fits 32 bits)
+__device__ __forceinline__ unsigned cidx(int i, int j, int k, int lg) {
+  return ((((unsigned)i << lg) + (unsigned)j) << lg) + (unsigned)k;
 }
 
 // bounded software grid barrier; false when a wait gave up

@@ -19,8 +19,9 @@ namespace {
 
 constexpr int BS = 256;
 
-__device__ __forceinline__ long long cidx(int i, int j, int k, int lg) {
-  return ((((long long)i << lg) + j) << lg) + k;
+// linear index of (i, j, k) on an N = 2^lg grid (N <= 1024: fits 32 bits)
+__device__ __forceinline__ unsigned cidx(int i, int j, int k, int lg) {
+  return ((((unsigned)i << lg) + (unsigned)j) << lg) + (unsigned)k;
 }
 
 struct ModelF {
@@ -39,7 +40,7 @@ struct Pair {
   float km, kp;  // u[k0-1], u[k1+1]
 };
 
-__device__ __forceinline__ Pair load_pair(const float* __restrict__ u, long long rowbase, int kp,
+__device__ __forceinline__ Pair load_pair(const float* __restrict__ u, unsigned rowbase, int kp,
                                           int np, int lane) {
   const float2* u2 = reinterpret_cast<const float2*>(u + rowbase);
   Pair p;
@@ -58,20 +59,20 @@ __device__ __forceinline__ Pair load_pair(const float* __restrict__ u, long long
 __global__ void __launch_bounds__(BS) k_sweep32(float* __restrict__ u, const float* __restrict__ f,
                                                 int lg, int colour, ModelF m, float ih2,
                                                 float cap) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = 1 << lg, M = N - 1, np = N >> 1;
-  const bool live = t < (1LL << (3 * lg - 1));
-  const long long tt = live ? t : 0;
+  const bool live = t < (1u << (3 * lg - 1));
+  const unsigned tt = live ? t : 0;
   const int kp = (int)(tt & (np - 1));
-  const long long rr = tt >> (lg - 1);
+  const unsigned rr = tt >> (lg - 1);
   const int j = (int)(rr & M), i = (int)(rr >> lg);
-  const long long row = cidx(i, j, 0, lg);
+  const unsigned row = cidx(i, j, 0, lg);
   const int lane = threadIdx.x & 31;
   Pair p = load_pair(u, row, kp, np, lane);
   if (!live) return;
   const int odd = (i + j + colour) & 1;  // active cell is k0 + odd
   const float2* u2 = reinterpret_cast<const float2*>(u);
-  const long long q = row / 2 + kp;
+  const unsigned q = row / 2 + kp;
   const float2 a = u2[cidx((i - 1) & M, j, 0, lg) / 2 + kp];
   const float2 b = u2[cidx((i + 1) & M, j, 0, lg) / 2 + kp];
   const float2 c = u2[cidx(i, (j - 1) & M, 0, lg) / 2 + kp];
@@ -145,14 +146,14 @@ __global__ void __launch_bounds__(BS) k_restrict32(const float* __restrict__ u,
                                                    float* __restrict__ uc, float* __restrict__ ucold,
                                                    float* __restrict__ fc, ModelF m, float ih2) {
   const int lgc = lgf - 1, Nc = 1 << lgc;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (1LL << (3 * lgc))) return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (1u << (3 * lgc))) return;
   const int K = (int)(t & (Nc - 1)), J = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
   float su = 0.f, sr = 0.f;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int i = 2 * I + (q >> 2), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q & 1);
-    const long long c = cidx(i, j, k, lgf);
+    const unsigned c = cidx(i, j, k, lgf);
     su += u[c];
     sr += f[c] - Lpoint32(u, i, j, k, lgf, m, ih2);
   }
@@ -164,8 +165,8 @@ __global__ void __launch_bounds__(BS) k_restrict32(const float* __restrict__ u,
 __global__ void __launch_bounds__(BS) k_fas_rhs32(const float* __restrict__ u, float* __restrict__ f,
                                                   int lg, ModelF m, float ih2) {
   const int N = 1 << lg;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (1LL << (3 * lg))) return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (1u << (3 * lg))) return;
   const int k = (int)(t & (N - 1)), j = (int)((t >> lg) & (N - 1)), i = (int)(t >> (2 * lg));
   f[t] += Lpoint32(u, i, j, k, lg, m, ih2);
 }
@@ -176,12 +177,12 @@ __global__ void __launch_bounds__(BS) k_prolong32(float* __restrict__ u, const f
                                                   const float* __restrict__ ucold, int lgf,
                                                   int linear) {
   const int N = 1 << lgf, lgc = lgf - 1, Mc = (N >> 1) - 1;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (1LL << (3 * lgf))) return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (1u << (3 * lgf))) return;
   const int k = (int)(t & (N - 1)), j = (int)((t >> lgf) & (N - 1)), i = (int)(t >> (2 * lgf));
   const int I = i >> 1, J = j >> 1, K = k >> 1;
   auto corr = [&](int a, int b, int c) {
-    const long long q = cidx(a & Mc, b & Mc, c & Mc, lgc);
+    const unsigned q = cidx(a & Mc, b & Mc, c & Mc, lgc);
     return ucold ? uc[q] - ucold[q] : uc[q];
   };
   float v = corr(I, J, K);
@@ -235,8 +236,8 @@ __global__ void __launch_bounds__(BS) k_norm32(const float* __restrict__ u, cons
                                                double* __restrict__ partials) {
   double ss = 0.0, mx = 0.0;
   const int N = 1 << lg;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += gridDim.x * blockDim.x) {
     const int k = (int)(t & (N - 1)), j = (int)((t >> lg) & (N - 1)), i = (int)(t >> (2 * lg));
     const double r = (double)(f[t] - Lpoint32(u, i, j, k, lg, m, ih2));
     ss = fma(r, r, ss);
@@ -246,13 +247,13 @@ __global__ void __launch_bounds__(BS) k_norm32(const float* __restrict__ u, cons
 }
 
 __global__ void k_from64(const double* __restrict__ x, float* __restrict__ y, long long n) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) y[t] = (float)x[t];
 }
 
 __global__ void k_to64(const float* __restrict__ u32, double* __restrict__ u, double* __restrict__ E,
                        long long n) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const double v = (double)u32[t];
   u[t] = v;
@@ -273,12 +274,12 @@ __global__ void __launch_bounds__(BS) k_resid64(const double* __restrict__ u,
                                                 float* __restrict__ u32, float* __restrict__ e32,
                                                 double* __restrict__ partials) {
   const int N = 1 << lg, M = N - 1;
-  const long long n = 1LL << (3 * lg);
+  const unsigned n = 1u << (3 * lg);
   double ss = 0.0, mx = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += gridDim.x * blockDim.x) {
     const int k = (int)(t & M), j = (int)((t >> lg) & M), i = (int)(t >> (2 * lg));
-    const long long nb[6] = {cidx((i - 1) & M, j, k, lg), cidx((i + 1) & M, j, k, lg),
+    const unsigned nb[6] = {cidx((i - 1) & M, j, k, lg), cidx((i + 1) & M, j, k, lg),
                              cidx(i, (j - 1) & M, k, lg), cidx(i, (j + 1) & M, k, lg),
                              cidx(i, j, (k - 1) & M, lg), cidx(i, j, (k + 1) & M, lg)};
     const double uc = u[t], Ec = E[t];
@@ -333,14 +334,14 @@ __device__ __forceinline__ void nb6(const float* __restrict__ x, int i, int j, i
 __global__ void __launch_bounds__(BS) k_lin_sweep(float* __restrict__ e, const float* __restrict__ r,
                                                   const float* __restrict__ u, int lg, int colour,
                                                   ModelF m, float ih2) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = 1 << lg, M = N - 1;
-  if (t >= (1LL << (3 * lg - 1))) return;
+  if (t >= (1u << (3 * lg - 1))) return;
   const int k2 = (int)(t & ((N >> 1) - 1));
-  const long long rr = t >> (lg - 1);
+  const unsigned rr = t >> (lg - 1);
   const int j = (int)(rr & M), i = (int)(rr >> lg);
   const int k = 2 * k2 + ((i + j + colour) & 1);
-  const long long c = cidx(i, j, k, lg);
+  const unsigned c = cidx(i, j, k, lg);
   float un[6], en[6];
   nb6(u, i, j, k, lg, un);
   nb6(e, i, j, k, lg, en);
@@ -358,14 +359,14 @@ __global__ void __launch_bounds__(BS) k_lin_restrict(const float* __restrict__ e
                                                      float* __restrict__ ec, float* __restrict__ rc,
                                                      float* __restrict__ uc, ModelF m, float ih2) {
   const int lgc = lgf - 1, Nc = 1 << lgc;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (1LL << (3 * lgc))) return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (1u << (3 * lgc))) return;
   const int K = (int)(t & (Nc - 1)), J = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
   float su = 0.f, sr = 0.f;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int i = 2 * I + (q >> 2), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q & 1);
-    const long long c = cidx(i, j, k, lgf);
+    const unsigned c = cidx(i, j, k, lgf);
     float un[6], en[6];
     nb6(u, i, j, k, lgf, un);
     nb6(e, i, j, k, lgf, en);
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(64) k_lin_coarse(float* __restrict__ eg, const
 
 __global__ void k_apply_corr(double* __restrict__ u, double* __restrict__ E,
                              const float* __restrict__ e, long long n, double cap) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const double d = fmin(fmax((double)e[t], -cap), cap);
   const double v = u[t] + d;
@@ -418,7 +419,7 @@ __global__ void k_apply_corr(double* __restrict__ u, double* __restrict__ E,
 }
 
 __global__ void k_zero(float* __restrict__ x, long long n) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) x[t] = 0.f;
 }
 

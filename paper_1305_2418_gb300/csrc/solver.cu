@@ -435,9 +435,13 @@ mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stat
   DenseLevel& L0 = H.L[0];
   const mgfr_config& g = c->cfg;
   double* hs = c->host_scal;
+  // ||f|| in FP64 (a sum of squares); the initial residual, which only decides
+  // whether to iterate, from the FP32 copies the V-cycles start from
   f64::norm(L0.f, L0.n, H.partials, H.nparts, H.scal + 2, c->s);
-  f64::resid_norm(L0, m, H.partials, H.nparts, H.scal, c->s);
-  c->launches += 4;
+  f32::from64(L0.f, L0.f32, L0.n, c->s);
+  f32::from64(L0.u, L0.u32, L0.n, c->s);
+  f32::norm32(L0, m, H.partials, H.nparts, H.scal, c->s);
+  c->launches += 6;
   MG_CK(c, cudaMemcpyAsync(hs, H.scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
   mgfr_status rs = sync_read(c);
   if (rs != MGFR_OK) return rs;
@@ -487,9 +491,6 @@ mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stat
   }
   int vc = 0, outer = 0;
   double r = r0;
-  f32::from64(L0.f, L0.f32, L0.n, c->s);
-  f32::from64(L0.u, L0.u32, L0.n, c->s);
-  c->launches += 2;
   // Phases alternate: A until it reaches mixed_switch or stalls, then B while
   // the FP64 residual keeps falling; a rise in B sends the iterate back to A.
   for (int round = 0; round < 8 && r > target; ++round) {
