@@ -484,7 +484,7 @@ static void free_level(AmrLevel& L) {
   void* ps[] = {L.son,  L.refined, L.count,  L.opos, L.pcell,   L.nbr,     L.mass,
                 L.w,    L.wE,      L.wf,     L.wold, L.mask,    L.ghost,   L.ghostE,
                 L.acc,  L.pnbr,    L.w32,    L.wE32, L.wf32,    L.wold32,  L.ghost32,
-                L.ghostE32, L.ghostUE32, L.olist};
+                L.olist};
   for (void* p : ps)
     if (p) cudaFree(p);
   // u, E, f of level >= 1 are owned here too
@@ -555,7 +555,7 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
   L.nbr = nullptr; L.mass = nullptr; L.w = nullptr; L.wE = nullptr; L.wf = nullptr;
   L.wold = nullptr; L.mask = nullptr; L.ghost = nullptr; L.ghostE = nullptr; L.acc = nullptr;
   L.pnbr = nullptr; L.w32 = nullptr; L.wE32 = nullptr; L.wf32 = nullptr; L.wold32 = nullptr;
-  L.ghost32 = nullptr; L.ghostE32 = nullptr; L.ghostUE32 = nullptr; L.olist = nullptr;
+  L.ghost32 = nullptr; L.olist = nullptr;
   TRY(grow(c, &L.son, n));
   TRY(grow(c, &L.refined, n));
   TRY(grow(c, &L.count, n));
@@ -572,8 +572,6 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
   if (l > 0) {
     TRY(grow(c, &L.pnbr, 6 * no));
     TRY(grow(c, &L.ghost32, 24 * no));
-    TRY(grow(c, &L.ghostE32, 24 * no));
-    TRY(grow(c, &L.ghostUE32, 24 * no));
     TRY(grow(c, &L.olist, no));
     TRY(grow(c, &L.opos, no));
     TRY(grow(c, &L.pcell, no));

@@ -35,8 +35,7 @@ struct AmrLevel {
   int* pnbr = nullptr;                // [n_oct*6] parent's face-neighbour cells (-1: none)
   // FP32 work arrays (mixed precision phase of the level solves)
   float *w32 = nullptr, *wE32 = nullptr, *wf32 = nullptr, *wold32 = nullptr;
-  float *ghost32 = nullptr, *ghostE32 = nullptr;
-  float2* ghostUE32 = nullptr;        // [n_oct*24] interleaved (u, E) ghost pairs
+  float* ghost32 = nullptr;           // [n_oct*24] FP32 ghost u (e^u recomputed)
   long long relaxed = 0;              // cells relaxed in the current level solve
   int* olist = nullptr;               // [n_oct] octs with a relaxed cell (coarse level of a solve)
   long long n_list = 0;               // entries of olist in use

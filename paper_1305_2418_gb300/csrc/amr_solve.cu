@@ -52,6 +52,18 @@ struct NB {
   T u, E;
 };
 
+// e^u at slot q.  The FP64 oct arrays store E = e^u beside u; the FP32 oct
+// arrays carry u only and e^u is recomputed by the SFU where it is needed
+// (a stored FP32 E would add a read and a write stream to every sweep).
+__device__ __forceinline__ double Eat(const double* __restrict__ E, const double* __restrict__,
+                                      long long q) {
+  return E[q];
+}
+__device__ __forceinline__ float Eat(const float* __restrict__, const float* __restrict__ u,
+                                     long long q) {
+  return __expf(u[q]);
+}
+
 // neighbour of cell (o, ch) in direction d: same oct, neighbouring oct, or
 // the ghost slot of that face.
 template <class T>
@@ -63,17 +75,17 @@ __device__ __forceinline__ NB<T> onb(const T* __restrict__ u, const T* __restric
   const int chn = ch ^ (1 << (2 - ax));
   if (bit != plus) {
     const long long q = 8 * o + chn;
-    return NB<T>{u[q], E[q]};
+    return NB<T>{u[q], Eat(E, u, q)};
   }
   const int no = nbr[6 * o + d];
   if (no >= 0) {
     const long long q = 8LL * no + chn;
-    return NB<T>{u[q], E[q]};
+    return NB<T>{u[q], Eat(E, u, q)};
   }
   const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
   const int qi = (((ch >> (2 - t1)) & 1) << 1) | ((ch >> (2 - t2)) & 1);
   const long long g = 24 * o + 4 * d + qi;
-  return NB<T>{gh[g], ghE[g]};
+  return NB<T>{gh[g], Eat(ghE, gh, g)};
 }
 
 // L_i (Sec. 3.2) from the centre and its six neighbours
@@ -122,9 +134,9 @@ __global__ void __launch_bounds__(BS) k_osweep(T* __restrict__ u, T* __restrict_
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
   const T uc = u[c];
-  const T un = uc - newton(uc, E[c], nb, f[c], m, ih2, cap);
+  const T un = uc - newton(uc, Eat(E, u, c), nb, f[c], m, ih2, cap);
   u[c] = un;
-  E[c] = ex(un);
+  if constexpr (std::is_same<T, double>::value) E[c] = ex(un);
 }
 
 // restrict oct level to its parents: u average, masked residual average
@@ -146,7 +158,7 @@ __global__ void __launch_bounds__(BS) k_orestrict(
       NB<T> nb[6];
 #pragma unroll
       for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
-      sr += f[c] - Lval(u[c], E[c], nb, m, ih2);
+      sr += f[c] - Lval(u[c], Eat(E, u, c), nb, m, ih2);
     }
   }
   const int p = pcell[o];
@@ -174,7 +186,7 @@ __global__ void __launch_bounds__(BS) k_ofas(const T* __restrict__ u, const T* _
   NB<T> nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
-  f[c] += Lval(u[c], E[c], nb, m, ih2);
+  f[c] += Lval(u[c], Eat(E, u, c), nb, m, ih2);
 }
 
 // u += P(uc - ucold) on relaxed cells (eq. fine_correction), the parent's
@@ -206,7 +218,7 @@ __global__ void __launch_bounds__(BS) k_oprolong(long long ncell, const int* __r
   }
   const T un = u[c] + v;
   u[c] = un;
-  E[c] = ex(un);
+  if constexpr (std::is_same<T, double>::value) E[c] = ex(un);
 }
 
 // residual norms of level L (sum r^2, max |r|, sum f^2), accumulated in FP64
@@ -224,7 +236,7 @@ __global__ void __launch_bounds__(BS) k_onorm(const T* __restrict__ u, const T* 
     NB<T> nb[6];
 #pragma unroll
     for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
-    const double r = (double)(f[c] - Lval(u[c], E[c], nb, m, ih2));
+    const double r = (double)(f[c] - Lval(u[c], Eat(E, u, c), nb, m, ih2));
     ss = fma(r, r, ss);
     mx = fmax(mx, fabs(r));
     fs = fma((double)f[c], (double)f[c], fs);
@@ -461,7 +473,7 @@ __global__ void __launch_bounds__(BS) k_oresid_lin(
     const double* __restrict__ u, const double* __restrict__ E, const double* __restrict__ f,
     const int* __restrict__ nbr, const double* __restrict__ gh, const double* __restrict__ ghE,
     long long ncell, MT<double> m, double ih2, float* __restrict__ r32, float* __restrict__ u32,
-    float* __restrict__ E32, float* __restrict__ e32, double* __restrict__ partials) {
+    float* __restrict__ e32, double* __restrict__ partials) {
   double ss = 0.0, mx = 0.0, fs = 0.0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
@@ -473,7 +485,6 @@ __global__ void __launch_bounds__(BS) k_oresid_lin(
     const double r = f[c] - Lval(u[c], E[c], nb, m, ih2);
     r32[c] = (float)r;
     u32[c] = (float)u[c];
-    E32[c] = (float)E[c];
     e32[c] = 0.f;
     ss = fma(r, r, ss);
     mx = fmax(mx, fabs(r));
@@ -523,7 +534,7 @@ __global__ void __launch_bounds__(BS) k_olin_restrict(
       NB<float> nb[6];
 #pragma unroll
       for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
-      const JR J = jrow(u[c], E[c], nb, m, ih2);
+      const JR J = jrow(u[c], Eat(E, u, c), nb, m, ih2);
       float Je = J.diag * e[c];
 #pragma unroll
       for (int d = 0; d < 6; ++d) Je = fmaf(J.off[d], onb_e(e, nbr, o, ch, d), Je);
@@ -715,19 +726,25 @@ __device__ __forceinline__ int face_q(int ch, int ax) {
   return (((ch >> (2 - t1)) & 1) << 1) | ((ch >> (2 - t2)) & 1);
 }
 
-// LIN = true : Gauss-Seidel on J(u) e = r  (arrays u, E fixed; e updated)
-// LIN = false: Newton-Gauss-Seidel on L(u) = f (u, E updated)
+// LIN = true : Gauss-Seidel on J(u) e = r  (u fixed; e updated)
+// LIN = false: Newton-Gauss-Seidel on L(u) = f (u updated)
+// e^u of the oct and of the face neighbours is recomputed by the SFU from u,
+// so a half-sweep streams u (and e), f or r, the neighbour table and the FP32
+// ghost u of faces without a neighbouring oct, and writes one array.
 template <bool LIN, int COL>
 __global__ void __launch_bounds__(BS) k_oct_sweep32(
-    float* __restrict__ u, float* __restrict__ E, float* __restrict__ e,
-    const float* __restrict__ rf, const int* __restrict__ nbr, const float2* __restrict__ ghUE,
-    const float* __restrict__ mask, float mthr, long long n_oct, const int* __restrict__ olist,
-    MT<float> m, float ih2, float cap) {
+    float* __restrict__ u, float* __restrict__ e, const float* __restrict__ rf,
+    const int* __restrict__ nbr, const float* __restrict__ gh, const float* __restrict__ mask,
+    float mthr, long long n_oct, const int* __restrict__ olist, MT<float> m, float ih2,
+    float cap) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n_oct) return;
   const long long o = olist ? olist[t] : t;
   constexpr int CC[2][4] = {{0, 3, 5, 6}, {1, 2, 4, 7}};
-  const Oct8 U = ld8(u, o), EE = ld8(E, o), R = ld8(rf, o);
+  const Oct8 U = ld8(u, o), R = ld8(rf, o);
+  Oct8 EE;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) EE.v[i] = __expf(U.v[i]);
   Oct8 X = LIN ? ld8(e, o) : U;  // LIN: correction; else unused copy
   bool act[4];
   float s1[4], s2[4], s3[4];  // LIN: (sum off*e, diag sum, -); NL: (sum b du, sum du, sum b)
@@ -757,36 +774,32 @@ __global__ void __launch_bounds__(BS) k_oct_sweep32(
   for (int d = 0; d < 6; ++d) {
     const int a = d >> 1, plus = d & 1;
     const int no = nbr[6 * o + d];
-    Oct8 NU, NE, NX;
-    float2 G[4];
+    Oct8 NU, NX;
+    float G[4];
     if (no >= 0) {
       NU = ld8(u, no);
-      NE = ld8(E, no);
       if (LIN) NX = ld8(e, no);
     } else {
-      const float4* gp = reinterpret_cast<const float4*>(ghUE + 24 * o + 4 * d);
-      const float4 g0 = gp[0], g1 = gp[1];
-      G[0] = make_float2(g0.x, g0.y);
-      G[1] = make_float2(g0.z, g0.w);
-      G[2] = make_float2(g1.x, g1.y);
-      G[3] = make_float2(g1.z, g1.w);
+      const float4 g = *reinterpret_cast<const float4*>(gh + 24 * o + 4 * d);
+      G[0] = g.x;
+      G[1] = g.y;
+      G[2] = g.z;
+      G[3] = g.w;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int ch = CC[COL][q];
       if (((ch >> (2 - a)) & 1) != plus) continue;  // not on this face
-      float un, En, xn;
+      float un, xn;
       if (no >= 0) {
         const int cn = ch ^ (1 << (2 - a));
         un = NU.v[cn];
-        En = NE.v[cn];
         xn = LIN ? NX.v[cn] : 0.f;
       } else {
-        const float2 g = G[face_q(ch, a)];
-        un = g.x;
-        En = g.y;
+        un = G[face_q(ch, a)];
         xn = 0.f;
       }
+      const float En = __expf(un);
       const float du = un - U.v[ch];
       if (LIN) {
         s1[q] = fmaf(0.5f * ih2 * fmaf(En, du, EE.v[ch] + En), xn, s1[q]);
@@ -799,7 +812,7 @@ __global__ void __launch_bounds__(BS) k_oct_sweep32(
       }
     }
   }
-  Oct8 UO = U, EO = EE;
+  Oct8 UO = U;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     if (!act[q]) continue;
@@ -814,15 +827,12 @@ __global__ void __launch_bounds__(BS) k_oct_sweep32(
       float step = __fdividef(L - R.v[ch], dL);
       step = fminf(fmaxf(step, -cap), cap);
       UO.v[ch] = U.v[ch] - step;
-      EO.v[ch] = __expf(UO.v[ch]);
     }
   }
-  if (LIN) {
+  if (LIN)
     st8(e, o, X);
-  } else {
+  else
     st8(u, o, UO);
-    st8(E, o, EO);
-  }
 }
 
 // ---- set-up kernels --------------------------------------------------------
@@ -831,7 +841,7 @@ __global__ void __launch_bounds__(BS) k_oct_sweep32(
 __global__ void k_init_level(long long ncell, const int* __restrict__ pcell,
                              const int* __restrict__ pnbr, const double* __restrict__ up,
                              int linear, double* __restrict__ w, double* __restrict__ wE,
-                             float* __restrict__ w32, float* __restrict__ wE32) {
+                             float* __restrict__ w32) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= ncell) return;
   const long long o = c >> 3;
@@ -844,11 +854,11 @@ __global__ void k_init_level(long long ncell, const int* __restrict__ pcell,
       v += (((ch >> (2 - ax)) & 1) ? 0.125 : -0.125) * (up[pp] - up[pm]);
     }
   }
-  w[c] = v;
-  wE[c] = exp(v);
   if (w32) {
-    w32[c] = (float)v;
-    wE32[c] = __expf((float)v);
+    w32[c] = (float)v;  // mixed form: the FP64 iterate is taken from w32 later
+  } else {
+    w[c] = v;
+    wE[c] = exp(v);
   }
 }
 
@@ -858,12 +868,10 @@ __global__ void k_init_level(long long ncell, const int* __restrict__ pcell,
 // normal, so P and its six neighbours are looked up once per face.  A ghost is
 // P's value plus, per axis, s (c+ - c-)/8, s = +1 or -1 for the ghost's
 // high or low daughter position in P (a component is 0 where one of P's
-// neighbours does not exist).  Written as FP64 (u, e^u), FP32 copies and
-// interleaved FP32 (u, E) pairs.
+// neighbours does not exist).  Written as FP64 (u, e^u) and FP32 u.
 __global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restrict__ nbr,
                          const double* __restrict__ up, int linear, double* __restrict__ ghost,
-                         double* __restrict__ ghostE, float* __restrict__ g32,
-                         float* __restrict__ gE32, float2* __restrict__ ghUE) {
+                         double* __restrict__ ghostE, float* __restrict__ g32) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= 6 * n_oct) return;
   const long long o = t / 6;
@@ -905,12 +913,9 @@ __global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restri
     for (int a = 0; a < 3; ++a)
       if (have[a]) v += (hi[a] ? 0.125 : -0.125) * g[a];
     const long long q = 24 * o + 4 * d + qi;
-    const double E = exp(v);
     ghost[q] = v;
-    ghostE[q] = E;
+    ghostE[q] = exp(v);
     g32[q] = (float)v;
-    gE32[q] = __expf((float)v);
-    ghUE[q] = make_float2((float)v, (float)E);
   }
 }
 
@@ -1007,7 +1012,7 @@ TA<double> tarr<double>(AmrLevel& L) {
 }
 template <>
 TA<float> tarr<float>(AmrLevel& L) {
-  return TA<float>{L.w32, L.wE32, L.wf32, L.wold32, L.ghost32, L.ghostE32};
+  return TA<float>{L.w32, L.wE32, L.wf32, L.wold32, L.ghost32, nullptr};
 }
 
 // work arrays of dense level k of the hierarchy below the base (k >= 1)
@@ -1058,11 +1063,11 @@ void relax(SolveCtx& S, int l, int sweeps) {
           const float* mk = l == S.L ? nullptr : L.mask;
           if (col == 0)
             k_oct_sweep32<false, 0><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-                L.w32, L.wE32, nullptr, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, R.n, R.list, m,
+                L.w32, nullptr, L.wf32, L.nbr, L.ghost32, mk, S.mthr, R.n, R.list, m,
                 (float)L.ih2, (float)g.step_cap);
           else
             k_oct_sweep32<false, 1><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-                L.w32, L.wE32, nullptr, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, R.n, R.list, m,
+                L.w32, nullptr, L.wf32, L.nbr, L.ghost32, mk, S.mthr, R.n, R.list, m,
                 (float)L.ih2, (float)g.step_cap);
         } else {
           k_osweep<T><<<nblocks(4 * R.n, BS), BS, 0, c->s>>>(
@@ -1232,11 +1237,11 @@ void lin_relax(SolveCtx& S, int l, int sweeps) {
         if (l == S.L) prof_begin(c, 4, L.ncell);
         if (col == 0)
           k_oct_sweep32<true, 0><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-              L.w32, L.wE32, L.wold32, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, R.n, R.list, m,
+              L.w32, L.wold32, L.wf32, L.nbr, L.ghost32, mk, S.mthr, R.n, R.list, m,
               (float)L.ih2, 0.f);
         else
           k_oct_sweep32<true, 1><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-              L.w32, L.wE32, L.wold32, L.wf32, L.nbr, L.ghostUE32, mk, S.mthr, R.n, R.list, m,
+              L.w32, L.wold32, L.wf32, L.nbr, L.ghost32, mk, S.mthr, R.n, R.list, m,
               (float)L.ih2, 0.f);
         if (l == S.L) prof_end(c);
       } else
@@ -1297,7 +1302,7 @@ void lin_vcycle_tree(SolveCtx& S, int l) {
     const ORange R = orange(S, F, l);
     if (R.n > 0)
       k_olin_restrict<<<nblocks(R.n, BS), BS, 0, c->s>>>(
-          F.wold32, F.wf32, F.w32, F.wE32, F.nbr, F.ghost32, F.ghostE32, fmask, S.mthr, R.n,
+          F.wold32, F.wf32, F.w32, F.wE32, F.nbr, F.ghost32, nullptr, fmask, S.mthr, R.n,
           R.list, F.pcell, m, (float)F.ih2, P.wf32, P.w32, P.wE32, P.wold32);
     c->launches += 1;
     lin_vcycle_tree(S, l - 1);
@@ -1330,7 +1335,7 @@ mgfr_status lin_resid(SolveCtx& S, double* hs) {
   const int nparts = (int)std::min<long long>(H.nparts / 2, nblocks(L.ncell, BS));
   if (c->capturing >= 0) prof_begin(c, 2, L.ncell);
   k_oresid_lin<<<nparts, BS, 0, c->s>>>(L.w, L.wE, L.wf, L.nbr, L.ghost, L.ghostE, L.ncell,
-                                        mt<double>(S.m), L.ih2, L.wf32, L.w32, L.wE32, L.wold32,
+                                        mt<double>(S.m), L.ih2, L.wf32, L.w32, L.wold32,
                                         H.partials);
   if (c->capturing >= 0) prof_end(c);
   k_finish3<<<1, 256, 0, c->s>>>(H.partials, nparts, H.scal + 8);
@@ -1368,11 +1373,11 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
   const double* up = Lv - 1 == 0 ? H.L[0].u : A->L[Lv - 1].u;
   k_ghosts<<<nblocks(6 * F.n_oct, BS), BS, 0, c->s>>>(F.n_oct, Lv, T, F.nbr, up,
                                                       g.prolong_linear, F.ghost, F.ghostE,
-                                                      F.ghost32, F.ghostE32, F.ghostUE32);
+                                                      F.ghost32);
   c->launches += 1;
   k_init_level<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.ncell, F.pcell, F.pnbr, up,
                                                       g.prolong_linear, F.w, F.wE,
-                                                      mixed ? F.w32 : nullptr, F.wE32);
+                                                      mixed ? F.w32 : nullptr);
   MG_CK(c, cudaMemcpyAsync(F.wf, F.f, sizeof(double) * (size_t)F.ncell, cudaMemcpyDeviceToDevice,
                            c->s));
   k_fill_f<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.mask, F.ncell, 1.f);
@@ -1382,19 +1387,32 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
     c->launches += 1;
   }
   F.relaxed = F.ncell;
+  // FP64 work copies of the coarser levels: set up front in the FP64 form; in
+  // the mixed form only the FP64 fallback V-cycles below need them
+  auto fp64_coarse = [&]() -> mgfr_status {
+    for (int l = Lv - 1; l >= 0; --l) {
+      AmrLevel& P = A->L[l];
+      const double* uu = l == 0 ? H.L[0].u : P.u;
+      const double* EE = l == 0 ? H.L[0].E : P.E;
+      const size_t b8 = sizeof(double) * (size_t)P.ncell;
+      MG_CK(c, cudaMemcpyAsync(P.w, uu, b8, cudaMemcpyDeviceToDevice, c->s));
+      MG_CK(c, cudaMemcpyAsync(P.wE, EE, b8, cudaMemcpyDeviceToDevice, c->s));
+      MG_CK(c, cudaMemcpyAsync(P.wold, uu, b8, cudaMemcpyDeviceToDevice, c->s));
+    }
+    return MGFR_OK;
+  };
+  if (!mixed) TRY(fp64_coarse());
   for (int l = Lv - 1; l >= 0; --l) {
     AmrLevel& P = A->L[l];
     const double* uu = l == 0 ? H.L[0].u : P.u;
-    const double* EE = l == 0 ? H.L[0].E : P.E;
-    const size_t b8 = sizeof(double) * (size_t)P.ncell;
-    MG_CK(c, cudaMemcpyAsync(P.w, uu, b8, cudaMemcpyDeviceToDevice, c->s));
-    MG_CK(c, cudaMemcpyAsync(P.wE, EE, b8, cudaMemcpyDeviceToDevice, c->s));
-    MG_CK(c, cudaMemcpyAsync(P.wold, uu, b8, cudaMemcpyDeviceToDevice, c->s));
     if (mixed) {
       k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(uu, P.w32, P.ncell);
-      k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(EE, P.wE32, P.ncell);
       k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(uu, P.wold32, P.ncell);
-      c->launches += 3;
+      c->launches += 2;
+      if (l == 0) {  // the dense kernels of the base level read a stored FP32 e^u
+        k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(H.L[0].E, P.wE32, P.ncell);
+        c->launches += 1;
+      }
     }
     MG_CK(c, cudaMemsetAsync(P.mask, 0, sizeof(float) * (size_t)P.ncell, c->s));
     AmrLevel& Ch = A->L[l + 1];
@@ -1464,6 +1482,12 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
       rprev = r;
     }
   }
+  if (mixed && !(r > target) && it32 == 0) {
+    // converged at the start: the FP64 iterate is the FP32 initial guess
+    k_f2d_exp<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.w32, F.w, F.wE, F.ncell);
+    c->launches += 1;
+  }
+  if (mixed && r > target) TRY(fp64_coarse());
   while (r > target && it < g.max_vcycles) {
     TRY(run_vcycle<double>(S, st, hs));
     r = std::sqrt(hs[0]);
