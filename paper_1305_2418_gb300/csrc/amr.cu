@@ -21,6 +21,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "amr.cuh"
@@ -210,14 +211,42 @@ struct LevelPtrs {
 };
 
 struct GatherPtrs {
-  const double* acc[AMR_MAXL];  // level 0: [3][N0^3]; l >= 1: [ncell][3]
+  const double* acc[AMR_MAXL];    // FP64: level 0 [3][N0^3]; l >= 1 [ncell][3]
+  const float4* acc32[AMR_MAXL];  // FP32 (mixed form): [ncell] (x, y, z, 0)
   long long n0;
 };
 
-template <bool GATHER>
-__device__ __forceinline__ void touch(int lev, long long c, double w, LevelPtrs& D,
-                                      const GatherPtrs& G, double* out) {
-  if (GATHER) {
+// Weight arithmetic of the traversal.  double: the integer overlap lengths
+// exactly, one scale 2^(-3F) to the fraction of the cube (deposit and the
+// FP64 gather).  float (gather of the mixed form): the top 24 bits of each
+// length relative to the cube side 2^F, scale 2^-72; the weights then carry
+// a relative error of about 2^-24.
+template <class W>
+struct Wt;
+template <>
+struct Wt<double> {
+  static __device__ __forceinline__ double len(long long v, int) { return (double)v; }
+  static __device__ __forceinline__ double scale(int F) {
+    return __longlong_as_double((long long)(1023 - 3 * F) << 52);
+  }
+};
+template <>
+struct Wt<float> {
+  static __device__ __forceinline__ float len(long long v, int F) {
+    return (float)(int)((v + (1LL << (F - 25))) >> (F - 24));  // rounded to nearest
+  }
+  static __device__ __forceinline__ float scale(int) { return 0x1p-72f; }
+};
+
+template <bool GATHER, class W>
+__device__ __forceinline__ void touch(int lev, long long c, W w, LevelPtrs& D,
+                                      const GatherPtrs& G, W* out) {
+  if constexpr (GATHER && std::is_same<W, float>::value) {
+    const float4 a = G.acc32[lev][c];
+    out[0] = fmaf(w, a.x, out[0]);
+    out[1] = fmaf(w, a.y, out[1]);
+    out[2] = fmaf(w, a.z, out[2]);
+  } else if (GATHER) {
     if (lev == 0) {
       out[0] += w * G.acc[0][c];
       out[1] += w * G.acc[0][G.n0 + c];
@@ -257,15 +286,15 @@ struct StackEnt {
 // that is refined again is split one more level in registers (DEPTH = 2) or
 // pushed on the explicit stack (DEPTH = 1).  No recursion: the stack frame
 // size is static.
-template <bool GATHER, int DEPTH>
+template <bool GATHER, class W, int DEPTH>
 __device__ __forceinline__ void split_q(const TreeView& T, int l, long long c, const long long* lo,
-                                        const long long* hi, double scale, LevelPtrs& D,
-                                        const GatherPtrs& G, double* out, StackEnt* st, int& sp,
+                                        const long long* hi, int F, W scale, LevelPtrs& D,
+                                        const GatherPtrs& G, W* out, StackEnt* st, int& sp,
                                         unsigned long long* err) {
   const int o = T.son[l][c];
   const int lc = l + 1, sh = QB - lc;
   long long clo[3][2], chi[3][2];
-  double len[3][2];
+  W len[3][2];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const long long mid = ((lo[a] >> sh) | 1LL) * (1LL << sh);
@@ -274,7 +303,7 @@ __device__ __forceinline__ void split_q(const TreeView& T, int l, long long c, c
     clo[a][1] = max(lo[a], mid);
     chi[a][1] = hi[a];
 #pragma unroll
-    for (int b = 0; b < 2; ++b) len[a][b] = (double)(chi[a][b] - clo[a][b]);
+    for (int b = 0; b < 2; ++b) len[a][b] = Wt<W>::len(chi[a][b] - clo[a][b], F);
   }
   len[0][0] *= scale;
   len[0][1] *= scale;
@@ -284,13 +313,13 @@ __device__ __forceinline__ void split_q(const TreeView& T, int l, long long c, c
     const long long cc = 8LL * o + ch;
     const bool ref = lc + 1 < T.nlev && T.son[lc][cc] >= 0;
     if (!ref) {
-      touch<GATHER>(lc, cc, len[0][b0] * len[1][b1] * len[2][b2], D, G, out);
+      touch<GATHER, W>(lc, cc, len[0][b0] * len[1][b1] * len[2][b2], D, G, out);
       continue;
     }
     const long long nlo[3] = {clo[0][b0], clo[1][b1], clo[2][b2]};
     const long long nhi[3] = {chi[0][b0], chi[1][b1], chi[2][b2]};
     if constexpr (DEPTH > 1) {
-      split_q<GATHER, DEPTH - 1>(T, lc, cc, nlo, nhi, scale, D, G, out, st, sp, err);
+      split_q<GATHER, W, DEPTH - 1>(T, lc, cc, nlo, nhi, F, scale, D, G, out, st, sp, err);
     } else {
       if (sp < 48) {
         StackEnt& n = st[sp++];
@@ -307,9 +336,9 @@ __device__ __forceinline__ void split_q(const TreeView& T, int l, long long c, c
   }
 }
 
-template <bool GATHER>
+template <bool GATHER, class W>
 __device__ void visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, const GatherPtrs& G,
-                               double* out, unsigned long long* err) {
+                               W* out, unsigned long long* err) {
   const long long X[3] = {qfix(t.x), qfix(t.y), qfix(t.z)};
   // leaf level lam of the particle and the oct holding its leaf cell
   int lam = 0, own = -1;
@@ -326,16 +355,16 @@ __device__ void visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
   const int F = QB - lam;
   const long long one = 1LL << F;
   long long cl[3], i0[3], edge[3];
-  double Lw[3][2];
-  // 2^(-3F): fixed-point volume -> fraction of the cube (a normal double)
-  const double scale = __longlong_as_double((long long)(1023 - 3 * F) << 52);
+  W Lw[3][2];
+  // fixed-point volume -> fraction of the cube
+  const W scale = Wt<W>::scale(F);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     cl[a] = X[a] - (one >> 1);
     i0[a] = cl[a] >> F;
     edge[a] = (i0[a] + 1) * one;  // boundary between the two cells the cube spans
-    Lw[a][0] = (double)(edge[a] - cl[a]);
-    Lw[a][1] = (double)(cl[a] + one - edge[a]);
+    Lw[a][0] = Wt<W>::len(edge[a] - cl[a], F);
+    Lw[a][1] = Wt<W>::len(cl[a] + one - edge[a], F);
   }
   Lw[0][0] *= scale;
   Lw[0][1] *= scale;
@@ -359,7 +388,7 @@ __device__ void visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
     }
     const bool refined = lev == lam && lam + 1 < T.nlev && T.son[lam][cq] >= 0;
     if (!refined) {
-      touch<GATHER>(lev, cq, Lw[0][bits[0]] * Lw[1][bits[1]] * Lw[2][bits[2]], D, G, out);
+      touch<GATHER, W>(lev, cq, Lw[0][bits[0]] * Lw[1][bits[1]] * Lw[2][bits[2]], D, G, out);
       continue;
     }
     long long lo[3], hi[3];
@@ -368,12 +397,12 @@ __device__ void visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
       lo[a] = bits[a] ? edge[a] : cl[a];
       hi[a] = bits[a] ? cl[a] + one : edge[a];
     }
-    split_q<GATHER, 2>(T, lam, cq, lo, hi, scale, D, G, out, st, sp, err);
+    split_q<GATHER, W, 2>(T, lam, cq, lo, hi, F, scale, D, G, out, st, sp, err);
   }
   // pieces refined three or more levels below the particle's leaf
   while (sp > 0) {
     const StackEnt e = st[--sp];
-    split_q<GATHER, 1>(T, e.l, e.c, e.lo, e.hi, scale, D, G, out, st, sp, err);
+    split_q<GATHER, W, 1>(T, e.l, e.c, e.lo, e.hi, F, scale, D, G, out, st, sp, err);
   }
 }
 
@@ -383,7 +412,7 @@ __global__ void k_deposit(const double* __restrict__ pos, long long Np, double i
   if (p >= Np) return;
   const P3 t = particle_t(pos, p, inv, N0);
   GatherPtrs G{};
-  visit_particle<false>(T, t, D, G, nullptr, err);
+  visit_particle<false, double>(T, t, D, G, nullptr, err);
 }
 
 __global__ void k_gather(const double* __restrict__ pos, long long Np, double inv, double N0,
@@ -394,10 +423,31 @@ __global__ void k_gather(const double* __restrict__ pos, long long Np, double in
   const P3 t = particle_t(pos, p, inv, N0);
   LevelPtrs D{};
   double out[3] = {0.0, 0.0, 0.0};
-  visit_particle<true>(T, t, D, G, out, err);
+  visit_particle<true, double>(T, t, D, G, out, err);
   acc[3 * p] = out[0];
   acc[3 * p + 1] = out[1];
   acc[3 * p + 2] = out[2];
+}
+
+// mixed form: FP32 weights and FP32 force fields, FP64 output
+__global__ void k_gather32(const double* __restrict__ pos, long long Np, double inv, double N0,
+                           TreeView T, GatherPtrs G, double* __restrict__ acc,
+                           unsigned long long* err) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= Np) return;
+  const P3 t = particle_t(pos, p, inv, N0);
+  LevelPtrs D{};
+  float out[3] = {0.f, 0.f, 0.f};
+  visit_particle<true, float>(T, t, D, G, out, err);
+  acc[3 * p] = out[0];
+  acc[3 * p + 1] = out[1];
+  acc[3 * p + 2] = out[2];
+}
+
+// base-level force [3][n] (FP64) -> (x, y, z, 0) per cell (FP32)
+__global__ void k_acc_pack(const double* __restrict__ acc, long long n, float4* __restrict__ a32) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < n) a32[t] = make_float4((float)acc[t], (float)acc[n + t], (float)acc[2 * n + t], 0.f);
 }
 
 // coarse cell mass = sum of its daughters (Sec. 3.1)
@@ -459,7 +509,8 @@ __global__ void k_oct_pnbrs(long long n_oct, int l, TreeView T, int* __restrict_
 // f_R and a_MG/c^2 on a refined level (central differences, ghosts at edges)
 __global__ void k_oct_force(const double* __restrict__ E, const int* __restrict__ nbr,
                             const double* __restrict__ ghostE, long long ncell, double fbar,
-                            double g_scale, double* __restrict__ fr, double* __restrict__ acc) {
+                            double g_scale, double* __restrict__ fr, double* __restrict__ acc,
+                            float4* __restrict__ acc32) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= ncell) return;
   const long long o = c >> 3;
@@ -470,6 +521,8 @@ __global__ void k_oct_force(const double* __restrict__ E, const int* __restrict_
     const double ep = oct_nbE(E, nbr, ghostE, o, ch, 2 * ax + 1);
     acc[3 * c + ax] = g_scale * (ep - em);
   }
+  if (acc32)
+    acc32[c] = make_float4((float)acc[3 * c], (float)acc[3 * c + 1], (float)acc[3 * c + 2], 0.f);
 }
 
 }  // namespace
@@ -484,7 +537,7 @@ static void free_level(AmrLevel& L) {
   void* ps[] = {L.son,  L.refined, L.count,  L.opos, L.pcell,   L.nbr,     L.mass,
                 L.w,    L.wE,      L.wf,     L.wold, L.mask,    L.ghost,   L.ghostE,
                 L.acc,  L.pnbr,    L.w32,    L.wE32, L.wf32,    L.wold32,  L.ghost32,
-                L.olist};
+                L.olist,  L.acc32};
   for (void* p : ps)
     if (p) cudaFree(p);
   // u, E, f of level >= 1 are owned here too
@@ -507,6 +560,7 @@ void amr_free(mgfr_ctx* c) {
   if (A->d_small) cudaFree(A->d_small);
   if (A->acc0) cudaFree(A->acc0);
   if (A->fr0) cudaFree(A->fr0);
+  if (A->acc0_32) cudaFree(A->acc0_32);
   delete A;
   c->amr = nullptr;
 }
@@ -555,7 +609,7 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
   L.nbr = nullptr; L.mass = nullptr; L.w = nullptr; L.wE = nullptr; L.wf = nullptr;
   L.wold = nullptr; L.mask = nullptr; L.ghost = nullptr; L.ghostE = nullptr; L.acc = nullptr;
   L.pnbr = nullptr; L.w32 = nullptr; L.wE32 = nullptr; L.wf32 = nullptr; L.wold32 = nullptr;
-  L.ghost32 = nullptr; L.olist = nullptr;
+  L.ghost32 = nullptr; L.olist = nullptr; L.acc32 = nullptr;
   TRY(grow(c, &L.son, n));
   TRY(grow(c, &L.refined, n));
   TRY(grow(c, &L.count, n));
@@ -579,6 +633,7 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
     TRY(grow(c, &L.ghost, 24 * no));
     TRY(grow(c, &L.ghostE, 24 * no));
     TRY(grow(c, &L.acc, 3 * n));
+    TRY(grow(c, &L.acc32, n));
     TRY(grow(c, &L.u, n));
     TRY(grow(c, &L.E, n));
     TRY(grow(c, &L.f, n));
@@ -707,7 +762,9 @@ mgfr_status mgfr_solve_particles(mgfr_ctx* c, const double* pos, long long Np, i
       }
     if (A->acc0) cudaFree(A->acc0);
     if (A->fr0) cudaFree(A->fr0);
+    if (A->acc0_32) cudaFree(A->acc0_32);
     A->acc0 = A->fr0 = nullptr;
+    A->acc0_32 = nullptr;
   }
   A->N0 = N0;
   A->lg0 = lg0;
@@ -718,6 +775,8 @@ mgfr_status mgfr_solve_particles(mgfr_ctx* c, const double* pos, long long Np, i
     if (!A->dmask[k]) MG_CK(c, cudaMalloc(&A->dmask[k], sizeof(float) * (size_t)H.L[k].n));
   if (!A->acc0) MG_CK(c, cudaMalloc(&A->acc0, sizeof(double) * 3 * (size_t)H.L[0].n));
   if (!A->fr0) MG_CK(c, cudaMalloc(&A->fr0, sizeof(double) * (size_t)H.L[0].n));
+  if (mixed && !A->acc0_32)
+    MG_CK(c, cudaMalloc(&A->acc0_32, sizeof(float4) * (size_t)H.L[0].n));
   auto w0 = std::chrono::steady_clock::now();
   MG_CK(c, cudaEventRecord(c->ev_in, c->user));
   MG_CK(c, cudaStreamWaitEvent(c->s, c->ev_in, 0));
@@ -761,21 +820,33 @@ mgfr_status mgfr_solve_particles(mgfr_ctx* c, const double* pos, long long Np, i
   if (fr_out)
     MG_CK(c, cudaMemcpyAsync(fr_out, A->fr0, sizeof(double) * (size_t)L0.n,
                              cudaMemcpyDeviceToDevice, c->s));
+  // the mixed form gathers FP32 copies of the force fields with FP32 weights
+  const bool g32 = mixed && acc_out;
   GatherPtrs G{};
   G.acc[0] = A->acc0;
+  G.acc32[0] = A->acc0_32;
   G.n0 = L0.n;
+  if (g32) {
+    k_acc_pack<<<nblocks(L0.n, BS), BS, 0, c->s>>>(A->acc0, L0.n, A->acc0_32);
+    c->launches += 1;
+  }
   for (int l = 1; l < A->nlev; ++l) {
     AmrLevel& L = A->L[l];
     const double gs = m.fbar / (2.0 * L.h) / (2.0 * m.a);
     k_oct_force<<<nblocks(L.ncell, BS), BS, 0, c->s>>>(L.E, L.nbr, L.ghostE, L.ncell, m.fbar, gs,
-                                                       L.w, L.acc);
+                                                       L.w, L.acc, g32 ? L.acc32 : nullptr);
     G.acc[l] = L.acc;
+    G.acc32[l] = L.acc32;
     c->launches += 1;
   }
   if (acc_out) {
     TreeView T = tree_view(A);
-    k_gather<<<nblocks(Np, BS), BS, 0, c->s>>>(pos, Np, (double)N0 / box, (double)N0, T, G,
-                                               acc_out, (unsigned long long*)(A->d_small + 1));
+    if (g32)
+      k_gather32<<<nblocks(Np, BS), BS, 0, c->s>>>(pos, Np, (double)N0 / box, (double)N0, T, G,
+                                                   acc_out, (unsigned long long*)(A->d_small + 1));
+    else
+      k_gather<<<nblocks(Np, BS), BS, 0, c->s>>>(pos, Np, (double)N0 / box, (double)N0, T, G,
+                                                 acc_out, (unsigned long long*)(A->d_small + 1));
     c->launches += 1;
   }
   MG_CK(c, cudaEventRecord(c->ev_out, c->s));

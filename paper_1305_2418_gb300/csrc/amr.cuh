@@ -32,6 +32,7 @@ struct AmrLevel {
   float* mask = nullptr;              // [ncell] multigrid mask
   double *ghost = nullptr, *ghostE = nullptr;  // [n_oct*24]
   double* acc = nullptr;              // [ncell*3] (level >= 1)
+  float4* acc32 = nullptr;            // [ncell] FP32 force for the mixed-form gather
   int* pnbr = nullptr;                // [n_oct*6] parent's face-neighbour cells (-1: none)
   // FP32 work arrays (mixed precision phase of the level solves)
   float *w32 = nullptr, *wE32 = nullptr, *wf32 = nullptr, *wold32 = nullptr;
@@ -99,6 +100,7 @@ struct AmrWork {
   long long* d_small = nullptr;       // device scalars (totals, error flags)
   double* acc0 = nullptr;             // base force [3][N0^3]
   double* fr0 = nullptr;              // base fR [N0^3]
+  float4* acc0_32 = nullptr;          // base force, FP32 (x, y, z, 0) per cell
   long long cap_cells[AMR_MAXL] = {}; // allocated capacity per level (cells)
   long long cap_oct[AMR_MAXL] = {};
 };

@@ -687,9 +687,10 @@ __global__ void k_apply_lin(double* __restrict__ w, double* __restrict__ wE,
                             const float* __restrict__ e, long long n, double cap) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double v = w[i] + fmin(fmax((double)e[i], -cap), cap);
+  const double d = fmin(fmax((double)e[i], -cap), cap);
+  const double v = w[i] + d;
   w[i] = v;
-  wE[i] = exp(v);
+  wE[i] = exp_after_step(wE[i], v, d);
 }
 
 __global__ void k_zero32(float* __restrict__ x, long long n) {
@@ -1034,7 +1035,15 @@ struct SolveCtx {
   int L;
   float mthr;
   long long updates;
+  int kmax;  // deepest dense level below the base holding a relaxed cell (0: none)
 };
+
+// whether the coarse grid below tree level l >= 1 of the level-S.L solve has
+// a relaxed cell (otherwise the cycle stops at level l)
+bool has_coarse(const SolveCtx& S, int l) {
+  const AmrLevel& P = S.A->L[l - 1];
+  return l - 1 >= 1 ? P.n_list > 0 : P.relaxed > 0;
+}
 
 // Octs visited on tree level l >= 1 of the level-S.L solve: every oct of the
 // solved level, the active-oct list on a coarser level.
@@ -1107,17 +1116,19 @@ void vcycle_dense(SolveCtx& S, int k) {
                                                          (T)g.step_cap, mk, S.mthr);
       c->launches += 1;
     }
-  DenseLevel& C = H.L[k + 1];
-  TA<T> b = darr<T>(C);
-  k_drestrict<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lg, b.w, b.wE, b.wold,
-                                                    b.wf, m, (T)F.ih2, mk, S.mthr);
-  k_dfas<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, C.lg, m, (T)C.ih2,
-                                               S.A->dmask[k + 1], S.mthr);
-  c->launches += 2;
-  vcycle_dense<T>(S, k + 1);
-  k_dprolong<T><<<nblocks(F.n, BS), BS, 0, c->s>>>(a.w, a.wE, b.w, b.wold, F.lg,
-                                                   g.prolong_linear, mk, S.mthr);
-  c->launches += 1;
+  if (k + 1 <= S.kmax) {
+    DenseLevel& C = H.L[k + 1];
+    TA<T> b = darr<T>(C);
+    k_drestrict<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lg, b.w, b.wE, b.wold,
+                                                      b.wf, m, (T)F.ih2, mk, S.mthr);
+    k_dfas<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, C.lg, m, (T)C.ih2,
+                                                 S.A->dmask[k + 1], S.mthr);
+    c->launches += 2;
+    vcycle_dense<T>(S, k + 1);
+    k_dprolong<T><<<nblocks(F.n, BS), BS, 0, c->s>>>(a.w, a.wE, b.w, b.wold, F.lg,
+                                                     g.prolong_linear, mk, S.mthr);
+    c->launches += 1;
+  }
   for (int s = 0; s < g.n_post; ++s)
     for (int col = 0; col < 2; ++col) {
       k_dsweep<T><<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lg, col, m, (T)F.ih2,
@@ -1137,7 +1148,7 @@ void vcycle_tree(SolveCtx& S, int l) {
   TA<T> a = tarr<T>(F);
   relax<T>(S, l, g.n_pre);
   const float* fmask = l == S.L ? nullptr : F.mask;
-  if (l >= 1) {
+  if (l >= 1 && has_coarse(S, l)) {
     AmrLevel& P = A->L[l - 1];
     TA<T> b = tarr<T>(P);
     const ORange R = orange(S, F, l);
@@ -1162,7 +1173,7 @@ void vcycle_tree(SolveCtx& S, int l) {
                                                            b.w, b.wold, fmask, S.mthr,
                                                            g.prolong_linear, a.w, a.wE);
     c->launches += 1;
-  } else {
+  } else if (l == 0 && S.kmax >= 1) {
     DenseHier& H = c->dh;
     DenseLevel& C = H.L[1];
     TA<T> b = darr<T>(C);
@@ -1271,15 +1282,17 @@ void lin_vcycle_dense(SolveCtx& S, int k) {
                                                          m, (float)F.ih2, mk, S.mthr);
       c->launches += 1;
     }
-  DenseLevel& C = H.L[k + 1];
-  k_dlin_restrict<<<nblocks(C.n, BS), BS, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, F.lg, C.r32,
-                                                     C.u32, C.e32, C.uold32, m, (float)F.ih2, mk,
-                                                     S.mthr);
-  c->launches += 1;
-  lin_vcycle_dense(S, k + 1);
-  k_dlin_prolong<<<nblocks(F.n, BS), BS, 0, c->s>>>(F.uold32, C.uold32, F.lg, g.prolong_linear, mk,
-                                                    S.mthr);
-  c->launches += 1;
+  if (k + 1 <= S.kmax) {
+    DenseLevel& C = H.L[k + 1];
+    k_dlin_restrict<<<nblocks(C.n, BS), BS, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, F.lg,
+                                                       C.r32, C.u32, C.e32, C.uold32, m,
+                                                       (float)F.ih2, mk, S.mthr);
+    c->launches += 1;
+    lin_vcycle_dense(S, k + 1);
+    k_dlin_prolong<<<nblocks(F.n, BS), BS, 0, c->s>>>(F.uold32, C.uold32, F.lg, g.prolong_linear,
+                                                      mk, S.mthr);
+    c->launches += 1;
+  }
   for (int s = 0; s < g.n_post; ++s)
     for (int col = 0; col < 2; ++col) {
       k_dlin_sweep<<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, F.lg, col,
@@ -1297,7 +1310,7 @@ void lin_vcycle_tree(SolveCtx& S, int l) {
   lin_relax(S, l, g.n_pre);
   S.updates += (long long)g.n_pre * F.relaxed;
   const float* fmask = l == S.L ? nullptr : F.mask;
-  if (l >= 1) {
+  if (l >= 1 && has_coarse(S, l)) {
     AmrLevel& P = A->L[l - 1];
     const ORange R = orange(S, F, l);
     if (R.n > 0)
@@ -1311,7 +1324,7 @@ void lin_vcycle_tree(SolveCtx& S, int l) {
                                                             P.wold32, fmask, S.mthr,
                                                             g.prolong_linear, F.wold32);
     c->launches += 1;
-  } else {
+  } else if (l == 0 && S.kmax >= 1) {
     DenseHier& H = c->dh;
     DenseLevel& C = H.L[1];
     k_dlin_restrict<<<nblocks(C.n, BS), BS, 0, c->s>>>(F.wold32, F.wf32, F.w32, F.wE32, F.lgN,
@@ -1426,7 +1439,18 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
     k_mask_dense<<<nblocks(H.L[k].n, BS), BS, 0, c->s>>>(mf, H.L[k - 1].lg, A->dmask[k]);
     c->launches += 1;
   }
-  SolveCtx S{c, A, m, Lv, mthr, 0};
+  // the dense levels below the base that hold relaxed cells (the cycles stop
+  // at the deepest one; coarser grids would only relax nothing)
+  int kmax = 0;
+  if (A->L[0].relaxed > 0) {
+    for (int k = 1; k < H.nlev; ++k) {
+      long long nk = 0;
+      TRY(count_relaxed(c, A, A->dmask[k], H.L[k].n, mthr, &nk));
+      if (nk == 0) break;
+      kmax = k;
+    }
+  }
+  SolveCtx S{c, A, m, Lv, mthr, 0, kmax};
   if (g.profile) prof_reserve_public(c, 64);
   double hs[3];
   // initial norms (the reference ||f|| and whether to iterate at all): FP32

@@ -415,7 +415,7 @@ __global__ void k_apply_corr(double* __restrict__ u, double* __restrict__ E,
   const double d = fmin(fmax((double)e[t], -cap), cap);
   const double v = u[t] + d;
   u[t] = v;
-  E[t] = exp(v);
+  E[t] = exp_after_step(E[t], v, d);
 }
 
 __global__ void k_zero(float* __restrict__ x, long long n) {
