@@ -51,6 +51,18 @@ __device__ __forceinline__ P3 particle_t(const double* __restrict__ pos, long lo
             wrap_coord(pos[3 * p + 2], inv, N0)};
 }
 
+// Fixed point for the traversal: a coordinate is held as X = floor(t 2^52),
+// t in level-0 cell units (t < N0 <= 2^10, so X < 2^62).  For every level m,
+// X >> (52 - m) = floor(t 2^m) exactly (nested floors), so the cells chosen are
+// those of the floating-point definition; every overlap length is an integer,
+// exact in double, and a weight is rounded only by its two products.  All of
+// the traversal but those products runs on the integer pipes.
+constexpr int QB = 52;
+
+__device__ __forceinline__ long long qfix(double t) {
+  return (long long)__dmul_rn(t, 4503599627370496.0);  // exact scaling by 2^52, then floor
+}
+
 // ---- structure kernels -----------------------------------------------------
 __global__ void k_count(const double* __restrict__ pos, long long Np, double inv, double N0, int l,
                         TreeView T, int* __restrict__ count) {
@@ -58,9 +70,9 @@ __global__ void k_count(const double* __restrict__ pos, long long Np, double inv
   if (p >= Np) return;
   const P3 t = particle_t(pos, p, inv, N0);
   int lev;
-  const long long c = find_cell(T, l, (long long)floor(ldexp(t.x, l)),
-                                (long long)floor(ldexp(t.y, l)), (long long)floor(ldexp(t.z, l)),
-                                &lev);
+  const int sh = QB - l;  // X >> (52 - l) = floor(t 2^l)
+  const long long c =
+      find_cell(T, l, qfix(t.x) >> sh, qfix(t.y) >> sh, qfix(t.z) >> sh, &lev);
   if (lev == l) atomicAdd(count + c, 1);
 }
 
@@ -259,18 +271,6 @@ __device__ __forceinline__ void touch(int lev, long long c, W w, LevelPtrs& D,
   } else {
     atomicAdd(D.a[lev] + c, w);
   }
-}
-
-// Fixed point for the traversal: a coordinate is held as X = floor(t 2^52),
-// t in level-0 cell units (t < N0 <= 2^10, so X < 2^62).  For every level m,
-// X >> (52 - m) = floor(t 2^m) exactly (nested floors), so the cells chosen are
-// those of the floating-point definition; every overlap length is an integer,
-// exact in double, and a weight is rounded only by its two products.  All of
-// the traversal but those products runs on the integer pipes.
-constexpr int QB = 52;
-
-__device__ __forceinline__ long long qfix(double t) {
-  return (long long)__dmul_rn(t, 4503599627370496.0);  // exact scaling by 2^52, then floor
 }
 
 struct StackEnt {

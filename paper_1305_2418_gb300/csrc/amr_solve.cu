@@ -456,17 +456,6 @@ __device__ __forceinline__ JR jrow(float uc, float Ec, const NB<float>* nb, cons
   return J;
 }
 
-// correction of the neighbour in direction d (0 at ghosts)
-__device__ __forceinline__ float onb_e(const float* __restrict__ e, const int* __restrict__ nbr,
-                                       long long o, int ch, int d) {
-  const int ax = d >> 1, plus = d & 1;
-  const int bit = (ch >> (2 - ax)) & 1;
-  const int chn = ch ^ (1 << (2 - ax));
-  if (bit != plus) return e[8 * o + chn];
-  const int no = nbr[6 * o + d];
-  return no >= 0 ? e[8LL * no + chn] : 0.f;
-}
-
 // FP64 residual of level L on the FP64 iterate; writes r, the FP32
 // linearisation point (u, E) and e = 0, and accumulates the norms
 __global__ void __launch_bounds__(BS) k_oresid_lin(
@@ -513,40 +502,6 @@ __global__ void __launch_bounds__(BS) k_oresid_lin(
     partials[3 * blockIdx.x + 1] = b;
     partials[3 * blockIdx.x + 2] = ee;
   }
-}
-
-// r_c = R(r - J e) over relaxed daughters, u_c = R(u), E_c = e^{u_c}, e_c = 0
-__global__ void __launch_bounds__(BS) k_olin_restrict(
-    const float* __restrict__ e, const float* __restrict__ r, const float* __restrict__ u,
-    const float* __restrict__ E, const int* __restrict__ nbr, const float* __restrict__ gh,
-    const float* __restrict__ ghE, const float* __restrict__ mask, float mthr, long long n_oct,
-    const int* __restrict__ olist, const int* __restrict__ pcell, MT<float> m, float ih2,
-    float* __restrict__ rc, float* __restrict__ uc, float* __restrict__ Ec,
-    float* __restrict__ ec) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= n_oct) return;
-  const long long o = olist ? olist[t] : t;
-  float su = 0.f, sr = 0.f;
-  for (int ch = 0; ch < 8; ++ch) {
-    const long long c = 8 * o + ch;
-    su += u[c];
-    if (!mask || mask[c] > mthr) {
-      NB<float> nb[6];
-#pragma unroll
-      for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
-      const JR J = jrow(u[c], Eat(E, u, c), nb, m, ih2);
-      float Je = J.diag * e[c];
-#pragma unroll
-      for (int d = 0; d < 6; ++d) Je = fmaf(J.off[d], onb_e(e, nbr, o, ch, d), Je);
-      sr += r[c] - Je;
-    }
-  }
-  const int p = pcell[o];
-  const float um = 0.125f * su;
-  uc[p] = um;
-  Ec[p] = __expf(um);
-  rc[p] = 0.125f * sr;
-  ec[p] = 0.f;
 }
 
 // e += P(e_c) on relaxed cells (linear reconstruction from the parent)
@@ -834,6 +789,204 @@ __global__ void __launch_bounds__(BS) k_oct_sweep32(
     st8(e, o, X);
   else
     st8(u, o, UO);
+}
+
+// ---- thread-per-oct FP32 operator sums ------------------------------------
+// For every cell c of oct o, over its six neighbours j (three in the oct, one
+// across each of its three outer faces: the neighbouring oct or the ghost),
+// with E = e^u from the SFU:
+//   NL : s1_c = sum_j 1/2 (E_j + E_c)(u_j - u_c)          (h^2 times the
+//        divergence term of L_c, Sec. 3.2)
+//   LIN: s1_c = sum_j (E_j (u_j - u_c) + E_c + E_j) x_j   (2 h^2 times the
+//        off-diagonal part of (J x)_c; x = 0 at ghosts)
+//        s2_c = sum_j (E_c (u_j - u_c) - E_c - E_j)       (2 h^2 times the
+//        divergence part of J_cc)
+// Each face is loaded once per oct instead of once per cell.
+template <bool LIN>
+__device__ __forceinline__ void oct_sums(const float* __restrict__ u, const float* __restrict__ x,
+                                         const int* __restrict__ nbr,
+                                         const float* __restrict__ gh, long long o, const Oct8& U,
+                                         const Oct8& EE, const Oct8& X, float* s1, float* s2) {
+#pragma unroll
+  for (int ch = 0; ch < 8; ++ch) {
+    s1[ch] = 0.f;
+    s2[ch] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int cn = ch ^ (1 << (2 - a));
+      const float du = U.v[cn] - U.v[ch];
+      if (LIN) {
+        s1[ch] = fmaf(fmaf(EE.v[cn], du, EE.v[ch] + EE.v[cn]), X.v[cn], s1[ch]);
+        s2[ch] += fmaf(EE.v[ch], du, -EE.v[ch] - EE.v[cn]);
+      } else {
+        s1[ch] = fmaf(0.5f * (EE.v[cn] + EE.v[ch]), du, s1[ch]);
+      }
+    }
+  }
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    const int a = d >> 1, plus = d & 1;
+    const int no = nbr[6 * o + d];
+    Oct8 NU, NX;
+    float G[4];
+    if (no >= 0) {
+      NU = ld8(u, no);
+      if (LIN) NX = ld8(x, no);
+    } else {
+      const float4 g = *reinterpret_cast<const float4*>(gh + 24 * o + 4 * d);
+      G[0] = g.x;
+      G[1] = g.y;
+      G[2] = g.z;
+      G[3] = g.w;
+    }
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+      if (((ch >> (2 - a)) & 1) != plus) continue;  // not on this face
+      float un, xn;
+      if (no >= 0) {
+        const int cn = ch ^ (1 << (2 - a));
+        un = NU.v[cn];
+        xn = LIN ? NX.v[cn] : 0.f;
+      } else {
+        un = G[face_q(ch, a)];
+        xn = 0.f;
+      }
+      const float En = __expf(un), du = un - U.v[ch];
+      if (LIN) {
+        s1[ch] = fmaf(fmaf(En, du, EE.v[ch] + En), xn, s1[ch]);
+        s2[ch] += fmaf(EE.v[ch], du, -EE.v[ch] - En);
+      } else {
+        s1[ch] = fmaf(0.5f * (En + EE.v[ch]), du, s1[ch]);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void block_partials3(double ss, double mx, double fs,
+                                                double* __restrict__ partials) {
+  __shared__ double s1[BS / 32], s2[BS / 32], s3[BS / 32];
+  for (int q = 16; q > 0; q >>= 1) {
+    ss += __shfl_xor_sync(0xffffffffu, ss, q);
+    fs += __shfl_xor_sync(0xffffffffu, fs, q);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, q));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s1[threadIdx.x >> 5] = ss;
+    s2[threadIdx.x >> 5] = mx;
+    s3[threadIdx.x >> 5] = fs;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, e = 0.0;
+    for (int w = 0; w < BS / 32; ++w) {
+      a += s1[w];
+      b = fmax(b, s2[w]);
+      e += s3[w];
+    }
+    partials[3 * blockIdx.x] = a;
+    partials[3 * blockIdx.x + 1] = b;
+    partials[3 * blockIdx.x + 2] = e;
+  }
+}
+
+// FP32 residual norms of the solved level (sum r^2, max |r|, sum f^2), one
+// thread per oct; the oct's eight terms are summed in FP32, the octs in FP64.
+__global__ void __launch_bounds__(BS) k_onorm32(const float* __restrict__ u,
+                                                const float* __restrict__ f,
+                                                const int* __restrict__ nbr,
+                                                const float* __restrict__ gh, long long n_oct,
+                                                MT<float> m, float ih2,
+                                                double* __restrict__ partials) {
+  double ss = 0.0, mx = 0.0, fs = 0.0;
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n_oct;
+       o += (long long)gridDim.x * blockDim.x) {
+    const Oct8 U = ld8(u, o), Fv = ld8(f, o);
+    Oct8 EE;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) EE.v[i] = __expf(U.v[i]);
+    float s1[8], s2[8];
+    oct_sums<false>(u, nullptr, nbr, gh, o, U, EE, U, s1, s2);
+    float ss8 = 0.f, mx8 = 0.f, fs8 = 0.f;
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+      const float L = s1[ch] * ih2 + m.aRt * (1.f - nls(U.v[ch], EE.v[ch], m));
+      const float r = Fv.v[ch] - L;
+      ss8 = fmaf(r, r, ss8);
+      mx8 = fmaxf(mx8, fabsf(r));
+      fs8 = fmaf(Fv.v[ch], Fv.v[ch], fs8);
+    }
+    ss += ss8;
+    mx = fmax(mx, (double)mx8);
+    fs += fs8;
+  }
+  block_partials3(ss, mx, fs, partials);
+}
+
+// FAS restriction of one oct to its parent (FP32): u average, average of the
+// residual f - L(u) over the oct's relaxed cells.
+__global__ void __launch_bounds__(BS) k_orestrict32(
+    const float* __restrict__ u, const float* __restrict__ f, const int* __restrict__ nbr,
+    const float* __restrict__ gh, const float* __restrict__ mask, float mthr, long long n,
+    const int* __restrict__ olist, const int* __restrict__ pcell, MT<float> m, float ih2,
+    float* __restrict__ uc, float* __restrict__ Ec, float* __restrict__ ucold,
+    float* __restrict__ fc) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const long long o = olist ? olist[t] : t;
+  const Oct8 U = ld8(u, o), Fv = ld8(f, o);
+  Oct8 EE;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) EE.v[i] = __expf(U.v[i]);
+  float s1[8], s2[8];
+  oct_sums<false>(u, nullptr, nbr, gh, o, U, EE, U, s1, s2);
+  float su = 0.f, sr = 0.f;
+#pragma unroll
+  for (int ch = 0; ch < 8; ++ch) {
+    su += U.v[ch];
+    if (!mask || mask[8 * o + ch] > mthr)
+      sr += Fv.v[ch] - (s1[ch] * ih2 + m.aRt * (1.f - nls(U.v[ch], EE.v[ch], m)));
+  }
+  const int p = pcell[o];
+  const float um = 0.125f * su;
+  uc[p] = um;
+  ucold[p] = um;
+  Ec[p] = __expf(um);
+  fc[p] = 0.125f * sr;
+}
+
+// Linear-phase restriction of one oct: r_c = R(r - J e) over relaxed cells,
+// u_c = R(u), E_c = e^{u_c}, e_c = 0.
+__global__ void __launch_bounds__(BS) k_olin_restrict32(
+    const float* __restrict__ e, const float* __restrict__ r, const float* __restrict__ u,
+    const int* __restrict__ nbr, const float* __restrict__ gh, const float* __restrict__ mask,
+    float mthr, long long n, const int* __restrict__ olist, const int* __restrict__ pcell,
+    MT<float> m, float ih2, float* __restrict__ rc, float* __restrict__ uc,
+    float* __restrict__ Ec, float* __restrict__ ec) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const long long o = olist ? olist[t] : t;
+  const Oct8 U = ld8(u, o), X = ld8(e, o), R = ld8(r, o);
+  Oct8 EE;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) EE.v[i] = __expf(U.v[i]);
+  float s1[8], s2[8];
+  oct_sums<true>(u, e, nbr, gh, o, U, EE, X, s1, s2);
+  const float h2 = 0.5f * ih2;
+  float su = 0.f, sr = 0.f;
+#pragma unroll
+  for (int ch = 0; ch < 8; ++ch) {
+    su += U.v[ch];
+    if (!mask || mask[8 * o + ch] > mthr) {
+      const float diag = s2[ch] * h2 + m.aRt_np1 * nls(U.v[ch], EE.v[ch], m);
+      sr += R.v[ch] - fmaf(diag, X.v[ch], s1[ch] * h2);
+    }
+  }
+  const int p = pcell[o];
+  const float um = 0.125f * su;
+  uc[p] = um;
+  Ec[p] = __expf(um);
+  rc[p] = 0.125f * sr;
+  ec[p] = 0.f;
 }
 
 // ---- set-up kernels --------------------------------------------------------
@@ -1152,10 +1305,16 @@ void vcycle_tree(SolveCtx& S, int l) {
     AmrLevel& P = A->L[l - 1];
     TA<T> b = tarr<T>(P);
     const ORange R = orange(S, F, l);
-    if (R.n > 0)
-      k_orestrict<T><<<nblocks(R.n, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.nbr, a.gh, a.ghE,
-                                                        fmask, S.mthr, R.n, R.list, F.pcell, m,
-                                                        (T)F.ih2, b.w, b.wE, b.wold, b.wf);
+    if (R.n > 0) {
+      if constexpr (std::is_same<T, float>::value)
+        k_orestrict32<<<nblocks(R.n, BS), BS, 0, c->s>>>(a.w, a.wf, F.nbr, a.gh, fmask, S.mthr,
+                                                         R.n, R.list, F.pcell, m, (T)F.ih2, b.w,
+                                                         b.wE, b.wold, b.wf);
+      else
+        k_orestrict<T><<<nblocks(R.n, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.nbr, a.gh, a.ghE,
+                                                          fmask, S.mthr, R.n, R.list, F.pcell, m,
+                                                          (T)F.ih2, b.w, b.wE, b.wold, b.wf);
+    }
     if (l - 1 >= 1) {
       if (P.n_list > 0)
         k_ofas<T><<<nblocks(8 * P.n_list, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, P.nbr, b.gh,
@@ -1197,9 +1356,16 @@ mgfr_status level_norm(SolveCtx& S, double* hs) {
   AmrLevel& L = S.A->L[S.L];
   DenseHier& H = c->dh;
   TA<T> a = tarr<T>(L);
-  const int nparts = (int)std::min<long long>(H.nparts / 2, nblocks(L.ncell, BS));
-  k_onorm<T><<<nparts, BS, 0, c->s>>>(a.w, a.wE, a.wf, L.nbr, a.gh, a.ghE, L.ncell, mt<T>(S.m),
-                                      (T)L.ih2, H.partials);
+  int nparts;
+  if constexpr (std::is_same<T, float>::value) {
+    nparts = (int)std::min<long long>(H.nparts / 2, nblocks(L.n_oct, BS));
+    k_onorm32<<<nparts, BS, 0, c->s>>>(a.w, a.wf, L.nbr, a.gh, L.n_oct, mt<float>(S.m),
+                                       (float)L.ih2, H.partials);
+  } else {
+    nparts = (int)std::min<long long>(H.nparts / 2, nblocks(L.ncell, BS));
+    k_onorm<T><<<nparts, BS, 0, c->s>>>(a.w, a.wE, a.wf, L.nbr, a.gh, a.ghE, L.ncell,
+                                        mt<T>(S.m), (T)L.ih2, H.partials);
+  }
   k_finish3<<<1, 256, 0, c->s>>>(H.partials, nparts, H.scal + 8);
   c->launches += 2;
   MG_CK(c, cudaMemcpyAsync(hs, H.scal + 8, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
@@ -1314,9 +1480,9 @@ void lin_vcycle_tree(SolveCtx& S, int l) {
     AmrLevel& P = A->L[l - 1];
     const ORange R = orange(S, F, l);
     if (R.n > 0)
-      k_olin_restrict<<<nblocks(R.n, BS), BS, 0, c->s>>>(
-          F.wold32, F.wf32, F.w32, F.wE32, F.nbr, F.ghost32, nullptr, fmask, S.mthr, R.n,
-          R.list, F.pcell, m, (float)F.ih2, P.wf32, P.w32, P.wE32, P.wold32);
+      k_olin_restrict32<<<nblocks(R.n, BS), BS, 0, c->s>>>(
+          F.wold32, F.wf32, F.w32, F.nbr, F.ghost32, fmask, S.mthr, R.n, R.list, F.pcell, m,
+          (float)F.ih2, P.wf32, P.w32, P.wE32, P.wold32);
     c->launches += 1;
     lin_vcycle_tree(S, l - 1);
     if (R.n > 0)
