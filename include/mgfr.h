@@ -74,7 +74,7 @@ typedef struct {
   /* mixed precision: FP32 nonlinear V-cycles until the relative residual is
    * below mixed_switch, then FP64 defect-correction iterations, each with
    * mixed_inner FP32 linear V-cycles on the Jacobian system.               */
-  double mixed_switch; /* default 1e-5                                      */
+  double mixed_switch; /* default 3e-6                                      */
   int mixed_inner;     /* default 3                                         */
   long long max_spins; /* bound on any device-side wait (default 1<<26)     */
   int profile;         /* 1: time the base-level sweep kernels with CUDA
@@ -116,7 +116,7 @@ typedef struct {
 
 /* Fill *cfg with the defaults above (omega_m 0.3, fr0_abs 1e-5, n 1, FP64,
  * tol 1e-8, 2+2 sweeps, 100 V-cycles, linear prolongation, step cap 2,
- * max_level 0, refine_count 8, mixed_switch 1e-5, mixed_inner 3,
+ * max_level 0, refine_count 8, mixed_switch 3e-6, mixed_inner 3,
  * mask_thres 0.99). */
 void mgfr_config_default(mgfr_config* cfg);
 

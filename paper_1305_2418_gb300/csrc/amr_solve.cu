@@ -307,7 +307,19 @@ __device__ __forceinline__ void dnb(const T* __restrict__ u, const T* __restrict
                           cidx(i, (j - 1) & M, k, lg), cidx(i, (j + 1) & M, k, lg),
                           cidx(i, j, (k - 1) & M, lg), cidx(i, j, (k + 1) & M, lg)};
 #pragma unroll
-  for (int d = 0; d < 6; ++d) nb[d] = NB<T>{u[q[d]], E[q[d]]};
+  for (int d = 0; d < 6; ++d) nb[d] = NB<T>{u[q[d]], Eat(E, u, q[d])};
+}
+
+// the six neighbour values of x at (i, j, k)
+__device__ __forceinline__ void dnb_x(const float* __restrict__ x, int i, int j, int k, int lg,
+                                      float* out) {
+  const int M = (1 << lg) - 1;
+  out[0] = x[cidx((i - 1) & M, j, k, lg)];
+  out[1] = x[cidx((i + 1) & M, j, k, lg)];
+  out[2] = x[cidx(i, (j - 1) & M, k, lg)];
+  out[3] = x[cidx(i, (j + 1) & M, k, lg)];
+  out[4] = x[cidx(i, j, (k - 1) & M, lg)];
+  out[5] = x[cidx(i, j, (k + 1) & M, lg)];
 }
 
 template <class T>
@@ -327,9 +339,9 @@ __global__ void __launch_bounds__(BS) k_dsweep(T* __restrict__ u, T* __restrict_
   NB<T> nb[6];
   dnb(u, E, i, j, k, lg, nb);
   const T uc = u[c];
-  const T un = uc - newton(uc, E[c], nb, f[c], m, ih2, cap);
+  const T un = uc - newton(uc, Eat(E, u, c), nb, f[c], m, ih2, cap);
   u[c] = un;
-  E[c] = ex(un);
+  if constexpr (std::is_same<T, double>::value) E[c] = ex(un);
 }
 
 template <class T>
@@ -350,13 +362,13 @@ __global__ void __launch_bounds__(BS) k_drestrict(const T* __restrict__ u, const
     if (!mask || mask[c] > mthr) {
       NB<T> nb[6];
       dnb(u, E, i, j, k, lgf, nb);
-      sr += f[c] - Lval(u[c], E[c], nb, m, ih2);
+      sr += f[c] - Lval(u[c], Eat(E, u, c), nb, m, ih2);
     }
   }
   const T um = (T)0.125 * su;
   uc[t] = um;
   ucold[t] = um;
-  Ec[t] = ex(um);
+  if constexpr (std::is_same<T, double>::value) Ec[t] = ex(um);
   fc[t] = (T)0.125 * sr;
 }
 
@@ -371,7 +383,7 @@ __global__ void __launch_bounds__(BS) k_dfas(const T* __restrict__ u, const T* _
   const int k = (int)(t & (N - 1)), j = (int)((t >> lg) & (N - 1)), i = (int)(t >> (2 * lg));
   NB<T> nb[6];
   dnb(u, E, i, j, k, lg, nb);
-  f[t] += Lval(u[t], E[t], nb, m, ih2);
+  f[t] += Lval(u[t], Eat(E, u, t), nb, m, ih2);
 }
 
 template <class T>
@@ -397,7 +409,7 @@ __global__ void __launch_bounds__(BS) k_dprolong(T* __restrict__ u, T* __restric
   }
   const T un = u[t] + v;
   u[t] = un;
-  E[t] = ex(un);
+  if constexpr (std::is_same<T, double>::value) E[t] = ex(un);
 }
 
 // masked NGS on the 4^3 grid, fixed sweep count (one block of 64 threads)
@@ -409,7 +421,7 @@ __global__ void __launch_bounds__(64) k_dcoarse(T* __restrict__ ug, T* __restric
   __shared__ T u[64], E[64];
   const int t = threadIdx.x;
   u[t] = ug[t];
-  E[t] = Eg[t];
+  E[t] = Eat(Eg, ug, t);
   const T f = fg[t];
   const bool active = !mask || mask[t] > mthr;
   const int i = t >> 4, j = (t >> 2) & 3, k = t & 3, colour = (i + j + k) & 1;
@@ -429,7 +441,7 @@ __global__ void __launch_bounds__(64) k_dcoarse(T* __restrict__ ug, T* __restric
       __syncthreads();
     }
   ug[t] = u[t];
-  Eg[t] = E[t];
+  if constexpr (std::is_same<T, double>::value) Eg[t] = E[t];
 }
 
 
@@ -504,30 +516,6 @@ __global__ void __launch_bounds__(BS) k_oresid_lin(
   }
 }
 
-// e += P(e_c) on relaxed cells (linear reconstruction from the parent)
-__global__ void __launch_bounds__(BS) k_olin_prolong(long long ncell, const int* __restrict__ olist,
-                                                     const int* __restrict__ pcell,
-                                                     const int* __restrict__ pnbr,
-                                                     const float* __restrict__ ec,
-                                                     const float* __restrict__ mask, float mthr,
-                                                     int linear, float* __restrict__ e) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= ncell) return;
-  const long long o = olist ? olist[t >> 3] : t >> 3;
-  const int ch = (int)(t & 7);
-  const long long c = 8 * o + ch;
-  if (mask && !(mask[c] > mthr)) return;
-  float v = ec[pcell[o]];
-  if (linear) {
-    for (int ax = 0; ax < 3; ++ax) {
-      const int pm = pnbr[6 * o + 2 * ax], pp = pnbr[6 * o + 2 * ax + 1];
-      if (pm < 0 || pp < 0) continue;
-      v += (((ch >> (2 - ax)) & 1) ? 0.125f : -0.125f) * (ec[pp] - ec[pm]);
-    }
-  }
-  e[c] += v;
-}
-
 __global__ void __launch_bounds__(BS) k_dlin_sweep(float* __restrict__ e, const float* __restrict__ r,
                                                    const float* __restrict__ u,
                                                    const float* __restrict__ E, int lg, int colour,
@@ -544,12 +532,12 @@ __global__ void __launch_bounds__(BS) k_dlin_sweep(float* __restrict__ e, const 
   if (mask && !(mask[c] > mthr)) return;
   NB<float> nb[6];
   dnb(u, E, i, j, k, lg, nb);
-  const JR J = jrow(u[c], E[c], nb, m, ih2);
-  NB<float> en[6];
-  dnb(e, e, i, j, k, lg, en);
+  const JR J = jrow(u[c], Eat(E, u, c), nb, m, ih2);
+  float en[6];
+  dnb_x(e, i, j, k, lg, en);
   float acc = r[c];
 #pragma unroll
-  for (int d = 0; d < 6; ++d) acc = fmaf(-J.off[d], en[d].u, acc);
+  for (int d = 0; d < 6; ++d) acc = fmaf(-J.off[d], en[d], acc);
   e[c] = __fdividef(acc, J.diag);
 }
 
@@ -571,19 +559,19 @@ __global__ void __launch_bounds__(BS) k_dlin_restrict(const float* __restrict__ 
     const unsigned c = cidx(i, j, k, lgf);
     su += u[c];
     if (!mask || mask[c] > mthr) {
-      NB<float> nb[6], en[6];
+      NB<float> nb[6];
+      float en[6];
       dnb(u, E, i, j, k, lgf, nb);
-      dnb(e, e, i, j, k, lgf, en);
-      const JR J = jrow(u[c], E[c], nb, m, ih2);
+      dnb_x(e, i, j, k, lgf, en);
+      const JR J = jrow(u[c], Eat(E, u, c), nb, m, ih2);
       float Je = J.diag * e[c];
 #pragma unroll
-      for (int d = 0; d < 6; ++d) Je = fmaf(J.off[d], en[d].u, Je);
+      for (int d = 0; d < 6; ++d) Je = fmaf(J.off[d], en[d], Je);
       sr += r[c] - Je;
     }
   }
   const float um = 0.125f * su;
   uc[t] = um;
-  Ec[t] = __expf(um);
   rc[t] = 0.125f * sr;
   ec[t] = 0.f;
 }
@@ -620,8 +608,8 @@ __global__ void __launch_bounds__(64) k_dlin_coarse(float* __restrict__ eg, cons
                     (i << 4) | (((j + 3) & 3) << 2) | k, (i << 4) | (((j + 1) & 3) << 2) | k,
                     (i << 4) | (j << 2) | ((k + 3) & 3), (i << 4) | (j << 2) | ((k + 1) & 3)};
   NB<float> nb[6];
-  for (int d = 0; d < 6; ++d) nb[d] = NB<float>{ug[q[d]], Eg[q[d]]};
-  const JR J = jrow(ug[t], Eg[t], nb, m, ih2);
+  for (int d = 0; d < 6; ++d) nb[d] = NB<float>{ug[q[d]], Eat(Eg, ug, q[d])};
+  const JR J = jrow(ug[t], Eat(Eg, ug, t), nb, m, ih2);
   const float rc = rg[t];
   e[t] = eg[t];
   __syncthreads();
@@ -950,7 +938,6 @@ __global__ void __launch_bounds__(BS) k_orestrict32(
   const float um = 0.125f * su;
   uc[p] = um;
   ucold[p] = um;
-  Ec[p] = __expf(um);
   fc[p] = 0.125f * sr;
 }
 
@@ -984,9 +971,55 @@ __global__ void __launch_bounds__(BS) k_olin_restrict32(
   const int p = pcell[o];
   const float um = 0.125f * su;
   uc[p] = um;
-  Ec[p] = __expf(um);
   rc[p] = 0.125f * sr;
   ec[p] = 0.f;
+}
+
+// Prolongation of a coarse correction to the relaxed cells of one oct (FP32):
+// the parent's value c plus, per axis, s (c+ - c-)/8 from the parent's two
+// neighbours (a component is 0 where one is missing), s = +1 or -1 for the
+// daughter's high or low position.  NL: c = uc - ucold (FAS), added to u;
+// LIN: c = e_c, added to e.  The oct is read and written whole.
+template <bool LIN>
+__global__ void __launch_bounds__(BS) k_oprolong32(long long n, const int* __restrict__ olist,
+                                                   const int* __restrict__ pcell,
+                                                   const int* __restrict__ pnbr,
+                                                   const float* __restrict__ uc,
+                                                   const float* __restrict__ ucold,
+                                                   const float* __restrict__ mask, float mthr,
+                                                   int linear, float* __restrict__ u) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const long long o = olist ? olist[t] : t;
+  auto corr = [&](int q) -> float {
+    if constexpr (LIN)
+      return uc[q];
+    else
+      return uc[q] - ucold[q];
+  };
+  const float v0 = corr(pcell[o]);
+  float g[3] = {0.f, 0.f, 0.f};
+  bool have[3] = {false, false, false};
+  if (linear) {
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      const int pm = pnbr[6 * o + 2 * ax], pp = pnbr[6 * o + 2 * ax + 1];
+      if (pm < 0 || pp < 0) continue;
+      g[ax] = corr(pp) - corr(pm);
+      have[ax] = true;
+    }
+  }
+  Oct8 U = ld8(u, o);
+#pragma unroll
+  for (int ch = 0; ch < 8; ++ch) {
+    if (mask && !(mask[8 * o + ch] > mthr)) continue;
+    float v = v0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax)
+      if (have[ax]) v += (((ch >> (2 - ax)) & 1) ? 0.125f : -0.125f) * g[ax];
+    U.v[ch] += v;
+  }
+  st8(u, o, U);
 }
 
 // ---- set-up kernels --------------------------------------------------------
@@ -1327,10 +1360,16 @@ void vcycle_tree(SolveCtx& S, int l) {
     }
     c->launches += 2;
     vcycle_tree<T>(S, l - 1);
-    if (R.n > 0)
-      k_oprolong<T><<<nblocks(8 * R.n, BS), BS, 0, c->s>>>(8 * R.n, R.list, F.pcell, F.pnbr,
-                                                           b.w, b.wold, fmask, S.mthr,
-                                                           g.prolong_linear, a.w, a.wE);
+    if (R.n > 0) {
+      if constexpr (std::is_same<T, float>::value)
+        k_oprolong32<false><<<nblocks(R.n, BS), BS, 0, c->s>>>(R.n, R.list, F.pcell, F.pnbr, b.w,
+                                                              b.wold, fmask, S.mthr,
+                                                              g.prolong_linear, a.w);
+      else
+        k_oprolong<T><<<nblocks(8 * R.n, BS), BS, 0, c->s>>>(8 * R.n, R.list, F.pcell, F.pnbr,
+                                                             b.w, b.wold, fmask, S.mthr,
+                                                             g.prolong_linear, a.w, a.wE);
+    }
     c->launches += 1;
   } else if (l == 0 && S.kmax >= 1) {
     DenseHier& H = c->dh;
@@ -1486,9 +1525,9 @@ void lin_vcycle_tree(SolveCtx& S, int l) {
     c->launches += 1;
     lin_vcycle_tree(S, l - 1);
     if (R.n > 0)
-      k_olin_prolong<<<nblocks(8 * R.n, BS), BS, 0, c->s>>>(8 * R.n, R.list, F.pcell, F.pnbr,
-                                                            P.wold32, fmask, S.mthr,
-                                                            g.prolong_linear, F.wold32);
+      k_oprolong32<true><<<nblocks(R.n, BS), BS, 0, c->s>>>(R.n, R.list, F.pcell, F.pnbr,
+                                                           P.wold32, nullptr, fmask, S.mthr,
+                                                           g.prolong_linear, F.wold32);
     c->launches += 1;
   } else if (l == 0 && S.kmax >= 1) {
     DenseHier& H = c->dh;
@@ -1588,10 +1627,6 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
       k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(uu, P.w32, P.ncell);
       k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(uu, P.wold32, P.ncell);
       c->launches += 2;
-      if (l == 0) {  // the dense kernels of the base level read a stored FP32 e^u
-        k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(H.L[0].E, P.wE32, P.ncell);
-        c->launches += 1;
-      }
     }
     MG_CK(c, cudaMemsetAsync(P.mask, 0, sizeof(float) * (size_t)P.ncell, c->s));
     AmrLevel& Ch = A->L[l + 1];

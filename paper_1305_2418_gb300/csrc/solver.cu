@@ -122,7 +122,7 @@ void mgfr_config_default(mgfr_config* c) {
   c->step_cap = 2.0;
   c->max_level = 0;
   c->refine_count = 8;
-  c->mixed_switch = 1e-5;
+  c->mixed_switch = 3e-6;
   c->mixed_inner = 3;
   c->max_spins = 1LL << 26;
   c->mask_thres = 0.99;
