@@ -1693,9 +1693,10 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
     c->capturing = -1;
     r = std::sqrt(hs[0]);
     double rprev = r;
+    int inner = g.mixed_inner;
     while (r > target && it < g.max_vcycles) {
       c->capturing = 3;
-      for (int q = 0; q < g.mixed_inner; ++q) lin_vcycle_tree(S, Lv);
+      for (int q = 0; q < inner; ++q) lin_vcycle_tree(S, Lv);
       k_apply_lin<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.w, F.wE, F.wold32, F.ncell, g.step_cap);
       c->launches += 1;
       TRY(lin_resid(S, hs));
@@ -1704,6 +1705,15 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
       r = std::sqrt(hs[0]);
       ++it;
       if (!std::isfinite(r) || r > rprev) break;  // finish with FP64 V-cycles below
+      // linear cycles of the next outer iteration: from the reduction per
+      // cycle just measured, as many as bring r to half the target (at most
+      // mixed_inner); a residual just above the target then costs one cycle
+      const double rho = std::pow(r / rprev, 1.0 / inner);
+      inner = g.mixed_inner;
+      if (r > target && rho > 0.0 && rho < 1.0) {
+        const double need = std::ceil(std::log(0.5 * target / r) / std::log(rho));
+        inner = (int)std::max(1.0, std::min((double)g.mixed_inner, need));
+      }
       rprev = r;
     }
   }
