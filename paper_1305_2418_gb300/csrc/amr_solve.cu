@@ -20,6 +20,7 @@
 #include <type_traits>
 
 #include "amr.cuh"
+#include "dfloat.cuh"
 
 namespace {
 
@@ -468,54 +469,6 @@ __device__ __forceinline__ JR jrow(float uc, float Ec, const NB<float>* nb, cons
   return J;
 }
 
-// FP64 residual of level L on the FP64 iterate; writes r, the FP32
-// linearisation point (u, E) and e = 0, and accumulates the norms
-__global__ void __launch_bounds__(BS) k_oresid_lin(
-    const double* __restrict__ u, const double* __restrict__ E, const double* __restrict__ f,
-    const int* __restrict__ nbr, const double* __restrict__ gh, const double* __restrict__ ghE,
-    long long ncell, MT<double> m, double ih2, float* __restrict__ r32, float* __restrict__ u32,
-    float* __restrict__ e32, double* __restrict__ partials) {
-  double ss = 0.0, mx = 0.0, fs = 0.0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
-       c += (long long)gridDim.x * blockDim.x) {
-    const long long o = c >> 3;
-    const int ch = (int)(c & 7);
-    NB<double> nb[6];
-#pragma unroll
-    for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
-    const double r = f[c] - Lval(u[c], E[c], nb, m, ih2);
-    r32[c] = (float)r;
-    u32[c] = (float)u[c];
-    e32[c] = 0.f;
-    ss = fma(r, r, ss);
-    mx = fmax(mx, fabs(r));
-    fs = fma(f[c], f[c], fs);
-  }
-  __shared__ double s1[BS / 32], s2[BS / 32], s3[BS / 32];
-  for (int q = 16; q > 0; q >>= 1) {
-    ss += __shfl_xor_sync(0xffffffffu, ss, q);
-    fs += __shfl_xor_sync(0xffffffffu, fs, q);
-    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, q));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    s1[threadIdx.x >> 5] = ss;
-    s2[threadIdx.x >> 5] = mx;
-    s3[threadIdx.x >> 5] = fs;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0, ee = 0.0;
-    for (int w = 0; w < BS / 32; ++w) {
-      a += s1[w];
-      b = fmax(b, s2[w]);
-      ee += s3[w];
-    }
-    partials[3 * blockIdx.x] = a;
-    partials[3 * blockIdx.x + 1] = b;
-    partials[3 * blockIdx.x + 2] = ee;
-  }
-}
-
 __global__ void __launch_bounds__(BS) k_dlin_sweep(float* __restrict__ e, const float* __restrict__ r,
                                                    const float* __restrict__ u,
                                                    const float* __restrict__ E, int lg, int colour,
@@ -623,17 +576,6 @@ __global__ void __launch_bounds__(64) k_dlin_coarse(float* __restrict__ eg, cons
       __syncthreads();
     }
   eg[t] = e[t];
-}
-
-// w += clamp(e), wE = e^w on level L (FP64)
-__global__ void k_apply_lin(double* __restrict__ w, double* __restrict__ wE,
-                            const float* __restrict__ e, long long n, double cap) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double d = fmin(fmax((double)e[i], -cap), cap);
-  const double v = w[i] + d;
-  w[i] = v;
-  wE[i] = exp_after_step(wE[i], v, d);
 }
 
 __global__ void k_zero32(float* __restrict__ x, long long n) {
@@ -1022,6 +964,129 @@ __global__ void __launch_bounds__(BS) k_oprolong32(long long n, const int* __res
   st8(u, o, U);
 }
 
+// ---- phase B in double-float (mixed form) ---------------------------------
+// From the end of phase A until the level is finished, the FP64 work arrays of
+// the level being solved (w, wE, wf) and its FP64 ghost slots hold
+// double-float pairs in their 8 bytes; the FP64-accurate residual, e^u and
+// the corrections then run on the FP32 pipes.  k_df2d turns them back into
+// FP64 (level output, or the FP64 fallback).
+
+struct MDF {
+  dfl aRt, inv_np1, ih2h;  // alpha Rt, 1/(n+1), 1/(2 h^2)
+  int n;
+};
+
+MDF mdf(const Model& m, double ih2) {
+  return MDF{df_from_double(m.aRt), df_from_double(m.inv_np1), df_from_double(0.5 * ih2), m.n};
+}
+
+// a + b with error below ~2^-46 (|a| + |b|): the absolute accuracy the FP64
+// residual needs (its inputs carry the same relative error)
+__device__ __forceinline__ dfl df_add_abs(dfl a, dfl b) {
+  const dfl s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+// neighbour of cell (o, ch) in direction d: same oct, neighbouring oct, or ghost
+__device__ __forceinline__ void onb_df(const dfl* __restrict__ u, const dfl* __restrict__ E,
+                                       const int* __restrict__ nbr, const dfl* __restrict__ gh,
+                                       const dfl* __restrict__ ghE, long long o, int ch, int d,
+                                       dfl& un, dfl& En) {
+  const int ax = d >> 1, plus = d & 1;
+  const int bit = (ch >> (2 - ax)) & 1;
+  const int chn = ch ^ (1 << (2 - ax));
+  if (bit != plus) {
+    const long long q = 8 * o + chn;
+    un = u[q];
+    En = E[q];
+    return;
+  }
+  const int no = nbr[6 * o + d];
+  if (no >= 0) {
+    const long long q = 8LL * no + chn;
+    un = u[q];
+    En = E[q];
+    return;
+  }
+  const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+  const int qi = (((ch >> (2 - t1)) & 1) << 1) | ((ch >> (2 - t2)) & 1);
+  const long long g = 24 * o + 4 * d + qi;
+  un = gh[g];
+  En = ghE[g];
+}
+
+// r = f - L(u) to FP64 accuracy in double-float (Sec. 3.2 operator); stores r
+// and u rounded to FP32 for the linear cycles, zeroes the correction e, and
+// accumulates the norms (FP32 within a thread, FP64 across threads: they feed
+// only the stopping test).
+__global__ void __launch_bounds__(BS) k_oresid_df(
+    const dfl* __restrict__ u, const dfl* __restrict__ E, const dfl* __restrict__ f,
+    const int* __restrict__ nbr, const dfl* __restrict__ gh, const dfl* __restrict__ ghE,
+    long long ncell, MDF m, float* __restrict__ r32, float* __restrict__ u32,
+    float* __restrict__ e32, double* __restrict__ partials) {
+  float ss = 0.f, mx = 0.f, fs = 0.f;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    const long long o = c >> 3;
+    const int ch = (int)(c & 7);
+    const dfl uc = u[c], Ec = E[c];
+    dfl acc = {0.f, 0.f};
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      dfl un, En;
+      onb_df(u, E, nbr, gh, ghE, o, ch, d, un, En);
+      acc = df_add_abs(acc, df_mul(df_add_abs(En, Ec), df_add_abs(un, df_neg(uc))));
+    }
+    const dfl sN = m.n == 1 ? df_rsqrt(Ec) : df_exp(df_neg(df_mul(uc, m.inv_np1)));
+    const dfl L = df_add(df_mul(acc, m.ih2h), df_mul(m.aRt, df_add_f(df_neg(sN), 1.f)));
+    const dfl fc = f[c];
+    const dfl r = df_sub(fc, L);
+    r32[c] = r.hi;
+    u32[c] = uc.hi;
+    e32[c] = 0.f;
+    ss = fmaf(r.hi, r.hi, ss);
+    mx = fmaxf(mx, fabsf(r.hi));
+    fs = fmaf(fc.hi, fc.hi, fs);
+  }
+  block_partials3((double)ss, (double)mx, (double)fs, partials);
+}
+
+// FP32 iterate -> double-float iterate and its e^u
+__global__ void k_f2df_exp(const float* __restrict__ w32, dfl* __restrict__ w, dfl* __restrict__ wE,
+                           long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const dfl v{w32[i], 0.f};
+  w[i] = v;
+  wE[i] = df_exp(v);
+}
+
+// w += clamp(e), wE = e^w (double-float)
+__global__ void k_apply_df(dfl* __restrict__ w, dfl* __restrict__ wE, const float* __restrict__ e,
+                           long long n, float cap) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const dfl v = df_add_f(w[i], fminf(fmaxf(e[i], -cap), cap));
+  w[i] = v;
+  wE[i] = df_exp(v);
+}
+
+// double-float -> FP64 (in place allowed) and back
+__global__ void k_df2d(const dfl* __restrict__ x, double* __restrict__ y, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const dfl v = x[i];
+    y[i] = df_to_double(v);
+  }
+}
+__global__ void k_d2df(const double* __restrict__ x, dfl* __restrict__ y, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double v = x[i];
+    y[i] = df_from_double(v);
+  }
+}
+
 // ---- set-up kernels --------------------------------------------------------
 // initial guess of level L from the converged level L-1 (linear
 // reconstruction with the parent's neighbours), FP64 and FP32 copies
@@ -1055,10 +1120,11 @@ __global__ void k_init_level(long long ncell, const int* __restrict__ pcell,
 // normal, so P and its six neighbours are looked up once per face.  A ghost is
 // P's value plus, per axis, s (c+ - c-)/8, s = +1 or -1 for the ghost's
 // high or low daughter position in P (a component is 0 where one of P's
-// neighbours does not exist).  Written as FP64 (u, e^u) and FP32 u.
+// neighbours does not exist).  Written as (u, e^u) in FP64 (double-float pairs
+// in the mixed form) and FP32 u.
 __global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restrict__ nbr,
                          const double* __restrict__ up, int linear, double* __restrict__ ghost,
-                         double* __restrict__ ghostE, float* __restrict__ g32) {
+                         double* __restrict__ ghostE, float* __restrict__ g32, int dfmode) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= 6 * n_oct) return;
   const long long o = t / 6;
@@ -1100,9 +1166,16 @@ __global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restri
     for (int a = 0; a < 3; ++a)
       if (have[a]) v += (hi[a] ? 0.125 : -0.125) * g[a];
     const long long q = 24 * o + 4 * d + qi;
-    ghost[q] = v;
-    ghostE[q] = exp(v);
-    g32[q] = (float)v;
+    if (dfmode) {  // double-float slots (phase B of the mixed form), e^v on the FP32 pipes
+      const dfl V = df_from_double(v);
+      reinterpret_cast<dfl*>(ghost)[q] = V;
+      reinterpret_cast<dfl*>(ghostE)[q] = df_exp(V);
+      g32[q] = V.hi;
+    } else {
+      ghost[q] = v;
+      ghostE[q] = exp(v);
+      g32[q] = (float)v;
+    }
   }
 }
 
@@ -1552,9 +1625,11 @@ mgfr_status lin_resid(SolveCtx& S, double* hs) {
   DenseHier& H = c->dh;
   const int nparts = (int)std::min<long long>(H.nparts / 2, nblocks(L.ncell, BS));
   if (c->capturing >= 0) prof_begin(c, 2, L.ncell);
-  k_oresid_lin<<<nparts, BS, 0, c->s>>>(L.w, L.wE, L.wf, L.nbr, L.ghost, L.ghostE, L.ncell,
-                                        mt<double>(S.m), L.ih2, L.wf32, L.w32, L.wold32,
-                                        H.partials);
+  k_oresid_df<<<nparts, BS, 0, c->s>>>(
+      reinterpret_cast<const dfl*>(L.w), reinterpret_cast<const dfl*>(L.wE),
+      reinterpret_cast<const dfl*>(L.wf), L.nbr, reinterpret_cast<const dfl*>(L.ghost),
+      reinterpret_cast<const dfl*>(L.ghostE), L.ncell, mdf(S.m, L.ih2), L.wf32, L.w32, L.wold32,
+      H.partials);
   if (c->capturing >= 0) prof_end(c);
   k_finish3<<<1, 256, 0, c->s>>>(H.partials, nparts, H.scal + 8);
   c->launches += 2;
@@ -1589,15 +1664,22 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
   const float mthr = (float)g.mask_thres;
   TreeView T = tree_view(A);
   const double* up = Lv - 1 == 0 ? H.L[0].u : A->L[Lv - 1].u;
+  // the mixed form keeps the FP64 ghost slots as double-float pairs until the
+  // level is finished
+  bool gh_df = mixed, w_df = false;
   k_ghosts<<<nblocks(6 * F.n_oct, BS), BS, 0, c->s>>>(F.n_oct, Lv, T, F.nbr, up,
                                                       g.prolong_linear, F.ghost, F.ghostE,
-                                                      F.ghost32);
+                                                      F.ghost32, mixed ? 1 : 0);
   c->launches += 1;
   k_init_level<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.ncell, F.pcell, F.pnbr, up,
                                                       g.prolong_linear, F.w, F.wE,
                                                       mixed ? F.w32 : nullptr);
-  MG_CK(c, cudaMemcpyAsync(F.wf, F.f, sizeof(double) * (size_t)F.ncell, cudaMemcpyDeviceToDevice,
-                           c->s));
+  if (mixed) {
+    k_d2df<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.f, reinterpret_cast<dfl*>(F.wf), F.ncell);
+  } else {
+    MG_CK(c, cudaMemcpyAsync(F.wf, F.f, sizeof(double) * (size_t)F.ncell,
+                             cudaMemcpyDeviceToDevice, c->s));
+  }
   k_fill_f<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.mask, F.ncell, 1.f);
   c->launches += 3;
   if (mixed) {
@@ -1676,9 +1758,12 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
         break;
       prev = r32;
     }
-    k_f2d_exp<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.w32, F.w, F.wE, F.ncell);
+    k_f2df_exp<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.w32, reinterpret_cast<dfl*>(F.w),
+                                                      reinterpret_cast<dfl*>(F.wE), F.ncell);
     c->launches += 1;
-    // phase B: FP64 residual, FP32 linear masked V-cycle on J(u) e = r, u += e
+    w_df = true;
+    // phase B: FP64-accurate residual (double-float), FP32 linear masked
+    // V-cycles on J(u) e = r, u += e
     for (int l = Lv - 1; l >= 0; --l) {
       AmrLevel& P = A->L[l];
       k_zero32<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(P.wold32, P.ncell);
@@ -1697,7 +1782,9 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
     while (r > target && it < g.max_vcycles) {
       c->capturing = 3;
       for (int q = 0; q < inner; ++q) lin_vcycle_tree(S, Lv);
-      k_apply_lin<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.w, F.wE, F.wold32, F.ncell, g.step_cap);
+      k_apply_df<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(reinterpret_cast<dfl*>(F.w),
+                                                        reinterpret_cast<dfl*>(F.wE), F.wold32,
+                                                        F.ncell, (float)g.step_cap);
       c->launches += 1;
       TRY(lin_resid(S, hs));
       c->capturing = -1;
@@ -1722,17 +1809,50 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
     k_f2d_exp<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.w32, F.w, F.wE, F.ncell);
     c->launches += 1;
   }
-  if (mixed && r > target) TRY(fp64_coarse());
+  if (mixed && r > target) {
+    // FP64 fallback: the iterate, source and ghosts back to FP64
+    if (w_df) {
+      k_df2d<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(reinterpret_cast<const dfl*>(F.w), F.w,
+                                                    F.ncell);
+      k_df2d<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(reinterpret_cast<const dfl*>(F.wE), F.wE,
+                                                    F.ncell);
+      c->launches += 2;
+      w_df = false;
+    }
+    MG_CK(c, cudaMemcpyAsync(F.wf, F.f, sizeof(double) * (size_t)F.ncell,
+                             cudaMemcpyDeviceToDevice, c->s));
+    k_ghosts<<<nblocks(6 * F.n_oct, BS), BS, 0, c->s>>>(F.n_oct, Lv, T, F.nbr, up,
+                                                        g.prolong_linear, F.ghost, F.ghostE,
+                                                        F.ghost32, 0);
+    c->launches += 1;
+    gh_df = false;
+    TRY(fp64_coarse());
+  }
   while (r > target && it < g.max_vcycles) {
     TRY(run_vcycle<double>(S, st, hs));
     r = std::sqrt(hs[0]);
     ++it;
     if (!std::isfinite(r)) break;
   }
-  MG_CK(c, cudaMemcpyAsync(F.u, F.w, sizeof(double) * (size_t)F.ncell, cudaMemcpyDeviceToDevice,
-                           c->s));
-  MG_CK(c, cudaMemcpyAsync(F.E, F.wE, sizeof(double) * (size_t)F.ncell, cudaMemcpyDeviceToDevice,
-                           c->s));
+  if (w_df) {
+    k_df2d<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(reinterpret_cast<const dfl*>(F.w), F.u,
+                                                  F.ncell);
+    k_df2d<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(reinterpret_cast<const dfl*>(F.wE), F.E,
+                                                  F.ncell);
+    c->launches += 2;
+  } else {
+    MG_CK(c, cudaMemcpyAsync(F.u, F.w, sizeof(double) * (size_t)F.ncell,
+                             cudaMemcpyDeviceToDevice, c->s));
+    MG_CK(c, cudaMemcpyAsync(F.E, F.wE, sizeof(double) * (size_t)F.ncell,
+                             cudaMemcpyDeviceToDevice, c->s));
+  }
+  if (gh_df) {  // FP64 ghosts for the force at patch edges
+    k_df2d<<<nblocks(24 * F.n_oct, BS), BS, 0, c->s>>>(reinterpret_cast<const dfl*>(F.ghost),
+                                                       F.ghost, 24 * F.n_oct);
+    k_df2d<<<nblocks(24 * F.n_oct, BS), BS, 0, c->s>>>(reinterpret_cast<const dfl*>(F.ghostE),
+                                                       F.ghostE, 24 * F.n_oct);
+    c->launches += 2;
+  }
   if (st) {
     st->level_iters[Lv] = it + it32;
     st->level_res[Lv] = r / ref;
