@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "amr.cuh"
+#include "dfloat.cuh"
 
 namespace {
 
@@ -481,8 +482,8 @@ struct OctNbE {
 // oct, or the ghost slot of the face).
 __device__ __forceinline__ double oct_nbE(const double* __restrict__ E,
                                          const int* __restrict__ nbr,
-                                         const double* __restrict__ ghostE, long long o, int ch,
-                                         int d) {
+                                         const double* __restrict__ ghostE, int gdf, long long o,
+                                         int ch, int d) {
   const int ax = d >> 1, plus = d & 1;
   const int bit = (ch >> (2 - ax)) & 1;
   const int chn = ch ^ (1 << (2 - ax));
@@ -491,7 +492,8 @@ __device__ __forceinline__ double oct_nbE(const double* __restrict__ E,
   if (no >= 0) return E[8LL * no + chn];
   const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
   const int qi = (((ch >> (2 - t1)) & 1) << 1) | ((ch >> (2 - t2)) & 1);
-  return ghostE[24 * o + 4 * d + qi];
+  const long long g = 24 * o + 4 * d + qi;
+  return gdf ? df_to_double(reinterpret_cast<const dfl*>(ghostE)[g]) : ghostE[g];
 }
 
 __global__ void k_oct_pnbrs(long long n_oct, int l, TreeView T, int* __restrict__ pnbr) {
@@ -508,7 +510,8 @@ __global__ void k_oct_pnbrs(long long n_oct, int l, TreeView T, int* __restrict_
 
 // f_R and a_MG/c^2 on a refined level (central differences, ghosts at edges)
 __global__ void k_oct_force(const double* __restrict__ E, const int* __restrict__ nbr,
-                            const double* __restrict__ ghostE, long long ncell, double fbar,
+                            const double* __restrict__ ghostE, int gdf, long long ncell,
+                            double fbar,
                             double g_scale, double* __restrict__ fr, double* __restrict__ acc,
                             float4* __restrict__ acc32) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -517,8 +520,8 @@ __global__ void k_oct_force(const double* __restrict__ E, const int* __restrict_
   const int ch = (int)(c & 7);
   fr[c] = fbar * E[c];
   for (int ax = 0; ax < 3; ++ax) {
-    const double em = oct_nbE(E, nbr, ghostE, o, ch, 2 * ax);
-    const double ep = oct_nbE(E, nbr, ghostE, o, ch, 2 * ax + 1);
+    const double em = oct_nbE(E, nbr, ghostE, gdf, o, ch, 2 * ax);
+    const double ep = oct_nbE(E, nbr, ghostE, gdf, o, ch, 2 * ax + 1);
     acc[3 * c + ax] = g_scale * (ep - em);
   }
   if (acc32)
@@ -833,7 +836,8 @@ mgfr_status mgfr_solve_particles(mgfr_ctx* c, const double* pos, long long Np, i
   for (int l = 1; l < A->nlev; ++l) {
     AmrLevel& L = A->L[l];
     const double gs = m.fbar / (2.0 * L.h) / (2.0 * m.a);
-    k_oct_force<<<nblocks(L.ncell, BS), BS, 0, c->s>>>(L.E, L.nbr, L.ghostE, L.ncell, m.fbar, gs,
+    k_oct_force<<<nblocks(L.ncell, BS), BS, 0, c->s>>>(L.E, L.nbr, L.ghostE, L.ghost_df ? 1 : 0,
+                                                       L.ncell, m.fbar, gs,
                                                        L.w, L.acc, g32 ? L.acc32 : nullptr);
     G.acc[l] = L.acc;
     G.acc32[l] = L.acc32;

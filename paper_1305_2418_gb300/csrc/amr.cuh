@@ -38,6 +38,7 @@ struct AmrLevel {
   float *w32 = nullptr, *wE32 = nullptr, *wf32 = nullptr, *wold32 = nullptr;
   float* ghost32 = nullptr;           // [n_oct*24] FP32 ghost u (e^u recomputed)
   long long relaxed = 0;              // cells relaxed in the current level solve
+  bool ghost_df = false;              // FP64 ghost slots hold double-float pairs (mixed form)
   int* olist = nullptr;               // [n_oct] octs with a relaxed cell (coarse level of a solve)
   long long n_list = 0;               // entries of olist in use
 };

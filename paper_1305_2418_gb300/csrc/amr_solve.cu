@@ -980,13 +980,6 @@ MDF mdf(const Model& m, double ih2) {
   return MDF{df_from_double(m.aRt), df_from_double(m.inv_np1), df_from_double(0.5 * ih2), m.n};
 }
 
-// a + b with error below ~2^-46 (|a| + |b|): the absolute accuracy the FP64
-// residual needs (its inputs carry the same relative error)
-__device__ __forceinline__ dfl df_add_abs(dfl a, dfl b) {
-  const dfl s = df_two_sum(a.hi, b.hi);
-  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-
 // neighbour of cell (o, ch) in direction d: same oct, neighbouring oct, or ghost
 __device__ __forceinline__ void onb_df(const dfl* __restrict__ u, const dfl* __restrict__ E,
                                        const int* __restrict__ nbr, const dfl* __restrict__ gh,
@@ -1846,13 +1839,7 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
     MG_CK(c, cudaMemcpyAsync(F.E, F.wE, sizeof(double) * (size_t)F.ncell,
                              cudaMemcpyDeviceToDevice, c->s));
   }
-  if (gh_df) {  // FP64 ghosts for the force at patch edges
-    k_df2d<<<nblocks(24 * F.n_oct, BS), BS, 0, c->s>>>(reinterpret_cast<const dfl*>(F.ghost),
-                                                       F.ghost, 24 * F.n_oct);
-    k_df2d<<<nblocks(24 * F.n_oct, BS), BS, 0, c->s>>>(reinterpret_cast<const dfl*>(F.ghostE),
-                                                       F.ghostE, 24 * F.n_oct);
-    c->launches += 2;
-  }
+  F.ghost_df = gh_df;  // the force kernel reads the ghosts in either form
   if (st) {
     st->level_iters[Lv] = it + it32;
     st->level_res[Lv] = r / ref;

@@ -13,6 +13,7 @@
 // nonlinear FP32 correction.
 #include <algorithm>
 
+#include "dfloat.cuh"
 #include "mgfr_internal.cuh"
 
 namespace {
@@ -251,49 +252,56 @@ __global__ void k_from64(const double* __restrict__ x, float* __restrict__ y, lo
   if (t < n) y[t] = (float)x[t];
 }
 
-__global__ void k_to64(const float* __restrict__ u32, double* __restrict__ u, double* __restrict__ E,
-                       long long n) {
+// FP32 iterate -> double-float iterate and its e^u (start of phase B)
+__global__ void k_to_df(const float* __restrict__ u32, dfl* __restrict__ u, dfl* __restrict__ E,
+                        long long n) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const double v = (double)u32[t];
+  const dfl v{u32[t], 0.f};
   u[t] = v;
-  E[t] = exp(v);
+  E[t] = df_exp(v);
 }
 
 // ---- Phase B ---------------------------------------------------------------
-__device__ __forceinline__ double nl_s64(double u, double E, int n, double inv_np1) {
-  return n == 1 ? rsqrt(E) : exp(-u * inv_np1);
-}
+// Model constants as double-float pairs (phase B in double-float)
+struct DFM {
+  dfl aRt, inv_np1, ih2h;  // alpha Rt, 1/(n+1), 1/(2 h^2)
+  int n;
+};
 
-// r = f - L(u) in FP64 on the FP64 iterate; stores r and u rounded to FP32,
-// zeroes the correction e, and accumulates the norms.
-__global__ void __launch_bounds__(BS) k_resid64(const double* __restrict__ u,
-                                                const double* __restrict__ E,
-                                                const double* __restrict__ f, int lg, Model m,
-                                                double ih2, float* __restrict__ r32,
-                                                float* __restrict__ u32, float* __restrict__ e32,
-                                                double* __restrict__ partials) {
-  const int N = 1 << lg, M = N - 1;
+// r = f - L(u) to FP64 accuracy in double-float on the FP32 pipes (u, E, f
+// held as hi + lo pairs); stores r and u rounded to FP32, zeroes the
+// correction e, and accumulates the norms (FP32 within a thread).
+__global__ void __launch_bounds__(BS) k_resid_df(const dfl* __restrict__ u,
+                                                 const dfl* __restrict__ E,
+                                                 const dfl* __restrict__ f, int lg, DFM m,
+                                                 float* __restrict__ r32,
+                                                 float* __restrict__ u32, float* __restrict__ e32,
+                                                 double* __restrict__ partials) {
+  const int M = (1 << lg) - 1;
   const unsigned n = 1u << (3 * lg);
-  double ss = 0.0, mx = 0.0;
+  float ss = 0.f, mx = 0.f;
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += gridDim.x * blockDim.x) {
     const int k = (int)(t & M), j = (int)((t >> lg) & M), i = (int)(t >> (2 * lg));
     const unsigned nb[6] = {cidx((i - 1) & M, j, k, lg), cidx((i + 1) & M, j, k, lg),
                              cidx(i, (j - 1) & M, k, lg), cidx(i, (j + 1) & M, k, lg),
                              cidx(i, j, (k - 1) & M, lg), cidx(i, j, (k + 1) & M, lg)};
-    const double uc = u[t], Ec = E[t];
-    double sbd = 0.0;
+    const dfl uc = u[t], Ec = E[t];
+    dfl acc = {0.f, 0.f};
 #pragma unroll
-    for (int q = 0; q < 6; ++q) sbd = fma(0.5 * (E[nb[q]] + Ec), u[nb[q]] - uc, sbd);
-    const double r = f[t] - (sbd * ih2 + m.aRt * (1.0 - nl_s64(uc, Ec, m.n, m.inv_np1)));
-    r32[t] = (float)r;
-    u32[t] = (float)uc;
+    for (int q = 0; q < 6; ++q)
+      acc = df_add_abs(acc, df_mul(df_add_abs(E[nb[q]], Ec), df_add_abs(u[nb[q]], df_neg(uc))));
+    const dfl sN = m.n == 1 ? df_rsqrt(Ec) : df_exp(df_neg(df_mul(uc, m.inv_np1)));
+    const dfl L = df_add(df_mul(acc, m.ih2h), df_mul(m.aRt, df_add_f(df_neg(sN), 1.f)));
+    const dfl r = df_sub(f[t], L);
+    r32[t] = r.hi;
+    u32[t] = uc.hi;
     e32[t] = 0.f;
-    ss = fma(r, r, ss);
-    mx = fmax(mx, fabs(r));
+    ss = fmaf(r.hi, r.hi, ss);
+    mx = fmaxf(mx, fabsf(r.hi));
   }
-  block_partial(ss, mx, partials);
+  block_partial((double)ss, (double)mx, partials);
 }
 
 // Jacobian of L at u (neighbours j of cell i):
@@ -408,14 +416,28 @@ __global__ void __launch_bounds__(64) k_lin_coarse(float* __restrict__ eg, const
   eg[t] = e[t];
 }
 
-__global__ void k_apply_corr(double* __restrict__ u, double* __restrict__ E,
-                             const float* __restrict__ e, long long n, double cap) {
+__global__ void k_apply_corr(dfl* __restrict__ u, dfl* __restrict__ E, const float* __restrict__ e,
+                             long long n, float cap) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const double d = fmin(fmax((double)e[t], -cap), cap);
-  const double v = u[t] + d;
+  const dfl v = df_add_f(u[t], fminf(fmaxf(e[t], -cap), cap));
   u[t] = v;
-  E[t] = exp_after_step(E[t], v, d);
+  E[t] = df_exp(v);
+}
+
+__global__ void k_d2df(const double* __restrict__ x, dfl* __restrict__ y, long long n) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    const double v = x[t];
+    y[t] = df_from_double(v);
+  }
+}
+__global__ void k_df2d(const dfl* __restrict__ x, double* __restrict__ y, long long n) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    const dfl v = x[t];
+    y[t] = df_to_double(v);
+  }
 }
 
 __global__ void k_zero(float* __restrict__ x, long long n) {
@@ -453,7 +475,17 @@ namespace f32 {
 void from64(const double* x, float* y, long long n, cudaStream_t s) {
   k_from64<<<nblocks(n, BS), BS, 0, s>>>(x, y, n);
 }
-void to64(DenseLevel& L, cudaStream_t s) { k_to64<<<nblocks(L.n, BS), BS, 0, s>>>(L.u32, L.u, L.E, L.n); }
+void to_df(DenseLevel& L, cudaStream_t s) {
+  k_to_df<<<nblocks(L.n, BS), BS, 0, s>>>(L.u32, reinterpret_cast<dfl*>(L.u),
+                                          reinterpret_cast<dfl*>(L.E), L.n);
+}
+void f_to_df(const double* f, double* fdf, long long n, cudaStream_t s) {
+  k_d2df<<<nblocks(n, BS), BS, 0, s>>>(f, reinterpret_cast<dfl*>(fdf), n);
+}
+void state_to_fp64(DenseLevel& L, cudaStream_t s) {
+  k_df2d<<<nblocks(L.n, BS), BS, 0, s>>>(reinterpret_cast<const dfl*>(L.u), L.u, L.n);
+  k_df2d<<<nblocks(L.n, BS), BS, 0, s>>>(reinterpret_cast<const dfl*>(L.E), L.E, L.n);
+}
 
 void sweep(DenseLevel& L, const Model& m, int colour, float cap, cudaStream_t s) {
   k_sweep32<<<nblocks(L.n / 2, BS), BS, 0, s>>>(L.u32, L.f32, L.lg, colour, to_f(m), (float)L.ih2,
@@ -478,10 +510,14 @@ void norm32(DenseLevel& L, const Model& m, double* partials, int nparts, double*
   k_norm32<<<nb, BS, 0, s>>>(L.u32, L.f32, L.lg, L.n, to_f(m), (float)L.ih2, partials);
   k_finish32<<<1, 256, 0, s>>>(partials, nb, out);
 }
-void resid64(DenseLevel& L, const Model& m, double* partials, int nparts, double* out,
-             cudaStream_t s) {
+void resid_df(DenseLevel& L, const double* fdf, const Model& m, double* partials, int nparts,
+              double* out, cudaStream_t s) {
   int nb = (int)std::min<long long>(nparts, nblocks(L.n, BS));
-  k_resid64<<<nb, BS, 0, s>>>(L.u, L.E, L.f, L.lg, m, L.ih2, L.r32, L.u32, L.e32, partials);
+  const DFM dm{df_from_double(m.aRt), df_from_double(m.inv_np1), df_from_double(0.5 * L.ih2),
+               m.n};
+  k_resid_df<<<nb, BS, 0, s>>>(reinterpret_cast<const dfl*>(L.u), reinterpret_cast<const dfl*>(L.E),
+                               reinterpret_cast<const dfl*>(fdf), L.lg, dm, L.r32, L.u32, L.e32,
+                               partials);
   k_finish32<<<1, 256, 0, s>>>(partials, nb, out);
 }
 void lin_sweep(DenseLevel& L, const Model& m, int colour, cudaStream_t s) {
@@ -500,7 +536,8 @@ void lin_coarse(DenseLevel& C, const Model& m, int sweeps, cudaStream_t s) {
 }
 void zero(float* x, long long n, cudaStream_t s) { k_zero<<<nblocks(n, BS), BS, 0, s>>>(x, n); }
 void apply_corr(DenseLevel& L, double cap, cudaStream_t s) {
-  k_apply_corr<<<nblocks(L.n, BS), BS, 0, s>>>(L.u, L.E, L.e32, L.n, cap);
+  k_apply_corr<<<nblocks(L.n, BS), BS, 0, s>>>(reinterpret_cast<dfl*>(L.u),
+                                               reinterpret_cast<dfl*>(L.E), L.e32, L.n, (float)cap);
 }
 
 }  // namespace f32

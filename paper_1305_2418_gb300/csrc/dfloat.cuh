@@ -68,6 +68,14 @@ __host__ __device__ __forceinline__ dfl df_add(dfl a, dfl b) {
 
 __host__ __device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
 
+// a + b with error below ~2^-46 (|a| + |b|): the absolute accuracy of the
+// inputs themselves, enough where the result is not needed relative to a
+// cancelled sum
+__host__ __device__ __forceinline__ dfl df_add_abs(dfl a, dfl b) {
+  const dfl s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, DF_ADD(s.lo, DF_ADD(a.lo, b.lo)));
+}
+
 // a + b with b a float
 __host__ __device__ __forceinline__ dfl df_add_f(dfl a, float b) {
   dfl s = df_two_sum(a.hi, b);

@@ -74,6 +74,7 @@ struct DenseHier {
   DenseLevel L[MGFR_MAX_DENSE];
   double* partials = nullptr;  // reduction scratch (2 doubles per block)
   double* scal = nullptr;      // device scalars: [0..1] last norm, [2..7] spare
+  double* fdf = nullptr;       // base-level f as double-float pairs (mixed form)
   int nparts = 0;
 };
 
@@ -107,20 +108,27 @@ void coarse_solve(DenseLevel& C, const Model& m, float step_cap, int max_sweeps,
 // FP32 residual norms of the FP32 iterate (sum r^2, max|r|) into out.
 void norm32(DenseLevel& L, const Model& m, double* partials, int nparts, double* out,
             cudaStream_t s);
-// Phase B: FP64 residual of u64; writes r32 = (f - L(u)), u32 = u, and
-// norms (sum r^2, max|r|) into out.
-void resid64(DenseLevel& L, const Model& m, double* partials, int nparts, double* out,
-             cudaStream_t s);
+// Phase B.  From to_df until state_to_fp64, L.u and L.E hold the iterate and
+// e^u as double-float pairs (hi + lo floats in each 8-byte slot).
+// FP64-accurate residual in double-float (fdf: f as pairs, see f_to_df);
+// writes r32 = f - L(u), u32 = u rounded, e32 = 0, and the norms (sum r^2,
+// max|r|) into out.
+void resid_df(DenseLevel& L, const double* fdf, const Model& m, double* partials, int nparts,
+              double* out, cudaStream_t s);
 // Linear Gauss-Seidel on J(u32) e = r (J: Jacobian of L at u32).
 void lin_sweep(DenseLevel& L, const Model& m, int colour, cudaStream_t s);
 void lin_restrict(DenseLevel& F, DenseLevel& C, const Model& m, cudaStream_t s);
 void lin_prolong(DenseLevel& F, DenseLevel& C, int linear, cudaStream_t s);
 void lin_coarse(DenseLevel& C, const Model& m, int sweeps, cudaStream_t s);
 void zero(float* x, long long n, cudaStream_t s);
-// u64 += clamp(e, cap); E64 = exp(u64)
+// u += clamp(e, cap); E = e^u (double-float)
 void apply_corr(DenseLevel& L, double cap, cudaStream_t s);
-// u64 = u32; E64 = exp(u64)
-void to64(DenseLevel& L, cudaStream_t s);
+// u = u32, E = e^u as double-float pairs
+void to_df(DenseLevel& L, cudaStream_t s);
+// f (FP64) -> fdf (double-float pairs, same size)
+void f_to_df(const double* f, double* fdf, long long n, cudaStream_t s);
+// L.u, L.E: double-float pairs -> FP64 (in place)
+void state_to_fp64(DenseLevel& L, cudaStream_t s);
 }  // namespace f32
 
 // ---- context ---------------------------------------------------------------

@@ -166,6 +166,7 @@ static void free_dense(DenseHier& H) {
   }
   if (H.partials) cudaFree(H.partials);
   if (H.scal) cudaFree(H.scal);
+  if (H.fdf) cudaFree(H.fdf);
   H = DenseHier();
 }
 
@@ -209,6 +210,7 @@ static mgfr_status ensure_dense(mgfr_ctx* c, int N, bool mixed) {
     }
   }
   H.nparts = 152 * 8;
+  if (mixed) MG_CK(c, cudaMalloc(&H.fdf, sizeof(double) * (size_t)H.L[0].n));
   MG_CK(c, cudaMalloc(&H.partials, sizeof(double) * 2 * H.nparts));
   MG_CK(c, cudaMalloc(&H.scal, sizeof(double) * 16));
   return MGFR_OK;
@@ -477,7 +479,7 @@ mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stat
     for (int q = 0; q < g.mixed_inner; ++q) vcycle_lin(c, m, 0, upd);
     f32::apply_corr(L0, g.step_cap, c->s);
     prof_begin(c, 2, L0.n);
-    f32::resid64(L0, m, H.partials, H.nparts, H.scal, c->s);
+    f32::resid_df(L0, H.fdf, m, H.partials, H.nparts, H.scal, c->s);
     prof_end(c);
     cudaMemcpyAsync(hs, H.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s);
   };
@@ -491,6 +493,11 @@ mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stat
   }
   int vc = 0, outer = 0;
   double r = r0;
+  bool state_df = false;  // L0.u, L0.E hold double-float pairs (phase B)
+  if (r > target) {
+    f32::f_to_df(L0.f, H.fdf, L0.n, c->s);
+    c->launches += 1;
+  }
   // Phases alternate: A until it reaches mixed_switch or stalls, then B while
   // the FP64 residual keeps falling; a rise in B sends the iterate back to A.
   for (int round = 0; round < 8 && r > target; ++round) {
@@ -506,9 +513,10 @@ mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stat
       if (prev > 0.0 && r32 > 0.7 * prev) break;
       prev = r32;
     }
-    f32::to64(L0, c->s);
-    f32::resid64(L0, m, H.partials, H.nparts, H.scal, c->s);
+    f32::to_df(L0, c->s);
+    f32::resid_df(L0, H.fdf, m, H.partials, H.nparts, H.scal, c->s);
     c->launches += 3;
+    state_df = true;
     MG_CK(c, cudaMemcpyAsync(hs, H.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
     if ((rs = sync_read(c)) != MGFR_OK) return rs;
     r = std::sqrt(hs[0]);
@@ -528,6 +536,10 @@ mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stat
     }
     if (!rose || vc >= g.max_vcycles) break;
     // back to phase A from the current FP64 iterate (u32 = fp32(u) already)
+  }
+  if (state_df) {  // the FP64 iterate and e^u for the caller
+    f32::state_to_fp64(L0, c->s);
+    c->launches += 2;
   }
   if (st) {
     st->vcycles = vc;
