@@ -135,7 +135,9 @@ def test_full_size_sampled_residual(dev, prec):
     # consistent with the reported global max-norm residual
     assert np.abs(r).max() <= 1.01 * st["res_max_final"] + 1e-300
     assert np.abs(r).max() <= 1e-6 * np.abs(f).max()
-    # f_R and u consistent at the samples
+    # f_R = fbar e^u at the samples (Sec. 3.2); the mixed form takes e^u from
+    # the double-float exponential (relative error <= 1e-13, test_dfloat_host)
     fbar = oracle.model_constants(fr0)["fbar"]
+    rtol = 1e-15 if prec == mgfr.PREC_FP64 else 1e-13
     assert np.allclose(got["fr"].ravel()[cells], fbar * np.exp(got["u"].ravel()[cells]),
-                       rtol=1e-15, atol=0)
+                       rtol=rtol, atol=0)
