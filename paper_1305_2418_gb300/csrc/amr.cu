@@ -540,7 +540,7 @@ static void free_level(AmrLevel& L) {
   void* ps[] = {L.son,  L.refined, L.count,  L.opos, L.pcell,   L.nbr,     L.mass,
                 L.w,    L.wE,      L.wf,     L.wold, L.mask,    L.ghost,   L.ghostE,
                 L.acc,  L.pnbr,    L.w32,    L.wE32, L.wf32,    L.wold32,  L.ghost32,
-                L.olist,  L.acc32};
+                L.olist,  L.acc32, L.act};
   for (void* p : ps)
     if (p) cudaFree(p);
   // u, E, f of level >= 1 are owned here too
@@ -557,8 +557,10 @@ void amr_free(mgfr_ctx* c) {
       if (A->L[l].f) cudaFree(A->L[l].f);
     }
   }
-  for (int l = 0; l < MGFR_MAX_DENSE; ++l)
+  for (int l = 0; l < MGFR_MAX_DENSE; ++l) {
     if (A->dmask[l]) cudaFree(A->dmask[l]);
+    if (A->dact[l]) cudaFree(A->dact[l]);
+  }
   if (A->blocksums) cudaFree(A->blocksums);
   if (A->d_small) cudaFree(A->d_small);
   if (A->acc0) cudaFree(A->acc0);
@@ -612,7 +614,7 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
   L.nbr = nullptr; L.mass = nullptr; L.w = nullptr; L.wE = nullptr; L.wf = nullptr;
   L.wold = nullptr; L.mask = nullptr; L.ghost = nullptr; L.ghostE = nullptr; L.acc = nullptr;
   L.pnbr = nullptr; L.w32 = nullptr; L.wE32 = nullptr; L.wf32 = nullptr; L.wold32 = nullptr;
-  L.ghost32 = nullptr; L.olist = nullptr; L.acc32 = nullptr;
+  L.ghost32 = nullptr; L.olist = nullptr; L.acc32 = nullptr; L.act = nullptr;
   TRY(grow(c, &L.son, n));
   TRY(grow(c, &L.refined, n));
   TRY(grow(c, &L.count, n));
@@ -622,6 +624,7 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
   TRY(grow(c, &L.wf, n));
   TRY(grow(c, &L.wold, n));
   TRY(grow(c, &L.mask, n));
+  TRY(grow(c, &L.act, n));
   TRY(grow(c, &L.w32, n));
   TRY(grow(c, &L.wE32, n));
   TRY(grow(c, &L.wf32, n));
@@ -758,11 +761,16 @@ mgfr_status mgfr_solve_particles(mgfr_ctx* c, const double* pos, long long Np, i
   int lg0 = 0;
   while ((1 << lg0) < N0) ++lg0;
   if (A->N0 != N0) {
-    for (int k = 0; k < MGFR_MAX_DENSE; ++k)
+    for (int k = 0; k < MGFR_MAX_DENSE; ++k) {
       if (A->dmask[k]) {
         cudaFree(A->dmask[k]);
         A->dmask[k] = nullptr;
       }
+      if (A->dact[k]) {
+        cudaFree(A->dact[k]);
+        A->dact[k] = nullptr;
+      }
+    }
     if (A->acc0) cudaFree(A->acc0);
     if (A->fr0) cudaFree(A->fr0);
     if (A->acc0_32) cudaFree(A->acc0_32);
@@ -774,8 +782,10 @@ mgfr_status mgfr_solve_particles(mgfr_ctx* c, const double* pos, long long Np, i
   A->box = box;
   A->Np = Np;
   DenseHier& H = c->dh;
-  for (int k = 1; k < H.nlev; ++k)
+  for (int k = 1; k < H.nlev; ++k) {
     if (!A->dmask[k]) MG_CK(c, cudaMalloc(&A->dmask[k], sizeof(float) * (size_t)H.L[k].n));
+    if (!A->dact[k]) MG_CK(c, cudaMalloc(&A->dact[k], (size_t)H.L[k].n));
+  }
   if (!A->acc0) MG_CK(c, cudaMalloc(&A->acc0, sizeof(double) * 3 * (size_t)H.L[0].n));
   if (!A->fr0) MG_CK(c, cudaMalloc(&A->fr0, sizeof(double) * (size_t)H.L[0].n));
   if (mixed && !A->acc0_32)

@@ -39,6 +39,7 @@ struct AmrLevel {
   float* ghost32 = nullptr;           // [n_oct*24] FP32 ghost u (e^u recomputed)
   long long relaxed = 0;              // cells relaxed in the current level solve
   bool ghost_df = false;              // FP64 ghost slots hold double-float pairs (mixed form)
+  unsigned char* act = nullptr;       // [ncell] mask > threshold (coarse level of a solve)
   int* olist = nullptr;               // [n_oct] octs with a relaxed cell (coarse level of a solve)
   long long n_list = 0;               // entries of olist in use
 };
@@ -96,6 +97,7 @@ struct AmrWork {
   long long Np = 0;
   AmrLevel L[AMR_MAXL];
   float* dmask[MGFR_MAX_DENSE] = {};  // masks of the dense levels below the base
+  unsigned char* dact[MGFR_MAX_DENSE] = {};  // their mask > threshold flags
   int* blocksums = nullptr;
   long long blocksums_cap = 0;
   long long* d_small = nullptr;       // device scalars (totals, error flags)

@@ -122,7 +122,7 @@ template <class T>
 __global__ void __launch_bounds__(BS) k_osweep(T* __restrict__ u, T* __restrict__ E,
                                                const T* __restrict__ f, const int* __restrict__ nbr,
                                                const T* __restrict__ gh, const T* __restrict__ ghE,
-                                               const float* __restrict__ mask, float mthr,
+                                               const unsigned char* __restrict__ act,
                                                long long n_oct, const int* __restrict__ olist,
                                                int colour, MT<T> m, T ih2, T cap) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(BS) k_osweep(T* __restrict__ u, T* __restrict_
   const long long o = olist ? olist[t >> 2] : t >> 2;
   const int ch = kColourChild[colour][t & 3];
   const long long c = 8 * o + ch;
-  if (mask && !(mask[c] > mthr)) return;
+  if (act && !(act[c])) return;
   NB<T> nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
@@ -145,7 +145,7 @@ template <class T>
 __global__ void __launch_bounds__(BS) k_orestrict(
     const T* __restrict__ u, const T* __restrict__ E, const T* __restrict__ f,
     const int* __restrict__ nbr, const T* __restrict__ gh, const T* __restrict__ ghE,
-    const float* __restrict__ mask, float mthr, long long n_oct, const int* __restrict__ olist,
+    const unsigned char* __restrict__ act, long long n_oct, const int* __restrict__ olist,
     const int* __restrict__ pcell, MT<T> m, T ih2, T* __restrict__ uc, T* __restrict__ Ec,
     T* __restrict__ ucold, T* __restrict__ fc) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(BS) k_orestrict(
   for (int ch = 0; ch < 8; ++ch) {
     const long long c = 8 * o + ch;
     su += u[c];
-    if (!mask || mask[c] > mthr) {
+    if (!act || act[c]) {
       NB<T> nb[6];
 #pragma unroll
       for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
@@ -175,7 +175,7 @@ template <class T>
 __global__ void __launch_bounds__(BS) k_ofas(const T* __restrict__ u, const T* __restrict__ E,
                                              T* __restrict__ f, const int* __restrict__ nbr,
                                              const T* __restrict__ gh, const T* __restrict__ ghE,
-                                             const float* __restrict__ mask, float mthr,
+                                             const unsigned char* __restrict__ act,
                                              long long ncell, const int* __restrict__ olist,
                                              MT<T> m, T ih2) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(BS) k_ofas(const T* __restrict__ u, const T* _
   const long long o = olist ? olist[t >> 3] : t >> 3;
   const int ch = (int)(t & 7);
   const long long c = 8 * o + ch;
-  if (!(mask[c] > mthr)) return;
+  if (!(act[c])) return;
   NB<T> nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = onb(u, E, nbr, gh, ghE, o, ch, d);
@@ -199,14 +199,14 @@ __global__ void __launch_bounds__(BS) k_oprolong(long long ncell, const int* __r
                                                  const int* __restrict__ pnbr,
                                                  const T* __restrict__ uc,
                                                  const T* __restrict__ ucold,
-                                                 const float* __restrict__ mask, float mthr,
+                                                 const unsigned char* __restrict__ act,
                                                  int linear, T* __restrict__ u, T* __restrict__ E) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= ncell) return;
   const long long o = olist ? olist[t >> 3] : t >> 3;
   const int ch = (int)(t & 7);
   const long long c = 8 * o + ch;
-  if (mask && !(mask[c] > mthr)) return;
+  if (act && !(act[c])) return;
   const int p = pcell[o];
   T v = uc[p] - ucold[p];
   if (linear) {
@@ -326,8 +326,7 @@ __device__ __forceinline__ void dnb_x(const float* __restrict__ x, int i, int j,
 template <class T>
 __global__ void __launch_bounds__(BS) k_dsweep(T* __restrict__ u, T* __restrict__ E,
                                                const T* __restrict__ f, int lg, int colour, MT<T> m,
-                                               T ih2, T cap, const float* __restrict__ mask,
-                                               float mthr) {
+                                               T ih2, T cap, const unsigned char* __restrict__ act) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = 1 << lg, M = N - 1;
   if (t >= (1u << (3 * lg - 1))) return;
@@ -336,7 +335,7 @@ __global__ void __launch_bounds__(BS) k_dsweep(T* __restrict__ u, T* __restrict_
   const int j = (int)(r & M), i = (int)(r >> lg);
   const int k = 2 * k2 + ((i + j + colour) & 1);
   const unsigned c = cidx(i, j, k, lg);
-  if (mask && !(mask[c] > mthr)) return;
+  if (act && !(act[c])) return;
   NB<T> nb[6];
   dnb(u, E, i, j, k, lg, nb);
   const T uc = u[c];
@@ -350,7 +349,7 @@ __global__ void __launch_bounds__(BS) k_drestrict(const T* __restrict__ u, const
                                                   const T* __restrict__ f, int lgf,
                                                   T* __restrict__ uc, T* __restrict__ Ec,
                                                   T* __restrict__ ucold, T* __restrict__ fc, MT<T> m,
-                                                  T ih2, const float* __restrict__ mask, float mthr) {
+                                                  T ih2, const unsigned char* __restrict__ act) {
   const int lgc = lgf - 1, Nc = 1 << lgc;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (1u << (3 * lgc))) return;
@@ -360,7 +359,7 @@ __global__ void __launch_bounds__(BS) k_drestrict(const T* __restrict__ u, const
     const int i = 2 * I + (q >> 2), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q & 1);
     const unsigned c = cidx(i, j, k, lgf);
     su += u[c];
-    if (!mask || mask[c] > mthr) {
+    if (!act || act[c]) {
       NB<T> nb[6];
       dnb(u, E, i, j, k, lgf, nb);
       sr += f[c] - Lval(u[c], Eat(E, u, c), nb, m, ih2);
@@ -376,11 +375,11 @@ __global__ void __launch_bounds__(BS) k_drestrict(const T* __restrict__ u, const
 template <class T>
 __global__ void __launch_bounds__(BS) k_dfas(const T* __restrict__ u, const T* __restrict__ E,
                                              T* __restrict__ f, int lg, MT<T> m, T ih2,
-                                             const float* __restrict__ mask, float mthr) {
+                                             const unsigned char* __restrict__ act) {
   const int N = 1 << lg;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (1u << (3 * lg))) return;
-  if (mask && !(mask[t] > mthr)) return;
+  if (act && !(act[t])) return;
   const int k = (int)(t & (N - 1)), j = (int)((t >> lg) & (N - 1)), i = (int)(t >> (2 * lg));
   NB<T> nb[6];
   dnb(u, E, i, j, k, lg, nb);
@@ -390,12 +389,11 @@ __global__ void __launch_bounds__(BS) k_dfas(const T* __restrict__ u, const T* _
 template <class T>
 __global__ void __launch_bounds__(BS) k_dprolong(T* __restrict__ u, T* __restrict__ E,
                                                  const T* __restrict__ uc, const T* __restrict__ ucold,
-                                                 int lgf, int linear, const float* __restrict__ mask,
-                                                 float mthr) {
+                                                 int lgf, int linear, const unsigned char* __restrict__ act) {
   const int N = 1 << lgf, lgc = lgf - 1, Mc = (N >> 1) - 1;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (1u << (3 * lgf))) return;
-  if (mask && !(mask[t] > mthr)) return;
+  if (act && !(act[t])) return;
   const int k = (int)(t & (N - 1)), j = (int)((t >> lgf) & (N - 1)), i = (int)(t >> (2 * lgf));
   const int I = i >> 1, J = j >> 1, K = k >> 1;
   auto corr = [&](int a, int b, int c) {
@@ -417,14 +415,13 @@ __global__ void __launch_bounds__(BS) k_dprolong(T* __restrict__ u, T* __restric
 template <class T>
 __global__ void __launch_bounds__(64) k_dcoarse(T* __restrict__ ug, T* __restrict__ Eg,
                                                 const T* __restrict__ fg, MT<T> m, T ih2, T cap,
-                                                int sweeps, const float* __restrict__ mask,
-                                                float mthr) {
+                                                int sweeps, const unsigned char* __restrict__ act) {
   __shared__ T u[64], E[64];
   const int t = threadIdx.x;
   u[t] = ug[t];
   E[t] = Eat(Eg, ug, t);
   const T f = fg[t];
-  const bool active = !mask || mask[t] > mthr;
+  const bool active = !act || act[t];
   const int i = t >> 4, j = (t >> 2) & 3, k = t & 3, colour = (i + j + k) & 1;
   const int q[6] = {(((i + 3) & 3) << 4) | (j << 2) | k, (((i + 1) & 3) << 4) | (j << 2) | k,
                     (i << 4) | (((j + 3) & 3) << 2) | k, (i << 4) | (((j + 1) & 3) << 2) | k,
@@ -473,7 +470,7 @@ __global__ void __launch_bounds__(BS) k_dlin_sweep(float* __restrict__ e, const 
                                                    const float* __restrict__ u,
                                                    const float* __restrict__ E, int lg, int colour,
                                                    MT<float> m, float ih2,
-                                                   const float* __restrict__ mask, float mthr) {
+                                                   const unsigned char* __restrict__ act) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = 1 << lg, M = N - 1;
   if (t >= (1u << (3 * lg - 1))) return;
@@ -482,7 +479,7 @@ __global__ void __launch_bounds__(BS) k_dlin_sweep(float* __restrict__ e, const 
   const int j = (int)(rr & M), i = (int)(rr >> lg);
   const int k = 2 * k2 + ((i + j + colour) & 1);
   const unsigned c = cidx(i, j, k, lg);
-  if (mask && !(mask[c] > mthr)) return;
+  if (act && !(act[c])) return;
   NB<float> nb[6];
   dnb(u, E, i, j, k, lg, nb);
   const JR J = jrow(u[c], Eat(E, u, c), nb, m, ih2);
@@ -501,7 +498,7 @@ __global__ void __launch_bounds__(BS) k_dlin_restrict(const float* __restrict__ 
                                                       float* __restrict__ rc, float* __restrict__ uc,
                                                       float* __restrict__ Ec, float* __restrict__ ec,
                                                       MT<float> m, float ih2,
-                                                      const float* __restrict__ mask, float mthr) {
+                                                      const unsigned char* __restrict__ act) {
   const int lgc = lgf - 1, Nc = 1 << lgc;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (1u << (3 * lgc))) return;
@@ -511,7 +508,7 @@ __global__ void __launch_bounds__(BS) k_dlin_restrict(const float* __restrict__ 
     const int i = 2 * I + (q >> 2), j = 2 * J0 + ((q >> 1) & 1), k = 2 * K + (q & 1);
     const unsigned c = cidx(i, j, k, lgf);
     su += u[c];
-    if (!mask || mask[c] > mthr) {
+    if (!act || act[c]) {
       NB<float> nb[6];
       float en[6];
       dnb(u, E, i, j, k, lgf, nb);
@@ -531,11 +528,11 @@ __global__ void __launch_bounds__(BS) k_dlin_restrict(const float* __restrict__ 
 
 __global__ void __launch_bounds__(BS) k_dlin_prolong(float* __restrict__ e, const float* __restrict__ ec,
                                                      int lgf, int linear,
-                                                     const float* __restrict__ mask, float mthr) {
+                                                     const unsigned char* __restrict__ act) {
   const int N = 1 << lgf, lgc = lgf - 1, Mc = (N >> 1) - 1;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (1u << (3 * lgf))) return;
-  if (mask && !(mask[t] > mthr)) return;
+  if (act && !(act[t])) return;
   const int k = (int)(t & (N - 1)), j = (int)((t >> lgf) & (N - 1)), i = (int)(t >> (2 * lgf));
   const int I = i >> 1, J = j >> 1, K = k >> 1;
   auto cv = [&](int a, int b, int c) { return ec[cidx(a & Mc, b & Mc, c & Mc, lgc)]; };
@@ -552,10 +549,10 @@ __global__ void __launch_bounds__(64) k_dlin_coarse(float* __restrict__ eg, cons
                                                     const float* __restrict__ ug,
                                                     const float* __restrict__ Eg, MT<float> m,
                                                     float ih2, int sweeps,
-                                                    const float* __restrict__ mask, float mthr) {
+                                                    const unsigned char* __restrict__ act) {
   __shared__ float e[64];
   const int t = threadIdx.x;
-  const bool active = !mask || mask[t] > mthr;
+  const bool active = !act || act[t];
   const int i = t >> 4, j = (t >> 2) & 3, k = t & 3, colour = (i + j + k) & 1;
   const int q[6] = {(((i + 3) & 3) << 4) | (j << 2) | k, (((i + 1) & 3) << 4) | (j << 2) | k,
                     (i << 4) | (((j + 3) & 3) << 2) | k, (i << 4) | (((j + 1) & 3) << 2) | k,
@@ -620,8 +617,7 @@ __device__ __forceinline__ int face_q(int ch, int ax) {
 template <bool LIN, int COL>
 __global__ void __launch_bounds__(BS) k_oct_sweep32(
     float* __restrict__ u, float* __restrict__ e, const float* __restrict__ rf,
-    const int* __restrict__ nbr, const float* __restrict__ gh, const float* __restrict__ mask,
-    float mthr, long long n_oct, const int* __restrict__ olist, MT<float> m, float ih2,
+    const int* __restrict__ nbr, const float* __restrict__ gh, const unsigned char* __restrict__ act, long long n_oct, const int* __restrict__ olist, MT<float> m, float ih2,
     float cap) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n_oct) return;
@@ -632,12 +628,12 @@ __global__ void __launch_bounds__(BS) k_oct_sweep32(
 #pragma unroll
   for (int i = 0; i < 8; ++i) EE.v[i] = __expf(U.v[i]);
   Oct8 X = LIN ? ld8(e, o) : U;  // LIN: correction; else unused copy
-  bool act[4];
+  bool on[4];
   float s1[4], s2[4], s3[4];  // LIN: (sum off*e, diag sum, -); NL: (sum b du, sum du, sum b)
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int ch = CC[COL][q];
-    act[q] = !mask || mask[8 * o + ch] > mthr;
+    on[q] = !act || act[8 * o + ch];
     s1[q] = s2[q] = s3[q] = 0.f;
     // in-oct neighbours (other colour, unchanged in this half-sweep)
 #pragma unroll
@@ -701,7 +697,7 @@ __global__ void __launch_bounds__(BS) k_oct_sweep32(
   Oct8 UO = U;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    if (!act[q]) continue;
+    if (!on[q]) continue;
     const int ch = CC[COL][q];
     const float sN = nls(U.v[ch], EE.v[ch], m);
     if (LIN) {
@@ -856,7 +852,7 @@ __global__ void __launch_bounds__(BS) k_onorm32(const float* __restrict__ u,
 // residual f - L(u) over the oct's relaxed cells.
 __global__ void __launch_bounds__(BS) k_orestrict32(
     const float* __restrict__ u, const float* __restrict__ f, const int* __restrict__ nbr,
-    const float* __restrict__ gh, const float* __restrict__ mask, float mthr, long long n,
+    const float* __restrict__ gh, const unsigned char* __restrict__ act, long long n,
     const int* __restrict__ olist, const int* __restrict__ pcell, MT<float> m, float ih2,
     float* __restrict__ uc, float* __restrict__ Ec, float* __restrict__ ucold,
     float* __restrict__ fc) {
@@ -873,7 +869,7 @@ __global__ void __launch_bounds__(BS) k_orestrict32(
 #pragma unroll
   for (int ch = 0; ch < 8; ++ch) {
     su += U.v[ch];
-    if (!mask || mask[8 * o + ch] > mthr)
+    if (!act || act[8 * o + ch])
       sr += Fv.v[ch] - (s1[ch] * ih2 + m.aRt * (1.f - nls(U.v[ch], EE.v[ch], m)));
   }
   const int p = pcell[o];
@@ -887,8 +883,7 @@ __global__ void __launch_bounds__(BS) k_orestrict32(
 // u_c = R(u), E_c = e^{u_c}, e_c = 0.
 __global__ void __launch_bounds__(BS) k_olin_restrict32(
     const float* __restrict__ e, const float* __restrict__ r, const float* __restrict__ u,
-    const int* __restrict__ nbr, const float* __restrict__ gh, const float* __restrict__ mask,
-    float mthr, long long n, const int* __restrict__ olist, const int* __restrict__ pcell,
+    const int* __restrict__ nbr, const float* __restrict__ gh, const unsigned char* __restrict__ act, long long n, const int* __restrict__ olist, const int* __restrict__ pcell,
     MT<float> m, float ih2, float* __restrict__ rc, float* __restrict__ uc,
     float* __restrict__ Ec, float* __restrict__ ec) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -905,7 +900,7 @@ __global__ void __launch_bounds__(BS) k_olin_restrict32(
 #pragma unroll
   for (int ch = 0; ch < 8; ++ch) {
     su += U.v[ch];
-    if (!mask || mask[8 * o + ch] > mthr) {
+    if (!act || act[8 * o + ch]) {
       const float diag = s2[ch] * h2 + m.aRt_np1 * nls(U.v[ch], EE.v[ch], m);
       sr += R.v[ch] - fmaf(diag, X.v[ch], s1[ch] * h2);
     }
@@ -928,7 +923,7 @@ __global__ void __launch_bounds__(BS) k_oprolong32(long long n, const int* __res
                                                    const int* __restrict__ pnbr,
                                                    const float* __restrict__ uc,
                                                    const float* __restrict__ ucold,
-                                                   const float* __restrict__ mask, float mthr,
+                                                   const unsigned char* __restrict__ act,
                                                    int linear, float* __restrict__ u) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n) return;
@@ -954,7 +949,7 @@ __global__ void __launch_bounds__(BS) k_oprolong32(long long n, const int* __res
   Oct8 U = ld8(u, o);
 #pragma unroll
   for (int ch = 0; ch < 8; ++ch) {
-    if (mask && !(mask[8 * o + ch] > mthr)) continue;
+    if (act && !(act[8 * o + ch])) continue;
     float v = v0;
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax)
@@ -1212,6 +1207,14 @@ __global__ void k_fill_f(float* __restrict__ x, long long n, float v) {
   if (i < n) x[i] = v;
 }
 
+// act[c] = 1 where the multigrid mask relaxes cell c (mask > threshold): one
+// byte per cell for the sweeps instead of the float mask
+__global__ void k_act(const float* __restrict__ mask, long long n, float mthr,
+                      unsigned char* __restrict__ act) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) act[i] = mask[i] > mthr ? 1 : 0;
+}
+
 __global__ void k_count_relaxed(const float* __restrict__ mask, long long n, float mthr,
                                 long long* __restrict__ out) {
   long long cnt = 0;
@@ -1321,26 +1324,25 @@ void relax(SolveCtx& S, int l, int sweeps) {
         if (R.n == 0) continue;
         if (l == S.L) prof_begin(c, 3, L.ncell);
         if constexpr (std::is_same<T, float>::value) {
-          const float* mk = l == S.L ? nullptr : L.mask;
+          const unsigned char* mk = l == S.L ? nullptr : L.act;
           if (col == 0)
             k_oct_sweep32<false, 0><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-                L.w32, nullptr, L.wf32, L.nbr, L.ghost32, mk, S.mthr, R.n, R.list, m,
+                L.w32, nullptr, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, m,
                 (float)L.ih2, (float)g.step_cap);
           else
             k_oct_sweep32<false, 1><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-                L.w32, nullptr, L.wf32, L.nbr, L.ghost32, mk, S.mthr, R.n, R.list, m,
+                L.w32, nullptr, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, m,
                 (float)L.ih2, (float)g.step_cap);
         } else {
           k_osweep<T><<<nblocks(4 * R.n, BS), BS, 0, c->s>>>(
-              a.w, a.wE, a.wf, L.nbr, a.gh, a.ghE, l == S.L ? nullptr : L.mask, S.mthr, R.n,
+              a.w, a.wE, a.wf, L.nbr, a.gh, a.ghE, l == S.L ? nullptr : L.act, R.n,
               R.list, col, m, (T)L.ih2, (T)g.step_cap);
         }
         if (l == S.L) prof_end(c);
       } else {
         const int lg = L.lgN;
         k_dsweep<T><<<nblocks(L.ncell / 2, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, lg, col, m,
-                                                              (T)L.ih2, (T)g.step_cap, L.mask,
-                                                              S.mthr);
+                                                              (T)L.ih2, (T)g.step_cap, L.act);
       }
       c->launches += 1;
     }
@@ -1354,37 +1356,37 @@ void vcycle_dense(SolveCtx& S, int k) {
   const mgfr_config& g = c->cfg;
   DenseHier& H = c->dh;
   DenseLevel& F = H.L[k];
-  const float* mk = S.A->dmask[k];
+  const unsigned char* mk = S.A->dact[k];
   const MT<T> m = mt<T>(S.m);
   TA<T> a = darr<T>(F);
   if (F.N <= 4) {
-    k_dcoarse<T><<<1, 64, 0, c->s>>>(a.w, a.wE, a.wf, m, (T)F.ih2, (T)g.step_cap, 20, mk, S.mthr);
+    k_dcoarse<T><<<1, 64, 0, c->s>>>(a.w, a.wE, a.wf, m, (T)F.ih2, (T)g.step_cap, 20, mk);
     c->launches += 1;
     return;
   }
   for (int s = 0; s < g.n_pre; ++s)
     for (int col = 0; col < 2; ++col) {
       k_dsweep<T><<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lg, col, m, (T)F.ih2,
-                                                         (T)g.step_cap, mk, S.mthr);
+                                                         (T)g.step_cap, mk);
       c->launches += 1;
     }
   if (k + 1 <= S.kmax) {
     DenseLevel& C = H.L[k + 1];
     TA<T> b = darr<T>(C);
     k_drestrict<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lg, b.w, b.wE, b.wold,
-                                                      b.wf, m, (T)F.ih2, mk, S.mthr);
+                                                      b.wf, m, (T)F.ih2, mk);
     k_dfas<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, C.lg, m, (T)C.ih2,
-                                                 S.A->dmask[k + 1], S.mthr);
+                                                 S.A->dact[k + 1]);
     c->launches += 2;
     vcycle_dense<T>(S, k + 1);
     k_dprolong<T><<<nblocks(F.n, BS), BS, 0, c->s>>>(a.w, a.wE, b.w, b.wold, F.lg,
-                                                     g.prolong_linear, mk, S.mthr);
+                                                     g.prolong_linear, mk);
     c->launches += 1;
   }
   for (int s = 0; s < g.n_post; ++s)
     for (int col = 0; col < 2; ++col) {
       k_dsweep<T><<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lg, col, m, (T)F.ih2,
-                                                         (T)g.step_cap, mk, S.mthr);
+                                                         (T)g.step_cap, mk);
       c->launches += 1;
     }
 }
@@ -1399,41 +1401,41 @@ void vcycle_tree(SolveCtx& S, int l) {
   AmrLevel& F = A->L[l];
   TA<T> a = tarr<T>(F);
   relax<T>(S, l, g.n_pre);
-  const float* fmask = l == S.L ? nullptr : F.mask;
+  const unsigned char* fmask = l == S.L ? nullptr : F.act;
   if (l >= 1 && has_coarse(S, l)) {
     AmrLevel& P = A->L[l - 1];
     TA<T> b = tarr<T>(P);
     const ORange R = orange(S, F, l);
     if (R.n > 0) {
       if constexpr (std::is_same<T, float>::value)
-        k_orestrict32<<<nblocks(R.n, BS), BS, 0, c->s>>>(a.w, a.wf, F.nbr, a.gh, fmask, S.mthr,
+        k_orestrict32<<<nblocks(R.n, BS), BS, 0, c->s>>>(a.w, a.wf, F.nbr, a.gh, fmask,
                                                          R.n, R.list, F.pcell, m, (T)F.ih2, b.w,
                                                          b.wE, b.wold, b.wf);
       else
         k_orestrict<T><<<nblocks(R.n, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.nbr, a.gh, a.ghE,
-                                                          fmask, S.mthr, R.n, R.list, F.pcell, m,
+                                                          fmask, R.n, R.list, F.pcell, m,
                                                           (T)F.ih2, b.w, b.wE, b.wold, b.wf);
     }
     if (l - 1 >= 1) {
       if (P.n_list > 0)
         k_ofas<T><<<nblocks(8 * P.n_list, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, P.nbr, b.gh,
-                                                              b.ghE, P.mask, S.mthr,
+                                                              b.ghE, P.act,
                                                               8 * P.n_list, P.olist, m,
                                                               (T)P.ih2);
     } else {
       k_dfas<T><<<nblocks(P.ncell, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, P.lgN, m, (T)P.ih2,
-                                                       P.mask, S.mthr);
+                                                       P.act);
     }
     c->launches += 2;
     vcycle_tree<T>(S, l - 1);
     if (R.n > 0) {
       if constexpr (std::is_same<T, float>::value)
         k_oprolong32<false><<<nblocks(R.n, BS), BS, 0, c->s>>>(R.n, R.list, F.pcell, F.pnbr, b.w,
-                                                              b.wold, fmask, S.mthr,
+                                                              b.wold, fmask,
                                                               g.prolong_linear, a.w);
       else
         k_oprolong<T><<<nblocks(8 * R.n, BS), BS, 0, c->s>>>(8 * R.n, R.list, F.pcell, F.pnbr,
-                                                             b.w, b.wold, fmask, S.mthr,
+                                                             b.w, b.wold, fmask,
                                                              g.prolong_linear, a.w, a.wE);
     }
     c->launches += 1;
@@ -1442,13 +1444,12 @@ void vcycle_tree(SolveCtx& S, int l) {
     DenseLevel& C = H.L[1];
     TA<T> b = darr<T>(C);
     k_drestrict<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lgN, b.w, b.wE, b.wold,
-                                                      b.wf, m, (T)F.ih2, F.mask, S.mthr);
-    k_dfas<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, C.lg, m, (T)C.ih2, A->dmask[1],
-                                                 S.mthr);
+                                                      b.wf, m, (T)F.ih2, F.act);
+    k_dfas<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, C.lg, m, (T)C.ih2, A->dact[1]);
     c->launches += 2;
     vcycle_dense<T>(S, 1);
     k_dprolong<T><<<nblocks(F.ncell, BS), BS, 0, c->s>>>(a.w, a.wE, b.w, b.wold, F.lgN,
-                                                         g.prolong_linear, F.mask, S.mthr);
+                                                         g.prolong_linear, F.act);
     c->launches += 1;
   }
   relax<T>(S, l, g.n_post);
@@ -1513,23 +1514,23 @@ void lin_relax(SolveCtx& S, int l, int sweeps) {
   for (int s = 0; s < sweeps; ++s) {
     for (int col = 0; col < 2; ++col) {
       if (l >= 1) {
-        const float* mk = l == S.L ? nullptr : L.mask;
+        const unsigned char* mk = l == S.L ? nullptr : L.act;
         const ORange R = orange(S, L, l);
         if (R.n == 0) continue;
         if (l == S.L) prof_begin(c, 4, L.ncell);
         if (col == 0)
           k_oct_sweep32<true, 0><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-              L.w32, L.wold32, L.wf32, L.nbr, L.ghost32, mk, S.mthr, R.n, R.list, m,
+              L.w32, L.wold32, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, m,
               (float)L.ih2, 0.f);
         else
           k_oct_sweep32<true, 1><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-              L.w32, L.wold32, L.wf32, L.nbr, L.ghost32, mk, S.mthr, R.n, R.list, m,
+              L.w32, L.wold32, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, m,
               (float)L.ih2, 0.f);
         if (l == S.L) prof_end(c);
       } else
         k_dlin_sweep<<<nblocks(L.ncell / 2, BS), BS, 0, c->s>>>(L.wold32, L.wf32, L.w32, L.wE32,
                                                                L.lgN, col, m, (float)L.ih2,
-                                                               L.mask, S.mthr);
+                                                               L.act);
       c->launches += 1;
     }
   }
@@ -1540,34 +1541,34 @@ void lin_vcycle_dense(SolveCtx& S, int k) {
   const mgfr_config& g = c->cfg;
   DenseHier& H = c->dh;
   DenseLevel& F = H.L[k];
-  const float* mk = S.A->dmask[k];
+  const unsigned char* mk = S.A->dact[k];
   const MT<float> m = mt<float>(S.m);
   if (F.N <= 4) {
-    k_dlin_coarse<<<1, 64, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, m, (float)F.ih2, 20, mk, S.mthr);
+    k_dlin_coarse<<<1, 64, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, m, (float)F.ih2, 20, mk);
     c->launches += 1;
     return;
   }
   for (int s = 0; s < g.n_pre; ++s)
     for (int col = 0; col < 2; ++col) {
       k_dlin_sweep<<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, F.lg, col,
-                                                         m, (float)F.ih2, mk, S.mthr);
+                                                         m, (float)F.ih2, mk);
       c->launches += 1;
     }
   if (k + 1 <= S.kmax) {
     DenseLevel& C = H.L[k + 1];
     k_dlin_restrict<<<nblocks(C.n, BS), BS, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, F.lg,
                                                        C.r32, C.u32, C.e32, C.uold32, m,
-                                                       (float)F.ih2, mk, S.mthr);
+                                                       (float)F.ih2, mk);
     c->launches += 1;
     lin_vcycle_dense(S, k + 1);
     k_dlin_prolong<<<nblocks(F.n, BS), BS, 0, c->s>>>(F.uold32, C.uold32, F.lg, g.prolong_linear,
-                                                      mk, S.mthr);
+                                                      mk);
     c->launches += 1;
   }
   for (int s = 0; s < g.n_post; ++s)
     for (int col = 0; col < 2; ++col) {
       k_dlin_sweep<<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, F.lg, col,
-                                                         m, (float)F.ih2, mk, S.mthr);
+                                                         m, (float)F.ih2, mk);
       c->launches += 1;
     }
 }
@@ -1580,19 +1581,19 @@ void lin_vcycle_tree(SolveCtx& S, int l) {
   AmrLevel& F = A->L[l];
   lin_relax(S, l, g.n_pre);
   S.updates += (long long)g.n_pre * F.relaxed;
-  const float* fmask = l == S.L ? nullptr : F.mask;
+  const unsigned char* fmask = l == S.L ? nullptr : F.act;
   if (l >= 1 && has_coarse(S, l)) {
     AmrLevel& P = A->L[l - 1];
     const ORange R = orange(S, F, l);
     if (R.n > 0)
       k_olin_restrict32<<<nblocks(R.n, BS), BS, 0, c->s>>>(
-          F.wold32, F.wf32, F.w32, F.nbr, F.ghost32, fmask, S.mthr, R.n, R.list, F.pcell, m,
+          F.wold32, F.wf32, F.w32, F.nbr, F.ghost32, fmask, R.n, R.list, F.pcell, m,
           (float)F.ih2, P.wf32, P.w32, P.wE32, P.wold32);
     c->launches += 1;
     lin_vcycle_tree(S, l - 1);
     if (R.n > 0)
       k_oprolong32<true><<<nblocks(R.n, BS), BS, 0, c->s>>>(R.n, R.list, F.pcell, F.pnbr,
-                                                           P.wold32, nullptr, fmask, S.mthr,
+                                                           P.wold32, nullptr, fmask,
                                                            g.prolong_linear, F.wold32);
     c->launches += 1;
   } else if (l == 0 && S.kmax >= 1) {
@@ -1600,11 +1601,11 @@ void lin_vcycle_tree(SolveCtx& S, int l) {
     DenseLevel& C = H.L[1];
     k_dlin_restrict<<<nblocks(C.n, BS), BS, 0, c->s>>>(F.wold32, F.wf32, F.w32, F.wE32, F.lgN,
                                                        C.r32, C.u32, C.e32, C.uold32, m,
-                                                       (float)F.ih2, F.mask, S.mthr);
+                                                       (float)F.ih2, F.act);
     c->launches += 1;
     lin_vcycle_dense(S, 1);
     k_dlin_prolong<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.wold32, C.uold32, F.lgN,
-                                                          g.prolong_linear, F.mask, S.mthr);
+                                                          g.prolong_linear, F.act);
     c->launches += 1;
   }
   lin_relax(S, l, g.n_post);
@@ -1708,6 +1709,8 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
     k_mask_up<<<nblocks(Ch.n_oct, BS), BS, 0, c->s>>>(Ch.mask, Ch.n_oct, Ch.pcell, P.mask);
     c->launches += 1;
     TRY(count_relaxed(c, A, P.mask, P.ncell, mthr, &P.relaxed));
+    k_act<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(P.mask, P.ncell, mthr, P.act);
+    c->launches += 1;
     if (l >= 1) TRY(build_oct_list(c, A, P, mthr));
   }
   for (int k = 1; k < H.nlev; ++k) {
@@ -1724,6 +1727,8 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
       TRY(count_relaxed(c, A, A->dmask[k], H.L[k].n, mthr, &nk));
       if (nk == 0) break;
       kmax = k;
+      k_act<<<nblocks(H.L[k].n, BS), BS, 0, c->s>>>(A->dmask[k], H.L[k].n, mthr, A->dact[k]);
+      c->launches += 1;
     }
   }
   SolveCtx S{c, A, m, Lv, mthr, 0, kmax};
