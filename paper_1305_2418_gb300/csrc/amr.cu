@@ -34,7 +34,10 @@ constexpr int BS = 256;
 // ---- particle coordinates ------------------------------------------------
 __device__ __forceinline__ double wrap_coord(double x, double inv, double N0) {
   double t = __dmul_rn(x, inv);
-  if (t < 0.0 || t >= N0) {
+  // 0 <= t < N0 tested on the bit patterns (ordered like the values for
+  // non-negative doubles; -0.0 and negatives have the sign bit set)
+  const long long tb = __double_as_longlong(t);
+  if (tb < 0 || tb >= __double_as_longlong(N0)) {
     const double q = floor(__ddiv_rn(t, N0));
     t = __dsub_rn(t, __dmul_rn(N0, q));
     if (t >= N0 || t < 0.0) t = 0.0;
@@ -60,8 +63,23 @@ __device__ __forceinline__ P3 particle_t(const double* __restrict__ pos, long lo
 // the traversal but those products runs on the integer pipes.
 constexpr int QB = 52;
 
+// floor(t 2^52) for 0 <= t < 2^10, read off t's bits: with t = 1.f 2^e and
+// s = 2^52 + f the 53-bit significand, t 2^52 = s 2^e, so X = s << e for
+// e >= 0 and s >> -e (the floor) for e < 0.  Equal to the truncating FP64
+// conversion of t 2^52, without FP64 instructions.
 __device__ __forceinline__ long long qfix(double t) {
-  return (long long)__dmul_rn(t, 4503599627370496.0);  // exact scaling by 2^52, then floor
+  const long long b = __double_as_longlong(t);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  const long long sig = (b & ((1LL << 52) - 1)) | (1LL << 52);
+  if (e >= 0) return sig << e;
+  return e > -53 ? sig >> -e : 0;  // also t = +-0 and subnormals: 0
+}
+
+// v as a double for 0 <= v <= 2^52 (exact): 2^52 + v has v as its significand
+// bits, one FP64 subtraction removes the 2^52
+__device__ __forceinline__ double exact_i2d(long long v) {
+  return v == (1LL << 52) ? 4503599627370496.0
+                          : __longlong_as_double(v | 0x4330000000000000LL) - 4503599627370496.0;
 }
 
 // ---- structure kernels -----------------------------------------------------
@@ -238,7 +256,7 @@ template <class W>
 struct Wt;
 template <>
 struct Wt<double> {
-  static __device__ __forceinline__ double len(long long v, int) { return (double)v; }
+  static __device__ __forceinline__ double len(long long v, int) { return exact_i2d(v); }
   static __device__ __forceinline__ double scale(int F) {
     return __longlong_as_double((long long)(1023 - 3 * F) << 52);
   }
