@@ -581,26 +581,52 @@ __global__ void k_zero32(float* __restrict__ x, long long n) {
 }
 
 
-// ---- thread-per-oct FP32 sweeps ------------------------------------------------
-// One thread updates the 4 cells of one colour in its oct: the oct's 8 values
-// are two float4 loads, each face is visited once (a neighbouring oct's cells
-// or the ghost face, stored as interleaved (u, E) pairs = one 32-byte sector),
-// and the oct is written back whole.  Consecutive threads own consecutive
-// octs, so the oct loads and stores are fully coalesced.
+// ---- FP32 storage of oct levels -------------------------------------------
+// The FP32 arrays of an oct level (u, f or r, e) are stored by colour: plane k
+// (k = 0, 1) holds, for every oct o, the four cells of colour k as one float4
+// at floats (k n_oct + o) 4.  The colour is the parity of the child-index bits
+// (the red-black colour of the sweeps; parent coordinates contribute an even
+// amount), and a cell's place in its float4 is ch >> 1 (colour 0: children
+// 0, 3, 5, 6; colour 1: 1, 2, 4, 7).  A half-sweep then moves whole 16-byte
+// vectors of the colour it reads or writes.  n_oct = 0 marks a dense level
+// (C order).
+__device__ __forceinline__ long long pidx(long long c, long long n_oct) {
+  if (n_oct == 0) return c;
+  const int ch = (int)(c & 7);
+  return (((long long)(__popc(ch) & 1) * n_oct + (c >> 3)) << 2) + (ch >> 1);
+}
+
 struct Oct8 {
   float v[8];
 };
 
-__device__ __forceinline__ Oct8 ld8(const float* __restrict__ p, long long o) {
-  const float4* q = reinterpret_cast<const float4*>(p + 8 * o);
-  const float4 a = q[0], b = q[1];
-  return Oct8{{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w}};
+__device__ __forceinline__ float4 ldc(const float* __restrict__ p, long long o, long long no,
+                                      int col) {
+  return *reinterpret_cast<const float4*>(p + 4 * (col * no + o));
 }
 
-__device__ __forceinline__ void st8(float* __restrict__ p, long long o, const Oct8& x) {
-  float4* q = reinterpret_cast<float4*>(p + 8 * o);
-  q[0] = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
-  q[1] = make_float4(x.v[4], x.v[5], x.v[6], x.v[7]);
+__device__ __forceinline__ void stc(float* __restrict__ p, long long o, long long no, int col,
+                                    float4 v) {
+  *reinterpret_cast<float4*>(p + 4 * (col * no + o)) = v;
+}
+
+// the float4 of one colour <-> the oct's cells of that colour
+__device__ __forceinline__ float f4(const float4& v, int r) {
+  return r == 0 ? v.x : r == 1 ? v.y : r == 2 ? v.z : v.w;
+}
+
+__device__ __forceinline__ Oct8 ld8(const float* __restrict__ p, long long o, long long no) {
+  const float4 a = ldc(p, o, no, 0), b = ldc(p, o, no, 1);
+  Oct8 r;
+  r.v[0] = a.x; r.v[3] = a.y; r.v[5] = a.z; r.v[6] = a.w;
+  r.v[1] = b.x; r.v[2] = b.y; r.v[4] = b.z; r.v[7] = b.w;
+  return r;
+}
+
+__device__ __forceinline__ void st8(float* __restrict__ p, long long o, long long no,
+                                    const Oct8& x) {
+  stc(p, o, no, 0, make_float4(x.v[0], x.v[3], x.v[5], x.v[6]));
+  stc(p, o, no, 1, make_float4(x.v[1], x.v[2], x.v[4], x.v[7]));
 }
 
 // tangential face index of cell ch on a face normal to axis ax
@@ -609,25 +635,33 @@ __device__ __forceinline__ int face_q(int ch, int ax) {
   return (((ch >> (2 - t1)) & 1) << 1) | ((ch >> (2 - t2)) & 1);
 }
 
-// LIN = true : Gauss-Seidel on J(u) e = r  (u fixed; e updated)
-// LIN = false: Newton-Gauss-Seidel on L(u) = f (u updated)
-// e^u of the oct and of the face neighbours is recomputed by the SFU from u,
-// so a half-sweep streams u (and e), f or r, the neighbour table and the FP32
-// ghost u of faces without a neighbouring oct, and writes one array.
+// ---- thread-per-oct FP32 sweeps ------------------------------------------------
+// One thread updates the 4 cells of colour COL in its oct.  It reads both
+// colours of its own u, the colour-COL vector of f (or r), and from each face
+// the other colour of the neighbouring oct (the cells across the face from
+// colour-COL cells have the other colour) or the ghost face; it writes the
+// colour-COL vector of u (or e).  e^u is recomputed by the SFU from u.
+//   LIN = true : Gauss-Seidel on J(u) e = r  (u fixed; e updated)
+//   LIN = false: Newton-Gauss-Seidel on L(u) = f (u updated)
+// no: octs of the level (plane stride); n, olist: the octs visited.
 template <bool LIN, int COL>
 __global__ void __launch_bounds__(BS) k_oct_sweep32(
     float* __restrict__ u, float* __restrict__ e, const float* __restrict__ rf,
-    const int* __restrict__ nbr, const float* __restrict__ gh, const unsigned char* __restrict__ act, long long n_oct, const int* __restrict__ olist, MT<float> m, float ih2,
-    float cap) {
+    const int* __restrict__ nbr, const float* __restrict__ gh,
+    const unsigned char* __restrict__ act, long long n, const int* __restrict__ olist,
+    long long no, MT<float> m, float ih2, float cap) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= n_oct) return;
+  if (t >= n) return;
   const long long o = olist ? olist[t] : t;
   constexpr int CC[2][4] = {{0, 3, 5, 6}, {1, 2, 4, 7}};
-  const Oct8 U = ld8(u, o), R = ld8(rf, o);
+  constexpr int OC = 1 - COL;
+  const Oct8 U = ld8(u, o, no);
+  const float4 R4 = ldc(rf, o, no, COL);
   Oct8 EE;
 #pragma unroll
   for (int i = 0; i < 8; ++i) EE.v[i] = __expf(U.v[i]);
-  Oct8 X = LIN ? ld8(e, o) : U;  // LIN: correction; else unused copy
+  // LIN: corrections of the other colour (the in-oct neighbours)
+  const float4 XO = LIN ? ldc(e, o, no, OC) : make_float4(0.f, 0.f, 0.f, 0.f);
   bool on[4];
   float s1[4], s2[4], s3[4];  // LIN: (sum off*e, diag sum, -); NL: (sum b du, sum du, sum b)
 #pragma unroll
@@ -641,7 +675,8 @@ __global__ void __launch_bounds__(BS) k_oct_sweep32(
       const int cn = ch ^ (1 << (2 - a));
       const float du = U.v[cn] - U.v[ch];
       if (LIN) {
-        s1[q] = fmaf(0.5f * ih2 * fmaf(EE.v[cn], du, EE.v[ch] + EE.v[cn]), X.v[cn], s1[q]);
+        s1[q] = fmaf(0.5f * ih2 * fmaf(EE.v[cn], du, EE.v[ch] + EE.v[cn]), f4(XO, cn >> 1),
+                     s1[q]);
         s2[q] += fmaf(EE.v[ch], du, -EE.v[ch] - EE.v[cn]);
       } else {
         const float b = 0.5f * (EE.v[cn] + EE.v[ch]);
@@ -655,30 +690,25 @@ __global__ void __launch_bounds__(BS) k_oct_sweep32(
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     const int a = d >> 1, plus = d & 1;
-    const int no = nbr[6 * o + d];
-    Oct8 NU, NX;
-    float G[4];
-    if (no >= 0) {
-      NU = ld8(u, no);
-      if (LIN) NX = ld8(e, no);
+    const int nb = nbr[6 * o + d];
+    float4 NU, NX;
+    if (nb >= 0) {
+      NU = ldc(u, nb, no, OC);
+      if (LIN) NX = ldc(e, nb, no, OC);
     } else {
-      const float4 g = *reinterpret_cast<const float4*>(gh + 24 * o + 4 * d);
-      G[0] = g.x;
-      G[1] = g.y;
-      G[2] = g.z;
-      G[3] = g.w;
+      NU = *reinterpret_cast<const float4*>(gh + 24 * o + 4 * d);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int ch = CC[COL][q];
       if (((ch >> (2 - a)) & 1) != plus) continue;  // not on this face
       float un, xn;
-      if (no >= 0) {
+      if (nb >= 0) {
         const int cn = ch ^ (1 << (2 - a));
-        un = NU.v[cn];
-        xn = LIN ? NX.v[cn] : 0.f;
+        un = f4(NU, cn >> 1);
+        xn = LIN ? f4(NX, cn >> 1) : 0.f;
       } else {
-        un = G[face_q(ch, a)];
+        un = f4(NU, face_q(ch, a));
         xn = 0.f;
       }
       const float En = __expf(un);
@@ -694,7 +724,11 @@ __global__ void __launch_bounds__(BS) k_oct_sweep32(
       }
     }
   }
-  Oct8 UO = U;
+  // the colour-COL vector: new values on relaxed cells, the old ones elsewhere
+  float4 out = LIN ? (act ? ldc(e, o, no, COL) : make_float4(0.f, 0.f, 0.f, 0.f))
+                   : make_float4(U.v[CC[COL][0]], U.v[CC[COL][1]], U.v[CC[COL][2]],
+                                 U.v[CC[COL][3]]);
+  float res[4] = {out.x, out.y, out.z, out.w};
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     if (!on[q]) continue;
@@ -702,19 +736,16 @@ __global__ void __launch_bounds__(BS) k_oct_sweep32(
     const float sN = nls(U.v[ch], EE.v[ch], m);
     if (LIN) {
       const float diag = s2[q] * 0.5f * ih2 + m.aRt_np1 * sN;
-      X.v[ch] = __fdividef(R.v[ch] - s1[q], diag);
+      res[q] = __fdividef(f4(R4, q) - s1[q], diag);
     } else {
       const float L = s1[q] * ih2 + m.aRt * (1.f - sN);
       const float dL = (0.5f * EE.v[ch] * s2[q] - s3[q]) * ih2 + m.aRt_np1 * sN;
-      float step = __fdividef(L - R.v[ch], dL);
+      float step = __fdividef(L - f4(R4, q), dL);
       step = fminf(fmaxf(step, -cap), cap);
-      UO.v[ch] = U.v[ch] - step;
+      res[q] = U.v[ch] - step;
     }
   }
-  if (LIN)
-    st8(e, o, X);
-  else
-    st8(u, o, UO);
+  stc(LIN ? e : u, o, no, COL, make_float4(res[0], res[1], res[2], res[3]));
 }
 
 // ---- thread-per-oct FP32 operator sums ------------------------------------
@@ -731,8 +762,9 @@ __global__ void __launch_bounds__(BS) k_oct_sweep32(
 template <bool LIN>
 __device__ __forceinline__ void oct_sums(const float* __restrict__ u, const float* __restrict__ x,
                                          const int* __restrict__ nbr,
-                                         const float* __restrict__ gh, long long o, const Oct8& U,
-                                         const Oct8& EE, const Oct8& X, float* s1, float* s2) {
+                                         const float* __restrict__ gh, long long o, long long no,
+                                         const Oct8& U, const Oct8& EE, const Oct8& X, float* s1,
+                                         float* s2) {
 #pragma unroll
   for (int ch = 0; ch < 8; ++ch) {
     s1[ch] = 0.f;
@@ -752,12 +784,12 @@ __device__ __forceinline__ void oct_sums(const float* __restrict__ u, const floa
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     const int a = d >> 1, plus = d & 1;
-    const int no = nbr[6 * o + d];
+    const int nb = nbr[6 * o + d];
     Oct8 NU, NX;
     float G[4];
-    if (no >= 0) {
-      NU = ld8(u, no);
-      if (LIN) NX = ld8(x, no);
+    if (nb >= 0) {
+      NU = ld8(u, nb, no);
+      if (LIN) NX = ld8(x, nb, no);
     } else {
       const float4 g = *reinterpret_cast<const float4*>(gh + 24 * o + 4 * d);
       G[0] = g.x;
@@ -769,7 +801,7 @@ __device__ __forceinline__ void oct_sums(const float* __restrict__ u, const floa
     for (int ch = 0; ch < 8; ++ch) {
       if (((ch >> (2 - a)) & 1) != plus) continue;  // not on this face
       float un, xn;
-      if (no >= 0) {
+      if (nb >= 0) {
         const int cn = ch ^ (1 << (2 - a));
         un = NU.v[cn];
         xn = LIN ? NX.v[cn] : 0.f;
@@ -826,12 +858,12 @@ __global__ void __launch_bounds__(BS) k_onorm32(const float* __restrict__ u,
   double ss = 0.0, mx = 0.0, fs = 0.0;
   for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n_oct;
        o += (long long)gridDim.x * blockDim.x) {
-    const Oct8 U = ld8(u, o), Fv = ld8(f, o);
+    const Oct8 U = ld8(u, o, n_oct), Fv = ld8(f, o, n_oct);
     Oct8 EE;
 #pragma unroll
     for (int i = 0; i < 8; ++i) EE.v[i] = __expf(U.v[i]);
     float s1[8], s2[8];
-    oct_sums<false>(u, nullptr, nbr, gh, o, U, EE, U, s1, s2);
+    oct_sums<false>(u, nullptr, nbr, gh, o, n_oct, U, EE, U, s1, s2);
     float ss8 = 0.f, mx8 = 0.f, fs8 = 0.f;
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
@@ -848,23 +880,47 @@ __global__ void __launch_bounds__(BS) k_onorm32(const float* __restrict__ u,
   block_partials3(ss, mx, fs, partials);
 }
 
-// FAS restriction of one oct to its parent (FP32): u average, average of the
-// residual f - L(u) over the oct's relaxed cells.
-__global__ void __launch_bounds__(BS) k_orestrict32(
-    const float* __restrict__ u, const float* __restrict__ f, const int* __restrict__ nbr,
-    const float* __restrict__ gh, const unsigned char* __restrict__ act, long long n,
-    const int* __restrict__ olist, const int* __restrict__ pcell, MT<float> m, float ih2,
-    float* __restrict__ uc, float* __restrict__ Ec, float* __restrict__ ucold,
-    float* __restrict__ fc) {
+// FAS right-hand side on a coarse oct level (FP32): f += L(u) at relaxed cells
+__global__ void __launch_bounds__(BS) k_ofas32(const float* __restrict__ u, float* __restrict__ f,
+                                               const int* __restrict__ nbr,
+                                               const float* __restrict__ gh,
+                                               const unsigned char* __restrict__ act, long long n,
+                                               const int* __restrict__ olist, long long no,
+                                               MT<float> m, float ih2) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n) return;
   const long long o = olist ? olist[t] : t;
-  const Oct8 U = ld8(u, o), Fv = ld8(f, o);
+  const Oct8 U = ld8(u, o, no);
   Oct8 EE;
 #pragma unroll
   for (int i = 0; i < 8; ++i) EE.v[i] = __expf(U.v[i]);
   float s1[8], s2[8];
-  oct_sums<false>(u, nullptr, nbr, gh, o, U, EE, U, s1, s2);
+  oct_sums<false>(u, nullptr, nbr, gh, o, no, U, EE, U, s1, s2);
+  Oct8 Fv = ld8(f, o, no);
+#pragma unroll
+  for (int ch = 0; ch < 8; ++ch)
+    if (act[8 * o + ch]) Fv.v[ch] += s1[ch] * ih2 + m.aRt * (1.f - nls(U.v[ch], EE.v[ch], m));
+  st8(f, o, no, Fv);
+}
+
+// FAS restriction of one oct to its parent (FP32): u average, average of the
+// residual f - L(u) over the oct's relaxed cells.  pno: octs of the parent
+// level (0: dense).
+__global__ void __launch_bounds__(BS) k_orestrict32(
+    const float* __restrict__ u, const float* __restrict__ f, const int* __restrict__ nbr,
+    const float* __restrict__ gh, const unsigned char* __restrict__ act, long long n,
+    const int* __restrict__ olist, long long no, const int* __restrict__ pcell, long long pno,
+    MT<float> m, float ih2, float* __restrict__ uc, float* __restrict__ ucold,
+    float* __restrict__ fc) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const long long o = olist ? olist[t] : t;
+  const Oct8 U = ld8(u, o, no), Fv = ld8(f, o, no);
+  Oct8 EE;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) EE.v[i] = __expf(U.v[i]);
+  float s1[8], s2[8];
+  oct_sums<false>(u, nullptr, nbr, gh, o, no, U, EE, U, s1, s2);
   float su = 0.f, sr = 0.f;
 #pragma unroll
   for (int ch = 0; ch < 8; ++ch) {
@@ -872,7 +928,7 @@ __global__ void __launch_bounds__(BS) k_orestrict32(
     if (!act || act[8 * o + ch])
       sr += Fv.v[ch] - (s1[ch] * ih2 + m.aRt * (1.f - nls(U.v[ch], EE.v[ch], m)));
   }
-  const int p = pcell[o];
+  const long long p = pidx(pcell[o], pno);
   const float um = 0.125f * su;
   uc[p] = um;
   ucold[p] = um;
@@ -880,21 +936,22 @@ __global__ void __launch_bounds__(BS) k_orestrict32(
 }
 
 // Linear-phase restriction of one oct: r_c = R(r - J e) over relaxed cells,
-// u_c = R(u), E_c = e^{u_c}, e_c = 0.
+// u_c = R(u), e_c = 0.
 __global__ void __launch_bounds__(BS) k_olin_restrict32(
     const float* __restrict__ e, const float* __restrict__ r, const float* __restrict__ u,
-    const int* __restrict__ nbr, const float* __restrict__ gh, const unsigned char* __restrict__ act, long long n, const int* __restrict__ olist, const int* __restrict__ pcell,
-    MT<float> m, float ih2, float* __restrict__ rc, float* __restrict__ uc,
-    float* __restrict__ Ec, float* __restrict__ ec) {
+    const int* __restrict__ nbr, const float* __restrict__ gh,
+    const unsigned char* __restrict__ act, long long n, const int* __restrict__ olist,
+    long long no, const int* __restrict__ pcell, long long pno, MT<float> m, float ih2,
+    float* __restrict__ rc, float* __restrict__ uc, float* __restrict__ ec) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n) return;
   const long long o = olist ? olist[t] : t;
-  const Oct8 U = ld8(u, o), X = ld8(e, o), R = ld8(r, o);
+  const Oct8 U = ld8(u, o, no), X = ld8(e, o, no), R = ld8(r, o, no);
   Oct8 EE;
 #pragma unroll
   for (int i = 0; i < 8; ++i) EE.v[i] = __expf(U.v[i]);
   float s1[8], s2[8];
-  oct_sums<true>(u, e, nbr, gh, o, U, EE, X, s1, s2);
+  oct_sums<true>(u, e, nbr, gh, o, no, U, EE, X, s1, s2);
   const float h2 = 0.5f * ih2;
   float su = 0.f, sr = 0.f;
 #pragma unroll
@@ -905,9 +962,8 @@ __global__ void __launch_bounds__(BS) k_olin_restrict32(
       sr += R.v[ch] - fmaf(diag, X.v[ch], s1[ch] * h2);
     }
   }
-  const int p = pcell[o];
-  const float um = 0.125f * su;
-  uc[p] = um;
+  const long long p = pidx(pcell[o], pno);
+  uc[p] = 0.125f * su;
   rc[p] = 0.125f * sr;
   ec[p] = 0.f;
 }
@@ -919,8 +975,8 @@ __global__ void __launch_bounds__(BS) k_olin_restrict32(
 // LIN: c = e_c, added to e.  The oct is read and written whole.
 template <bool LIN>
 __global__ void __launch_bounds__(BS) k_oprolong32(long long n, const int* __restrict__ olist,
-                                                   const int* __restrict__ pcell,
-                                                   const int* __restrict__ pnbr,
+                                                   long long no, const int* __restrict__ pcell,
+                                                   const int* __restrict__ pnbr, long long pno,
                                                    const float* __restrict__ uc,
                                                    const float* __restrict__ ucold,
                                                    const unsigned char* __restrict__ act,
@@ -929,10 +985,11 @@ __global__ void __launch_bounds__(BS) k_oprolong32(long long n, const int* __res
   if (t >= n) return;
   const long long o = olist ? olist[t] : t;
   auto corr = [&](int q) -> float {
+    const long long k = pidx(q, pno);
     if constexpr (LIN)
-      return uc[q];
+      return uc[k];
     else
-      return uc[q] - ucold[q];
+      return uc[k] - ucold[k];
   };
   const float v0 = corr(pcell[o]);
   float g[3] = {0.f, 0.f, 0.f};
@@ -946,7 +1003,7 @@ __global__ void __launch_bounds__(BS) k_oprolong32(long long n, const int* __res
       have[ax] = true;
     }
   }
-  Oct8 U = ld8(u, o);
+  Oct8 U = ld8(u, o, no);
 #pragma unroll
   for (int ch = 0; ch < 8; ++ch) {
     if (act && !(act[8 * o + ch])) continue;
@@ -956,7 +1013,7 @@ __global__ void __launch_bounds__(BS) k_oprolong32(long long n, const int* __res
       if (have[ax]) v += (((ch >> (2 - ax)) & 1) ? 0.125f : -0.125f) * g[ax];
     U.v[ch] += v;
   }
-  st8(u, o, U);
+  st8(u, o, no, U);
 }
 
 // ---- phase B in double-float (mixed form) ---------------------------------
@@ -1010,7 +1067,7 @@ __device__ __forceinline__ void onb_df(const dfl* __restrict__ u, const dfl* __r
 __global__ void __launch_bounds__(BS) k_oresid_df(
     const dfl* __restrict__ u, const dfl* __restrict__ E, const dfl* __restrict__ f,
     const int* __restrict__ nbr, const dfl* __restrict__ gh, const dfl* __restrict__ ghE,
-    long long ncell, MDF m, float* __restrict__ r32, float* __restrict__ u32,
+    long long ncell, MDF m, long long no, float* __restrict__ r32, float* __restrict__ u32,
     float* __restrict__ e32, double* __restrict__ partials) {
   float ss = 0.f, mx = 0.f, fs = 0.f;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
@@ -1029,9 +1086,10 @@ __global__ void __launch_bounds__(BS) k_oresid_df(
     const dfl L = df_add(df_mul(acc, m.ih2h), df_mul(m.aRt, df_add_f(df_neg(sN), 1.f)));
     const dfl fc = f[c];
     const dfl r = df_sub(fc, L);
-    r32[c] = r.hi;
-    u32[c] = uc.hi;
-    e32[c] = 0.f;
+    const long long k = pidx(c, no);
+    r32[k] = r.hi;
+    u32[k] = uc.hi;
+    e32[k] = 0.f;
     ss = fmaf(r.hi, r.hi, ss);
     mx = fmaxf(mx, fabsf(r.hi));
     fs = fmaf(fc.hi, fc.hi, fs);
@@ -1040,21 +1098,21 @@ __global__ void __launch_bounds__(BS) k_oresid_df(
 }
 
 // FP32 iterate -> double-float iterate and its e^u
-__global__ void k_f2df_exp(const float* __restrict__ w32, dfl* __restrict__ w, dfl* __restrict__ wE,
-                           long long n) {
+__global__ void k_f2df_exp(const float* __restrict__ w32, long long no, dfl* __restrict__ w,
+                           dfl* __restrict__ wE, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const dfl v{w32[i], 0.f};
+  const dfl v{w32[pidx(i, no)], 0.f};
   w[i] = v;
   wE[i] = df_exp(v);
 }
 
 // w += clamp(e), wE = e^w (double-float)
 __global__ void k_apply_df(dfl* __restrict__ w, dfl* __restrict__ wE, const float* __restrict__ e,
-                           long long n, float cap) {
+                           long long no, long long n, float cap) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const dfl v = df_add_f(w[i], fminf(fmaxf(e[i], -cap), cap));
+  const dfl v = df_add_f(w[i], fminf(fmaxf(e[pidx(i, no)], -cap), cap));
   w[i] = v;
   wE[i] = df_exp(v);
 }
@@ -1081,7 +1139,7 @@ __global__ void k_d2df(const double* __restrict__ x, dfl* __restrict__ y, long l
 __global__ void k_init_level(long long ncell, const int* __restrict__ pcell,
                              const int* __restrict__ pnbr, const double* __restrict__ up,
                              int linear, double* __restrict__ w, double* __restrict__ wE,
-                             float* __restrict__ w32) {
+                             float* __restrict__ w32, long long no) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= ncell) return;
   const long long o = c >> 3;
@@ -1095,7 +1153,7 @@ __global__ void k_init_level(long long ncell, const int* __restrict__ pcell,
     }
   }
   if (w32) {
-    w32[c] = (float)v;  // mixed form: the FP64 iterate is taken from w32 later
+    w32[pidx(c, no)] = (float)v;  // mixed form: the FP64 iterate is taken from w32 later
   } else {
     w[c] = v;
     wE[c] = exp(v);
@@ -1167,17 +1225,19 @@ __global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restri
   }
 }
 
-__global__ void k_d2f(const double* __restrict__ x, float* __restrict__ y, long long n) {
+// FP64 cell array -> FP32 array of a level (no: its octs, 0 for dense)
+__global__ void k_d2f(const double* __restrict__ x, float* __restrict__ y, long long n,
+                      long long no) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n) y[i] = (float)x[i];
+  if (i < n) y[pidx(i, no)] = (float)x[i];
 }
 
 // FP64 iterate from the FP32 one: w = w32, wE = e^w
-__global__ void k_f2d_exp(const float* __restrict__ w32, double* __restrict__ w,
+__global__ void k_f2d_exp(const float* __restrict__ w32, long long no, double* __restrict__ w,
                           double* __restrict__ wE, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double v = (double)w32[i];
+  const double v = (double)w32[pidx(i, no)];
   w[i] = v;
   wE[i] = exp(v);
 }
@@ -1327,11 +1387,11 @@ void relax(SolveCtx& S, int l, int sweeps) {
           const unsigned char* mk = l == S.L ? nullptr : L.act;
           if (col == 0)
             k_oct_sweep32<false, 0><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-                L.w32, nullptr, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, m,
+                L.w32, nullptr, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, L.n_oct, m,
                 (float)L.ih2, (float)g.step_cap);
           else
             k_oct_sweep32<false, 1><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-                L.w32, nullptr, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, m,
+                L.w32, nullptr, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, L.n_oct, m,
                 (float)L.ih2, (float)g.step_cap);
         } else {
           k_osweep<T><<<nblocks(4 * R.n, BS), BS, 0, c->s>>>(
@@ -1406,22 +1466,28 @@ void vcycle_tree(SolveCtx& S, int l) {
     AmrLevel& P = A->L[l - 1];
     TA<T> b = tarr<T>(P);
     const ORange R = orange(S, F, l);
+    const long long pno = l - 1 >= 1 ? P.n_oct : 0;  // FP32 parent layout (0: dense)
     if (R.n > 0) {
       if constexpr (std::is_same<T, float>::value)
         k_orestrict32<<<nblocks(R.n, BS), BS, 0, c->s>>>(a.w, a.wf, F.nbr, a.gh, fmask,
-                                                         R.n, R.list, F.pcell, m, (T)F.ih2, b.w,
-                                                         b.wE, b.wold, b.wf);
+                                                         R.n, R.list, F.n_oct, F.pcell, pno, m,
+                                                         (T)F.ih2, b.w, b.wold, b.wf);
       else
         k_orestrict<T><<<nblocks(R.n, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.nbr, a.gh, a.ghE,
                                                           fmask, R.n, R.list, F.pcell, m,
                                                           (T)F.ih2, b.w, b.wE, b.wold, b.wf);
     }
     if (l - 1 >= 1) {
-      if (P.n_list > 0)
-        k_ofas<T><<<nblocks(8 * P.n_list, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, P.nbr, b.gh,
-                                                              b.ghE, P.act,
-                                                              8 * P.n_list, P.olist, m,
-                                                              (T)P.ih2);
+      if (P.n_list > 0) {
+        if constexpr (std::is_same<T, float>::value)
+          k_ofas32<<<nblocks(P.n_list, BS), BS, 0, c->s>>>(b.w, b.wf, P.nbr, b.gh, P.act,
+                                                           P.n_list, P.olist, P.n_oct, m,
+                                                           (T)P.ih2);
+        else
+          k_ofas<T><<<nblocks(8 * P.n_list, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, P.nbr, b.gh,
+                                                                b.ghE, P.act, 8 * P.n_list,
+                                                                P.olist, m, (T)P.ih2);
+      }
     } else {
       k_dfas<T><<<nblocks(P.ncell, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, P.lgN, m, (T)P.ih2,
                                                        P.act);
@@ -1430,8 +1496,8 @@ void vcycle_tree(SolveCtx& S, int l) {
     vcycle_tree<T>(S, l - 1);
     if (R.n > 0) {
       if constexpr (std::is_same<T, float>::value)
-        k_oprolong32<false><<<nblocks(R.n, BS), BS, 0, c->s>>>(R.n, R.list, F.pcell, F.pnbr, b.w,
-                                                              b.wold, fmask,
+        k_oprolong32<false><<<nblocks(R.n, BS), BS, 0, c->s>>>(R.n, R.list, F.n_oct, F.pcell,
+                                                              F.pnbr, pno, b.w, b.wold, fmask,
                                                               g.prolong_linear, a.w);
       else
         k_oprolong<T><<<nblocks(8 * R.n, BS), BS, 0, c->s>>>(8 * R.n, R.list, F.pcell, F.pnbr,
@@ -1520,11 +1586,11 @@ void lin_relax(SolveCtx& S, int l, int sweeps) {
         if (l == S.L) prof_begin(c, 4, L.ncell);
         if (col == 0)
           k_oct_sweep32<true, 0><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-              L.w32, L.wold32, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, m,
+              L.w32, L.wold32, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, L.n_oct, m,
               (float)L.ih2, 0.f);
         else
           k_oct_sweep32<true, 1><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-              L.w32, L.wold32, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, m,
+              L.w32, L.wold32, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, L.n_oct, m,
               (float)L.ih2, 0.f);
         if (l == S.L) prof_end(c);
       } else
@@ -1585,15 +1651,16 @@ void lin_vcycle_tree(SolveCtx& S, int l) {
   if (l >= 1 && has_coarse(S, l)) {
     AmrLevel& P = A->L[l - 1];
     const ORange R = orange(S, F, l);
+    const long long pno = l - 1 >= 1 ? P.n_oct : 0;  // FP32 parent layout (0: dense)
     if (R.n > 0)
       k_olin_restrict32<<<nblocks(R.n, BS), BS, 0, c->s>>>(
-          F.wold32, F.wf32, F.w32, F.nbr, F.ghost32, fmask, R.n, R.list, F.pcell, m,
-          (float)F.ih2, P.wf32, P.w32, P.wE32, P.wold32);
+          F.wold32, F.wf32, F.w32, F.nbr, F.ghost32, fmask, R.n, R.list, F.n_oct, F.pcell, pno,
+          m, (float)F.ih2, P.wf32, P.w32, P.wold32);
     c->launches += 1;
     lin_vcycle_tree(S, l - 1);
     if (R.n > 0)
-      k_oprolong32<true><<<nblocks(R.n, BS), BS, 0, c->s>>>(R.n, R.list, F.pcell, F.pnbr,
-                                                           P.wold32, nullptr, fmask,
+      k_oprolong32<true><<<nblocks(R.n, BS), BS, 0, c->s>>>(R.n, R.list, F.n_oct, F.pcell,
+                                                           F.pnbr, pno, P.wold32, nullptr, fmask,
                                                            g.prolong_linear, F.wold32);
     c->launches += 1;
   } else if (l == 0 && S.kmax >= 1) {
@@ -1622,8 +1689,8 @@ mgfr_status lin_resid(SolveCtx& S, double* hs) {
   k_oresid_df<<<nparts, BS, 0, c->s>>>(
       reinterpret_cast<const dfl*>(L.w), reinterpret_cast<const dfl*>(L.wE),
       reinterpret_cast<const dfl*>(L.wf), L.nbr, reinterpret_cast<const dfl*>(L.ghost),
-      reinterpret_cast<const dfl*>(L.ghostE), L.ncell, mdf(S.m, L.ih2), L.wf32, L.w32, L.wold32,
-      H.partials);
+      reinterpret_cast<const dfl*>(L.ghostE), L.ncell, mdf(S.m, L.ih2), L.n_oct, L.wf32, L.w32,
+      L.wold32, H.partials);
   if (c->capturing >= 0) prof_end(c);
   k_finish3<<<1, 256, 0, c->s>>>(H.partials, nparts, H.scal + 8);
   c->launches += 2;
@@ -1667,7 +1734,7 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
   c->launches += 1;
   k_init_level<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.ncell, F.pcell, F.pnbr, up,
                                                       g.prolong_linear, F.w, F.wE,
-                                                      mixed ? F.w32 : nullptr);
+                                                      mixed ? F.w32 : nullptr, F.n_oct);
   if (mixed) {
     k_d2df<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.f, reinterpret_cast<dfl*>(F.wf), F.ncell);
   } else {
@@ -1677,7 +1744,7 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
   k_fill_f<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.mask, F.ncell, 1.f);
   c->launches += 3;
   if (mixed) {
-    k_d2f<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.f, F.wf32, F.ncell);
+    k_d2f<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.f, F.wf32, F.ncell, F.n_oct);
     c->launches += 1;
   }
   F.relaxed = F.ncell;
@@ -1700,8 +1767,9 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
     AmrLevel& P = A->L[l];
     const double* uu = l == 0 ? H.L[0].u : P.u;
     if (mixed) {
-      k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(uu, P.w32, P.ncell);
-      k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(uu, P.wold32, P.ncell);
+      const long long pno = l >= 1 ? P.n_oct : 0;  // FP32 layout (0: dense)
+      k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(uu, P.w32, P.ncell, pno);
+      k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(uu, P.wold32, P.ncell, pno);
       c->launches += 2;
     }
     MG_CK(c, cudaMemsetAsync(P.mask, 0, sizeof(float) * (size_t)P.ncell, c->s));
@@ -1756,7 +1824,7 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
         break;
       prev = r32;
     }
-    k_f2df_exp<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.w32, reinterpret_cast<dfl*>(F.w),
+    k_f2df_exp<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.w32, F.n_oct, reinterpret_cast<dfl*>(F.w),
                                                       reinterpret_cast<dfl*>(F.wE), F.ncell);
     c->launches += 1;
     w_df = true;
@@ -1782,7 +1850,7 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
       for (int q = 0; q < inner; ++q) lin_vcycle_tree(S, Lv);
       k_apply_df<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(reinterpret_cast<dfl*>(F.w),
                                                         reinterpret_cast<dfl*>(F.wE), F.wold32,
-                                                        F.ncell, (float)g.step_cap);
+                                                        F.n_oct, F.ncell, (float)g.step_cap);
       c->launches += 1;
       TRY(lin_resid(S, hs));
       c->capturing = -1;
@@ -1804,7 +1872,7 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
   }
   if (mixed && !(r > target) && it32 == 0) {
     // converged at the start: the FP64 iterate is the FP32 initial guess
-    k_f2d_exp<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.w32, F.w, F.wE, F.ncell);
+    k_f2d_exp<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.w32, F.n_oct, F.w, F.wE, F.ncell);
     c->launches += 1;
   }
   if (mixed && r > target) {
