@@ -510,8 +510,20 @@ __device__ __forceinline__ double oct_nbE(const double* __restrict__ E,
   if (no >= 0) return E[8LL * no + chn];
   const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
   const int qi = (((ch >> (2 - t1)) & 1) << 1) | ((ch >> (2 - t2)) & 1);
-  const long long g = 24 * o + 4 * d + qi;
+  const long long g = 4LL * (-no - 1) + qi;  // ghost slot of the face
   return gdf ? df_to_double(reinterpret_cast<const dfl*>(ghostE)[g]) : ghostE[g];
+}
+
+// Ghost faces (faces without a neighbouring oct) get consecutive slots in
+// storage order: flag them, scan, and store -(1 + slot) in the neighbour table.
+__global__ void k_face_flags(const int* __restrict__ nbr, long long n,
+                             unsigned char* __restrict__ flags) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) flags[i] = nbr[i] < 0 ? 1 : 0;
+}
+__global__ void k_face_slots(const int* __restrict__ slot, long long n, int* __restrict__ nbr) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n && slot[i] >= 0) nbr[i] = -(slot[i] + 1);
 }
 
 __global__ void k_oct_pnbrs(long long n_oct, int l, TreeView T, int* __restrict__ pnbr) {
@@ -633,6 +645,7 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
   L.wold = nullptr; L.mask = nullptr; L.ghost = nullptr; L.ghostE = nullptr; L.acc = nullptr;
   L.pnbr = nullptr; L.w32 = nullptr; L.wE32 = nullptr; L.wf32 = nullptr; L.wold32 = nullptr;
   L.ghost32 = nullptr; L.olist = nullptr; L.acc32 = nullptr; L.act = nullptr;
+  L.gcap = 0;
   TRY(grow(c, &L.son, n));
   TRY(grow(c, &L.refined, n));
   TRY(grow(c, &L.count, n));
@@ -649,13 +662,10 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
   TRY(grow(c, &L.wold32, n));
   if (l > 0) {
     TRY(grow(c, &L.pnbr, 6 * no));
-    TRY(grow(c, &L.ghost32, 24 * no));
     TRY(grow(c, &L.olist, no));
     TRY(grow(c, &L.opos, no));
     TRY(grow(c, &L.pcell, no));
     TRY(grow(c, &L.nbr, 6 * no));
-    TRY(grow(c, &L.ghost, 24 * no));
-    TRY(grow(c, &L.ghostE, 24 * no));
     TRY(grow(c, &L.acc, 3 * n));
     TRY(grow(c, &L.acc32, n));
     TRY(grow(c, &L.u, n));
@@ -725,6 +735,18 @@ static mgfr_status build_structure(mgfr_ctx* c, AmrWork* A, const double* pos) {
     k_oct_nbrs<<<nblocks(N.n_oct, BS), BS, 0, c->s>>>(N.n_oct, l + 1, T, N.nbr);
     k_oct_pnbrs<<<nblocks(N.n_oct, BS), BS, 0, c->s>>>(N.n_oct, l + 1, T, N.pnbr);
     c->launches += 3;
+    // ghost-face slots (scratch: the new level's refined and son arrays, set
+    // for real in the next pass)
+    k_face_flags<<<nblocks(6 * N.n_oct, BS), BS, 0, c->s>>>(N.nbr, 6 * N.n_oct, N.refined);
+    TRY(scan_flags(c, A, N.refined, 6 * N.n_oct, 0, N.son, &N.n_gslot));
+    k_face_slots<<<nblocks(6 * N.n_oct, BS), BS, 0, c->s>>>(N.son, 6 * N.n_oct, N.nbr);
+    c->launches += 2;
+    if (N.n_gslot > N.gcap) {
+      TRY(grow(c, &N.ghost, 4 * N.n_gslot));
+      TRY(grow(c, &N.ghostE, 4 * N.n_gslot));
+      TRY(grow(c, &N.ghost32, 4 * N.n_gslot));
+      N.gcap = N.n_gslot;
+    }
   }
   // the deepest level has no sons
   AmrLevel& D = A->L[A->nlev - 1];

@@ -25,18 +25,19 @@ struct AmrLevel {
   int* count = nullptr;               // [ncell]
   int4* opos = nullptr;               // [n_oct] parent coordinates at level l-1
   int* pcell = nullptr;               // [n_oct] parent cell index at level l-1
-  int* nbr = nullptr;                 // [n_oct*6] face-neighbour octs (-1: none)
+  int* nbr = nullptr;                 // [n_oct*6] face-neighbour oct, or -(1 + ghost slot)
+  long long n_gslot = 0, gcap = 0;    // ghost faces (faces without a neighbouring oct), capacity
   double* mass = nullptr;             // [ncell] deposited mass (particle units)
   double *u = nullptr, *E = nullptr, *f = nullptr;  // converged solution, source
   double *w = nullptr, *wE = nullptr, *wf = nullptr, *wold = nullptr;  // work
   float* mask = nullptr;              // [ncell] multigrid mask
-  double *ghost = nullptr, *ghostE = nullptr;  // [n_oct*24]
+  double *ghost = nullptr, *ghostE = nullptr;  // [n_gslot*4], 4 per ghost face
   double* acc = nullptr;              // [ncell*3] (level >= 1)
   float4* acc32 = nullptr;            // [ncell] FP32 force for the mixed-form gather
   int* pnbr = nullptr;                // [n_oct*6] parent's face-neighbour cells (-1: none)
   // FP32 work arrays (mixed precision phase of the level solves)
   float *w32 = nullptr, *wE32 = nullptr, *wf32 = nullptr, *wold32 = nullptr;
-  float* ghost32 = nullptr;           // [n_oct*24] FP32 ghost u (e^u recomputed)
+  float* ghost32 = nullptr;           // [n_gslot*4] FP32 ghost u (e^u recomputed)
   long long relaxed = 0;              // cells relaxed in the current level solve
   bool ghost_df = false;              // FP64 ghost slots hold double-float pairs (mixed form)
   unsigned char* act = nullptr;       // [ncell] mask > threshold (coarse level of a solve)

@@ -85,7 +85,7 @@ __device__ __forceinline__ NB<T> onb(const T* __restrict__ u, const T* __restric
   }
   const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
   const int qi = (((ch >> (2 - t1)) & 1) << 1) | ((ch >> (2 - t2)) & 1);
-  const long long g = 24 * o + 4 * d + qi;
+  const long long g = 4LL * (-no - 1) + qi;  // ghost slot of the face
   return NB<T>{gh[g], Eat(ghE, gh, g)};
 }
 
@@ -696,7 +696,7 @@ __global__ void __launch_bounds__(BS) k_oct_sweep32(
       NU = ldc(u, nb, no, OC);
       if (LIN) NX = ldc(e, nb, no, OC);
     } else {
-      NU = *reinterpret_cast<const float4*>(gh + 24 * o + 4 * d);
+      NU = *reinterpret_cast<const float4*>(gh + 4LL * (-nb - 1));
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -791,7 +791,7 @@ __device__ __forceinline__ void oct_sums(const float* __restrict__ u, const floa
       NU = ld8(u, nb, no);
       if (LIN) NX = ld8(x, nb, no);
     } else {
-      const float4 g = *reinterpret_cast<const float4*>(gh + 24 * o + 4 * d);
+      const float4 g = *reinterpret_cast<const float4*>(gh + 4LL * (-nb - 1));
       G[0] = g.x;
       G[1] = g.y;
       G[2] = g.z;
@@ -1055,7 +1055,7 @@ __device__ __forceinline__ void onb_df(const dfl* __restrict__ u, const dfl* __r
   }
   const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
   const int qi = (((ch >> (2 - t1)) & 1) << 1) | ((ch >> (2 - t2)) & 1);
-  const long long g = 24 * o + 4 * d + qi;
+  const long long g = 4LL * (-no - 1) + qi;  // ghost slot of the face
   un = gh[g];
   En = ghE[g];
 }
@@ -1175,7 +1175,9 @@ __global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restri
   if (t >= 6 * n_oct) return;
   const long long o = t / 6;
   const int d = (int)(t - 6 * o);
-  if (nbr[6 * o + d] >= 0) return;
+  const int nb = nbr[6 * o + d];
+  if (nb >= 0) return;
+  const long long slot = -(long long)nb - 1;
   const int ax = d >> 1, plus = d & 1;
   const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
   const int4 p = T.opos[l][o];
@@ -1211,7 +1213,7 @@ __global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restri
     double v = v0;
     for (int a = 0; a < 3; ++a)
       if (have[a]) v += (hi[a] ? 0.125 : -0.125) * g[a];
-    const long long q = 24 * o + 4 * d + qi;
+    const long long q = 4 * slot + qi;
     if (dfmode) {  // double-float slots (phase B of the mixed form), e^v on the FP32 pipes
       const dfl V = df_from_double(v);
       reinterpret_cast<dfl*>(ghost)[q] = V;
