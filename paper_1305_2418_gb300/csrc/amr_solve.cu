@@ -645,7 +645,7 @@ __device__ __forceinline__ int face_q(int ch, int ax) {
 //   LIN = false: Newton-Gauss-Seidel on L(u) = f (u updated)
 // no: octs of the level (plane stride); n, olist: the octs visited.
 template <bool LIN, int COL>
-__global__ void __launch_bounds__(BS) k_oct_sweep32(
+__global__ void __launch_bounds__(BS, 6) k_oct_sweep32(
     float* __restrict__ u, float* __restrict__ e, const float* __restrict__ rf,
     const int* __restrict__ nbr, const float* __restrict__ gh,
     const unsigned char* __restrict__ act, long long n, const int* __restrict__ olist,
