@@ -425,7 +425,7 @@ __device__ void visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
   }
 }
 
-__global__ void k_deposit(const double* __restrict__ pos, long long Np, double inv, double N0,
+__global__ void __launch_bounds__(256, 4) k_deposit(const double* __restrict__ pos, long long Np, double inv, double N0,
                           TreeView T, LevelPtrs D, unsigned long long* err) {
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= Np) return;
@@ -449,7 +449,7 @@ __global__ void k_gather(const double* __restrict__ pos, long long Np, double in
 }
 
 // mixed form: FP32 weights and FP32 force fields, FP64 output
-__global__ void k_gather32(const double* __restrict__ pos, long long Np, double inv, double N0,
+__global__ void __launch_bounds__(256, 4) k_gather32(const double* __restrict__ pos, long long Np, double inv, double N0,
                            TreeView T, GatherPtrs G, double* __restrict__ acc,
                            unsigned long long* err) {
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;

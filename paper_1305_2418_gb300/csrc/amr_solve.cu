@@ -1357,9 +1357,15 @@ struct SolveCtx {
 
 // whether the coarse grid below tree level l >= 1 of the level-S.L solve has
 // a relaxed cell (otherwise the cycle stops at level l)
+// A dense coarse grid (the base or a level below it) costs a pass over all its
+// cells per kernel but helps only where cells relax: the cycle descends to it
+// only when at least 1/kDenseMinDiv of its cells relax, and otherwise stops at
+// the finer level, whose few coarse-covered cells the smoothing settles.
+constexpr long long kDenseMinDiv = 64;
+
 bool has_coarse(const SolveCtx& S, int l) {
   const AmrLevel& P = S.A->L[l - 1];
-  return l - 1 >= 1 ? P.n_list > 0 : P.relaxed > 0;
+  return l - 1 >= 1 ? P.n_list > 0 : P.relaxed * kDenseMinDiv >= P.ncell;
 }
 
 // Octs visited on tree level l >= 1 of the level-S.L solve: every oct of the
@@ -1788,14 +1794,14 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
     k_mask_dense<<<nblocks(H.L[k].n, BS), BS, 0, c->s>>>(mf, H.L[k - 1].lg, A->dmask[k]);
     c->launches += 1;
   }
-  // the dense levels below the base that hold relaxed cells (the cycles stop
-  // at the deepest one; coarser grids would only relax nothing)
+  // the dense levels below the base the cycles visit: each must relax at
+  // least 1/kDenseMinDiv of its cells (and the base too, see has_coarse)
   int kmax = 0;
-  if (A->L[0].relaxed > 0) {
+  if (A->L[0].relaxed * kDenseMinDiv >= A->L[0].ncell) {
     for (int k = 1; k < H.nlev; ++k) {
       long long nk = 0;
       TRY(count_relaxed(c, A, A->dmask[k], H.L[k].n, mthr, &nk));
-      if (nk == 0) break;
+      if (nk == 0 || nk * kDenseMinDiv < H.L[k].n) break;
       kmax = k;
       k_act<<<nblocks(H.L[k].n, BS), BS, 0, c->s>>>(A->dmask[k], H.L[k].n, mthr, A->dact[k]);
       c->launches += 1;
