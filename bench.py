@@ -57,6 +57,11 @@ WORKLOAD = dict(name="particles256", N=256, box=100.0, a=1.0, fr0=1e-5, sigma_g=
 # the fractions below are lower bounds.)
 ALG_BYTES = {0: 8.0, 1: 12.0, 2: 36.0, 3: 11.0, 4: 15.0}
 FAMILY_BOUND = {0: "hbm", 1: "hbm", 2: "fp64", 3: "hbm", 4: "hbm"}
+# DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum / cells) of
+# one launch, from ncu on the half-density case of the same workload
+# (profiles/k_oct_sweep32_particles256_nbar05.md); scaled to a full launch by
+# its cells.
+TRAFFIC_PER_CELL = {3: 13.84}
 KERNEL_NAMES = {0: "k_sweep32 (FP32 NGS half-sweep, base level)",
                 1: "k_lin_sweep (FP32 linear GS half-sweep, base level)",
                 2: "k_resid64 / k_oresid_lin (FP64 residual of the level being solved)",
@@ -435,9 +440,11 @@ def main():
     bytes_per_launch = ALG_BYTES[fam] * kern_cells[fam] / max(kern_n[fam], 1)
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
     peak, peak_kind = peaks()
+    cells_per_launch = kern_cells[fam] / max(kern_n[fam], 1)
+    traffic = TRAFFIC_PER_CELL[fam] * cells_per_launch if fam in TRAFFIC_PER_CELL else None
     roof = {"bound": "hbm", "kernel": KERNEL_NAMES[fam], "achieved": achieved, "peak": peak,
             "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "launches": kern_n[fam], "avg_launch_us": 1e3 * avg_ms,
+            "traffic": traffic, "launches": kern_n[fam], "avg_launch_us": 1e3 * avg_ms,
             "alg_bytes_per_launch": bytes_per_launch,
             "kernel_share_of_step": kern_ms[fam] / ms_prof,
             "profiled_ms_per_step": ms_prof / args.steps,
