@@ -526,6 +526,40 @@ __global__ void k_face_slots(const int* __restrict__ slot, long long n, int* __r
   if (i < n && slot[i] >= 0) nbr[i] = -(slot[i] + 1);
 }
 
+// FP32 force copy of a refined level from e^u as double-float pairs (mixed
+// form): the central difference is formed exactly enough in double-float and
+// rounded once, on the FP32 pipes.  acc32 = g_scale (E+ - E-) per axis.
+__device__ __forceinline__ dfl oct_nbE_df(const dfl* __restrict__ E, const int* __restrict__ nbr,
+                                          const dfl* __restrict__ ghostE, long long o, int ch,
+                                          int d) {
+  const int ax = d >> 1, plus = d & 1;
+  const int bit = (ch >> (2 - ax)) & 1;
+  const int chn = ch ^ (1 << (2 - ax));
+  if (bit != plus) return E[8 * o + chn];
+  const int no = nbr[6 * o + d];
+  if (no >= 0) return E[8LL * no + chn];
+  const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+  const int qi = (((ch >> (2 - t1)) & 1) << 1) | ((ch >> (2 - t2)) & 1);
+  return ghostE[4LL * (-no - 1) + qi];
+}
+
+__global__ void k_oct_acc32_df(const dfl* __restrict__ E, const int* __restrict__ nbr,
+                               const dfl* __restrict__ ghostE, long long ncell, float g_scale,
+                               float4* __restrict__ acc32) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const long long o = c >> 3;
+  const int ch = (int)(c & 7);
+  float a[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const dfl em = oct_nbE_df(E, nbr, ghostE, o, ch, 2 * ax);
+    const dfl ep = oct_nbE_df(E, nbr, ghostE, o, ch, 2 * ax + 1);
+    a[ax] = g_scale * df_add_abs(ep, df_neg(em)).hi;
+  }
+  acc32[c] = make_float4(a[0], a[1], a[2], 0.f);
+}
+
 __global__ void k_oct_pnbrs(long long n_oct, int l, TreeView T, int* __restrict__ pnbr) {
   const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (o >= n_oct) return;
@@ -883,12 +917,24 @@ mgfr_status mgfr_solve_particles(mgfr_ctx* c, const double* pos, long long Np, i
     k_acc_pack<<<nblocks(L0.n, BS), BS, 0, c->s>>>(A->acc0, L0.n, A->acc0_32);
     c->launches += 1;
   }
+  A->fbar = m.fbar;
+  A->a = m.a;
   for (int l = 1; l < A->nlev; ++l) {
     AmrLevel& L = A->L[l];
     const double gs = m.fbar / (2.0 * L.h) / (2.0 * m.a);
-    k_oct_force<<<nblocks(L.ncell, BS), BS, 0, c->s>>>(L.E, L.nbr, L.ghostE, L.ghost_df ? 1 : 0,
-                                                       L.ncell, m.fbar, gs,
-                                                       L.w, L.acc, g32 ? L.acc32 : nullptr);
+    if (g32 && L.wE_df && L.ghost_df) {
+      // mixed form: the FP32 force copy straight from the double-float e^u; the
+      // FP64 f_R and force of the level are formed on request
+      k_oct_acc32_df<<<nblocks(L.ncell, BS), BS, 0, c->s>>>(
+          reinterpret_cast<const dfl*>(L.wE), L.nbr, reinterpret_cast<const dfl*>(L.ghostE),
+          L.ncell, (float)gs, L.acc32);
+      L.force_stale = true;
+    } else {
+      k_oct_force<<<nblocks(L.ncell, BS), BS, 0, c->s>>>(L.E, L.nbr, L.ghostE,
+                                                         L.ghost_df ? 1 : 0, L.ncell, m.fbar, gs,
+                                                         L.w, L.acc, g32 ? L.acc32 : nullptr);
+      L.force_stale = false;
+    }
     G.acc[l] = L.acc;
     G.acc32[l] = L.acc32;
     c->launches += 1;
@@ -958,10 +1004,23 @@ mgfr_status mgfr_get_level_field(mgfr_ctx* c, int level, int what, double* out_h
     case MGFR_FIELD_U: src = level == 0 ? c->dh.L[0].u : L.u; break;
     case MGFR_FIELD_SOURCE: src = level == 0 ? c->dh.L[0].f : L.f; break;
     case MGFR_FIELD_MASS: src = L.mass; break;
-    case MGFR_FIELD_FR: src = level == 0 ? A->fr0 : L.w; break;
+    case MGFR_FIELD_FR:
     case MGFR_FIELD_ACC:
-      src = level == 0 ? A->acc0 : L.acc;
-      cnt = 3 * n;
+      if (level >= 1 && L.force_stale) {  // deferred in the mixed form: form it now
+        const double gs = A->fbar / (2.0 * L.h) / (2.0 * A->a);
+        k_oct_force<<<nblocks(L.ncell, BS), BS, 0, c->s>>>(L.E, L.nbr, L.ghostE,
+                                                           L.ghost_df ? 1 : 0, L.ncell, A->fbar,
+                                                           gs, L.w, L.acc, nullptr);
+        MG_CK(c, cudaStreamSynchronize(c->s));
+        MG_CK(c, cudaGetLastError());
+        L.force_stale = false;
+      }
+      if (what == MGFR_FIELD_FR) {
+        src = level == 0 ? A->fr0 : L.w;
+      } else {
+        src = level == 0 ? A->acc0 : L.acc;
+        cnt = 3 * n;
+      }
       break;
     case MGFR_FIELD_COUNT: {
       std::vector<int> ci(n);

@@ -40,6 +40,8 @@ struct AmrLevel {
   float* ghost32 = nullptr;           // [n_gslot*4] FP32 ghost u (e^u recomputed)
   long long relaxed = 0;              // cells relaxed in the current level solve
   bool ghost_df = false;              // FP64 ghost slots hold double-float pairs (mixed form)
+  bool wE_df = false;                 // wE holds e^u as double-float pairs after the solve
+  bool force_stale = false;           // FP64 f_R (in w) and acc not yet formed (mixed form)
   unsigned char* act = nullptr;       // [ncell] mask > threshold (coarse level of a solve)
   int* olist = nullptr;               // [n_oct] octs with a relaxed cell (coarse level of a solve)
   long long n_list = 0;               // entries of olist in use
@@ -104,6 +106,7 @@ struct AmrWork {
   long long* d_small = nullptr;       // device scalars (totals, error flags)
   double* acc0 = nullptr;             // base force [3][N0^3]
   double* fr0 = nullptr;              // base fR [N0^3]
+  double fbar = 0.0, a = 1.0;         // of the last particle solve (deferred level forces)
   float4* acc0_32 = nullptr;          // base force, FP32 (x, y, z, 0) per cell
   long long cap_cells[AMR_MAXL] = {}; // allocated capacity per level (cells)
   long long cap_oct[AMR_MAXL] = {};

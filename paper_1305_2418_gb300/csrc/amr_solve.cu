@@ -1767,6 +1767,7 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
       MG_CK(c, cudaMemcpyAsync(P.w, uu, b8, cudaMemcpyDeviceToDevice, c->s));
       MG_CK(c, cudaMemcpyAsync(P.wE, EE, b8, cudaMemcpyDeviceToDevice, c->s));
       MG_CK(c, cudaMemcpyAsync(P.wold, uu, b8, cudaMemcpyDeviceToDevice, c->s));
+      P.wE_df = false;  // its e^u pairs are overwritten
     }
     return MGFR_OK;
   };
@@ -1921,6 +1922,7 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
                              cudaMemcpyDeviceToDevice, c->s));
   }
   F.ghost_df = gh_df;  // the force kernel reads the ghosts in either form
+  F.wE_df = w_df;      // e^u of the result still available as pairs in wE
   if (st) {
     st->level_iters[Lv] = it + it32;
     st->level_res[Lv] = r / ref;
