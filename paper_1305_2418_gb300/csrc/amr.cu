@@ -387,6 +387,10 @@ __device__ void visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
   }
   Lw[0][0] *= scale;
   Lw[0][1] *= scale;
+  // x-y products of the corner weights, shared by the two z pieces
+  W Lxy[4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) Lxy[b] = Lw[0][b >> 1] * Lw[1][b & 1];
   StackEnt st[48];
   int sp = 0;
   for (int q = 0; q < 8; ++q) {
@@ -407,7 +411,7 @@ __device__ void visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
     }
     const bool refined = lev == lam && lam + 1 < T.nlev && T.son[lam][cq] >= 0;
     if (!refined) {
-      touch<GATHER, W>(lev, cq, Lw[0][bits[0]] * Lw[1][bits[1]] * Lw[2][bits[2]], D, G, out);
+      touch<GATHER, W>(lev, cq, Lxy[(bits[0] << 1) | bits[1]] * Lw[2][bits[2]], D, G, out);
       continue;
     }
     long long lo[3], hi[3];
