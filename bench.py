@@ -41,9 +41,10 @@ WORKLOAD = dict(name="particles256", N=256, box=100.0, a=1.0, fr0=1e-5, sigma_g=
 #    active u (2)                                   = 8 B per cell of the level
 #  1 FP32 linear GS half-sweep: read u32 (4) + e (4) + r active (2) + write e
 #    active (2)                                     = 12 B per cell
-#  2 FP64 residual of the level being solved (k_resid64 on the base level,
-#    k_oresid_lin on a refined level): read u, E, f (24) + write r32, u32, e32
-#    (12) = 36 B per cell; bound by the FP64 pipe on this part, not by HBM
+#  2 FP64-accurate residual of the level being solved, in double-float on the
+#    FP32 pipes (k_resid_df on the base level, k_oresid_df on a refined level):
+#    read u, E, f pairs (24) + write r32, u32, e32 (12) = 36 B per cell; bound
+#    by FP32/ALU issue (~270 operations per cell), not by HBM
 #  (FP64 NGS half-sweep, plain path: read u, E (16) + f active (4) + write u, E
 #   active (8) = 28 B per cell)
 #  3 NGS half-sweep on the octs of the refined level being solved; in the
@@ -56,15 +57,15 @@ WORKLOAD = dict(name="particles256", N=256, box=100.0, a=1.0, fr0=1e-5, sigma_g=
 # (Ghost faces add bytes that depend on the patch geometry; not counted, so
 # the fractions below are lower bounds.)
 ALG_BYTES = {0: 8.0, 1: 12.0, 2: 36.0, 3: 11.0, 4: 15.0}
-FAMILY_BOUND = {0: "hbm", 1: "hbm", 2: "fp64", 3: "hbm", 4: "hbm"}
+FAMILY_BOUND = {0: "hbm", 1: "hbm", 2: "alu", 3: "hbm", 4: "hbm"}
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum / cells) of
 # one launch, from ncu on the half-density case of the same workload
 # (profiles/k_oct_sweep32_particles256_nbar05.md); scaled to a full launch by
 # its cells.
 TRAFFIC_PER_CELL = {3: 13.84}
-KERNEL_NAMES = {0: "k_sweep32 (FP32 NGS half-sweep, base level)",
-                1: "k_lin_sweep (FP32 linear GS half-sweep, base level)",
-                2: "k_resid64 / k_oresid_lin (FP64 residual of the level being solved)",
+KERNEL_NAMES = {0: "k_sweep32q (FP32 NGS half-sweep, base level)",
+                1: "k_lin_sweep_q (FP32 linear GS half-sweep, base level)",
+                2: "k_resid_df / k_oresid_df (FP64-accurate residual in double-float)",
                 3: "k_oct_sweep32<false> (FP32 NGS half-sweep on the octs of the refined level)",
                 4: "k_oct_sweep32<true> (FP32 linear GS half-sweep on the octs of the refined level)"}
 
@@ -433,8 +434,8 @@ def main():
         return
 
     # ---- roofline of the dominant profiled kernel ----
-    # the dominant sweep family (the FP64 residual is bound by the FP64 pipe,
-    # not by HBM, and is reported in the family table only)
+    # the dominant sweep family (the double-float residual is bound by
+    # arithmetic issue, not by HBM, and is reported in the family table only)
     fam = max((q for q in range(5) if FAMILY_BOUND[q] == "hbm"), key=lambda q: kern_ms[q])
     avg_ms = kern_ms[fam] / max(kern_n[fam], 1)
     bytes_per_launch = ALG_BYTES[fam] * kern_cells[fam] / max(kern_n[fam], 1)
