@@ -63,8 +63,8 @@ FAMILY_BOUND = {0: "hbm", 1: "hbm", 2: "alu", 3: "hbm", 4: "hbm"}
 # (profiles/k_oct_sweep32_particles256_nbar05.md); scaled to a full launch by
 # its cells.
 TRAFFIC_PER_CELL = {3: 13.84}
-KERNEL_NAMES = {0: "k_sweep32q (FP32 NGS half-sweep, base level)",
-                1: "k_lin_sweep_q (FP32 linear GS half-sweep, base level)",
+KERNEL_NAMES = {0: "k_sweep32 (FP32 NGS half-sweep, base level)",
+                1: "k_lin_sweep (FP32 linear GS half-sweep, base level)",
                 2: "k_resid_df / k_oresid_df (FP64-accurate residual in double-float)",
                 3: "k_oct_sweep32<false> (FP32 NGS half-sweep on the octs of the refined level)",
                 4: "k_oct_sweep32<true> (FP32 linear GS half-sweep on the octs of the refined level)"}

@@ -33,6 +33,78 @@ __host__ __device__ inline ModelF to_f(const Model& m) {
   return ModelF{(float)m.aRt, (float)m.aRt_np1, (float)m.inv_np1};
 }
 
+// Loads the float pair (k0 = 2kp, k1 = 2kp+1) of row (i,j) and the two
+// z-neighbours outside the pair (k0-1 and k1+1), using warp shuffles inside a
+// row and direct loads at warp and row edges (periodic in k).
+struct Pair {
+  float2 c;
+  float km, kp;  // u[k0-1], u[k1+1]
+};
+
+__device__ __forceinline__ Pair load_pair(const float* __restrict__ u, unsigned rowbase, int kp,
+                                          int np, int lane) {
+  const float2* u2 = reinterpret_cast<const float2*>(u + rowbase);
+  Pair p;
+  p.c = u2[kp];
+  float up = __shfl_up_sync(0xffffffffu, p.c.y, 1);
+  float dn = __shfl_down_sync(0xffffffffu, p.c.x, 1);
+  const int N = 2 * np;
+  p.km = (kp == 0 || lane == 0) ? u[rowbase + ((2 * kp - 1 + N) & (N - 1))] : up;
+  p.kp = (kp == np - 1 || lane == 31) ? u[rowbase + ((2 * kp + 2) & (N - 1))] : dn;
+  return p;
+}
+
+// ---- Phase A: nonlinear FP32 Newton-Gauss-Seidel half-sweep ----------------
+// Thread = one z-pair (2kp, 2kp+1) of one (i,j) row; it updates the pair's
+// cell of the active colour and writes the whole pair back (full sectors).
+__global__ void __launch_bounds__(BS) k_sweep32(float* __restrict__ u, const float* __restrict__ f,
+                                                int lg, int colour, ModelF m, float ih2,
+                                                float cap) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = 1 << lg, M = N - 1, np = N >> 1;
+  const bool live = t < (1u << (3 * lg - 1));
+  const unsigned tt = live ? t : 0;
+  const int kp = (int)(tt & (np - 1));
+  const unsigned rr = tt >> (lg - 1);
+  const int j = (int)(rr & M), i = (int)(rr >> lg);
+  const unsigned row = cidx(i, j, 0, lg);
+  const int lane = threadIdx.x & 31;
+  Pair p = load_pair(u, row, kp, np, lane);
+  if (!live) return;
+  const int odd = (i + j + colour) & 1;  // active cell is k0 + odd
+  const float2* u2 = reinterpret_cast<const float2*>(u);
+  const unsigned q = row / 2 + kp;
+  const float2 a = u2[cidx((i - 1) & M, j, 0, lg) / 2 + kp];
+  const float2 b = u2[cidx((i + 1) & M, j, 0, lg) / 2 + kp];
+  const float2 c = u2[cidx(i, (j - 1) & M, 0, lg) / 2 + kp];
+  const float2 d = u2[cidx(i, (j + 1) & M, 0, lg) / 2 + kp];
+  float uc, nb[6];
+  if (odd) {
+    uc = p.c.y;
+    nb[0] = a.y; nb[1] = b.y; nb[2] = c.y; nb[3] = d.y; nb[4] = p.c.x; nb[5] = p.kp;
+  } else {
+    uc = p.c.x;
+    nb[0] = a.x; nb[1] = b.x; nb[2] = c.x; nb[3] = d.x; nb[4] = p.km; nb[5] = p.c.y;
+  }
+  const float Ec = __expf(uc);
+  float sbd = 0.f, sd = 0.f, sb = 0.f;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const float bb = 0.5f * (__expf(nb[e]) + Ec), du = nb[e] - uc;
+    sbd = fmaf(bb, du, sbd);
+    sd += du;
+    sb += bb;
+  }
+  const float s = __expf(-uc * m.inv_np1);
+  const float L = sbd * ih2 + m.aRt * (1.f - s);
+  const float dL = (0.5f * Ec * sd - sb) * ih2 + m.aRt_np1 * s;
+  float step = __fdividef(L - f[row + 2 * kp + odd], dL);
+  step = fminf(fmaxf(step, -cap), cap);
+  float2 out = p.c;
+  if (odd) out.y = uc - step; else out.x = uc - step;
+  reinterpret_cast<float2*>(u)[q] = out;
+}
+
 __device__ __forceinline__ float Lpoint32(const float* __restrict__ u, int i, int j, int k, int lg,
                                           const ModelF& m, float ih2) {
   const int M = (1 << lg) - 1;
@@ -266,121 +338,26 @@ __device__ __forceinline__ void nb6(const float* __restrict__ x, int i, int j, i
   out[5] = x[cidx(i, j, (k + 1) & M, lg)];
 }
 
-// ---- quad kernels: one thread per four consecutive z-cells ------------------
-// The thread holds the cells 4kq..4kq+3 of row (i, j) as one float4, the four
-// neighbouring rows' float4s, and the two z-neighbours outside the quad (from
-// the neighbouring lanes by shuffle, direct loads at warp and row edges); it
-// updates the two cells of the active colour (k parity (i + j + colour) & 1)
-// and writes the float4 back.  Needs N >= 8.
-struct Quad {
-  float v[4];
-  float km, kp;  // x[4kq - 1], x[4kq + 4] (periodic)
-};
-
-__device__ __forceinline__ float4 ld4(const float* __restrict__ x, unsigned idx) {
-  return *reinterpret_cast<const float4*>(x + idx);
-}
-
-__device__ __forceinline__ Quad load_quad(const float* __restrict__ x, unsigned row, int kq, int nq,
-                                          int N, int lane) {
-  const float4 c = ld4(x, row + 4 * kq);
-  Quad q{{c.x, c.y, c.z, c.w}, 0.f, 0.f};
-  const float up = __shfl_up_sync(0xffffffffu, c.w, 1);
-  const float dn = __shfl_down_sync(0xffffffffu, c.x, 1);
-  q.km = (kq == 0 || lane == 0) ? x[row + ((4 * kq - 1 + N) & (N - 1))] : up;
-  q.kp = (kq == nq - 1 || lane == 31) ? x[row + ((4 * kq + 4) & (N - 1))] : dn;
-  return q;
-}
-
-__device__ __forceinline__ float f4v(const float4& v, int p) {
-  return p == 0 ? v.x : p == 1 ? v.y : p == 2 ? v.z : v.w;
-}
-
-// Nonlinear FP32 Newton-Gauss-Seidel half-sweep, quad form of k_sweep32.
-__global__ void __launch_bounds__(BS) k_sweep32q(float* __restrict__ u, const float* __restrict__ f,
-                                                 int lg, int colour, ModelF m, float ih2,
-                                                 float cap) {
+// Gauss-Seidel half-sweep on J e = r: e_i = (r_i - sum_j J_ij e_j) / J_ii.
+__global__ void __launch_bounds__(BS) k_lin_sweep(float* __restrict__ e, const float* __restrict__ r,
+                                                  const float* __restrict__ u, int lg, int colour,
+                                                  ModelF m, float ih2) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int N = 1 << lg, M = N - 1, nq = N >> 2;
-  const bool live = t < (1u << (3 * lg - 2));
-  const unsigned tt = live ? t : 0;
-  const int kq = (int)(tt & (nq - 1));
-  const unsigned rr = tt >> (lg - 2);
+  const int N = 1 << lg, M = N - 1;
+  if (t >= (1u << (3 * lg - 1))) return;
+  const int k2 = (int)(t & ((N >> 1) - 1));
+  const unsigned rr = t >> (lg - 1);
   const int j = (int)(rr & M), i = (int)(rr >> lg);
-  const unsigned row = cidx(i, j, 0, lg);
-  const int lane = threadIdx.x & 31;
-  const Quad q = load_quad(u, row, kq, nq, N, lane);  // every lane joins the shuffles
-  if (!live) return;
-  const float4 a = ld4(u, cidx((i - 1) & M, j, 0, lg) + 4 * kq);
-  const float4 b = ld4(u, cidx((i + 1) & M, j, 0, lg) + 4 * kq);
-  const float4 c = ld4(u, cidx(i, (j - 1) & M, 0, lg) + 4 * kq);
-  const float4 d = ld4(u, cidx(i, (j + 1) & M, 0, lg) + 4 * kq);
-  const float4 fq = ld4(f, row + 4 * kq);
-  const int p0 = (i + j + colour) & 1;
-  float out[4] = {q.v[0], q.v[1], q.v[2], q.v[3]};
+  const int k = 2 * k2 + ((i + j + colour) & 1);
+  const unsigned c = cidx(i, j, k, lg);
+  float un[6], en[6];
+  nb6(u, i, j, k, lg, un);
+  nb6(e, i, j, k, lg, en);
+  const Jrow J = jac_row(u[c], un, m, ih2);
+  float s = r[c];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int p = p0 + 2 * h;
-    const float uc = q.v[p];
-    const float nb[6] = {f4v(a, p), f4v(b, p), f4v(c, p), f4v(d, p),
-                         p == 0 ? q.km : q.v[p - 1], p == 3 ? q.kp : q.v[p + 1]};
-    const float Ec = __expf(uc);
-    float sbd = 0.f, sd = 0.f, sb = 0.f;
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      const float bb = 0.5f * (__expf(nb[e]) + Ec), du = nb[e] - uc;
-      sbd = fmaf(bb, du, sbd);
-      sd += du;
-      sb += bb;
-    }
-    const float sN = __expf(-uc * m.inv_np1);
-    const float L = sbd * ih2 + m.aRt * (1.f - sN);
-    const float dL = (0.5f * Ec * sd - sb) * ih2 + m.aRt_np1 * sN;
-    float step = __fdividef(L - f4v(fq, p), dL);
-    step = fminf(fmaxf(step, -cap), cap);
-    out[p] = uc - step;
-  }
-  *reinterpret_cast<float4*>(u + row + 4 * kq) = make_float4(out[0], out[1], out[2], out[3]);
-}
-
-// Gauss-Seidel half-sweep on J e = r, quad form of k_lin_sweep.
-__global__ void __launch_bounds__(BS) k_lin_sweep_q(float* __restrict__ e,
-                                                    const float* __restrict__ r,
-                                                    const float* __restrict__ u, int lg,
-                                                    int colour, ModelF m, float ih2) {
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int N = 1 << lg, M = N - 1, nq = N >> 2;
-  const bool live = t < (1u << (3 * lg - 2));
-  const unsigned tt = live ? t : 0;
-  const int kq = (int)(tt & (nq - 1));
-  const unsigned rr = tt >> (lg - 2);
-  const int j = (int)(rr & M), i = (int)(rr >> lg);
-  const unsigned row = cidx(i, j, 0, lg);
-  const int lane = threadIdx.x & 31;
-  const Quad qu = load_quad(u, row, kq, nq, N, lane);
-  const Quad qe = load_quad(e, row, kq, nq, N, lane);
-  if (!live) return;
-  const unsigned ra = cidx((i - 1) & M, j, 0, lg) + 4 * kq, rb = cidx((i + 1) & M, j, 0, lg) + 4 * kq,
-                 rc = cidx(i, (j - 1) & M, 0, lg) + 4 * kq, rd = cidx(i, (j + 1) & M, 0, lg) + 4 * kq;
-  const float4 ua = ld4(u, ra), ub = ld4(u, rb), uc4 = ld4(u, rc), ud = ld4(u, rd);
-  const float4 ea = ld4(e, ra), eb = ld4(e, rb), ec = ld4(e, rc), ed = ld4(e, rd);
-  const float4 rq = ld4(r, row + 4 * kq);
-  const int p0 = (i + j + colour) & 1;
-  float out[4] = {qe.v[0], qe.v[1], qe.v[2], qe.v[3]};
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int p = p0 + 2 * h;
-    const float un[6] = {f4v(ua, p), f4v(ub, p), f4v(uc4, p), f4v(ud, p),
-                         p == 0 ? qu.km : qu.v[p - 1], p == 3 ? qu.kp : qu.v[p + 1]};
-    const float en[6] = {f4v(ea, p), f4v(eb, p), f4v(ec, p), f4v(ed, p),
-                         p == 0 ? qe.km : qe.v[p - 1], p == 3 ? qe.kp : qe.v[p + 1]};
-    const Jrow J = jac_row(qu.v[p], un, m, ih2);
-    float acc = f4v(rq, p);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) acc = fmaf(-J.off[k], en[k], acc);
-    out[p] = __fdividef(acc, J.diag);
-  }
-  *reinterpret_cast<float4*>(e + row + 4 * kq) = make_float4(out[0], out[1], out[2], out[3]);
+  for (int q = 0; q < 6; ++q) s = fmaf(-J.off[q], en[q], s);
+  e[c] = __fdividef(s, J.diag);
 }
 
 // Coarse linear problem: r_c = R(r - J e), u_c = R(u), e_c = 0.
@@ -511,7 +488,7 @@ void state_to_fp64(DenseLevel& L, cudaStream_t s) {
 }
 
 void sweep(DenseLevel& L, const Model& m, int colour, float cap, cudaStream_t s) {
-  k_sweep32q<<<nblocks(L.n / 4, BS), BS, 0, s>>>(L.u32, L.f32, L.lg, colour, to_f(m), (float)L.ih2,
+  k_sweep32<<<nblocks(L.n / 2, BS), BS, 0, s>>>(L.u32, L.f32, L.lg, colour, to_f(m), (float)L.ih2,
                                                 cap);
 }
 void restrict_resid(DenseLevel& F, DenseLevel& C, const Model& m, double*, int, cudaStream_t s) {
@@ -544,7 +521,7 @@ void resid_df(DenseLevel& L, const double* fdf, const Model& m, double* partials
   k_finish32<<<1, 256, 0, s>>>(partials, nb, out);
 }
 void lin_sweep(DenseLevel& L, const Model& m, int colour, cudaStream_t s) {
-  k_lin_sweep_q<<<nblocks(L.n / 4, BS), BS, 0, s>>>(L.e32, L.r32, L.u32, L.lg, colour, to_f(m),
+  k_lin_sweep<<<nblocks(L.n / 2, BS), BS, 0, s>>>(L.e32, L.r32, L.u32, L.lg, colour, to_f(m),
                                                   (float)L.ih2);
 }
 void lin_restrict(DenseLevel& F, DenseLevel& C, const Model& m, cudaStream_t s) {
