@@ -83,6 +83,9 @@ typedef struct {
                           where the mask exceeds this (Sec. 3.3 uses 0.4;
                           default 0.99 relaxes only fully covered cells,
                           which converges also for weak screening)        */
+  int n_coarse;        /* red-black sweeps before and after the coarse grid
+                          on the coarser levels of a refined-level solve
+                          (0: n_pre and n_post, the default)               */
 } mgfr_config;
 
 typedef struct {
@@ -117,7 +120,7 @@ typedef struct {
 /* Fill *cfg with the defaults above (omega_m 0.3, fr0_abs 1e-5, n 1, FP64,
  * tol 1e-8, 2+2 sweeps, 100 V-cycles, linear prolongation, step cap 2,
  * max_level 0, refine_count 8, mixed_switch 3e-6, mixed_inner 3,
- * mask_thres 0.99). */
+ * mask_thres 0.99, n_coarse 0). */
 void mgfr_config_default(mgfr_config* cfg);
 
 /* Create a context on CUDA device `device`, working on `cuda_stream`

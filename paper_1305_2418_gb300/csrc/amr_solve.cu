@@ -1374,6 +1374,12 @@ struct ORange {
   const int* list;
   long long n;
 };
+
+// red-black sweeps on tree level l (l < S.L, or k >= 1 dense: a coarse grid)
+int sweeps_of(const SolveCtx& S, int l, int n) {
+  const int nc = S.c->cfg.n_coarse;
+  return l != S.L && nc > 0 ? nc : n;
+}
 ORange orange(const SolveCtx& S, const AmrLevel& L, int l) {
   return l == S.L ? ORange{nullptr, L.n_oct} : ORange{L.olist, L.n_list};
 }
@@ -1432,7 +1438,7 @@ void vcycle_dense(SolveCtx& S, int k) {
     c->launches += 1;
     return;
   }
-  for (int s = 0; s < g.n_pre; ++s)
+  for (int s = 0; s < sweeps_of(S, -1, g.n_pre); ++s)
     for (int col = 0; col < 2; ++col) {
       k_dsweep<T><<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lg, col, m, (T)F.ih2,
                                                          (T)g.step_cap, mk);
@@ -1451,7 +1457,7 @@ void vcycle_dense(SolveCtx& S, int k) {
                                                      g.prolong_linear, mk);
     c->launches += 1;
   }
-  for (int s = 0; s < g.n_post; ++s)
+  for (int s = 0; s < sweeps_of(S, -1, g.n_post); ++s)
     for (int col = 0; col < 2; ++col) {
       k_dsweep<T><<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lg, col, m, (T)F.ih2,
                                                          (T)g.step_cap, mk);
@@ -1468,7 +1474,7 @@ void vcycle_tree(SolveCtx& S, int l) {
   const MT<T> m = mt<T>(S.m);
   AmrLevel& F = A->L[l];
   TA<T> a = tarr<T>(F);
-  relax<T>(S, l, g.n_pre);
+  relax<T>(S, l, sweeps_of(S, l, g.n_pre));
   const unsigned char* fmask = l == S.L ? nullptr : F.act;
   if (l >= 1 && has_coarse(S, l)) {
     AmrLevel& P = A->L[l - 1];
@@ -1526,7 +1532,7 @@ void vcycle_tree(SolveCtx& S, int l) {
                                                          g.prolong_linear, F.act);
     c->launches += 1;
   }
-  relax<T>(S, l, g.n_post);
+  relax<T>(S, l, sweeps_of(S, l, g.n_post));
 }
 
 // residual norms of level L in precision T -> hs[0..2] (sum r^2, max, sum f^2)
@@ -1622,7 +1628,7 @@ void lin_vcycle_dense(SolveCtx& S, int k) {
     c->launches += 1;
     return;
   }
-  for (int s = 0; s < g.n_pre; ++s)
+  for (int s = 0; s < sweeps_of(S, -1, g.n_pre); ++s)
     for (int col = 0; col < 2; ++col) {
       k_dlin_sweep<<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, F.lg, col,
                                                          m, (float)F.ih2, mk);
@@ -1639,7 +1645,7 @@ void lin_vcycle_dense(SolveCtx& S, int k) {
                                                       mk);
     c->launches += 1;
   }
-  for (int s = 0; s < g.n_post; ++s)
+  for (int s = 0; s < sweeps_of(S, -1, g.n_post); ++s)
     for (int col = 0; col < 2; ++col) {
       k_dlin_sweep<<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, F.lg, col,
                                                          m, (float)F.ih2, mk);
@@ -1653,8 +1659,9 @@ void lin_vcycle_tree(SolveCtx& S, int l) {
   const mgfr_config& g = c->cfg;
   const MT<float> m = mt<float>(S.m);
   AmrLevel& F = A->L[l];
-  lin_relax(S, l, g.n_pre);
-  S.updates += (long long)g.n_pre * F.relaxed;
+  const int npre = sweeps_of(S, l, g.n_pre), npost = sweeps_of(S, l, g.n_post);
+  lin_relax(S, l, npre);
+  S.updates += (long long)npre * F.relaxed;
   const unsigned char* fmask = l == S.L ? nullptr : F.act;
   if (l >= 1 && has_coarse(S, l)) {
     AmrLevel& P = A->L[l - 1];
@@ -1683,8 +1690,8 @@ void lin_vcycle_tree(SolveCtx& S, int l) {
                                                           g.prolong_linear, F.act);
     c->launches += 1;
   }
-  lin_relax(S, l, g.n_post);
-  S.updates += (long long)g.n_post * F.relaxed;
+  lin_relax(S, l, npost);
+  S.updates += (long long)npost * F.relaxed;
 }
 
 // FP64 residual of level L with the linear system set up for phase B

@@ -126,6 +126,7 @@ void mgfr_config_default(mgfr_config* c) {
   c->mixed_inner = 3;
   c->max_spins = 1LL << 26;
   c->mask_thres = 0.99;
+  c->n_coarse = 0;
 }
 
 }  // extern "C"
@@ -153,6 +154,7 @@ static bool validate_cfg(const mgfr_config* c, std::string& why) {
   if (c->mixed_inner < 1 || c->mixed_inner > 16) return bad("mixed_inner in [1, 16]");
   if (c->max_spins < 0) return bad("max_spins must be >= 0");
   if (!(c->mask_thres >= 0.0 && c->mask_thres < 1.0)) return bad("mask_thres in [0, 1)");
+  if (c->n_coarse < 0 || c->n_coarse > 16) return bad("n_coarse in [0, 16]");
   return true;
 }
 

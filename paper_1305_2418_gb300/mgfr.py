@@ -27,7 +27,7 @@ class Config(C.Structure):
         ("n_post", C.c_int), ("max_vcycles", C.c_int), ("prolong_linear", C.c_int),
         ("step_cap", C.c_double), ("max_level", C.c_int), ("refine_count", C.c_int),
         ("mixed_switch", C.c_double), ("mixed_inner", C.c_int), ("max_spins", C.c_longlong),
-        ("profile", C.c_int), ("mask_thres", C.c_double),
+        ("profile", C.c_int), ("mask_thres", C.c_double), ("n_coarse", C.c_int),
     ]
 
 
