@@ -470,7 +470,9 @@ __global__ void __launch_bounds__(256, 4) k_gather32(const double* __restrict__ 
 // base-level force [3][n] (FP64) -> (x, y, z, 0) per cell (FP32)
 __global__ void k_acc_pack(const double* __restrict__ acc, long long n, float4* __restrict__ a32) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t < n) a32[t] = make_float4((float)acc[t], (float)acc[n + t], (float)acc[2 * n + t], 0.f);
+  if (t < n)
+    a32[t] = make_float4(f_from_double_bits(acc[t]), f_from_double_bits(acc[n + t]),
+                         f_from_double_bits(acc[2 * n + t]), 0.f);
 }
 
 // coarse cell mass = sum of its daughters (Sec. 3.1)

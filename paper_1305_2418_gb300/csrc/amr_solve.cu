@@ -1032,67 +1032,95 @@ MDF mdf(const Model& m, double ih2) {
   return MDF{df_from_double(m.aRt), df_from_double(m.inv_np1), df_from_double(0.5 * ih2), m.n};
 }
 
-// neighbour of cell (o, ch) in direction d: same oct, neighbouring oct, or ghost
-__device__ __forceinline__ void onb_df(const dfl* __restrict__ u, const dfl* __restrict__ E,
-                                       const int* __restrict__ nbr, const dfl* __restrict__ gh,
-                                       const dfl* __restrict__ ghE, long long o, int ch, int d,
-                                       dfl& un, dfl& En) {
-  const int ax = d >> 1, plus = d & 1;
-  const int bit = (ch >> (2 - ax)) & 1;
-  const int chn = ch ^ (1 << (2 - ax));
-  if (bit != plus) {
-    const long long q = 8 * o + chn;
-    un = u[q];
-    En = E[q];
-    return;
+// one double-float value as a single 8-byte load
+__device__ __forceinline__ dfl ldf(const dfl* __restrict__ p, long long i) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p) + i);
+  return dfl{v.x, v.y};
+}
+
+// the eight double-float values of oct o (64 contiguous bytes, four 16-byte loads)
+__device__ __forceinline__ void ld8df(const dfl* __restrict__ p, long long o, dfl* x) {
+  const float4* q = reinterpret_cast<const float4*>(p + 8 * o);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4 v = __ldg(q + i);
+    x[2 * i] = dfl{v.x, v.y};
+    x[2 * i + 1] = dfl{v.z, v.w};
   }
-  const int no = nbr[6 * o + d];
-  if (no >= 0) {
-    const long long q = 8LL * no + chn;
-    un = u[q];
-    En = E[q];
-    return;
-  }
-  const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
-  const int qi = (((ch >> (2 - t1)) & 1) << 1) | ((ch >> (2 - t2)) & 1);
-  const long long g = 4LL * (-no - 1) + qi;  // ghost slot of the face
-  un = gh[g];
-  En = ghE[g];
 }
 
 // r = f - L(u) to FP64 accuracy in double-float (Sec. 3.2 operator); stores r
 // and u rounded to FP32 for the linear cycles, zeroes the correction e, and
 // accumulates the norms (FP32 within a thread, FP64 across threads: they feed
-// only the stopping test).
+// only the stopping test).  One thread per oct: the flux across each of the
+// oct's 12 inner faces, (E_i + E_j)(u_j - u_i), is formed once and enters
+// the two cells with opposite signs (the double-float sum, difference and
+// product are odd under negation, so each cell's terms are those of a
+// cell-by-cell evaluation); every cell sums its six terms in the direction
+// order -x, +x, -y, +y, -z, +z.
 __global__ void __launch_bounds__(BS) k_oresid_df(
     const dfl* __restrict__ u, const dfl* __restrict__ E, const dfl* __restrict__ f,
     const int* __restrict__ nbr, const dfl* __restrict__ gh, const dfl* __restrict__ ghE,
-    long long ncell, MDF m, long long no, float* __restrict__ r32, float* __restrict__ u32,
+    MDF m, long long no, float* __restrict__ r32, float* __restrict__ u32,
     float* __restrict__ e32, double* __restrict__ partials) {
   float ss = 0.f, mx = 0.f, fs = 0.f;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
-       c += (long long)gridDim.x * blockDim.x) {
-    const long long o = c >> 3;
-    const int ch = (int)(c & 7);
-    const dfl uc = u[c], Ec = E[c];
-    dfl acc = {0.f, 0.f};
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < no;
+       o += (long long)gridDim.x * blockDim.x) {
+    dfl U[8], Ev[8], acc[8];
+    ld8df(u, o, U);
+    ld8df(E, o, Ev);
 #pragma unroll
-    for (int d = 0; d < 6; ++d) {
-      dfl un, En;
-      onb_df(u, E, nbr, gh, ghE, o, ch, d, un, En);
-      acc = df_add_abs(acc, df_mul(df_add_abs(En, Ec), df_add_abs(un, df_neg(uc))));
+    for (int ch = 0; ch < 8; ++ch) acc[ch] = dfl{0.f, 0.f};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      const int sh = 2 - ax;
+      const int nm = nbr[6 * o + 2 * ax], np = nbr[6 * o + 2 * ax + 1];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        // ch0 has bit sh clear (the minus half), ch1 is its partner across the face
+        const int ch0 = ((q >> sh) << (sh + 1)) | (q & ((1 << sh) - 1));
+        const int ch1 = ch0 | (1 << sh);
+        const int qi = face_q(ch0, ax);
+        dfl um, Em, up, Ep;  // across the minus face of ch0, the plus face of ch1
+        if (nm >= 0) {
+          um = ldf(u, 8LL * nm + ch1);
+          Em = ldf(E, 8LL * nm + ch1);
+        } else {
+          um = ldf(gh, 4LL * (-nm - 1) + qi);
+          Em = ldf(ghE, 4LL * (-nm - 1) + qi);
+        }
+        if (np >= 0) {
+          up = ldf(u, 8LL * np + ch0);
+          Ep = ldf(E, 8LL * np + ch0);
+        } else {
+          up = ldf(gh, 4LL * (-np - 1) + qi);
+          Ep = ldf(ghE, 4LL * (-np - 1) + qi);
+        }
+        const dfl Fin = df_mul(df_add_abs(Ev[ch1], Ev[ch0]), df_add_abs(U[ch1], df_neg(U[ch0])));
+        acc[ch0] = df_add_abs(acc[ch0], df_mul(df_add_abs(Em, Ev[ch0]), df_add_abs(um, df_neg(U[ch0]))));
+        acc[ch0] = df_add_abs(acc[ch0], Fin);
+        acc[ch1] = df_add_abs(acc[ch1], df_neg(Fin));
+        acc[ch1] = df_add_abs(acc[ch1], df_mul(df_add_abs(Ep, Ev[ch1]), df_add_abs(up, df_neg(U[ch1]))));
+      }
     }
-    const dfl sN = m.n == 1 ? df_rsqrt(Ec) : df_exp(df_neg(df_mul(uc, m.inv_np1)));
-    const dfl L = df_add(df_mul(acc, m.ih2h), df_mul(m.aRt, df_add_f(df_neg(sN), 1.f)));
-    const dfl fc = f[c];
-    const dfl r = df_sub(fc, L);
-    const long long k = pidx(c, no);
-    r32[k] = r.hi;
-    u32[k] = uc.hi;
-    e32[k] = 0.f;
-    ss = fmaf(r.hi, r.hi, ss);
-    mx = fmaxf(mx, fabsf(r.hi));
-    fs = fmaf(fc.hi, fc.hi, fs);
+    dfl F8[8];
+    ld8df(f, o, F8);
+    Oct8 R, Uh;
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+      const dfl sN = m.n == 1 ? df_rsqrt(Ev[ch]) : df_exp(df_neg(df_mul(U[ch], m.inv_np1)));
+      const dfl L = df_add(df_mul(acc[ch], m.ih2h), df_mul(m.aRt, df_add_f(df_neg(sN), 1.f)));
+      const dfl r = df_sub(F8[ch], L);
+      R.v[ch] = r.hi;
+      Uh.v[ch] = U[ch].hi;
+      ss = fmaf(r.hi, r.hi, ss);
+      mx = fmaxf(mx, fabsf(r.hi));
+      fs = fmaf(F8[ch].hi, F8[ch].hi, fs);
+    }
+    st8(r32, o, no, R);
+    st8(u32, o, no, Uh);
+    stc(e32, o, no, 0, make_float4(0.f, 0.f, 0.f, 0.f));
+    stc(e32, o, no, 1, make_float4(0.f, 0.f, 0.f, 0.f));
   }
   block_partials3((double)ss, (double)mx, (double)fs, partials);
 }
@@ -1122,14 +1150,14 @@ __global__ void k_df2d(const dfl* __restrict__ x, double* __restrict__ y, long l
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n) {
     const dfl v = x[i];
-    y[i] = df_to_double(v);
+    y[i] = df_to_double_bits(v);
   }
 }
 __global__ void k_d2df(const double* __restrict__ x, dfl* __restrict__ y, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n) {
     const double v = x[i];
-    y[i] = df_from_double(v);
+    y[i] = df_from_double_bits(v);
   }
 }
 
@@ -1144,6 +1172,21 @@ __global__ void k_init_level(long long ncell, const int* __restrict__ pcell,
   if (c >= ncell) return;
   const long long o = c >> 3;
   const int ch = (int)(c & 7);
+  if (w32) {
+    // mixed form: an FP32 guess (the FP64 iterate is taken from w32 later),
+    // with the parent values converted on the integer pipes
+    float v = f_from_double_bits(up[pcell[o]]);
+    if (linear) {
+      for (int ax = 0; ax < 3; ++ax) {
+        const int pm = pnbr[6 * o + 2 * ax], pp = pnbr[6 * o + 2 * ax + 1];
+        if (pm < 0 || pp < 0) continue;
+        v = fmaf(((ch >> (2 - ax)) & 1) ? 0.125f : -0.125f,
+                 f_from_double_bits(up[pp]) - f_from_double_bits(up[pm]), v);
+      }
+    }
+    w32[pidx(c, no)] = v;
+    return;
+  }
   double v = up[pcell[o]];
   if (linear) {
     for (int ax = 0; ax < 3; ++ax) {
@@ -1152,12 +1195,8 @@ __global__ void k_init_level(long long ncell, const int* __restrict__ pcell,
       v += (((ch >> (2 - ax)) & 1) ? 0.125 : -0.125) * (up[pp] - up[pm]);
     }
   }
-  if (w32) {
-    w32[pidx(c, no)] = (float)v;  // mixed form: the FP64 iterate is taken from w32 later
-  } else {
-    w[c] = v;
-    wE[c] = exp(v);
-  }
+  w[c] = v;
+  wE[c] = exp(v);
 }
 
 // Ghost values on the faces of level-l octs that have no neighbouring oct
@@ -1179,51 +1218,69 @@ __global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restri
   if (nb >= 0) return;
   const long long slot = -(long long)nb - 1;
   const int ax = d >> 1, plus = d & 1;
-  const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+  const int t1 = ax == 0 ? 1 : 0;  // the first tangential axis
   const int4 p = T.opos[l][o];
-  long long P[3] = {p.x, p.y, p.z};
-  P[ax] += plus ? 1 : -1;
+  const long long P0 = p.x + (ax == 0 ? (plus ? 1 : -1) : 0);
+  const long long P1 = p.y + (ax == 1 ? (plus ? 1 : -1) : 0);
+  const long long P2 = p.z + (ax == 2 ? (plus ? 1 : -1) : 0);
   int lev;
-  const long long pc = find_cell(T, l - 1, P[0], P[1], P[2], &lev);
-  double v0 = 0.0, g[3] = {0.0, 0.0, 0.0};
-  bool have[3] = {false, false, false};
-  if (lev == l - 1) {
-    v0 = up[pc];
-    if (linear) {
-      for (int a = 0; a < 3; ++a) {
-        long long Qp[3] = {P[0], P[1], P[2]}, Qm[3] = {P[0], P[1], P[2]};
-        Qp[a] += 1;
-        Qm[a] -= 1;
-        int lp, lm;
-        const long long cp = find_cell(T, l - 1, Qp[0], Qp[1], Qp[2], &lp);
-        const long long cm = find_cell(T, l - 1, Qm[0], Qm[1], Qm[2], &lm);
-        if (lp != l - 1 || lm != l - 1) continue;
-        g[a] = up[cp] - up[cm];
-        have[a] = true;
+  const long long pc = find_cell(T, l - 1, P0, P1, P2, &lev);
+  // P's value and, per axis, the indices of its two neighbours (-1: no gradient)
+  long long cm[3] = {-1, -1, -1}, cp[3] = {-1, -1, -1};
+  if (lev == l - 1 && linear) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int lp, lm;
+      const long long qp = find_cell(T, l - 1, P0 + (a == 0), P1 + (a == 1), P2 + (a == 2), &lp);
+      const long long qm = find_cell(T, l - 1, P0 - (a == 0), P1 - (a == 1), P2 - (a == 2), &lm);
+      if (lp == l - 1 && lm == l - 1) {
+        cp[a] = qp;
+        cm[a] = qm;
       }
     }
   }
-  for (int qi = 0; qi < 4; ++qi) {
-    // daughter position of the ghost inside P: along the normal the side
-    // facing the oct, tangentially the oct cell's own bits
-    int hi[3];
-    hi[ax] = plus ? 0 : 1;
-    hi[t1] = (qi >> 1) & 1;
-    hi[t2] = qi & 1;
-    double v = v0;
+  // daughter bit of the ghost along each axis inside P: along the normal the
+  // side facing the oct, tangentially the oct cell's own bits (qi's two bits)
+  auto hbit = [&](int a, int qi) {
+    return a == ax ? 1 - plus : a == t1 ? (qi >> 1) & 1 : qi & 1;
+  };
+  if (dfmode) {
+    // double-float slots (phase B of the mixed form): the parent's FP64
+    // values converted on the integer pipes, the stencil and e^v on the FP32
+    // pipes
+    dfl v0{0.f, 0.f}, g[3];
+    if (lev == l - 1) v0 = df_from_double_bits(up[pc]);
+#pragma unroll
     for (int a = 0; a < 3; ++a)
-      if (have[a]) v += (hi[a] ? 0.125 : -0.125) * g[a];
-    const long long q = 4 * slot + qi;
-    if (dfmode) {  // double-float slots (phase B of the mixed form), e^v on the FP32 pipes
-      const dfl V = df_from_double(v);
+      g[a] = cp[a] >= 0 ? df_mul_f(df_sub(df_from_double_bits(up[cp[a]]),
+                                          df_from_double_bits(up[cm[a]])),
+                                   0.125f)
+                        : dfl{0.f, 0.f};
+    for (int qi = 0; qi < 4; ++qi) {
+      dfl V = v0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (cp[a] >= 0) V = df_add(V, hbit(a, qi) ? g[a] : df_neg(g[a]));
+      const long long q = 4 * slot + qi;
       reinterpret_cast<dfl*>(ghost)[q] = V;
       reinterpret_cast<dfl*>(ghostE)[q] = df_exp(V);
       g32[q] = V.hi;
-    } else {
-      ghost[q] = v;
-      ghostE[q] = exp(v);
-      g32[q] = (float)v;
     }
+    return;
+  }
+  const double v0 = lev == l - 1 ? up[pc] : 0.0;
+  double g[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) g[a] = cp[a] >= 0 ? up[cp[a]] - up[cm[a]] : 0.0;
+  for (int qi = 0; qi < 4; ++qi) {
+    double v = v0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (cp[a] >= 0) v += (hbit(a, qi) ? 0.125 : -0.125) * g[a];
+    const long long q = 4 * slot + qi;
+    ghost[q] = v;
+    ghostE[q] = exp(v);
+    g32[q] = (float)v;
   }
 }
 
@@ -1231,7 +1288,7 @@ __global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restri
 __global__ void k_d2f(const double* __restrict__ x, float* __restrict__ y, long long n,
                       long long no) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n) y[pidx(i, no)] = (float)x[i];
+  if (i < n) y[pidx(i, no)] = f_from_double_bits(x[i]);
 }
 
 // FP64 iterate from the FP32 one: w = w32, wE = e^w
@@ -1699,12 +1756,12 @@ mgfr_status lin_resid(SolveCtx& S, double* hs) {
   mgfr_ctx* c = S.c;
   AmrLevel& L = S.A->L[S.L];
   DenseHier& H = c->dh;
-  const int nparts = (int)std::min<long long>(H.nparts / 2, nblocks(L.ncell, BS));
+  const int nparts = (int)std::min<long long>(H.nparts / 2, nblocks(L.n_oct, BS));
   if (c->capturing >= 0) prof_begin(c, 2, L.ncell);
   k_oresid_df<<<nparts, BS, 0, c->s>>>(
       reinterpret_cast<const dfl*>(L.w), reinterpret_cast<const dfl*>(L.wE),
       reinterpret_cast<const dfl*>(L.wf), L.nbr, reinterpret_cast<const dfl*>(L.ghost),
-      reinterpret_cast<const dfl*>(L.ghostE), L.ncell, mdf(S.m, L.ih2), L.n_oct, L.wf32, L.w32,
+      reinterpret_cast<const dfl*>(L.ghostE), mdf(S.m, L.ih2), L.n_oct, L.wf32, L.w32,
       L.wold32, H.partials);
   if (c->capturing >= 0) prof_end(c);
   k_finish3<<<1, 256, 0, c->s>>>(H.partials, nparts, H.scal + 8);

@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(BS) k_norm32(const float* __restrict__ u, cons
 
 __global__ void k_from64(const double* __restrict__ x, float* __restrict__ y, long long n) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) y[t] = (float)x[t];
+  if (t < n) y[t] = f_from_double_bits(x[t]);
 }
 
 // FP32 iterate -> double-float iterate and its e^u (start of phase B)
@@ -429,14 +429,14 @@ __global__ void k_d2df(const double* __restrict__ x, dfl* __restrict__ y, long l
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) {
     const double v = x[t];
-    y[t] = df_from_double(v);
+    y[t] = df_from_double_bits(v);
   }
 }
 __global__ void k_df2d(const dfl* __restrict__ x, double* __restrict__ y, long long n) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) {
     const dfl v = x[t];
-    y[t] = df_to_double(v);
+    y[t] = df_to_double_bits(v);
   }
 }
 

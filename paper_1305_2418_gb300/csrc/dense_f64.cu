@@ -51,7 +51,12 @@ __global__ void k_init(const double* __restrict__ u0, double* __restrict__ u,
                        double* __restrict__ E, long long n) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n) return;
-  double v = u0 ? u0[t] : 0.0;
+  if (!u0) {  // the zero start: e^0 = 1
+    u[t] = 0.0;
+    E[t] = 1.0;
+    return;
+  }
+  const double v = u0[t];
   u[t] = v;
   E[t] = exp(v);
 }

@@ -11,6 +11,7 @@
 // compiles as host C++ (with -ffp-contract=off) for testing.
 #pragma once
 #include <math.h>
+#include <string.h>
 
 #ifndef __CUDACC__
 #define __host__
@@ -109,6 +110,102 @@ __host__ __device__ __forceinline__ dfl df_from_double(double x) {
 }
 __host__ __device__ __forceinline__ double df_to_double(dfl a) {
   return (double)a.hi + (double)a.lo;
+}
+
+// ---- conversions on the integer pipes --------------------------------------
+// On GB300 a conversion to or from FP64 issues on the FP64 pipe, like an FP64
+// add.  Kernels that only move values between FP64 arrays and FP32 or
+// double-float ones use these instead: they take the IEEE bit patterns apart
+// with integer instructions.  FP32 results that would be subnormal are
+// flushed to zero (|x| < 2^-126), and the low part of a pair is dropped when
+// |x| < 2^-74: losses far below the accuracy of every value they carry here.
+__host__ __device__ __forceinline__ unsigned long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long b;
+  memcpy(&b, &x, 8);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ double dfrombits(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  memcpy(&x, &b, 8);
+  return x;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned fbits(float x) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(x);
+#else
+  unsigned b;
+  memcpy(&b, &x, 4);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ float ffrombits(unsigned b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float x;
+  memcpy(&x, &b, 4);
+  return x;
+#endif
+}
+
+// FP64 -> FP32, rounded to nearest even (the cast's result wherever it is a
+// normal number): the 29 dropped significand bits are rounded into the kept
+// ones by an integer add, whose carry moves on into the exponent.
+__host__ __device__ __forceinline__ float f_from_double_bits(double x) {
+  unsigned long long b = dbits(x);
+  const unsigned s = (unsigned)(b >> 63) << 31;
+  b &= 0x7fffffffffffffffULL;
+  if (b >= 0x7ff0000000000000ULL)  // inf, nan
+    return ffrombits(s | 0x7f800000u | (b > 0x7ff0000000000000ULL ? 0x400000u : 0u));
+  b += 0x0fffffffULL + ((b >> 29) & 1);
+  const int e = (int)(b >> 52) - 1023 + 127;
+  if (e <= 0) return ffrombits(s);
+  if (e >= 255) return ffrombits(s | 0x7f800000u);
+  return ffrombits(s | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+}
+
+// FP32 -> FP64, exact (subnormal inputs flushed to zero)
+__host__ __device__ __forceinline__ double d_from_float_bits(float x) {
+  const unsigned b = fbits(x);
+  const unsigned long long s = (unsigned long long)(b >> 31) << 63;
+  const int e = (int)((b >> 23) & 255);
+  const unsigned long long m = (unsigned long long)(b & 0x7fffffu) << 29;
+  if (e == 0) return dfrombits(s);
+  if (e == 255) return dfrombits(s | 0x7ff0000000000000ULL | m);
+  return dfrombits(s | ((unsigned long long)(e - 127 + 1023) << 52) | m);
+}
+
+// FP64 -> double-float: hi = x rounded to FP32, lo = x - hi rounded to FP32
+// (the pair df_from_double forms).  With M the 53-bit significand and E the
+// exponent, x - hi = (M - H 2^29) 2^(E-52), H = hi's 24-bit significand: an
+// integer below 2^28 in magnitude, converted once and scaled exactly.
+__host__ __device__ __forceinline__ dfl df_from_double_bits(double x) {
+  const unsigned long long b = dbits(x) & 0x7fffffffffffffffULL;
+  const float hi = f_from_double_bits(x);
+  const int E = (int)(b >> 52) - 1023;
+  if (E < -74 || E > 127 || fbits(hi) << 1 == 0u || (fbits(hi) & 0x7f800000u) == 0x7f800000u)
+    return dfl{hi, 0.f};
+  const long long M = (long long)((b & 0xfffffffffffffULL) | 0x10000000000000ULL);
+  // hi's significand scaled to x's exponent (a round-up to 2^24 is included)
+  const long long H = (long long)((fbits(hi) & 0x7fffffu) | 0x800000u)
+                      << (((fbits(hi) >> 23) & 255) - 127 - E);
+  const float r = (float)(int)(M - (H << 29));  // |M - H 2^29| <= 2^28
+  const float sc = ffrombits((unsigned)(E - 52 + 127) << 23);
+  const float lo = DF_MUL(r, sc);
+  return (long long)dbits(x) < 0 ? dfl{hi, -lo} : dfl{hi, lo};
+}
+
+// double-float -> FP64: the exact widenings of both parts, one FP64 add
+__host__ __device__ __forceinline__ double df_to_double_bits(dfl a) {
+  return d_from_float_bits(a.hi) + d_from_float_bits(a.lo);
 }
 
 // 2^(j/32), j = 0..31, as double-float pairs: the FP64 value of 2^(j/32)
