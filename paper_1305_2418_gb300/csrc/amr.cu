@@ -527,9 +527,13 @@ __global__ void k_face_flags(const int* __restrict__ nbr, long long n,
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n) flags[i] = nbr[i] < 0 ? 1 : 0;
 }
-__global__ void k_face_slots(const int* __restrict__ slot, long long n, int* __restrict__ nbr) {
+__global__ void k_face_slots(const int* __restrict__ slot, long long n, int* __restrict__ nbr,
+                             unsigned* __restrict__ gface) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n && slot[i] >= 0) nbr[i] = -(slot[i] + 1);
+  if (i < n && slot[i] >= 0) {
+    nbr[i] = -(slot[i] + 1);
+    gface[slot[i]] = (unsigned)i;
+  }
 }
 
 // FP32 force copy of a refined level from e^u as double-float pairs (mixed
@@ -609,7 +613,7 @@ static AmrWork* W(mgfr_ctx* c) { return (AmrWork*)c->amr; }
 static void free_level(AmrLevel& L) {
   void* ps[] = {L.son,  L.refined, L.count,  L.opos, L.pcell,   L.nbr,     L.mass,
                 L.w,    L.wE,      L.wf,     L.wold, L.mask,    L.ghost,   L.ghostE,
-                L.acc,  L.pnbr,    L.w32,    L.wE32, L.wf32,    L.wold32,  L.ghost32,
+                L.acc,  L.pnbr,    L.w32,    L.wE32, L.wf32,    L.wold32,  L.ghost32, L.gface,
                 L.olist,  L.acc32, L.act};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -684,7 +688,7 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
   L.nbr = nullptr; L.mass = nullptr; L.w = nullptr; L.wE = nullptr; L.wf = nullptr;
   L.wold = nullptr; L.mask = nullptr; L.ghost = nullptr; L.ghostE = nullptr; L.acc = nullptr;
   L.pnbr = nullptr; L.w32 = nullptr; L.wE32 = nullptr; L.wf32 = nullptr; L.wold32 = nullptr;
-  L.ghost32 = nullptr; L.olist = nullptr; L.acc32 = nullptr; L.act = nullptr;
+  L.ghost32 = nullptr; L.olist = nullptr; L.acc32 = nullptr; L.act = nullptr; L.gface = nullptr;
   L.gcap = 0;
   TRY(grow(c, &L.son, n));
   TRY(grow(c, &L.refined, n));
@@ -764,6 +768,8 @@ static mgfr_status build_structure(mgfr_ctx* c, AmrWork* A, const double* pos) {
     long long nref = 0;
     TRY(scan_flags(c, A, L.refined, L.ncell, l == 0 ? A->lg0 : 0, L.son, &nref));
     if (nref == 0) break;
+    // oct and face indices are 32-bit (neighbour tables, ghost slots)
+    if (6 * nref > 0x7fffffffLL) return set_err(c, MGFR_E_INVALID, "refined level too large");
     AmrLevel& N = A->L[l + 1];
     N.n_oct = nref;
     N.ncell = 8 * nref;
@@ -779,14 +785,15 @@ static mgfr_status build_structure(mgfr_ctx* c, AmrWork* A, const double* pos) {
     // for real in the next pass)
     k_face_flags<<<nblocks(6 * N.n_oct, BS), BS, 0, c->s>>>(N.nbr, 6 * N.n_oct, N.refined);
     TRY(scan_flags(c, A, N.refined, 6 * N.n_oct, 0, N.son, &N.n_gslot));
-    k_face_slots<<<nblocks(6 * N.n_oct, BS), BS, 0, c->s>>>(N.son, 6 * N.n_oct, N.nbr);
-    c->launches += 2;
     if (N.n_gslot > N.gcap) {
       TRY(grow(c, &N.ghost, 4 * N.n_gslot));
       TRY(grow(c, &N.ghostE, 4 * N.n_gslot));
       TRY(grow(c, &N.ghost32, 4 * N.n_gslot));
+      TRY(grow(c, &N.gface, N.n_gslot));
       N.gcap = N.n_gslot;
     }
+    k_face_slots<<<nblocks(6 * N.n_oct, BS), BS, 0, c->s>>>(N.son, 6 * N.n_oct, N.nbr, N.gface);
+    c->launches += 2;
   }
   // the deepest level has no sons
   AmrLevel& D = A->L[A->nlev - 1];

@@ -38,6 +38,7 @@ struct AmrLevel {
   // FP32 work arrays (mixed precision phase of the level solves)
   float *w32 = nullptr, *wE32 = nullptr, *wf32 = nullptr, *wold32 = nullptr;
   float* ghost32 = nullptr;           // [n_gslot*4] FP32 ghost u (e^u recomputed)
+  unsigned* gface = nullptr;          // [n_gslot] face 6 o + d of each ghost slot
   long long relaxed = 0;              // cells relaxed in the current level solve
   bool ghost_df = false;              // FP64 ghost slots hold double-float pairs (mixed form)
   bool wE_df = false;                 // wE holds e^u as double-float pairs after the solve

@@ -1200,23 +1200,23 @@ __global__ void k_init_level(long long ncell, const int* __restrict__ pcell,
 }
 
 // Ghost values on the faces of level-l octs that have no neighbouring oct
-// (Sec. 3.3), one thread per (oct, face).  The face's four outside cells are
+// (Sec. 3.3), one thread per ghost value: slot s = t / 4 (its face 6 o + d
+// from gface), qi = t % 4 the face cell.  The face's four outside cells are
 // daughters of one level-(l-1) cell P, the oct's parent shifted along the face
-// normal, so P and its six neighbours are looked up once per face.  A ghost is
-// P's value plus, per axis, s (c+ - c-)/8, s = +1 or -1 for the ghost's
-// high or low daughter position in P (a component is 0 where one of P's
-// neighbours does not exist).  Written as (u, e^u) in FP64 (double-float pairs
-// in the mixed form) and FP32 u.
-__global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restrict__ nbr,
+// normal; the four threads of a face look up P and its six neighbours (the
+// same addresses).  A ghost is P's value plus, per axis, s (c+ - c-)/8,
+// s = +1 or -1 for the ghost's high or low daughter position in P (a
+// component is 0 where one of P's neighbours does not exist).  Written as
+// (u, e^u) in FP64 (double-float pairs in the mixed form) and FP32 u.
+__global__ void k_ghosts(long long n_gslot, int l, TreeView T, const unsigned* __restrict__ gface,
                          const double* __restrict__ up, int linear, double* __restrict__ ghost,
                          double* __restrict__ ghostE, float* __restrict__ g32, int dfmode) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= 6 * n_oct) return;
-  const long long o = t / 6;
-  const int d = (int)(t - 6 * o);
-  const int nb = nbr[6 * o + d];
-  if (nb >= 0) return;
-  const long long slot = -(long long)nb - 1;
+  if (t >= 4 * n_gslot) return;
+  const unsigned f = gface[t >> 2];
+  const int qi = (int)(t & 3);
+  const unsigned o = f / 6u;
+  const int d = (int)(f - 6u * o);
   const int ax = d >> 1, plus = d & 1;
   const int t1 = ax == 0 ? 1 : 0;  // the first tangential axis
   const int4 p = T.opos[l][o];
@@ -1225,7 +1225,7 @@ __global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restri
   const long long P2 = p.z + (ax == 2 ? (plus ? 1 : -1) : 0);
   int lev;
   const long long pc = find_cell(T, l - 1, P0, P1, P2, &lev);
-  // P's value and, per axis, the indices of its two neighbours (-1: no gradient)
+  // per axis, the indices of P's two neighbours (-1: no gradient)
   long long cm[3] = {-1, -1, -1}, cp[3] = {-1, -1, -1};
   if (lev == l - 1 && linear) {
 #pragma unroll
@@ -1239,49 +1239,35 @@ __global__ void k_ghosts(long long n_oct, int l, TreeView T, const int* __restri
       }
     }
   }
-  // daughter bit of the ghost along each axis inside P: along the normal the
+  // daughter bit of the ghost along axis a inside P: along the normal the
   // side facing the oct, tangentially the oct cell's own bits (qi's two bits)
-  auto hbit = [&](int a, int qi) {
-    return a == ax ? 1 - plus : a == t1 ? (qi >> 1) & 1 : qi & 1;
-  };
+  auto hbit = [&](int a) { return a == ax ? 1 - plus : a == t1 ? (qi >> 1) & 1 : qi & 1; };
   if (dfmode) {
     // double-float slots (phase B of the mixed form): the parent's FP64
     // values converted on the integer pipes, the stencil and e^v on the FP32
     // pipes
-    dfl v0{0.f, 0.f}, g[3];
-    if (lev == l - 1) v0 = df_from_double_bits(up[pc]);
+    dfl V{0.f, 0.f};
+    if (lev == l - 1) V = df_from_double_bits(up[pc]);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-      g[a] = cp[a] >= 0 ? df_mul_f(df_sub(df_from_double_bits(up[cp[a]]),
-                                          df_from_double_bits(up[cm[a]])),
-                                   0.125f)
-                        : dfl{0.f, 0.f};
-    for (int qi = 0; qi < 4; ++qi) {
-      dfl V = v0;
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        if (cp[a] >= 0) V = df_add(V, hbit(a, qi) ? g[a] : df_neg(g[a]));
-      const long long q = 4 * slot + qi;
-      reinterpret_cast<dfl*>(ghost)[q] = V;
-      reinterpret_cast<dfl*>(ghostE)[q] = df_exp(V);
-      g32[q] = V.hi;
-    }
+      if (cp[a] >= 0) {
+        const dfl g = df_mul_f(df_sub(df_from_double_bits(up[cp[a]]),
+                                      df_from_double_bits(up[cm[a]])),
+                               hbit(a) ? 0.125f : -0.125f);
+        V = df_add(V, g);
+      }
+    reinterpret_cast<dfl*>(ghost)[t] = V;
+    reinterpret_cast<dfl*>(ghostE)[t] = df_exp(V);
+    g32[t] = V.hi;
     return;
   }
-  const double v0 = lev == l - 1 ? up[pc] : 0.0;
-  double g[3];
+  double v = lev == l - 1 ? up[pc] : 0.0;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) g[a] = cp[a] >= 0 ? up[cp[a]] - up[cm[a]] : 0.0;
-  for (int qi = 0; qi < 4; ++qi) {
-    double v = v0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      if (cp[a] >= 0) v += (hbit(a, qi) ? 0.125 : -0.125) * g[a];
-    const long long q = 4 * slot + qi;
-    ghost[q] = v;
-    ghostE[q] = exp(v);
-    g32[q] = (float)v;
-  }
+  for (int a = 0; a < 3; ++a)
+    if (cp[a] >= 0) v += (hbit(a) ? 0.125 : -0.125) * (up[cp[a]] - up[cm[a]]);
+  ghost[t] = v;
+  ghostE[t] = exp(v);
+  g32[t] = (float)v;
 }
 
 // FP64 cell array -> FP32 array of a level (no: its octs, 0 for dense)
@@ -1800,9 +1786,10 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
   // the mixed form keeps the FP64 ghost slots as double-float pairs until the
   // level is finished
   bool gh_df = mixed, w_df = false;
-  k_ghosts<<<nblocks(6 * F.n_oct, BS), BS, 0, c->s>>>(F.n_oct, Lv, T, F.nbr, up,
-                                                      g.prolong_linear, F.ghost, F.ghostE,
-                                                      F.ghost32, mixed ? 1 : 0);
+  if (F.n_gslot > 0)
+    k_ghosts<<<nblocks(4 * F.n_gslot, BS), BS, 0, c->s>>>(F.n_gslot, Lv, T, F.gface, up,
+                                                          g.prolong_linear, F.ghost, F.ghostE,
+                                                          F.ghost32, mixed ? 1 : 0);
   c->launches += 1;
   k_init_level<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.ncell, F.pcell, F.pnbr, up,
                                                       g.prolong_linear, F.w, F.wE,
@@ -1960,9 +1947,10 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
     }
     MG_CK(c, cudaMemcpyAsync(F.wf, F.f, sizeof(double) * (size_t)F.ncell,
                              cudaMemcpyDeviceToDevice, c->s));
-    k_ghosts<<<nblocks(6 * F.n_oct, BS), BS, 0, c->s>>>(F.n_oct, Lv, T, F.nbr, up,
-                                                        g.prolong_linear, F.ghost, F.ghostE,
-                                                        F.ghost32, 0);
+    if (F.n_gslot > 0)
+      k_ghosts<<<nblocks(4 * F.n_gslot, BS), BS, 0, c->s>>>(F.n_gslot, Lv, T, F.gface, up,
+                                                            g.prolong_linear, F.ghost, F.ghostE,
+                                                            F.ghost32, 0);
     c->launches += 1;
     gh_df = false;
     TRY(fp64_coarse());
