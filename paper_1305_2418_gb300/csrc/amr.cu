@@ -634,6 +634,7 @@ void amr_free(mgfr_ctx* c) {
   for (int l = 0; l < MGFR_MAX_DENSE; ++l) {
     if (A->dmask[l]) cudaFree(A->dmask[l]);
     if (A->dact[l]) cudaFree(A->dact[l]);
+    if (A->dlist[l]) cudaFree(A->dlist[l]);
   }
   if (A->blocksums) cudaFree(A->blocksums);
   if (A->d_small) cudaFree(A->d_small);
@@ -857,6 +858,10 @@ mgfr_status mgfr_solve_particles(mgfr_ctx* c, const double* pos, long long Np, i
         cudaFree(A->dact[k]);
         A->dact[k] = nullptr;
       }
+      if (A->dlist[k]) {
+        cudaFree(A->dlist[k]);
+        A->dlist[k] = nullptr;
+      }
     }
     if (A->acc0) cudaFree(A->acc0);
     if (A->fr0) cudaFree(A->fr0);
@@ -873,6 +878,8 @@ mgfr_status mgfr_solve_particles(mgfr_ctx* c, const double* pos, long long Np, i
     if (!A->dmask[k]) MG_CK(c, cudaMalloc(&A->dmask[k], sizeof(float) * (size_t)H.L[k].n));
     if (!A->dact[k]) MG_CK(c, cudaMalloc(&A->dact[k], (size_t)H.L[k].n));
   }
+  for (int k = 0; k < H.nlev; ++k)
+    if (!A->dlist[k]) MG_CK(c, cudaMalloc(&A->dlist[k], sizeof(int) * (size_t)H.L[k].n));
   if (!A->acc0) MG_CK(c, cudaMalloc(&A->acc0, sizeof(double) * 3 * (size_t)H.L[0].n));
   if (!A->fr0) MG_CK(c, cudaMalloc(&A->fr0, sizeof(double) * (size_t)H.L[0].n));
   if (mixed && !A->acc0_32)

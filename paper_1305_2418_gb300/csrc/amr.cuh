@@ -102,6 +102,10 @@ struct AmrWork {
   AmrLevel L[AMR_MAXL];
   float* dmask[MGFR_MAX_DENSE] = {};  // masks of the dense levels below the base
   unsigned char* dact[MGFR_MAX_DENSE] = {};  // their mask > threshold flags
+  // relaxed cells of the masked dense levels (index 0: the base, k >= 1: the
+  // dense levels below it), per colour: colour q at [q n/2, q n/2 + dlist_n[k][q])
+  int* dlist[MGFR_MAX_DENSE] = {};
+  long long dlist_n[MGFR_MAX_DENSE][2] = {};
   int* blocksums = nullptr;
   long long blocksums_cap = 0;
   long long* d_small = nullptr;       // device scalars (totals, error flags)

@@ -323,25 +323,50 @@ __device__ __forceinline__ void dnb_x(const float* __restrict__ x, int i, int j,
   out[5] = x[cidx(i, j, (k + 1) & M, lg)];
 }
 
+// masked Newton-Gauss-Seidel half-sweep of a dense level (the base or one below
+// it as a coarse grid of a refined-level solve), one thread per relaxed cell of
+// the colour, from a list of their C-order indices
 template <class T>
-__global__ void __launch_bounds__(BS) k_dsweep(T* __restrict__ u, T* __restrict__ E,
-                                               const T* __restrict__ f, int lg, int colour, MT<T> m,
-                                               T ih2, T cap, const unsigned char* __restrict__ act) {
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int N = 1 << lg, M = N - 1;
-  if (t >= (1u << (3 * lg - 1))) return;
-  const int k2 = (int)(t & ((N >> 1) - 1));
-  const unsigned r = t >> (lg - 1);
-  const int j = (int)(r & M), i = (int)(r >> lg);
-  const int k = 2 * k2 + ((i + j + colour) & 1);
-  const unsigned c = cidx(i, j, k, lg);
-  if (act && !(act[c])) return;
+__global__ void __launch_bounds__(BS) k_dsweep_list(T* __restrict__ u, T* __restrict__ E,
+                                                    const T* __restrict__ f, int lg,
+                                                    const int* __restrict__ list, long long n,
+                                                    MT<T> m, T ih2, T cap) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const unsigned c = (unsigned)list[t];
+  const int M = (1 << lg) - 1;
+  const int k = (int)(c & M), j = (int)((c >> lg) & M), i = (int)(c >> (2 * lg));
   NB<T> nb[6];
   dnb(u, E, i, j, k, lg, nb);
   const T uc = u[c];
   const T un = uc - newton(uc, Eat(E, u, c), nb, f[c], m, ih2, cap);
   u[c] = un;
   if constexpr (std::is_same<T, double>::value) E[c] = ex(un);
+}
+
+// the relaxed cells of one colour of a masked dense level -> list (in warp
+// order; a red-black half-sweep does not depend on the order), count += n
+__global__ void __launch_bounds__(BS) k_dense_list(const unsigned char* __restrict__ act, int lg,
+                                                   int colour, int* __restrict__ list,
+                                                   unsigned long long* __restrict__ count) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = 1 << lg, M = N - 1;
+  const bool live = t < (1u << (3 * lg - 1));
+  const unsigned tt = live ? t : 0;
+  const int k2 = (int)(tt & ((N >> 1) - 1));
+  const unsigned r = tt >> (lg - 1);
+  const int j = (int)(r & M), i = (int)(r >> lg);
+  const int k = 2 * k2 + ((i + j + colour) & 1);
+  const unsigned c = cidx(i, j, k, lg);
+  const bool on = live && act[c];
+  const unsigned ballot = __ballot_sync(0xffffffffu, on);  // whole warps reach here
+  if (ballot == 0u) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(ballot) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(ballot));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (on) list[base + __popc(ballot & ((1u << lane) - 1u))] = (int)c;
 }
 
 template <class T>
@@ -466,20 +491,19 @@ __device__ __forceinline__ JR jrow(float uc, float Ec, const NB<float>* nb, cons
   return J;
 }
 
-__global__ void __launch_bounds__(BS) k_dlin_sweep(float* __restrict__ e, const float* __restrict__ r,
-                                                   const float* __restrict__ u,
-                                                   const float* __restrict__ E, int lg, int colour,
-                                                   MT<float> m, float ih2,
-                                                   const unsigned char* __restrict__ act) {
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int N = 1 << lg, M = N - 1;
-  if (t >= (1u << (3 * lg - 1))) return;
-  const int k2 = (int)(t & ((N >> 1) - 1));
-  const unsigned rr = t >> (lg - 1);
-  const int j = (int)(rr & M), i = (int)(rr >> lg);
-  const int k = 2 * k2 + ((i + j + colour) & 1);
-  const unsigned c = cidx(i, j, k, lg);
-  if (act && !(act[c])) return;
+// masked Gauss-Seidel half-sweep on J(u) e = r of a dense level, one thread per
+// relaxed cell of the colour (list of C-order indices)
+__global__ void __launch_bounds__(BS) k_dlin_sweep_list(float* __restrict__ e,
+                                                        const float* __restrict__ r,
+                                                        const float* __restrict__ u,
+                                                        const float* __restrict__ E, int lg,
+                                                        const int* __restrict__ list,
+                                                        long long n, MT<float> m, float ih2) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const unsigned c = (unsigned)list[t];
+  const int M = (1 << lg) - 1;
+  const int k = (int)(c & M), j = (int)((c >> lg) & M), i = (int)(c >> (2 * lg));
   NB<float> nb[6];
   dnb(u, E, i, j, k, lg, nb);
   const JR J = jrow(u[c], Eat(E, u, c), nb, m, ih2);
@@ -1457,9 +1481,11 @@ void relax(SolveCtx& S, int l, int sweeps) {
         }
         if (l == S.L) prof_end(c);
       } else {
-        const int lg = L.lgN;
-        k_dsweep<T><<<nblocks(L.ncell / 2, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, lg, col, m,
-                                                              (T)L.ih2, (T)g.step_cap, L.act);
+        const long long nl = S.A->dlist_n[0][col];
+        if (nl == 0) continue;
+        k_dsweep_list<T><<<nblocks(nl, BS), BS, 0, c->s>>>(
+            a.w, a.wE, a.wf, L.lgN, S.A->dlist[0] + col * (L.ncell / 2), nl, m, (T)L.ih2,
+            (T)g.step_cap);
       }
       c->launches += 1;
     }
@@ -1481,12 +1507,18 @@ void vcycle_dense(SolveCtx& S, int k) {
     c->launches += 1;
     return;
   }
-  for (int s = 0; s < sweeps_of(S, -1, g.n_pre); ++s)
-    for (int col = 0; col < 2; ++col) {
-      k_dsweep<T><<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lg, col, m, (T)F.ih2,
-                                                         (T)g.step_cap, mk);
-      c->launches += 1;
-    }
+  auto sweep = [&](int sweeps) {
+    for (int s = 0; s < sweeps; ++s)
+      for (int col = 0; col < 2; ++col) {
+        const long long nl = S.A->dlist_n[k][col];
+        if (nl == 0) continue;
+        k_dsweep_list<T><<<nblocks(nl, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lg,
+                                                            S.A->dlist[k] + col * (F.n / 2), nl,
+                                                            m, (T)F.ih2, (T)g.step_cap);
+        c->launches += 1;
+      }
+  };
+  sweep(sweeps_of(S, -1, g.n_pre));
   if (k + 1 <= S.kmax) {
     DenseLevel& C = H.L[k + 1];
     TA<T> b = darr<T>(C);
@@ -1500,12 +1532,7 @@ void vcycle_dense(SolveCtx& S, int k) {
                                                      g.prolong_linear, mk);
     c->launches += 1;
   }
-  for (int s = 0; s < sweeps_of(S, -1, g.n_post); ++s)
-    for (int col = 0; col < 2; ++col) {
-      k_dsweep<T><<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lg, col, m, (T)F.ih2,
-                                                         (T)g.step_cap, mk);
-      c->launches += 1;
-    }
+  sweep(sweeps_of(S, -1, g.n_post));
 }
 
 // masked FAS V-cycle of the level-S.L solve at tree level l >= 0
@@ -1614,6 +1641,22 @@ mgfr_status count_relaxed(mgfr_ctx* c, AmrWork* A, const float* mask, long long 
 }
 
 
+// per-colour lists of the relaxed cells of masked dense level k (0: the base)
+mgfr_status build_dense_lists(mgfr_ctx* c, AmrWork* A, int k, const unsigned char* act, int lg) {
+  const long long half = 1LL << (3 * lg - 1);
+  MG_CK(c, cudaMemsetAsync(A->d_small + 4, 0, 2 * sizeof(long long), c->s));
+  for (int q = 0; q < 2; ++q)
+    k_dense_list<<<nblocks(half, BS), BS, 0, c->s>>>(act, lg, q, A->dlist[k] + q * half,
+                                                     (unsigned long long*)(A->d_small + 4 + q));
+  c->launches += 2;
+  long long n[2] = {0, 0};
+  MG_CK(c, cudaMemcpyAsync(n, A->d_small + 4, 2 * sizeof(long long), cudaMemcpyDeviceToHost, c->s));
+  MG_CK(c, cudaStreamSynchronize(c->s));
+  A->dlist_n[k][0] = n[0];
+  A->dlist_n[k][1] = n[1];
+  return MGFR_OK;
+}
+
 // active-oct list of coarse tree level P (octs with a relaxed cell) -> P.olist
 mgfr_status build_oct_list(mgfr_ctx* c, AmrWork* A, AmrLevel& P, float mthr) {
   MG_CK(c, cudaMemsetAsync(A->d_small + 3, 0, sizeof(long long), c->s));
@@ -1650,10 +1693,13 @@ void lin_relax(SolveCtx& S, int l, int sweeps) {
               L.w32, L.wold32, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, L.n_oct, m,
               (float)L.ih2, 0.f);
         if (l == S.L) prof_end(c);
-      } else
-        k_dlin_sweep<<<nblocks(L.ncell / 2, BS), BS, 0, c->s>>>(L.wold32, L.wf32, L.w32, L.wE32,
-                                                               L.lgN, col, m, (float)L.ih2,
-                                                               L.act);
+      } else {
+        const long long nl = S.A->dlist_n[0][col];
+        if (nl == 0) continue;
+        k_dlin_sweep_list<<<nblocks(nl, BS), BS, 0, c->s>>>(
+            L.wold32, L.wf32, L.w32, L.wE32, L.lgN, S.A->dlist[0] + col * (L.ncell / 2), nl, m,
+            (float)L.ih2);
+      }
       c->launches += 1;
     }
   }
@@ -1671,12 +1717,18 @@ void lin_vcycle_dense(SolveCtx& S, int k) {
     c->launches += 1;
     return;
   }
-  for (int s = 0; s < sweeps_of(S, -1, g.n_pre); ++s)
-    for (int col = 0; col < 2; ++col) {
-      k_dlin_sweep<<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, F.lg, col,
-                                                         m, (float)F.ih2, mk);
-      c->launches += 1;
-    }
+  auto sweep = [&](int sweeps) {
+    for (int s = 0; s < sweeps; ++s)
+      for (int col = 0; col < 2; ++col) {
+        const long long nl = S.A->dlist_n[k][col];
+        if (nl == 0) continue;
+        k_dlin_sweep_list<<<nblocks(nl, BS), BS, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, F.lg,
+                                                            S.A->dlist[k] + col * (F.n / 2), nl,
+                                                            m, (float)F.ih2);
+        c->launches += 1;
+      }
+  };
+  sweep(sweeps_of(S, -1, g.n_pre));
   if (k + 1 <= S.kmax) {
     DenseLevel& C = H.L[k + 1];
     k_dlin_restrict<<<nblocks(C.n, BS), BS, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, F.lg,
@@ -1688,12 +1740,7 @@ void lin_vcycle_dense(SolveCtx& S, int k) {
                                                       mk);
     c->launches += 1;
   }
-  for (int s = 0; s < sweeps_of(S, -1, g.n_post); ++s)
-    for (int col = 0; col < 2; ++col) {
-      k_dlin_sweep<<<nblocks(F.n / 2, BS), BS, 0, c->s>>>(F.uold32, F.r32, F.u32, F.e32, F.lg, col,
-                                                         m, (float)F.ih2, mk);
-      c->launches += 1;
-    }
+  sweep(sweeps_of(S, -1, g.n_post));
 }
 
 void lin_vcycle_tree(SolveCtx& S, int l) {
@@ -1857,8 +1904,10 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
       kmax = k;
       k_act<<<nblocks(H.L[k].n, BS), BS, 0, c->s>>>(A->dmask[k], H.L[k].n, mthr, A->dact[k]);
       c->launches += 1;
+      if (H.L[k].N > 4) TRY(build_dense_lists(c, A, k, A->dact[k], H.L[k].lg));
     }
   }
+  TRY(build_dense_lists(c, A, 0, A->L[0].act, A->L[0].lgN));
   SolveCtx S{c, A, m, Lv, mthr, 0, kmax};
   if (g.profile) prof_reserve_public(c, 64);
   double hs[3];
