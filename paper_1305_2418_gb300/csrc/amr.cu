@@ -185,25 +185,33 @@ __global__ void __launch_bounds__(SCAN_BS) k_scan_scatter(const unsigned char* _
                                                           long long n, int mlg,
                                                           const int* __restrict__ offs,
                                                           int* __restrict__ son) {
-  __shared__ int buf[SCAN_BS];
+  // rank of a set flag = set flags before it in its warp (ballot) + in the
+  // warps before (a scan of the 32 warp counts)
+  __shared__ int wsum[SCAN_BS / 32];
   const long long base = (long long)blockIdx.x * SCAN_TILE;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int run = offs[blockIdx.x];
   for (int q = 0; q < SCAN_ITEMS; ++q) {
     const long long i = base + (long long)q * SCAN_BS + threadIdx.x;
     const long long c = i < n ? scan_cell(i, mlg) : 0;
-    const int v = (i < n && flags[c]) ? 1 : 0;
-    buf[threadIdx.x] = v;
+    const bool v = i < n && flags[c];
+    const unsigned ballot = __ballot_sync(0xffffffffu, v);
+    if (lane == 0) wsum[w] = __popc(ballot);
     __syncthreads();
-    for (int off = 1; off < SCAN_BS; off <<= 1) {
-      const int add = threadIdx.x >= (unsigned)off ? buf[threadIdx.x - off] : 0;
-      __syncthreads();
-      buf[threadIdx.x] += add;
-      __syncthreads();
+    if (w == 0) {
+      int x = wsum[lane];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+      }
+      wsum[lane] = x;  // inclusive
     }
-    if (i < n) son[c] = v ? run + buf[threadIdx.x] - 1 : -1;
-    const int tot = buf[SCAN_BS - 1];
     __syncthreads();
-    run += tot;
+    const int before = (w > 0 ? wsum[w - 1] : 0) + __popc(ballot & ((1u << lane) - 1u));
+    if (i < n) son[c] = v ? run + before : -1;
+    run += wsum[SCAN_BS / 32 - 1];
+    __syncthreads();
   }
 }
 

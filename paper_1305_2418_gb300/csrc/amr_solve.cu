@@ -397,14 +397,40 @@ __global__ void __launch_bounds__(BS) k_drestrict(const T* __restrict__ u, const
   fc[t] = (T)0.125 * sr;
 }
 
+// The relaxed cells of a masked dense level as the two per-colour lists
+// (colour q at p + q half, n[q] entries); p == nullptr: none built (the
+// kernels then visit every cell and test the relax flags).
+struct CList {
+  const int* p;
+  long long half, n0, n1;
+};
+
+// cell of thread tid: from the lists, else tid itself if its flag is set
+__device__ __forceinline__ bool dcell(const CList& L, const unsigned char* __restrict__ act,
+                                      int lg, long long tid, unsigned* c) {
+  if (L.p) {
+    if (tid < L.n0) {
+      *c = (unsigned)L.p[tid];
+      return true;
+    }
+    tid -= L.n0;
+    if (tid >= L.n1) return false;
+    *c = (unsigned)L.p[L.half + tid];
+    return true;
+  }
+  if (tid >= (1LL << (3 * lg))) return false;
+  if (act && !act[tid]) return false;
+  *c = (unsigned)tid;
+  return true;
+}
+
 template <class T>
 __global__ void __launch_bounds__(BS) k_dfas(const T* __restrict__ u, const T* __restrict__ E,
                                              T* __restrict__ f, int lg, MT<T> m, T ih2,
-                                             const unsigned char* __restrict__ act) {
+                                             const unsigned char* __restrict__ act, CList cl) {
   const int N = 1 << lg;
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (1u << (3 * lg))) return;
-  if (act && !(act[t])) return;
+  unsigned t;
+  if (!dcell(cl, act, lg, blockIdx.x * (long long)blockDim.x + threadIdx.x, &t)) return;
   const int k = (int)(t & (N - 1)), j = (int)((t >> lg) & (N - 1)), i = (int)(t >> (2 * lg));
   NB<T> nb[6];
   dnb(u, E, i, j, k, lg, nb);
@@ -414,11 +440,11 @@ __global__ void __launch_bounds__(BS) k_dfas(const T* __restrict__ u, const T* _
 template <class T>
 __global__ void __launch_bounds__(BS) k_dprolong(T* __restrict__ u, T* __restrict__ E,
                                                  const T* __restrict__ uc, const T* __restrict__ ucold,
-                                                 int lgf, int linear, const unsigned char* __restrict__ act) {
+                                                 int lgf, int linear, const unsigned char* __restrict__ act,
+                                                 CList cl) {
   const int N = 1 << lgf, lgc = lgf - 1, Mc = (N >> 1) - 1;
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (1u << (3 * lgf))) return;
-  if (act && !(act[t])) return;
+  unsigned t;
+  if (!dcell(cl, act, lgf, blockIdx.x * (long long)blockDim.x + threadIdx.x, &t)) return;
   const int k = (int)(t & (N - 1)), j = (int)((t >> lgf) & (N - 1)), i = (int)(t >> (2 * lgf));
   const int I = i >> 1, J = j >> 1, K = k >> 1;
   auto corr = [&](int a, int b, int c) {
@@ -552,11 +578,11 @@ __global__ void __launch_bounds__(BS) k_dlin_restrict(const float* __restrict__ 
 
 __global__ void __launch_bounds__(BS) k_dlin_prolong(float* __restrict__ e, const float* __restrict__ ec,
                                                      int lgf, int linear,
-                                                     const unsigned char* __restrict__ act) {
+                                                     const unsigned char* __restrict__ act,
+                                                     CList cl) {
   const int N = 1 << lgf, lgc = lgf - 1, Mc = (N >> 1) - 1;
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (1u << (3 * lgf))) return;
-  if (act && !(act[t])) return;
+  unsigned t;
+  if (!dcell(cl, act, lgf, blockIdx.x * (long long)blockDim.x + threadIdx.x, &t)) return;
   const int k = (int)(t & (N - 1)), j = (int)((t >> lgf) & (N - 1)), i = (int)(t >> (2 * lgf));
   const int I = i >> 1, J = j >> 1, K = k >> 1;
   auto cv = [&](int a, int b, int c) { return ec[cidx(a & Mc, b & Mc, c & Mc, lgc)]; };
@@ -1301,6 +1327,18 @@ __global__ void k_d2f(const double* __restrict__ x, float* __restrict__ y, long 
   if (i < n) y[pidx(i, no)] = f_from_double_bits(x[i]);
 }
 
+// the same into two arrays
+__global__ void k_d2f2(const double* __restrict__ x, float* __restrict__ y, float* __restrict__ z,
+                       long long n, long long no) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float v = f_from_double_bits(x[i]);
+    const long long q = pidx(i, no);
+    y[q] = v;
+    z[q] = v;
+  }
+}
+
 // FP64 iterate from the FP32 one: w = w32, wE = e^w
 __global__ void k_f2d_exp(const float* __restrict__ w32, long long no, double* __restrict__ w,
                           double* __restrict__ wE, long long n) {
@@ -1442,6 +1480,16 @@ struct ORange {
   long long n;
 };
 
+// the relaxed-cell lists of dense level k (0: the base) where this solve
+// built them
+CList clist(const SolveCtx& S, int k) {
+  const DenseHier& H = S.c->dh;
+  if (!(k == 0 || (k <= S.kmax && H.L[k].N > 4))) return CList{nullptr, 0, 0, 0};
+  return CList{S.A->dlist[k], H.L[k].n / 2, S.A->dlist_n[k][0], S.A->dlist_n[k][1]};
+}
+// threads of a launch over dense level cells: the listed ones, else all n
+long long cl_threads(const CList& L, long long n) { return L.p ? L.n0 + L.n1 : n; }
+
 // red-black sweeps on tree level l (l < S.L, or k >= 1 dense: a coarse grid)
 int sweeps_of(const SolveCtx& S, int l, int n) {
   const int nc = S.c->cfg.n_coarse;
@@ -1524,12 +1572,16 @@ void vcycle_dense(SolveCtx& S, int k) {
     TA<T> b = darr<T>(C);
     k_drestrict<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lg, b.w, b.wE, b.wold,
                                                       b.wf, m, (T)F.ih2, mk);
-    k_dfas<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, C.lg, m, (T)C.ih2,
-                                                 S.A->dact[k + 1]);
+    const CList cc = clist(S, k + 1);
+    if (cl_threads(cc, C.n) > 0)
+      k_dfas<T><<<nblocks(cl_threads(cc, C.n), BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, C.lg, m,
+                                                                     (T)C.ih2, S.A->dact[k + 1], cc);
     c->launches += 2;
     vcycle_dense<T>(S, k + 1);
-    k_dprolong<T><<<nblocks(F.n, BS), BS, 0, c->s>>>(a.w, a.wE, b.w, b.wold, F.lg,
-                                                     g.prolong_linear, mk);
+    const CList cf = clist(S, k);
+    if (cl_threads(cf, F.n) > 0)
+      k_dprolong<T><<<nblocks(cl_threads(cf, F.n), BS), BS, 0, c->s>>>(
+          a.w, a.wE, b.w, b.wold, F.lg, g.prolong_linear, mk, cf);
     c->launches += 1;
   }
   sweep(sweeps_of(S, -1, g.n_post));
@@ -1573,8 +1625,10 @@ void vcycle_tree(SolveCtx& S, int l) {
                                                                 P.olist, m, (T)P.ih2);
       }
     } else {
-      k_dfas<T><<<nblocks(P.ncell, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, P.lgN, m, (T)P.ih2,
-                                                       P.act);
+      const CList c0 = clist(S, 0);
+      if (cl_threads(c0, P.ncell) > 0)
+        k_dfas<T><<<nblocks(cl_threads(c0, P.ncell), BS), BS, 0, c->s>>>(
+            b.w, b.wE, b.wf, P.lgN, m, (T)P.ih2, P.act, c0);
     }
     c->launches += 2;
     vcycle_tree<T>(S, l - 1);
@@ -1595,11 +1649,15 @@ void vcycle_tree(SolveCtx& S, int l) {
     TA<T> b = darr<T>(C);
     k_drestrict<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(a.w, a.wE, a.wf, F.lgN, b.w, b.wE, b.wold,
                                                       b.wf, m, (T)F.ih2, F.act);
-    k_dfas<T><<<nblocks(C.n, BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, C.lg, m, (T)C.ih2, A->dact[1]);
+    const CList c1 = clist(S, 1), c0 = clist(S, 0);
+    if (cl_threads(c1, C.n) > 0)
+      k_dfas<T><<<nblocks(cl_threads(c1, C.n), BS), BS, 0, c->s>>>(b.w, b.wE, b.wf, C.lg, m,
+                                                                     (T)C.ih2, A->dact[1], c1);
     c->launches += 2;
     vcycle_dense<T>(S, 1);
-    k_dprolong<T><<<nblocks(F.ncell, BS), BS, 0, c->s>>>(a.w, a.wE, b.w, b.wold, F.lgN,
-                                                         g.prolong_linear, F.act);
+    if (cl_threads(c0, F.ncell) > 0)
+      k_dprolong<T><<<nblocks(cl_threads(c0, F.ncell), BS), BS, 0, c->s>>>(
+          a.w, a.wE, b.w, b.wold, F.lgN, g.prolong_linear, F.act, c0);
     c->launches += 1;
   }
   relax<T>(S, l, sweeps_of(S, l, g.n_post));
@@ -1736,8 +1794,10 @@ void lin_vcycle_dense(SolveCtx& S, int k) {
                                                        (float)F.ih2, mk);
     c->launches += 1;
     lin_vcycle_dense(S, k + 1);
-    k_dlin_prolong<<<nblocks(F.n, BS), BS, 0, c->s>>>(F.uold32, C.uold32, F.lg, g.prolong_linear,
-                                                      mk);
+    const CList cf = clist(S, k);
+    if (cl_threads(cf, F.n) > 0)
+      k_dlin_prolong<<<nblocks(cl_threads(cf, F.n), BS), BS, 0, c->s>>>(
+          F.uold32, C.uold32, F.lg, g.prolong_linear, mk, cf);
     c->launches += 1;
   }
   sweep(sweeps_of(S, -1, g.n_post));
@@ -1776,8 +1836,10 @@ void lin_vcycle_tree(SolveCtx& S, int l) {
                                                        (float)F.ih2, F.act);
     c->launches += 1;
     lin_vcycle_dense(S, 1);
-    k_dlin_prolong<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.wold32, C.uold32, F.lgN,
-                                                          g.prolong_linear, F.act);
+    const CList c0 = clist(S, 0);
+    if (cl_threads(c0, F.ncell) > 0)
+      k_dlin_prolong<<<nblocks(cl_threads(c0, F.ncell), BS), BS, 0, c->s>>>(
+          F.wold32, C.uold32, F.lgN, g.prolong_linear, F.act, c0);
     c->launches += 1;
   }
   lin_relax(S, l, npost);
@@ -1875,9 +1937,8 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
     const double* uu = l == 0 ? H.L[0].u : P.u;
     if (mixed) {
       const long long pno = l >= 1 ? P.n_oct : 0;  // FP32 layout (0: dense)
-      k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(uu, P.w32, P.ncell, pno);
-      k_d2f<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(uu, P.wold32, P.ncell, pno);
-      c->launches += 2;
+      k_d2f2<<<nblocks(P.ncell, BS), BS, 0, c->s>>>(uu, P.w32, P.wold32, P.ncell, pno);
+      c->launches += 1;
     }
     MG_CK(c, cudaMemsetAsync(P.mask, 0, sizeof(float) * (size_t)P.ncell, c->s));
     AmrLevel& Ch = A->L[l + 1];
