@@ -33,59 +33,59 @@ __host__ __device__ inline ModelF to_f(const Model& m) {
   return ModelF{(float)m.aRt, (float)m.aRt_np1, (float)m.inv_np1};
 }
 
-// Loads the float pair (k0 = 2kp, k1 = 2kp+1) of row (i,j) and the two
-// z-neighbours outside the pair (k0-1 and k1+1), using warp shuffles inside a
-// row and direct loads at warp and row edges (periodic in k).
-struct Pair {
-  float2 c;
-  float km, kp;  // u[k0-1], u[k1+1]
-};
-
-__device__ __forceinline__ Pair load_pair(const float* __restrict__ u, unsigned rowbase, int kp,
-                                          int np, int lane) {
-  const float2* u2 = reinterpret_cast<const float2*>(u + rowbase);
-  Pair p;
-  p.c = u2[kp];
-  float up = __shfl_up_sync(0xffffffffu, p.c.y, 1);
-  float dn = __shfl_down_sync(0xffffffffu, p.c.x, 1);
-  const int N = 2 * np;
-  p.km = (kp == 0 || lane == 0) ? u[rowbase + ((2 * kp - 1 + N) & (N - 1))] : up;
-  p.kp = (kp == np - 1 || lane == 31) ? u[rowbase + ((2 * kp + 2) & (N - 1))] : dn;
-  return p;
+// ---- colour-split storage of the FP32 arrays ----------------------------------
+// Every FP32 array of a dense level (u, f, u_old, e, r) is stored by colour:
+// plane q = (i + j + k) & 1 holds the cells of that red-black colour, in C
+// order of (i, j, k >> 1).  The six neighbours of a cell all lie in the other
+// plane, four of them at the same (k >> 1) in neighbouring rows and two in
+// the same row (at k >> 1 and one step along it).  A half-sweep then reads
+// one plane, reads and writes the other, each in whole coalesced rows.
+__device__ __forceinline__ unsigned prow(int i, int j, int lg) {
+  return (((unsigned)i << lg) + (unsigned)j) << (lg - 1);
+}
+// colour-split index of (i, j, k), each in [0, N)
+__device__ __forceinline__ unsigned pdx(int i, int j, int k, int lg) {
+  return ((unsigned)((i + j + k) & 1) << (3 * lg - 1)) + prow(i, j, lg) + ((unsigned)k >> 1);
+}
+// cell of colour-split index t
+__device__ __forceinline__ void pcell(unsigned t, int lg, int* i, int* j, int* k) {
+  const int M = (1 << lg) - 1;
+  const unsigned q = t >> (3 * lg - 1);
+  const unsigned p = t & ((1u << (3 * lg - 1)) - 1u);
+  *i = (int)(p >> (2 * lg - 1));
+  *j = (int)((p >> (lg - 1)) & M);
+  *k = 2 * (int)(p & (M >> 1)) + (int)((q + *i + *j) & 1);
+}
+// colour-split indices of the six neighbours (-x, +x, -y, +y, -z, +z)
+__device__ __forceinline__ void pnb6(int i, int j, int k, int lg, unsigned* q) {
+  const int M = (1 << lg) - 1, hm = M >> 1;
+  const unsigned ob = (unsigned)((i + j + k + 1) & 1) << (3 * lg - 1);
+  const int kh = k >> 1;
+  q[0] = ob + prow((i - 1) & M, j, lg) + kh;
+  q[1] = ob + prow((i + 1) & M, j, lg) + kh;
+  q[2] = ob + prow(i, (j - 1) & M, lg) + kh;
+  q[3] = ob + prow(i, (j + 1) & M, lg) + kh;
+  const unsigned r = ob + prow(i, j, lg);
+  q[4] = r + ((k & 1) ? kh : ((kh - 1) & hm));
+  q[5] = r + ((k & 1) ? ((kh + 1) & hm) : kh);
 }
 
 // ---- Phase A: nonlinear FP32 Newton-Gauss-Seidel half-sweep ----------------
-// Thread = one z-pair (2kp, 2kp+1) of one (i,j) row; it updates the pair's
-// cell of the active colour and writes the whole pair back (full sectors).
+// Thread = one cell of the active colour (plane `colour`, index t in it).
 __global__ void __launch_bounds__(BS) k_sweep32(float* __restrict__ u, const float* __restrict__ f,
                                                 int lg, int colour, ModelF m, float ih2,
                                                 float cap) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int N = 1 << lg, M = N - 1, np = N >> 1;
-  const bool live = t < (1u << (3 * lg - 1));
-  const unsigned tt = live ? t : 0;
-  const int kp = (int)(tt & (np - 1));
-  const unsigned rr = tt >> (lg - 1);
-  const int j = (int)(rr & M), i = (int)(rr >> lg);
-  const unsigned row = cidx(i, j, 0, lg);
-  const int lane = threadIdx.x & 31;
-  Pair p = load_pair(u, row, kp, np, lane);
-  if (!live) return;
-  const int odd = (i + j + colour) & 1;  // active cell is k0 + odd
-  const float2* u2 = reinterpret_cast<const float2*>(u);
-  const unsigned q = row / 2 + kp;
-  const float2 a = u2[cidx((i - 1) & M, j, 0, lg) / 2 + kp];
-  const float2 b = u2[cidx((i + 1) & M, j, 0, lg) / 2 + kp];
-  const float2 c = u2[cidx(i, (j - 1) & M, 0, lg) / 2 + kp];
-  const float2 d = u2[cidx(i, (j + 1) & M, 0, lg) / 2 + kp];
-  float uc, nb[6];
-  if (odd) {
-    uc = p.c.y;
-    nb[0] = a.y; nb[1] = b.y; nb[2] = c.y; nb[3] = d.y; nb[4] = p.c.x; nb[5] = p.kp;
-  } else {
-    uc = p.c.x;
-    nb[0] = a.x; nb[1] = b.x; nb[2] = c.x; nb[3] = d.x; nb[4] = p.km; nb[5] = p.c.y;
-  }
+  if (t >= (1u << (3 * lg - 1))) return;
+  const unsigned c = ((unsigned)colour << (3 * lg - 1)) + t;
+  int i, j, k;
+  pcell(c, lg, &i, &j, &k);
+  unsigned q[6];
+  pnb6(i, j, k, lg, q);
+  float nb[6];
+#pragma unroll
+  for (int e = 0; e < 6; ++e) nb[e] = u[q[e]];
+  const float uc = u[c];
   const float Ec = __expf(uc);
   float sbd = 0.f, sd = 0.f, sb = 0.f;
 #pragma unroll
@@ -98,23 +98,22 @@ __global__ void __launch_bounds__(BS) k_sweep32(float* __restrict__ u, const flo
   const float s = __expf(-uc * m.inv_np1);
   const float L = sbd * ih2 + m.aRt * (1.f - s);
   const float dL = (0.5f * Ec * sd - sb) * ih2 + m.aRt_np1 * s;
-  float step = __fdividef(L - f[row + 2 * kp + odd], dL);
+  float step = __fdividef(L - f[c], dL);
   step = fminf(fmaxf(step, -cap), cap);
-  float2 out = p.c;
-  if (odd) out.y = uc - step; else out.x = uc - step;
-  reinterpret_cast<float2*>(u)[q] = out;
+  u[c] = uc - step;
 }
 
 __device__ __forceinline__ float Lpoint32(const float* __restrict__ u, int i, int j, int k, int lg,
                                           const ModelF& m, float ih2) {
-  const int M = (1 << lg) - 1;
-  const float uc = u[cidx(i, j, k, lg)], Ec = __expf(uc);
-  const float nb[6] = {u[cidx((i - 1) & M, j, k, lg)], u[cidx((i + 1) & M, j, k, lg)],
-                       u[cidx(i, (j - 1) & M, k, lg)], u[cidx(i, (j + 1) & M, k, lg)],
-                       u[cidx(i, j, (k - 1) & M, lg)], u[cidx(i, j, (k + 1) & M, lg)]};
+  unsigned q[6];
+  pnb6(i, j, k, lg, q);
+  const float uc = u[pdx(i, j, k, lg)], Ec = __expf(uc);
   float sbd = 0.f;
 #pragma unroll
-  for (int e = 0; e < 6; ++e) sbd = fmaf(0.5f * (__expf(nb[e]) + Ec), nb[e] - uc, sbd);
+  for (int e = 0; e < 6; ++e) {
+    const float un = u[q[e]];
+    sbd = fmaf(0.5f * (__expf(un) + Ec), un - uc, sbd);
+  }
   return sbd * ih2 + m.aRt * (1.f - __expf(-uc * m.inv_np1));
 }
 
@@ -146,15 +145,16 @@ __global__ void __launch_bounds__(BS) k_restrict32(const float* __restrict__ u,
                                                    const float* __restrict__ f, int lgf,
                                                    float* __restrict__ uc, float* __restrict__ ucold,
                                                    float* __restrict__ fc, ModelF m, float ih2) {
-  const int lgc = lgf - 1, Nc = 1 << lgc;
+  const int lgc = lgf - 1;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (1u << (3 * lgc))) return;
-  const int K = (int)(t & (Nc - 1)), J = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
+  int I, J, K;
+  pcell(t, lgc, &I, &J, &K);
   float su = 0.f, sr = 0.f;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int i = 2 * I + (q >> 2), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q & 1);
-    const unsigned c = cidx(i, j, k, lgf);
+    const unsigned c = pdx(i, j, k, lgf);
     su += u[c];
     sr += f[c] - Lpoint32(u, i, j, k, lgf, m, ih2);
   }
@@ -165,10 +165,10 @@ __global__ void __launch_bounds__(BS) k_restrict32(const float* __restrict__ u,
 
 __global__ void __launch_bounds__(BS) k_fas_rhs32(const float* __restrict__ u, float* __restrict__ f,
                                                   int lg, ModelF m, float ih2) {
-  const int N = 1 << lg;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (1u << (3 * lg))) return;
-  const int k = (int)(t & (N - 1)), j = (int)((t >> lg) & (N - 1)), i = (int)(t >> (2 * lg));
+  int i, j, k;
+  pcell(t, lg, &i, &j, &k);
   f[t] += Lpoint32(u, i, j, k, lg, m, ih2);
 }
 
@@ -180,10 +180,11 @@ __global__ void __launch_bounds__(BS) k_prolong32(float* __restrict__ u, const f
   const int N = 1 << lgf, lgc = lgf - 1, Mc = (N >> 1) - 1;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (1u << (3 * lgf))) return;
-  const int k = (int)(t & (N - 1)), j = (int)((t >> lgf) & (N - 1)), i = (int)(t >> (2 * lgf));
+  int i, j, k;
+  pcell(t, lgf, &i, &j, &k);
   const int I = i >> 1, J = j >> 1, K = k >> 1;
   auto corr = [&](int a, int b, int c) {
-    const unsigned q = cidx(a & Mc, b & Mc, c & Mc, lgc);
+    const unsigned q = pdx(a & Mc, b & Mc, c & Mc, lgc);
     return ucold ? uc[q] - ucold[q] : uc[q];
   };
   float v = corr(I, J, K);
@@ -199,11 +200,12 @@ __global__ void __launch_bounds__(BS) k_prolong32(float* __restrict__ u, const f
 
 __global__ void __launch_bounds__(64) k_coarse32(float* __restrict__ ug, const float* __restrict__ fg,
                                                  ModelF m, float ih2, float cap, int sweeps) {
-  __shared__ float u[64];
+  __shared__ float u[64];  // C order in shared memory
   const int t = threadIdx.x;
-  u[t] = ug[t];
-  const float fc = fg[t];
   const int i = t >> 4, j = (t >> 2) & 3, k = t & 3, colour = (i + j + k) & 1;
+  const unsigned g = pdx(i, j, k, 2);
+  u[t] = ug[g];
+  const float fc = fg[g];
   const int nb[6] = {(((i + 3) & 3) << 4) | (j << 2) | k, (((i + 1) & 3) << 4) | (j << 2) | k,
                      (i << 4) | (((j + 3) & 3) << 2) | k, (i << 4) | (((j + 1) & 3) << 2) | k,
                      (i << 4) | (j << 2) | ((k + 3) & 3), (i << 4) | (j << 2) | ((k + 1) & 3)};
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(64) k_coarse32(float* __restrict__ ug, const f
       }
       __syncthreads();
     }
-  ug[t] = u[t];
+  ug[g] = u[t];
 }
 
 // FP32 residual norm on the finest level (phase A stopping test).
@@ -236,10 +238,10 @@ __global__ void __launch_bounds__(BS) k_norm32(const float* __restrict__ u, cons
                                                int lg, long long n, ModelF m, float ih2,
                                                double* __restrict__ partials) {
   double ss = 0.0, mx = 0.0;
-  const int N = 1 << lg;
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += gridDim.x * blockDim.x) {
-    const int k = (int)(t & (N - 1)), j = (int)((t >> lg) & (N - 1)), i = (int)(t >> (2 * lg));
+    int i, j, k;
+    pcell(t, lg, &i, &j, &k);
     const double r = (double)(f[t] - Lpoint32(u, i, j, k, lg, m, ih2));
     ss = fma(r, r, ss);
     mx = fmax(mx, fabs(r));
@@ -247,17 +249,21 @@ __global__ void __launch_bounds__(BS) k_norm32(const float* __restrict__ u, cons
   block_partial(ss, mx, partials);
 }
 
-__global__ void k_from64(const double* __restrict__ x, float* __restrict__ y, long long n) {
+// C-order FP64 -> colour-split FP32
+__global__ void k_from64(const double* __restrict__ x, float* __restrict__ y, int lg) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) y[t] = f_from_double_bits(x[t]);
+  if (t >= (1u << (3 * lg))) return;
+  const int M = (1 << lg) - 1;
+  y[pdx((int)(t >> (2 * lg)), (int)((t >> lg) & M), (int)(t & M), lg)] = f_from_double_bits(x[t]);
 }
 
 // FP32 iterate -> double-float iterate and its e^u (start of phase B)
 __global__ void k_to_df(const float* __restrict__ u32, dfl* __restrict__ u, dfl* __restrict__ E,
-                        long long n) {
+                        int lg) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const dfl v{u32[t], 0.f};
+  if (t >= (1u << (3 * lg))) return;
+  const int M = (1 << lg) - 1;
+  const dfl v{u32[pdx((int)(t >> (2 * lg)), (int)((t >> lg) & M), (int)(t & M), lg)], 0.f};
   u[t] = v;
   E[t] = df_exp(v);
 }
@@ -295,9 +301,10 @@ __global__ void __launch_bounds__(BS) k_resid_df(const dfl* __restrict__ u,
     const dfl sN = m.n == 1 ? df_rsqrt(Ec) : df_exp(df_neg(df_mul(uc, m.inv_np1)));
     const dfl L = df_add(df_mul(acc, m.ih2h), df_mul(m.aRt, df_add_f(df_neg(sN), 1.f)));
     const dfl r = df_sub(f[t], L);
-    r32[t] = r.hi;
-    u32[t] = uc.hi;
-    e32[t] = 0.f;
+    const unsigned p = pdx(i, j, k, lg);
+    r32[p] = r.hi;
+    u32[p] = uc.hi;
+    e32[p] = 0.f;
     ss = fmaf(r.hi, r.hi, ss);
     mx = fmaxf(mx, fabsf(r.hi));
   }
@@ -327,15 +334,9 @@ __device__ __forceinline__ Jrow jac_row(float uc, const float* nb, const ModelF&
   return J;
 }
 
-__device__ __forceinline__ void nb6(const float* __restrict__ x, int i, int j, int k, int lg,
-                                    float* out) {
-  const int M = (1 << lg) - 1;
-  out[0] = x[cidx((i - 1) & M, j, k, lg)];
-  out[1] = x[cidx((i + 1) & M, j, k, lg)];
-  out[2] = x[cidx(i, (j - 1) & M, k, lg)];
-  out[3] = x[cidx(i, (j + 1) & M, k, lg)];
-  out[4] = x[cidx(i, j, (k - 1) & M, lg)];
-  out[5] = x[cidx(i, j, (k + 1) & M, lg)];
+__device__ __forceinline__ void nb6(const float* __restrict__ x, const unsigned* q, float* out) {
+#pragma unroll
+  for (int e = 0; e < 6; ++e) out[e] = x[q[e]];
 }
 
 // Gauss-Seidel half-sweep on J e = r: e_i = (r_i - sum_j J_ij e_j) / J_ii.
@@ -343,16 +344,15 @@ __global__ void __launch_bounds__(BS) k_lin_sweep(float* __restrict__ e, const f
                                                   const float* __restrict__ u, int lg, int colour,
                                                   ModelF m, float ih2) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int N = 1 << lg, M = N - 1;
   if (t >= (1u << (3 * lg - 1))) return;
-  const int k2 = (int)(t & ((N >> 1) - 1));
-  const unsigned rr = t >> (lg - 1);
-  const int j = (int)(rr & M), i = (int)(rr >> lg);
-  const int k = 2 * k2 + ((i + j + colour) & 1);
-  const unsigned c = cidx(i, j, k, lg);
+  const unsigned c = ((unsigned)colour << (3 * lg - 1)) + t;
+  int i, j, k;
+  pcell(c, lg, &i, &j, &k);
+  unsigned q[6];
+  pnb6(i, j, k, lg, q);
   float un[6], en[6];
-  nb6(u, i, j, k, lg, un);
-  nb6(e, i, j, k, lg, en);
+  nb6(u, q, un);
+  nb6(e, q, en);
   const Jrow J = jac_row(u[c], un, m, ih2);
   float s = r[c];
 #pragma unroll
@@ -366,18 +366,21 @@ __global__ void __launch_bounds__(BS) k_lin_restrict(const float* __restrict__ e
                                                      const float* __restrict__ u, int lgf,
                                                      float* __restrict__ ec, float* __restrict__ rc,
                                                      float* __restrict__ uc, ModelF m, float ih2) {
-  const int lgc = lgf - 1, Nc = 1 << lgc;
+  const int lgc = lgf - 1;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (1u << (3 * lgc))) return;
-  const int K = (int)(t & (Nc - 1)), J = (int)((t >> lgc) & (Nc - 1)), I = (int)(t >> (2 * lgc));
+  int I, J, K;
+  pcell(t, lgc, &I, &J, &K);
   float su = 0.f, sr = 0.f;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int i = 2 * I + (q >> 2), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q & 1);
-    const unsigned c = cidx(i, j, k, lgf);
+    const unsigned c = pdx(i, j, k, lgf);
+    unsigned nq[6];
+    pnb6(i, j, k, lgf, nq);
     float un[6], en[6];
-    nb6(u, i, j, k, lgf, un);
-    nb6(e, i, j, k, lgf, en);
+    nb6(u, nq, un);
+    nb6(e, nq, en);
     const Jrow Jr = jac_row(u[c], un, m, ih2);
     float Je = Jr.diag * e[c];
     for (int p = 0; p < 6; ++p) Je = fmaf(Jr.off[p], en[p], Je);
@@ -392,17 +395,20 @@ __global__ void __launch_bounds__(BS) k_lin_restrict(const float* __restrict__ e
 __global__ void __launch_bounds__(64) k_lin_coarse(float* __restrict__ eg, const float* __restrict__ rg,
                                                    const float* __restrict__ ug, ModelF m, float ih2,
                                                    int sweeps) {
-  __shared__ float e[64];
+  __shared__ float e[64];  // C order in shared memory
   const int t = threadIdx.x;
   const int i = t >> 4, j = (t >> 2) & 3, k = t & 3, colour = (i + j + k) & 1;
   const int nb[6] = {(((i + 3) & 3) << 4) | (j << 2) | k, (((i + 1) & 3) << 4) | (j << 2) | k,
                      (i << 4) | (((j + 3) & 3) << 2) | k, (i << 4) | (((j + 1) & 3) << 2) | k,
                      (i << 4) | (j << 2) | ((k + 3) & 3), (i << 4) | (j << 2) | ((k + 1) & 3)};
+  unsigned gq[6];
+  pnb6(i, j, k, 2, gq);
   float un[6];
-  for (int q = 0; q < 6; ++q) un[q] = ug[nb[q]];
-  const Jrow J = jac_row(ug[t], un, m, ih2);
-  const float rc = rg[t];
-  e[t] = eg[t];
+  for (int q = 0; q < 6; ++q) un[q] = ug[gq[q]];
+  const unsigned g = pdx(i, j, k, 2);
+  const Jrow J = jac_row(ug[g], un, m, ih2);
+  const float rc = rg[g];
+  e[t] = eg[g];
   __syncthreads();
   for (int s = 0; s < sweeps; ++s)
     for (int c = 0; c < 2; ++c) {
@@ -413,14 +419,16 @@ __global__ void __launch_bounds__(64) k_lin_coarse(float* __restrict__ eg, const
       }
       __syncthreads();
     }
-  eg[t] = e[t];
+  eg[g] = e[t];
 }
 
 __global__ void k_apply_corr(dfl* __restrict__ u, dfl* __restrict__ E, const float* __restrict__ e,
-                             long long n, float cap) {
+                             int lg, float cap) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const dfl v = df_add_f(u[t], fminf(fmaxf(e[t], -cap), cap));
+  if (t >= (1u << (3 * lg))) return;
+  const int M = (1 << lg) - 1;
+  const float et = e[pdx((int)(t >> (2 * lg)), (int)((t >> lg) & M), (int)(t & M), lg)];
+  const dfl v = df_add_f(u[t], fminf(fmaxf(et, -cap), cap));
   u[t] = v;
   E[t] = df_exp(v);
 }
@@ -472,12 +480,12 @@ __global__ void k_finish32(const double* __restrict__ partials, int nparts, doub
 
 namespace f32 {
 
-void from64(const double* x, float* y, long long n, cudaStream_t s) {
-  k_from64<<<nblocks(n, BS), BS, 0, s>>>(x, y, n);
+void from64(const double* x, float* y, const DenseLevel& L, cudaStream_t s) {
+  k_from64<<<nblocks(L.n, BS), BS, 0, s>>>(x, y, L.lg);
 }
 void to_df(DenseLevel& L, cudaStream_t s) {
   k_to_df<<<nblocks(L.n, BS), BS, 0, s>>>(L.u32, reinterpret_cast<dfl*>(L.u),
-                                          reinterpret_cast<dfl*>(L.E), L.n);
+                                          reinterpret_cast<dfl*>(L.E), L.lg);
 }
 void f_to_df(const double* f, double* fdf, long long n, cudaStream_t s) {
   k_d2df<<<nblocks(n, BS), BS, 0, s>>>(f, reinterpret_cast<dfl*>(fdf), n);
@@ -537,7 +545,7 @@ void lin_coarse(DenseLevel& C, const Model& m, int sweeps, cudaStream_t s) {
 void zero(float* x, long long n, cudaStream_t s) { k_zero<<<nblocks(n, BS), BS, 0, s>>>(x, n); }
 void apply_corr(DenseLevel& L, double cap, cudaStream_t s) {
   k_apply_corr<<<nblocks(L.n, BS), BS, 0, s>>>(reinterpret_cast<dfl*>(L.u),
-                                               reinterpret_cast<dfl*>(L.E), L.e32, L.n, (float)cap);
+                                               reinterpret_cast<dfl*>(L.E), L.e32, L.lg, (float)cap);
 }
 
 }  // namespace f32

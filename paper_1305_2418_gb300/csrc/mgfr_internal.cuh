@@ -97,8 +97,12 @@ void force(const DenseLevel& L, const Model& m, double* fr, double* acc, cudaStr
 }  // namespace f64
 
 // ---- FP32 dense kernels, mixed precision (dense_f32.cu) -------------------
+// The FP32 arrays of a dense level (u32, f32, uold32, e32, r32) are stored by
+// red-black colour (plane (i + j + k) & 1, then C order of (i, j, k >> 1));
+// the FP64 and double-float arrays are in C order.
 namespace f32 {
-void from64(const double* x, float* y, long long n, cudaStream_t s);
+// C-order FP64 x -> colour-split FP32 y on level L's grid
+void from64(const double* x, float* y, const DenseLevel& L, cudaStream_t s);
 void sweep(DenseLevel& L, const Model& m, int colour, float step_cap, cudaStream_t s);
 void restrict_resid(DenseLevel& F, DenseLevel& C, const Model& m, double* partials, int nparts,
                     cudaStream_t s);

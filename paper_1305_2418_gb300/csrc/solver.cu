@@ -442,8 +442,8 @@ mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stat
   // ||f|| in FP64 (a sum of squares); the initial residual, which only decides
   // whether to iterate, from the FP32 copies the V-cycles start from
   f64::norm(L0.f, L0.n, H.partials, H.nparts, H.scal + 2, c->s);
-  f32::from64(L0.f, L0.f32, L0.n, c->s);
-  f32::from64(L0.u, L0.u32, L0.n, c->s);
+  f32::from64(L0.f, L0.f32, L0, c->s);
+  f32::from64(L0.u, L0.u32, L0, c->s);
   f32::norm32(L0, m, H.partials, H.nparts, H.scal, c->s);
   c->launches += 6;
   MG_CK(c, cudaMemcpyAsync(hs, H.scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
