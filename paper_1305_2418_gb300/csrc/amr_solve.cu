@@ -344,29 +344,43 @@ __global__ void __launch_bounds__(BS) k_dsweep_list(T* __restrict__ u, T* __rest
   if constexpr (std::is_same<T, double>::value) E[c] = ex(un);
 }
 
-// the relaxed cells of one colour of a masked dense level -> list (in warp
-// order; a red-black half-sweep does not depend on the order), count += n
+// the relaxed cells of a masked dense level -> one list per colour (colour q
+// at list + q half, in block order: a red-black half-sweep does not depend on
+// the order), count[q] += their number; one atomic per block and colour
 __global__ void __launch_bounds__(BS) k_dense_list(const unsigned char* __restrict__ act, int lg,
-                                                   int colour, int* __restrict__ list,
+                                                   int* __restrict__ list,
                                                    unsigned long long* __restrict__ count) {
+  __shared__ int woff[2][BS / 32];
+  __shared__ unsigned long long bbase[2];
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int N = 1 << lg, M = N - 1;
-  const bool live = t < (1u << (3 * lg - 1));
-  const unsigned tt = live ? t : 0;
-  const int k2 = (int)(tt & ((N >> 1) - 1));
-  const unsigned r = tt >> (lg - 1);
-  const int j = (int)(r & M), i = (int)(r >> lg);
-  const int k = 2 * k2 + ((i + j + colour) & 1);
-  const unsigned c = cidx(i, j, k, lg);
-  const bool on = live && act[c];
-  const unsigned ballot = __ballot_sync(0xffffffffu, on);  // whole warps reach here
-  if (ballot == 0u) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(ballot) - 1;
-  unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(ballot));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (on) list[base + __popc(ballot & ((1u << lane) - 1u))] = (int)c;
+  const int M = (1 << lg) - 1;
+  const bool live = t < (1u << (3 * lg));
+  const int colour = live ? (int)(((t >> (2 * lg)) + ((t >> lg) & M) + (t & M)) & 1) : 0;
+  const bool on = live && act[t];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned ballot[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    ballot[q] = __ballot_sync(0xffffffffu, on && colour == q);  // whole warps reach here
+    if (lane == 0) woff[q][w] = __popc(ballot[q]);
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {  // exclusive offsets of the warps, and the block's base
+    const int q = threadIdx.x;
+    int run = 0;
+    for (int v = 0; v < BS / 32; ++v) {
+      const int n = woff[q][v];
+      woff[q][v] = run;
+      run += n;
+    }
+    bbase[q] = run > 0 ? atomicAdd(count + q, (unsigned long long)run) : 0ULL;
+  }
+  __syncthreads();
+  if (on) {
+    const int q = colour;
+    list[((long long)q << (3 * lg - 1)) + bbase[q] + woff[q][w] +
+         __popc(ballot[q] & ((1u << lane) - 1u))] = (int)t;
+  }
 }
 
 template <class T>
@@ -1088,48 +1102,80 @@ __device__ __forceinline__ dfl ldf(const dfl* __restrict__ p, long long i) {
   return dfl{v.x, v.y};
 }
 
-// the eight double-float values of oct o (64 contiguous bytes, four 16-byte loads)
-__device__ __forceinline__ void ld8df(const dfl* __restrict__ p, long long o, dfl* x) {
-  const float4* q = reinterpret_cast<const float4*>(p + 8 * o);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float4 v = __ldg(q + i);
-    x[2 * i] = dfl{v.x, v.y};
-    x[2 * i + 1] = dfl{v.z, v.w};
-  }
+// the four double-float values of half h of oct o (cells 4h .. 4h+3: 32
+// contiguous bytes, two 16-byte loads)
+__device__ __forceinline__ void ld4df(const dfl* __restrict__ p, long long o, int h, dfl* x) {
+  const float4* q = reinterpret_cast<const float4*>(p + 8 * o + 4 * h);
+  const float4 a = __ldg(q), b = __ldg(q + 1);
+  x[0] = dfl{a.x, a.y};
+  x[1] = dfl{a.z, a.w};
+  x[2] = dfl{b.x, b.y};
+  x[3] = dfl{b.z, b.w};
 }
 
 // r = f - L(u) to FP64 accuracy in double-float (Sec. 3.2 operator); stores r
 // and u rounded to FP32 for the linear cycles, zeroes the correction e, and
 // accumulates the norms (FP32 within a thread, FP64 across threads: they feed
-// only the stopping test).  One thread per oct: the flux across each of the
-// oct's 12 inner faces, (E_i + E_j)(u_j - u_i), is formed once and enters
-// the two cells with opposite signs (the double-float sum, difference and
-// product are odd under negation, so each cell's terms are those of a
-// cell-by-cell evaluation); every cell sums its six terms in the direction
-// order -x, +x, -y, +y, -z, +z.
-__global__ void __launch_bounds__(BS) k_oresid_df(
+// only the stopping test).  Two threads per oct, one per x half (cells 4h +
+// q, q = 2 y + z): the flux across each inner face, (E_i + E_j)(u_j - u_i),
+// is formed once per face inside a half and once by each thread across the
+// middle x face, and enters the two cells with opposite signs (the
+// double-float sum, difference and product are odd under negation, so each
+// cell's terms are those of a cell-by-cell evaluation); every cell sums its
+// six terms in the direction order -x, +x, -y, +y, -z, +z.
+__global__ void __launch_bounds__(BS, 4) k_oresid_df(
     const dfl* __restrict__ u, const dfl* __restrict__ E, const dfl* __restrict__ f,
     const int* __restrict__ nbr, const dfl* __restrict__ gh, const dfl* __restrict__ ghE,
     MDF m, long long no, float* __restrict__ r32, float* __restrict__ u32,
     float* __restrict__ e32, double* __restrict__ partials) {
   float ss = 0.f, mx = 0.f, fs = 0.f;
-  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < no;
-       o += (long long)gridDim.x * blockDim.x) {
-    dfl U[8], Ev[8], acc[8];
-    ld8df(u, o, U);
-    ld8df(E, o, Ev);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 2 * no;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long o = t >> 1;
+    const int h = (int)(t & 1);
+    dfl U[4], Ev[4], acc[4];
+    ld4df(u, o, h, U);
+    ld4df(E, o, h, Ev);
+    // x: the outer face on side h, and the middle face (cell 4h + q against
+    // 4(1-h) + q of the other half)
+    {
+      dfl Up[4], Ep[4];
+      ld4df(u, o, 1 - h, Up);
+      ld4df(E, o, 1 - h, Ep);
+      const int nb = nbr[6 * o + h];
 #pragma unroll
-    for (int ch = 0; ch < 8; ++ch) acc[ch] = dfl{0.f, 0.f};
+      for (int q = 0; q < 4; ++q) {
+        const int ch = 4 * h + q;
+        dfl ue, Ee;
+        if (nb >= 0) {
+          ue = ldf(u, 8LL * nb + (ch ^ 4));
+          Ee = ldf(E, 8LL * nb + (ch ^ 4));
+        } else {
+          ue = ldf(gh, 4LL * (-nb - 1) + face_q(ch, 0));
+          Ee = ldf(ghE, 4LL * (-nb - 1) + face_q(ch, 0));
+        }
+        const dfl ext = df_mul(df_add_abs(Ee, Ev[q]), df_add_abs(ue, df_neg(U[q])));
+        const dfl zero{0.f, 0.f};
+        if (h == 0) {  // this cell is ch0 of the middle face: -x outer, then +x inner
+          const dfl Fin = df_mul(df_add_abs(Ep[q], Ev[q]), df_add_abs(Up[q], df_neg(U[q])));
+          acc[q] = df_add_abs(df_add_abs(zero, ext), Fin);
+        } else {       // ch1: -x inner, then +x outer
+          const dfl Fin = df_mul(df_add_abs(Ev[q], Ep[q]), df_add_abs(U[q], df_neg(Up[q])));
+          acc[q] = df_add_abs(df_add_abs(zero, df_neg(Fin)), ext);
+        }
+      }
+    }
+    // y and z: faces inside the half, outer faces on both sides
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
+    for (int ax = 1; ax < 3; ++ax) {
       const int sh = 2 - ax;
       const int nm = nbr[6 * o + 2 * ax], np = nbr[6 * o + 2 * ax + 1];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        // ch0 has bit sh clear (the minus half), ch1 is its partner across the face
-        const int ch0 = ((q >> sh) << (sh + 1)) | (q & ((1 << sh) - 1));
-        const int ch1 = ch0 | (1 << sh);
+      for (int p = 0; p < 2; ++p) {
+        // q0 has bit sh clear, q1 is its partner across the face
+        const int q0 = ((p >> sh) << (sh + 1)) | (p & ((1 << sh) - 1));
+        const int q1 = q0 | (1 << sh);
+        const int ch0 = 4 * h + q0, ch1 = 4 * h + q1;
         const int qi = face_q(ch0, ax);
         dfl um, Em, up, Ep;  // across the minus face of ch0, the plus face of ch1
         if (nm >= 0) {
@@ -1146,31 +1192,28 @@ __global__ void __launch_bounds__(BS) k_oresid_df(
           up = ldf(gh, 4LL * (-np - 1) + qi);
           Ep = ldf(ghE, 4LL * (-np - 1) + qi);
         }
-        const dfl Fin = df_mul(df_add_abs(Ev[ch1], Ev[ch0]), df_add_abs(U[ch1], df_neg(U[ch0])));
-        acc[ch0] = df_add_abs(acc[ch0], df_mul(df_add_abs(Em, Ev[ch0]), df_add_abs(um, df_neg(U[ch0]))));
-        acc[ch0] = df_add_abs(acc[ch0], Fin);
-        acc[ch1] = df_add_abs(acc[ch1], df_neg(Fin));
-        acc[ch1] = df_add_abs(acc[ch1], df_mul(df_add_abs(Ep, Ev[ch1]), df_add_abs(up, df_neg(U[ch1]))));
+        const dfl Fin = df_mul(df_add_abs(Ev[q1], Ev[q0]), df_add_abs(U[q1], df_neg(U[q0])));
+        acc[q0] = df_add_abs(acc[q0], df_mul(df_add_abs(Em, Ev[q0]), df_add_abs(um, df_neg(U[q0]))));
+        acc[q0] = df_add_abs(acc[q0], Fin);
+        acc[q1] = df_add_abs(acc[q1], df_neg(Fin));
+        acc[q1] = df_add_abs(acc[q1], df_mul(df_add_abs(Ep, Ev[q1]), df_add_abs(up, df_neg(U[q1]))));
       }
     }
-    dfl F8[8];
-    ld8df(f, o, F8);
-    Oct8 R, Uh;
+    dfl F4[4];
+    ld4df(f, o, h, F4);
 #pragma unroll
-    for (int ch = 0; ch < 8; ++ch) {
-      const dfl sN = m.n == 1 ? df_rsqrt(Ev[ch]) : df_exp(df_neg(df_mul(U[ch], m.inv_np1)));
-      const dfl L = df_add(df_mul(acc[ch], m.ih2h), df_mul(m.aRt, df_add_f(df_neg(sN), 1.f)));
-      const dfl r = df_sub(F8[ch], L);
-      R.v[ch] = r.hi;
-      Uh.v[ch] = U[ch].hi;
+    for (int q = 0; q < 4; ++q) {
+      const dfl sN = m.n == 1 ? df_rsqrt(Ev[q]) : df_exp(df_neg(df_mul(U[q], m.inv_np1)));
+      const dfl L = df_add(df_mul(acc[q], m.ih2h), df_mul(m.aRt, df_add_f(df_neg(sN), 1.f)));
+      const dfl r = df_sub(F4[q], L);
+      const long long k = pidx(8 * o + 4 * h + q, no);
+      r32[k] = r.hi;
+      u32[k] = U[q].hi;
+      e32[k] = 0.f;
       ss = fmaf(r.hi, r.hi, ss);
       mx = fmaxf(mx, fabsf(r.hi));
-      fs = fmaf(F8[ch].hi, F8[ch].hi, fs);
+      fs = fmaf(F4[q].hi, F4[q].hi, fs);
     }
-    st8(r32, o, no, R);
-    st8(u32, o, no, Uh);
-    stc(e32, o, no, 0, make_float4(0.f, 0.f, 0.f, 0.f));
-    stc(e32, o, no, 1, make_float4(0.f, 0.f, 0.f, 0.f));
   }
   block_partials3((double)ss, (double)mx, (double)fs, partials);
 }
@@ -1701,12 +1744,10 @@ mgfr_status count_relaxed(mgfr_ctx* c, AmrWork* A, const float* mask, long long 
 
 // per-colour lists of the relaxed cells of masked dense level k (0: the base)
 mgfr_status build_dense_lists(mgfr_ctx* c, AmrWork* A, int k, const unsigned char* act, int lg) {
-  const long long half = 1LL << (3 * lg - 1);
   MG_CK(c, cudaMemsetAsync(A->d_small + 4, 0, 2 * sizeof(long long), c->s));
-  for (int q = 0; q < 2; ++q)
-    k_dense_list<<<nblocks(half, BS), BS, 0, c->s>>>(act, lg, q, A->dlist[k] + q * half,
-                                                     (unsigned long long*)(A->d_small + 4 + q));
-  c->launches += 2;
+  k_dense_list<<<nblocks(1LL << (3 * lg), BS), BS, 0, c->s>>>(
+      act, lg, A->dlist[k], (unsigned long long*)(A->d_small + 4));
+  c->launches += 1;
   long long n[2] = {0, 0};
   MG_CK(c, cudaMemcpyAsync(n, A->d_small + 4, 2 * sizeof(long long), cudaMemcpyDeviceToHost, c->s));
   MG_CK(c, cudaStreamSynchronize(c->s));
@@ -1851,7 +1892,7 @@ mgfr_status lin_resid(SolveCtx& S, double* hs) {
   mgfr_ctx* c = S.c;
   AmrLevel& L = S.A->L[S.L];
   DenseHier& H = c->dh;
-  const int nparts = (int)std::min<long long>(H.nparts / 2, nblocks(L.n_oct, BS));
+  const int nparts = (int)std::min<long long>(H.nparts / 2, nblocks(2 * L.n_oct, BS));
   if (c->capturing >= 0) prof_begin(c, 2, L.ncell);
   k_oresid_df<<<nparts, BS, 0, c->s>>>(
       reinterpret_cast<const dfl*>(L.w), reinterpret_cast<const dfl*>(L.wE),
