@@ -728,10 +728,17 @@ __global__ void __launch_bounds__(BS, 6) k_oct_sweep32(
   const float4 XO = LIN ? ldc(e, o, no, OC) : make_float4(0.f, 0.f, 0.f, 0.f);
   bool on[4];
   float s1[4], s2[4], s3[4];  // LIN: (sum off*e, diag sum, -); NL: (sum b du, sum du, sum b)
+  // the oct's eight relax flags in one 8-byte load
+  const unsigned long long a8 = act ? __ldg(reinterpret_cast<const unsigned long long*>(act) + o)
+                                    : ~0ULL;
+  // the six face neighbours as three 8-byte loads (6 o ints: 8-byte aligned)
+  const int2* nb2 = reinterpret_cast<const int2*>(nbr + 6 * o);
+  const int2 n01 = __ldg(nb2), n23 = __ldg(nb2 + 1), n45 = __ldg(nb2 + 2);
+  const int nbv[6] = {n01.x, n01.y, n23.x, n23.y, n45.x, n45.y};
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int ch = CC[COL][q];
-    on[q] = !act || act[8 * o + ch];
+    on[q] = ((a8 >> (8 * ch)) & 0xffULL) != 0ULL;
     s1[q] = s2[q] = s3[q] = 0.f;
     // in-oct neighbours (other colour, unchanged in this half-sweep)
 #pragma unroll
@@ -754,7 +761,7 @@ __global__ void __launch_bounds__(BS, 6) k_oct_sweep32(
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     const int a = d >> 1, plus = d & 1;
-    const int nb = nbr[6 * o + d];
+    const int nb = nbv[d];
     float4 NU, NX;
     if (nb >= 0) {
       NU = ldc(u, nb, no, OC);
