@@ -420,6 +420,42 @@ def test_ghost_linear_reconstruction_exact_for_linear_field():
     assert checked > 0
 
 
+def test_ghost_reconstruction_error_for_quadratic_field():
+    """Central slopes: for u = a x^2 + b y^2 + c z^2 + (linear) in coarse-cell
+    units, P + s (u+ - u-)/8 at the daughter centre P + s/4 misses u there by
+    exactly -(a + b + c)/16 (each axis: (x+1)^2 - (x-1)^2 = 4x, and
+    (x + s/4)^2 - x^2 - s x/2 = 1/16).  A one-sided slope, a wrong daughter
+    offset or a wrong factor gives an error that depends on the side s."""
+    N0, box = 16, 16.0
+    rng = np.random.default_rng(5)
+    pos = 6.0 + 3.0 * rng.random((400, 3))
+    A = oracle.AMR(pos, N0, box, 1, 8)
+    assert A.nlev == 2
+    x0 = np.arange(N0) + 0.5
+    X, Y, Z = np.meshgrid(x0, x0, x0, indexing="ij")
+    qa, qb, qc = 0.03, -0.01, 0.02  # a + b + c != 0
+    quad = lambda x, y, z: qa * x * x + qb * y * y + qc * z * z + 0.3 * x - 0.1 * z + 1.0
+    A.set_u(0, quad(X, Y, Z).ravel())
+    g = A.ghosts(1)
+    keys = A.keys(1)
+    dirs = [(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+    want = -(qa + qb + qc) / 16.0
+    checked = 0
+    for o, key in enumerate(keys):
+        pi, pj, pk = key // (N0 * N0), (key // N0) % N0, key % N0
+        for ch in range(8):
+            I, J, K = 2 * pi + (ch >> 2 & 1), 2 * pj + (ch >> 1 & 1), 2 * pk + (ch & 1)
+            for d, (a, b, c) in enumerate(dirs):
+                v = g[8 * o + ch, d]
+                if np.isnan(v):
+                    continue
+                gi, gj, gk = I + a, J + b, K + c
+                exact = quad((gi + 0.5) / 2, (gj + 0.5) / 2, (gk + 0.5) / 2)
+                assert abs((v - exact) - want) < 1e-12
+                checked += 1
+    assert checked > 0
+
+
 # --------------------------------------------------------------------------
 # P8: refining the whole box makes level 1 a uniform (2N)^3 grid with no
 # patch boundary; its one-way solution must equal the uniform fine solve.
