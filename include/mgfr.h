@@ -172,6 +172,26 @@ mgfr_status mgfr_solve_particles(mgfr_ctx* ctx, const double* pos_dev, long long
                                  double box, double a, const double* u_init_dev,
                                  double* fr_base_out_dev, double* acc_out_dev, mgfr_stats* st);
 
+/*
+ * mgfr_solve_particles with the particle arrays in host memory: the same
+ * solve (Sec. 3.1 and 3.3) on positions copied to the device by the call, and
+ * the force at the particles copied back while it is being gathered (the
+ * gather runs in chunks; each chunk's copy overlaps the next chunk's gather).
+ *   pos_host     [Np][3] FP64 positions in host memory (page-locked memory,
+ *                e.g. from cudaHostAlloc, lets the copies run asynchronously;
+ *                pageable memory works but the copies then stage through the
+ *                driver).
+ *   acc_out_host [Np][3] host memory for a_MG / c^2 at the particles (required).
+ *   u_init_dev, fr_base_out_dev: device pointers or NULL, as above.
+ * The device copies of the particle arrays are context workspace (grown to
+ * Np, kept for the next call).  The call returns when acc_out_host is filled.
+ * Errors as mgfr_solve_particles; MGFR_E_INVALID if acc_out_host is NULL.
+ */
+mgfr_status mgfr_solve_particles_host(mgfr_ctx* ctx, const double* pos_host, long long Np,
+                                      int N_base, double box, double a, const double* u_init_dev,
+                                      double* fr_base_out_dev, double* acc_out_host,
+                                      mgfr_stats* st);
+
 /* Size of level `level` of the last particle solve: octs (0 on the base)
  * and cells (N_base^3 on the base, 8 per oct above). */
 mgfr_status mgfr_get_level_info(mgfr_ctx* ctx, int level, long long* n_oct, long long* ncell);

@@ -649,6 +649,8 @@ void amr_free(mgfr_ctx* c) {
   if (A->acc0) cudaFree(A->acc0);
   if (A->fr0) cudaFree(A->fr0);
   if (A->acc0_32) cudaFree(A->acc0_32);
+  if (A->pos_dev) cudaFree(A->pos_dev);
+  if (A->acc_dev) cudaFree(A->acc_dev);
   delete A;
   c->amr = nullptr;
 }
@@ -836,15 +838,23 @@ mgfr_status ensure_dense_public(mgfr_ctx* c, int N, bool mixed, double box);
 
 extern "C" {
 
-mgfr_status mgfr_solve_particles(mgfr_ctx* c, const double* pos, long long Np, int N0, double box,
-                                 double a, const double* u_init, double* fr_out, double* acc_out,
-                                 mgfr_stats* st) {
-  if (!c) return MGFR_E_INVALID;
+// The particle solve; acc_out is a device array, and acc_host (if not NULL)
+// receives it chunk by chunk while the gather runs.
+static mgfr_status check_particle_args(mgfr_ctx* c, const double* pos, long long Np, int N0,
+                                       double box, double a) {
   if (!pos || Np <= 0) return set_err(c, MGFR_E_INVALID, "need Np >= 1 particle positions");
   if (Np >= (1LL << 40)) return set_err(c, MGFR_E_INVALID, "Np too large");
   if (N0 < 8 || N0 > 1024 || (N0 & (N0 - 1))) return set_err(c, MGFR_E_INVALID, "N_base must be a power of two in [8, 1024]");
   if (!(box > 0.0) || !std::isfinite(box)) return set_err(c, MGFR_E_INVALID, "box must be > 0");
   if (!(a > 0.0) || !std::isfinite(a)) return set_err(c, MGFR_E_INVALID, "a must be > 0");
+  return MGFR_OK;
+}
+
+static mgfr_status solve_particles(mgfr_ctx* c, const double* pos, long long Np, int N0, double box,
+                                   double a, const double* u_init, double* fr_out,
+                                   double* acc_out, double* acc_host, mgfr_stats* st) {
+  if (!c) return MGFR_E_INVALID;
+  TRY(check_particle_args(c, pos, Np, N0, box, a));
   const mgfr_config& g = c->cfg;
   MG_CK(c, cudaSetDevice(c->device));
   if (st) std::memset(st, 0, sizeof(*st));
@@ -969,13 +979,33 @@ mgfr_status mgfr_solve_particles(mgfr_ctx* c, const double* pos, long long Np, i
   }
   if (acc_out) {
     TreeView T = tree_view(A);
-    if (g32)
-      k_gather32<<<nblocks(Np, BS), BS, 0, c->s>>>(pos, Np, (double)N0 / box, (double)N0, T, G,
-                                                   acc_out, (unsigned long long*)(A->d_small + 1));
-    else
-      k_gather<<<nblocks(Np, BS), BS, 0, c->s>>>(pos, Np, (double)N0 / box, (double)N0, T, G,
-                                                 acc_out, (unsigned long long*)(A->d_small + 1));
-    c->launches += 1;
+    // with a host destination: chunks, each copied back on the copy stream
+    // while the next one is gathered
+    const int nch = acc_host ? 8 : 1;
+    const long long per = (Np + nch - 1) / nch;
+    for (int q = 0; q < nch; ++q) {
+      const long long p0 = q * per, n = std::min(per, Np - p0);
+      if (n <= 0) break;
+      if (g32)
+        k_gather32<<<nblocks(n, BS), BS, 0, c->s>>>(pos + 3 * p0, n, (double)N0 / box, (double)N0,
+                                                    T, G, acc_out + 3 * p0,
+                                                    (unsigned long long*)(A->d_small + 1));
+      else
+        k_gather<<<nblocks(n, BS), BS, 0, c->s>>>(pos + 3 * p0, n, (double)N0 / box, (double)N0, T,
+                                                  G, acc_out + 3 * p0,
+                                                  (unsigned long long*)(A->d_small + 1));
+      c->launches += 1;
+      if (acc_host) {
+        MG_CK(c, cudaEventRecord(c->ev_chunk[q], c->s));
+        MG_CK(c, cudaStreamWaitEvent(c->cs, c->ev_chunk[q], 0));
+        MG_CK(c, cudaMemcpyAsync(acc_host + 3 * p0, acc_out + 3 * p0, sizeof(double) * 3 * (size_t)n,
+                                 cudaMemcpyDeviceToHost, c->cs));
+      }
+    }
+    if (acc_host) {
+      MG_CK(c, cudaEventRecord(c->ev_copy, c->cs));
+      MG_CK(c, cudaStreamWaitEvent(c->s, c->ev_copy, 0));
+    }
   }
   MG_CK(c, cudaEventRecord(c->ev_out, c->s));
   MG_CK(c, cudaStreamWaitEvent(c->user, c->ev_out, 0));
@@ -995,6 +1025,50 @@ mgfr_status mgfr_solve_particles(mgfr_ctx* c, const double* pos, long long Np, i
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
   }
   return worst;
+}
+
+mgfr_status mgfr_solve_particles(mgfr_ctx* c, const double* pos, long long Np, int N0, double box,
+                                 double a, const double* u_init, double* fr_out, double* acc_out,
+                                 mgfr_stats* st) {
+  return solve_particles(c, pos, Np, N0, box, a, u_init, fr_out, acc_out, nullptr, st);
+}
+
+mgfr_status mgfr_solve_particles_host(mgfr_ctx* c, const double* pos_host, long long Np, int N0,
+                                      double box, double a, const double* u_init, double* fr_out,
+                                      double* acc_host, mgfr_stats* st) {
+  if (!c) return MGFR_E_INVALID;
+  TRY(check_particle_args(c, pos_host, Np, N0, box, a));
+  if (!acc_host) return set_err(c, MGFR_E_INVALID, "acc_out_host is required");
+  MG_CK(c, cudaSetDevice(c->device));
+  if (!c->cs) {
+    MG_CK(c, cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking));
+    for (auto& ev : c->ev_chunk) MG_CK(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    MG_CK(c, cudaEventCreateWithFlags(&c->ev_copy, cudaEventDisableTiming));
+  }
+  if (!c->amr) c->amr = new AmrWork();
+  AmrWork* A = W(c);
+  if (Np > A->pio_cap) {
+    if (A->pos_dev) cudaFree(A->pos_dev);
+    if (A->acc_dev) cudaFree(A->acc_dev);
+    A->pos_dev = A->acc_dev = nullptr;
+    A->pio_cap = 0;
+    MG_CK(c, cudaMalloc(&A->pos_dev, sizeof(double) * 3 * (size_t)Np));
+    MG_CK(c, cudaMalloc(&A->acc_dev, sizeof(double) * 3 * (size_t)Np));
+    A->pio_cap = Np;
+  }
+  // in the caller's stream order
+  MG_CK(c, cudaEventRecord(c->ev_in, c->user));
+  MG_CK(c, cudaStreamWaitEvent(c->s, c->ev_in, 0));
+  MG_CK(c, cudaMemcpyAsync(A->pos_dev, pos_host, sizeof(double) * 3 * (size_t)Np,
+                           cudaMemcpyHostToDevice, c->s));
+  const mgfr_status rs =
+      solve_particles(c, A->pos_dev, Np, N0, box, a, u_init, fr_out, A->acc_dev, acc_host, st);
+  if (rs != MGFR_OK && rs != MGFR_E_NOCONVERGE) {
+    // the host arrays may still be in use by copies queued before the error
+    cudaStreamSynchronize(c->s);
+    if (c->cs) cudaStreamSynchronize(c->cs);
+  }
+  return rs;
 }
 
 mgfr_status mgfr_get_level_info(mgfr_ctx* c, int level, long long* n_oct, long long* ncell) {

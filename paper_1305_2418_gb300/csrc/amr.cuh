@@ -113,6 +113,8 @@ struct AmrWork {
   double* fr0 = nullptr;              // base fR [N0^3]
   double fbar = 0.0, a = 1.0;         // of the last particle solve (deferred level forces)
   float4* acc0_32 = nullptr;          // base force, FP32 (x, y, z, 0) per cell
+  double *pos_dev = nullptr, *acc_dev = nullptr;  // particle arrays of the host-buffer call
+  long long pio_cap = 0;                          // their capacity (particles)
   long long cap_cells[AMR_MAXL] = {}; // allocated capacity per level (cells)
   long long cap_oct[AMR_MAXL] = {};
 };

@@ -142,6 +142,10 @@ struct mgfr_ctx {
   cudaStream_t user = nullptr;  // caller's stream
   cudaStream_t s = nullptr;     // internal work stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
+  // host-buffer particle solve: copy stream and per-chunk events (created on
+  // first use)
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_chunk[8] = {}, ev_copy = nullptr;
   std::string err;
   DenseHier dh;
   double* host_scal = nullptr;  // pinned: norms read back by the host

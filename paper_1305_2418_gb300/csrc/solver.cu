@@ -600,6 +600,7 @@ void mgfr_destroy(mgfr_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->s) cudaStreamSynchronize(c->s);
+  if (c->cs) cudaStreamSynchronize(c->cs);
   drop_graphs(c);
   free_dense(c->dh);
   amr_free(c);
@@ -608,10 +609,13 @@ void mgfr_destroy(mgfr_ctx* c) {
   for (auto e : c->evpool) cudaEventDestroy(e);
   c->evpool.clear();
   if (c->host_scal) cudaFreeHost(c->host_scal);
-  cudaEvent_t evs[] = {c->ev_in, c->ev_out, c->t0, c->t1};
+  cudaEvent_t evs[] = {c->ev_in, c->ev_out, c->t0, c->t1, c->ev_copy};
   for (auto ev : evs)
     if (ev) cudaEventDestroy(ev);
+  for (auto ev : c->ev_chunk)
+    if (ev) cudaEventDestroy(ev);
   if (c->s) cudaStreamDestroy(c->s);
+  if (c->cs) cudaStreamDestroy(c->cs);
   delete c;
 }
 

@@ -79,6 +79,9 @@ SIGNATURES = {
     "mgfr_solve_particles": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_int, C.c_double,
                                        C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p]),
+    "mgfr_solve_particles_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_int,
+                                            C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_void_p]),
     "mgfr_get_level_info": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "mgfr_get_level_keys": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "mgfr_get_level_field": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
@@ -203,6 +206,26 @@ class Solver:
                                         _ptr(u_init), _ptr(fr), _ptr(acc), C.byref(stats))
         self._check(st, allow_noconverge)
         return {"fr": fr, "acc": acc, "stats": stats.to_dict(), "status": st}
+
+    def solve_particles_host(self, pos_host, N_base: int, box: float, a: float = 1.0,
+                             acc_out=None, u_init=None, want_fr=False, allow_noconverge=False):
+        """mgfr_solve_particles_host: positions and forces in host memory (CPU FP64
+        tensors, contiguous; page-locked ones let the copies overlap the gather)."""
+        import torch
+        assert pos_host.device.type == "cpu" and pos_host.dtype == torch.float64
+        assert pos_host.is_contiguous() and pos_host.ndim == 2 and pos_host.shape[1] == 3
+        if acc_out is None:
+            acc_out = torch.empty_like(pos_host, pin_memory=pos_host.is_pinned())
+        assert acc_out.device.type == "cpu" and acc_out.dtype == torch.float64
+        assert acc_out.is_contiguous() and acc_out.shape == pos_host.shape
+        fr = torch.empty((N_base,) * 3, dtype=torch.float64, device=f"cuda:{self.device}") \
+            if want_fr else None
+        stats = Stats()
+        st = lib().mgfr_solve_particles_host(
+            self.h, C.c_void_p(pos_host.data_ptr()), pos_host.shape[0], N_base, box, a,
+            _ptr(u_init), _ptr(fr), C.c_void_p(acc_out.data_ptr()), C.byref(stats))
+        self._check(st, allow_noconverge)
+        return {"fr": fr, "acc": acc_out, "stats": stats.to_dict(), "status": st}
 
     def level_info(self, level: int):
         no, nc = C.c_longlong(), C.c_longlong()

@@ -144,3 +144,37 @@ def test_invalid_particles_rejected(dev):
     ok = s.solve_particles(torch.rand((100, 3), dtype=torch.float64, device=dev) * 10, 16, 10.0)
     assert ok["status"] == mgfr.MGFR_OK
     s.close()
+
+
+@pytest.mark.parametrize("prec", [mgfr.PREC_FP64, mgfr.PREC_MIXED])
+def test_host_buffer_solve_matches_device_solve(dev, prec):
+    """mgfr_solve_particles_host (positions and forces in page-locked host
+    memory, the gather in chunks with overlapped copies) gives the force of
+    the device-buffer call (to rounding: the deposit's FP64 atomics add in
+    any order, 1e-11 of the largest force), and the oracle's within
+    tolerance; it also accepts pageable host memory and an Np that is not a
+    multiple of the chunk count."""
+    N0, box, fr0 = 32, 100.0, 1e-5
+    d = synth.lognormal_delta(N0, box, 1.5, 3041)
+    pos = synth.poisson_particles(d, box, 1.0, 3141)[:-5]
+    s = mgfr.Solver(0, fr0_abs=fr0, precision=prec, max_level=2, tol_rel=1e-8, max_vcycles=200)
+    ref = s.solve_particles(torch.from_numpy(pos).to(dev), N0, box)["acc"].cpu()
+    host = torch.from_numpy(pos).pin_memory()
+    out = s.solve_particles_host(host, N0, box)
+    assert out["acc"].is_pinned()
+    same = lambda x: (x - ref).abs().max().item() <= 1e-11 * ref.abs().max().item()
+    assert same(out["acc"])
+    pageable = s.solve_particles_host(torch.from_numpy(pos.copy()), N0, box)
+    assert same(pageable["acc"])
+    A = oracle.AMR(pos, N0, box, 2, 8)
+    A.deposit()
+    A.set_model(fr0)
+    rc, _ = A.solve(tol=1e-11, max_vcycles=300)
+    assert rc == 0
+    acc_ref = A.particle_force()
+    tol = 1e-6 if prec == mgfr.PREC_FP64 else 1e-5
+    assert np.abs(out["acc"].numpy() - acc_ref).max() / np.abs(acc_ref).max() <= tol
+    with pytest.raises(mgfr.MGFRError) as ei:
+        s.solve_particles_host(host, 12, box)  # base size not a power of two
+    assert ei.value.status == mgfr.MGFR_E_INVALID
+    s.close()
