@@ -247,7 +247,16 @@ __global__ void k_oct_nbrs(long long n_oct, int l, TreeView T, int* __restrict__
 // cell does not exist goes to the deepest existing ancestor, a leaf.
 struct LevelPtrs {
   double* a[AMR_MAXL];  // per-level array (mass for deposit)
+  // the deposit's record of each particle's cells for the FP32 gather (NULL:
+  // none): 8 slots per particle (its cube's corners q = 4 bx + 2 by + bz),
+  // cell level << 27 | index; slot q of particle p at q np + p
+  int* rec_idx;
+  long long np;
 };
+
+// record slot values: a zero-width corner, and (slot 0) a particle whose cube
+// splits over finer cells (its pieces are not recorded)
+constexpr int kRecSkip = 0x7fffffff, kRecSplit = -1;
 
 struct GatherPtrs {
   const double* acc[AMR_MAXL];    // FP64: level 0 [3][N0^3]; l >= 1 [ncell][3]
@@ -363,9 +372,16 @@ __device__ __forceinline__ void split_q(const TreeView& T, int l, long long c, c
   }
 }
 
+// Visits the pieces of particle p's cube (deposit: adds the weights; gather:
+// sums weight x force).  Returns whether the cube split over finer cells.
 template <bool GATHER, class W>
-__device__ void visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, const GatherPtrs& G,
-                               W* out, unsigned long long* err) {
+__device__ bool visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, const GatherPtrs& G,
+                               W* out, unsigned long long* err, long long p = 0) {
+  const bool rec = !GATHER && D.rec_idx;
+  bool split = false;
+  // the record's slots, written out together after the traversal (whole
+  // warps, coalesced) rather than from the divergent corner paths
+  int ri[8];
   const long long X[3] = {qfix(t.x), qfix(t.y), qfix(t.z)};
   // leaf level lam of the particle and the oct holding its leaf cell
   int lam = 0, own = -1;
@@ -404,8 +420,10 @@ __device__ void visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
   for (int q = 0; q < 8; ++q) {
     const int bits[3] = {(q >> 2) & 1, (q >> 1) & 1, q & 1};
     if ((bits[0] && edge[0] == cl[0] + one) || (bits[1] && edge[1] == cl[1] + one) ||
-        (bits[2] && edge[2] == cl[2] + one))
+        (bits[2] && edge[2] == cl[2] + one)) {
+      ri[q] = kRecSkip;
       continue;  // zero-width piece
+    }
     const long long K[3] = {i0[0] + bits[0], i0[1] + bits[1], i0[2] + bits[2]};
     int lev;
     long long cq;
@@ -419,9 +437,13 @@ __device__ void visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
     }
     const bool refined = lev == lam && lam + 1 < T.nlev && T.son[lam][cq] >= 0;
     if (!refined) {
-      touch<GATHER, W>(lev, cq, Lxy[(bits[0] << 1) | bits[1]] * Lw[2][bits[2]], D, G, out);
+      const W w = Lxy[(bits[0] << 1) | bits[1]] * Lw[2][bits[2]];
+      touch<GATHER, W>(lev, cq, w, D, G, out);
+      ri[q] = (lev << 27) | (int)cq;
       continue;
     }
+    split = true;
+    ri[q] = kRecSkip;
     long long lo[3], hi[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -435,15 +457,51 @@ __device__ void visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
     const StackEnt e = st[--sp];
     split_q<GATHER, W, 1>(T, e.l, e.c, e.lo, e.hi, F, scale, D, G, out, st, sp, err);
   }
+  if (rec) {
+    if (split) ri[0] = kRecSplit;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) D.rec_idx[q * D.np + p] = ri[q];
+  }
+  return split;
 }
 
+// With a record (D.rec_idx), the particles whose cube split are appended to
+// the list of their chunk (chunk = p / per, its list at split_list + chunk per,
+// counted in n_split[chunk]; one atomic per block, any order within the
+// chunk).  Launched with 256 threads; per = 256 bpc, so a block lies in one
+// chunk (a 32-bit division: a 64-bit one would be a call, which costs the
+// traversal registers).
 __global__ void __launch_bounds__(256, 4) k_deposit(const double* __restrict__ pos, long long Np, double inv, double N0,
-                          TreeView T, LevelPtrs D, unsigned long long* err) {
+                          TreeView T, LevelPtrs D, unsigned long long* err,
+                          int* __restrict__ split_list, unsigned long long* __restrict__ n_split,
+                          unsigned bpc) {
+  __shared__ int woff[8];
+  __shared__ unsigned long long bbase;
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (p >= Np) return;
-  const P3 t = particle_t(pos, p, inv, N0);
-  GatherPtrs G{};
-  visit_particle<false, double>(T, t, D, G, nullptr, err);
+  bool split = false;
+  if (p < Np) {
+    const P3 t = particle_t(pos, p, inv, N0);
+    GatherPtrs G{};
+    split = visit_particle<false, double>(T, t, D, G, nullptr, err, p);
+  }
+  if (!D.rec_idx) return;  // uniform over the launch
+  // whole blocks reach here (no early exit above)
+  const unsigned b = __ballot_sync(0xffffffffu, split);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) woff[w] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int v = 0; v < 8; ++v) {
+      const int k = woff[v];
+      woff[v] = run;
+      run += k;
+    }
+    const unsigned q = blockIdx.x / bpc;
+    bbase = 256ULL * bpc * q + (run > 0 ? atomicAdd(n_split + q, (unsigned long long)run) : 0ULL);
+  }
+  __syncthreads();
+  if (split) split_list[bbase + woff[w] + __popc(b & ((1u << lane) - 1u))] = (int)p;
 }
 
 __global__ void k_gather(const double* __restrict__ pos, long long Np, double inv, double N0,
@@ -470,6 +528,79 @@ __global__ void __launch_bounds__(256, 4) k_gather32(const double* __restrict__ 
   LevelPtrs D{};
   float out[3] = {0.f, 0.f, 0.f};
   visit_particle<true, float>(T, t, D, G, out, err);
+  acc[3 * p] = out[0];
+  acc[3 * p + 1] = out[1];
+  acc[3 * p + 2] = out[2];
+}
+
+// mixed form, from the deposit's record: the cells of each particle's cube
+// are read from the record instead of found by walking the tree; the FP32
+// weights and the sum are those of the traversal (same arithmetic, same
+// order).  The particle's leaf level is the deepest recorded level (its leaf
+// cell is one of the corners).  Particles whose cube split are left to
+// k_gather32_list.  Particles p0 .. p0 + n - 1; np: the record's slot stride.
+__global__ void __launch_bounds__(256) k_gather32_rec(const double* __restrict__ pos,
+                                                      const int* __restrict__ rec_idx,
+                                                      long long np, long long p0, long long n,
+                                                      double inv, double N0, GatherPtrs G,
+                                                      double* __restrict__ acc) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const long long p = p0 + t;
+  int id[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) id[q] = __ldg(rec_idx + q * np + p);
+  if (id[0] == kRecSplit) return;
+  int lam = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (id[q] != kRecSkip) lam = max(lam, id[q] >> 27);
+  const P3 tp = particle_t(pos, p, inv, N0);
+  const long long X[3] = {qfix(tp.x), qfix(tp.y), qfix(tp.z)};
+  const int F = QB - lam;
+  const long long one = 1LL << F;
+  float Lw[3][2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const long long cl = X[a] - (one >> 1);
+    const long long edge = ((cl >> F) + 1) * one;
+    Lw[a][0] = Wt<float>::len(edge - cl, F);
+    Lw[a][1] = Wt<float>::len(cl + one - edge, F);
+  }
+  const float scale = Wt<float>::scale(F);
+  Lw[0][0] *= scale;
+  Lw[0][1] *= scale;
+  float Lxy[4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) Lxy[b] = Lw[0][b >> 1] * Lw[1][b & 1];
+  float out[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (id[q] == kRecSkip) continue;
+    const float w = Lxy[q >> 1] * Lw[2][q & 1];
+    const float4 a = __ldg(G.acc32[id[q] >> 27] + (id[q] & ((1 << 27) - 1)));
+    out[0] = fmaf(w, a.x, out[0]);
+    out[1] = fmaf(w, a.y, out[1]);
+    out[2] = fmaf(w, a.z, out[2]);
+  }
+  acc[3 * p] = out[0];
+  acc[3 * p + 1] = out[1];
+  acc[3 * p + 2] = out[2];
+}
+
+// mixed form, the listed particles (those whose cube split): full traversal
+__global__ void __launch_bounds__(256, 4) k_gather32_list(const double* __restrict__ pos,
+                                                          const int* __restrict__ list, long long n,
+                                                          double inv, double N0, TreeView T,
+                                                          GatherPtrs G, double* __restrict__ acc,
+                                                          unsigned long long* err) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const long long p = list[t];
+  const P3 tp = particle_t(pos, p, inv, N0);
+  LevelPtrs D{};
+  float out[3] = {0.f, 0.f, 0.f};
+  visit_particle<true, float>(T, tp, D, G, out, err);
   acc[3 * p] = out[0];
   acc[3 * p + 1] = out[1];
   acc[3 * p + 2] = out[2];
@@ -651,6 +782,9 @@ void amr_free(mgfr_ctx* c) {
   if (A->acc0_32) cudaFree(A->acc0_32);
   if (A->pos_dev) cudaFree(A->pos_dev);
   if (A->acc_dev) cudaFree(A->acc_dev);
+  if (A->rec_idx) cudaFree(A->rec_idx);
+  if (A->split_list) cudaFree(A->split_list);
+  if (A->d_split) cudaFree(A->d_split);
   delete A;
   c->amr = nullptr;
 }
@@ -813,16 +947,43 @@ static mgfr_status build_structure(mgfr_ctx* c, AmrWork* A, const double* pos) {
   return MGFR_OK;
 }
 
-static mgfr_status deposit(mgfr_ctx* c, AmrWork* A, const double* pos) {
+// record: keep each particle's cells for the FP32 gather (cell indices must
+// fit the record's 27 bits), with the split particles listed per chunk of
+// `per` particles (per a multiple of 256, at most 8 chunks)
+static mgfr_status deposit(mgfr_ctx* c, AmrWork* A, const double* pos, bool record,
+                           long long per) {
   const double inv = (double)A->N0 / A->box, N0d = (double)A->N0;
   LevelPtrs D{};
   for (int l = 0; l < A->nlev; ++l) {
     MG_CK(c, cudaMemsetAsync(A->L[l].mass, 0, sizeof(double) * (size_t)A->L[l].ncell, c->s));
     D.a[l] = A->L[l].mass;
+    if (A->L[l].ncell > (1LL << 27)) record = false;
+  }
+  A->rec_on = record;
+  A->rec_per = per;
+  for (auto& n : A->n_split) n = 0;
+  if (record) {
+    if (!A->d_split) MG_CK(c, cudaMalloc(&A->d_split, sizeof(long long) * 8));
+    MG_CK(c, cudaMemsetAsync(A->d_split, 0, sizeof(long long) * 8, c->s));
+    if (A->Np > A->rec_cap) {
+      if (A->rec_idx) cudaFree(A->rec_idx);
+      if (A->split_list) cudaFree(A->split_list);
+      A->rec_idx = nullptr;
+      A->split_list = nullptr;
+      A->rec_cap = 0;
+      MG_CK(c, cudaMalloc(&A->rec_idx, sizeof(int) * 8 * (size_t)A->Np));
+      MG_CK(c, cudaMalloc(&A->split_list, sizeof(int) * 8 * (size_t)((A->Np + 7) / 8 + 256)));
+      A->rec_cap = A->Np;
+    }
+    D.rec_idx = A->rec_idx;
+    D.np = A->Np;
   }
   TreeView T = tree_view(A);
   k_deposit<<<nblocks(A->Np, BS), BS, 0, c->s>>>(pos, A->Np, inv, N0d, T, D,
-                                                 (unsigned long long*)(A->d_small + 1));
+                                                 (unsigned long long*)(A->d_small + 1),
+                                                 A->split_list,
+                                                 (unsigned long long*)A->d_split,
+                                                 (unsigned)(per / 256));
   c->launches += 1;
   for (int l = A->nlev - 1; l >= 1; --l) {
     k_mass_up<<<nblocks(A->L[l].n_oct, BS), BS, 0, c->s>>>(A->L[l].mass, A->L[l].n_oct,
@@ -910,7 +1071,11 @@ static mgfr_status solve_particles(mgfr_ctx* c, const double* pos, long long Np,
   c->launches += 1;
   // structure, deposit, sources
   TRY(build_structure(c, A, pos));
-  TRY(deposit(c, A, pos));
+  // the FP32 gather of the mixed form replays the deposit's record; with a
+  // host destination it runs (and is copied back) in 8 chunks
+  const int nch = acc_host ? 8 : 1;
+  const long long per = ((Np + nch - 1) / nch + 255) / 256 * 256;
+  TRY(deposit(c, A, pos, mixed && acc_out, per));
   const Model m = make_model(g, a);
   for (int l = 0; l < A->nlev; ++l) {
     AmrLevel& L = A->L[l];
@@ -922,6 +1087,9 @@ static mgfr_status solve_particles(mgfr_ctx* c, const double* pos, long long Np,
   }
   long long flags = 0;
   MG_CK(c, cudaMemcpyAsync(&flags, A->d_small + 1, sizeof(long long), cudaMemcpyDeviceToHost, c->s));
+  if (A->rec_on)
+    MG_CK(c, cudaMemcpyAsync(A->n_split, A->d_split, sizeof(long long) * 8,
+                             cudaMemcpyDeviceToHost, c->s));
   MG_CK(c, cudaStreamSynchronize(c->s));
   if (flags & 2) return set_err(c, MGFR_E_INVALID, "non-finite particle position");
   if (flags & 1) return set_err(c, MGFR_E_UNSUPPORTED, "cloud-in-cell split stack overflow");
@@ -979,14 +1147,24 @@ static mgfr_status solve_particles(mgfr_ctx* c, const double* pos, long long Np,
   }
   if (acc_out) {
     TreeView T = tree_view(A);
-    // with a host destination: chunks, each copied back on the copy stream
-    // while the next one is gathered
-    const int nch = acc_host ? 8 : 1;
-    const long long per = (Np + nch - 1) / nch;
+    // FP32 gather from the deposit's record, per chunk: the particles whose
+    // cube split (full traversal), then the rest from their recorded cells.
+    // With a host destination each chunk is copied back on the copy stream
+    // while the next one is gathered.
+    const bool replay = g32 && A->rec_on;
     for (int q = 0; q < nch; ++q) {
       const long long p0 = q * per, n = std::min(per, Np - p0);
       if (n <= 0) break;
-      if (g32)
+      if (replay && A->n_split[q] > 0) {
+        k_gather32_list<<<nblocks(A->n_split[q], BS), BS, 0, c->s>>>(
+            pos, A->split_list + q * per, A->n_split[q], (double)N0 / box, (double)N0, T, G,
+            acc_out, (unsigned long long*)(A->d_small + 1));
+        c->launches += 1;
+      }
+      if (replay)
+        k_gather32_rec<<<nblocks(n, BS), BS, 0, c->s>>>(pos, A->rec_idx, Np, p0, n,
+                                                        (double)N0 / box, (double)N0, G, acc_out);
+      else if (g32)
         k_gather32<<<nblocks(n, BS), BS, 0, c->s>>>(pos + 3 * p0, n, (double)N0 / box, (double)N0,
                                                     T, G, acc_out + 3 * p0,
                                                     (unsigned long long*)(A->d_small + 1));

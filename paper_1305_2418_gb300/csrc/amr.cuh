@@ -115,6 +115,13 @@ struct AmrWork {
   float4* acc0_32 = nullptr;          // base force, FP32 (x, y, z, 0) per cell
   double *pos_dev = nullptr, *acc_dev = nullptr;  // particle arrays of the host-buffer call
   long long pio_cap = 0;                          // their capacity (particles)
+  // the deposit's record for the FP32 gather (mixed form): the 8 cells of
+  // each particle's cube, and the particles whose cube split over finer cells
+  int* rec_idx = nullptr;
+  int* split_list = nullptr;                      // per chunk q at q rec_per
+  long long* d_split = nullptr;                   // [8] split particles per chunk
+  long long rec_cap = 0, rec_per = 0, n_split[8] = {};
+  bool rec_on = false;                            // the last deposit recorded
   long long cap_cells[AMR_MAXL] = {}; // allocated capacity per level (cells)
   long long cap_oct[AMR_MAXL] = {};
 };
