@@ -35,8 +35,7 @@ UNIT = "cell-updates/s"
 WORKLOAD = dict(name="particles256", N=256, box=100.0, a=1.0, fr0=1e-5, sigma_g=1.5, seed=2002,
                 lmax=2, nbar=1.0, refine_count=8)
 
-# Algorithmic bytes per cell of one launch, per profiled kernel family
-# ("Kernels and rooflines"):
+# Algorithmic bytes per cell of one launch, per profiled kernel family:
 #  0 FP32 NGS half-sweep: read u (4) + f of the active colour (2) + write the
 #    active u (2)                                   = 8 B per cell of the level
 #  1 FP32 linear GS half-sweep: read u32 (4) + e (4) + r active (2) + write e

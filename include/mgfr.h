@@ -51,7 +51,7 @@ typedef enum {
   MGFR_E_OOM = 3,         /* device workspace allocation failed           */
   MGFR_E_NOCONVERGE = 4,  /* max_vcycles reached; outputs hold last iterate */
   MGFR_E_TIMEOUT = 5,     /* a bounded device wait gave up                */
-  MGFR_E_UNSUPPORTED = 6  /* feature not available in this build           */
+  MGFR_E_UNSUPPORTED = 6  /* case the library does not handle               */
 } mgfr_status;
 
 typedef enum { MGFR_PREC_FP64 = 0, MGFR_PREC_MIXED = 1 } mgfr_precision;

@@ -29,7 +29,7 @@
  *   - f_R = fR_bar e^u and the extra force (c^2/2) grad f_R [Sec. 2,
  *     eq. modgrav_accel], on cells and interpolated back to particles.
  *
- * Readings where the paper is silent (each one is listed in the design doc):
+ * Readings where the paper is silent:
  *   - dL/du is the full derivative of the discrete L_i w.r.t. u_i with the
  *     neighbours fixed; the Newton step is clamped to |du| <= step_cap (the
  *     clamp changes the path, never the fixed point);
