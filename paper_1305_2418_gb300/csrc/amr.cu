@@ -372,16 +372,15 @@ __device__ __forceinline__ void split_q(const TreeView& T, int l, long long c, c
   }
 }
 
-// Visits the pieces of particle p's cube (deposit: adds the weights; gather:
+// Visits the pieces of a particle's cube (deposit: adds the weights; gather:
 // sums weight x force).  Returns whether the cube split over finer cells.
+// ri (deposit with a record): the record's 8 slots, which the caller stores
+// once its warp has reconverged (whole-warp, coalesced stores).
 template <bool GATHER, class W>
 __device__ bool visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, const GatherPtrs& G,
-                               W* out, unsigned long long* err, long long p = 0) {
+                               W* out, unsigned long long* err, int* ri = nullptr) {
   const bool rec = !GATHER && D.rec_idx;
   bool split = false;
-  // the record's slots, written out together after the traversal (whole
-  // warps, coalesced) rather than from the divergent corner paths
-  int ri[8];
   const long long X[3] = {qfix(t.x), qfix(t.y), qfix(t.z)};
   // leaf level lam of the particle and the oct holding its leaf cell
   int lam = 0, own = -1;
@@ -421,7 +420,7 @@ __device__ bool visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
     const int bits[3] = {(q >> 2) & 1, (q >> 1) & 1, q & 1};
     if ((bits[0] && edge[0] == cl[0] + one) || (bits[1] && edge[1] == cl[1] + one) ||
         (bits[2] && edge[2] == cl[2] + one)) {
-      ri[q] = kRecSkip;
+      if (rec) ri[q] = kRecSkip;
       continue;  // zero-width piece
     }
     const long long K[3] = {i0[0] + bits[0], i0[1] + bits[1], i0[2] + bits[2]};
@@ -439,11 +438,11 @@ __device__ bool visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
     if (!refined) {
       const W w = Lxy[(bits[0] << 1) | bits[1]] * Lw[2][bits[2]];
       touch<GATHER, W>(lev, cq, w, D, G, out);
-      ri[q] = (lev << 27) | (int)cq;
+      if (rec) ri[q] = (lev << 27) | (int)cq;
       continue;
     }
     split = true;
-    ri[q] = kRecSkip;
+    if (rec) ri[q] = kRecSkip;
     long long lo[3], hi[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -457,11 +456,7 @@ __device__ bool visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
     const StackEnt e = st[--sp];
     split_q<GATHER, W, 1>(T, e.l, e.c, e.lo, e.hi, F, scale, D, G, out, st, sp, err);
   }
-  if (rec) {
-    if (split) ri[0] = kRecSplit;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) D.rec_idx[q * D.np + p] = ri[q];
-  }
+  if (rec && split) ri[0] = kRecSplit;
   return split;
 }
 
@@ -479,14 +474,19 @@ __global__ void __launch_bounds__(256, 4) k_deposit(const double* __restrict__ p
   __shared__ unsigned long long bbase;
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   bool split = false;
+  int ri[8];
   if (p < Np) {
     const P3 t = particle_t(pos, p, inv, N0);
     GatherPtrs G{};
-    split = visit_particle<false, double>(T, t, D, G, nullptr, err, p);
+    split = visit_particle<false, double>(T, t, D, G, nullptr, err, ri);
   }
   if (!D.rec_idx) return;  // uniform over the launch
   // whole blocks reach here (no early exit above)
   const unsigned b = __ballot_sync(0xffffffffu, split);
+  if (p < Np) {  // the warp has reconverged at the ballot: full-sector stores
+#pragma unroll
+    for (int q = 0; q < 8; ++q) D.rec_idx[q * D.np + p] = ri[q];
+  }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) woff[w] = __popc(b);
   __syncthreads();
