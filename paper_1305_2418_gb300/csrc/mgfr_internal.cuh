@@ -32,24 +32,6 @@ struct Model {
 
 Model make_model(const mgfr_config& cfg, double a);
 
-#ifdef __CUDACC__
-// e^(w + d) from E = e^w after an additive correction d of the iterate:
-// E e^d, with e^d from its Taylor series through d^5/5! when |d| < 2^-10
-// (the omitted terms are below |d|^6/6! < 2e-21 relative), else e^(w + d)
-// evaluated directly.  Keeps E consistent with w to a few ulp for the FP64
-// residual at a fraction of the cost of an FP64 exp per cell.
-__device__ __forceinline__ double exp_after_step(double E, double w_new, double d) {
-  if (fabs(d) < 0x1p-10) {
-    double p = fma(d, 1.0 / 120.0, 1.0 / 24.0);
-    p = fma(p, d, 1.0 / 6.0);
-    p = fma(p, d, 0.5);
-    p = fma(p, d, 1.0);
-    p = fma(p, d, 1.0);
-    return E * p;
-  }
-  return exp(w_new);
-}
-#endif
 
 // One dense periodic level of the multigrid hierarchy (N = 2^lg).
 struct DenseLevel {
