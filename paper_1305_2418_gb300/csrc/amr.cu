@@ -75,11 +75,14 @@ __device__ __forceinline__ long long qfix(double t) {
   return e > -53 ? sig >> -e : 0;  // also t = +-0 and subnormals: 0
 }
 
-// v as a double for 0 <= v <= 2^52 (exact): 2^52 + v has v as its significand
-// bits, one FP64 subtraction removes the 2^52
-__device__ __forceinline__ double exact_i2d(long long v) {
-  return v == (1LL << 52) ? 4503599627370496.0
-                          : __longlong_as_double(v | 0x4330000000000000LL) - 4503599627370496.0;
+// v as a double for 0 <= v <= 2^52 (exact), built on the integer pipes: the
+// leading bit gives the exponent, the bits below it the significand
+// (times 2^k, exact while the result is a normal number)
+__device__ __forceinline__ double exact_i2d(long long v, int k = 0) {
+  if (v == 0) return 0.0;
+  const int e = 63 - __clzll(v);  // v in [2^e, 2^(e+1)), e <= 52
+  const unsigned long long m = ((unsigned long long)v << (52 - e)) & 0xfffffffffffffULL;
+  return __longlong_as_double((long long)(((unsigned long long)(e + k + 1023) << 52) | m));
 }
 
 // ---- structure kernels -----------------------------------------------------
@@ -265,8 +268,8 @@ struct GatherPtrs {
 };
 
 // Weight arithmetic of the traversal.  double: the integer overlap lengths
-// exactly, one scale 2^(-3F) to the fraction of the cube (deposit and the
-// FP64 gather).  float (gather of the mixed form): the top 24 bits of each
+// exactly, the scale 2^(-3F) to the fraction of the cube in the exponent of
+// the x lengths (deposit and the FP64 gather).  float (gather of the mixed form): the top 24 bits of each
 // length relative to the cube side 2^F, scale 2^-72; the weights then carry
 // a relative error of about 2^-24.
 template <class W>
@@ -274,8 +277,10 @@ struct Wt;
 template <>
 struct Wt<double> {
   static __device__ __forceinline__ double len(long long v, int) { return exact_i2d(v); }
-  static __device__ __forceinline__ double scale(int F) {
-    return __longlong_as_double((long long)(1023 - 3 * F) << 52);
+  // len(v) 2^(-3F), the scale entering the exponent (exact: v = 0, or v >= 1 and
+  // the result >= 2^-156, a normal number)
+  static __device__ __forceinline__ double len_scaled(long long v, int F) {
+    return exact_i2d(v, -3 * F);
   }
 };
 template <>
@@ -284,6 +289,9 @@ struct Wt<float> {
     return (float)(int)((v + (1LL << (F - 25))) >> (F - 24));  // rounded to nearest
   }
   static __device__ __forceinline__ float scale(int) { return 0x1p-72f; }
+  static __device__ __forceinline__ float len_scaled(long long v, int F) {
+    return len(v, F) * scale(F);
+  }
 };
 
 template <bool GATHER, class W>
@@ -324,7 +332,7 @@ struct StackEnt {
 // size is static.
 template <bool GATHER, class W, int DEPTH>
 __device__ __forceinline__ void split_q(const TreeView& T, int l, long long c, const long long* lo,
-                                        const long long* hi, int F, W scale, LevelPtrs& D,
+                                        const long long* hi, int F, LevelPtrs& D,
                                         const GatherPtrs& G, W* out, StackEnt* st, int& sp,
                                         unsigned long long* err) {
   const int o = T.son[l][c];
@@ -339,10 +347,10 @@ __device__ __forceinline__ void split_q(const TreeView& T, int l, long long c, c
     clo[a][1] = max(lo[a], mid);
     chi[a][1] = hi[a];
 #pragma unroll
-    for (int b = 0; b < 2; ++b) len[a][b] = Wt<W>::len(chi[a][b] - clo[a][b], F);
+    for (int b = 0; b < 2; ++b)  // the fraction of the cube enters through axis 0
+      len[a][b] = a == 0 ? Wt<W>::len_scaled(chi[a][b] - clo[a][b], F)
+                         : Wt<W>::len(chi[a][b] - clo[a][b], F);
   }
-  len[0][0] *= scale;
-  len[0][1] *= scale;
   for (int ch = 0; ch < 8; ++ch) {
     const int b0 = (ch >> 2) & 1, b1 = (ch >> 1) & 1, b2 = ch & 1;
     if (chi[0][b0] <= clo[0][b0] || chi[1][b1] <= clo[1][b1] || chi[2][b2] <= clo[2][b2]) continue;
@@ -355,7 +363,7 @@ __device__ __forceinline__ void split_q(const TreeView& T, int l, long long c, c
     const long long nlo[3] = {clo[0][b0], clo[1][b1], clo[2][b2]};
     const long long nhi[3] = {chi[0][b0], chi[1][b1], chi[2][b2]};
     if constexpr (DEPTH > 1) {
-      split_q<GATHER, W, DEPTH - 1>(T, lc, cc, nlo, nhi, F, scale, D, G, out, st, sp, err);
+      split_q<GATHER, W, DEPTH - 1>(T, lc, cc, nlo, nhi, F, D, G, out, st, sp, err);
     } else {
       if (sp < 48) {
         StackEnt& n = st[sp++];
@@ -399,17 +407,16 @@ __device__ bool visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
   long long cl[3], i0[3], edge[3];
   W Lw[3][2];
   // fixed-point volume -> fraction of the cube
-  const W scale = Wt<W>::scale(F);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     cl[a] = X[a] - (one >> 1);
     i0[a] = cl[a] >> F;
     edge[a] = (i0[a] + 1) * one;  // boundary between the two cells the cube spans
-    Lw[a][0] = Wt<W>::len(edge[a] - cl[a], F);
-    Lw[a][1] = Wt<W>::len(cl[a] + one - edge[a], F);
+    // the fraction of the cube (scale) enters through axis 0
+    Lw[a][0] = a == 0 ? Wt<W>::len_scaled(edge[a] - cl[a], F) : Wt<W>::len(edge[a] - cl[a], F);
+    Lw[a][1] = a == 0 ? Wt<W>::len_scaled(cl[a] + one - edge[a], F)
+                      : Wt<W>::len(cl[a] + one - edge[a], F);
   }
-  Lw[0][0] *= scale;
-  Lw[0][1] *= scale;
   // x-y products of the corner weights, shared by the two z pieces
   W Lxy[4];
 #pragma unroll
@@ -449,12 +456,12 @@ __device__ bool visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
       lo[a] = bits[a] ? edge[a] : cl[a];
       hi[a] = bits[a] ? cl[a] + one : edge[a];
     }
-    split_q<GATHER, W, 2>(T, lam, cq, lo, hi, F, scale, D, G, out, st, sp, err);
+    split_q<GATHER, W, 2>(T, lam, cq, lo, hi, F, D, G, out, st, sp, err);
   }
   // pieces refined three or more levels below the particle's leaf
   while (sp > 0) {
     const StackEnt e = st[--sp];
-    split_q<GATHER, W, 1>(T, e.l, e.c, e.lo, e.hi, F, scale, D, G, out, st, sp, err);
+    split_q<GATHER, W, 1>(T, e.l, e.c, e.lo, e.hi, F, D, G, out, st, sp, err);
   }
   if (rec && split) ri[0] = kRecSplit;
   return split;
