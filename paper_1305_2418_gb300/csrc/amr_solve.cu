@@ -20,6 +20,7 @@
 #include <type_traits>
 
 #include "amr.cuh"
+#include "colour_split.cuh"
 #include "dfloat.cuh"
 
 namespace {
@@ -646,19 +647,9 @@ __global__ void k_zero32(float* __restrict__ x, long long n) {
 
 
 // ---- FP32 storage of oct levels -------------------------------------------
-// The FP32 arrays of an oct level (u, f or r, e) are stored by colour: plane k
-// (k = 0, 1) holds, for every oct o, the four cells of colour k as one float4
-// at floats (k n_oct + o) 4.  The colour is the parity of the child-index bits
-// (the red-black colour of the sweeps; parent coordinates contribute an even
-// amount), and a cell's place in its float4 is ch >> 1 (colour 0: children
-// 0, 3, 5, 6; colour 1: 1, 2, 4, 7).  A half-sweep then moves whole 16-byte
-// vectors of the colour it reads or writes.  n_oct = 0 marks a dense level
-// (C order).
-__device__ __forceinline__ long long pidx(long long c, long long n_oct) {
-  if (n_oct == 0) return c;
-  const int ch = (int)(c & 7);
-  return (((long long)(__popc(ch) & 1) * n_oct + (c >> 3)) << 2) + (ch >> 1);
-}
+// The FP32 arrays of an oct level (u, f or r, e) are stored by colour
+// (colour_split.cuh, pidx): one float4 per colour and oct, so that a
+// half-sweep moves whole 16-byte vectors of the colour it reads or writes.
 
 struct Oct8 {
   float v[8];

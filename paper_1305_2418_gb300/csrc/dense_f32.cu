@@ -13,6 +13,7 @@
 // nonlinear FP32 correction.
 #include <algorithm>
 
+#include "colour_split.cuh"
 #include "dfloat.cuh"
 #include "mgfr_internal.cuh"
 
@@ -33,42 +34,9 @@ __host__ __device__ inline ModelF to_f(const Model& m) {
   return ModelF{(float)m.aRt, (float)m.aRt_np1, (float)m.inv_np1};
 }
 
-// ---- colour-split storage of the FP32 arrays ----------------------------------
-// Every FP32 array of a dense level (u, f, u_old, e, r) is stored by colour:
-// plane q = (i + j + k) & 1 holds the cells of that red-black colour, in C
-// order of (i, j, k >> 1).  The six neighbours of a cell all lie in the other
-// plane, four of them at the same (k >> 1) in neighbouring rows and two in
-// the same row (at k >> 1 and one step along it).  A half-sweep then reads
-// one plane, reads and writes the other, each in whole coalesced rows.
-__device__ __forceinline__ unsigned prow(int i, int j, int lg) {
-  return (((unsigned)i << lg) + (unsigned)j) << (lg - 1);
-}
-// colour-split index of (i, j, k), each in [0, N)
-__device__ __forceinline__ unsigned pdx(int i, int j, int k, int lg) {
-  return ((unsigned)((i + j + k) & 1) << (3 * lg - 1)) + prow(i, j, lg) + ((unsigned)k >> 1);
-}
-// cell of colour-split index t
-__device__ __forceinline__ void pcell(unsigned t, int lg, int* i, int* j, int* k) {
-  const int M = (1 << lg) - 1;
-  const unsigned q = t >> (3 * lg - 1);
-  const unsigned p = t & ((1u << (3 * lg - 1)) - 1u);
-  *i = (int)(p >> (2 * lg - 1));
-  *j = (int)((p >> (lg - 1)) & M);
-  *k = 2 * (int)(p & (M >> 1)) + (int)((q + *i + *j) & 1);
-}
-// colour-split indices of the six neighbours (-x, +x, -y, +y, -z, +z)
-__device__ __forceinline__ void pnb6(int i, int j, int k, int lg, unsigned* q) {
-  const int M = (1 << lg) - 1, hm = M >> 1;
-  const unsigned ob = (unsigned)((i + j + k + 1) & 1) << (3 * lg - 1);
-  const int kh = k >> 1;
-  q[0] = ob + prow((i - 1) & M, j, lg) + kh;
-  q[1] = ob + prow((i + 1) & M, j, lg) + kh;
-  q[2] = ob + prow(i, (j - 1) & M, lg) + kh;
-  q[3] = ob + prow(i, (j + 1) & M, lg) + kh;
-  const unsigned r = ob + prow(i, j, lg);
-  q[4] = r + ((k & 1) ? kh : ((kh - 1) & hm));
-  q[5] = r + ((k & 1) ? ((kh + 1) & hm) : kh);
-}
+// The FP32 arrays of a dense level (u, f, u_old, e, r) are stored by colour
+// (colour_split.cuh): a half-sweep reads one plane, reads and writes the
+// other, each in whole coalesced rows.
 
 // ---- Phase A: nonlinear FP32 Newton-Gauss-Seidel half-sweep ----------------
 // Thread = one cell of the active colour (plane `colour`, index t in it).
