@@ -63,8 +63,10 @@ def test_default_config_and_validation(lib):
     assert cfg.omega_m == 0.3 and cfg.fr0_abs == 1e-5 and cfg.n == 1
     assert cfg.tol_rel == 1e-8 and cfg.n_pre == 2 and cfg.n_post == 2
     assert lib.mgfr_version().decode().startswith("mgfr")
+    assert cfg.n_coarse == 0 and cfg.mixed_inner == 3 and cfg.mask_thres == 0.99
     bad = [dict(fr0_abs=0.0), dict(n=0), dict(tol_rel=2.0), dict(n_pre=0, n_post=0),
-           dict(precision=7), dict(omega_m=-1.0), dict(step_cap=0.0)]
+           dict(precision=7), dict(omega_m=-1.0), dict(step_cap=0.0), dict(n_coarse=-1),
+           dict(n_coarse=17), dict(mixed_inner=0), dict(mask_thres=1.0)]
     for kw in bad:
         c = mgfr.default_config(**kw)
         h = C.c_void_p()
@@ -72,4 +74,9 @@ def test_default_config_and_validation(lib):
         assert st == mgfr.MGFR_E_INVALID, kw
         assert not h.value
     assert lib.mgfr_last_error(None) == b"NULL context"
+    # entry points reject a NULL context before touching any device state
+    assert lib.mgfr_solve_particles(None, None, 1, 16, 1.0, 1.0, None, None, None, None) == \
+        mgfr.MGFR_E_INVALID
+    assert lib.mgfr_solve_particles_host(None, None, 1, 16, 1.0, 1.0, None, None, None,
+                                         None) == mgfr.MGFR_E_INVALID
     lib.mgfr_destroy(None)
