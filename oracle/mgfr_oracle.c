@@ -104,6 +104,23 @@ void orc_model_constants(double omega_m, double fr0_abs, int n, double a, double
   out4[3] = m.src;
 }
 
+/*
+ * Effective mass density [Sec. 2.4, eqs. phi_poisson_eq_with_eff_mass and
+ * effective_density]: delta rho_eff = delta rho / 3 - delta R / (24 pi G),
+ * with delta R = R_bar ((fR_bar / f_R)^{1/(n+1)} - 1) [eq. dR_fR, general n
+ * by eq. fR-R,n_relation] = R_bar (e^{-u/(n+1)} - 1).  In units of the mean
+ * matter density, with R_bar = 3 H0^2 Rt and 24 pi G rho_bar = 9 H0^2 Om a^-3:
+ *     delta_eff = delta / 3 + Rt / (3 Om a^-3) (1 - e^{-u/(n+1)}).
+ * Per cell of any level (u, delta, out: n values).
+ */
+void orc_effective_density(long long ncell, const double* u, const double* delta,
+                           double omega_m, double fr0_abs, int n, double a, double* out) {
+  orc_model m = model_make(omega_m, fr0_abs, n, a);
+  const double rho = omega_m / (a * a * a);
+  for (long long c = 0; c < ncell; ++c)
+    out[c] = delta[c] / 3.0 + m.Rt / (3.0 * rho) * (1.0 - exp(-u[c] / (m.n + 1)));
+}
+
 /* ------------------------------------------------------------------------ */
 /* Dense periodic grids (the levels that cover the whole box).              */
 /* Layout: C order a[i][j][k], i along x (slowest), k along z (fastest).    */

@@ -43,6 +43,7 @@ def lib():
             P = C.POINTER
             sig = {
                 "orc_model_constants": (None, [d, d, i, d, vp]),
+                "orc_effective_density": (None, [ll, vp, vp, d, d, i, d, vp]),
                 "orc_solve_dense": (i, [i, d, vp, d, d, i, d, vp, d, i, i, i, i, d, vp]),
                 "orc_solve_dense_f": (i, [i, d, vp, d, d, i, d, vp, d, i, i, i, i, d, vp]),
                 "orc_residual_dense": (None, [i, d, vp, d, d, i, d, vp, vp]),
@@ -99,6 +100,18 @@ def model_constants(fr0_abs: float, a: float = 1.0, n: int = 1, omega_m: float =
     out = np.zeros(4)
     lib().orc_model_constants(omega_m, fr0_abs, n, a, _p(out))
     return {"Rt": out[0], "fbar": out[1], "alpha": out[2], "src": out[3]}
+
+
+def effective_density(u, delta, fr0_abs: float, a: float = 1.0, n: int = 1,
+                      omega_m: float = OMEGA_M) -> np.ndarray:
+    """delta rho_eff / rho_bar per cell from u and delta (Sec. 2.4, eq.
+    effective_density with delta R from eq. dR_fR); any level, any shape."""
+    u = _f64(u)
+    d = _f64(delta)
+    assert u.shape == d.shape
+    out = np.empty_like(u)
+    lib().orc_effective_density(u.size, _p(u), _p(d), omega_m, fr0_abs, n, a, _p(out))
+    return out
 
 
 def solve_dense(delta, box: float, fr0_abs: float, a: float = 1.0, n: int = 1,

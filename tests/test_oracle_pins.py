@@ -222,6 +222,43 @@ def test_screened_tophat_interior():
 
 
 # --------------------------------------------------------------------------
+# Effective mass density (Sec. 2.4): delta_eff = delta/3 - delta R/(24 pi G rho)
+# with delta R from eq. dR_fR.  Unscreened limits give the 1/3 enhancement,
+# full screening gives 0 (GR), and on a converged periodic solve the box sum
+# is fixed by the discrete equation itself.
+# --------------------------------------------------------------------------
+def test_effective_density_limits_and_box_sum():
+    rng = np.random.default_rng(9)
+    d = rng.standard_normal((8, 8, 8))
+    # u = 0 (f_R at its background value): delta R = 0, delta_eff = delta / 3
+    np.testing.assert_allclose(oracle.effective_density(np.zeros_like(d), d, 1e-5), d / 3.0,
+                               rtol=0, atol=1e-15)
+    # local screening, u = -(n+1) ln(1 + Om a^-3 delta / Rt): delta_eff = 0, any a and n
+    for a, n in ((1.0, 1), (0.5, 1), (1.0, 2)):
+        mc = oracle.model_constants(1e-5, a=a, n=n)
+        dd = np.abs(d) * 5.0
+        u = -(n + 1) * np.log1p(0.3 / a ** 3 * dd / mc["Rt"])
+        eff = oracle.effective_density(u, dd, 1e-5, a=a, n=n)
+        assert np.abs(eff).max() < 1e-13 * np.abs(dd).max()
+    # converged periodic solve: the divergence term sums to zero, so
+    # sum(L) = alpha Rt sum(1 - e^{-u/2}) = sum(f) - sum(r), i.e.
+    # sum(delta_eff) = -sum(r) / (3 alpha Om a^-3) whatever sum(delta) is (a
+    # mean of 0.2 here, so that a wrong coefficient would show)
+    N, box, fr0 = 16, 50.0, 1e-5
+    delta = synth.lognormal_delta(N, box, 1.5, 90) + 0.2
+    u, st = oracle.solve_dense(delta, box, fr0, tol=1e-12)
+    assert st["converged"] == 1.0
+    r = oracle.residual_dense(u, delta, box, fr0)
+    mc = oracle.model_constants(fr0)
+    eff = oracle.effective_density(u, delta, fr0)
+    want = -r.sum() / (3.0 * mc["alpha"] * 0.3)
+    assert abs(eff.sum() - want) < 1e-9 * np.abs(eff).sum()
+    assert abs(delta.sum() / 3.0) > 1e3 * abs(eff.sum())
+    # (delta R is not negligible here: the case is not the u = 0 limit)
+    assert np.abs(eff - delta / 3.0).max() > 1e-2 * np.abs(delta / 3.0).max()
+
+
+# --------------------------------------------------------------------------
 # P7: invariants of the discrete problem and independence of accelerators.
 # --------------------------------------------------------------------------
 def test_shift_and_permutation_invariance():
