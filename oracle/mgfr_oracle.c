@@ -777,6 +777,45 @@ void orc_amr_delta(void* h, int l, double* out) {
   for (long long c = 0; c < A->ncell[l]; ++c) out[c] = A->mass[l][c] * scale - 1.0;
 }
 
+/*
+ * Effective mass of the solved hierarchy on a periodic PM grid of level lpm
+ * (N_pm = N0 2^lpm) [Sec. 2.4, long-range part]: every leaf cell (a cell
+ * with no daughters) carries delta_eff [eq. effective_density] times its
+ * volume, and hands to each PM cell it overlaps the fraction of that mass
+ * given by the overlapping volume over its own.  The grids are nested, so a
+ * leaf either covers whole PM cells (each receives delta_eff as a density)
+ * or lies inside one (which receives delta_eff 8^-(l - lpm)).  out: N_pm^3
+ * density contrasts (C order).  Needs a model (orc_amr_set_model) and u.
+ */
+void orc_amr_effective_pm(void* h, int lpm, double* out) {
+  orc_amr* A = (orc_amr*)h;
+  const orc_model* m = &A->model;
+  const int64_t Npm = lev_dim(A, lpm);
+  const double rho = m->omega_m / (m->a * m->a * m->a);
+  for (long long q = 0; q < Npm * Npm * Npm; ++q) out[q] = 0.0;
+  for (int l = 0; l < A->nlev; ++l) {
+    const double Nl = (double)lev_dim(A, l);
+    const double scale = Nl * Nl * Nl / (double)A->Np;
+    for (long long c = 0; c < A->ncell[l]; ++c) {
+      if (A->refined[l][c]) continue;
+      const double d = A->mass[l][c] * scale - 1.0;
+      const double eff = d / 3.0 + m->Rt / (3.0 * rho) * (1.0 - exp(-A->u[l][c] / (m->n + 1)));
+      int64_t I, J, K;
+      cell_coords(A, l, c, &I, &J, &K);
+      if (l <= lpm) {
+        const int64_t sc = (int64_t)1 << (lpm - l);
+        for (int64_t a = 0; a < sc; ++a)
+          for (int64_t b = 0; b < sc; ++b)
+            for (int64_t e = 0; e < sc; ++e)
+              out[((I * sc + a) * Npm + (J * sc + b)) * Npm + (K * sc + e)] = eff;
+      } else {
+        const int sh = l - lpm;
+        out[((I >> sh) * Npm + (J >> sh)) * Npm + (K >> sh)] += eff / (double)((int64_t)1 << (3 * sh));
+      }
+    }
+  }
+}
+
 /* Neighbour table of a level: nb[6c+d] >= 0 is a cell index, -1 a ghost.
  * Directions d: 0:-x 1:+x 2:-y 3:+y 4:-z 5:+z. */
 static const int DIRS[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};

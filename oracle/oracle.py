@@ -44,6 +44,7 @@ def lib():
             sig = {
                 "orc_model_constants": (None, [d, d, i, d, vp]),
                 "orc_effective_density": (None, [ll, vp, vp, d, d, i, d, vp]),
+                "orc_amr_effective_pm": (None, [vp, i, vp]),
                 "orc_solve_dense": (i, [i, d, vp, d, d, i, d, vp, d, i, i, i, i, d, vp]),
                 "orc_solve_dense_f": (i, [i, d, vp, d, d, i, d, vp, d, i, i, i, i, d, vp]),
                 "orc_residual_dense": (None, [i, d, vp, d, d, i, d, vp, vp]),
@@ -285,6 +286,15 @@ class AMR:
         rc = lib().orc_amr_solve(self.h, tol, max_vcycles, max_sweeps_refined, n_pre, n_post,
                                  int(prolong_linear), step_cap, _p(u0), _p(st))
         return rc, st
+
+    def effective_pm(self, lpm: int = 0) -> np.ndarray:
+        """Effective mass density contrast of the solved hierarchy on the
+        periodic PM grid of level lpm (Sec. 2.4: each leaf cell's effective
+        mass shared among the PM cells it overlaps by volume)."""
+        Npm = self.N0 << lpm
+        out = np.empty((Npm, Npm, Npm))
+        lib().orc_amr_effective_pm(self.h, lpm, _p(out))
+        return out
 
     def level_force(self, l, prolong_linear=True):
         n = self.ncell(l)

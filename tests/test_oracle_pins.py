@@ -258,6 +258,69 @@ def test_effective_density_limits_and_box_sum():
     assert np.abs(eff - delta / 3.0).max() > 1e-2 * np.abs(delta / 3.0).max()
 
 
+def _leaf_effective_by_brute_force(A, L, a=1.0, n=1, fr0=1e-5):
+    """delta_eff sampled at every cell of the uniform level-L grid, from the
+    leaf that contains it (found by descending the hierarchy cell by cell)."""
+    N0 = A.N0
+    NL = N0 << L
+    eff = [oracle.effective_density(A.u(l), A.delta(l), fr0, a=a, n=n) for l in range(A.nlev)]
+    keys = [None] + [A.keys(l) for l in range(1, A.nlev)]
+    out = np.empty((NL, NL, NL))
+    for i in range(NL):
+        for j in range(NL):
+            for k in range(NL):
+                for l in range(A.nlev):
+                    sh = L - l
+                    I, J, K = i >> sh, j >> sh, k >> sh
+                    Nl = N0 << l
+                    if l == 0:
+                        c = (I * Nl + J) * Nl + K
+                    else:
+                        Np = Nl // 2
+                        key = ((I >> 1) * Np + (J >> 1)) * Np + (K >> 1)
+                        o = np.searchsorted(keys[l], key)
+                        c = 8 * o + ((I & 1) << 2) + ((J & 1) << 1) + (K & 1)
+                    if l == A.nlev - 1 or not A.refined(l)[c]:
+                        out[i, j, k] = eff[l][c]
+                        break
+    return out
+
+
+def test_effective_mass_on_pm_grid_matches_brute_force():
+    """Sec. 2.4 long-range part: each leaf's effective mass shared among the
+    PM cells it overlaps by volume.  Against sampling the leaf field on the
+    finest grid and averaging it over each PM cell, for PM grids coarser
+    than, equal to and finer than the leaves; the total is conserved."""
+    N0, box, fr0 = 8, 20.0, 1e-5
+    rng = np.random.default_rng(21)
+    pos = np.concatenate([4.0 + 3.0 * rng.random((600, 3)), box * rng.random((200, 3))])
+    A = oracle.AMR(pos, N0, box, 2, 8)
+    assert A.nlev == 3
+    A.deposit()
+    A.set_model(fr0)
+    for l in range(A.nlev):
+        A.set_u(l, 0.5 * rng.standard_normal(A.ncell(l)))
+    fine = _leaf_effective_by_brute_force(A, 2, fr0=fr0)
+    for lpm in (0, 1, 2, 3):
+        pm = A.effective_pm(lpm)
+        Npm = N0 << lpm
+        if lpm <= 2:
+            s = 1 << (2 - lpm)
+            want = fine.reshape(Npm, s, Npm, s, Npm, s).mean(axis=(1, 3, 5))
+        else:
+            want = np.repeat(np.repeat(np.repeat(fine, 2, 0), 2, 1), 2, 2)
+        np.testing.assert_allclose(pm, want, rtol=1e-12, atol=1e-12)
+        assert abs(pm.mean() - fine.mean()) < 1e-12
+    # no refinement: the PM field is the base level's delta_eff itself
+    B = oracle.AMR(pos, N0, box, 0, 8)
+    B.deposit()
+    B.set_model(fr0)
+    u0 = 0.3 * rng.standard_normal(B.ncell(0))
+    B.set_u(0, u0)
+    np.testing.assert_array_equal(B.effective_pm(0).ravel(),
+                                  oracle.effective_density(u0, B.delta(0), fr0))
+
+
 # --------------------------------------------------------------------------
 # P7: invariants of the discrete problem and independence of accelerators.
 # --------------------------------------------------------------------------
