@@ -149,6 +149,12 @@ def _oracle_particle_sample():
     return upd, dt
 
 
+# the workload both arms report in config["workload"]
+WORKLOAD_DESC = ("particles256: 256^3 particles Poisson-sampled (nbar 1) from a 256^3 lognormal "
+                 "delta (sigma_g 1.5, P(k)~k^-1.5), box 100 Mpc/h, 256^3 base grid + 2 refinement "
+                 "levels (> 8 particles, 1-cell buffer), adaptive CIC, |fR0| 1e-5, n 1, a 1; every "
+                 "level solved to 1e-8 from a zero start; force gathered to the particles")
+
 SAMPLE_DESC = ("full FP64 oracle particle solve (structure, adaptive CIC, every level to 1e-8, "
                "particle force) of a 32^3-base sample: box 12.5 Mpc/h (same cell size), nbar 1, "
                "sigma_g 1.5, 2 refinement levels, |fR0| 1e-5")
@@ -183,9 +189,10 @@ def run_reference(args, rank: int) -> None:
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"] + " (bounded 32^3-base sample per step)"},
+            "config": {"workload": WORKLOAD_DESC, "parallelism": f"replicas x{args.gpus}"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "one " + SAMPLE_DESC + " per step"},
+                             "sample": "one " + SAMPLE_DESC + " per step (a bounded sample "
+                                       "of the workload)"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -473,11 +480,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"{w['name']}: {n_part} particles Poisson-sampled (nbar 1) from a "
-                               f"256^3 lognormal delta (sigma_g 1.5, P(k)~k^-1.5), box 100 Mpc/h, "
-                               f"256^3 base grid + 2 refinement levels (> 8 particles, 1-cell "
-                               f"buffer), adaptive CIC, |fR0| 1e-5, n 1, a 1; every level solved "
-                               f"to 1e-8 from a zero start; force gathered to the particles",
+        "config": {"workload": WORKLOAD_DESC, "particles": n_part,
                    "levels_cells": last["cells_per_level"][:last["n_levels"]],
                    "precision": "mixed (FP32 smoothing, FP64 residual/defect correction)",
                    "l2": "working set (u, E, f FP64 + FP32 levels, ~700 MB) larger than L2",
