@@ -27,7 +27,10 @@
  *   - one-way solves of refined levels with fixed ghost cells prolonged from
  *     the parent level [Sec. 3.3, steps 9-12];
  *   - f_R = fR_bar e^u and the extra force (c^2/2) grad f_R [Sec. 2,
- *     eq. modgrav_accel], on cells and interpolated back to particles.
+ *     eq. modgrav_accel], on cells and interpolated back to particles;
+ *   - the effective mass density delta rho_eff [Sec. 2.4, eq.
+ *     effective_density] per cell, and its share on a nested PM grid by
+ *     overlapping volume [Sec. 2.4].
  *
  * Readings where the paper is silent:
  *   - dL/du is the full derivative of the discrete L_i w.r.t. u_i with the
