@@ -215,6 +215,27 @@ typedef enum {
  * (out_host: ncell doubles, 3 ncell for MGFR_FIELD_ACC). */
 mgfr_status mgfr_get_level_field(mgfr_ctx* ctx, int level, int what, double* out_host);
 
+/*
+ * Effective mass density of the last particle solve (Sec. 2.4, eqs.
+ * phi_poisson_eq_with_eff_mass and effective_density): in units of the mean
+ * matter density, delta_eff = delta / 3 - delta R / (24 pi G rho_bar) with
+ * delta R = R_bar ((fR_bar / f_R)^{1/(n+1)} - 1) (eq. dR_fR), i.e.
+ * delta / 3 + Rt / (3 Om a^-3) (1 - e^{-u/(n+1)}), with the model and a of
+ * that solve.
+ *   mgfr_get_effective_density: per cell of one level, out_dev [ncell] device
+ *     FP64, cells in the order of the level fields.
+ *   mgfr_effective_mass_pm: on the periodic PM grid of level lpm (N_pm =
+ *     N_base 2^lpm <= 1024 per axis), out_dev [N_pm^3] device FP64, C order:
+ *     each leaf cell (a cell with no daughters) shares its effective mass
+ *     among the PM cells it overlaps in proportion to the overlapping volume
+ *     (Sec. 2.4, long-range part), expressed as a density contrast.
+ * Both are ordered on the context's stream after the solve; the PM grid sums
+ * contributions with FP64 atomics (order-dependent rounding).
+ * MGFR_E_INVALID without a particle solve or for an invalid level / lpm.
+ */
+mgfr_status mgfr_get_effective_density(mgfr_ctx* ctx, int level, double* out_dev);
+mgfr_status mgfr_effective_mass_pm(mgfr_ctx* ctx, int lpm, double* out_dev);
+
 /* One independent periodic solve of a batch (Sec. 3.2-3.3 per item). */
 typedef struct {
   int N;                     /* power of two, 8..512                          */

@@ -637,6 +637,53 @@ __global__ void k_source_lvl(const double* __restrict__ mass, long long n, doubl
   if (c < n) f[c] = src * (mass[c] * scale - 1.0);
 }
 
+// ---- effective mass density [Sec. 2.4] ---------------------------------------
+// delta rho_eff / rho_bar = delta / 3 - delta R / (24 pi G rho_bar), delta R =
+// R_bar (e^{-u/(n+1)} - 1) [eq. dR_fR]: with R_bar = 3 H0^2 Rt and
+// 24 pi G rho_bar = 9 H0^2 Om a^-3, delta / 3 + c3 (1 - e^{-u/(n+1)}),
+// c3 = Rt / (3 Om a^-3); delta = mass scale - 1 per level (mass in particle
+// masses, scale = N_l^3 / Np).
+struct EffPar {
+  double scale, c3, inv_np1;
+};
+
+__device__ __forceinline__ double eff_density(double mass, double u, const EffPar& q) {
+  return (mass * q.scale - 1.0) / 3.0 + q.c3 * (1.0 - exp(-u * q.inv_np1));
+}
+
+__global__ void k_eff_level(const double* __restrict__ mass, const double* __restrict__ u,
+                            long long n, EffPar q, double* __restrict__ out) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c < n) out[c] = eff_density(mass[c], u[c], q);
+}
+
+// Each leaf cell of level l hands its effective mass to the cells of the
+// nested periodic PM grid of level lpm (N_pm = N0 2^lpm) by overlapping
+// volume: a leaf at l <= lpm covers 2^(lpm-l) PM cells per axis and gives
+// each delta_eff as a density (plain stores: leaves do not overlap); a leaf
+// at l > lpm lies in one PM cell and adds delta_eff 8^-(l-lpm) (atomics).
+__global__ void k_eff_pm(int l, int lpm, TreeView T, const double* __restrict__ mass,
+                         const double* __restrict__ u, long long n, EffPar q,
+                         double* __restrict__ out) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= n || T.son[l][c] >= 0) return;  // not a leaf
+  const double eff = eff_density(mass[c], u[c], q);
+  long long I, J, K;
+  cell_coords(T, l, c, &I, &J, &K);
+  const long long Npm = 1LL << (T.lg0 + lpm);
+  if (l <= lpm) {
+    const long long s = 1LL << (lpm - l);
+    for (long long a = 0; a < s; ++a)
+      for (long long b = 0; b < s; ++b)
+        for (long long e = 0; e < s; ++e)
+          out[((I * s + a) * Npm + (J * s + b)) * Npm + (K * s + e)] = eff;
+  } else {
+    const int sh = l - lpm;
+    atomicAdd(out + ((I >> sh) * Npm + (J >> sh)) * Npm + (K >> sh),
+              eff / (double)(1LL << (3 * sh)));
+  }
+}
+
 __global__ void k_nan_check(const double* __restrict__ x, long long n,
                             unsigned long long* __restrict__ err) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1131,6 +1178,8 @@ static mgfr_status solve_particles(mgfr_ctx* c, const double* pos, long long Np,
     c->launches += 1;
   }
   A->fbar = m.fbar;
+  A->omega_m = g.omega_m;
+  A->nexp = g.n;
   A->a = m.a;
   for (int l = 1; l < A->nlev; ++l) {
     AmrLevel& L = A->L[l];
@@ -1254,6 +1303,50 @@ mgfr_status mgfr_solve_particles_host(mgfr_ctx* c, const double* pos_host, long 
     if (c->cs) cudaStreamSynchronize(c->cs);
   }
   return rs;
+}
+
+static EffPar eff_par(const AmrWork* A, int l) {
+  const double Nl = (double)(1LL << (A->lg0 + l));
+  const double a3 = A->a * A->a * A->a, rho = A->omega_m / a3;
+  const double Rt = rho + 4.0 * (1.0 - A->omega_m);
+  return EffPar{Nl * Nl * Nl / (double)A->Np, Rt / (3.0 * rho), 1.0 / (A->nexp + 1)};
+}
+
+mgfr_status mgfr_get_effective_density(mgfr_ctx* c, int level, double* out_dev) {
+  if (!c || !out_dev) return MGFR_E_INVALID;
+  AmrWork* A = W(c);
+  if (!A || A->nlev == 0 || level < 0 || level >= A->nlev)
+    return set_err(c, MGFR_E_INVALID, "no such level of a particle solve");
+  MG_CK(c, cudaSetDevice(c->device));
+  AmrLevel& L = A->L[level];
+  const double* u = level == 0 ? c->dh.L[0].u : L.u;
+  k_eff_level<<<nblocks(L.ncell, BS), BS, 0, c->s>>>(L.mass, u, L.ncell, eff_par(A, level),
+                                                     out_dev);
+  MG_CK(c, cudaEventRecord(c->ev_out, c->s));
+  MG_CK(c, cudaStreamWaitEvent(c->user, c->ev_out, 0));
+  MG_CK(c, cudaGetLastError());
+  return MGFR_OK;
+}
+
+mgfr_status mgfr_effective_mass_pm(mgfr_ctx* c, int lpm, double* out_dev) {
+  if (!c || !out_dev) return MGFR_E_INVALID;
+  AmrWork* A = W(c);
+  if (!A || A->nlev == 0) return set_err(c, MGFR_E_INVALID, "no particle solve yet");
+  if (lpm < 0 || A->lg0 + lpm > 10) return set_err(c, MGFR_E_INVALID, "PM grid of 2^0..2^10 cells per axis");
+  MG_CK(c, cudaSetDevice(c->device));
+  const long long Npm = 1LL << (A->lg0 + lpm);
+  MG_CK(c, cudaMemsetAsync(out_dev, 0, sizeof(double) * (size_t)(Npm * Npm * Npm), c->s));
+  TreeView T = tree_view(A);
+  for (int l = 0; l < A->nlev; ++l) {
+    AmrLevel& L = A->L[l];
+    const double* u = l == 0 ? c->dh.L[0].u : L.u;
+    k_eff_pm<<<nblocks(L.ncell, BS), BS, 0, c->s>>>(l, lpm, T, L.mass, u, L.ncell,
+                                                    eff_par(A, l), out_dev);
+  }
+  MG_CK(c, cudaEventRecord(c->ev_out, c->s));
+  MG_CK(c, cudaStreamWaitEvent(c->user, c->ev_out, 0));
+  MG_CK(c, cudaGetLastError());
+  return MGFR_OK;
 }
 
 mgfr_status mgfr_get_level_info(mgfr_ctx* c, int level, long long* n_oct, long long* ncell) {

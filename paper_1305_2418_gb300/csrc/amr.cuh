@@ -112,6 +112,8 @@ struct AmrWork {
   double* acc0 = nullptr;             // base force [3][N0^3]
   double* fr0 = nullptr;              // base fR [N0^3]
   double fbar = 0.0, a = 1.0;         // of the last particle solve (deferred level forces)
+  double omega_m = 0.3;               // of the last particle solve (effective density)
+  int nexp = 1;
   float4* acc0_32 = nullptr;          // base force, FP32 (x, y, z, 0) per cell
   double *pos_dev = nullptr, *acc_dev = nullptr;  // particle arrays of the host-buffer call
   long long pio_cap = 0;                          // their capacity (particles)

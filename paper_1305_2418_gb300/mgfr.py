@@ -85,6 +85,8 @@ SIGNATURES = {
     "mgfr_get_level_info": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "mgfr_get_level_keys": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "mgfr_get_level_field": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "mgfr_get_effective_density": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "mgfr_effective_mass_pm": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "mgfr_solve_density_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                              C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_void_p]),
@@ -244,6 +246,24 @@ class Solver:
         _, nc = self.level_info(level)
         out = np.empty(3 * nc if what == FIELD_ACC else nc)
         self._check(lib().mgfr_get_level_field(self.h, level, what, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def effective_density(self, level: int):
+        """delta rho_eff / rho_bar per cell of a level of the last particle
+        solve (mgfr_get_effective_density), as a CUDA FP64 tensor."""
+        import torch
+        _, nc = self.level_info(level)
+        out = torch.empty(nc, dtype=torch.float64, device=f"cuda:{self.device}")
+        self._check(lib().mgfr_get_effective_density(self.h, level, _ptr(out)))
+        return out
+
+    def effective_mass_pm(self, N_base: int, lpm: int = 0):
+        """The effective mass on the periodic PM grid of level lpm
+        (mgfr_effective_mass_pm), as a CUDA FP64 tensor of shape (N_pm,)*3."""
+        import torch
+        Npm = N_base << lpm
+        out = torch.empty((Npm,) * 3, dtype=torch.float64, device=f"cuda:{self.device}")
+        self._check(lib().mgfr_effective_mass_pm(self.h, lpm, _ptr(out)))
         return out
 
     def _batch_items(self, deltas, boxes, a, fr0s, ns, u_inits, want_acc):

@@ -79,4 +79,6 @@ def test_default_config_and_validation(lib):
         mgfr.MGFR_E_INVALID
     assert lib.mgfr_solve_particles_host(None, None, 1, 16, 1.0, 1.0, None, None, None,
                                          None) == mgfr.MGFR_E_INVALID
+    assert lib.mgfr_get_effective_density(None, 0, None) == mgfr.MGFR_E_INVALID
+    assert lib.mgfr_effective_mass_pm(None, 0, None) == mgfr.MGFR_E_INVALID
     lib.mgfr_destroy(None)
