@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY: the CUDA product path never imports this module.
 It compiles the oracle with gcc on first use (``build()``), in FP64 without
 floating-point contraction, and exposes numpy-level helpers.  Every function
-states the paper passage it follows; the arithmetic lives in the C file.
+states the paper passage it follows; the arithmetic lives in the C file, but
+for the periodic Poisson solve (numpy FFT).
 """
 from __future__ import annotations
 
@@ -113,6 +114,26 @@ def effective_density(u, delta, fr0_abs: float, a: float = 1.0, n: int = 1,
     out = np.empty_like(u)
     lib().orc_effective_density(u.size, _p(u), _p(d), omega_m, fr0_abs, n, a, _p(out))
     return out
+
+
+def poisson_periodic(rhs, box: float) -> np.ndarray:
+    """phi with lap_h phi = rhs - mean(rhs) on a periodic N^3 grid, mean(phi) = 0,
+    lap_h the 7-point Laplacian (spacing box/N): the exact solution of the
+    discrete problem by FFT (the library transform is a step; the eigenvalues
+    of lap_h are (2 cos(2 pi m / N) - 2) / h^2 per axis).  For the potential of
+    the effective mass (Sec. 2.4, eq. phi_poisson_eq_with_eff_mass)."""
+    r = _f64(rhs)
+    N = r.shape[0]
+    h = box / N
+    m = np.arange(N)
+    lam1 = (2.0 * np.cos(2.0 * np.pi * m / N) - 2.0) / (h * h)
+    lamz = lam1[: N // 2 + 1]
+    lam = lam1[:, None, None] + lam1[None, :, None] + lamz[None, None, :]
+    rk = np.fft.rfftn(r)
+    lam[0, 0, 0] = 1.0
+    pk = rk / lam
+    pk[0, 0, 0] = 0.0
+    return np.fft.irfftn(pk, s=r.shape, axes=(0, 1, 2))
 
 
 def solve_dense(delta, box: float, fr0_abs: float, a: float = 1.0, n: int = 1,

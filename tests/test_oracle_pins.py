@@ -321,6 +321,48 @@ def test_effective_mass_on_pm_grid_matches_brute_force():
                                   oracle.effective_density(u0, B.delta(0), fr0))
 
 
+def _lap7(phi, box):
+    h = box / phi.shape[0]
+    out = -6.0 * phi
+    for ax in range(3):
+        out += np.roll(phi, 1, ax) + np.roll(phi, -1, ax)
+    return out / (h * h)
+
+
+def test_periodic_poisson_inverts_the_seven_point_laplacian():
+    rng = np.random.default_rng(31)
+    phi = rng.standard_normal((16, 16, 16))
+    phi -= phi.mean()
+    got = oracle.poisson_periodic(_lap7(phi, 40.0), 40.0)
+    assert np.abs(got - phi).max() < 1e-11 * np.abs(phi).max()
+    # a constant right-hand side has no periodic solution: its mean is dropped
+    got = oracle.poisson_periodic(_lap7(phi, 40.0) + 3.0, 40.0)
+    assert np.abs(got - phi).max() < 1e-11 * np.abs(phi).max()
+
+
+def test_effective_mass_potential_reproduces_the_field():
+    """With delta R from eq. dR_fR the field equation reads lap f_R =
+    -3 a^2 (H0/c)^2 Om a^-3 delta_eff (Sec. 2.4), so the potential of the
+    effective mass is -(c^2/2) f_R: the Poisson solve of delta_eff gives back
+    E = e^u up to its mean.  The discrete operator's flux 1/2 (E_j + E_i)
+    (u_j - u_i) differs from E_j - E_i by -E_i (u_j - u_i)^3 / 12 + ..., so on
+    a mildly nonlinear field the two agree to the square of the link
+    differences."""
+    N, box, fr0 = 16, 100.0, 1e-4
+    delta = synth.lognormal_delta(N, box, 0.3, 95)
+    u, st = oracle.solve_dense(delta, box, fr0, tol=1e-13)
+    assert st["converged"] == 1.0
+    mc = oracle.model_constants(fr0)
+    eff = oracle.effective_density(u, delta, fr0)
+    E = np.exp(u)
+    got = oracle.poisson_periodic(-3.0 * mc["alpha"] * 0.3 * eff, box)
+    var = E - E.mean()
+    links = max(np.abs(np.diff(u, axis=ax)).max() for ax in range(3))
+    assert links > 1e-3  # not the linear limit
+    err = np.abs(got - var).max() / np.abs(var).max()
+    assert err < 0.5 * links * links, (err, links)
+
+
 # --------------------------------------------------------------------------
 # P7: invariants of the discrete problem and independence of accelerators.
 # --------------------------------------------------------------------------
