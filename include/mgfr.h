@@ -3,12 +3,12 @@
  *
  * The library solves the quasi-static scalar-field equation of Hu-Sawicki
  * f(R) gravity in the log variable u = ln(f_R / fR_bar(a)) (Puchwein, Baldi &
- * Springel, arXiv:1305.2418, Sec. 3.2, eqs. fR_u and u_field_eq) with
+ * Springel, arXiv:1305.2418, Sec. 3.2, Eqs. (15) and (16)) with
  * red-black Newton-Gauss-Seidel relaxation accelerated by FAS multigrid
- * (Sec. 3.3, eqs. iterative_correction, u_coarse_grid, fine_correction), on a
+ * (Sec. 3.3, Eqs. (23), (27), (29)), on a
  * periodic base grid or on a hierarchy refined where particle counts are high
  * (Sec. 3.1), and returns f_R = fR_bar e^u and the extra acceleration
- * a_MG = (c^2/2) grad f_R (Sec. 2, eq. modgrav_accel).
+ * a_MG = (c^2/2) grad f_R (Sec. 2, Eq. (13)).
  *
  * Conventions shared by every entry point:
  *  - Lengths are comoving Mpc/h; positions are wrapped periodically into
@@ -216,10 +216,10 @@ typedef enum {
 mgfr_status mgfr_get_level_field(mgfr_ctx* ctx, int level, int what, double* out_host);
 
 /*
- * Effective mass density of the last particle solve (Sec. 2.4, eqs.
- * phi_poisson_eq_with_eff_mass and effective_density): in units of the mean
+ * Effective mass density of the last particle solve (Sec. 2.4, Eqs.
+ * (30) and (31)): in units of the mean
  * matter density, delta_eff = delta / 3 - delta R / (24 pi G rho_bar) with
- * delta R = R_bar ((fR_bar / f_R)^{1/(n+1)} - 1) (eq. dR_fR), i.e.
+ * delta R = R_bar ((fR_bar / f_R)^{1/(n+1)} - 1) (Eq. (11)), i.e.
  * delta / 3 + Rt / (3 Om a^-3) (1 - e^{-u/(n+1)}), with the model and a of
  * that solve.
  *   mgfr_get_effective_density: per cell of one level, out_dev [ncell] device

@@ -14,22 +14,22 @@
  *
  * What it computes (paper section / equation in brackets):
  *   - model constants: background curvature R(a) and background field
- *     fR(a) of the Hu-Sawicki model [Sec. 2, eqs. fR_mean, dR_fR];
+ *     fR(a) of the Hu-Sawicki model [Sec. 2, Eqs. (10), (11)];
  *   - the discrete operator L and source f of the field equation for
- *     u = ln(fR / fR_bar) [Sec. 3.2, eqs. fR_u, u_field_eq,
- *     u_discrete_field_eq], in comoving units (see model_make below);
+ *     u = ln(fR / fR_bar) [Sec. 3.2, Eqs. (15), (16), (22)], in comoving
+ *     units (see model_make below);
  *   - Newton-Gauss-Seidel point updates in red-black order
- *     [Sec. 3.3, eq. iterative_correction];
- *   - FAS multigrid V-cycles down to a 4^3 grid [Sec. 3.3, eqs.
- *     u_coarse_grid, fine_correction, steps 1-8];
+ *     [Sec. 3.3, Eq. (23)];
+ *   - FAS multigrid V-cycles down to a 4^3 grid [Sec. 3.3, Eqs.
+ *     (27), (29), steps 1-8];
  *   - the refinement hierarchy from particle counts, adaptive cloud-in-cell
  *     mass assignment and upward mass sums [Sec. 3.1];
  *   - one-way solves of refined levels with fixed ghost cells prolonged from
  *     the parent level [Sec. 3.3, steps 9-12];
  *   - f_R = fR_bar e^u and the extra force (c^2/2) grad f_R [Sec. 2,
- *     eq. modgrav_accel], on cells and interpolated back to particles;
- *   - the effective mass density delta rho_eff [Sec. 2.4, eq.
- *     effective_density] per cell, and its share on a nested PM grid by
+ *     Eq. (13)], on cells and interpolated back to particles;
+ *   - the effective mass density delta rho_eff [Sec. 2.4, Eq.
+ *     (31)] per cell, and its share on a nested PM grid by
  *     overlapping volume [Sec. 2.4].
  *
  * Readings where the paper is silent:
@@ -75,13 +75,13 @@ typedef struct {
 } orc_model;
 
 /*
- * Dividing the physical field equation [eq. u_field_eq] by a^-2 (the
+ * Dividing the physical field equation [Eq. (16)] by a^-2 (the
  * physical Laplacian is a^-2 times the comoving one) and using
  * R_bar = 3 H0^2 Rt [Sec. 2] and 8 pi G rho_bar = 3 H0^2 Om a^-3 gives
  *     lap_x e^u + alpha [Rt (1 - e^{-u/(n+1)}) + Om a^-3 delta] = 0,
  * with alpha = a^2 (H0/c)^2 / fR_bar(a).  fR_bar(a) = -|fR0| (Rt(1)/Rt(a))^{n+1}
- * [eq. fR_mean for n = 1; the exponent n+1 follows from eq.
- * fR-R,n_relation].  Flatness: OL = 1 - Om.
+ * [Eq. (10) for n = 1; the exponent n+1 follows from Eq.
+ * (7)].  Flatness: OL = 1 - Om.
  */
 static orc_model model_make(double omega_m, double fr0_abs, int n, double a) {
   orc_model m;
@@ -108,10 +108,10 @@ void orc_model_constants(double omega_m, double fr0_abs, int n, double a, double
 }
 
 /*
- * Effective mass density [Sec. 2.4, eqs. phi_poisson_eq_with_eff_mass and
- * effective_density]: delta rho_eff = delta rho / 3 - delta R / (24 pi G),
- * with delta R = R_bar ((fR_bar / f_R)^{1/(n+1)} - 1) [eq. dR_fR, general n
- * by eq. fR-R,n_relation] = R_bar (e^{-u/(n+1)} - 1).  In units of the mean
+ * Effective mass density [Sec. 2.4, Eqs. (30) and (31)]:
+ * delta rho_eff = delta rho / 3 - delta R / (24 pi G),
+ * with delta R = R_bar ((fR_bar / f_R)^{1/(n+1)} - 1) [Eq. (11), general n
+ * by Eq. (7)] = R_bar (e^{-u/(n+1)} - 1).  In units of the mean
  * matter density, with R_bar = 3 H0^2 Rt and 24 pi G rho_bar = 9 H0^2 Om a^-3:
  *     delta_eff = delta / 3 + Rt / (3 Om a^-3) (1 - e^{-u/(n+1)}).
  * Per cell of any level (u, delta, out: n values).
@@ -178,7 +178,7 @@ static double dense_dL(const double* u, int N, int i, int j, int k, double ih2,
   return d * ih2 + m->alpha * m->Rt / (m->n + 1) * exp(-uc / (m->n + 1));
 }
 
-/* Newton-Gauss-Seidel red-black sweep [eq. iterative_correction]: red cells
+/* Newton-Gauss-Seidel red-black sweep [Eq. (23)]: red cells
  * ((i+j+k) even) first, then black. */
 static void dense_rb_sweep(double* u, const double* f, int N, double h, const orc_model* m,
                            double step_cap) {
@@ -283,9 +283,9 @@ static void dense_coarse_solve(double* u, const double* f, int N, double h, cons
 /*
  * One FAS V-cycle on the dense level of size N [Sec. 3.3, steps 3-7]:
  * pre-smooth; restrict u and the residual; coarse RHS
- * f^{2h} = L^{2h}(R u) + R(f - L(u)) [eq. u_coarse_grid]; solve the coarse
+ * f^{2h} = L^{2h}(R u) + R(f - L(u)) [Eq. (27)]; solve the coarse
  * problem (recursively while the coarse grid is larger than 4^3, directly on
- * 4^3); correct u += P(u^{2h} - R u) [eq. fine_correction]; post-smooth.
+ * 4^3); correct u += P(u^{2h} - R u) [Eq. (29)]; post-smooth.
  */
 static void dense_vcycle(double* u, const double* f, int N, double h, const orc_model* m,
                          orc_mg* mg) {
@@ -424,7 +424,7 @@ void orc_residual_dense_at(int N, double box, double omega_m, double fr0_abs, in
 }
 
 /*
- * Field and force on a dense periodic level [Sec. 2, eq. modgrav_accel]:
+ * Field and force on a dense periodic level [Sec. 2, Eq. (13)]:
  * fR = fR_bar e^u; a_MG / c^2 = grad_x fR / (2a), the gradient by central
  * differences.  acc layout: [3][N^3] (component-major).
  */
@@ -783,7 +783,7 @@ void orc_amr_delta(void* h, int l, double* out) {
 /*
  * Effective mass of the solved hierarchy on a periodic PM grid of level lpm
  * (N_pm = N0 2^lpm) [Sec. 2.4, long-range part]: every leaf cell (a cell
- * with no daughters) carries delta_eff [eq. effective_density] times its
+ * with no daughters) carries delta_eff [Eq. (31)] times its
  * volume, and hands to each PM cell it overlaps the fraction of that mass
  * given by the overlapping volume over its own.  The grids are nested, so a
  * leaf either covers whole PM cells (each receives delta_eff as a density)
@@ -1102,7 +1102,7 @@ int orc_amr_solve(void* h, double tol, int max_vcycles, long long max_sweeps_ref
 }
 
 /*
- * f_R and a_MG / c^2 = grad_x f_R / (2a) per level [Sec. 2, eq. modgrav_accel];
+ * f_R and a_MG / c^2 = grad_x f_R / (2a) per level [Sec. 2, Eq. (13)];
  * central differences with ghost values at patch edges.  acc: [ncell][3].
  */
 void orc_amr_level_force(void* h, int l, int prolong_linear, double* fr, double* acc) {

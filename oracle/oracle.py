@@ -98,7 +98,7 @@ OMEGA_M = 0.3
 
 
 def model_constants(fr0_abs: float, a: float = 1.0, n: int = 1, omega_m: float = OMEGA_M) -> dict:
-    """R~(a), fR_bar(a), alpha(a) and the source factor (Sec. 2, eq. fR_mean)."""
+    """R~(a), fR_bar(a), alpha(a) and the source factor (Sec. 2, Eq. (10))."""
     out = np.zeros(4)
     lib().orc_model_constants(omega_m, fr0_abs, n, a, _p(out))
     return {"Rt": out[0], "fbar": out[1], "alpha": out[2], "src": out[3]}
@@ -106,8 +106,8 @@ def model_constants(fr0_abs: float, a: float = 1.0, n: int = 1, omega_m: float =
 
 def effective_density(u, delta, fr0_abs: float, a: float = 1.0, n: int = 1,
                       omega_m: float = OMEGA_M) -> np.ndarray:
-    """delta rho_eff / rho_bar per cell from u and delta (Sec. 2.4, eq.
-    effective_density with delta R from eq. dR_fR); any level, any shape."""
+    """delta rho_eff / rho_bar per cell from u and delta (Sec. 2.4, Eq.
+    (31) with delta R from Eq. (11)); any level, any shape."""
     u = _f64(u)
     d = _f64(delta)
     assert u.shape == d.shape
@@ -121,7 +121,7 @@ def poisson_periodic(rhs, box: float) -> np.ndarray:
     lap_h the 7-point Laplacian (spacing box/N): the exact solution of the
     discrete problem by FFT (the library transform is a step; the eigenvalues
     of lap_h are (2 cos(2 pi m / N) - 2) / h^2 per axis).  For the potential of
-    the effective mass (Sec. 2.4, eq. phi_poisson_eq_with_eff_mass)."""
+    the effective mass (Sec. 2.4, Eq. (30))."""
     r = _f64(rhs)
     N = r.shape[0]
     h = box / N

@@ -1,6 +1,6 @@
 // amr.cu -- refined hierarchy from particle counts, adaptive cloud-in-cell,
 // one-way refined-level solves and the force at the particles
-// (Puchwein, Baldi & Springel 2013, Sec. 3.1 and 3.3, eq. modgrav_accel).
+// (Puchwein, Baldi & Springel 2013, Sec. 3.1 and 3.3, Eq. (13)).
 //
 // Structure build, per level l < lmax: nearest-grid-point counts (int32
 // atomics), flags = count > refine_count dilated over the 26 neighbours,
@@ -639,7 +639,7 @@ __global__ void k_source_lvl(const double* __restrict__ mass, long long n, doubl
 
 // ---- effective mass density [Sec. 2.4] ---------------------------------------
 // delta rho_eff / rho_bar = delta / 3 - delta R / (24 pi G rho_bar), delta R =
-// R_bar (e^{-u/(n+1)} - 1) [eq. dR_fR]: with R_bar = 3 H0^2 Rt and
+// R_bar (e^{-u/(n+1)} - 1) [Eq. (11)]: with R_bar = 3 H0^2 Rt and
 // 24 pi G rho_bar = 9 H0^2 Om a^-3, delta / 3 + c3 (1 - e^{-u/(n+1)}),
 // c3 = Rt / (3 Om a^-3); delta = mass scale - 1 per level (mass in particle
 // masses, scale = N_l^3 / Np).
@@ -841,6 +841,10 @@ void amr_free(mgfr_ctx* c) {
   if (A->d_split) cudaFree(A->d_split);
   delete A;
   c->amr = nullptr;
+}
+
+void amr_invalidate(mgfr_ctx* c) {
+  if (c && c->amr) W(c)->nlev = 0;
 }
 
 TreeView tree_view(const AmrWork* A) {
@@ -1075,6 +1079,7 @@ static mgfr_status solve_particles(mgfr_ctx* c, const double* pos, long long Np,
   if (st) std::memset(st, 0, sizeof(*st));
   c->launches = 0;
   const bool mixed = g.precision == MGFR_PREC_MIXED;
+  amr_invalidate(c);  // valid again only once this solve has built its levels
   TRY(ensure_dense_public(c, N0, mixed, box));
   if (!c->amr) c->amr = new AmrWork();
   AmrWork* A = W(c);
@@ -1318,6 +1323,9 @@ mgfr_status mgfr_get_effective_density(mgfr_ctx* c, int level, double* out_dev) 
   if (!A || A->nlev == 0 || level < 0 || level >= A->nlev)
     return set_err(c, MGFR_E_INVALID, "no such level of a particle solve");
   MG_CK(c, cudaSetDevice(c->device));
+  // out_dev is written in the caller's stream order
+  MG_CK(c, cudaEventRecord(c->ev_in, c->user));
+  MG_CK(c, cudaStreamWaitEvent(c->s, c->ev_in, 0));
   AmrLevel& L = A->L[level];
   const double* u = level == 0 ? c->dh.L[0].u : L.u;
   k_eff_level<<<nblocks(L.ncell, BS), BS, 0, c->s>>>(L.mass, u, L.ncell, eff_par(A, level),
@@ -1334,6 +1342,8 @@ mgfr_status mgfr_effective_mass_pm(mgfr_ctx* c, int lpm, double* out_dev) {
   if (!A || A->nlev == 0) return set_err(c, MGFR_E_INVALID, "no particle solve yet");
   if (lpm < 0 || A->lg0 + lpm > 10) return set_err(c, MGFR_E_INVALID, "PM grid of 2^0..2^10 cells per axis");
   MG_CK(c, cudaSetDevice(c->device));
+  MG_CK(c, cudaEventRecord(c->ev_in, c->user));
+  MG_CK(c, cudaStreamWaitEvent(c->s, c->ev_in, 0));
   const long long Npm = 1LL << (A->lg0 + lpm);
   MG_CK(c, cudaMemsetAsync(out_dev, 0, sizeof(double) * (size_t)(Npm * Npm * Npm), c->s));
   TreeView T = tree_view(A);

@@ -129,6 +129,10 @@ struct AmrWork {
 };
 
 void amr_free(mgfr_ctx* c);
+// Forget the hierarchy of the last particle solve (its level-0 arrays live in
+// the dense workspace, which other solves reuse); the level getters then
+// return MGFR_E_INVALID until the next particle solve completes.
+void amr_invalidate(mgfr_ctx* c);
 TreeView tree_view(const AmrWork* A);
 // One-way solve of refined level L >= 1 (amr_solve.cu).
 mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int L, const Model& m, mgfr_stats* st);

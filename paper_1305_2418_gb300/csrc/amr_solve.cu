@@ -99,7 +99,7 @@ __device__ __forceinline__ T Lval(T uc, T Ec, const NB<T>* nb, const MT<T>& m, T
   return sbd * ih2 + m.aRt * ((T)1 - nls(uc, Ec, m));
 }
 
-// Newton step (L - f)/(dL/du), clamped (Sec. 3.3, eq. iterative_correction)
+// Newton step (L - f)/(dL/du), clamped (Sec. 3.3, Eq. (23))
 template <class T>
 __device__ __forceinline__ T newton(T uc, T Ec, const NB<T>* nb, T f, const MT<T>& m, T ih2, T cap) {
   T sbd = 0, sd = 0, sb = 0;
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(BS) k_ofas(const T* __restrict__ u, const T* _
   f[c] += Lval(u[c], Eat(E, u, c), nb, m, ih2);
 }
 
-// u += P(uc - ucold) on relaxed cells (eq. fine_correction), the parent's
+// u += P(uc - ucold) on relaxed cells (Eq. (29)), the parent's
 // neighbours from the pnbr table (a gradient component is 0 where one is
 // missing).
 template <class T>

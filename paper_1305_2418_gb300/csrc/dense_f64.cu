@@ -62,7 +62,7 @@ __global__ void k_init(const double* __restrict__ u0, double* __restrict__ u,
 }
 
 // One red (colour 0: i+j+k even) or black half-sweep of the Newton update
-// u <- u - (L - f) / (dL/du) (Sec. 3.3, eq. iterative_correction), one thread
+// u <- u - (L - f) / (dL/du) (Sec. 3.3, Eq. (23)), one thread
 // per cell of the active colour.  dL/du holds the neighbours fixed; the step
 // is clamped to |du| <= cap.
 __global__ void __launch_bounds__(BS) k_sweep(double* __restrict__ u, double* __restrict__ E,
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(BS) k_restrict_resid(const double* __restrict_
   fc[t] = 0.125 * sr;
 }
 
-// FAS right-hand side f^{2h} = L^{2h}(R u) + R(f - L(u)) (eq. u_coarse_grid).
+// FAS right-hand side f^{2h} = L^{2h}(R u) + R(f - L(u)) (Eq. (27)).
 __global__ void __launch_bounds__(BS) k_fas_rhs(const double* __restrict__ u,
                                                 const double* __restrict__ E,
                                                 double* __restrict__ f, int lg, Model m,
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(BS) k_fas_rhs(const double* __restrict__ u,
   f[t] += Lpoint(u, E, i, j, k, lg, m, ih2);
 }
 
-// u^h += P(u^{2h} - R u^h) (eq. fine_correction), P linear (parent value plus
+// u^h += P(u^{2h} - R u^h) (Eq. (29)), P linear (parent value plus
 // s_d (c_{+d} - c_{-d})/8 per axis) or injection; then E = e^u.
 __global__ void __launch_bounds__(BS) k_prolong_corr(double* __restrict__ u,
                                                      double* __restrict__ E,
@@ -301,7 +301,7 @@ __global__ void k_finish(const double* __restrict__ partials, int nparts, double
 }
 
 // fR = fR_bar e^u and a_MG/c^2 = (fR_{+} - fR_{-}) / (2h) / (2a) per axis
-// (Sec. 2, eq. modgrav_accel).  acc is [3][N^3].
+// (Sec. 2, Eq. (13)).  acc is [3][N^3].
 __global__ void __launch_bounds__(BS) k_force(const double* __restrict__ E, int lg, double fbar,
                                               double g_scale, double* __restrict__ fr,
                                               double* __restrict__ acc) {

@@ -162,6 +162,8 @@ void prof_collect(mgfr_ctx* c, int graph, mgfr_stats* st);
 void prof_clear(mgfr_ctx* c, int graph);
 
 mgfr_status set_err(mgfr_ctx* c, mgfr_status st, const std::string& msg);
+// Range checks of a configuration (false and the reason in why if invalid).
+bool validate_cfg(const mgfr_config* c, std::string& why);
 void batch_free(mgfr_ctx* c);
 void unet_free(mgfr_ctx* c);
 #define MG_CK(ctx, call)                                                                  \

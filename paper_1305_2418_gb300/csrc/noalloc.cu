@@ -136,10 +136,8 @@ extern "C" mgfr_status mgfr_solve_density_noalloc(const mgfr_config* cfg, const 
   if (N < 8 || N > NA_MAX_N || (N & (N - 1))) return MGFR_E_INVALID;  // beyond the scratch
   if (!(box > 0.0) || !std::isfinite(box) || !(a > 0.0) || !std::isfinite(a)) return MGFR_E_INVALID;
   const mgfr_config& g = *cfg;
-  if (!(g.fr0_abs > 0.0) || g.n < 1 || !(g.omega_m > 0.0 && g.omega_m <= 1.0) ||
-      !(g.tol_rel > 0.0 && g.tol_rel < 1.0) || g.n_pre < 0 || g.n_post < 0 ||
-      g.n_pre + g.n_post < 1 || g.max_vcycles < 1 || !(g.step_cap > 0.0))
-    return MGFR_E_INVALID;
+  std::string why;
+  if (!validate_cfg(cfg, why)) return MGFR_E_INVALID;  // the same checks as mgfr_create
   if (st) std::memset(st, 0, sizeof(*st));
   double* base = nullptr;
   mgfr_status rs = na_scratch(&base);

@@ -131,7 +131,7 @@ void mgfr_config_default(mgfr_config* c) {
 
 }  // extern "C"
 
-static bool validate_cfg(const mgfr_config* c, std::string& why) {
+bool validate_cfg(const mgfr_config* c, std::string& why) {
   auto bad = [&](const char* w) {
     why = w;
     return false;
@@ -633,6 +633,9 @@ mgfr_status mgfr_solve_density(mgfr_ctx* c, const double* delta, int N, double b
   MG_CK(c, cudaSetDevice(c->device));
   if (st) std::memset(st, 0, sizeof(*st));
   const bool mixed = c->cfg.precision == MGFR_PREC_MIXED;
+  // the base level of a particle solve lives in the dense workspace this
+  // solve overwrites: its hierarchy is no longer queryable
+  amr_invalidate(c);
   mgfr_status rs = ensure_dense(c, N, mixed);
   if (rs != MGFR_OK) return rs;
   DenseHier& H = c->dh;

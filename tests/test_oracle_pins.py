@@ -19,7 +19,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def paper_background(fr0_abs, a, omega_m=0.3, n=1):
-    """R_bar(a) in units of H0^2 and fR_bar(a) (Sec. 2, eq. fR_mean), flat LCDM."""
+    """R_bar(a) in units of H0^2 and fR_bar(a) (Sec. 2, Eq. (10)), flat LCDM."""
     ol = 1.0 - omega_m
     R = 3.0 * omega_m * (a ** -3 + 4.0 * ol / omega_m)
     R0 = 3.0 * omega_m * (1.0 + 4.0 * ol / omega_m)
@@ -59,7 +59,7 @@ def test_linear_limit_matches_fft_helmholtz(fr0, a):
     delta = 1e-6 * synth.lognormal_delta(N, box, 1.0, 4242)
     Rbar, fbar = paper_background(fr0, a, om)
     kappa = 1.0 / C_OVER_H0 ** 2
-    # dR/dfR from delta R = R_bar (sqrt(fR_bar / fR) - 1)  (eq. dR_fR)
+    # dR/dfR from delta R = R_bar (sqrt(fR_bar / fR) - 1)  (Eq. (11))
     dRdf = Rbar / (2.0 * abs(fbar))
     mu2 = a * a * kappa * dRdf / 3.0
     S = a * a * kappa * om * a ** -3 / abs(fbar)
@@ -151,9 +151,9 @@ def test_manufactured_solution(offset, amp, fr0):
 
 
 # --------------------------------------------------------------------------
-# P5: the paper's 1D density peak (Sec. 4.2, eq. fR_gauss_1D).
+# P5: the paper's 1D density peak (Sec. 4.2, Eq. (36)).
 # (a) The printed amplitude A ~ 2.7e-5 follows from mean(delta rho) = 0 and
-#     delta R(fR) of eq. dR_fR: A = |fR_bar| mean((1 - alpha e^{-x^2/w^2})^{-1/2})^2.
+#     delta R(fR) of Eq. (11): A = |fR_bar| mean((1 - alpha e^{-x^2/w^2})^{-1/2})^2.
 # (b) With a resolved peak the discrete solution converges to the analytic
 #     fR at second order in the cell size.
 # --------------------------------------------------------------------------
@@ -223,7 +223,7 @@ def test_screened_tophat_interior():
 
 # --------------------------------------------------------------------------
 # Effective mass density (Sec. 2.4): delta_eff = delta/3 - delta R/(24 pi G rho)
-# with delta R from eq. dR_fR.  Unscreened limits give the 1/3 enhancement,
+# with delta R from Eq. (11).  Unscreened limits give the 1/3 enhancement,
 # full screening gives 0 (GR), and on a converged periodic solve the box sum
 # is fixed by the discrete equation itself.
 # --------------------------------------------------------------------------
@@ -341,7 +341,7 @@ def test_periodic_poisson_inverts_the_seven_point_laplacian():
 
 
 def test_effective_mass_potential_reproduces_the_field():
-    """With delta R from eq. dR_fR the field equation reads lap f_R =
+    """With delta R from Eq. (11) the field equation reads lap f_R =
     -3 a^2 (H0/c)^2 Om a^-3 delta_eff (Sec. 2.4), so the potential of the
     effective mass is -(c^2/2) f_R: the Poisson solve of delta_eff gives back
     E = e^u up to its mean.  The discrete operator's flux 1/2 (E_j + E_i)

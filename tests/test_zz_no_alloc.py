@@ -3,8 +3,9 @@ context-based solve, through the C ABI, on a GPU.
 
 Callers that cannot allocate device memory use the fixed in-library scratch;
 its results must match mgfr_solve_density's FP64 path within the parity
-tolerance (1e-6 relative on f_R and force), on two calls in a row with
-different inputs (the second call must not see the first call's state).
+tolerance (1e-6 relative on f_R and force), on calls in a row with
+different inputs: two at the same size, so that the second finds the first
+call's values in the same layout and must not use them, then a larger one.
 This file is collected last on purpose.
 """
 import ctypes as C
@@ -37,7 +38,9 @@ def test_noalloc_matches_context_solve_twice():
     box, fr0 = 100.0, 1e-5
     cfg = mgfr.default_config(fr0_abs=fr0)
     ref = mgfr.Solver(0, fr0_abs=fr0)
-    for seed, N, sig in ((11, 32, 1.0), (12, 64, 1.5)):
+    # two calls at the same size with different fields (the second call's
+    # scratch has the first call's layout and contents), then a larger size
+    for seed, N, sig in ((11, 32, 1.0), (13, 32, 1.5), (12, 64, 1.5)):
         delta = torch.from_numpy(synth.lognormal_delta(N, box, sig, seed)).to(dev)
         rc, fr, acc, st = _noalloc(cfg, delta, box, 1.0, stream)
         torch.cuda.synchronize()
