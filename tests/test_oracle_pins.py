@@ -158,15 +158,38 @@ def test_manufactured_solution(offset, amp, fr0):
 #     fR at second order in the cell size.
 # --------------------------------------------------------------------------
 def test_peak_amplitude_matches_paper():
+    """The oracle's discrete operator reproduces the printed amplitude.
+
+    Summed over a periodic grid, the flux terms of L cancel pairwise, so
+    sum_i L_i(u) = alpha Rt sum_i (1 - e^{-u_i/(n+1)}) for any field, and
+    mean(delta rho) = 0 (mean f = 0) is sum_i L_i(u) = 0.  The field u of
+    Eq. (36) is sampled at 64^3 points spaced 0.001 Mpc/h along x (the core of
+    width w sqrt(1 - alpha) ~ 0.05 Mpc/h is resolved) and laid out on a 64^3
+    grid; the A for which the oracle's sum of L vanishes must be the paper's
+    A ~ 2.7e-5.  The same root with the exponent of n = 2 lands far away, so
+    the pin sees the 1/(n+1) of the nonlinear term."""
+    from scipy.optimize import brentq
     with open(os.path.join(GOLDEN, "peak1d_amplitude.json")) as fh:
         gold = json.load(fh)
-    from scipy.integrate import quad
     L, w, al, fb = gold["box"], gold["w"], gold["alpha"], gold["fr_bar_abs"]
-    half = L / 2
-    M, _ = quad(lambda x: (1.0 - al * np.exp(-x * x / w ** 2)) ** -0.5, -half, half,
-                points=[0.0], limit=500, epsabs=1e-12)
-    A = fb * (M / L) ** 2
+    N = 64
+    M = N ** 3
+    x = (np.arange(M) + 0.5) * (L / M) - L / 2
+    e = np.exp(-x * x / w ** 2)
+
+    def total_L(A, n=1):
+        u = np.log((A / fb) * (1.0 - al * e)).reshape(N, N, N)
+        return float(oracle.apply_L_dense(u, L, fb, n=n).sum())
+
+    A = brentq(total_L, 1e-6, 1e-3, xtol=1e-12)
     assert abs(A - gold["A"]) <= gold["tol"], A
+    # the oracle's mean source is zero there: mean delta rho = 0
+    u = np.log((A / fb) * (1.0 - al * e)).reshape(N, N, N)
+    mc = oracle.model_constants(fb)
+    f = oracle.apply_L_dense(u, L, fb)
+    assert abs(f.mean() / (mc["alpha"] * 0.3)) < 1e-9
+    A2 = brentq(lambda a_: total_L(a_, n=2), 1e-7, 1e-3, xtol=1e-12)
+    assert abs(A2 - gold["A"]) > 5 * gold["tol"], A2
 
 
 def _peak_delta(N, box, w, al, fb, om):
@@ -398,7 +421,7 @@ def test_gradient_sums_to_zero_on_periodic_level():
 # --------------------------------------------------------------------------
 # Refinement structure (Sec. 3.1): brute force with dense masks per level.
 # --------------------------------------------------------------------------
-def _brute_structure(pos, N0, box, lmax, thr):
+def _brute_structure(pos, N0, box, lmax, thr, want_exists=False):
     t = pos * (N0 / box)
     exists = [np.ones((N0,) * 3, bool)]
     keys = [None]
@@ -420,7 +443,19 @@ def _brute_structure(pos, N0, box, lmax, thr):
         keys.append(np.flatnonzero(ref.ravel()))
         ex = np.repeat(np.repeat(np.repeat(ref, 2, 0), 2, 1), 2, 2)
         exists.append(ex)
-    return keys
+    return (keys, exists) if want_exists else keys
+
+
+def _brute_leaf_levels(pos, N0, box, exists):
+    """Level of the deepest existing cell holding each particle (Sec. 3.1:
+    the AMR cell a particle resides in), from the dense existence masks."""
+    t = pos * (N0 / box)
+    lev = np.zeros(len(pos), np.int64)
+    for l in range(1, len(exists)):
+        idx = np.floor(t * 2 ** l).astype(np.int64)
+        inside = exists[l][idx[:, 0], idx[:, 1], idx[:, 2]]
+        lev[inside] = l
+    return lev
 
 
 @pytest.mark.parametrize("N0,lmax,sig,thr", [(16, 2, 1.5, 8), (16, 3, 2.0, 2), (8, 2, 1.0, 0)])
@@ -429,10 +464,14 @@ def test_structure_matches_brute_force(N0, lmax, sig, thr):
     d = synth.lognormal_delta(N0, box, sig, 40 + N0)
     pos = synth.poisson_particles(d, box, 2.0, 41)
     A = oracle.AMR(pos, N0, box, lmax, thr)
-    keys = _brute_structure(pos, N0, box, lmax, thr)
+    keys, exists = _brute_structure(pos, N0, box, lmax, thr, want_exists=True)
     assert A.nlev == len(keys)
     for l in range(1, A.nlev):
         np.testing.assert_array_equal(A.keys(l), keys[l])
+    # each particle's leaf level (the cube side of the adaptive CIC)
+    lev = _brute_leaf_levels(pos, N0, box, exists)
+    assert (lev > 0).any()
+    np.testing.assert_array_equal(A.particle_levels(), lev)
     for l in range(A.nlev):
         assert A.counts(l).max() >= 0
     # every leaf holds at most thr particles unless it sits on the deepest level
@@ -452,7 +491,8 @@ def test_adaptive_cic_brute_force():
     N0, box, lmax = 8, 8.0, 2
     rng = np.random.default_rng(3)
     clump = 2.3 + 0.6 * rng.random((150, 3))
-    pos = np.concatenate([clump, box * rng.random((40, 3))])
+    near = 1.05 + 0.4 * rng.random((6, 3))  # refined base cell, unrefined level-1 cell
+    pos = np.concatenate([clump, near, box * rng.random((40, 3))])
     A = oracle.AMR(pos, N0, box, lmax, 8)
     assert A.nlev == 3
     A.deposit()
@@ -485,7 +525,11 @@ def test_adaptive_cic_brute_force():
 
     mass = {l: np.zeros(A.ncell(l)) for l in range(A.nlev)}
     t = pos * (N0 / box)
-    lev = A.particle_levels()
+    # cube sides from the brute-force structure, not from the oracle
+    _, exists = _brute_structure(pos, N0, box, lmax, 8, want_exists=True)
+    lev = _brute_leaf_levels(pos, N0, box, exists)
+    np.testing.assert_array_equal(A.particle_levels(), lev)
+    assert set(np.unique(lev)) == {0, 1, 2}
     for p in range(len(pos)):
         side = 2.0 ** -lev[p]
         lo = t[p] - side / 2
@@ -596,6 +640,67 @@ def test_ghost_reconstruction_error_for_quadratic_field():
                 assert abs((v - exact) - want) < 1e-12
                 checked += 1
     assert checked > 0
+
+
+def test_ghost_gradient_component_zero_where_parent_neighbour_missing():
+    """Level-2 ghosts whose parent (a level-1 cell) lacks a level-1
+    neighbour along an axis take that gradient component as 0 (Sec. 3.3,
+    ghost cells from the parent by the linear reconstruction; reading: the
+    component is dropped where one of the two neighbours does not exist).
+    For a field linear in space, g . x, the reconstruction is exact along
+    axes with both neighbours; along a dropped axis the ghost misses the
+    exact value by -s g_d / 8 (base-cell units; daughter offset s/4 of a
+    level-1 cell of side 1/2).  A tight clump just above a base-cell corner
+    makes level 2 reach the edge of level 1."""
+    N0, box = 8, 8.0
+    rng = np.random.default_rng(11)
+    pos = 3.02 + 0.05 * rng.random((60, 3))
+    A = oracle.AMR(pos, N0, box, 2, 8)
+    assert A.nlev == 3
+    gvec = np.array([0.3, -0.2, 0.1])
+    lin = lambda x, y, z: gvec[0] * x + gvec[1] * y + gvec[2] * z + 1.0
+    x0 = np.arange(N0) + 0.5
+    X, Y, Z = np.meshgrid(x0, x0, x0, indexing="ij")
+    A.set_u(0, lin(X, Y, Z).ravel())
+    keys1 = A.keys(1)
+    kp = np.stack([keys1 // (N0 * N0), (keys1 // N0) % N0, keys1 % N0], 1)
+    ch = np.array([[c >> 2 & 1, c >> 1 & 1, c & 1] for c in range(8)])
+    cen1 = ((2 * kp[:, None, :] + ch[None, :, :]) + 0.5) / 2.0  # level-1 centres, base units
+    A.set_u(1, lin(cen1[..., 0], cen1[..., 1], cen1[..., 2]).ravel())
+    key1_set = set(int(k) for k in keys1)
+
+    def exists1(I, J, K):  # level-1 cell exists iff its base parent is refined
+        I, J, K = I % (2 * N0), J % (2 * N0), K % (2 * N0)
+        return ((I // 2) * N0 + J // 2) * N0 + K // 2 in key1_set
+
+    g = A.ghosts(2)
+    keys2 = A.keys(2)
+    N1 = 2 * N0
+    dirs = [(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+    n_drop = n_full = 0
+    for o, key in enumerate(keys2):
+        pi, pj, pk = key // (N1 * N1), (key // N1) % N1, key % N1
+        for c in range(8):
+            I, J, K = 2 * pi + (c >> 2 & 1), 2 * pj + (c >> 1 & 1), 2 * pk + (c & 1)
+            for d, (a, b, cc) in enumerate(dirs):
+                v = g[8 * o + c, d]
+                if np.isnan(v):
+                    continue
+                G = np.array([I + a, J + b, K + cc])  # ghost, level-2 units
+                P = G // 2                            # its parent, level-1 units
+                assert exists1(*P)
+                s = 2 * (G % 2) - 1                   # side of the ghost in its parent
+                want = lin(*((G + 0.5) / 4.0))
+                dropped = False
+                for ax in range(3):
+                    e = np.eye(3, dtype=np.int64)[ax]
+                    if not (exists1(*(P + e)) and exists1(*(P - e))):
+                        want -= s[ax] * gvec[ax] / 8.0
+                        dropped = True
+                assert abs(v - want) < 1e-12, (o, c, d, v, want)
+                n_drop += dropped
+                n_full += not dropped
+    assert n_drop > 0 and n_full > 0, (n_drop, n_full)
 
 
 # --------------------------------------------------------------------------
