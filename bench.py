@@ -1,10 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the f(R) field solve on GB300.
 
-One step = one full solve of the synthetic workload to ||f - L(u)|| <= 1e-8 ||f||
-from a zero start with the mixed-precision form (FP32 smoothing, FP64
-residual and defect correction), inputs resident in HBM.  The plain FP64
-solve of the same input is timed beside it (time-to-tolerance).
+One step = one full particle solve of the 512^3 workload: 512^3 particles
+Poisson-sampled from a lognormal field (sigma_g 2), 512^3 base grid with 3
+refinement levels, |fR0| = 1e-6 (strongly screened), every level solved to
+||f - L(u)|| <= 1e-8 ||f|| from a zero start with the mixed-precision form
+(FP32 smoothing, FP64-accurate residual and defect correction), and the force
+gathered to every particle.  Positions are resident in HBM when the timed
+region starts.  The plain FP64 solve of the same input is timed beside it
+(time-to-tolerance), and the other workloads are reported as extra keys.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -17,6 +21,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -28,45 +33,55 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1305_2418_gb300 import synth  # noqa: E402  (input generator only)
+
 METRIC = ("cell-updates/s & time-to-residual 1e-8 per f(R) solve "
           "(plain FP64 vs mixed+learned), HBM %")
 UNIT = "cell-updates/s"
 
-WORKLOAD = dict(name="particles256", N=256, box=100.0, a=1.0, fr0=1e-5, sigma_g=1.5, seed=2002,
-                lmax=2, nbar=1.0, refine_count=8)
+WORKLOAD = dict(synth.WORKLOADS["particles512"], name="particles512", refine_count=8)
+W256 = dict(synth.WORKLOADS["particles256"], name="particles256", refine_count=8)
 
-# Algorithmic bytes per cell of one launch, per profiled kernel family:
-#  0 FP32 NGS half-sweep: read u (4) + f of the active colour (2) + write the
-#    active u (2)                                   = 8 B per cell of the level
-#  1 FP32 linear GS half-sweep: read u32 (4) + e (4) + r active (2) + write e
-#    active (2)                                     = 12 B per cell
+# Algorithmic bytes per cell of one launch (what the method must move), per
+# profiled kernel family:
+#  0 FP32 NGS half-sweep (dense base level): read u (4) + f of the active
+#    colour (2) + write the active u (2)            = 8 B per cell of the level
+#  1 FP32 linear GS half-sweep on J e = r (base level): read u32 (4) + e (4) +
+#    r active (2) + write e active (2)              = 12 B per cell
 #  2 FP64-accurate residual of the level being solved, in double-float on the
-#    FP32 pipes (k_resid_df on the base level, k_oresid_df on a refined level):
-#    read u, E, f pairs (24) + write r32, u32, e32 (12) = 36 B per cell; bound
-#    by FP32/ALU issue (~270 operations per cell), not by HBM
-#  (FP64 NGS half-sweep, plain path: read u, E (16) + f active (4) + write u, E
-#   active (8) = 28 B per cell)
-#  3 NGS half-sweep on the octs of the refined level being solved; in the
-#    mixed form these are FP32 with e^u recomputed from u: read u (4) + f
-#    active (2) + write u active (2) + neighbour-oct table (24 B per oct = 3)
-#    = 11 B per cell  (FP64 form, E stored: 16 + 4 + 8 + 3 = 31 B per cell)
-#  4 FP32 linear Gauss-Seidel half-sweep on the octs of the refined level:
-#    read u, e (8) + r active (2) + write e active (2) + neighbour table (3)
-#    = 15 B per cell
-# (Ghost faces add bytes that depend on the patch geometry; not counted, so
-# the fractions below are lower bounds.)
-ALG_BYTES = {0: 8.0, 1: 12.0, 2: 36.0, 3: 11.0, 4: 15.0}
+#    FP32 pipes: read u, E, f pairs (24) + write r32, u32, e32 (12)
+#                                                    = 36 B per cell; bound by
+#    FP32/ALU issue (~270 operations per cell), not by HBM
+#  3 NGS half-sweep on the octs of the refined level being solved (FP32, e^u
+#    recomputed from u): as family 0               = 8 B per cell
+#  4 FP32 linear GS half-sweep on the octs of the refined level: as family 1
+#                                                    = 12 B per cell
+# The oct families also read the face-neighbour table (6 ints per oct, 3 B per
+# cell) and ghost faces; those are overhead of the refined-level layout, not
+# bytes the method needs, and are not counted.
+ALG_BYTES = {0: 8.0, 1: 12.0, 2: 36.0, 3: 8.0, 4: 12.0}
+TABLE_BYTES = {0: 0.0, 1: 0.0, 2: 0.0, 3: 3.0, 4: 3.0}
 FAMILY_BOUND = {0: "hbm", 1: "hbm", 2: "alu", 3: "hbm", 4: "hbm"}
-# DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum / cells) of
-# one launch, from ncu on the half-density case of the same workload
-# (profiles/k_oct_sweep32_particles256_nbar05.md); scaled to a full launch by
-# its cells.
-TRAFFIC_PER_CELL = {3: 13.84}
+# DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum over the
+# launch's cells), from ncu on the half-density 256^3-base sample of the same
+# workload (same cell size, sigma_g, levels and |fR0|); scaled to a full
+# launch by its cells.  None until captured for the current kernels.
+TRAFFIC_PER_CELL = {}
 KERNEL_NAMES = {0: "k_sweep32 (FP32 NGS half-sweep, base level)",
                 1: "k_lin_sweep (FP32 linear GS half-sweep, base level)",
                 2: "k_resid_df / k_oresid_df (FP64-accurate residual in double-float)",
                 3: "k_oct_sweep32<false> (FP32 NGS half-sweep on the octs of the refined level)",
                 4: "k_oct_sweep32<true> (FP32 linear GS half-sweep on the octs of the refined level)"}
+# FP64 form: FP64 operations per NGS point update counted from the kernels
+# (6 faces x (E sum, half, difference, FMA as 2, two running sums) = 42; L and
+# dL/du 10; step, clamp, update 4) = 56, plus one rsqrt (n = 1), one division
+# and one exponential, which the FP64 pipe also executes but are not counted.
+FP64_FLOPS_PER_UPDATE = 56.0
+FP64_KERNEL_NAMES = {0: "k_sweep (FP64 NGS half-sweep, base level)",
+                     3: "k_osweep<double> (FP64 NGS half-sweep on the octs of the refined level)"}
+# GB300 FP64: 1.25 TFLOP/s nominal (about 2 FP64 FMA per clock per SM at
+# 2.07 GHz on 152 SMs); no measured figure is available on this machine.
+FP64_PEAK_TFLOPS = 1.25
 
 
 def peaks():
@@ -125,20 +140,31 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def _oracle_particle_sample():
-    """One full oracle solve of a bounded sample of the particle workload: a
-    32^3 base grid in a 12.5 Mpc/h box (the workload's cell size), particles
-    drawn the same way (nbar 1, sigma_g 1.5), the same refinement rule,
-    |fR0| and tolerance.  Returns (cell updates, seconds)."""
-    import oracle
-    from paper_1305_2418_gb300 import synth
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+SAMPLE_N = 32
+
+
+def _sample_inputs():
     w = WORKLOAD
-    N = 32
-    box = w["box"] * N / w["N"]
-    d = synth.lognormal_delta(N, box, w["sigma_g"], w["seed"])
+    box = w["box"] * SAMPLE_N / w["N"]
+    d = synth.lognormal_delta(SAMPLE_N, box, w["sigma_g"], w["seed"])
     pos = synth.poisson_particles(d, box, w["nbar"], w["seed"])
+    return pos, box
+
+
+def _oracle_particle_sample(threads: int):
+    """One full oracle solve of a bounded sample of the workload: a 32^3 base
+    grid in a 6.25 Mpc/h box (the workload's cell size), particles drawn the
+    same way (nbar 1, sigma_g 2), the same refinement rule and levels, |fR0|
+    and tolerance.  Returns (nonlinear cell updates, seconds)."""
+    import oracle
+    w = WORKLOAD
+    oracle.set_threads(threads)
+    pos, box = _sample_inputs()
     t0 = time.perf_counter()
-    A = oracle.AMR(pos, N, box, w["lmax"], w["refine_count"])
+    A = oracle.AMR(pos, SAMPLE_N, box, w["lmax"], w["refine_count"])
     A.deposit()
     A.set_model(w["fr0"], a=w["a"])
     rc, st = A.solve(tol=1e-8)
@@ -146,42 +172,67 @@ def _oracle_particle_sample():
     dt = time.perf_counter() - t0
     upd = st[3] + sum(st[4 + 4 * (l - 1)] * A.ncell(l) for l in range(1, A.nlev))
     A.close()
+    oracle.set_threads(1)
     return upd, dt
 
 
-# the workload both arms report in config["workload"]
-WORKLOAD_DESC = ("particles256: 256^3 particles Poisson-sampled (nbar 1) from a 256^3 lognormal "
-                 "delta (sigma_g 1.5, P(k)~k^-1.5), box 100 Mpc/h, 256^3 base grid + 2 refinement "
-                 "levels (> 8 particles, 1-cell buffer), adaptive CIC, |fR0| 1e-5, n 1, a 1; every "
+def host_cpu() -> dict:
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
+WORKLOAD_DESC = ("particles512: 512^3 particles Poisson-sampled (nbar 1) from a 512^3 lognormal "
+                 "delta (sigma_g 2.0, P(k)~k^-1.5), box 100 Mpc/h, 512^3 base grid + 3 refinement "
+                 "levels (> 8 particles, 1-cell buffer), adaptive CIC, |fR0| 1e-6, n 1, a 1; every "
                  "level solved to 1e-8 from a zero start; force gathered to the particles")
 
 SAMPLE_DESC = ("full FP64 oracle particle solve (structure, adaptive CIC, every level to 1e-8, "
-               "particle force) of a 32^3-base sample: box 12.5 Mpc/h (same cell size), nbar 1, "
-               "sigma_g 1.5, 2 refinement levels, |fR0| 1e-5")
+               "particle force) of a 32^3-base sample: box 6.25 Mpc/h (same cell size), nbar 1, "
+               "sigma_g 2.0, 3 refinement levels, |fR0| 1e-6")
 
 
-def cpu_baseline_sample(max_seconds: float = 20.0) -> dict:
-    """The CPU oracle (single thread, FP64) on a bounded sample of the workload."""
-    t0 = time.perf_counter()
-    upd = dt = 0.0
-    n = 0
-    while n < 1 or (time.perf_counter() - t0 < max_seconds / 2 and n < 8):
-        u, t = _oracle_particle_sample()
-        upd += u
-        dt += t
-        n += 1
-    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} x {SAMPLE_DESC}, {dt:.1f} s"}
+def cpu_baseline_sample(max_seconds: float = 12.0) -> dict:
+    """The CPU oracle (FP64) on a bounded sample of the workload, on all host
+    cores (OpenMP over each red-black colour; bit-identical to one thread) and
+    on one core."""
+    nproc = os.cpu_count() or 1
+    res = {}
+    for threads in (nproc, 1):
+        t0 = time.perf_counter()
+        upd = dt = 0.0
+        n = 0
+        while n < 1 or (time.perf_counter() - t0 < max_seconds and n < 6):
+            u, t = _oracle_particle_sample(threads)
+            upd += u
+            dt += t
+            n += 1
+        res[threads] = (upd / dt, n, dt)
+    v, n, dt = res[nproc]
+    v1, n1, dt1 = res[1]
+    return {"value": v, "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "sample": f"{n} x {SAMPLE_DESC}, {dt:.1f} s on {nproc} threads",
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": f"{n1} x the same sample, {dt1:.1f} s"},
+            "host": host_cpu()}
 
 
 def run_reference(args, rank: int) -> None:
     if rank != 0:
         return
+    threads = os.cpu_count() or 1
     for _ in range(args.warmup):
-        _oracle_particle_sample()
+        _oracle_particle_sample(threads)
     upd = dt = 0.0
     for _ in range(args.steps):
-        u, t = _oracle_particle_sample()
+        u, t = _oracle_particle_sample(threads)
         upd += u
         dt += t
     val = upd / dt
@@ -190,14 +241,67 @@ def run_reference(args, rank: int) -> None:
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC, "parallelism": f"replicas x{args.gpus}"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": "one " + SAMPLE_DESC + " per step (a bounded sample "
-                                       "of the workload)"},
+                                       "of the workload), OpenMP over each red-black colour",
+                             "host": host_cpu()},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def batched_extra(mgfr, synth, torch, dev, local):
+# ---------------------------------------------------------------------------
+# extra workloads (reported beside the headline)
+# ---------------------------------------------------------------------------
+def grid32_extra(mgfr, torch, dev, local):
+    """32^3 periodic grid (delta lognormal, sigma_g 1), |fR0| 1e-5, plain FP64:
+    V-cycles, device time per V-cycle and cell-updates/s (L2-resident, so no
+    HBM roofline applies)."""
+    w = synth.WORKLOADS["grid32"]
+    d = torch.from_numpy(synth.lognormal_delta(w["N"], w["box"], w["sigma_g"], w["seed"])).to(dev)
+    s = mgfr.Solver(local, fr0_abs=w["fr0"], precision=mgfr.PREC_FP64)
+    for _ in range(3):
+        s.solve_density(d, w["box"], w["a"], want_acc=False)
+    rows = []
+    for _ in range(20):
+        o = s.solve_density(d, w["box"], w["a"], want_acc=False)
+        rows.append(o["stats"])
+    s.close()
+    t = statistics.median(r["t_solve_ms"] for r in rows)
+    vc = rows[0]["vcycles"]
+    upd = rows[0]["cell_updates"]
+    return {"workload": "grid32: 32^3 lognormal delta (sigma_g 1), box 100, |fR0| 1e-5, "
+                        "plain FP64 to 1e-8",
+            "vcycles": vc, "solve_ms": t, "us_per_vcycle": 1e3 * t / vc,
+            "cell_updates_per_s": upd / (t / 1e3)}
+
+
+def particles256_extra(mgfr, torch, dev, local, steps=5):
+    """256^3 particles, 2 levels, |fR0| 1e-5: mixed step time and FP64
+    time-to-tolerance."""
+    w = W256
+    d = synth.lognormal_delta(w["N"], w["box"], w["sigma_g"], w["seed"])
+    pos = torch.from_numpy(synth.poisson_particles(d, w["box"], w["nbar"], w["seed"])).to(dev)
+    out = {}
+    for prec, name, k in ((mgfr.PREC_MIXED, "mixed", steps), (mgfr.PREC_FP64, "fp64", 1)):
+        s = mgfr.Solver(local, fr0_abs=w["fr0"], precision=prec, max_level=w["lmax"])
+        s.solve_particles(pos, w["N"], w["box"], w["a"], want_fr=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        upd = 0
+        e0.record()
+        for _ in range(k):
+            st = s.solve_particles(pos, w["N"], w["box"], w["a"], want_fr=False)["stats"]
+            upd += st["cell_updates"]
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        out[name] = {"ms_per_solve": ms, "nonlinear_cell_updates_per_s": upd / k / (ms / 1e3)}
+        s.close()
+    return {"workload": "particles256: 256^3 particles (sigma_g 1.5), 256^3 base + 2 levels, "
+                        "|fR0| 1e-5, to 1e-8", **out}
+
+
+def batched_extra(mgfr, torch, dev, local):
     """96 independent periodic solves of 32^3/64^3/128^3 (about 32 each),
     sigma_g uniform in [0.5, 2], |fR0| log-uniform in [1e-6, 1e-4], box 100:
     one persistent launch (mixed precision, autotuned launch shape) against a
@@ -244,7 +348,7 @@ def batched_extra(mgfr, synth, torch, dev, local):
             "all_converged": ok}
 
 
-def learned_extra(mgfr, synth, learned, torch, dev, local):
+def learned_extra(mgfr, learned, torch, dev, local):
     """Learned start: the U-Net trained on 2000 solver-generated 64^3 samples
     (box 25, the 0.39 Mpc/h cell), then 256^3 / 100 Mpc/h fields, sigma_g in
     {0.5,1,1.5,2} x |fR0| in {1e-6,1e-5,1e-4}: V-cycles and time to 1e-8 from
@@ -290,6 +394,23 @@ def learned_extra(mgfr, synth, learned, torch, dev, local):
                          "fields": len(rows)}}
 
 
+def family_table(kern_ms, kern_n, kern_cells, steps, peak):
+    fams = []
+    for q in range(5):
+        if kern_n[q] == 0:
+            continue
+        a_ms = kern_ms[q] / kern_n[q]
+        cells = kern_cells[q] / kern_n[q]
+        gbs = ALG_BYTES[q] * cells / (a_ms / 1e3) / 1e9
+        fams.append({"kernel": KERNEL_NAMES[q], "bound": FAMILY_BOUND[q],
+                     "launches_per_step": kern_n[q] / steps, "avg_launch_us": 1e3 * a_ms,
+                     "alg_bytes_per_cell": ALG_BYTES[q], "achieved_gbs": gbs,
+                     "frac_of_hbm": gbs / peak,
+                     "with_table_gbs": (ALG_BYTES[q] + TABLE_BYTES[q]) * cells / (a_ms / 1e3) / 1e9,
+                     "ms_per_step": kern_ms[q] / steps})
+    return fams
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -298,12 +419,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched-solve and learned-start measurements")
+                    help="skip the other workloads (32^3 grid, 256^3 particles, batched, learned)")
     ap.add_argument("--only-mixed", action="store_true",
                     help="run only the timed mixed-precision steps (for profiler captures)")
     ap.add_argument("--profile-case", action="store_true",
-                    help="half the particle density (nbar 0.5): a smaller hierarchy for "
-                         "full-metric profiler captures (about 3 GB on the device)")
+                    help="a smaller sample of the workload for full-metric profiler captures: "
+                         "256^3 base in a 50 Mpc/h box (same cell size), nbar 0.5")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -315,7 +436,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_1305_2418_gb300 import build, mgfr, synth
+    from paper_1305_2418_gb300 import build, mgfr
     from paper_1305_2418_gb300 import dist as D
 
     build.build()
@@ -330,20 +451,19 @@ def main():
 
     w = dict(WORKLOAD)
     if args.profile_case:
-        w["nbar"] = 0.5
+        w.update(N=256, box=50.0, nbar=0.5)
     delta_h = synth.lognormal_delta(w["N"], w["box"], w["sigma_g"], w["seed"])
     pos_h = synth.poisson_particles(delta_h, w["box"], w["nbar"], w["seed"])
+    del delta_h
     pos = torch.from_numpy(pos_h).to(dev)
-    n = w["N"] ** 3
     n_part = pos_h.shape[0]
 
     def solver(prec, profile=1):
         return mgfr.Solver(local, fr0_abs=w["fr0"], precision=prec, profile=profile,
                            max_level=w["lmax"], refine_count=w["refine_count"])
 
-    def step(s, p=None, want_fr=False):
-        return s.solve_particles(pos if p is None else p, w["N"], w["box"], w["a"],
-                                 want_fr=want_fr)
+    def step(s, want_fr=False):
+        return s.solve_particles(pos, w["N"], w["box"], w["a"], want_fr=want_fr)
 
     if args.only_mixed:
         sm = solver(mgfr.PREC_MIXED, profile=0)
@@ -352,18 +472,17 @@ def main():
         torch.cuda.synchronize()
         sm.close()
         return
-    # ---- plain FP64 solve, time to tolerance (reported beside) ----
+
+    # ---- plain FP64 solve: time to tolerance, FP64-pipe figures ----
     s64 = solver(mgfr.PREC_FP64)
     step(s64)
     torch.cuda.synchronize()
-    t64 = []
-    for _ in range(2):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        o64 = step(s64)
-        e1.record()
-        torch.cuda.synchronize()
-        t64.append(e0.elapsed_time(e1))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    o64 = step(s64)
+    e1.record()
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1)
     st64 = o64["stats"]
     s64.close()
 
@@ -376,40 +495,22 @@ def main():
     clocks = Clocks(local)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    kern_ms = [0.0] * 6
-    kern_n = [0] * 6
-    kern_cells = [0] * 6
     launches = 0
-    upd = 0
+    upd = lin = 0
     e0.record()
     for _ in range(args.steps):
         out = step(sm)
         st = out["stats"]
         launches += st["gpu_launches"]
-        upd += st["cell_updates"] + st["linear_updates"]
+        upd += st["cell_updates"]
+        lin += st["linear_updates"]
     e1.record()
     torch.cuda.synchronize()
     barrier()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
-    # Same steps again with per-launch CUDA events around the profiled kernels
-    # (launched directly on the library's stream instead of from graphs).
-    sp = solver(mgfr.PREC_MIXED, profile=1)
-    step(sp)
-    torch.cuda.synchronize()
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record()
-    for _ in range(args.steps):
-        stp = step(sp)["stats"]
-        for q in range(5):
-            kern_ms[q] += stp["kern_ms"][q]
-            kern_n[q] += stp["kern_launches"][q]
-            kern_cells[q] += stp["kern_cells"][q]
-    p1.record()
-    torch.cuda.synchronize()
-    ms_prof = p0.elapsed_time(p1)
-    sp.close()
     value, ms_max = D.whole_job_rate(upd, ms, dev)
+    lin_value, _ = D.whole_job_rate(lin, ms, dev)
     last = st
 
     # ---- end to end through the public API: host buffers, copies timed ----
@@ -429,72 +530,107 @@ def main():
     e2e_upd = 0
     for _ in range(args.steps):
         r = step_host()
-        e2e_upd += r["stats"]["cell_updates"] + r["stats"]["linear_updates"]
+        e2e_upd += r["stats"]["cell_updates"]
     f1.record()
     torch.cuda.synchronize()
     e2e_value, _ = D.whole_job_rate(e2e_upd, f0.elapsed_time(f1), dev)
     sm.close()
+    del host_in, host_out
+
+    # ---- the same steps with CUDA events around each profiled launch ----
+    # (launched directly on the library's stream instead of from graphs)
+    ksteps = min(args.steps, 5)
+    kern_ms, kern_n, kern_cells = [0.0] * 6, [0] * 6, [0] * 6
+    sp = solver(mgfr.PREC_MIXED, profile=1)
+    step(sp)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    for _ in range(ksteps):
+        stp = step(sp)["stats"]
+        for q in range(5):
+            kern_ms[q] += stp["kern_ms"][q]
+            kern_n[q] += stp["kern_launches"][q]
+            kern_cells[q] += stp["kern_cells"][q]
+    p1.record()
+    torch.cuda.synchronize()
+    ms_prof = p0.elapsed_time(p1)
+    sp.close()
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant profiled kernel ----
-    # the dominant sweep family (the double-float residual is bound by
-    # arithmetic issue, not by HBM, and is reported in the family table only)
+    # ---- roofline of the dominant profiled kernel family ----
+    # (the double-float residual is bound by arithmetic issue, not by HBM, and
+    # is reported in the family table only)
+    peak, peak_kind = peaks()
     fam = max((q for q in range(5) if FAMILY_BOUND[q] == "hbm"), key=lambda q: kern_ms[q])
     avg_ms = kern_ms[fam] / max(kern_n[fam], 1)
-    bytes_per_launch = ALG_BYTES[fam] * kern_cells[fam] / max(kern_n[fam], 1)
-    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-    peak, peak_kind = peaks()
     cells_per_launch = kern_cells[fam] / max(kern_n[fam], 1)
+    bytes_per_launch = ALG_BYTES[fam] * cells_per_launch
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
     traffic = TRAFFIC_PER_CELL[fam] * cells_per_launch if fam in TRAFFIC_PER_CELL else None
     roof = {"bound": "hbm", "kernel": KERNEL_NAMES[fam], "achieved": achieved, "peak": peak,
             "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "launches": kern_n[fam], "avg_launch_us": 1e3 * avg_ms,
+            "cells_per_launch": cells_per_launch, "alg_bytes_per_cell": ALG_BYTES[fam],
             "alg_bytes_per_launch": bytes_per_launch,
             "kernel_share_of_step": kern_ms[fam] / ms_prof,
-            "profiled_ms_per_step": ms_prof / args.steps,
-            "per_family_ms": {KERNEL_NAMES[q]: kern_ms[q] / args.steps for q in range(5)}}
-    fams = []
-    for q in range(5):
-        if kern_n[q] == 0:
+            "profiled_ms_per_step": ms_prof / ksteps,
+            "families": family_table(kern_ms, kern_n, kern_cells, ksteps, peak)}
+    fp64 = {"bound": "fp64", "peak_tflops": FP64_PEAK_TFLOPS, "peak_source": "nominal",
+            "flops_per_update": FP64_FLOPS_PER_UPDATE, "families": []}
+    for q in (0, 3):
+        if st64["kern_launches"][q] == 0:
             continue
-        a_ms = kern_ms[q] / kern_n[q]
-        gbs = ALG_BYTES[q] * kern_cells[q] / kern_n[q] / (a_ms / 1e3) / 1e9
-        fams.append({"kernel": KERNEL_NAMES[q], "bound": FAMILY_BOUND[q],
-                     "launches_per_step": kern_n[q] / args.steps, "avg_launch_us": 1e3 * a_ms,
-                     "alg_bytes_per_cell": ALG_BYTES[q], "achieved_gbs": gbs,
-                     "frac_of_hbm": gbs / peak})
-    roof["families"] = fams
+        a_ms = st64["kern_ms"][q] / st64["kern_launches"][q]
+        cells = st64["kern_cells"][q] / st64["kern_launches"][q]
+        tfl = FP64_FLOPS_PER_UPDATE * cells / 2 / (a_ms / 1e3) / 1e12  # half the cells update
+        fp64["families"].append({"kernel": FP64_KERNEL_NAMES[q],
+                                 "launches": st64["kern_launches"][q],
+                                 "avg_launch_us": 1e3 * a_ms, "achieved_tflops": tfl,
+                                 "frac": tfl / FP64_PEAK_TFLOPS,
+                                 "ms_per_solve": st64["kern_ms"][q]})
 
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline_sample()
     extras = {}
     if not args.no_extras:
         from paper_1305_2418_gb300 import learned
-        extras["batched"] = batched_extra(mgfr, synth, torch, dev, local)
-        extras["learned_start"] = learned_extra(mgfr, synth, learned, torch, dev, local)
+        extras["grid32"] = grid32_extra(mgfr, torch, dev, local)
+        extras["particles256"] = particles256_extra(mgfr, torch, dev, local)
+        extras["batched"] = batched_extra(mgfr, torch, dev, local)
+        extras["learned_start"] = learned_extra(mgfr, learned, torch, dev, local)
 
+    nl = last["n_levels"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "particles": n_part,
-                   "levels_cells": last["cells_per_level"][:last["n_levels"]],
-                   "precision": "mixed (FP32 smoothing, FP64 residual/defect correction)",
-                   "l2": "working set (u, E, f FP64 + FP32 levels, ~700 MB) larger than L2",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC if not args.profile_case else
+                   "profile sample of particles512: 256^3 base, box 50, nbar 0.5",
+                   "particles": n_part,
+                   "levels_cells": last["cells_per_level"][:nl],
+                   "precision": "mixed (FP32 smoothing; residual and defect correction in "
+                                "double-float, about 48-bit)",
+                   "l2": "inputs larger than L2 (positions 3.2 GB; every level's arrays "
+                         "above 129 MB but level 3's FP32 ones)",
                    "parallelism": f"replicas x{world}"},
-        "time_to_tol_ms": {"mixed": ms_max / args.steps, "fp64": min(t64)},
+        "value_counts": "nonlinear NGS cell updates (all levels) per second of the whole step",
+        "linear_cell_updates_per_s": lin_value,
+        "time_to_tol_ms": {"mixed": ms_max / args.steps, "fp64": t64},
         "vcycles": {"mixed_fp32": last["vcycles"], "mixed_outer_fp64": last["outer_iters"],
                     "fp64": st64["vcycles"],
-                    "refined_levels_mixed": last["level_iters"][1:last["n_levels"]],
+                    "refined_levels_mixed": last["level_iters"][1:nl],
                     "refined_levels_fp64": st64["level_iters"][1:st64["n_levels"]]},
         "cell_updates_per_step": {"nonlinear": last["cell_updates"],
                                   "linear": last["linear_updates"],
                                   "fp64_path": st64["cell_updates"]},
         "res_rel_final": last["res_l2_final"] / last["f_l2"],
+        "level_res": last["level_res"][:nl],
         "roofline": roof,
+        "fp64_roofline": fp64,
         "clocks": ck,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * n_part,

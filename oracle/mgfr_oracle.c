@@ -11,6 +11,11 @@
  * Everything is FP64, round-to-nearest, compiled without contraction
  * (-ffp-contract=off) and without fast-math, written for legibility: loops
  * over cells in the order the paper describes, no blocking, no fusion.
+ * Loops whose iterations write distinct cells and read only values no other
+ * iteration of the same loop writes (one colour of a red-black sweep, a
+ * residual, a restriction or prolongation) may run on several threads
+ * (OpenMP, orc_set_threads); sums and the particle deposit stay sequential,
+ * so every result is bit-identical to the single-threaded run.
  *
  * What it computes (paper section / equation in brackets):
  *   - model constants: background curvature R(a) and background field
@@ -56,6 +61,22 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the parallel loops (<= 0: all available); returns the count
+ * in use.  Without OpenMP the oracle runs on one thread. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n <= 0) n = omp_get_num_procs();
+  omp_set_num_threads(n);
+  return n;
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 #define ORC_MAXLEV 16
 #define ORC_CLIGHT_OVER_H0 2997.92458 /* c / H0 in Mpc/h */
@@ -184,6 +205,7 @@ static void dense_rb_sweep(double* u, const double* f, int N, double h, const or
                            double step_cap) {
   double ih2 = 1.0 / (h * h);
   for (int colour = 0; colour < 2; ++colour)
+#pragma omp parallel for schedule(static) if (N >= 32)
     for (int i = 0; i < N; ++i)
       for (int j = 0; j < N; ++j)
         for (int k = 0; k < N; ++k) {
@@ -199,6 +221,7 @@ static void dense_rb_sweep(double* u, const double* f, int N, double h, const or
 static void dense_residual(const double* u, const double* f, int N, double h, const orc_model* m,
                            double* r) {
   double ih2 = 1.0 / (h * h);
+#pragma omp parallel for schedule(static) if (N >= 32)
   for (int i = 0; i < N; ++i)
     for (int j = 0; j < N; ++j)
       for (int k = 0; k < N; ++k) {
@@ -223,6 +246,7 @@ static double normmax(const double* a, long n) {
 /* Restriction R [Sec. 3.3]: parent value = average of its 8 daughters. */
 static void dense_restrict(const double* fine, int Nf, double* coarse) {
   int Nc = Nf / 2;
+#pragma omp parallel for schedule(static) if (Nc >= 32)
   for (int I = 0; I < Nc; ++I)
     for (int J = 0; J < Nc; ++J)
       for (int K = 0; K < Nc; ++K) {
@@ -242,6 +266,7 @@ static void dense_restrict(const double* fine, int Nf, double* coarse) {
  */
 static void dense_prolong_add(const double* coarse, int Nc, double* fine, int linear) {
   int Nf = 2 * Nc;
+#pragma omp parallel for schedule(static) if (Nf >= 32)
   for (int i = 0; i < Nf; ++i)
     for (int j = 0; j < Nf; ++j)
       for (int k = 0; k < Nf; ++k) {
@@ -306,6 +331,7 @@ static void dense_vcycle(double* u, const double* f, int N, double h, const orc_
   dense_restrict(u, N, uc);
   dense_restrict(r, N, rc);
   double ihc2 = 1.0 / (hc * hc);
+#pragma omp parallel for schedule(static) if (Nc >= 32)
   for (int I = 0; I < Nc; ++I)
     for (int J = 0; J < Nc; ++J)
       for (int K = 0; K < Nc; ++K) {
@@ -862,6 +888,7 @@ static void graph_build(const orc_amr* A, int l, level_graph* G, int linear) {
   G->nb = (long long*)malloc(sizeof(long long) * 6 * (size_t)n);
   G->ghost = (double*)calloc(6 * (size_t)n, sizeof(double));
   G->colour = (unsigned char*)malloc((size_t)n);
+#pragma omp parallel for schedule(static) if (n >= 32768)
   for (long long c = 0; c < n; ++c) {
     int64_t I, J, K;
     cell_coords(A, l, c, &I, &J, &K);
@@ -912,11 +939,11 @@ static double graph_dL(const level_graph* G, const double* u, long long c, doubl
 static double graph_residual(const level_graph* G, const double* u, const double* f, double h,
                              const orc_model* m, double* r) {
   double ih2 = 1.0 / (h * h), s = 0.0;
-  for (long long c = 0; c < G->n; ++c) {
-    double rc = f[c] - graph_L(G, u, c, ih2, m);
-    if (r) r[c] = rc;
-    s += rc * rc;
-  }
+  double* rr = r ? r : (double*)malloc(sizeof(double) * (size_t)G->n);
+#pragma omp parallel for schedule(static) if (G->n >= 32768)
+  for (long long c = 0; c < G->n; ++c) rr[c] = f[c] - graph_L(G, u, c, ih2, m);
+  for (long long c = 0; c < G->n; ++c) s += rr[c] * rr[c];
+  if (!r) free(rr);
   return sqrt(s);
 }
 
@@ -924,6 +951,7 @@ static void graph_rb_sweep(const level_graph* G, double* u, const double* f, dou
                            const orc_model* m, double step_cap) {
   double ih2 = 1.0 / (h * h);
   for (int colour = 0; colour < 2; ++colour)
+#pragma omp parallel for schedule(static) if (G->n >= 32768)
     for (long long c = 0; c < G->n; ++c) {
       if (G->colour[c] != colour) continue;
       double step = (graph_L(G, u, c, ih2, m) - f[c]) / graph_dL(G, u, c, ih2, m);

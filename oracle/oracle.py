@@ -22,7 +22,7 @@ _LIB = os.path.join(_LIBDIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-fopenmp"]
 
 
 def build(force: bool = False) -> str:
@@ -43,6 +43,7 @@ def lib():
             d, i, ll, vp = C.c_double, C.c_int, C.c_longlong, C.c_void_p
             P = C.POINTER
             sig = {
+                "orc_set_threads": (i, [i]),
                 "orc_model_constants": (None, [d, d, i, d, vp]),
                 "orc_effective_density": (None, [ll, vp, vp, d, d, i, d, vp]),
                 "orc_amr_effective_pm": (None, [vp, i, vp]),
@@ -81,8 +82,15 @@ def lib():
                 fn = getattr(L, name)
                 fn.restype = res
                 fn.argtypes = args
+            L.orc_set_threads(1)  # one thread unless set_threads asks for more
             _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops (<= 0: all cores; 1 after
+    loading); results do not depend on it.  Returns the number in use."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def _p(a: np.ndarray | None):

@@ -1497,8 +1497,9 @@ struct SolveCtx {
   Model m;
   int L;
   float mthr;
-  long long updates;
+  long long updates;      // nonlinear NGS cell updates (tree levels)
   int kmax;  // deepest dense level below the base holding a relaxed cell (0: none)
+  long long lin_updates = 0;  // FP32 linear Gauss-Seidel cell updates (tree levels)
 };
 
 // whether the coarse grid below tree level l >= 1 of the level-S.L solve has
@@ -1850,7 +1851,7 @@ void lin_vcycle_tree(SolveCtx& S, int l) {
   AmrLevel& F = A->L[l];
   const int npre = sweeps_of(S, l, g.n_pre), npost = sweeps_of(S, l, g.n_post);
   lin_relax(S, l, npre);
-  S.updates += (long long)npre * F.relaxed;
+  S.lin_updates += (long long)npre * F.relaxed;
   const unsigned char* fmask = l == S.L ? nullptr : F.act;
   if (l >= 1 && has_coarse(S, l)) {
     AmrLevel& P = A->L[l - 1];
@@ -1882,7 +1883,7 @@ void lin_vcycle_tree(SolveCtx& S, int l) {
     c->launches += 1;
   }
   lin_relax(S, l, npost);
-  S.updates += (long long)npost * F.relaxed;
+  S.lin_updates += (long long)npost * F.relaxed;
 }
 
 // FP64 residual of level L with the linear system set up for phase B
@@ -2128,6 +2129,7 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
     st->level_iters[Lv] = it + it32;
     st->level_res[Lv] = r / ref;
     st->cell_updates += S.updates;
+    st->linear_updates += S.lin_updates;
   }
   if (!(r <= target)) return set_err(c, MGFR_E_NOCONVERGE, "refined level did not converge");
   return MGFR_OK;
