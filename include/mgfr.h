@@ -86,7 +86,25 @@ typedef struct {
   int n_coarse;        /* red-black sweeps before and after the coarse grid
                           on the coarser levels of a refined-level solve
                           (0: n_pre and n_post, the default)               */
+  int start;           /* mgfr_start: initial guess of the (base-level) solve */
 } mgfr_config;
+
+/* Initial guess of a solve.  The paper starts each step from the previous
+ * step's solution (Sec. 3.3, step 2); the learned start is an addition of
+ * this library.
+ *   MGFR_START_ZERO    u = 0 unless the call passes u_init (the default);
+ *   MGFR_START_USER    u = u_init, which the call must pass (MGFR_E_INVALID
+ *                      if it is NULL): the previous-step warm start;
+ *   MGFR_START_LEARNED u = the context's network (mgfr_unet_init or
+ *                      mgfr_unet_load) applied to the density contrast with
+ *                      the context's |fR0|, n and Omega_m; u_init must be
+ *                      NULL.  The grid (the base grid of a particle solve)
+ *                      must be a power of two in [32, 512].  Batch items
+ *                      keep a u_init_dev they pass; the others of 32^3 and
+ *                      more are predicted in groups of one size, those below
+ *                      32^3 start from zero.  The prediction runs inside the
+ *                      call, on the context's stream. */
+typedef enum { MGFR_START_ZERO = 0, MGFR_START_USER = 1, MGFR_START_LEARNED = 2 } mgfr_start;
 
 typedef struct {
   int vcycles;               /* nonlinear V-cycles (all precisions), base level */
@@ -120,7 +138,7 @@ typedef struct {
 /* Fill *cfg with the defaults above (omega_m 0.3, fr0_abs 1e-5, n 1, FP64,
  * tol 1e-8, 2+2 sweeps, 100 V-cycles, linear prolongation, step cap 2,
  * max_level 0, refine_count 8, mixed_switch 3e-6, mixed_inner 3,
- * mask_thres 0.99, n_coarse 0). */
+ * mask_thres 0.99, n_coarse 0, start MGFR_START_ZERO). */
 void mgfr_config_default(mgfr_config* cfg);
 
 /* Create a context on CUDA device `device`, working on `cuda_stream`
@@ -135,7 +153,8 @@ mgfr_status mgfr_set_config(mgfr_ctx* ctx, const mgfr_config* cfg);
  *   delta_dev   [N^3] FP64 density contrast rho/rho_bar - 1 (C order).
  *   N           power of two, 8 <= N <= 1024.   box > 0, a > 0.
  *   u_init_dev  [N^3] FP64 initial guess for u, or NULL for u = 0
- *               (the previous-step warm start of Sec. 3.3, step 2).
+ *               (the previous-step warm start of Sec. 3.3, step 2); see
+ *               cfg.start for the learned start.
  *   fr_out_dev  [N^3] FP64 f_R (required).
  *   acc_out_dev [3][N^3] FP64 a_MG / c^2, or NULL.
  *   u_out_dev   [N^3] FP64 solution u, or NULL.
@@ -160,7 +179,9 @@ mgfr_status mgfr_solve_density(mgfr_ctx* ctx, const double* delta_dev, int N, do
  *   Solve: base level as mgfr_solve_density, then each refined level in turn
  *   with ghost cells and initial guess prolonged from the converged coarser
  *   level (one-way interface); the coarser solutions are not modified.
- *   u_init_dev   [N_base^3] initial guess of the base level or NULL.
+ *   u_init_dev   [N_base^3] initial guess of the base level or NULL (cfg.start
+ *                as for mgfr_solve_density; the learned start predicts the
+ *                base level from its deposited density contrast).
  *   fr_base_out_dev [N_base^3] f_R on the base level, or NULL.
  *   acc_out_dev  [Np][3] a_MG / c^2 at the particles, gathered from the leaf
  *                cells with the mass-assignment weights, or NULL.
@@ -243,9 +264,10 @@ typedef struct {
   double fr0_abs;            /* |fR_bar0| of this solve (omega_m from cfg)    */
   int n;                     /* Hu-Sawicki exponent                           */
   const double* delta_dev;   /* [N^3] density contrast                        */
-  const double* u_init_dev;  /* [N^3] initial guess or NULL (zero start)      */
+  const double* u_init_dev;  /* [N^3] initial guess or NULL (cfg.start)       */
   double* fr_out_dev;        /* [N^3] f_R                                     */
   double* acc_out_dev;       /* [3][N^3] a_MG / c^2, or NULL                  */
+  double* u_out_dev;         /* [N^3] the solution u = ln(f_R / fR_bar), or NULL */
 } mgfr_batch_item;
 
 /*
@@ -296,8 +318,30 @@ mgfr_status mgfr_unet_train_step(mgfr_ctx* ctx, int B, int D, const double* delt
 mgfr_status mgfr_unet_predict(mgfr_ctx* ctx, int D, const double* delta_dev, double fr0_abs,
                               double* u_out_dev);
 /* Copy the FP32 master parameters to (set = 0) or from (set = 1) host memory;
- * *count receives their number (host may be NULL to query it). */
+ * *count receives their number (host may be NULL to query it).
+ * Network and parameter layout: the input is 16 channels per voxel
+ * [ln(1 + delta), log10|fR0| + 5, 1, u_scr, 0 x 12] with the local screening
+ * value u_scr = -(n+1) ln(1 + Om delta / Rt) at a = 1 (clamped to [-20, 5];
+ * logarithm arguments floored at 1e-3 and 1e-6).  Encoder levels 0..2:
+ * e_l = relu(conv(relu(conv(p_l)))) with 16/32/64 channels, p_0 = input,
+ * p_{l+1} = 2^3 average of e_l; bottom: the same with 128 channels on p_3;
+ * decoder levels 2..0: d_l = relu(conv(relu(conv([up(d_{l+1}), e_l])))) with
+ * 64/32/16 channels (nearest upsampling, upsampled channels first);
+ * head v = w . d_0 + c; u = 0.01 sinh(v).  Activations, pre-activation
+ * gradients and the convolutions' weight copies are BF16; accumulation,
+ * biases, the head and the master parameters are FP32.  The flat parameter
+ * vector holds, for the 14 convolutions in the order enc0a, enc0b, enc1a,
+ * enc1b, enc2a, enc2b, bottom a, bottom b, dec2a, dec2b, dec1a, dec1b, dec0a,
+ * dec0b, W [27][Cin][Cout] then b [Cout]; then the head's 16 weights and its
+ * bias (1,466,065 values). */
 mgfr_status mgfr_unet_params(mgfr_ctx* ctx, int set, float* host, long long* count);
+/* Write the network's FP32 master parameters to the file `path` (8-byte
+ * tag "MGFRUNT1", the parameter count as a little-endian int64, then the
+ * parameters as little-endian FP32), or read such a file into the context's
+ * network (created if needed; the optimiser state restarts).  MGFR_E_INVALID
+ * if the file cannot be opened, is truncated or holds another count. */
+mgfr_status mgfr_unet_save(mgfr_ctx* ctx, const char* path);
+mgfr_status mgfr_unet_load(mgfr_ctx* ctx, const char* path);
 /* Gradients of the last training step (same layout as the parameters). */
 mgfr_status mgfr_unet_grads(mgfr_ctx* ctx, float* host);
 /* One convolution of the network on caller device buffers (NDHWC, channel

@@ -1152,9 +1152,11 @@ static mgfr_status solve_particles(mgfr_ctx* c, const double* pos, long long Np,
   MG_CK(c, cudaStreamSynchronize(c->s));
   if (flags & 2) return set_err(c, MGFR_E_INVALID, "non-finite particle position");
   if (flags & 1) return set_err(c, MGFR_E_UNSUPPORTED, "cloud-in-cell split stack overflow");
-  // base level
+  // base level (the learned start predicts it from delta = f / src)
   DenseLevel& L0 = H.L[0];
-  f64::init_u(u_init, L0.u, L0.E, L0.n, c->s);
+  const double* u0 = nullptr;
+  TRY(start_guess(c, N0, L0.f, 1.0 / m.src, u_init, &u0));
+  f64::init_u(u0, L0.u, L0.E, L0.n, c->s);
   c->launches += 1;
   MG_CK(c, cudaEventRecord(c->t0, c->s));
   mgfr_status rs = mixed ? dense_solve_mixed(c, m, box, st) : dense_solve64(c, m, box, st);

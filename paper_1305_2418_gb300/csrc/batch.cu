@@ -43,6 +43,7 @@ struct BSolve {
   const double* uinit;
   double* fr_out;
   double* acc_out;
+  double* u_out;
 };
 
 enum { BM_A = 0, BM_B = 1, BM_TRANS = 2, BM_DONE = 3 };
@@ -600,6 +601,7 @@ __global__ void __launch_bounds__(512) k_batch(BArgs A) {
     const long long n = 1LL << (3 * lg);
     const int kk = (int)(t & M), jj = (int)((t >> lg) & M), ii = (int)(t >> (2 * lg));
     S.fr_out[t] = S.fbar * S.E64[t];
+    if (S.u_out) S.u_out[t] = S.u64[t];
     if (S.acc_out) {
       const double* E = S.E64;
       S.acc_out[t] = S.gscale * (E[cidx((ii + 1) & M, jj, kk, lg)] - E[cidx((ii - 1) & M, jj, kk, lg)]);
@@ -627,6 +629,9 @@ struct BatchWork {
   std::map<std::string, std::pair<int, int>> tuned;  // signature -> (threads, blocks/SM)
   cudaGraphExec_t gx = nullptr;
   std::string gkey;
+  // learned start: network input staging and the predicted initial guesses
+  double *lrn_in = nullptr, *lrn_out = nullptr;
+  long long lrn_in_cap = 0, lrn_out_cap = 0;
 };
 
 static void batch_release(BatchWork* B) {
@@ -643,6 +648,69 @@ static void batch_release(BatchWork* B) {
   if (B->gx) cudaGraphExecDestroy(B->gx);
   B->gx = nullptr;
   B->gkey.clear();
+  if (B->lrn_in) cudaFree(B->lrn_in);
+  if (B->lrn_out) cudaFree(B->lrn_out);
+  B->lrn_in = B->lrn_out = nullptr;
+  B->lrn_in_cap = B->lrn_out_cap = 0;
+}
+
+// Learned start of the batch items of N >= 32 without an initial guess: their
+// density contrasts are staged in groups of one size (at most kLearnVox cells
+// per network pass) and the predictions kept in lrn_out for the solve.
+constexpr long long kLearnVox = 1LL << 22;
+
+static mgfr_status batch_learned_start(mgfr_ctx* c, BatchWork* B, const mgfr_batch_item* items,
+                                       const std::vector<int>& order, std::vector<BSolve>& hs) {
+  long long total = 0;
+  const int ns = (int)order.size();
+  for (int q = 0; q < ns; ++q)
+    if (hs[q].N >= 32 && !items[order[q]].u_init_dev) total += 1LL << (3 * hs[q].lg);
+  if (total == 0) return MGFR_OK;
+  if (B->lrn_out_cap < total) {
+    if (B->lrn_out) cudaFree(B->lrn_out);
+    B->lrn_out = nullptr;
+    B->lrn_out_cap = 0;
+    MG_CK(c, cudaMalloc(&B->lrn_out, sizeof(double) * (size_t)total));
+    B->lrn_out_cap = total;
+  }
+  long long off = 0;
+  int q = 0;
+  while (q < ns) {
+    // a run of solves of one size (order is sorted by size)
+    if (hs[q].N < 32 || items[order[q]].u_init_dev) {
+      ++q;
+      continue;
+    }
+    const int N = hs[q].N;
+    const long long per = 1LL << (3 * hs[q].lg);
+    std::vector<int> grp;
+    std::vector<double> fr0;
+    while (q < ns && hs[q].N == N && (long long)(grp.size() + 1) * per <= std::max(per, kLearnVox)) {
+      if (!items[order[q]].u_init_dev) {
+        grp.push_back(q);
+        fr0.push_back(items[order[q]].fr0_abs);
+      }
+      ++q;
+    }
+    if (grp.empty()) continue;
+    const long long need = per * (long long)grp.size();
+    if (B->lrn_in_cap < need) {
+      if (B->lrn_in) cudaFree(B->lrn_in);
+      B->lrn_in = nullptr;
+      B->lrn_in_cap = 0;
+      MG_CK(c, cudaMalloc(&B->lrn_in, sizeof(double) * (size_t)need));
+      B->lrn_in_cap = need;
+    }
+    for (size_t k = 0; k < grp.size(); ++k)
+      MG_CK(c, cudaMemcpyAsync(B->lrn_in + k * per, items[order[grp[k]]].delta_dev,
+                               sizeof(double) * (size_t)per, cudaMemcpyDeviceToDevice, c->s));
+    mgfr_status rs = unet_predict_batch(c, (int)grp.size(), N, B->lrn_in, 1.0, fr0.data(),
+                                        B->lrn_out + off);
+    if (rs != MGFR_OK) return rs;
+    for (size_t k = 0; k < grp.size(); ++k) hs[grp[k]].uinit = B->lrn_out + off + k * per;
+    off += need;
+  }
+  return MGFR_OK;
 }
 
 void batch_free(mgfr_ctx* c) {
@@ -714,6 +782,8 @@ mgfr_status mgfr_batch_solve(mgfr_ctx* c, int nsolves, const mgfr_batch_item* it
     if (!(it.box > 0.0) || !(it.a > 0.0) || !(it.fr0_abs > 0.0) || it.n < 1 || !it.delta_dev ||
         !it.fr_out_dev)
       return set_err(c, MGFR_E_INVALID, "invalid batch item");
+    if (g.start == MGFR_START_USER && !it.u_init_dev)
+      return set_err(c, MGFR_E_INVALID, "start = user needs u_init_dev on every batch item");
   }
   auto w0 = std::chrono::steady_clock::now();
   MG_CK(c, cudaSetDevice(c->device));
@@ -789,6 +859,7 @@ mgfr_status mgfr_batch_solve(mgfr_ctx* c, int nsolves, const mgfr_batch_item* it
     S.uinit = it.u_init_dev;
     S.fr_out = it.fr_out_dev;
     S.acc_out = it.acc_out_dev;
+    S.u_out = it.u_out_dev;
   }
   if (!B->dS) MG_CK(c, cudaMalloc(&B->dS, sizeof(BSolve) * nsolves));
   if (!B->dst) MG_CK(c, cudaMalloc(&B->dst, sizeof(BState) * nsolves));
@@ -796,6 +867,10 @@ mgfr_status mgfr_batch_solve(mgfr_ctx* c, int nsolves, const mgfr_batch_item* it
   if (!B->err) MG_CK(c, cudaMalloc(&B->err, 2 * sizeof(int)));
   MG_CK(c, cudaEventRecord(c->ev_in, c->user));
   MG_CK(c, cudaStreamWaitEvent(c->s, c->ev_in, 0));
+  if (g.start == MGFR_START_LEARNED) {
+    mgfr_status ls = batch_learned_start(c, B, items, order, hs);
+    if (ls != MGFR_OK) return ls;
+  }
   MG_CK(c, cudaMemcpyAsync(B->dS, hs.data(), sizeof(BSolve) * nsolves, cudaMemcpyHostToDevice, c->s));
   MG_CK(c, cudaMemsetAsync(B->dst, 0, sizeof(BState) * nsolves, c->s));
   BArgs A{};

@@ -149,7 +149,21 @@ struct mgfr_ctx {
   int capturing = -1;            // graph being captured (-1: none)
   long long graph_kernels[4] = {0, 0, 0, 0};  // kernel nodes per captured graph
   long long launches = 0;        // kernels launched by the current call
+  double* u_learn = nullptr;     // learned initial guess of a solve (MGFR_START_LEARNED)
+  long long u_learn_cap = 0;
 };
+
+// Network prediction for B boxes of D^3 cells (unet.cu): u_out [B][D^3] from
+// the density contrast dscale * x [B][D^3] (device) and |fR0| per box (host),
+// on the context's stream, without synchronising.  MGFR_E_INVALID when there
+// is no network or D is not a power of two in [32, 512].
+mgfr_status unet_predict_batch(mgfr_ctx* c, int B, int D, const double* x, double dscale,
+                               const double* fr0_host, double* u_out);
+// The initial guess of a base-level solve under cfg.start: *u0 = u_init
+// (zero / user start) or the network's prediction from dscale * x (learned),
+// held in context workspace (solver.cu).
+mgfr_status start_guess(mgfr_ctx* c, int N, const double* x, double dscale, const double* u_init,
+                        const double** u0);
 
 // Count of kernel nodes in a graph.
 long long count_kernel_nodes(cudaGraph_t g);

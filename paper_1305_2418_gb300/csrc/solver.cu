@@ -127,6 +127,7 @@ void mgfr_config_default(mgfr_config* c) {
   c->max_spins = 1LL << 26;
   c->mask_thres = 0.99;
   c->n_coarse = 0;
+  c->start = MGFR_START_ZERO;
 }
 
 }  // extern "C"
@@ -155,7 +156,31 @@ bool validate_cfg(const mgfr_config* c, std::string& why) {
   if (c->max_spins < 0) return bad("max_spins must be >= 0");
   if (!(c->mask_thres >= 0.0 && c->mask_thres < 1.0)) return bad("mask_thres in [0, 1)");
   if (c->n_coarse < 0 || c->n_coarse > 16) return bad("n_coarse in [0, 16]");
+  if (c->start != MGFR_START_ZERO && c->start != MGFR_START_USER && c->start != MGFR_START_LEARNED)
+    return bad("start must be 0 (zero), 1 (user) or 2 (learned)");
   return true;
+}
+
+mgfr_status start_guess(mgfr_ctx* c, int N, const double* x, double dscale, const double* u_init,
+                        const double** u0) {
+  *u0 = u_init;
+  if (c->cfg.start == MGFR_START_USER && !u_init)
+    return set_err(c, MGFR_E_INVALID, "start = user needs u_init");
+  if (c->cfg.start != MGFR_START_LEARNED) return MGFR_OK;
+  if (u_init) return set_err(c, MGFR_E_INVALID, "start = learned takes no u_init");
+  const long long n = (long long)N * N * N;
+  if (c->u_learn_cap < n) {
+    if (c->u_learn) cudaFree(c->u_learn);
+    c->u_learn = nullptr;
+    c->u_learn_cap = 0;
+    MG_CK(c, cudaMalloc(&c->u_learn, sizeof(double) * (size_t)n));
+    c->u_learn_cap = n;
+  }
+  const double fr0 = c->cfg.fr0_abs;
+  mgfr_status rs = unet_predict_batch(c, 1, N, x, dscale, &fr0, c->u_learn);
+  if (rs != MGFR_OK) return rs;
+  *u0 = c->u_learn;
+  return MGFR_OK;
 }
 
 static void free_dense(DenseHier& H) {
@@ -606,6 +631,7 @@ void mgfr_destroy(mgfr_ctx* c) {
   amr_free(c);
   batch_free(c);
   unet_free(c);
+  if (c->u_learn) cudaFree(c->u_learn);
   for (auto e : c->evpool) cudaEventDestroy(e);
   c->evpool.clear();
   if (c->host_scal) cudaFreeHost(c->host_scal);
@@ -645,8 +671,10 @@ mgfr_status mgfr_solve_density(mgfr_ctx* c, const double* delta, int N, double b
   MG_CK(c, cudaStreamWaitEvent(c->s, c->ev_in, 0));
   DenseLevel& L0 = H.L[0];
   c->launches = 0;
+  const double* u0 = nullptr;
+  if ((rs = start_guess(c, N, delta, 1.0, u_init, &u0)) != MGFR_OK) return rs;
   f64::source(delta, L0.f, L0.n, m.src, c->s);
-  f64::init_u(u_init, L0.u, L0.E, L0.n, c->s);
+  f64::init_u(u0, L0.u, L0.E, L0.n, c->s);
   c->launches += 2;
   MG_CK(c, cudaEventRecord(c->t0, c->s));
   rs = mixed ? dense_solve_mixed(c, m, box, st) : dense_solve64(c, m, box, st);

@@ -46,10 +46,10 @@ const ConvSpec kConvs[14] = {
 // scales beyond the Compton length), clamped to [-20, 5].
 __global__ void k_features(const double* __restrict__ delta, const double* __restrict__ fr0s,
                            long long per, long long M, __nv_bfloat16* __restrict__ x,
-                           double scr, double np1) {
+                           double scr, double np1, double dscale) {
   const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (m >= M) return;
-  const double d = delta[m];
+  const double d = dscale * delta[m];
   const double fr0 = fr0s[m / per];
   __nv_bfloat16* o = x + m * 16;
   o[0] = __float2bfloat16((float)log(fmax(1.0 + d, 1e-3)));
@@ -522,6 +522,31 @@ static int lg_of(int D) {
   return lg;
 }
 
+static const char kUnetTag[9] = "MGFRUNT1";
+
+mgfr_status unet_predict_batch(mgfr_ctx* c, int B, int D, const double* x, double dscale,
+                               const double* fr0_host, double* u_out) {
+  if (!c->unet) return set_err(c, MGFR_E_INVALID, "no network (mgfr_unet_init or mgfr_unet_load)");
+  if (B < 1 || B > 4096 || D < 32 || D > 512 || (D & (D - 1)) || !x || !u_out || !fr0_host)
+    return set_err(c, MGFR_E_INVALID, "network input: D must be a power of two in [32, 512]");
+  for (int b = 0; b < B; ++b)
+    if (!(fr0_host[b] > 0.0)) return set_err(c, MGFR_E_INVALID, "network input: |fR0| > 0");
+  UNet* U = (UNet*)c->unet;
+  mgfr_status rs = unet_alloc(c, U, B, lg_of(D));
+  if (rs != MGFR_OK) return rs;
+  const long long per = (long long)D * D * D, M0 = per * B;
+  MG_CK(c, cudaMemcpyAsync(U->fr0d, fr0_host, sizeof(double) * B, cudaMemcpyHostToDevice, c->s));
+  const Model mm = make_model(c->cfg, 1.0);
+  k_features<<<nblocks(M0, BS), BS, 0, c->s>>>(x, U->fr0d, per, M0, U->X0, c->cfg.omega_m / mm.Rt,
+                                               (double)(c->cfg.n + 1), dscale);
+  forward(c, U);
+  k_out_to_double<<<nblocks(M0, BS), BS, 0, c->s>>>(U->OUT, u_out, M0);
+  c->launches += 2;
+  // fr0_host may be a caller's stack value: the copy must be done before return
+  MG_CK(c, cudaStreamSynchronize(c->s));
+  return MGFR_OK;
+}
+
 extern "C" {
 
 mgfr_status mgfr_unet_init(mgfr_ctx* c, unsigned long long seed) {
@@ -545,7 +570,8 @@ mgfr_status mgfr_unet_train_step(mgfr_ctx* c, int B, int D, const double* delta_
   MG_CK(c, cudaMemcpyAsync(U->fr0d, fr0_host, sizeof(double) * B, cudaMemcpyHostToDevice, c->s));
   const Model mm = make_model(c->cfg, 1.0);
   k_features<<<nblocks(M0, BS), BS, 0, c->s>>>(delta_dev, U->fr0d, (long long)D * D * D, M0, U->X0,
-                                               c->cfg.omega_m / mm.Rt, (double)(c->cfg.n + 1));
+                                               c->cfg.omega_m / mm.Rt, (double)(c->cfg.n + 1),
+                                               1.0);
   forward(c, U);
   const int nb = 1024;
   k_mse<<<nb, BS, 0, c->s>>>(U->OUT, u_target_dev, M0, U->GOUT, U->lossp);
@@ -568,22 +594,85 @@ mgfr_status mgfr_unet_train_step(mgfr_ctx* c, int B, int D, const double* delta_
 
 mgfr_status mgfr_unet_predict(mgfr_ctx* c, int D, const double* delta_dev, double fr0_abs,
                               double* u_out_dev) {
-  if (!c || !c->unet) return c ? set_err(c, MGFR_E_INVALID, "call mgfr_unet_init first") : MGFR_E_INVALID;
-  if (D < 32 || D > 512 || (D & (D - 1)) || !delta_dev || !u_out_dev || !(fr0_abs > 0.0))
+  if (!c) return MGFR_E_INVALID;
+  if (!delta_dev || !u_out_dev || !(fr0_abs > 0.0))
     return set_err(c, MGFR_E_INVALID, "bad U-Net input");
-  UNet* U = (UNet*)c->unet;
   MG_CK(c, cudaSetDevice(c->device));
-  mgfr_status rs = unet_alloc(c, U, 1, lg_of(D));
+  MG_CK(c, cudaEventRecord(c->ev_in, c->user));
+  MG_CK(c, cudaStreamWaitEvent(c->s, c->ev_in, 0));
+  mgfr_status rs = unet_predict_batch(c, 1, D, delta_dev, 1.0, &fr0_abs, u_out_dev);
   if (rs != MGFR_OK) return rs;
-  const long long M0 = (long long)D * D * D;
-  MG_CK(c, cudaMemcpyAsync(U->fr0d, &fr0_abs, sizeof(double), cudaMemcpyHostToDevice, c->s));
-  const Model mm = make_model(c->cfg, 1.0);
-  k_features<<<nblocks(M0, BS), BS, 0, c->s>>>(delta_dev, U->fr0d, M0, M0, U->X0,
-                                               c->cfg.omega_m / mm.Rt, (double)(c->cfg.n + 1));
-  forward(c, U);
-  k_out_to_double<<<nblocks(M0, BS), BS, 0, c->s>>>(U->OUT, u_out_dev, M0);
   MG_CK(c, cudaStreamSynchronize(c->s));
   MG_CK(c, cudaGetLastError());
+  return MGFR_OK;
+}
+
+mgfr_status mgfr_unet_save(mgfr_ctx* c, const char* path) {
+  if (!c || !path) return MGFR_E_INVALID;
+  if (!c->unet) return set_err(c, MGFR_E_INVALID, "no network (mgfr_unet_init or mgfr_unet_load)");
+  UNet* U = (UNet*)c->unet;
+  MG_CK(c, cudaSetDevice(c->device));
+  std::vector<float> h((size_t)U->nparam);
+  MG_CK(c, cudaStreamSynchronize(c->s));
+  MG_CK(c, cudaMemcpy(h.data(), U->P, sizeof(float) * h.size(), cudaMemcpyDeviceToHost));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return set_err(c, MGFR_E_INVALID, std::string("cannot open ") + path);
+  unsigned char hdr[16];
+  std::memcpy(hdr, kUnetTag, 8);
+  const unsigned long long n = (unsigned long long)U->nparam;
+  for (int q = 0; q < 8; ++q) hdr[8 + q] = (unsigned char)(n >> (8 * q));
+  bool ok = std::fwrite(hdr, 1, 16, f) == 16;
+  for (size_t i = 0; ok && i < h.size(); ++i) {
+    unsigned u;
+    std::memcpy(&u, &h[i], 4);
+    const unsigned char b[4] = {(unsigned char)u, (unsigned char)(u >> 8), (unsigned char)(u >> 16),
+                                (unsigned char)(u >> 24)};
+    ok = std::fwrite(b, 1, 4, f) == 4;
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? MGFR_OK : set_err(c, MGFR_E_INVALID, std::string("write failed: ") + path);
+}
+
+mgfr_status mgfr_unet_load(mgfr_ctx* c, const char* path) {
+  if (!c || !path) return MGFR_E_INVALID;
+  MG_CK(c, cudaSetDevice(c->device));
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return set_err(c, MGFR_E_INVALID, std::string("cannot open ") + path);
+  unsigned char hdr[16];
+  if (std::fread(hdr, 1, 16, f) != 16 || std::memcmp(hdr, kUnetTag, 8) != 0) {
+    std::fclose(f);
+    return set_err(c, MGFR_E_INVALID, "not a network parameter file");
+  }
+  unsigned long long n = 0;
+  for (int q = 0; q < 8; ++q) n |= (unsigned long long)hdr[8 + q] << (8 * q);
+  if (!c->unet) {
+    mgfr_status rs = unet_make(c, 0);
+    if (rs != MGFR_OK) {
+      std::fclose(f);
+      return rs;
+    }
+  }
+  UNet* U = (UNet*)c->unet;
+  if (n != (unsigned long long)U->nparam) {
+    std::fclose(f);
+    return set_err(c, MGFR_E_INVALID, "parameter count in the file does not match the network");
+  }
+  std::vector<float> h((size_t)n);
+  bool ok = true;
+  for (size_t i = 0; ok && i < h.size(); ++i) {
+    unsigned char b[4];
+    ok = std::fread(b, 1, 4, f) == 4;
+    const unsigned u = b[0] | ((unsigned)b[1] << 8) | ((unsigned)b[2] << 16) | ((unsigned)b[3] << 24);
+    std::memcpy(&h[i], &u, 4);
+  }
+  std::fclose(f);
+  if (!ok) return set_err(c, MGFR_E_INVALID, "truncated network parameter file");
+  MG_CK(c, cudaMemcpy(U->P, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice));
+  MG_CK(c, cudaMemset(U->M1, 0, sizeof(float) * h.size()));
+  MG_CK(c, cudaMemset(U->M2, 0, sizeof(float) * h.size()));
+  U->step = 0;
+  refresh_bf16(c, U);
+  MG_CK(c, cudaStreamSynchronize(c->s));
   return MGFR_OK;
 }
 

@@ -34,9 +34,9 @@ def make_training_set(solver: "mgfr.Solver", n: int, D: int, box: float, seed: i
     for s in range(0, n, chunk):
         e = min(n, s + chunk)
         outs, _ = solver.batch_solve([deltas[q] for q in range(s, e)], [box] * (e - s),
-                                     list(fr0s[s:e]))
+                                     list(fr0s[s:e]), want_u=True)
         for q, o in zip(range(s, e), outs):
-            us[q] = torch.log(o["fr"] / (-fr0s[q]))  # a = 1: fR_bar = -|fR0|
+            us[q] = o["u"]
     return deltas, fr0s, us
 
 

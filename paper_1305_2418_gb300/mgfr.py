@@ -17,6 +17,7 @@ MGFR_OK, MGFR_E_INVALID, MGFR_E_CUDA, MGFR_E_OOM, MGFR_E_NOCONVERGE, MGFR_E_TIME
     MGFR_E_UNSUPPORTED = range(7)
 STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "NOCONVERGE", "TIMEOUT", "UNSUPPORTED"]
 PREC_FP64, PREC_MIXED = 0, 1
+START_ZERO, START_USER, START_LEARNED = 0, 1, 2
 FIELD_U, FIELD_FR, FIELD_SOURCE, FIELD_MASS, FIELD_ACC, FIELD_COUNT = range(6)
 
 
@@ -28,6 +29,7 @@ class Config(C.Structure):
         ("step_cap", C.c_double), ("max_level", C.c_int), ("refine_count", C.c_int),
         ("mixed_switch", C.c_double), ("mixed_inner", C.c_int), ("max_spins", C.c_longlong),
         ("profile", C.c_int), ("mask_thres", C.c_double), ("n_coarse", C.c_int),
+        ("start", C.c_int),
     ]
 
 
@@ -55,7 +57,7 @@ class BatchItem(C.Structure):
     _fields_ = [
         ("N", C.c_int), ("box", C.c_double), ("a", C.c_double), ("fr0_abs", C.c_double),
         ("n", C.c_int), ("delta_dev", C.c_void_p), ("u_init_dev", C.c_void_p),
-        ("fr_out_dev", C.c_void_p), ("acc_out_dev", C.c_void_p),
+        ("fr_out_dev", C.c_void_p), ("acc_out_dev", C.c_void_p), ("u_out_dev", C.c_void_p),
     ]
 
 
@@ -98,6 +100,8 @@ SIGNATURES = {
     "mgfr_unet_predict": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_double, C.c_void_p]),
     "mgfr_unet_params": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "mgfr_unet_grads": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mgfr_unet_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "mgfr_unet_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "mgfr_nn_conv3d": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]),
@@ -266,7 +270,7 @@ class Solver:
         self._check(lib().mgfr_effective_mass_pm(self.h, lpm, _ptr(out)))
         return out
 
-    def _batch_items(self, deltas, boxes, a, fr0s, ns, u_inits, want_acc):
+    def _batch_items(self, deltas, boxes, a, fr0s, ns, u_inits, want_acc, want_u=False):
         import torch
         k = len(deltas)
         items = (BatchItem * k)()
@@ -275,19 +279,20 @@ class Solver:
             fr = torch.empty_like(d)
             acc = torch.empty((3,) + tuple(d.shape), dtype=d.dtype, device=d.device) \
                 if want_acc else None
-            outs.append({"fr": fr, "acc": acc})
+            u = torch.empty_like(d) if want_u else None
+            outs.append({"fr": fr, "acc": acc, "u": u})
             u0 = None if u_inits is None else u_inits[i]
             items[i] = BatchItem(d.shape[0], boxes[i], a[i], fr0s[i], ns[i], _ptr(d), _ptr(u0),
-                                 _ptr(fr), _ptr(acc))
+                                 _ptr(fr), _ptr(acc), _ptr(u))
         return items, outs
 
     def batch_solve(self, deltas, boxes, fr0s, a=None, ns=None, u_inits=None, want_acc=False,
-                    allow_noconverge=False):
+                    want_u=False, allow_noconverge=False):
         """Many independent periodic solves in one persistent launch (mgfr_batch_solve)."""
         k = len(deltas)
         a = [1.0] * k if a is None else a
         ns = [1] * k if ns is None else ns
-        items, outs = self._batch_items(deltas, boxes, a, fr0s, ns, u_inits, want_acc)
+        items, outs = self._batch_items(deltas, boxes, a, fr0s, ns, u_inits, want_acc, want_u)
         stats = (Stats * k)()
         st = lib().mgfr_batch_solve(self.h, k, items, stats)
         self._check(st, allow_noconverge)
@@ -337,6 +342,12 @@ class Solver:
         import numpy as np
         p = np.ascontiguousarray(p, dtype=np.float32)
         self._check(lib().mgfr_unet_params(self.h, 1, p.ctypes.data_as(C.c_void_p), None))
+
+    def unet_save(self, path: str):
+        self._check(lib().mgfr_unet_save(self.h, os.fsencode(path)))
+
+    def unet_load(self, path: str):
+        self._check(lib().mgfr_unet_load(self.h, os.fsencode(path)))
 
     def unet_grads(self):
         import numpy as np

@@ -45,9 +45,10 @@ def test_struct_layout_matches_header(tmp_path):
 #include <stddef.h>
 #include "mgfr.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(mgfr_config), sizeof(mgfr_stats),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mgfr_config), sizeof(mgfr_stats),
          offsetof(mgfr_config, profile), offsetof(mgfr_stats, kern_ms),
-         offsetof(mgfr_stats, level_res));
+         offsetof(mgfr_stats, level_res), offsetof(mgfr_config, start),
+         sizeof(mgfr_batch_item), offsetof(mgfr_batch_item, u_out_dev));
   return 0;
 }
 ''')
@@ -55,7 +56,9 @@ int main(void) {
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert vals == [C.sizeof(mgfr.Config), C.sizeof(mgfr.Stats), mgfr.Config.profile.offset,
-                    mgfr.Stats.kern_ms.offset, mgfr.Stats.level_res.offset]
+                    mgfr.Stats.kern_ms.offset, mgfr.Stats.level_res.offset,
+                    mgfr.Config.start.offset, C.sizeof(mgfr.BatchItem),
+                    mgfr.BatchItem.u_out_dev.offset]
 
 
 def test_default_config_and_validation(lib):
@@ -64,9 +67,11 @@ def test_default_config_and_validation(lib):
     assert cfg.tol_rel == 1e-8 and cfg.n_pre == 2 and cfg.n_post == 2
     assert lib.mgfr_version().decode().startswith("mgfr")
     assert cfg.n_coarse == 0 and cfg.mixed_inner == 3 and cfg.mask_thres == 0.99
+    assert cfg.start == mgfr.START_ZERO
     bad = [dict(fr0_abs=0.0), dict(n=0), dict(tol_rel=2.0), dict(n_pre=0, n_post=0),
            dict(precision=7), dict(omega_m=-1.0), dict(step_cap=0.0), dict(n_coarse=-1),
-           dict(n_coarse=17), dict(mixed_inner=0), dict(mask_thres=1.0)]
+           dict(n_coarse=17), dict(mixed_inner=0), dict(mask_thres=1.0), dict(start=3),
+           dict(start=-1)]
     for kw in bad:
         c = mgfr.default_config(**kw)
         h = C.c_void_p()
@@ -81,4 +86,12 @@ def test_default_config_and_validation(lib):
                                          None) == mgfr.MGFR_E_INVALID
     assert lib.mgfr_get_effective_density(None, 0, None) == mgfr.MGFR_E_INVALID
     assert lib.mgfr_effective_mass_pm(None, 0, None) == mgfr.MGFR_E_INVALID
+    assert lib.mgfr_unet_save(None, b"x") == mgfr.MGFR_E_INVALID
+    assert lib.mgfr_unet_load(None, b"x") == mgfr.MGFR_E_INVALID
+    # the allocation-free solve applies the same configuration checks
+    for kw in (dict(n=17), dict(fr0_abs=float("inf")), dict(n_pre=17), dict(max_vcycles=100001)):
+        c = mgfr.default_config(**kw)
+        fake = C.c_void_p(256)  # never dereferenced: the configuration is rejected first
+        assert lib.mgfr_solve_density_noalloc(C.byref(c), fake, 16, 1.0, 1.0, fake, None, None,
+                                              None) == mgfr.MGFR_E_INVALID, kw
     lib.mgfr_destroy(None)

@@ -48,23 +48,64 @@ def test_batch_parity_with_oracle(dev):
     s.close()
 
 
-def test_batch_matches_single_solves_mixed_sizes(dev):
-    """Uneven sizes up to 128^3 against the single-solve FP64 path, whose
-    oracle parity is tested elsewhere."""
+def test_batch_mixed_sizes_against_oracle(dev):
+    """Uneven sizes up to 128^3 in one launch: a 128^3, a 64^3 and a 32^3 item
+    against the CPU oracle (f_R, force and u from the u output), the others
+    against the single-solve FP64 path, whose oracle parity is tested
+    elsewhere."""
     items = make_batch([128, 32, 64, 64, 32, 128, 64, 32], 6000)
     s = mgfr.Solver(0, precision=mgfr.PREC_MIXED)
     deltas = [torch.from_numpy(d).to(dev) for (_, d, _, _) in items]
     outs, st = s.batch_solve(deltas, [b for (*_, b) in items], [f for (_, _, f, _) in items],
-                             want_acc=True)
+                             want_acc=True, want_u=True)
     assert st == mgfr.MGFR_OK
-    for (N, d, fr0, box), o, dd in zip(items, outs, deltas):
-        ref = mgfr.Solver(0, fr0_abs=fr0, tol_rel=1e-10)
-        r = ref.solve_density(dd, box)
-        fr_ref, acc_ref = r["fr"].cpu().numpy(), r["acc"].cpu().numpy()
-        ref.close()
-        rel = np.abs(o["fr"].cpu().numpy() / fr_ref - 1.0).max()
-        arel = np.abs(o["acc"].cpu().numpy() - acc_ref).max() / np.abs(acc_ref).max()
-        assert rel <= 1e-5 and arel <= 1e-5, (N, fr0, rel, arel)
+    oracle.set_threads(0)
+    try:
+        for q, ((N, d, fr0, box), o, dd) in enumerate(zip(items, outs, deltas)):
+            if q in (0, 1, 2):
+                u_ref, sr = oracle.solve_dense(d, box, fr0, tol=1e-11, max_vcycles=300)
+                assert sr["converged"] == 1.0
+                fr_ref, acc_ref = oracle.force_dense(u_ref, box, fr0)
+                assert np.abs(o["u"].cpu().numpy() - u_ref).max() <= 1e-5, (N, fr0)
+            else:
+                ref = mgfr.Solver(0, fr0_abs=fr0, tol_rel=1e-10)
+                r = ref.solve_density(dd, box)
+                fr_ref, acc_ref = r["fr"].cpu().numpy(), r["acc"].cpu().numpy()
+                ref.close()
+            rel = np.abs(o["fr"].cpu().numpy() / fr_ref - 1.0).max()
+            arel = np.abs(o["acc"].cpu().numpy() - acc_ref).max() / np.abs(acc_ref).max()
+            assert rel <= 1e-5 and arel <= 1e-5, (N, fr0, rel, arel)
+    finally:
+        oracle.set_threads(1)
+    s.close()
+
+
+def test_batch_scan_over_n_against_oracle(dev):
+    """A parameter scan over the Hu-Sawicki exponent (n = 1, 2, 3; Sec. 2,
+    Eq. (7)) and |fR0| through the batched path, each item against the
+    oracle at its own n."""
+    rng = np.random.default_rng(9100)
+    cases = []
+    for q, (N, n) in enumerate([(32, 1), (32, 2), (32, 3), (16, 2), (16, 3), (64, 2)]):
+        fr0 = float(10 ** rng.uniform(-6, -4))
+        d = synth.lognormal_delta(N, 100.0, float(rng.uniform(0.5, 2.0)), 9100 + q)
+        cases.append((N, n, fr0, d))
+    s = mgfr.Solver(0, precision=mgfr.PREC_MIXED)
+    deltas = [torch.from_numpy(d).to(dev) for (*_, d) in cases]
+    outs, st = s.batch_solve(deltas, [100.0] * len(cases), [f for (_, _, f, _) in cases],
+                             ns=[n for (_, n, _, _) in cases], want_acc=True)
+    assert st == mgfr.MGFR_OK
+    oracle.set_threads(0)
+    try:
+        for (N, n, fr0, d), o in zip(cases, outs):
+            u_ref, sr = oracle.solve_dense(d, 100.0, fr0, n=n, tol=1e-11, max_vcycles=300)
+            assert sr["converged"] == 1.0
+            fr_ref, acc_ref = oracle.force_dense(u_ref, 100.0, fr0, n=n)
+            rel = np.abs(o["fr"].cpu().numpy() / fr_ref - 1.0).max()
+            arel = np.abs(o["acc"].cpu().numpy() - acc_ref).max() / np.abs(acc_ref).max()
+            assert rel <= 1e-5 and arel <= 1e-5, (N, n, fr0, rel, arel)
+    finally:
+        oracle.set_threads(1)
     s.close()
 
 

@@ -1,6 +1,7 @@
 """GPU tests of the learned-start network: its BF16 tensor-core convolution
 kernels against the FP64 NumPy oracle (forward, input gradient, weight
-gradient), and the trained network's gain over a zero start.
+gradient), one whole training step and prediction against the network
+oracle, and the trained network's gain over a zero start.
 
 Tolerances: forward output is BF16, so |diff| <= 8e-3 max|ref|; the
 gradients are accumulated and returned in FP32: |diff| <= 2e-5 max|ref|.
@@ -51,6 +52,52 @@ def test_conv_kernels_match_oracle(dev, B, D, Cin, Cout):
     dW_ref, db_ref = nn.conv3d_wgrad(x64, g64)
     assert np.abs(dW - dW_ref).max() <= 2e-5 * np.abs(dW_ref).max()
     assert np.abs(db.cpu().numpy() - db_ref).max() <= 2e-5 * np.abs(db_ref).max()
+
+
+def _rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def test_unet_training_step_matches_oracle(dev):
+    """One training step of the whole network through the C ABI (features, 14
+    convolutions, pooling, upsampling, concatenation, head, loss in v,
+    backward pass, Adam) against the FP64 network oracle, which rounds to
+    bfloat16 where the library stores bfloat16: the loss, every parameter
+    block's gradient, the parameters after the Adam step, and the prediction.
+
+    Tolerances: the two sides differ only by FP32 against FP64 accumulation,
+    and by the rare bfloat16 rounding that this flips (one bfloat16 ulp,
+    2^-8 relative); 1e-3 on the loss, 1e-2 relative L2 per gradient block and
+    on the prediction; the Adam update is elementwise FP32 (1e-6 absolute)."""
+    D, box, fr0, lr = 32, 12.5, 1e-5, 1e-3
+    s = mgfr.Solver(0, precision=mgfr.PREC_MIXED)
+    s.unet_init(seed=21)
+    P0 = s.unet_params()
+    delta = synth.lognormal_delta(D, box, 1.5, 31)
+    ut = 0.05 * synth.gaussian_field(D, box, 1.0, 32) - 0.5
+    dd = torch.from_numpy(delta).to(dev)
+    loss = s.unet_train_step(dd[None].contiguous(), np.array([fr0]),
+                             torch.from_numpy(ut).to(dev)[None].contiguous(), lr=lr)
+    G = s.unet_grads()
+    P1 = s.unet_params()
+    x0 = nn.features(delta, fr0)[None]
+    v, cache = nn.unet_forward(P0.astype(np.float64), x0, bf16_storage=True)
+    loss_ref, gv = nn.mse_v(v, ut[None])
+    G_ref = nn.unet_backward(cache, gv, bf16_storage=True)
+    assert abs(loss / loss_ref - 1.0) <= 1e-3, (loss, loss_ref)
+    offs, hoff, n = nn.param_layout()
+    assert len(G) == n
+    blocks = [(wo, bo, bo + co) for (wo, bo), (_, co, _) in zip(offs, nn.CONVS)]
+    for i, (wo, bo, be) in enumerate(blocks):
+        assert _rel_l2(G[wo:bo], G_ref[wo:bo]) <= 1e-2, ("W", i)
+        assert _rel_l2(G[bo:be], G_ref[bo:be]) <= 1e-2, ("b", i)
+    assert _rel_l2(G[hoff:], G_ref[hoff:]) <= 1e-2
+    P1_ref, _, _ = nn.adam_step(P0, G, np.zeros(n), np.zeros(n), 1, lr, dtype=np.float32)
+    assert np.abs(P1 - P1_ref).max() <= 1e-6
+    u = s.unet_predict(dd, fr0).cpu().numpy()
+    v1, _ = nn.unet_forward(P1.astype(np.float64), x0, bf16_storage=True)
+    assert _rel_l2(u, nn.U_SCALE * np.sinh(v1[0])) <= 1e-2
+    s.close()
 
 
 def test_unet_training_and_learned_start(dev):
