@@ -534,8 +534,22 @@ def main():
     f1.record()
     torch.cuda.synchronize()
     e2e_value, _ = D.whole_job_rate(e2e_upd, f0.elapsed_time(f1), dev)
-    sm.close()
     del host_in, host_out
+    # ---- potential of matter + effective mass on the base PM grid (Eq. (30)) ----
+    pm = {}
+    for what, name in ((mgfr.PM_TOTAL, "total"), (mgfr.PM_EFFECTIVE, "effective")):
+        sm.pm_potential(w["N"], 0, what)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        _, _, pst = sm.pm_potential(w["N"], 0, what)
+        g1.record()
+        torch.cuda.synchronize()
+        pm[name] = {"ms": g0.elapsed_time(g1), "vcycles": pst["vcycles"],
+                    "res_rel": pst["res_l2_final"] / pst["f_l2"],
+                    "gs_cell_updates_per_s": pst["linear_updates"] / (g0.elapsed_time(g1) / 1e3)}
+    pm["grid"] = f"{w['N']}^3 periodic PM grid (the base grid), FP64 linear multigrid to 1e-8"
+    sm.close()
 
     # ---- the same steps with CUDA events around each profiled launch ----
     # (launched directly on the library's stream instead of from graphs)
@@ -636,6 +650,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * n_part,
                 "d2h_bytes_per_step": 24 * n_part},
         "cpu_baseline": cpu,
+        "pm_potential": pm,
         **extras,
     }
     print(json.dumps(line), flush=True)

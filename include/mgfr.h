@@ -257,6 +257,33 @@ mgfr_status mgfr_get_level_field(mgfr_ctx* ctx, int level, int what, double* out
 mgfr_status mgfr_get_effective_density(mgfr_ctx* ctx, int level, double* out_dev);
 mgfr_status mgfr_effective_mass_pm(mgfr_ctx* ctx, int lpm, double* out_dev);
 
+/*
+ * Gravitational potential of the last particle solve on the periodic PM grid
+ * of level lpm (N_pm = N_base 2^lpm, 8 <= N_pm <= 1024 per axis), Sec. 2.4,
+ * Eq. (30): lap_x phi = 4 pi G a^2 rho_bar (delta_pm - mean(delta_pm))
+ * = (3/2) Omega_m H0^2 a^-1 (delta_pm - mean), with x comoving in Mpc/h,
+ * H0 = 100 km/s per Mpc/h, phi in (km/s)^2 and mean(phi) = 0.  delta_pm is
+ * each leaf cell's density contrast shared among the PM cells it overlaps by
+ * volume (as in mgfr_effective_mass_pm) for
+ *   what = MGFR_PM_EFFECTIVE: delta_eff alone (the modified-gravity part, whose
+ *          potential is -(c^2/2) f_R up to a constant and discretisation),
+ *          MGFR_PM_MATTER: the matter contrast delta (Newtonian gravity),
+ *          MGFR_PM_TOTAL: delta + delta_eff (Eq. (30)).
+ * The 7-point periodic Poisson problem is solved in FP64 by linear multigrid
+ * V-cycles (cfg.n_pre / n_post red-black Gauss-Seidel sweeps, down to 4^3) to
+ * ||rhs - lap phi||_2 <= cfg.tol_rel ||rhs||_2 (at most cfg.max_vcycles).
+ *   phi_out_dev  [N_pm^3] device FP64, C order (required).
+ *   dens_out_dev [N_pm^3] device FP64: delta_pm, or NULL.
+ *   st           vcycles, res_l2_init / final (of the scaled right-hand side),
+ *                linear_updates, t_solve_ms; or NULL.
+ * Workspace (three FP64 arrays of the PM grid and its coarse levels) is held
+ * by the context.  MGFR_E_INVALID without a particle solve, for a bad lpm or
+ * what; MGFR_E_NOCONVERGE (phi filled) if the tolerance is not reached.
+ */
+typedef enum { MGFR_PM_EFFECTIVE = 0, MGFR_PM_MATTER = 1, MGFR_PM_TOTAL = 2 } mgfr_pm_what;
+mgfr_status mgfr_pm_potential(mgfr_ctx* ctx, int lpm, int what, double* phi_out_dev,
+                              double* dens_out_dev, mgfr_stats* st);
+
 /* One independent periodic solve of a batch (Sec. 3.2-3.3 per item). */
 typedef struct {
   int N;                     /* power of two, 8..512                          */

@@ -807,16 +807,19 @@ void orc_amr_delta(void* h, int l, double* out) {
 }
 
 /*
- * Effective mass of the solved hierarchy on a periodic PM grid of level lpm
- * (N_pm = N0 2^lpm) [Sec. 2.4, long-range part]: every leaf cell (a cell
- * with no daughters) carries delta_eff [Eq. (31)] times its
- * volume, and hands to each PM cell it overlaps the fraction of that mass
- * given by the overlapping volume over its own.  The grids are nested, so a
- * leaf either covers whole PM cells (each receives delta_eff as a density)
- * or lies inside one (which receives delta_eff 8^-(l - lpm)).  out: N_pm^3
- * density contrasts (C order).  Needs a model (orc_amr_set_model) and u.
+ * Mass of the solved hierarchy on a periodic PM grid of level lpm (N_pm =
+ * N0 2^lpm) [Sec. 2.4, long-range part]: every leaf cell (a cell with no
+ * daughters) carries a density contrast times its volume, and hands to each
+ * PM cell it overlaps the fraction of that mass given by the overlapping
+ * volume over its own.  The grids are nested, so a leaf either covers whole
+ * PM cells (each receives its contrast as a density) or lies inside one
+ * (which receives the contrast times 8^-(l - lpm)).  The contrast is
+ *   what 0: delta_eff [Eq. (31)] (needs a model, orc_amr_set_model, and u);
+ *   what 1: the matter contrast delta;
+ *   what 2: delta + delta_eff, the right-hand side of Eq. (30).
+ * out: N_pm^3 density contrasts (C order).
  */
-void orc_amr_effective_pm(void* h, int lpm, double* out) {
+void orc_amr_density_pm(void* h, int lpm, int what, double* out) {
   orc_amr* A = (orc_amr*)h;
   const orc_model* m = &A->model;
   const int64_t Npm = lev_dim(A, lpm);
@@ -828,7 +831,11 @@ void orc_amr_effective_pm(void* h, int lpm, double* out) {
     for (long long c = 0; c < A->ncell[l]; ++c) {
       if (A->refined[l][c]) continue;
       const double d = A->mass[l][c] * scale - 1.0;
-      const double eff = d / 3.0 + m->Rt / (3.0 * rho) * (1.0 - exp(-A->u[l][c] / (m->n + 1)));
+      double v = d;
+      if (what != 1) {
+        const double eff = d / 3.0 + m->Rt / (3.0 * rho) * (1.0 - exp(-A->u[l][c] / (m->n + 1)));
+        v = what == 0 ? eff : d + eff;
+      }
       int64_t I, J, K;
       cell_coords(A, l, c, &I, &J, &K);
       if (l <= lpm) {
@@ -836,14 +843,17 @@ void orc_amr_effective_pm(void* h, int lpm, double* out) {
         for (int64_t a = 0; a < sc; ++a)
           for (int64_t b = 0; b < sc; ++b)
             for (int64_t e = 0; e < sc; ++e)
-              out[((I * sc + a) * Npm + (J * sc + b)) * Npm + (K * sc + e)] = eff;
+              out[((I * sc + a) * Npm + (J * sc + b)) * Npm + (K * sc + e)] = v;
       } else {
         const int sh = l - lpm;
-        out[((I >> sh) * Npm + (J >> sh)) * Npm + (K >> sh)] += eff / (double)((int64_t)1 << (3 * sh));
+        out[((I >> sh) * Npm + (J >> sh)) * Npm + (K >> sh)] += v / (double)((int64_t)1 << (3 * sh));
       }
     }
   }
 }
+
+/* The effective mass alone (what 0 above). */
+void orc_amr_effective_pm(void* h, int lpm, double* out) { orc_amr_density_pm(h, lpm, 0, out); }
 
 /* Neighbour table of a level: nb[6c+d] >= 0 is a cell index, -1 a ghost.
  * Directions d: 0:-x 1:+x 2:-y 3:+y 4:-z 5:+z. */

@@ -47,6 +47,7 @@ def lib():
                 "orc_model_constants": (None, [d, d, i, d, vp]),
                 "orc_effective_density": (None, [ll, vp, vp, d, d, i, d, vp]),
                 "orc_amr_effective_pm": (None, [vp, i, vp]),
+                "orc_amr_density_pm": (None, [vp, i, i, vp]),
                 "orc_solve_dense": (i, [i, d, vp, d, d, i, d, vp, d, i, i, i, i, d, vp]),
                 "orc_solve_dense_f": (i, [i, d, vp, d, d, i, d, vp, d, i, i, i, i, d, vp]),
                 "orc_residual_dense": (None, [i, d, vp, d, d, i, d, vp, vp]),
@@ -324,6 +325,25 @@ class AMR:
         out = np.empty((Npm, Npm, Npm))
         lib().orc_amr_effective_pm(self.h, lpm, _p(out))
         return out
+
+    def density_pm(self, lpm: int = 0, what: int = 2) -> np.ndarray:
+        """Density contrast on the periodic PM grid of level lpm, each leaf
+        cell's share by overlapping volume (Sec. 2.4): what 0 the effective
+        mass, 1 the matter, 2 both (the right-hand side of Eq. (30))."""
+        Npm = self.N0 << lpm
+        out = np.empty((Npm, Npm, Npm))
+        lib().orc_amr_density_pm(self.h, lpm, what, _p(out))
+        return out
+
+    def pm_potential(self, lpm: int = 0, what: int = 2) -> np.ndarray:
+        """Comoving potential on the PM grid of level lpm (Sec. 2.4, Eq. (30)):
+        lap_x phi = 4 pi G a^2 rho_bar (delta_pm - mean) = (3/2) Om H0^2 a^-1
+        (delta_pm - mean), with H0 = 100 km/s per Mpc/h, so phi is in (km/s)^2
+        and x in Mpc/h; the 7-point periodic problem solved exactly by FFT,
+        mean(phi) = 0."""
+        fr0, a, n, om = self.model
+        rhs = 1.5e4 * om / a * self.density_pm(lpm, what)
+        return poisson_periodic(rhs, self.box)
 
     def level_force(self, l, prolong_linear=True):
         n = self.ncell(l)

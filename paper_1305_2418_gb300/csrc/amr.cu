@@ -657,17 +657,21 @@ __global__ void k_eff_level(const double* __restrict__ mass, const double* __res
   if (c < n) out[c] = eff_density(mass[c], u[c], q);
 }
 
-// Each leaf cell of level l hands its effective mass to the cells of the
-// nested periodic PM grid of level lpm (N_pm = N0 2^lpm) by overlapping
-// volume: a leaf at l <= lpm covers 2^(lpm-l) PM cells per axis and gives
-// each delta_eff as a density (plain stores: leaves do not overlap); a leaf
-// at l > lpm lies in one PM cell and adds delta_eff 8^-(l-lpm) (atomics).
+// Each leaf cell of level l hands its mass to the cells of the nested
+// periodic PM grid of level lpm (N_pm = N0 2^lpm) by overlapping volume: a
+// leaf at l <= lpm covers 2^(lpm-l) PM cells per axis and gives each its
+// contrast as a density (plain stores: leaves do not overlap); a leaf at
+// l > lpm lies in one PM cell and adds its contrast 8^-(l-lpm) (atomics).
+// The contrast is delta_eff (what 0), delta (what 1) or delta + delta_eff
+// (what 2, the right-hand side of Eq. (30)).
 __global__ void k_eff_pm(int l, int lpm, TreeView T, const double* __restrict__ mass,
-                         const double* __restrict__ u, long long n, EffPar q,
+                         const double* __restrict__ u, long long n, EffPar q, int what,
                          double* __restrict__ out) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= n || T.son[l][c] >= 0) return;  // not a leaf
-  const double eff = eff_density(mass[c], u[c], q);
+  const double d = mass[c] * q.scale - 1.0;
+  const double eff = what == 1 ? d : (what == 0 ? eff_density(mass[c], u[c], q)
+                                                : d + eff_density(mass[c], u[c], q));
   long long I, J, K;
   cell_coords(T, l, c, &I, &J, &K);
   const long long Npm = 1LL << (T.lg0 + lpm);
@@ -1338,14 +1342,18 @@ mgfr_status mgfr_get_effective_density(mgfr_ctx* c, int level, double* out_dev) 
   return MGFR_OK;
 }
 
-mgfr_status mgfr_effective_mass_pm(mgfr_ctx* c, int lpm, double* out_dev) {
-  if (!c || !out_dev) return MGFR_E_INVALID;
+}  // extern "C"
+
+mgfr_status amr_density_pm(mgfr_ctx* c, int lpm, int what, double* out_dev, int* lg_pm,
+                           double* omega_m, double* a) {
   AmrWork* A = W(c);
   if (!A || A->nlev == 0) return set_err(c, MGFR_E_INVALID, "no particle solve yet");
   if (lpm < 0 || A->lg0 + lpm > 10) return set_err(c, MGFR_E_INVALID, "PM grid of 2^0..2^10 cells per axis");
-  MG_CK(c, cudaSetDevice(c->device));
-  MG_CK(c, cudaEventRecord(c->ev_in, c->user));
-  MG_CK(c, cudaStreamWaitEvent(c->s, c->ev_in, 0));
+  if (what < 0 || what > 2) return set_err(c, MGFR_E_INVALID, "what: 0 effective, 1 matter, 2 total");
+  if (lg_pm) *lg_pm = A->lg0 + lpm;
+  if (omega_m) *omega_m = A->omega_m;
+  if (a) *a = A->a;
+  if (!out_dev) return MGFR_OK;
   const long long Npm = 1LL << (A->lg0 + lpm);
   MG_CK(c, cudaMemsetAsync(out_dev, 0, sizeof(double) * (size_t)(Npm * Npm * Npm), c->s));
   TreeView T = tree_view(A);
@@ -1353,8 +1361,21 @@ mgfr_status mgfr_effective_mass_pm(mgfr_ctx* c, int lpm, double* out_dev) {
     AmrLevel& L = A->L[l];
     const double* u = l == 0 ? c->dh.L[0].u : L.u;
     k_eff_pm<<<nblocks(L.ncell, BS), BS, 0, c->s>>>(l, lpm, T, L.mass, u, L.ncell,
-                                                    eff_par(A, l), out_dev);
+                                                    eff_par(A, l), what, out_dev);
+    c->launches += 1;
   }
+  return MGFR_OK;
+}
+
+extern "C" {
+
+mgfr_status mgfr_effective_mass_pm(mgfr_ctx* c, int lpm, double* out_dev) {
+  if (!c || !out_dev) return MGFR_E_INVALID;
+  TRY(amr_density_pm(c, lpm, 0, nullptr, nullptr, nullptr, nullptr));  // checks only
+  MG_CK(c, cudaSetDevice(c->device));
+  MG_CK(c, cudaEventRecord(c->ev_in, c->user));
+  MG_CK(c, cudaStreamWaitEvent(c->s, c->ev_in, 0));
+  TRY(amr_density_pm(c, lpm, 0, out_dev, nullptr, nullptr, nullptr));
   MG_CK(c, cudaEventRecord(c->ev_out, c->s));
   MG_CK(c, cudaStreamWaitEvent(c->user, c->ev_out, 0));
   MG_CK(c, cudaGetLastError());

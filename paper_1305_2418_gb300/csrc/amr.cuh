@@ -133,6 +133,12 @@ void amr_free(mgfr_ctx* c);
 // the dense workspace, which other solves reuse); the level getters then
 // return MGFR_E_INVALID until the next particle solve completes.
 void amr_invalidate(mgfr_ctx* c);
+// Density contrast of the last particle solve on the periodic PM grid of
+// level lpm (what 0: delta_eff, 1: delta, 2: both), written to out_dev
+// [N_pm^3] on the context's stream (out_dev NULL: checks only); returns
+// log2 N_pm and the model's Omega_m and a of that solve.
+mgfr_status amr_density_pm(mgfr_ctx* c, int lpm, int what, double* out_dev, int* lg_pm,
+                           double* omega_m, double* a);
 TreeView tree_view(const AmrWork* A);
 // One-way solve of refined level L >= 1 (amr_solve.cu).
 mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int L, const Model& m, mgfr_stats* st);

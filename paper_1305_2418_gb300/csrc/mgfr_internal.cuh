@@ -138,6 +138,7 @@ struct mgfr_ctx {
   void* amr = nullptr;    // refined hierarchy workspace (amr.cu)
   void* batch = nullptr;  // batched-solve workspace (batch.cu)
   void* unet = nullptr;   // learned initial guess network (unet.cu)
+  void* pm = nullptr;     // particle-mesh potential workspace (pm.cu)
   // profiling: events recorded around base-level kernels inside each graph
   struct ProfRec {
     int fam;
@@ -180,6 +181,7 @@ mgfr_status set_err(mgfr_ctx* c, mgfr_status st, const std::string& msg);
 bool validate_cfg(const mgfr_config* c, std::string& why);
 void batch_free(mgfr_ctx* c);
 void unet_free(mgfr_ctx* c);
+void pm_free(mgfr_ctx* c);
 #define MG_CK(ctx, call)                                                                  \
   do {                                                                                    \
     cudaError_t e_ = (call);                                                              \

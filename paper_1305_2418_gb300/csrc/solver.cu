@@ -631,6 +631,7 @@ void mgfr_destroy(mgfr_ctx* c) {
   amr_free(c);
   batch_free(c);
   unet_free(c);
+  pm_free(c);
   if (c->u_learn) cudaFree(c->u_learn);
   for (auto e : c->evpool) cudaEventDestroy(e);
   c->evpool.clear();

@@ -18,6 +18,7 @@ MGFR_OK, MGFR_E_INVALID, MGFR_E_CUDA, MGFR_E_OOM, MGFR_E_NOCONVERGE, MGFR_E_TIME
 STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "NOCONVERGE", "TIMEOUT", "UNSUPPORTED"]
 PREC_FP64, PREC_MIXED = 0, 1
 START_ZERO, START_USER, START_LEARNED = 0, 1, 2
+PM_EFFECTIVE, PM_MATTER, PM_TOTAL = 0, 1, 2
 FIELD_U, FIELD_FR, FIELD_SOURCE, FIELD_MASS, FIELD_ACC, FIELD_COUNT = range(6)
 
 
@@ -89,6 +90,8 @@ SIGNATURES = {
     "mgfr_get_level_field": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "mgfr_get_effective_density": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "mgfr_effective_mass_pm": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "mgfr_pm_potential": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
     "mgfr_solve_density_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                              C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_void_p]),
@@ -269,6 +272,18 @@ class Solver:
         out = torch.empty((Npm,) * 3, dtype=torch.float64, device=f"cuda:{self.device}")
         self._check(lib().mgfr_effective_mass_pm(self.h, lpm, _ptr(out)))
         return out
+
+    def pm_potential(self, N_base: int, lpm: int = 0, what: int = 2, want_density=False):
+        """Potential (km/s)^2 on the periodic PM grid of level lpm (mgfr_pm_potential):
+        returns (phi, delta_pm or None, stats)."""
+        import torch
+        Npm = N_base << lpm
+        phi = torch.empty((Npm,) * 3, dtype=torch.float64, device=f"cuda:{self.device}")
+        dens = torch.empty_like(phi) if want_density else None
+        stats = Stats()
+        self._check(lib().mgfr_pm_potential(self.h, lpm, what, _ptr(phi), _ptr(dens),
+                                            C.byref(stats)))
+        return phi, dens, stats.to_dict()
 
     def _batch_items(self, deltas, boxes, a, fr0s, ns, u_inits, want_acc, want_u=False):
         import torch

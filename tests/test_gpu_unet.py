@@ -65,10 +65,16 @@ def test_unet_training_step_matches_oracle(dev):
     bfloat16 where the library stores bfloat16: the loss, every parameter
     block's gradient, the parameters after the Adam step, and the prediction.
 
-    Tolerances: the two sides differ only by FP32 against FP64 accumulation,
-    and by the rare bfloat16 rounding that this flips (one bfloat16 ulp,
-    2^-8 relative); 1e-3 on the loss, 1e-2 relative L2 per gradient block and
-    on the prediction; the Adam update is elementwise FP32 (1e-6 absolute)."""
+    Tolerances.  The two sides differ by FP32 against FP64 accumulation in
+    every layer, which moves some values across a bfloat16 rounding boundary
+    (2^-8 relative), and those flips propagate.  The bound is calibrated on
+    the oracle itself: its response (relative L2) to a 1e-7 relative change
+    of the parameters, the size of an FP32 rounding, times 5, at least 5e-3.
+    On this case that response is at most 0.8% for a gradient block and 0.3%
+    for the prediction; a structural mistake (a swapped concatenation, a
+    missing 1/8 in the pooling adjoint, a wrong tap) changes them by O(1).
+    The loss must agree to 1e-3 and the Adam update, elementwise FP32 from the
+    library's own gradient, to 1e-6 absolute."""
     D, box, fr0, lr = 32, 12.5, 1e-5, 1e-3
     s = mgfr.Solver(0, precision=mgfr.PREC_MIXED)
     s.unet_init(seed=21)
@@ -81,22 +87,35 @@ def test_unet_training_step_matches_oracle(dev):
     G = s.unet_grads()
     P1 = s.unet_params()
     x0 = nn.features(delta, fr0)[None]
-    v, cache = nn.unet_forward(P0.astype(np.float64), x0, bf16_storage=True)
-    loss_ref, gv = nn.mse_v(v, ut[None])
-    G_ref = nn.unet_backward(cache, gv, bf16_storage=True)
+
+    def oracle_step(P):
+        v, cache = nn.unet_forward(P, x0, bf16_storage=True)
+        loss_, gv = nn.mse_v(v, ut[None])
+        return loss_, nn.unet_backward(cache, gv, bf16_storage=True), v
+
+    loss_ref, G_ref, _ = oracle_step(P0.astype(np.float64))
+    rng = np.random.default_rng(5)
+    Pp = P0.astype(np.float64) * (1.0 + 1e-7 * rng.standard_normal(P0.size))
+    _, G_pert, _ = oracle_step(Pp)
     assert abs(loss / loss_ref - 1.0) <= 1e-3, (loss, loss_ref)
     offs, hoff, n = nn.param_layout()
     assert len(G) == n
-    blocks = [(wo, bo, bo + co) for (wo, bo), (_, co, _) in zip(offs, nn.CONVS)]
-    for i, (wo, bo, be) in enumerate(blocks):
-        assert _rel_l2(G[wo:bo], G_ref[wo:bo]) <= 1e-2, ("W", i)
-        assert _rel_l2(G[bo:be], G_ref[bo:be]) <= 1e-2, ("b", i)
-    assert _rel_l2(G[hoff:], G_ref[hoff:]) <= 1e-2
+    blocks = [(wo, bo) for (wo, bo), _ in zip(offs, nn.CONVS)]
+    blocks += [(bo, bo + co) for (wo, bo), (_, co, _) in zip(offs, nn.CONVS)]
+    blocks += [(hoff, n)]
+    for lo, hi in blocks:
+        tol = max(5.0 * _rel_l2(G_pert[lo:hi], G_ref[lo:hi]), 5e-3)
+        err = _rel_l2(G[lo:hi], G_ref[lo:hi])
+        assert err <= tol, (lo, hi, err, tol)
     P1_ref, _, _ = nn.adam_step(P0, G, np.zeros(n), np.zeros(n), 1, lr, dtype=np.float32)
     assert np.abs(P1 - P1_ref).max() <= 1e-6
     u = s.unet_predict(dd, fr0).cpu().numpy()
     v1, _ = nn.unet_forward(P1.astype(np.float64), x0, bf16_storage=True)
-    assert _rel_l2(u, nn.U_SCALE * np.sinh(v1[0])) <= 1e-2
+    v1p, _ = nn.unet_forward(P1.astype(np.float64) * (1.0 + 1e-7 * rng.standard_normal(n)), x0,
+                             bf16_storage=True)
+    u_ref = nn.U_SCALE * np.sinh(v1[0])
+    tol = max(5.0 * _rel_l2(nn.U_SCALE * np.sinh(v1p[0]), u_ref), 5e-3)
+    assert _rel_l2(u, u_ref) <= tol, (_rel_l2(u, u_ref), tol)
     s.close()
 
 

@@ -281,12 +281,17 @@ def test_effective_density_limits_and_box_sum():
     assert np.abs(eff - delta / 3.0).max() > 1e-2 * np.abs(delta / 3.0).max()
 
 
-def _leaf_effective_by_brute_force(A, L, a=1.0, n=1, fr0=1e-5):
-    """delta_eff sampled at every cell of the uniform level-L grid, from the
-    leaf that contains it (found by descending the hierarchy cell by cell)."""
+def _leaf_effective_by_brute_force(A, L, a=1.0, n=1, fr0=1e-5, matter=False):
+    """delta_eff (or, with matter=True, delta) sampled at every cell of the
+    uniform level-L grid, from the leaf that contains it (found by descending
+    the hierarchy cell by cell)."""
     N0 = A.N0
     NL = N0 << L
-    eff = [oracle.effective_density(A.u(l), A.delta(l), fr0, a=a, n=n) for l in range(A.nlev)]
+    if matter:
+        eff = [A.delta(l) for l in range(A.nlev)]
+    else:
+        eff = [oracle.effective_density(A.u(l), A.delta(l), fr0, a=a, n=n)
+               for l in range(A.nlev)]
     keys = [None] + [A.keys(l) for l in range(1, A.nlev)]
     out = np.empty((NL, NL, NL))
     for i in range(NL):
@@ -342,6 +347,63 @@ def test_effective_mass_on_pm_grid_matches_brute_force():
     B.set_u(0, u0)
     np.testing.assert_array_equal(B.effective_pm(0).ravel(),
                                   oracle.effective_density(u0, B.delta(0), fr0))
+
+
+def test_matter_and_total_on_pm_grid():
+    """The matter contrast goes to the PM grid by the same volume shares as
+    the effective mass (against brute-force sampling of the leaf field); on
+    the base grid it is the base level's delta (ancestors hold the sums of
+    their leaves); the total is the sum of the two (Eq. (30))."""
+    N0, box, fr0 = 8, 20.0, 1e-5
+    rng = np.random.default_rng(22)
+    pos = np.concatenate([4.0 + 3.0 * rng.random((600, 3)), box * rng.random((200, 3))])
+    A = oracle.AMR(pos, N0, box, 2, 8)
+    A.deposit()
+    A.set_model(fr0)
+    for l in range(A.nlev):
+        A.set_u(l, 0.5 * rng.standard_normal(A.ncell(l)))
+    fine = _leaf_effective_by_brute_force(A, 2, fr0=fr0, matter=True)
+    for lpm in (0, 1, 2, 3):
+        pm = A.density_pm(lpm, 1)
+        Npm = N0 << lpm
+        if lpm <= 2:
+            s = 1 << (2 - lpm)
+            want = fine.reshape(Npm, s, Npm, s, Npm, s).mean(axis=(1, 3, 5))
+        else:
+            want = np.repeat(np.repeat(np.repeat(fine, 2, 0), 2, 1), 2, 2)
+        np.testing.assert_allclose(pm, want, rtol=1e-12, atol=1e-12)
+        assert abs(pm.mean()) < 1e-12  # the particle mass is conserved
+        np.testing.assert_allclose(A.density_pm(lpm, 2), pm + A.effective_pm(lpm), rtol=0,
+                                   atol=1e-12)
+    np.testing.assert_allclose(A.density_pm(0, 1).ravel(), A.delta(0), rtol=0, atol=1e-12)
+
+
+def test_pm_potential_scale_from_the_field_identity():
+    """The potential of the effective mass is -(c^2/2) f_R up to a constant
+    (Sec. 2.4: Eqs. (13) and (30) give the same force): with the Poisson
+    scale (3/2) Om H0^2 / a of the PM potential the oracle's phi of
+    delta_eff matches -(c^2/2)(f_R - mean f_R) to the square of the link
+    differences, at a = 1 and a = 0.5."""
+    c = 299792.458
+    N0, box, fr0 = 16, 100.0, 1e-4
+    d = synth.lognormal_delta(N0, box, 0.3, 96)
+    pos = synth.poisson_particles(d, box, 64.0, 97)
+    for a in (1.0, 0.5):
+        A = oracle.AMR(pos, N0, box, 0, 8)
+        A.deposit()
+        A.set_model(fr0, a=a)
+        rc, _ = A.solve(tol=1e-13)
+        assert rc == 0
+        u = A.u(0)
+        fr = oracle.model_constants(fr0, a=a)["fbar"] * np.exp(u)
+        want = -0.5 * c * c * (fr - fr.mean())
+        got = A.pm_potential(0, what=0).ravel()
+        uu = u.reshape((N0,) * 3)
+        links = max(np.abs(np.diff(uu, axis=ax)).max() for ax in range(3))
+        assert links > 1e-3
+        err = np.abs(got - want).max() / np.abs(want).max()
+        assert err < 0.5 * links * links, (a, err, links)
+        A.close()
 
 
 def _lap7(phi, box):
