@@ -376,6 +376,8 @@ def learned_extra(mgfr, learned, torch, dev, local):
             d = torch.from_numpy(synth.lognormal_delta(256, 100.0, sig, 9000 + q)).to(dev)
             fields.append((d, fr0))
     rows = learned.evaluate(s, fields, 100.0)
+    net_path = os.path.join(tempfile.mkdtemp(), "unet.bin")
+    s.unet_save(net_path)  # for the time-stepped loop
     s.close()
     zc = [r["zero_cycles"] for r in rows]
     lc = [r["learned_cycles"] for r in rows]
@@ -391,7 +393,31 @@ def learned_extra(mgfr, learned, torch, dev, local):
                          "predict_ms_mean": float(np.mean([r["predict_ms"] for r in rows])),
                          "start_rms_err_mean": float(np.mean([r["start_rms_err"] for r in rows])),
                          "max_rel_diff_fr": float(max(r["max_rel_diff_fr"] for r in rows)),
-                         "fields": len(rows)}}
+                         "fields": len(rows)},
+            "net_path": net_path}
+
+
+def time_stepped_extra(mgfr, torch, dev, local, net_path, steps=8):
+    """The 256^3-particle workload moved through a toy particle-mesh loop
+    (force of Eq. (30) on the base PM grid, leapfrog; the fastest particle
+    moves about one base cell over the run): per step the V-cycles of all
+    levels and the solve time from a zero start, from the previous step's
+    solution, and from the learned start."""
+    from paper_1305_2418_gb300 import pmloop
+    w = W256
+    d = synth.lognormal_delta(w["N"], w["box"], w["sigma_g"], w["seed"])
+    pos = torch.from_numpy(synth.poisson_particles(d, w["box"], w["nbar"], w["seed"])).to(dev)
+    rows = pmloop.run(pos, w["N"], w["box"], steps, w["fr0"], w["lmax"], net_path=net_path,
+                      device=local)
+    out = {"workload": "particles256 moved through %d toy PM steps (force of Eq. (30), "
+                       "leapfrog, about one base cell in all)" % steps,
+           "max_rel_diff_fr": max(r["max_rel_diff_fr"] for r in rows)}
+    for k in ("zero", "previous", "learned"):
+        if k in rows[0]:
+            later = rows[1:]
+            out[k] = {"cycles_mean": float(np.mean([r[k]["cycles"] for r in later])),
+                      "ms_mean": float(np.mean([r[k]["ms"] for r in later]))}
+    return out
 
 
 def family_table(kern_ms, kern_n, kern_cells, steps, peak):
@@ -616,6 +642,8 @@ def main():
         extras["particles256"] = particles256_extra(mgfr, torch, dev, local)
         extras["batched"] = batched_extra(mgfr, torch, dev, local)
         extras["learned_start"] = learned_extra(mgfr, learned, torch, dev, local)
+        extras["time_stepped"] = time_stepped_extra(mgfr, torch, dev, local,
+                                                    extras["learned_start"].pop("net_path"))
 
     nl = last["n_levels"]
     line = {

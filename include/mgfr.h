@@ -103,8 +103,19 @@ typedef struct {
  *                      keep a u_init_dev they pass; the others of 32^3 and
  *                      more are predicted in groups of one size, those below
  *                      32^3 start from zero.  The prediction runs inside the
- *                      call, on the context's stream. */
-typedef enum { MGFR_START_ZERO = 0, MGFR_START_USER = 1, MGFR_START_LEARNED = 2 } mgfr_start;
+ *                      call, on the context's stream.
+ *   MGFR_START_PREVIOUS u = the base-level solution of the context's last
+ *                      density or particle solve of the same grid size (the
+ *                      previous step's u, kept in the context: no copy);
+ *                      u_init must be NULL; MGFR_E_INVALID if there is none
+ *                      (first solve, another size or precision since).  Not
+ *                      for batches. */
+typedef enum {
+  MGFR_START_ZERO = 0,
+  MGFR_START_USER = 1,
+  MGFR_START_LEARNED = 2,
+  MGFR_START_PREVIOUS = 3
+} mgfr_start;
 
 typedef struct {
   int vcycles;               /* nonlinear V-cycles (all precisions), base level */
@@ -283,6 +294,32 @@ mgfr_status mgfr_effective_mass_pm(mgfr_ctx* ctx, int lpm, double* out_dev);
 typedef enum { MGFR_PM_EFFECTIVE = 0, MGFR_PM_MATTER = 1, MGFR_PM_TOTAL = 2 } mgfr_pm_what;
 mgfr_status mgfr_pm_potential(mgfr_ctx* ctx, int lpm, int what, double* phi_out_dev,
                               double* dens_out_dev, mgfr_stats* st);
+
+/*
+ * The force of that potential at the particles: after solving phi as
+ * mgfr_pm_potential does, g = -grad_x phi by central differences on the PM
+ * grid (periodic) is interpolated to each particle with cloud-in-cell weights
+ * of the PM grid (the 8 cells around x N_pm / box - 1/2).  With what =
+ * MGFR_PM_TOTAL this is the long-range force of Eq. (30) including the
+ * effective mass (Sec. 2.4); MGFR_PM_MATTER gives the Newtonian one.
+ *   pos_dev     [Np][3] FP64 comoving positions (Mpc/h), any values (wrapped).
+ *   acc_out_dev [Np][3] FP64 -grad_x phi in (km/s)^2 per Mpc/h (the comoving
+ *               gradient; the peculiar acceleration is this divided by a).
+ * Errors as mgfr_pm_potential; MGFR_E_INVALID without positions or output.
+ */
+mgfr_status mgfr_pm_accel(mgfr_ctx* ctx, int lpm, int what, const double* pos_dev, long long Np,
+                          double* acc_out_dev, mgfr_stats* st);
+
+/*
+ * One leapfrog kick-drift step of Np particles on `cuda_stream` (an addition
+ * for time-stepped use, Sec. 3.3, step 2: each step's solve starts from the
+ * previous step's solution): vel += kick * acc, then pos = wrap(pos + drift *
+ * vel) into [0, box).  pos_dev, vel_dev, acc_dev: [Np][3] FP64 device arrays.
+ * Asynchronous: returns after the launch.  MGFR_E_INVALID for NULL arrays, Np
+ * < 1, box <= 0 or a non-finite kick or drift.
+ */
+mgfr_status mgfr_kick_drift(double* pos_dev, double* vel_dev, const double* acc_dev, long long Np,
+                            double kick, double drift, double box, void* cuda_stream);
 
 /* One independent periodic solve of a batch (Sec. 3.2-3.3 per item). */
 typedef struct {

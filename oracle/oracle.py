@@ -145,6 +145,30 @@ def poisson_periodic(rhs, box: float) -> np.ndarray:
     return np.fft.irfftn(pk, s=r.shape, axes=(0, 1, 2))
 
 
+def pm_accel(phi, box: float, pos) -> np.ndarray:
+    """-grad phi on a periodic N^3 grid by central differences at the cell
+    centres, interpolated to the particles by cloud-in-cell (the 8 cells
+    around x N / box - 1/2, product of the 1D linear weights): the PM force
+    of Sec. 2.4.  phi (N, N, N), pos (Np, 3) in [0, box); returns (Np, 3)."""
+    phi = _f64(phi)
+    N = phi.shape[0]
+    h = box / N
+    g = [-(np.roll(phi, -1, ax) - np.roll(phi, 1, ax)) / (2.0 * h) for ax in range(3)]
+    t = _f64(pos) / h - 0.5
+    i0 = np.floor(t).astype(np.int64)
+    w1 = t - i0
+    acc = np.zeros((len(t), 3))
+    for a in (0, 1):
+        for b in (0, 1):
+            for c in (0, 1):
+                w = ((w1[:, 0] if a else 1.0 - w1[:, 0]) * (w1[:, 1] if b else 1.0 - w1[:, 1]) *
+                     (w1[:, 2] if c else 1.0 - w1[:, 2]))
+                I, J, K = (i0[:, 0] + a) % N, (i0[:, 1] + b) % N, (i0[:, 2] + c) % N
+                for d in range(3):
+                    acc[:, d] += w * g[d][I, J, K]
+    return acc
+
+
 def solve_dense(delta, box: float, fr0_abs: float, a: float = 1.0, n: int = 1,
                 omega_m: float = OMEGA_M, u0=None, tol: float = 1e-8, max_vcycles: int = 100,
                 n_pre: int = 2, n_post: int = 2, prolong_linear: bool = True,

@@ -252,14 +252,25 @@ struct LevelPtrs {
   double* a[AMR_MAXL];  // per-level array (mass for deposit)
   // the deposit's record of each particle's cells for the FP32 gather (NULL:
   // none): 8 slots per particle (its cube's corners q = 4 bx + 2 by + bz),
-  // cell level << 27 | index; slot q of particle p at q np + p
-  int* rec_idx;
+  // cell level << rb | index (rb = 32 minus the bits of the deepest level);
+  // slot q of particle p at q np + p
+  unsigned* rec_idx;
   long long np;
+  int rb;
 };
 
 // record slot values: a zero-width corner, and (slot 0) a particle whose cube
 // splits over finer cells (its pieces are not recorded)
-constexpr int kRecSkip = 0x7fffffff, kRecSplit = -1;
+constexpr unsigned kRecSkip = 0xffffffffu, kRecSplit = 0xfffffffeu;
+
+// index bits of a record slot for a hierarchy of nlev levels: the level takes
+// the top max(1, ceil(log2 nlev)) bits; cells of a level must stay below
+// 2^rb - 2 so that no slot equals a marker
+static inline int rec_bits(int nlev) {
+  int lb = 1;
+  while ((1 << lb) < nlev) ++lb;
+  return 32 - lb;
+}
 
 struct GatherPtrs {
   const double* acc[AMR_MAXL];    // FP64: level 0 [3][N0^3]; l >= 1 [ncell][3]
@@ -386,7 +397,7 @@ __device__ __forceinline__ void split_q(const TreeView& T, int l, long long c, c
 // once its warp has reconverged (whole-warp, coalesced stores).
 template <bool GATHER, class W>
 __device__ bool visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, const GatherPtrs& G,
-                               W* out, unsigned long long* err, int* ri = nullptr) {
+                               W* out, unsigned long long* err, unsigned* ri = nullptr) {
   const bool rec = !GATHER && D.rec_idx;
   bool split = false;
   const long long X[3] = {qfix(t.x), qfix(t.y), qfix(t.z)};
@@ -445,7 +456,7 @@ __device__ bool visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
     if (!refined) {
       const W w = Lxy[(bits[0] << 1) | bits[1]] * Lw[2][bits[2]];
       touch<GATHER, W>(lev, cq, w, D, G, out);
-      if (rec) ri[q] = (lev << 27) | (int)cq;
+      if (rec) ri[q] = ((unsigned)lev << D.rb) | (unsigned)cq;
       continue;
     }
     split = true;
@@ -481,7 +492,7 @@ __global__ void __launch_bounds__(256, 4) k_deposit(const double* __restrict__ p
   __shared__ unsigned long long bbase;
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   bool split = false;
-  int ri[8];
+  unsigned ri[8];
   if (p < Np) {
     const P3 t = particle_t(pos, p, inv, N0);
     GatherPtrs G{};
@@ -547,21 +558,21 @@ __global__ void __launch_bounds__(256, 4) k_gather32(const double* __restrict__ 
 // cell is one of the corners).  Particles whose cube split are left to
 // k_gather32_list.  Particles p0 .. p0 + n - 1; np: the record's slot stride.
 __global__ void __launch_bounds__(256) k_gather32_rec(const double* __restrict__ pos,
-                                                      const int* __restrict__ rec_idx,
-                                                      long long np, long long p0, long long n,
-                                                      double inv, double N0, GatherPtrs G,
-                                                      double* __restrict__ acc) {
+                                                      const unsigned* __restrict__ rec_idx,
+                                                      long long np, int rb, long long p0,
+                                                      long long n, double inv, double N0,
+                                                      GatherPtrs G, double* __restrict__ acc) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n) return;
   const long long p = p0 + t;
-  int id[8];
+  unsigned id[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) id[q] = __ldg(rec_idx + q * np + p);
   if (id[0] == kRecSplit) return;
   int lam = 0;
 #pragma unroll
   for (int q = 0; q < 8; ++q)
-    if (id[q] != kRecSkip) lam = max(lam, id[q] >> 27);
+    if (id[q] != kRecSkip) lam = max(lam, (int)(id[q] >> rb));
   const P3 tp = particle_t(pos, p, inv, N0);
   const long long X[3] = {qfix(tp.x), qfix(tp.y), qfix(tp.z)};
   const int F = QB - lam;
@@ -585,7 +596,7 @@ __global__ void __launch_bounds__(256) k_gather32_rec(const double* __restrict__
   for (int q = 0; q < 8; ++q) {
     if (id[q] == kRecSkip) continue;
     const float w = Lxy[q >> 1] * Lw[2][q & 1];
-    const float4 a = __ldg(G.acc32[id[q] >> 27] + (id[q] & ((1 << 27) - 1)));
+    const float4 a = __ldg(G.acc32[id[q] >> rb] + (id[q] & ((1u << rb) - 1u)));
     out[0] = fmaf(w, a.x, out[0]);
     out[1] = fmaf(w, a.y, out[1]);
     out[2] = fmaf(w, a.z, out[2]);
@@ -733,6 +744,32 @@ __global__ void k_face_slots(const int* __restrict__ slot, long long n, int* __r
   }
 }
 
+// The compact face table of the FP32 sweeps, one 16-byte record per oct:
+// per face the neighbouring oct as a 16-bit offset from the oct, kNbGhost for
+// a face without one (the ghost slots of an oct are consecutive in face order
+// from the record's first slot, since the slots are numbered over the faces in
+// storage order) or kNbFar beyond +-32766 octs.
+__global__ void k_nb16(const int* __restrict__ nbr, long long n_oct, int4* __restrict__ rec) {
+  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (o >= n_oct) return;
+  int g = -1;
+  unsigned h[6];
+  for (int d = 0; d < 6; ++d) {
+    const int v = nbr[6 * o + d];
+    int s;
+    if (v < 0) {
+      s = kNbGhost;
+      if (g < 0) g = -v - 1;
+    } else {
+      const long long off = (long long)v - o;
+      s = off >= -32766 && off <= 32766 ? (int)off : kNbFar;
+    }
+    h[d] = (unsigned)s & 0xffffu;
+  }
+  rec[o] = make_int4((int)(h[0] | (h[1] << 16)), (int)(h[2] | (h[3] << 16)),
+                     (int)(h[4] | (h[5] << 16)), g);
+}
+
 // FP32 force copy of a refined level from e^u as double-float pairs (mixed
 // form): the central difference is formed exactly enough in double-float and
 // rounded once, on the FP32 pipes.  acc32 = g_scale (E+ - E-) per axis.
@@ -811,7 +848,7 @@ static void free_level(AmrLevel& L) {
   void* ps[] = {L.son,  L.refined, L.count,  L.opos, L.pcell,   L.nbr,     L.mass,
                 L.w,    L.wE,      L.wf,     L.wold, L.mask,    L.ghost,   L.ghostE,
                 L.acc,  L.pnbr,    L.w32,    L.wE32, L.wf32,    L.wold32,  L.ghost32, L.gface,
-                L.olist,  L.acc32, L.act};
+                L.olist,  L.acc32, L.act, L.nb16};
   for (void* p : ps)
     if (p) cudaFree(p);
   // u, E, f of level >= 1 are owned here too
@@ -896,6 +933,7 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
   L.wold = nullptr; L.mask = nullptr; L.ghost = nullptr; L.ghostE = nullptr; L.acc = nullptr;
   L.pnbr = nullptr; L.w32 = nullptr; L.wE32 = nullptr; L.wf32 = nullptr; L.wold32 = nullptr;
   L.ghost32 = nullptr; L.olist = nullptr; L.acc32 = nullptr; L.act = nullptr; L.gface = nullptr;
+  L.nb16 = nullptr;
   L.gcap = 0;
   TRY(grow(c, &L.son, n));
   TRY(grow(c, &L.refined, n));
@@ -917,6 +955,7 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
     TRY(grow(c, &L.opos, no));
     TRY(grow(c, &L.pcell, no));
     TRY(grow(c, &L.nbr, 6 * no));
+    TRY(grow(c, &L.nb16, no));
     TRY(grow(c, &L.acc, 3 * n));
     TRY(grow(c, &L.acc32, n));
     TRY(grow(c, &L.u, n));
@@ -1000,7 +1039,8 @@ static mgfr_status build_structure(mgfr_ctx* c, AmrWork* A, const double* pos) {
       N.gcap = N.n_gslot;
     }
     k_face_slots<<<nblocks(6 * N.n_oct, BS), BS, 0, c->s>>>(N.son, 6 * N.n_oct, N.nbr, N.gface);
-    c->launches += 2;
+    k_nb16<<<nblocks(N.n_oct, BS), BS, 0, c->s>>>(N.nbr, N.n_oct, N.nb16);
+    c->launches += 3;
   }
   // the deepest level has no sons
   AmrLevel& D = A->L[A->nlev - 1];
@@ -1010,8 +1050,8 @@ static mgfr_status build_structure(mgfr_ctx* c, AmrWork* A, const double* pos) {
 }
 
 // record: keep each particle's cells for the FP32 gather (cell indices must
-// fit the record's 27 bits), with the split particles listed per chunk of
-// `per` particles (per a multiple of 256, at most 8 chunks)
+// fit the record's index bits, rec_bits), with the split particles listed per
+// chunk of `per` particles (per a multiple of 256, at most 8 chunks)
 static mgfr_status deposit(mgfr_ctx* c, AmrWork* A, const double* pos, bool record,
                            long long per) {
   const double inv = (double)A->N0 / A->box, N0d = (double)A->N0;
@@ -1019,7 +1059,7 @@ static mgfr_status deposit(mgfr_ctx* c, AmrWork* A, const double* pos, bool reco
   for (int l = 0; l < A->nlev; ++l) {
     MG_CK(c, cudaMemsetAsync(A->L[l].mass, 0, sizeof(double) * (size_t)A->L[l].ncell, c->s));
     D.a[l] = A->L[l].mass;
-    if (A->L[l].ncell > (1LL << 27)) record = false;
+    if (A->L[l].ncell > (1LL << rec_bits(A->nlev)) - 2) record = false;
   }
   A->rec_on = record;
   A->rec_per = per;
@@ -1033,12 +1073,13 @@ static mgfr_status deposit(mgfr_ctx* c, AmrWork* A, const double* pos, bool reco
       A->rec_idx = nullptr;
       A->split_list = nullptr;
       A->rec_cap = 0;
-      MG_CK(c, cudaMalloc(&A->rec_idx, sizeof(int) * 8 * (size_t)A->Np));
+      MG_CK(c, cudaMalloc(&A->rec_idx, sizeof(unsigned) * 8 * (size_t)A->Np));
       MG_CK(c, cudaMalloc(&A->split_list, sizeof(int) * 8 * (size_t)((A->Np + 7) / 8 + 256)));
       A->rec_cap = A->Np;
     }
     D.rec_idx = A->rec_idx;
     D.np = A->Np;
+    D.rb = rec_bits(A->nlev);
   }
   TreeView T = tree_view(A);
   k_deposit<<<nblocks(A->Np, BS), BS, 0, c->s>>>(pos, A->Np, inv, N0d, T, D,
@@ -1161,10 +1202,12 @@ static mgfr_status solve_particles(mgfr_ctx* c, const double* pos, long long Np,
   const double* u0 = nullptr;
   TRY(start_guess(c, N0, L0.f, 1.0 / m.src, u_init, &u0));
   f64::init_u(u0, L0.u, L0.E, L0.n, c->s);
+  c->u_prev_N = 0;  // valid again once the base level is solved
   c->launches += 1;
   MG_CK(c, cudaEventRecord(c->t0, c->s));
   mgfr_status rs = mixed ? dense_solve_mixed(c, m, box, st) : dense_solve64(c, m, box, st);
   if (rs != MGFR_OK && rs != MGFR_E_NOCONVERGE) return rs;
+  c->u_prev_N = N0;  // the refined levels never write the base level's u
   mgfr_status worst = rs;
   for (int l = 1; l < A->nlev; ++l) {
     mgfr_status ls = amr_solve_level(c, A, l, m, st);
@@ -1229,7 +1272,8 @@ static mgfr_status solve_particles(mgfr_ctx* c, const double* pos, long long Np,
         c->launches += 1;
       }
       if (replay)
-        k_gather32_rec<<<nblocks(n, BS), BS, 0, c->s>>>(pos, A->rec_idx, Np, p0, n,
+        k_gather32_rec<<<nblocks(n, BS), BS, 0, c->s>>>(pos, A->rec_idx, Np,
+                                                        rec_bits(A->nlev), p0, n,
                                                         (double)N0 / box, (double)N0, G, acc_out);
       else if (g32)
         k_gather32<<<nblocks(n, BS), BS, 0, c->s>>>(pos + 3 * p0, n, (double)N0 / box, (double)N0,

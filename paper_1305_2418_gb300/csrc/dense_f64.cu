@@ -47,6 +47,12 @@ __global__ void k_source(const double* __restrict__ d, double* __restrict__ f, l
   if (t < n) f[t] = src * d[t];
 }
 
+// E = e^u of an iterate already in place (the previous solution as the start)
+__global__ void k_init_inplace(const double* __restrict__ u, double* __restrict__ E, long long n) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < n) E[t] = exp(u[t]);
+}
+
 __global__ void k_init(const double* __restrict__ u0, double* __restrict__ u,
                        double* __restrict__ E, long long n) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -178,7 +184,8 @@ __global__ void __launch_bounds__(BS) k_prolong_corr(double* __restrict__ u,
 
 // Direct NGS on the 4^3 grid (Sec. 3.3, step 5): one block of 64 threads,
 // red-black sweeps in shared memory until max|r| drops by `rel` or
-// max_sweeps is reached (bounded loop).
+// max_sweeps is reached (bounded loop); the residual is checked before the
+// first sweep and after every kCheck sweeps.
 __global__ void __launch_bounds__(64) k_coarse(double* __restrict__ ug, double* __restrict__ Eg,
                                                const double* __restrict__ fg, Model m, double ih2,
                                                double cap, int max_sweeps, double rel,
@@ -195,26 +202,28 @@ __global__ void __launch_bounds__(64) k_coarse(double* __restrict__ ug, double* 
                      (i << 4) | (((j + 3) & 3) << 2) | k, (i << 4) | (((j + 1) & 3) << 2) | k,
                      (i << 4) | (j << 2) | ((k + 3) & 3), (i << 4) | (j << 2) | ((k + 1) & 3)};
   __syncthreads();
+  constexpr int kCheck = 4;
   double r0 = -1.0;
   for (int s = 0; s <= max_sweeps; ++s) {
-    // residual max (before sweep s)
-    double sbd = 0.0;
-    for (int q = 0; q < 6; ++q) sbd = fma(0.5 * (E[nb[q]] + E[t]), u[nb[q]] - u[t], sbd);
-    const double rr = fabs(f[t] - (sbd * ih2 + m.aRt * (1.0 - nl_s(u[t], E[t], m))));
-    red[t] = active ? rr : 0.0;
-    __syncthreads();
-    for (int w = 32; w > 0; w >>= 1) {
-      if (t < w) red[t] = fmax(red[t], red[t + w]);
+    if (s % kCheck == 0 || s == max_sweeps) {
+      // residual max (before sweep s)
+      double sbd = 0.0;
+      for (int q = 0; q < 6; ++q) sbd = fma(0.5 * (E[nb[q]] + E[t]), u[nb[q]] - u[t], sbd);
+      const double rr = fabs(f[t] - (sbd * ih2 + m.aRt * (1.0 - nl_s(u[t], E[t], m))));
+      red[t] = active ? rr : 0.0;
       __syncthreads();
+      for (int w = 32; w > 0; w >>= 1) {
+        if (t < w) red[t] = fmax(red[t], red[t + w]);
+        __syncthreads();
+      }
+      const double rmax = red[0];
+      __syncthreads();
+      if (r0 < 0.0) r0 = rmax;
+      if (s == max_sweeps || rmax <= rel * r0) break;
     }
-    const double rmax = red[0];
-    __syncthreads();
-    if (r0 < 0.0) r0 = rmax;
-    if (s == max_sweeps || rmax <= rel * r0) break;
     for (int c = 0; c < 2; ++c) {
       if (colour == c && active) {
-        double sb = 0.0, sd = 0.0;
-        sbd = 0.0;
+        double sb = 0.0, sd = 0.0, sbd = 0.0;
         const double uc = u[t], Ec = E[t];
         for (int q = 0; q < 6; ++q) {
           const double b = 0.5 * (E[nb[q]] + Ec), du = u[nb[q]] - uc;
@@ -326,7 +335,10 @@ void source(const double* delta, double* f, long long n, double src, cudaStream_
 }
 
 void init_u(const double* u0, double* u, double* E, long long n, cudaStream_t s) {
-  k_init<<<nblocks(n, BS), BS, 0, s>>>(u0, u, E, n);
+  if (u0 == u)
+    k_init_inplace<<<nblocks(n, BS), BS, 0, s>>>(u, E, n);
+  else
+    k_init<<<nblocks(n, BS), BS, 0, s>>>(u0, u, E, n);
 }
 
 void sweep(DenseLevel& L, const Model& m, int colour, double cap, cudaStream_t s) {

@@ -61,6 +61,9 @@ struct DenseHier {
 };
 
 // ---- FP64 dense kernels (dense_f64.cu) -----------------------------------
+// Relative drop of the max residual at which the FP64 4^3 coarsest-grid
+// solve stops (an accelerator: the fixed point does not depend on it).
+constexpr double kCoarseRel64 = 1e-6;
 namespace f64 {
 void source(const double* delta, double* f, long long n, double src, cudaStream_t s);
 void init_u(const double* u0, double* u, double* E, long long n, cudaStream_t s);
@@ -150,6 +153,7 @@ struct mgfr_ctx {
   int capturing = -1;            // graph being captured (-1: none)
   long long graph_kernels[4] = {0, 0, 0, 0};  // kernel nodes per captured graph
   long long launches = 0;        // kernels launched by the current call
+  int u_prev_N = 0;              // grid of the solution held in dh.L[0].u (0: none)
   double* u_learn = nullptr;     // learned initial guess of a solve (MGFR_START_LEARNED)
   long long u_learn_cap = 0;
 };

@@ -117,7 +117,7 @@ void na_vcycle(NaHier& H, const mgfr_config& g, const Model& m, int l, cudaStrea
   if (C.N > 4)
     na_vcycle(H, g, m, l + 1, s, upd);
   else
-    f64::coarse_solve(C, m, g.step_cap, 200, 1e-12, s);
+    f64::coarse_solve(C, m, g.step_cap, 200, kCoarseRel64, s);
   f64::prolong_corr(F, C, g.prolong_linear, s);
   for (int q = 0; q < g.n_post; ++q) {
     f64::sweep(F, m, 0, g.step_cap, s);

@@ -159,6 +159,68 @@ __global__ void k_pm_affine(const double* __restrict__ x, long long n, double sc
   if (i < n) y[i] = scale * (x[i] - shift);
 }
 
+// g = -grad phi by central differences (periodic), component-major [3][n]
+__global__ void __launch_bounds__(BS) k_pm_grad(const double* __restrict__ phi, int lg, double inv2h,
+                                                double* __restrict__ g) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n = 1LL << (3 * lg);
+  if (t >= n) return;
+  const int M = (1 << lg) - 1;
+  const int k = (int)(t & M), j = (int)((t >> lg) & M), i = (int)(t >> (2 * lg));
+  g[t] = -(phi[pidx((i + 1) & M, j, k, lg)] - phi[pidx((i - 1) & M, j, k, lg)]) * inv2h;
+  g[n + t] = -(phi[pidx(i, (j + 1) & M, k, lg)] - phi[pidx(i, (j - 1) & M, k, lg)]) * inv2h;
+  g[2 * n + t] = -(phi[pidx(i, j, (k + 1) & M, lg)] - phi[pidx(i, j, (k - 1) & M, lg)]) * inv2h;
+}
+
+// cloud-in-cell interpolation of g [3][N^3] (values at cell centres) to the
+// particles: position t = x N / box in cell units (wrapped), the 8 cells
+// around t - 1/2 with the product of the 1D linear weights
+__global__ void __launch_bounds__(BS) k_pm_cic(const double* __restrict__ pos, long long np, int lg,
+                                               double inv_h, const double* __restrict__ g,
+                                               double* __restrict__ acc) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const int N = 1 << lg, M = N - 1;
+  const long long n = 1LL << (3 * lg);
+  int i0[3];
+  double w1[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double t = pos[3 * p + a] * inv_h - 0.5;
+    const double fl = floor(t);
+    w1[a] = t - fl;
+    i0[a] = (int)((long long)fl & M);
+  }
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int a = q >> 2, b = (q >> 1) & 1, c = q & 1;
+    const double w = (a ? w1[0] : 1.0 - w1[0]) * (b ? w1[1] : 1.0 - w1[1]) * (c ? w1[2] : 1.0 - w1[2]);
+    const unsigned id = pidx((i0[0] + a) & M, (i0[1] + b) & M, (i0[2] + c) & M, lg);
+    s0 = fma(w, g[id], s0);
+    s1 = fma(w, g[n + id], s1);
+    s2 = fma(w, g[2 * n + id], s2);
+  }
+  acc[3 * p] = s0;
+  acc[3 * p + 1] = s1;
+  acc[3 * p + 2] = s2;
+}
+
+// leapfrog: v += kick acc, x = wrap(x + drift v); each operation rounded on
+// its own (no fused multiply-add), so the step is reproducible elsewhere
+__global__ void __launch_bounds__(BS) k_kick_drift(double* __restrict__ pos, double* __restrict__ vel,
+                                                   const double* __restrict__ acc, long long n3,
+                                                   double kick, double drift, double box) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  const double v = __dadd_rn(vel[i], __dmul_rn(kick, acc[i]));
+  vel[i] = v;
+  double x = __dadd_rn(pos[i], __dmul_rn(drift, v));
+  x = __dsub_rn(x, __dmul_rn(box, floor(__ddiv_rn(x, box))));
+  if (!(x < box)) x = 0.0;  // rounding at the upper edge
+  pos[i] = x;
+}
+
 struct PmLevel {
   int lg = 0;
   long long n = 0;
@@ -170,6 +232,7 @@ struct PmWork {
   int lg = 0, nlev = 0;
   PmLevel L[PM_MAXL];
   double* res = nullptr;      // residual of the finest level
+  double* grad = nullptr;     // -grad phi [3][n] of the finest level (force)
   double* part = nullptr;     // block sums (device)
   double* part_h = nullptr;   // block sums (page-locked host)
   int nparts = 0;
@@ -182,9 +245,10 @@ void pm_free_work(PmWork* P) {
     L = PmLevel();
   }
   if (P->res) cudaFree(P->res);
+  if (P->grad) cudaFree(P->grad);
   if (P->part) cudaFree(P->part);
   if (P->part_h) cudaFreeHost(P->part_h);
-  P->res = P->part = P->part_h = nullptr;
+  P->res = P->part = P->part_h = P->grad = nullptr;
   P->lg = P->nlev = 0;
 }
 
@@ -268,10 +332,11 @@ void pm_free(mgfr_ctx* c) {
   c->pm = nullptr;
 }
 
-extern "C" mgfr_status mgfr_pm_potential(mgfr_ctx* c, int lpm, int what, double* phi_out_dev,
-                                         double* dens_out_dev, mgfr_stats* st) {
-  if (!c) return MGFR_E_INVALID;
-  if (!phi_out_dev) return set_err(c, MGFR_E_INVALID, "phi_out_dev is required");
+// The potential of Eq. (30) on the PM grid of level lpm, left (zero mean) in
+// the workspace's finest phi; phi_out (nullable) receives a copy.  Runs after
+// the caller's stream, on the context's stream; synchronises.
+static mgfr_status pm_solve(mgfr_ctx* c, int lpm, int what, double* phi_out_dev,
+                            double* dens_out_dev, mgfr_stats* st, PmWork** work) {
   int lg = 0;
   double om = 0.3, a = 1.0;
   mgfr_status rs = amr_density_pm(c, lpm, what, nullptr, &lg, &om, &a);
@@ -316,14 +381,15 @@ extern "C" mgfr_status mgfr_pm_potential(mgfr_ctx* c, int lpm, int what, double*
   }
   // zero mean
   if ((rs = pm_sums(c, P, L0.phi, L0.n, &sum, &sq)) != MGFR_OK) return rs;
-  k_pm_affine<<<nblocks(L0.n, BS), BS, 0, c->s>>>(L0.phi, L0.n, 1.0, sum / (double)L0.n,
-                                                  phi_out_dev);
+  k_pm_affine<<<nblocks(L0.n, BS), BS, 0, c->s>>>(L0.phi, L0.n, 1.0, sum / (double)L0.n, L0.phi);
   c->launches += 1;
+  if (phi_out_dev)
+    MG_CK(c, cudaMemcpyAsync(phi_out_dev, L0.phi, sizeof(double) * (size_t)L0.n,
+                             cudaMemcpyDeviceToDevice, c->s));
   MG_CK(c, cudaEventRecord(c->t1, c->s));
-  MG_CK(c, cudaEventRecord(c->ev_out, c->s));
-  MG_CK(c, cudaStreamWaitEvent(c->user, c->ev_out, 0));
   MG_CK(c, cudaStreamSynchronize(c->s));
   MG_CK(c, cudaGetLastError());
+  *work = P;
   if (st) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->t0, c->t1);
@@ -341,5 +407,55 @@ extern "C" mgfr_status mgfr_pm_potential(mgfr_ctx* c, int lpm, int what, double*
   }
   if (!(r <= target))
     return set_err(c, MGFR_E_NOCONVERGE, "PM Poisson solve did not reach the tolerance");
+  return MGFR_OK;
+}
+
+static mgfr_status pm_finish(mgfr_ctx* c, mgfr_status rs) {
+  MG_CK(c, cudaEventRecord(c->ev_out, c->s));
+  MG_CK(c, cudaStreamWaitEvent(c->user, c->ev_out, 0));
+  MG_CK(c, cudaStreamSynchronize(c->s));
+  MG_CK(c, cudaGetLastError());
+  return rs;
+}
+
+extern "C" mgfr_status mgfr_pm_potential(mgfr_ctx* c, int lpm, int what, double* phi_out_dev,
+                                         double* dens_out_dev, mgfr_stats* st) {
+  if (!c) return MGFR_E_INVALID;
+  if (!phi_out_dev) return set_err(c, MGFR_E_INVALID, "phi_out_dev is required");
+  PmWork* P = nullptr;
+  mgfr_status rs = pm_solve(c, lpm, what, phi_out_dev, dens_out_dev, st, &P);
+  if (rs != MGFR_OK && rs != MGFR_E_NOCONVERGE) return rs;
+  return pm_finish(c, rs);
+}
+
+extern "C" mgfr_status mgfr_pm_accel(mgfr_ctx* c, int lpm, int what, const double* pos_dev,
+                                     long long Np, double* acc_out_dev, mgfr_stats* st) {
+  if (!c) return MGFR_E_INVALID;
+  if (!pos_dev || !acc_out_dev || Np <= 0 || Np >= (1LL << 40))
+    return set_err(c, MGFR_E_INVALID, "need positions and a force array of Np >= 1 particles");
+  PmWork* P = nullptr;
+  mgfr_status rs = pm_solve(c, lpm, what, nullptr, nullptr, st, &P);
+  if (rs != MGFR_OK && rs != MGFR_E_NOCONVERGE) return rs;
+  PmLevel& L0 = P->L[0];
+  if (!P->grad) MG_CK(c, cudaMalloc(&P->grad, sizeof(double) * 3 * (size_t)L0.n));
+  const double box = ((AmrWork*)c->amr)->box;
+  const double h = box / (double)(1LL << L0.lg);
+  k_pm_grad<<<nblocks(L0.n, BS), BS, 0, c->s>>>(L0.phi, L0.lg, 0.5 / h, P->grad);
+  k_pm_cic<<<nblocks(Np, BS), BS, 0, c->s>>>(pos_dev, Np, L0.lg, 1.0 / h, P->grad, acc_out_dev);
+  c->launches += 2;
+  if (st) st->gpu_launches = c->launches;
+  return pm_finish(c, rs);
+}
+
+extern "C" mgfr_status mgfr_kick_drift(double* pos_dev, double* vel_dev, const double* acc_dev,
+                                       long long Np, double kick, double drift, double box,
+                                       void* cuda_stream) {
+  if (!pos_dev || !vel_dev || !acc_dev || Np <= 0 || Np >= (1LL << 40) || !(box > 0.0) ||
+      !std::isfinite(kick) || !std::isfinite(drift))
+    return MGFR_E_INVALID;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  k_kick_drift<<<nblocks(3 * Np, BS), BS, 0, s>>>(pos_dev, vel_dev, acc_dev, 3 * Np, kick, drift,
+                                                  box);
+  if (cudaGetLastError() != cudaSuccess) return MGFR_E_CUDA;
   return MGFR_OK;
 }

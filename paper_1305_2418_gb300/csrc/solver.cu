@@ -156,8 +156,8 @@ bool validate_cfg(const mgfr_config* c, std::string& why) {
   if (c->max_spins < 0) return bad("max_spins must be >= 0");
   if (!(c->mask_thres >= 0.0 && c->mask_thres < 1.0)) return bad("mask_thres in [0, 1)");
   if (c->n_coarse < 0 || c->n_coarse > 16) return bad("n_coarse in [0, 16]");
-  if (c->start != MGFR_START_ZERO && c->start != MGFR_START_USER && c->start != MGFR_START_LEARNED)
-    return bad("start must be 0 (zero), 1 (user) or 2 (learned)");
+  if (c->start < MGFR_START_ZERO || c->start > MGFR_START_PREVIOUS)
+    return bad("start must be 0 (zero), 1 (user), 2 (learned) or 3 (previous)");
   return true;
 }
 
@@ -166,6 +166,13 @@ mgfr_status start_guess(mgfr_ctx* c, int N, const double* x, double dscale, cons
   *u0 = u_init;
   if (c->cfg.start == MGFR_START_USER && !u_init)
     return set_err(c, MGFR_E_INVALID, "start = user needs u_init");
+  if (c->cfg.start == MGFR_START_PREVIOUS) {
+    if (u_init) return set_err(c, MGFR_E_INVALID, "start = previous takes no u_init");
+    if (c->u_prev_N != N || c->dh.N != N)
+      return set_err(c, MGFR_E_INVALID, "start = previous: no solution of this size in the context");
+    *u0 = c->dh.L[0].u;  // kept in place; the initialisation forms e^u from it
+    return MGFR_OK;
+  }
   if (c->cfg.start != MGFR_START_LEARNED) return MGFR_OK;
   if (u_init) return set_err(c, MGFR_E_INVALID, "start = learned takes no u_init");
   const long long n = (long long)N * N * N;
@@ -213,6 +220,7 @@ static mgfr_status ensure_dense(mgfr_ctx* c, int N, bool mixed) {
   if (H.N == N && (H.mixed || !mixed)) return MGFR_OK;
   drop_graphs(c);
   free_dense(H);
+  c->u_prev_N = 0;
   H.N = N;
   H.mixed = mixed;
   int lg = 0;
@@ -276,7 +284,7 @@ static void vcycle64(mgfr_ctx* c, const Model& m, int l, long long& updates) {
   if (C.N > 4)
     vcycle64(c, m, l + 1, updates);
   else
-    f64::coarse_solve(C, m, g.step_cap, 200, 1e-12, c->s);
+    f64::coarse_solve(C, m, g.step_cap, 200, kCoarseRel64, c->s);
   f64::prolong_corr(F, C, g.prolong_linear, c->s);
   for (int s = 0; s < g.n_post; ++s) {
     for (int col = 0; col < 2; ++col) {
@@ -676,6 +684,7 @@ mgfr_status mgfr_solve_density(mgfr_ctx* c, const double* delta, int N, double b
   if ((rs = start_guess(c, N, delta, 1.0, u_init, &u0)) != MGFR_OK) return rs;
   f64::source(delta, L0.f, L0.n, m.src, c->s);
   f64::init_u(u0, L0.u, L0.E, L0.n, c->s);
+  c->u_prev_N = 0;  // valid again once solved
   c->launches += 2;
   MG_CK(c, cudaEventRecord(c->t0, c->s));
   rs = mixed ? dense_solve_mixed(c, m, box, st) : dense_solve64(c, m, box, st);
@@ -684,6 +693,9 @@ mgfr_status mgfr_solve_density(mgfr_ctx* c, const double* delta, int N, double b
     f64::force(L0, m, fr_out, acc_out, c->s);
     c->launches += 1;
     if (u_out) MG_CK(c, cudaMemcpyAsync(u_out, L0.u, sizeof(double) * L0.n, cudaMemcpyDeviceToDevice, c->s));
+    c->u_prev_N = N;  // the next solve may start from it
+  } else {
+    c->u_prev_N = 0;
   }
   MG_CK(c, cudaEventRecord(c->ev_out, c->s));
   MG_CK(c, cudaStreamWaitEvent(c->user, c->ev_out, 0));

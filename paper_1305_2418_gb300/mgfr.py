@@ -17,7 +17,7 @@ MGFR_OK, MGFR_E_INVALID, MGFR_E_CUDA, MGFR_E_OOM, MGFR_E_NOCONVERGE, MGFR_E_TIME
     MGFR_E_UNSUPPORTED = range(7)
 STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "NOCONVERGE", "TIMEOUT", "UNSUPPORTED"]
 PREC_FP64, PREC_MIXED = 0, 1
-START_ZERO, START_USER, START_LEARNED = 0, 1, 2
+START_ZERO, START_USER, START_LEARNED, START_PREVIOUS = 0, 1, 2, 3
 PM_EFFECTIVE, PM_MATTER, PM_TOTAL = 0, 1, 2
 FIELD_U, FIELD_FR, FIELD_SOURCE, FIELD_MASS, FIELD_ACC, FIELD_COUNT = range(6)
 
@@ -92,6 +92,10 @@ SIGNATURES = {
     "mgfr_effective_mass_pm": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "mgfr_pm_potential": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
+    "mgfr_pm_accel": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_longlong,
+                                C.c_void_p, C.c_void_p]),
+    "mgfr_kick_drift": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_double,
+                                  C.c_double, C.c_double, C.c_void_p]),
     "mgfr_solve_density_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                              C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_void_p]),
@@ -285,6 +289,15 @@ class Solver:
                                             C.byref(stats)))
         return phi, dens, stats.to_dict()
 
+    def pm_accel(self, pos, lpm: int = 0, what: int = 2):
+        """-grad phi of the PM potential at the particles (mgfr_pm_accel):
+        returns (acc [Np, 3] CUDA FP64, stats)."""
+        acc = torch_empty_like(pos)
+        stats = Stats()
+        self._check(lib().mgfr_pm_accel(self.h, lpm, what, _ptr(pos), pos.shape[0], _ptr(acc),
+                                        C.byref(stats)))
+        return acc, stats.to_dict()
+
     def _batch_items(self, deltas, boxes, a, fr0s, ns, u_inits, want_acc, want_u=False):
         import torch
         k = len(deltas)
@@ -371,6 +384,21 @@ class Solver:
         out = np.empty(n.value, dtype=np.float32)
         self._check(lib().mgfr_unet_grads(self.h, out.ctypes.data_as(C.c_void_p)))
         return out
+
+
+def torch_empty_like(t):
+    import torch
+    return torch.empty_like(t)
+
+
+def kick_drift(pos, vel, acc, kick: float, drift: float, box: float, stream=None):
+    """Leapfrog kick-drift of [Np, 3] CUDA FP64 arrays in place (mgfr_kick_drift)."""
+    import torch
+    s = torch.cuda.current_stream(pos.device) if stream is None else stream
+    st = lib().mgfr_kick_drift(_ptr(pos), _ptr(vel), _ptr(acc), pos.shape[0], kick, drift, box,
+                               C.c_void_p(s.cuda_stream))
+    if st != MGFR_OK:
+        raise MGFRError(st, "mgfr_kick_drift failed")
 
 
 def conv3d(op, x, w, bias=None, relu=False, g=None, db=None, stream=None):

@@ -63,3 +63,46 @@ def test_pm_potential_needs_a_particle_solve(dev):
     st = mgfr.lib().mgfr_pm_potential(s.h, 0, mgfr.PM_TOTAL, mgfr._ptr(phi), None, None)
     assert st == mgfr.MGFR_E_INVALID
     s.close()
+
+
+def test_pm_accel_and_kick_drift_match_oracle(dev):
+    """The PM force at the particles (Sec. 2.4, long-range part of Eq. (30))
+    against the oracle's central differences and cloud-in-cell interpolation
+    of its exact potential, and one leapfrog kick-drift step (exact FP64
+    arithmetic on both sides: x + d (v + k a), wrapped)."""
+    N0, box, fr0 = 16, 50.0, 1e-5
+    d = synth.lognormal_delta(N0, box, 1.5, 13011)
+    pos = synth.poisson_particles(d, box, 2.0, 13012)
+    s = mgfr.Solver(0, fr0_abs=fr0, max_level=2, tol_rel=1e-12, max_vcycles=200)
+    pt = torch.from_numpy(pos).to(dev)
+    s.solve_particles(pt, N0, box)
+    A = oracle.AMR(pos, N0, box, 2, 8)
+    A.deposit()
+    A.set_model(fr0)
+    for l in range(A.nlev):
+        u = s.level_field(l, mgfr.FIELD_U)
+        if l == 0:
+            A.set_u(0, u)
+        else:
+            perm = np.argsort(s.level_keys(l), kind="stable")
+            A.set_u(l, u[(8 * perm[:, None] + np.arange(8)[None, :]).ravel()])
+    for lpm, what in ((0, mgfr.PM_TOTAL), (1, mgfr.PM_MATTER), (2, mgfr.PM_EFFECTIVE)):
+        acc, st = s.pm_accel(pt, lpm, what)
+        want = oracle.pm_accel(A.pm_potential(lpm, what), box, pos)
+        err = np.abs(acc.cpu().numpy() - want).max() / np.abs(want).max()
+        assert err <= 1e-8, (lpm, what, err)
+    vel = torch.zeros_like(pt)
+    rng = np.random.default_rng(3)
+    v0 = rng.standard_normal(pos.shape)
+    vel.copy_(torch.from_numpy(v0))
+    acc, _ = s.pm_accel(pt, 0, mgfr.PM_TOTAL)
+    a_h = acc.cpu().numpy()
+    p1 = pt.clone()
+    mgfr.kick_drift(p1, vel, acc, 1e-3, 0.7, box)
+    torch.cuda.synchronize()
+    v1 = v0 + 1e-3 * a_h
+    x1 = pos + 0.7 * v1
+    x1 -= box * np.floor(x1 / box)
+    np.testing.assert_array_equal(vel.cpu().numpy(), v1)
+    np.testing.assert_array_equal(p1.cpu().numpy(), x1)
+    s.close()

@@ -406,6 +406,37 @@ def test_pm_potential_scale_from_the_field_identity():
         A.close()
 
 
+def test_pm_accel_central_difference_and_cic():
+    """The PM force: the central difference of a sine is its exact discrete
+    derivative, and the cloud-in-cell interpolation equals scipy's periodic
+    trilinear interpolation (map_coordinates, order 1, grid-wrap) of the same
+    cell-centred field."""
+    from scipy.ndimage import map_coordinates
+    N, box = 16, 40.0
+    h = box / N
+    x = (np.arange(N) + 0.5) * h
+    k = 2.0 * np.pi * 3 / box
+    phi = np.broadcast_to(np.sin(k * x)[:, None, None], (N, N, N)).copy()
+    rng = np.random.default_rng(41)
+    pos = box * rng.random((300, 3))
+    acc = oracle.pm_accel(phi, box, pos)
+    # g_x at cell centres is -cos(k x) sin(k h) / h exactly; at particles the
+    # interpolation of it
+    gx = -np.cos(k * x) * np.sin(k * h) / h
+    gfield = np.broadcast_to(gx[:, None, None], (N, N, N))
+    coords = (pos / h - 0.5).T
+    want = map_coordinates(gfield, coords, order=1, mode="grid-wrap")
+    np.testing.assert_allclose(acc[:, 0], want, rtol=0, atol=1e-13 * np.abs(gx).max())
+    assert np.abs(acc[:, 1:]).max() < 1e-13 * np.abs(gx).max()
+    # a general field, every component
+    phi = rng.standard_normal((N, N, N))
+    acc = oracle.pm_accel(phi, box, pos)
+    for d in range(3):
+        g = -(np.roll(phi, -1, d) - np.roll(phi, 1, d)) / (2 * h)
+        want = map_coordinates(g, coords, order=1, mode="grid-wrap")
+        np.testing.assert_allclose(acc[:, d], want, rtol=1e-12, atol=1e-12)
+
+
 def _lap7(phi, box):
     h = box / phi.shape[0]
     out = -6.0 * phi
