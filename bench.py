@@ -420,6 +420,36 @@ def time_stepped_extra(mgfr, torch, dev, local, net_path, steps=8):
     return out
 
 
+def enhancement_extra(torch, dev, local):
+    """The AMR-vs-fixed-grid test (Sec. 5.1) on a lognormal stand-in: 256^3
+    particles (sigma_g 1.5) in a 100 Mpc/h box solved on a 64^3 fixed grid, a
+    512^3 fixed grid and a 64^3 base with 3 refinement levels (peak 512^3);
+    the ratio P(delta + delta_eff) / P(delta) on a 512^3 PM grid, and how far
+    the AMR and 64^3 enhancements (ratio - 1) stray from the 512^3 one."""
+    from paper_1305_2418_gb300 import enhance
+    box = 100.0
+    d = synth.lognormal_delta(256, box, 1.5, 5100)
+    pos = torch.from_numpy(synth.poisson_particles(d, box, 1.0, 5100)).to(dev)
+    out = {"workload": "256^3 particles (sigma_g 1.5), box 100 Mpc/h; fixed 64^3, fixed 512^3, "
+                       "64^3 base + 3 levels; PM grid 512^3"}
+    for fr0 in (1e-5, 1e-6):
+        r = {}
+        for name, N0, L in (("fixed64", 64, 0), ("fixed512", 512, 0), ("amr64_3", 64, 3)):
+            k, ratio, _, _ = enhance.run(pos, box, fr0, N0, L, 512, device=local)
+            r[name] = ratio
+        e512 = r["fixed512"] - 1.0
+        out[f"fr0_{fr0:g}"] = {
+            "k": np.round(k, 4).tolist(),
+            "ratio_fixed512": np.round(r["fixed512"], 5).tolist(),
+            "ratio_amr64_3": np.round(r["amr64_3"], 5).tolist(),
+            "ratio_fixed64": np.round(r["fixed64"], 5).tolist(),
+            "amr_vs_fixed512_max_rel_dev_k_le_5": float(
+                np.abs((r["amr64_3"] - 1.0) / e512 - 1.0)[k <= 5.0].max()),
+            "fixed64_vs_fixed512_max_rel_dev_k_lt_0.5": float(
+                np.abs((r["fixed64"] - 1.0) / e512 - 1.0)[k < 0.5].max())}
+    return out
+
+
 def family_table(kern_ms, kern_n, kern_cells, steps, peak):
     fams = []
     for q in range(5):
@@ -644,6 +674,7 @@ def main():
         extras["learned_start"] = learned_extra(mgfr, learned, torch, dev, local)
         extras["time_stepped"] = time_stepped_extra(mgfr, torch, dev, local,
                                                     extras["learned_start"].pop("net_path"))
+        extras["amr_vs_fixed"] = enhancement_extra(torch, dev, local)
 
     nl = last["n_levels"]
     line = {

@@ -744,32 +744,6 @@ __global__ void k_face_slots(const int* __restrict__ slot, long long n, int* __r
   }
 }
 
-// The compact face table of the FP32 sweeps, one 16-byte record per oct:
-// per face the neighbouring oct as a 16-bit offset from the oct, kNbGhost for
-// a face without one (the ghost slots of an oct are consecutive in face order
-// from the record's first slot, since the slots are numbered over the faces in
-// storage order) or kNbFar beyond +-32766 octs.
-__global__ void k_nb16(const int* __restrict__ nbr, long long n_oct, int4* __restrict__ rec) {
-  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (o >= n_oct) return;
-  int g = -1;
-  unsigned h[6];
-  for (int d = 0; d < 6; ++d) {
-    const int v = nbr[6 * o + d];
-    int s;
-    if (v < 0) {
-      s = kNbGhost;
-      if (g < 0) g = -v - 1;
-    } else {
-      const long long off = (long long)v - o;
-      s = off >= -32766 && off <= 32766 ? (int)off : kNbFar;
-    }
-    h[d] = (unsigned)s & 0xffffu;
-  }
-  rec[o] = make_int4((int)(h[0] | (h[1] << 16)), (int)(h[2] | (h[3] << 16)),
-                     (int)(h[4] | (h[5] << 16)), g);
-}
-
 // FP32 force copy of a refined level from e^u as double-float pairs (mixed
 // form): the central difference is formed exactly enough in double-float and
 // rounded once, on the FP32 pipes.  acc32 = g_scale (E+ - E-) per axis.
@@ -848,7 +822,7 @@ static void free_level(AmrLevel& L) {
   void* ps[] = {L.son,  L.refined, L.count,  L.opos, L.pcell,   L.nbr,     L.mass,
                 L.w,    L.wE,      L.wf,     L.wold, L.mask,    L.ghost,   L.ghostE,
                 L.acc,  L.pnbr,    L.w32,    L.wE32, L.wf32,    L.wold32,  L.ghost32, L.gface,
-                L.olist,  L.acc32, L.act, L.nb16};
+                L.olist,  L.acc32, L.act};
   for (void* p : ps)
     if (p) cudaFree(p);
   // u, E, f of level >= 1 are owned here too
@@ -933,7 +907,6 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
   L.wold = nullptr; L.mask = nullptr; L.ghost = nullptr; L.ghostE = nullptr; L.acc = nullptr;
   L.pnbr = nullptr; L.w32 = nullptr; L.wE32 = nullptr; L.wf32 = nullptr; L.wold32 = nullptr;
   L.ghost32 = nullptr; L.olist = nullptr; L.acc32 = nullptr; L.act = nullptr; L.gface = nullptr;
-  L.nb16 = nullptr;
   L.gcap = 0;
   TRY(grow(c, &L.son, n));
   TRY(grow(c, &L.refined, n));
@@ -955,7 +928,6 @@ static mgfr_status alloc_level(mgfr_ctx* c, AmrWork* A, int l) {
     TRY(grow(c, &L.opos, no));
     TRY(grow(c, &L.pcell, no));
     TRY(grow(c, &L.nbr, 6 * no));
-    TRY(grow(c, &L.nb16, no));
     TRY(grow(c, &L.acc, 3 * n));
     TRY(grow(c, &L.acc32, n));
     TRY(grow(c, &L.u, n));
@@ -1039,8 +1011,7 @@ static mgfr_status build_structure(mgfr_ctx* c, AmrWork* A, const double* pos) {
       N.gcap = N.n_gslot;
     }
     k_face_slots<<<nblocks(6 * N.n_oct, BS), BS, 0, c->s>>>(N.son, 6 * N.n_oct, N.nbr, N.gface);
-    k_nb16<<<nblocks(N.n_oct, BS), BS, 0, c->s>>>(N.nbr, N.n_oct, N.nb16);
-    c->launches += 3;
+    c->launches += 2;
   }
   // the deepest level has no sons
   AmrLevel& D = A->L[A->nlev - 1];
@@ -1097,7 +1068,7 @@ static mgfr_status deposit(mgfr_ctx* c, AmrWork* A, const double* pos, bool reco
 }
 
 mgfr_status dense_solve64(mgfr_ctx* c, const Model& m, double box, mgfr_stats* st);
-mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stats* st);
+mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stats* st, bool warm);
 mgfr_status ensure_dense_public(mgfr_ctx* c, int N, bool mixed, double box);
 
 extern "C" {
@@ -1205,7 +1176,8 @@ static mgfr_status solve_particles(mgfr_ctx* c, const double* pos, long long Np,
   c->u_prev_N = 0;  // valid again once the base level is solved
   c->launches += 1;
   MG_CK(c, cudaEventRecord(c->t0, c->s));
-  mgfr_status rs = mixed ? dense_solve_mixed(c, m, box, st) : dense_solve64(c, m, box, st);
+  mgfr_status rs =
+      mixed ? dense_solve_mixed(c, m, box, st, u0 != nullptr) : dense_solve64(c, m, box, st);
   if (rs != MGFR_OK && rs != MGFR_E_NOCONVERGE) return rs;
   c->u_prev_N = N0;  // the refined levels never write the base level's u
   mgfr_status worst = rs;

@@ -26,11 +26,6 @@ struct AmrLevel {
   int4* opos = nullptr;               // [n_oct] parent coordinates at level l-1
   int* pcell = nullptr;               // [n_oct] parent cell index at level l-1
   int* nbr = nullptr;                 // [n_oct*6] face-neighbour oct, or -(1 + ghost slot)
-  int4* nb16 = nullptr;               // [n_oct] the FP32 sweeps' compact face table: per
-                                      // oct six 16-bit entries (x: faces 0, 1; y: 2, 3;
-                                      // z: 4, 5; low half first), each the neighbouring oct
-                                      // as an offset from the oct or kNbGhost / kNbFar,
-                                      // and w = the oct's first ghost slot (-1: none)
   long long n_gslot = 0, gcap = 0;    // ghost faces (faces without a neighbouring oct), capacity
   double* mass = nullptr;             // [ncell] deposited mass (particle units)
   double *u = nullptr, *E = nullptr, *f = nullptr;  // converged solution, source
@@ -52,10 +47,6 @@ struct AmrLevel {
   int* olist = nullptr;               // [n_oct] octs with a relaxed cell (coarse level of a solve)
   long long n_list = 0;               // entries of olist in use
 };
-
-// compact face table: a ghost face, or a neighbour more than 32766 octs away
-// (found in the full table)
-constexpr int kNbGhost = -32768, kNbFar = 32767;
 
 struct TreeView {
   int nlev, lg0;

@@ -655,19 +655,14 @@ struct Oct8 {
   float v[8];
 };
 
-// The float4 of colour `col` of oct o: o and the plane stride no are below
-// 2^31 / 6 (the refined-level limit), so the vector index col no + o fits 32
-// bits, which keeps the address arithmetic of the sweeps in single registers.
 __device__ __forceinline__ float4 ldc(const float* __restrict__ p, long long o, long long no,
                                       int col) {
-  const unsigned v = (unsigned)col * (unsigned)no + (unsigned)o;
-  return reinterpret_cast<const float4*>(p)[v];
+  return *reinterpret_cast<const float4*>(p + 4 * (col * no + o));
 }
 
 __device__ __forceinline__ void stc(float* __restrict__ p, long long o, long long no, int col,
                                     float4 v) {
-  const unsigned x = (unsigned)col * (unsigned)no + (unsigned)o;
-  reinterpret_cast<float4*>(p)[x] = v;
+  *reinterpret_cast<float4*>(p + 4 * (col * no + o)) = v;
 }
 
 // the float4 of one colour <-> the oct's cells of that colour
@@ -695,22 +690,6 @@ __device__ __forceinline__ int face_q(int ch, int ax) {
   return (((ch >> (2 - t1)) & 1) << 1) | ((ch >> (2 - t2)) & 1);
 }
 
-// FP32 ghost values of a ghost face (slot s, face positions q = 0..3) are
-// stored by the parity of q's two bits: plane 0 holds q = 0 and 3, plane 1
-// q = 1 and 2, each pair as a float2 at floats 2 (P ngs + s), q's place in its
-// pair being q >> 1.  The cells of colour COL on the face of side `plus` face
-// the ghosts of plane COL ^ plus only, so a half-sweep reads half of a face.
-struct G32 {
-  const float* p;
-  long long ngs;  // ghost faces of the level
-};
-__device__ __forceinline__ long long g32_at(long long s, int q, long long ngs) {
-  return 2 * (((q >> 1) ^ (q & 1)) * ngs + s) + (q >> 1);
-}
-__device__ __forceinline__ float2 g32_plane(const G32& g, long long s, int P) {
-  return __ldg(reinterpret_cast<const float2*>(g.p + 2 * (P * g.ngs + s)));
-}
-
 // ---- thread-per-oct FP32 sweeps ------------------------------------------------
 // One thread updates the 4 cells of colour COL in its oct.  It reads both
 // colours of its own u, the colour-COL vector of f (or r), and from each face
@@ -723,9 +702,9 @@ __device__ __forceinline__ float2 g32_plane(const G32& g, long long s, int P) {
 template <bool LIN, int COL>
 __global__ void __launch_bounds__(BS, 6) k_oct_sweep32(
     float* __restrict__ u, float* __restrict__ e, const float* __restrict__ rf,
-    const int* __restrict__ nbr, const int4* __restrict__ nb16, const G32 gh,
-    const unsigned char* __restrict__ act, long long n,
-    const int* __restrict__ olist, long long no, MT<float> m, float ih2, float cap) {
+    const int* __restrict__ nbr, const float* __restrict__ gh,
+    const unsigned char* __restrict__ act, long long n, const int* __restrict__ olist,
+    long long no, MT<float> m, float ih2, float cap) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n) return;
   const long long o = olist ? olist[t] : t;
@@ -739,27 +718,19 @@ __global__ void __launch_bounds__(BS, 6) k_oct_sweep32(
   // LIN: corrections of the other colour (the in-oct neighbours)
   const float4 XO = LIN ? ldc(e, o, no, OC) : make_float4(0.f, 0.f, 0.f, 0.f);
   bool on[4];
-  // LIN: s1 = sum off * e, s2 = diagonal sum; NL: s1 = sum b du, s2 = sum (E_c du / 2 - b),
-  // the divergence part of dL/du times h^2
-  float s1[4], s2[4];
+  float s1[4], s2[4], s3[4];  // LIN: (sum off*e, diag sum, -); NL: (sum b du, sum du, sum b)
   // the oct's eight relax flags in one 8-byte load
   const unsigned long long a8 = act ? __ldg(reinterpret_cast<const unsigned long long*>(act) + o)
                                     : ~0ULL;
-  // the six faces from the compact table (three 4-byte loads): the
-  // neighbouring oct o + offset, a ghost face, or (rarely) a far neighbour
-  // looked up in the full table
-  const int4 rec = __ldg(nb16 + o);
-  // face d's entry (d is a compile-time constant in the unrolled loop below)
-  auto ent = [&](int d) -> int {
-    const unsigned w = (unsigned)(d < 2 ? rec.x : (d < 4 ? rec.y : rec.z));
-    return (int)(short)((d & 1) ? (w >> 16) : (w & 0xffffu));
-  };
-  int gslot = rec.w;  // the ghost slot of the next ghost face of the oct
+  // the six face neighbours as three 8-byte loads (6 o ints: 8-byte aligned)
+  const int2* nb2 = reinterpret_cast<const int2*>(nbr + 6 * o);
+  const int2 n01 = __ldg(nb2), n23 = __ldg(nb2 + 1), n45 = __ldg(nb2 + 2);
+  const int nbv[6] = {n01.x, n01.y, n23.x, n23.y, n45.x, n45.y};
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int ch = CC[COL][q];
     on[q] = ((a8 >> (8 * ch)) & 0xffULL) != 0ULL;
-    s1[q] = s2[q] = 0.f;
+    s1[q] = s2[q] = s3[q] = 0.f;
     // in-oct neighbours (other colour, unchanged in this half-sweep)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -772,7 +743,8 @@ __global__ void __launch_bounds__(BS, 6) k_oct_sweep32(
       } else {
         const float b = 0.5f * (EE.v[cn] + EE.v[ch]);
         s1[q] = fmaf(b, du, s1[q]);
-        s2[q] += fmaf(0.5f * EE.v[ch], du, -b);
+        s2[q] += du;
+        s3[q] += b;
       }
     }
   }
@@ -780,29 +752,25 @@ __global__ void __launch_bounds__(BS, 6) k_oct_sweep32(
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     const int a = d >> 1, plus = d & 1;
-    const int en = ent(d);
-    const bool ghost = en == kNbGhost;
+    const int nb = nbv[d];
     float4 NU, NX;
-    if (!ghost) {
-      const long long nb = en == kNbFar ? (long long)__ldg(nbr + 6 * o + d) : o + en;
+    if (nb >= 0) {
       NU = ldc(u, nb, no, OC);
       if (LIN) NX = ldc(e, nb, no, OC);
-    } else {  // the ghost pair this colour faces, in NU.x and NU.y
-      const float2 gp = g32_plane(gh, gslot, COL ^ plus);
-      NU = make_float4(gp.x, gp.y, 0.f, 0.f);
-      ++gslot;
+    } else {
+      NU = *reinterpret_cast<const float4*>(gh + 4LL * (-nb - 1));
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int ch = CC[COL][q];
       if (((ch >> (2 - a)) & 1) != plus) continue;  // not on this face
       float un, xn;
-      if (!ghost) {
+      if (nb >= 0) {
         const int cn = ch ^ (1 << (2 - a));
         un = f4(NU, cn >> 1);
         xn = LIN ? f4(NX, cn >> 1) : 0.f;
       } else {
-        un = (face_q(ch, a) >> 1) ? NU.y : NU.x;
+        un = f4(NU, face_q(ch, a));
         xn = 0.f;
       }
       const float En = __expf(un);
@@ -813,7 +781,8 @@ __global__ void __launch_bounds__(BS, 6) k_oct_sweep32(
       } else {
         const float b = 0.5f * (En + EE.v[ch]);
         s1[q] = fmaf(b, du, s1[q]);
-        s2[q] += fmaf(0.5f * EE.v[ch], du, -b);
+        s2[q] += du;
+        s3[q] += b;
       }
     }
   }
@@ -832,7 +801,7 @@ __global__ void __launch_bounds__(BS, 6) k_oct_sweep32(
       res[q] = __fdividef(f4(R4, q) - s1[q], diag);
     } else {
       const float L = s1[q] * ih2 + m.aRt * (1.f - sN);
-      const float dL = s2[q] * ih2 + m.aRt_np1 * sN;
+      const float dL = (0.5f * EE.v[ch] * s2[q] - s3[q]) * ih2 + m.aRt_np1 * sN;
       float step = __fdividef(L - f4(R4, q), dL);
       step = fminf(fmaxf(step, -cap), cap);
       res[q] = U.v[ch] - step;
@@ -854,8 +823,8 @@ __global__ void __launch_bounds__(BS, 6) k_oct_sweep32(
 // Each face is loaded once per oct instead of once per cell.
 template <bool LIN>
 __device__ __forceinline__ void oct_sums(const float* __restrict__ u, const float* __restrict__ x,
-                                         const int* __restrict__ nbr, const G32 gh, long long o,
-                                         long long no,
+                                         const int* __restrict__ nbr,
+                                         const float* __restrict__ gh, long long o, long long no,
                                          const Oct8& U, const Oct8& EE, const Oct8& X, float* s1,
                                          float* s2) {
 #pragma unroll
@@ -884,11 +853,11 @@ __device__ __forceinline__ void oct_sums(const float* __restrict__ u, const floa
       NU = ld8(u, nb, no);
       if (LIN) NX = ld8(x, nb, no);
     } else {
-      const float2 g0 = g32_plane(gh, -nb - 1, 0), g1 = g32_plane(gh, -nb - 1, 1);
-      G[0] = g0.x;
-      G[3] = g0.y;
-      G[1] = g1.x;
-      G[2] = g1.y;
+      const float4 g = *reinterpret_cast<const float4*>(gh + 4LL * (-nb - 1));
+      G[0] = g.x;
+      G[1] = g.y;
+      G[2] = g.z;
+      G[3] = g.w;
     }
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
@@ -944,8 +913,9 @@ __device__ __forceinline__ void block_partials3(double ss, double mx, double fs,
 // thread per oct; the oct's eight terms are summed in FP32, the octs in FP64.
 __global__ void __launch_bounds__(BS) k_onorm32(const float* __restrict__ u,
                                                 const float* __restrict__ f,
-                                                const int* __restrict__ nbr, const G32 gh,
-                                                long long n_oct, MT<float> m, float ih2,
+                                                const int* __restrict__ nbr,
+                                                const float* __restrict__ gh, long long n_oct,
+                                                MT<float> m, float ih2,
                                                 double* __restrict__ partials) {
   double ss = 0.0, mx = 0.0, fs = 0.0;
   for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n_oct;
@@ -974,7 +944,8 @@ __global__ void __launch_bounds__(BS) k_onorm32(const float* __restrict__ u,
 
 // FAS right-hand side on a coarse oct level (FP32): f += L(u) at relaxed cells
 __global__ void __launch_bounds__(BS) k_ofas32(const float* __restrict__ u, float* __restrict__ f,
-                                               const int* __restrict__ nbr, const G32 gh,
+                                               const int* __restrict__ nbr,
+                                               const float* __restrict__ gh,
                                                const unsigned char* __restrict__ act, long long n,
                                                const int* __restrict__ olist, long long no,
                                                MT<float> m, float ih2) {
@@ -999,7 +970,7 @@ __global__ void __launch_bounds__(BS) k_ofas32(const float* __restrict__ u, floa
 // level (0: dense).
 __global__ void __launch_bounds__(BS) k_orestrict32(
     const float* __restrict__ u, const float* __restrict__ f, const int* __restrict__ nbr,
-    const G32 gh, const unsigned char* __restrict__ act, long long n,
+    const float* __restrict__ gh, const unsigned char* __restrict__ act, long long n,
     const int* __restrict__ olist, long long no, const int* __restrict__ pcell, long long pno,
     MT<float> m, float ih2, float* __restrict__ uc, float* __restrict__ ucold,
     float* __restrict__ fc) {
@@ -1030,7 +1001,7 @@ __global__ void __launch_bounds__(BS) k_orestrict32(
 // u_c = R(u), e_c = 0.
 __global__ void __launch_bounds__(BS) k_olin_restrict32(
     const float* __restrict__ e, const float* __restrict__ r, const float* __restrict__ u,
-    const int* __restrict__ nbr, const G32 gh,
+    const int* __restrict__ nbr, const float* __restrict__ gh,
     const unsigned char* __restrict__ act, long long n, const int* __restrict__ olist,
     long long no, const int* __restrict__ pcell, long long pno, MT<float> m, float ih2,
     float* __restrict__ rc, float* __restrict__ uc, float* __restrict__ ec) {
@@ -1378,7 +1349,7 @@ __global__ void k_ghosts(long long n_gslot, int l, TreeView T, const unsigned* _
       }
     reinterpret_cast<dfl*>(ghost)[t] = V;
     reinterpret_cast<dfl*>(ghostE)[t] = df_exp(V);
-    g32[g32_at(t >> 2, qi, n_gslot)] = V.hi;
+    g32[t] = V.hi;
     return;
   }
   double v = lev == l - 1 ? up[pc] : 0.0;
@@ -1387,7 +1358,7 @@ __global__ void k_ghosts(long long n_gslot, int l, TreeView T, const unsigned* _
     if (cp[a] >= 0) v += (hbit(a) ? 0.125 : -0.125) * (up[cp[a]] - up[cm[a]]);
   ghost[t] = v;
   ghostE[t] = exp(v);
-  g32[g32_at(t >> 2, qi, n_gslot)] = (float)v;
+  g32[t] = (float)v;
 }
 
 // FP64 cell array -> FP32 array of a level (no: its octs, 0 for dense)
@@ -1587,12 +1558,12 @@ void relax(SolveCtx& S, int l, int sweeps) {
           const unsigned char* mk = l == S.L ? nullptr : L.act;
           if (col == 0)
             k_oct_sweep32<false, 0><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-                L.w32, nullptr, L.wf32, L.nbr, L.nb16, G32{L.ghost32, L.n_gslot}, mk,
-                R.n, R.list, L.n_oct, m, (float)L.ih2, (float)g.step_cap);
+                L.w32, nullptr, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, L.n_oct, m,
+                (float)L.ih2, (float)g.step_cap);
           else
             k_oct_sweep32<false, 1><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-                L.w32, nullptr, L.wf32, L.nbr, L.nb16, G32{L.ghost32, L.n_gslot}, mk,
-                R.n, R.list, L.n_oct, m, (float)L.ih2, (float)g.step_cap);
+                L.w32, nullptr, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, L.n_oct, m,
+                (float)L.ih2, (float)g.step_cap);
         } else {
           k_osweep<T><<<nblocks(4 * R.n, BS), BS, 0, c->s>>>(
               a.w, a.wE, a.wf, L.nbr, a.gh, a.ghE, l == S.L ? nullptr : L.act, R.n,
@@ -1676,8 +1647,7 @@ void vcycle_tree(SolveCtx& S, int l) {
     const long long pno = l - 1 >= 1 ? P.n_oct : 0;  // FP32 parent layout (0: dense)
     if (R.n > 0) {
       if constexpr (std::is_same<T, float>::value)
-        k_orestrict32<<<nblocks(R.n, BS), BS, 0, c->s>>>(a.w, a.wf, F.nbr,
-                                                         G32{a.gh, F.n_gslot}, fmask,
+        k_orestrict32<<<nblocks(R.n, BS), BS, 0, c->s>>>(a.w, a.wf, F.nbr, a.gh, fmask,
                                                          R.n, R.list, F.n_oct, F.pcell, pno, m,
                                                          (T)F.ih2, b.w, b.wold, b.wf);
       else
@@ -1688,8 +1658,7 @@ void vcycle_tree(SolveCtx& S, int l) {
     if (l - 1 >= 1) {
       if (P.n_list > 0) {
         if constexpr (std::is_same<T, float>::value)
-          k_ofas32<<<nblocks(P.n_list, BS), BS, 0, c->s>>>(b.w, b.wf, P.nbr,
-                                                           G32{b.gh, P.n_gslot}, P.act,
+          k_ofas32<<<nblocks(P.n_list, BS), BS, 0, c->s>>>(b.w, b.wf, P.nbr, b.gh, P.act,
                                                            P.n_list, P.olist, P.n_oct, m,
                                                            (T)P.ih2);
         else
@@ -1746,8 +1715,7 @@ mgfr_status level_norm(SolveCtx& S, double* hs) {
   int nparts;
   if constexpr (std::is_same<T, float>::value) {
     nparts = (int)std::min<long long>(H.nparts / 2, nblocks(L.n_oct, BS));
-    k_onorm32<<<nparts, BS, 0, c->s>>>(a.w, a.wf, L.nbr, G32{a.gh, L.n_gslot}, L.n_oct,
-                                       mt<float>(S.m),
+    k_onorm32<<<nparts, BS, 0, c->s>>>(a.w, a.wf, L.nbr, a.gh, L.n_oct, mt<float>(S.m),
                                        (float)L.ih2, H.partials);
   } else {
     nparts = (int)std::min<long long>(H.nparts / 2, nblocks(L.ncell, BS));
@@ -1816,12 +1784,12 @@ void lin_relax(SolveCtx& S, int l, int sweeps) {
         if (l == S.L) prof_begin(c, 4, L.ncell);
         if (col == 0)
           k_oct_sweep32<true, 0><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-              L.w32, L.wold32, L.wf32, L.nbr, L.nb16, G32{L.ghost32, L.n_gslot}, mk,
-              R.n, R.list, L.n_oct, m, (float)L.ih2, 0.f);
+              L.w32, L.wold32, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, L.n_oct, m,
+              (float)L.ih2, 0.f);
         else
           k_oct_sweep32<true, 1><<<nblocks(R.n, BS), BS, 0, c->s>>>(
-              L.w32, L.wold32, L.wf32, L.nbr, L.nb16, G32{L.ghost32, L.n_gslot}, mk,
-              R.n, R.list, L.n_oct, m, (float)L.ih2, 0.f);
+              L.w32, L.wold32, L.wf32, L.nbr, L.ghost32, mk, R.n, R.list, L.n_oct, m,
+              (float)L.ih2, 0.f);
         if (l == S.L) prof_end(c);
       } else {
         const long long nl = S.A->dlist_n[0][col];
@@ -1891,8 +1859,7 @@ void lin_vcycle_tree(SolveCtx& S, int l) {
     const long long pno = l - 1 >= 1 ? P.n_oct : 0;  // FP32 parent layout (0: dense)
     if (R.n > 0)
       k_olin_restrict32<<<nblocks(R.n, BS), BS, 0, c->s>>>(
-          F.wold32, F.wf32, F.w32, F.nbr, G32{F.ghost32, F.n_gslot}, fmask, R.n, R.list,
-          F.n_oct, F.pcell, pno,
+          F.wold32, F.wf32, F.w32, F.nbr, F.ghost32, fmask, R.n, R.list, F.n_oct, F.pcell, pno,
           m, (float)F.ih2, P.wf32, P.w32, P.wold32);
     c->launches += 1;
     lin_vcycle_tree(S, l - 1);

@@ -416,6 +416,16 @@ __global__ void k_df2d(const dfl* __restrict__ x, double* __restrict__ y, long l
   }
 }
 
+// an FP64 iterate (in place) -> double-float pairs, and e^u as pairs
+__global__ void k_d2df_exp(dfl* __restrict__ u, dfl* __restrict__ E, long long n) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    const dfl v = df_from_double_bits(reinterpret_cast<const double*>(u)[t]);
+    u[t] = v;
+    E[t] = df_exp(v);
+  }
+}
+
 __global__ void k_zero(float* __restrict__ x, long long n) {
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) x[t] = 0.f;
@@ -457,6 +467,10 @@ void to_df(DenseLevel& L, cudaStream_t s) {
 }
 void f_to_df(const double* f, double* fdf, long long n, cudaStream_t s) {
   k_d2df<<<nblocks(n, BS), BS, 0, s>>>(f, reinterpret_cast<dfl*>(fdf), n);
+}
+void fp64_to_df(DenseLevel& L, cudaStream_t s) {
+  k_d2df_exp<<<nblocks(L.n, BS), BS, 0, s>>>(reinterpret_cast<dfl*>(L.u), reinterpret_cast<dfl*>(L.E),
+                                             L.n);
 }
 void state_to_fp64(DenseLevel& L, cudaStream_t s) {
   k_df2d<<<nblocks(L.n, BS), BS, 0, s>>>(reinterpret_cast<const dfl*>(L.u), L.u, L.n);

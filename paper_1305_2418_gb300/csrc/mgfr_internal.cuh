@@ -114,6 +114,8 @@ void zero(float* x, long long n, cudaStream_t s);
 void apply_corr(DenseLevel& L, double cap, cudaStream_t s);
 // u = u32, E = e^u as double-float pairs
 void to_df(DenseLevel& L, cudaStream_t s);
+// the FP64 iterate in L.u -> double-float pairs in place, E = e^u as pairs
+void fp64_to_df(DenseLevel& L, cudaStream_t s);
 // f (FP64) -> fdf (double-float pairs, same size)
 void f_to_df(const double* f, double* fdf, long long n, cudaStream_t s);
 // L.u, L.E: double-float pairs -> FP64 (in place)

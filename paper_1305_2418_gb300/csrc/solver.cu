@@ -467,7 +467,10 @@ static void vcycle_lin(mgfr_ctx* c, const Model& m, int l, long long& updates) {
 // Mixed form: FP32 nonlinear V-cycles until ||r|| <= mixed_switch ||f|| (or
 // they stall), then FP64 defect correction: r = f - L(u) in FP64, FP32 linear
 // V-cycles on J e = r, u += e in FP64, until the FP64 stopping test holds.
-mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stats* st) {
+// warm: the start is not zero; its FP64-accurate residual is formed first,
+// and if it already meets the switch point the FP32 phase (which would round
+// the start to FP32) is skipped.
+mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stats* st, bool warm) {
   DenseHier& H = c->dh;
   DenseLevel& L0 = H.L[0];
   const mgfr_config& g = c->cfg;
@@ -529,32 +532,46 @@ mgfr_status dense_solve_mixed(mgfr_ctx* c, const Model& m, double box, mgfr_stat
   int vc = 0, outer = 0;
   double r = r0;
   bool state_df = false;  // L0.u, L0.E hold double-float pairs (phase B)
-  if (r > target) {
+  bool skip_a = false;    // the start already meets the switch point
+  if (r > target || warm) {
     f32::f_to_df(L0.f, H.fdf, L0.n, c->s);
     c->launches += 1;
   }
-  // Phases alternate: A until it reaches mixed_switch or stalls, then B while
-  // the FP64 residual keeps falling; a rise in B sends the iterate back to A.
-  for (int round = 0; round < 8 && r > target; ++round) {
-    double prev = -1.0;
-    while (vc < g.max_vcycles) {
-      if ((rs = issue(c, 1, c->g_v32, body32)) != MGFR_OK) return rs;
-      if ((rs = sync_read(c)) != MGFR_OK) return rs;
-      prof_collect(c, 1, st);
-      ++vc;
-      const double r32 = std::sqrt(hs[0]);
-      if (!std::isfinite(r32)) break;
-      if (r32 <= g.mixed_switch * ref) break;
-      if (prev > 0.0 && r32 > 0.7 * prev) break;
-      prev = r32;
-    }
-    f32::to_df(L0, c->s);
+  if (warm) {
+    f32::fp64_to_df(L0, c->s);
     f32::resid_df(L0, H.fdf, m, H.partials, H.nparts, H.scal, c->s);
     c->launches += 3;
     state_df = true;
     MG_CK(c, cudaMemcpyAsync(hs, H.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
     if ((rs = sync_read(c)) != MGFR_OK) return rs;
     r = std::sqrt(hs[0]);
+    if (st) st->res_l2_init = r;
+    skip_a = r <= g.mixed_switch * ref;
+  }
+  // Phases alternate: A until it reaches mixed_switch or stalls, then B while
+  // the FP64 residual keeps falling; a rise in B sends the iterate back to A.
+  for (int round = 0; round < 8 && r > target; ++round) {
+    if (!(skip_a && round == 0)) {
+      double prev = -1.0;
+      while (vc < g.max_vcycles) {
+        if ((rs = issue(c, 1, c->g_v32, body32)) != MGFR_OK) return rs;
+        if ((rs = sync_read(c)) != MGFR_OK) return rs;
+        prof_collect(c, 1, st);
+        ++vc;
+        const double r32 = std::sqrt(hs[0]);
+        if (!std::isfinite(r32)) break;
+        if (r32 <= g.mixed_switch * ref) break;
+        if (prev > 0.0 && r32 > 0.7 * prev) break;
+        prev = r32;
+      }
+      f32::to_df(L0, c->s);
+      f32::resid_df(L0, H.fdf, m, H.partials, H.nparts, H.scal, c->s);
+      c->launches += 3;
+      state_df = true;
+      MG_CK(c, cudaMemcpyAsync(hs, H.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+      if ((rs = sync_read(c)) != MGFR_OK) return rs;
+      r = std::sqrt(hs[0]);
+    }
     bool rose = false;
     while (r > target && outer < g.max_vcycles) {
       if ((rs = issue(c, 2, c->g_lin, bodylin)) != MGFR_OK) return rs;
@@ -687,7 +704,7 @@ mgfr_status mgfr_solve_density(mgfr_ctx* c, const double* delta, int N, double b
   c->u_prev_N = 0;  // valid again once solved
   c->launches += 2;
   MG_CK(c, cudaEventRecord(c->t0, c->s));
-  rs = mixed ? dense_solve_mixed(c, m, box, st) : dense_solve64(c, m, box, st);
+  rs = mixed ? dense_solve_mixed(c, m, box, st, u0 != nullptr) : dense_solve64(c, m, box, st);
   MG_CK(c, cudaEventRecord(c->t1, c->s));
   if (rs == MGFR_OK || rs == MGFR_E_NOCONVERGE) {
     f64::force(L0, m, fr_out, acc_out, c->s);

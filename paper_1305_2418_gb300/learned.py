@@ -88,5 +88,6 @@ def evaluate(solver: "mgfr.Solver", fields, box: float):
         rows.append({"fr0": fr0, "zero_cycles": z_cyc, "learned_cycles": l_cyc,
                      "zero_ms": z_ms, "learned_ms": l_ms + p_ms, "predict_ms": p_ms,
                      "start_rms_err": float(torch.sqrt(torch.mean((u0 - z_out["u"]) ** 2))),
+                     "zero_rms_err": float(torch.sqrt(torch.mean(z_out["u"] ** 2))),
                      "max_rel_diff_fr": rel})
     return rows
