@@ -363,13 +363,16 @@ mgfr_status mgfr_batch_autotune(mgfr_ctx* ctx, int nsolves, const mgfr_batch_ite
  * (16/32/64/128 channels, 3^3 kernels, circular padding, BF16 weights and
  * activations, FP32 accumulation) maps per-voxel features (ln(1+delta),
  * log10|fR0| + 5, 1, and the local screening value -(n+1) ln(1 + Om delta/Rt)
- * at a = 1) to u; the multigrid then drives the residual to the same
- * tolerance from that start (pass it as u_init).  Training and inference run
- * on this library's own tensor-core kernels.  D (box cells per side) must be
+ * at a = 1, see mgfr_unet_params) to u; the multigrid then drives the
+ * residual to the same tolerance from that start (pass it as u_init or use
+ * MGFR_START_LEARNED).  Training and inference run on this library's own
+ * tensor-core kernels (tcgen05 for the forward and input-gradient
+ * convolutions, mma.sync for the weight gradient).  D (box cells per side) must be
  * a power of two in [32, 512]; the network applies at the cell size it was
  * trained at.
  */
-/* (Re)create the network with He-normal weights from `seed`. */
+/* (Re)create the network: He-normal convolution weights from `seed`, zero
+ * biases and a zero head (the first prediction is u = 0). */
 mgfr_status mgfr_unet_init(mgfr_ctx* ctx, unsigned long long seed);
 /* One Adam step (learning rate lr) on B samples of D^3: delta_dev [B][D^3],
  * fr0_host [B] (|fR0| per sample, host), u_target_dev [B][D^3]; *loss_out =
@@ -384,9 +387,9 @@ mgfr_status mgfr_unet_predict(mgfr_ctx* ctx, int D, const double* delta_dev, dou
 /* Copy the FP32 master parameters to (set = 0) or from (set = 1) host memory;
  * *count receives their number (host may be NULL to query it).
  * Network and parameter layout: the input is 16 channels per voxel
- * [ln(1 + delta), log10|fR0| + 5, 1, u_scr, 0 x 12] with the local screening
- * value u_scr = -(n+1) ln(1 + Om delta / Rt) at a = 1 (clamped to [-20, 5];
- * logarithm arguments floored at 1e-3 and 1e-6).  Encoder levels 0..2:
+ * [ln(1 + delta), log10|fR0| + 5, 1, asinh(u_scr / 0.01) / 5, 0 x 12] with
+ * the local screening value u_scr = -(n+1) ln(1 + Om delta / Rt) at a = 1
+ * (clamped to [-20, 5]; logarithm arguments floored at 1e-3 and 1e-6).  Encoder levels 0..2:
  * e_l = relu(conv(relu(conv(p_l)))) with 16/32/64 channels, p_0 = input,
  * p_{l+1} = 2^3 average of e_l; bottom: the same with 128 channels on p_3;
  * decoder levels 2..0: d_l = relu(conv(relu(conv([up(d_{l+1}), e_l])))) with

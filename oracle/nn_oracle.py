@@ -10,10 +10,10 @@ channel concatenation, the 1x1x1 head, the loss (mean squared error in
 v = asinh(u / 0.01)) and one Adam step (Kingma & Ba, bias-corrected).
 
 Network (the library's documented learned-start U-Net; not in the paper):
-  features x0 = [ln(1 + delta), log10|fR0| + 5, 1, u_scr, 0 x 12] with the
-  local screening value u_scr = -(n+1) ln(1 + Om delta / Rt) at a = 1
-  (clamped to [-20, 5]; the arguments of both logarithms floored at 1e-3
-  and 1e-6);
+  features x0 = [ln(1 + delta), log10|fR0| + 5, 1, asinh(u_scr / 0.01) / 5,
+  0 x 12] with the local screening value u_scr = -(n+1) ln(1 + Om delta /
+  Rt) at a = 1 (clamped to [-20, 5]; the arguments of both logarithms
+  floored at 1e-3 and 1e-6);
   encoder e_l = relu(conv(relu(conv(p_l)))) with 16/32/64 channels on
   levels 0..2, p_0 = x0, p_{l+1} = avgpool(e_l);
   bottom b = relu(conv(relu(conv(p_3)))) with 128 channels;
@@ -126,7 +126,8 @@ def features(delta, fr0_abs, omega_m=0.3, n=1):
     x[..., 0] = np.log(np.maximum(1.0 + delta, 1e-3))
     x[..., 1] = np.log10(fr0_abs) + 5.0
     x[..., 2] = 1.0
-    x[..., 3] = np.clip(-(n + 1) * np.log(np.maximum(1.0 + omega_m * delta / Rt, 1e-6)), -20.0, 5.0)
+    u_scr = np.clip(-(n + 1) * np.log(np.maximum(1.0 + omega_m * delta / Rt, 1e-6)), -20.0, 5.0)
+    x[..., 3] = np.arcsinh(u_scr / U_SCALE) / 5.0
     return x
 
 

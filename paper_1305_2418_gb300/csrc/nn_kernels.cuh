@@ -31,3 +31,29 @@ void nn_conv_dgrad(TView g, int Cout, const __nv_bfloat16* W, FView gx, int Cin,
 void nn_conv_wgrad(TView x, int Cin, TView g, int Cout, float* dW, float* db, float* partials,
                    int B, int lgD, cudaStream_t s);
 long long nn_wgrad_scratch(int Cin, int Cout);
+
+// ---- tensor-core (tcgen05) forward and input-gradient convolutions (nn_tc.cu)
+struct TcArgs {
+  const __nv_bfloat16* x;  // A rows: x (forward) or g (input gradient), view
+  int ldx, offx;
+  const __nv_bfloat16* Wp;  // packed weights (nn_tc_pack)
+  const float* bias;        // forward, nullable
+  int relu;
+  __nv_bfloat16* y;  // forward output view
+  int ldy, offy;
+  float* gx;  // input-gradient output view
+  int ldg, offg, accumulate;
+  int lgD;
+  long long Mtot;  // voxels (B D^3)
+  int* err;        // set to 1 if a bounded wait in the kernel gave up
+};
+// whether the (K, N) pair (forward: Cin, Cout; gradient: Cout, Cin) is built
+bool nn_tc_supported(int K, int N);
+// elements of a packed weight tensor (27 Cin Cout)
+long long nn_tc_packed_size(int Cin, int Cout);
+// W [27][Cin][Cout] BF16 -> the per-tap K-major tiles of the forward
+// (dgrad = 0) or input-gradient (dgrad = 1) convolution
+void nn_tc_pack(const __nv_bfloat16* W, int Cin, int Cout, int dgrad, __nv_bfloat16* Wp,
+                cudaStream_t s);
+// launch; false if (K, N) is not built
+bool nn_tc_conv(const TcArgs& a, int K, int N, bool dgrad, cudaStream_t s);

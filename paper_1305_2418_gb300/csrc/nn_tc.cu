@@ -1,0 +1,374 @@
+// nn_tc.cu -- the network's 3^3 convolutions (forward and input gradient) on
+// the fifth-generation tensor cores: tcgen05.mma with the FP32 accumulator in
+// tensor memory (TMEM), BF16 operands in shared memory.
+//
+// Implicit GEMM per CTA (128 threads): rows = an M tile of 128 consecutive
+// voxels, columns = all N output channels (N <= 256), reduction = 27 taps x
+// the K input channels.  Per tap:
+//   A (128 x K): each row the channel vector of the row voxel's neighbour at
+//     the tap offset (periodic), copied by cp.async in 16-byte chunks;
+//   B (N x K): the tap's weight slice, packed in advance in the shared-memory
+//     layout and brought in by one bulk asynchronous copy (cp.async.bulk,
+//     completion counted on an mbarrier).
+// Both tiles use the canonical K-major layout without swizzle: core matrices
+// of 8 rows x 16 bytes; for each 8-channel chunk the rows are contiguous (so
+// the 8-row groups are 128 B apart: SBO), and the chunks follow each other one
+// tile-height apart (LBO).  Thread 0 issues the tap's MMAs (K = 16 each) and
+// commits them to the stage's mbarrier; two stages overlap the copies of tap
+// t+1 with the MMAs of tap t.  The epilogue reads the accumulator with
+// tcgen05.ld (warp w its 32 TMEM lanes = rows 32w..32w+31).
+//
+// Forward: y[m][co] = sum_{tap,ci} x[m + d_tap][ci] W[tap][ci][co] (+bias,
+// ReLU), stored BF16.  Input gradient: gx[m][ci] = sum_{tap,co}
+// g[m - d_tap][co] W[tap][ci][co], stored (or added) FP32.
+//
+// Every wait on an mbarrier is bounded; a wait that runs out sets *err and the
+// CTA leaves through the normal exit (TMEM freed).
+#include <cstdint>
+
+#include "nn_kernels.cuh"
+
+namespace {
+
+constexpr int TC_THREADS = 128;
+constexpr int TC_M = 128;
+constexpr long long kSpin = 1LL << 22;  // try_wait rounds before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for the completion of the phase with this parity
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  for (long long i = 0; i < kSpin; ++i)
+    if (mbar_try(bar, parity)) return true;
+  atomicExch(err, 1);
+  return false;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  const int n = valid ? 16 : 0;  // 0: fill with zeros
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// one bulk copy global -> shared, its bytes counted on bar
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// canonical K-major shared-memory descriptor, no swizzle (version 1)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor: BF16 x BF16 -> FP32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// neighbour voxel of m at offset (dx,dy,dz), periodic in each sample
+__device__ __forceinline__ long long tc_nbr(long long m, int lgD, int dx, int dy, int dz) {
+  const int D = 1 << lgD, M = D - 1;
+  const long long per = 1LL << (3 * lgD);
+  const long long b = m >> (3 * lgD), r = m & (per - 1);
+  const int i = (int)(r >> (2 * lgD)), j = (int)((r >> lgD) & M), k = (int)(r & M);
+  return b * per + ((((long long)((i + dx) & M) << lgD) + ((j + dy) & M)) << lgD) + ((k + dz) & M);
+}
+
+// KC: channels of an A row (the reduction per tap); NC: output columns.
+// DGRAD: the input-gradient form (mirrored tap, FP32 output, optional add).
+template <int KC, int NC, bool DGRAD>
+__global__ void __launch_bounds__(TC_THREADS) k_conv_tc(
+    const __nv_bfloat16* __restrict__ x, int ldx, int offx, const __nv_bfloat16* __restrict__ Wp,
+    const float* __restrict__ bias, int relu, __nv_bfloat16* __restrict__ y, int ldy, int offy,
+    float* __restrict__ gx, int ldg, int offg, int accumulate, int lgD, long long Mtot,
+    int tmem_cols, int* __restrict__ err) {
+  constexpr int A_BYTES = TC_M * KC * 2, B_BYTES = NC * KC * 2;
+  constexpr uint32_t A_LBO = TC_M * 16, B_LBO = NC * 16, SBO = 128;
+  constexpr uint32_t IDESC = idesc_bf16(TC_M, NC);
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* As = smem;                        // [2][A_BYTES]
+  unsigned char* Bs = smem + 2 * A_BYTES;          // [2][B_BYTES]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Bs + 2 * B_BYTES);  // full[2], done[2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const long long m0 = (long long)blockIdx.x * TC_M;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int q = 0; q < 4; ++q) mbar_init(bars + q, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = *tslot;
+  bool ok = true;
+
+  // A copies of tap t into stage s (every thread a share of the 16-byte chunks)
+  auto load_a = [&](int t, int s) {
+    const int dx = t / 9 - 1, dy = (t / 3) % 3 - 1, dz = t % 3 - 1;
+    const int sg = DGRAD ? -1 : 1;
+    unsigned char* A = As + s * A_BYTES;
+    constexpr int CH = KC / 8;  // 16-byte chunks per row
+    for (int e = tid; e < TC_M * CH; e += TC_THREADS) {
+      const int r = e / CH, c = e - r * CH;
+      const long long m = m0 + r;
+      const bool v = m < Mtot;
+      const long long src = v ? tc_nbr(m, lgD, sg * dx, sg * dy, sg * dz) : 0;
+      cp_async16(A + c * (TC_M * 16) + r * 16, x + src * ldx + offx + 8 * c, v);
+    }
+    cp_async_commit();
+  };
+
+  // thread 0's account of what is in flight: bulk copies issued per stage
+  // (their completions are waited in order) and the stage of the last commit
+  int issued[2] = {0, 0}, landed[2] = {0, 0}, commits[2] = {0, 0}, last_commit = -1;
+  auto issue_b = [&](int t, int st) {
+    bulk_load(Bs + st * B_BYTES, Wp + (long long)t * NC * KC, B_BYTES, bars + st);
+    ++issued[st];
+  };
+  load_a(0, 0);
+  if (tid == 0) issue_b(0, 0);
+  for (int t = 0; t < 27; ++t) {
+    const int s = t & 1;
+    if (t + 1 < 27) {
+      const int s1 = (t + 1) & 1;
+      // stage s1 was last read by the MMAs of tap t-1
+      if (t >= 1 && !mbar_wait(bars + 2 + s1, ((t - 1) >> 1) & 1, err)) ok = false;
+      ok = __syncthreads_and(ok);
+      if (!ok) break;
+      load_a(t + 1, s1);
+      if (tid == 0) issue_b(t + 1, s1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    // this thread's A copies of tap t are done; make them visible to the
+    // tensor cores (async proxy) and to the issuing thread
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      if (!mbar_wait(bars + s, (t >> 1) & 1, err)) {
+        ok = false;
+      } else {
+        ++landed[s];
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(As + s * A_BYTES), b0 = smem_u32(Bs + s * B_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < KC / 16; ++kk) {
+          // K step of 16 = two 8-channel chunks
+          const uint64_t ad = sdesc(a0 + kk * 2 * A_LBO, A_LBO, SBO);
+          const uint64_t bd = sdesc(b0 + kk * 2 * B_LBO, B_LBO, SBO);
+          mma_bf16(tbase, ad, bd, IDESC, (t > 0 || kk > 0) ? 1u : 0u);
+        }
+        mma_commit(bars + 2 + s);
+        ++commits[s];
+        last_commit = s;
+      }
+    }
+  }
+  // the last tap's MMAs (and so all earlier ones) completed
+  ok = __syncthreads_and(ok);
+  if (ok && !mbar_wait(bars + 2 + (26 & 1), (26 >> 1) & 1, err)) ok = false;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  ok = __syncthreads_and(ok);
+  if (ok) {
+    const int row = warp * 32 + (tid & 31);
+    const long long m = m0 + row;
+    const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int n0 = 0; n0 < NC; n0 += 16) {
+      float v[16];
+      tmem_ld16(lane_addr + n0, v);
+      if (m < Mtot) {
+        if (!DGRAD) {
+          __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            float a = v[i] + (bias ? bias[n0 + i] : 0.f);
+            if (relu) a = fmaxf(a, 0.f);
+            o[i] = __float2bfloat16(a);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(y + m * ldy + offy + n0);
+          dst[0] = reinterpret_cast<const uint4*>(o)[0];
+          dst[1] = reinterpret_cast<const uint4*>(o)[1];
+        } else {
+          float* q = gx + m * ldg + offg + n0;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) q[i] = accumulate ? q[i] + v[i] : v[i];
+        }
+      }
+    }
+  } else {
+    // a wait ran out: let the copies and MMAs still in flight finish (each
+    // wait bounded) before the shared memory and TMEM are given up
+    cp_async_wait<0>();
+    if (tid == 0) {
+      for (int q = 0; q < 2; ++q)
+        while (landed[q] < issued[q]) {
+          if (!mbar_wait(bars + q, (uint32_t)(landed[q] & 1), err)) break;
+          ++landed[q];
+        }
+      if (last_commit >= 0)
+        mbar_wait(bars + 2 + last_commit, (uint32_t)((commits[last_commit] - 1) & 1), err);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                 "r"(tmem_cols)
+                 : "memory");
+}
+
+// Packed weight slices.  Forward (N = Cout, K = Cin):
+//   Wp[t][c][n][k8] = W[t][8c + k8][n]
+// Input gradient (N = Cin, K = Cout):
+//   Wp[t][c][n][k8] = W[t][n][8c + k8]
+// i.e. per tap the K-major N x K tile, 8-channel chunks of K one after the
+// other, the N rows of a chunk contiguous (the shared-memory layout).
+__global__ void k_pack_tc(const __nv_bfloat16* __restrict__ W, int Cin, int Cout, int dgrad,
+                          __nv_bfloat16* __restrict__ Wp) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long per = (long long)Cin * Cout;
+  if (e >= 27 * per) return;
+  const int t = (int)(e / per);
+  const long long r = e - t * per;
+  const int N = dgrad ? Cin : Cout;
+  const int k8 = (int)(r & 7), n = (int)((r >> 3) % N), c = (int)((r >> 3) / N);
+  const int kidx = 8 * c + k8;
+  const int ci = dgrad ? n : kidx, co = dgrad ? kidx : n;
+  Wp[e] = W[((long long)t * Cin + ci) * Cout + co];
+}
+
+template <int KC, int NC, bool DG>
+void launch_tc(const TcArgs& a, cudaStream_t s) {
+  constexpr int A_BYTES = TC_M * KC * 2, B_BYTES = NC * KC * 2;
+  const int cols = NC <= 32 ? 32 : (NC <= 64 ? 64 : (NC <= 128 ? 128 : 256));
+  const size_t need = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 4 * 8 + 16;
+  // at most 512 / cols CTAs per SM may hold TMEM at once: pad the shared
+  // memory so that no more are resident (tcgen05.alloc would wait)
+  // (each CTA also holds 1 KB of reserved shared memory)
+  const int k = 512 / cols;
+  const size_t cap = 233472 / (k + 1) - 1024 + 16;
+  const size_t smem = need > cap ? need : cap;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_conv_tc<KC, NC, DG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    attr = true;
+  }
+  const unsigned grid = (unsigned)((a.Mtot + TC_M - 1) / TC_M);
+  k_conv_tc<KC, NC, DG><<<grid, TC_THREADS, smem, s>>>(
+      a.x, a.ldx, a.offx, a.Wp, a.bias, a.relu, a.y, a.ldy, a.offy, a.gx, a.ldg, a.offg,
+      a.accumulate, a.lgD, a.Mtot, cols, a.err);
+}
+
+}  // namespace
+
+long long nn_tc_packed_size(int Cin, int Cout) { return 27LL * Cin * Cout; }
+
+void nn_tc_pack(const __nv_bfloat16* W, int Cin, int Cout, int dgrad, __nv_bfloat16* Wp,
+                cudaStream_t s) {
+  const long long n = 27LL * Cin * Cout;
+  k_pack_tc<<<nblocks(n, 256), 256, 0, s>>>(W, Cin, Cout, dgrad, Wp);
+}
+
+// (K, N) pairs of the network's convolutions: forward (Cin, Cout) and input
+// gradient (Cout, Cin)
+bool nn_tc_supported(int K, int N) {
+  static const int kn[][2] = {{16, 16},  {16, 32},  {32, 32},  {32, 64},  {64, 64},  {64, 128},
+                              {128, 128}, {192, 64}, {96, 32},  {48, 16},  {32, 16},  {64, 32},
+                              {128, 64}, {64, 192}, {32, 96},  {16, 48}};
+  for (auto& p : kn)
+    if (p[0] == K && p[1] == N) return true;
+  return false;
+}
+
+bool nn_tc_conv(const TcArgs& a, int K, int N, bool dgrad, cudaStream_t s) {
+#define TC_CASE(KK, NN)                                              \
+  if (K == KK && N == NN) {                                          \
+    if (dgrad) launch_tc<KK, NN, true>(a, s); else launch_tc<KK, NN, false>(a, s); \
+    return true;                                                     \
+  }
+  TC_CASE(16, 16) TC_CASE(16, 32) TC_CASE(32, 32) TC_CASE(32, 64) TC_CASE(64, 64)
+  TC_CASE(64, 128) TC_CASE(128, 128) TC_CASE(192, 64) TC_CASE(96, 32) TC_CASE(48, 16)
+  TC_CASE(32, 16) TC_CASE(64, 32) TC_CASE(128, 64) TC_CASE(64, 192) TC_CASE(32, 96)
+  TC_CASE(16, 48)
+#undef TC_CASE
+  return false;
+}

@@ -42,8 +42,11 @@ const ConvSpec kConvs[14] = {
 };
 
 // features: ln(1+delta), log10|fR0| + 5, 1, and the local screening value
-// -(n+1) ln(1 + Om a^-3 delta / Rt) (the solution where delta is uniform on
-// scales beyond the Compton length), clamped to [-20, 5].
+// u_scr = -(n+1) ln(1 + Om a^-3 delta / Rt) (the solution where delta is
+// uniform on scales beyond the Compton length), clamped to [-20, 5], in the
+// output's own variable: asinh(u_scr / 0.01) / 5 (of order one).
+constexpr double U_SCALE_F = 0.01;  // the output variable's scale (U_SCALE below)
+
 __global__ void k_features(const double* __restrict__ delta, const double* __restrict__ fr0s,
                            long long per, long long M, __nv_bfloat16* __restrict__ x,
                            double scr, double np1, double dscale) {
@@ -55,8 +58,8 @@ __global__ void k_features(const double* __restrict__ delta, const double* __res
   o[0] = __float2bfloat16((float)log(fmax(1.0 + d, 1e-3)));
   o[1] = __float2bfloat16((float)(log10(fr0) + 5.0));
   o[2] = __float2bfloat16(1.f);
-  const double ul = -np1 * log(fmax(1.0 + scr * d, 1e-6));
-  o[3] = __float2bfloat16((float)fmin(fmax(ul, -20.0), 5.0));
+  const double ul = fmin(fmax(-np1 * log(fmax(1.0 + scr * d, 1e-6)), -20.0), 5.0);
+  o[3] = __float2bfloat16((float)(asinh(ul / U_SCALE_F) / 5.0));
   for (int c = 4; c < 16; ++c) o[c] = __float2bfloat16(0.f);
 }
 
@@ -240,6 +243,10 @@ struct UNet {
   long long wbf_off[14], nwbf = 0;
   float *P = nullptr, *G = nullptr, *M1 = nullptr, *M2 = nullptr;  // device
   __nv_bfloat16* Wbf = nullptr;
+  // the BF16 weights packed for the tensor-core forward and input-gradient
+  // convolutions (same offsets as Wbf), and their kernels' error word
+  __nv_bfloat16 *Wtf = nullptr, *Wtd = nullptr;
+  int* tc_err = nullptr;
   long long step = 0;
   // activation buffers for one (B, lgD)
   int B = 0, lgD = 0;
@@ -263,7 +270,7 @@ void unet_free(mgfr_ctx* c) {
   UNet* U = (UNet*)c->unet;
   if (!U) return;
   unet_free_bufs(U);
-  void* ps[] = {U->P, U->G, U->M1, U->M2, U->Wbf};
+  void* ps[] = {U->P, U->G, U->M1, U->M2, U->Wbf, U->Wtf, U->Wtd, U->tc_err};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete U;
@@ -372,8 +379,25 @@ static void layer_views(UNet* U, LayerIO* L) {
 
 static void conv_fwd(mgfr_ctx* c, UNet* U, int i, const LayerIO& L) {
   const ConvSpec& s = kConvs[i];
-  nn_conv_fwd(L.x, s.cin, U->Wbf + U->wbf_off[i], U->P + U->boff[i], 1, L.y, s.cout, U->B, L.lgD,
-              c->s);
+  if (nn_tc_supported(s.cin, s.cout)) {
+    TcArgs a{};
+    a.x = L.x.p;
+    a.ldx = L.x.ld;
+    a.offx = L.x.off;
+    a.Wp = U->Wtf + U->wbf_off[i];
+    a.bias = U->P + U->boff[i];
+    a.relu = 1;
+    a.y = L.y.p;
+    a.ldy = L.y.ld;
+    a.offy = L.y.off;
+    a.lgD = L.lgD;
+    a.Mtot = (long long)U->B << (3 * L.lgD);
+    a.err = U->tc_err;
+    nn_tc_conv(a, s.cin, s.cout, false, c->s);
+  } else {
+    nn_conv_fwd(L.x, s.cin, U->Wbf + U->wbf_off[i], U->P + U->boff[i], 1, L.y, s.cout, U->B,
+                L.lgD, c->s);
+  }
   c->launches += 1;
 }
 
@@ -423,7 +447,25 @@ static void conv_bwd(mgfr_ctx* c, UNet* U, int i, const LayerIO& L, int acc_in) 
   const TView g = tv(U->Gpre, s.cout);
   nn_conv_wgrad(L.x, s.cin, g, s.cout, U->G + U->woff[i], U->G + U->boff[i], U->wpart, U->B, L.lgD,
                 c->s);
-  if (L.gx.p) nn_conv_dgrad(g, s.cout, U->Wbf + U->wbf_off[i], L.gx, s.cin, acc_in, U->B, L.lgD, c->s);
+  if (L.gx.p) {
+    if (nn_tc_supported(s.cout, s.cin)) {
+      TcArgs a{};
+      a.x = U->Gpre;
+      a.ldx = s.cout;
+      a.offx = 0;
+      a.Wp = U->Wtd + U->wbf_off[i];
+      a.gx = L.gx.p;
+      a.ldg = L.gx.ld;
+      a.offg = L.gx.off;
+      a.accumulate = acc_in;
+      a.lgD = L.lgD;
+      a.Mtot = M;
+      a.err = U->tc_err;
+      nn_tc_conv(a, s.cout, s.cin, true, c->s);
+    } else {
+      nn_conv_dgrad(g, s.cout, U->Wbf + U->wbf_off[i], L.gx, s.cin, acc_in, U->B, L.lgD, c->s);
+    }
+  }
   c->launches += 5;
 }
 
@@ -471,10 +513,24 @@ static void backward(mgfr_ctx* c, UNet* U) {
 
 static void refresh_bf16(mgfr_ctx* c, UNet* U) {
   for (int i = 0; i < 14; ++i) {
-    const long long n = 27LL * kConvs[i].cin * kConvs[i].cout;
+    const ConvSpec& s = kConvs[i];
+    const long long n = 27LL * s.cin * s.cout;
     k_to_bf16<<<nblocks(n, BS), BS, 0, c->s>>>(U->P + U->woff[i], U->Wbf + U->wbf_off[i], n);
-    c->launches += 1;
+    nn_tc_pack(U->Wbf + U->wbf_off[i], s.cin, s.cout, 0, U->Wtf + U->wbf_off[i], c->s);
+    nn_tc_pack(U->Wbf + U->wbf_off[i], s.cin, s.cout, 1, U->Wtd + U->wbf_off[i], c->s);
+    c->launches += 3;
   }
+}
+
+// the tensor-core kernels' error word (read after the stream has synchronised)
+static mgfr_status tc_check(mgfr_ctx* c, UNet* U) {
+  int e = 0;
+  MG_CK(c, cudaMemcpy(&e, U->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    MG_CK(c, cudaMemset(U->tc_err, 0, sizeof(int)));
+    return set_err(c, MGFR_E_TIMEOUT, "a bounded wait in a tensor-core convolution gave up");
+  }
+  return MGFR_OK;
 }
 
 static mgfr_status unet_make(mgfr_ctx* c, unsigned long long seed) {
@@ -499,6 +555,10 @@ static mgfr_status unet_make(mgfr_ctx* c, unsigned long long seed) {
   MG_CK(c, cudaMalloc(&U->M1, sizeof(float) * off));
   MG_CK(c, cudaMalloc(&U->M2, sizeof(float) * off));
   MG_CK(c, cudaMalloc(&U->Wbf, sizeof(__nv_bfloat16) * boff));
+  MG_CK(c, cudaMalloc(&U->Wtf, sizeof(__nv_bfloat16) * boff));
+  MG_CK(c, cudaMalloc(&U->Wtd, sizeof(__nv_bfloat16) * boff));
+  MG_CK(c, cudaMalloc(&U->tc_err, sizeof(int)));
+  MG_CK(c, cudaMemset(U->tc_err, 0, sizeof(int)));
   // He-normal initialisation from a seeded generator (host), zero biases
   std::vector<float> h((size_t)off, 0.f);
   std::mt19937_64 rng(seed);
@@ -506,8 +566,8 @@ static mgfr_status unet_make(mgfr_ctx* c, unsigned long long seed) {
     std::normal_distribution<float> nd(0.f, std::sqrt(2.f / (27.f * kConvs[i].cin)));
     for (long long q = 0; q < 27LL * kConvs[i].cin * kConvs[i].cout; ++q) h[U->woff[i] + q] = nd(rng);
   }
-  std::normal_distribution<float> nh(0.f, 0.25f);
-  for (int q = 0; q < 16; ++q) h[U->head_off + q] = nh(rng);
+  // the head starts at zero: the first prediction is u = 0 (the zero start),
+  // so early steps do not push the network into saturation
   MG_CK(c, cudaMemcpy(U->P, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice));
   MG_CK(c, cudaMemset(U->M1, 0, sizeof(float) * off));
   MG_CK(c, cudaMemset(U->M2, 0, sizeof(float) * off));
@@ -544,7 +604,7 @@ mgfr_status unet_predict_batch(mgfr_ctx* c, int B, int D, const double* x, doubl
   c->launches += 2;
   // fr0_host may be a caller's stack value: the copy must be done before return
   MG_CK(c, cudaStreamSynchronize(c->s));
-  return MGFR_OK;
+  return tc_check(c, U);
 }
 
 extern "C" {
@@ -586,6 +646,7 @@ mgfr_status mgfr_unet_train_step(mgfr_ctx* c, int B, int D, const double* delta_
   MG_CK(c, cudaMemcpyAsync(part.data(), U->lossp, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->s));
   MG_CK(c, cudaStreamSynchronize(c->s));
   MG_CK(c, cudaGetLastError());
+  if ((rs = tc_check(c, U)) != MGFR_OK) return rs;
   double s = 0.0;
   for (double v : part) s += v;
   if (loss_out) *loss_out = s / (double)M0;
@@ -709,6 +770,46 @@ mgfr_status mgfr_nn_conv3d(int op, int B, int D, int Cin, int Cout, const void* 
     return MGFR_E_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   const int lgD = lg_of(D);
+  const bool tc = (op == 0 && nn_tc_supported(Cin, Cout)) || (op == 1 && nn_tc_supported(Cout, Cin));
+  if (tc) {
+    // pack the weights for the tensor-core kernel (scratch of this call)
+    __nv_bfloat16* wp = nullptr;
+    int* err = nullptr;
+    if (cudaMalloc(&wp, sizeof(__nv_bfloat16) * (size_t)nn_tc_packed_size(Cin, Cout)) != cudaSuccess)
+      return MGFR_E_OOM;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+      cudaFree(wp);
+      return MGFR_E_OOM;
+    }
+    cudaMemsetAsync(err, 0, sizeof(int), s);
+    nn_tc_pack((const __nv_bfloat16*)w_bf16, Cin, Cout, op, wp, s);
+    TcArgs a{};
+    a.Wp = wp;
+    a.lgD = lgD;
+    a.Mtot = (long long)B << (3 * lgD);
+    a.err = err;
+    if (op == 0) {
+      a.x = (const __nv_bfloat16*)x_bf16;
+      a.ldx = Cin;
+      a.bias = bias;
+      a.relu = relu;
+      a.y = (__nv_bfloat16*)out;
+      a.ldy = Cout;
+    } else {
+      a.x = (const __nv_bfloat16*)g_bf16;
+      a.ldx = Cout;
+      a.gx = (float*)out;
+      a.ldg = Cin;
+    }
+    nn_tc_conv(a, op == 0 ? Cin : Cout, op == 0 ? Cout : Cin, op == 1, s);
+    int e = 0;
+    const bool okc = cudaStreamSynchronize(s) == cudaSuccess &&
+                     cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    cudaFree(wp);
+    cudaFree(err);
+    if (!okc || cudaGetLastError() != cudaSuccess) return MGFR_E_CUDA;
+    return e ? MGFR_E_TIMEOUT : MGFR_OK;
+  }
   if (op == 0) {
     nn_conv_fwd(TView{(__nv_bfloat16*)x_bf16, Cin, 0}, Cin, (const __nv_bfloat16*)w_bf16, bias,
                 relu, TView{(__nv_bfloat16*)out, Cout, 0}, Cout, B, lgD, s);
