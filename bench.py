@@ -392,6 +392,7 @@ def learned_extra(mgfr, learned, torch, dev, local):
                          "learned_ms_mean": float(np.mean([r["learned_ms"] for r in rows])),
                          "predict_ms_mean": float(np.mean([r["predict_ms"] for r in rows])),
                          "start_rms_err_mean": float(np.mean([r["start_rms_err"] for r in rows])),
+                         "zero_rms_err_mean": float(np.mean([r["zero_rms_err"] for r in rows])),
                          "max_rel_diff_fr": float(max(r["max_rel_diff_fr"] for r in rows)),
                          "fields": len(rows)},
             "net_path": net_path}

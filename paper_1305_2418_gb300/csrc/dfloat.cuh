@@ -257,7 +257,10 @@ static const dfl kDfExp2TabHost[32] = DF_EXP2_TABLE;
 #define DF_TAB(j) kDfExp2TabHost[j]
 #endif
 
-// e^x for a double-float x with |x| < 87 (the FP32 range of the result).
+// e^x for a double-float x with |x| < 87 (the FP32 range of the result), by
+// Tang's table-driven method (P. T. P. Tang, ACM TOMS 15 (1989) 144) with a
+// Cody-Waite split of the reduction constant (Cody & Waite, "Software Manual
+// for the Elementary Functions", 1980), both restated for float pairs:
 // x = n ln2/32 + r with n = round(32 x / ln2) and |r| <= ln2/64; e^r from its
 // Taylor series through r^7/7! (the omitted terms are below 5e-21 relative);
 // e^x = 2^(n div 32) 2^((n mod 32)/32) e^r.  ln2/32 is split as c1 + c2 + c3 + c4:

