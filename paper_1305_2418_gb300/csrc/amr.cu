@@ -395,7 +395,12 @@ __device__ __forceinline__ void split_q(const TreeView& T, int l, long long c, c
 // sums weight x force).  Returns whether the cube split over finer cells.
 // ri (deposit with a record): the record's 8 slots, which the caller stores
 // once its warp has reconverged (whole-warp, coalesced stores).
-template <bool GATHER, class W>
+// MODE 0: every piece.  MODE 1: only the corners that are not refined (the
+// split ones are left to a MODE 2 pass over the listed particles, so that the
+// warps of the first pass do not wait on the few lanes that split).  MODE 2:
+// only the pieces of refined corners.
+constexpr int kVisitAll = 0, kVisitUnsplit = 1, kVisitSplit = 2;
+template <bool GATHER, class W, int MODE = kVisitAll>
 __device__ bool visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, const GatherPtrs& G,
                                W* out, unsigned long long* err, unsigned* ri = nullptr) {
   const bool rec = !GATHER && D.rec_idx;
@@ -454,13 +459,16 @@ __device__ bool visit_particle(const TreeView& T, const P3& t, LevelPtrs& D, con
     }
     const bool refined = lev == lam && lam + 1 < T.nlev && T.son[lam][cq] >= 0;
     if (!refined) {
-      const W w = Lxy[(bits[0] << 1) | bits[1]] * Lw[2][bits[2]];
-      touch<GATHER, W>(lev, cq, w, D, G, out);
-      if (rec) ri[q] = ((unsigned)lev << D.rb) | (unsigned)cq;
+      if (MODE != kVisitSplit) {
+        const W w = Lxy[(bits[0] << 1) | bits[1]] * Lw[2][bits[2]];
+        touch<GATHER, W>(lev, cq, w, D, G, out);
+        if (rec) ri[q] = ((unsigned)lev << D.rb) | (unsigned)cq;
+      }
       continue;
     }
     split = true;
     if (rec) ri[q] = kRecSkip;
+    if (MODE == kVisitUnsplit) continue;
     long long lo[3], hi[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -496,7 +504,10 @@ __global__ void __launch_bounds__(256, 4) k_deposit(const double* __restrict__ p
   if (p < Np) {
     const P3 t = particle_t(pos, p, inv, N0);
     GatherPtrs G{};
-    split = visit_particle<false, double>(T, t, D, G, nullptr, err, ri);
+    if (D.rec_idx)  // the split pieces are left to k_deposit_split
+      split = visit_particle<false, double, kVisitUnsplit>(T, t, D, G, nullptr, err, ri);
+    else
+      split = visit_particle<false, double>(T, t, D, G, nullptr, err, ri);
   }
   if (!D.rec_idx) return;  // uniform over the launch
   // whole blocks reach here (no early exit above)
@@ -520,6 +531,25 @@ __global__ void __launch_bounds__(256, 4) k_deposit(const double* __restrict__ p
   }
   __syncthreads();
   if (split) split_list[bbase + woff[w] + __popc(b & ((1u << lane) - 1u))] = (int)p;
+}
+
+// The split pieces of the particles listed by k_deposit (chunk q's list at
+// split_list + q per, n_split[q] entries): a grid-stride loop over the eight
+// lists, whose lengths are read on the device.
+__global__ void __launch_bounds__(256, 4) k_deposit_split(
+    const double* __restrict__ pos, double inv, double N0, TreeView T, LevelPtrs D,
+    unsigned long long* err, const int* __restrict__ split_list,
+    const unsigned long long* __restrict__ n_split, long long per) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int q = 0; q < 8; ++q) {
+    const long long n = (long long)n_split[q];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += stride) {
+      const long long p = split_list[q * per + t];
+      const P3 tp = particle_t(pos, p, inv, N0);
+      GatherPtrs G{};
+      visit_particle<false, double, kVisitSplit>(T, tp, D, G, nullptr, err);
+    }
+  }
 }
 
 __global__ void k_gather(const double* __restrict__ pos, long long Np, double inv, double N0,
@@ -1059,6 +1089,17 @@ static mgfr_status deposit(mgfr_ctx* c, AmrWork* A, const double* pos, bool reco
                                                  (unsigned long long*)A->d_split,
                                                  (unsigned)(per / 256));
   c->launches += 1;
+  if (record) {
+    LevelPtrs Ds = D;  // the split pieces add masses only (no record)
+    Ds.rec_idx = nullptr;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    k_deposit_split<<<std::max(nsm, 1) * 8, BS, 0, c->s>>>(pos, inv, N0d, T, Ds,
+                                                 (unsigned long long*)(A->d_small + 1),
+                                                 A->split_list,
+                                                 (const unsigned long long*)A->d_split, per);
+    c->launches += 1;
+  }
   for (int l = A->nlev - 1; l >= 1; --l) {
     k_mass_up<<<nblocks(A->L[l].n_oct, BS), BS, 0, c->s>>>(A->L[l].mass, A->L[l].n_oct,
                                                            A->L[l].pcell, A->L[l - 1].mass);

@@ -707,23 +707,31 @@ __global__ void __launch_bounds__(BS, 6) k_oct_sweep32(
     long long no, MT<float> m, float ih2, float cap) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const long long o = olist ? olist[t] : t;
+  const int o = olist ? olist[t] : (int)t;
   constexpr int CC[2][4] = {{0, 3, 5, 6}, {1, 2, 4, 7}};
   constexpr int OC = 1 - COL;
-  const Oct8 U = ld8(u, o, no);
-  const float4 R4 = ldc(rf, o, no, COL);
+  // 32-bit oct indices into float4 planes (n_oct < 2^31 / 6, checked on the host)
+  const float4* __restrict__ u4 = reinterpret_cast<const float4*>(u);
+  const float4* __restrict__ uo = u4 + OC * no;  // the other colour's plane
+  const float4* __restrict__ e4 = reinterpret_cast<const float4*>(e);
+  const float4* __restrict__ g4 = reinterpret_cast<const float4*>(gh);
+  const float4 a0 = u4[o], a1 = u4[no + o];
+  Oct8 U;
+  U.v[0] = a0.x; U.v[3] = a0.y; U.v[5] = a0.z; U.v[6] = a0.w;
+  U.v[1] = a1.x; U.v[2] = a1.y; U.v[4] = a1.z; U.v[7] = a1.w;
+  const float4 R4 = reinterpret_cast<const float4*>(rf)[COL * no + o];
   Oct8 EE;
 #pragma unroll
   for (int i = 0; i < 8; ++i) EE.v[i] = __expf(U.v[i]);
   // LIN: corrections of the other colour (the in-oct neighbours)
-  const float4 XO = LIN ? ldc(e, o, no, OC) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 XO = LIN ? e4[OC * no + o] : make_float4(0.f, 0.f, 0.f, 0.f);
   bool on[4];
   float s1[4], s2[4], s3[4];  // LIN: (sum off*e, diag sum, -); NL: (sum b du, sum du, sum b)
   // the oct's eight relax flags in one 8-byte load
   const unsigned long long a8 = act ? __ldg(reinterpret_cast<const unsigned long long*>(act) + o)
                                     : ~0ULL;
   // the six face neighbours as three 8-byte loads (6 o ints: 8-byte aligned)
-  const int2* nb2 = reinterpret_cast<const int2*>(nbr + 6 * o);
+  const int2* nb2 = reinterpret_cast<const int2*>(nbr) + 3 * o;
   const int2 n01 = __ldg(nb2), n23 = __ldg(nb2 + 1), n45 = __ldg(nb2 + 2);
   const int nbv[6] = {n01.x, n01.y, n23.x, n23.y, n45.x, n45.y};
 #pragma unroll
@@ -748,31 +756,28 @@ __global__ void __launch_bounds__(BS, 6) k_oct_sweep32(
       }
     }
   }
-  // faces
+  // faces: the neighbouring oct's other colour, or the ghost face
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     const int a = d >> 1, plus = d & 1;
     const int nb = nbv[d];
-    float4 NU, NX;
-    if (nb >= 0) {
-      NU = ldc(u, nb, no, OC);
-      if (LIN) NX = ldc(e, nb, no, OC);
+    const bool has = nb >= 0;
+    float4 NU, NX = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!LIN) {
+      NU = has ? uo[nb] : g4[-nb - 1];  // one load, no divergent branch
+    } else if (has) {
+      NU = uo[nb];
+      NX = e4[OC * no + nb];
     } else {
-      NU = *reinterpret_cast<const float4*>(gh + 4LL * (-nb - 1));
+      NU = g4[-nb - 1];
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int ch = CC[COL][q];
       if (((ch >> (2 - a)) & 1) != plus) continue;  // not on this face
-      float un, xn;
-      if (nb >= 0) {
-        const int cn = ch ^ (1 << (2 - a));
-        un = f4(NU, cn >> 1);
-        xn = LIN ? f4(NX, cn >> 1) : 0.f;
-      } else {
-        un = f4(NU, face_q(ch, a));
-        xn = 0.f;
-      }
+      const int cn = ch ^ (1 << (2 - a));
+      const float un = has ? f4(NU, cn >> 1) : f4(NU, face_q(ch, a));
+      const float xn = (LIN && has) ? f4(NX, cn >> 1) : 0.f;
       const float En = __expf(un);
       const float du = un - U.v[ch];
       if (LIN) {
@@ -787,7 +792,7 @@ __global__ void __launch_bounds__(BS, 6) k_oct_sweep32(
     }
   }
   // the colour-COL vector: new values on relaxed cells, the old ones elsewhere
-  float4 out = LIN ? (act ? ldc(e, o, no, COL) : make_float4(0.f, 0.f, 0.f, 0.f))
+  float4 out = LIN ? (act ? e4[COL * no + o] : make_float4(0.f, 0.f, 0.f, 0.f))
                    : make_float4(U.v[CC[COL][0]], U.v[CC[COL][1]], U.v[CC[COL][2]],
                                  U.v[CC[COL][3]]);
   float res[4] = {out.x, out.y, out.z, out.w};
@@ -807,7 +812,8 @@ __global__ void __launch_bounds__(BS, 6) k_oct_sweep32(
       res[q] = U.v[ch] - step;
     }
   }
-  stc(LIN ? e : u, o, no, COL, make_float4(res[0], res[1], res[2], res[3]));
+  reinterpret_cast<float4*>(LIN ? e : u)[COL * no + o] =
+      make_float4(res[0], res[1], res[2], res[3]);
 }
 
 // ---- thread-per-oct FP32 operator sums ------------------------------------

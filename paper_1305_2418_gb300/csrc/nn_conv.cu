@@ -243,6 +243,13 @@ void nn_conv_dgrad(TView g, int Cout, const __nv_bfloat16* W, FView gx, int Cin,
 #undef LAUNCH_D
 }
 
+void nn_wgrad_finish(const float* partials, int S, int Cin, int Cout, float* dW, TView g,
+                     float* db, long long Mtot, cudaStream_t s) {
+  const long long n = 27LL * Cin * Cout;
+  k_wgrad_reduce<<<nblocks(n, 256), 256, 0, s>>>(partials, S, n, dW);
+  if (db) k_bias_grad<<<Cout, 256, 0, s>>>(g.p, g.ld, g.off, Mtot, db);
+}
+
 long long nn_wgrad_scratch(int Cin, int Cout) {
   const int S = std::max(1, WG_S_TARGET / (27 * (Cin / 16)));
   return (long long)S * 27 * Cin * Cout;
@@ -265,7 +272,5 @@ void nn_conv_wgrad(TView x, int Cin, TView g, int Cout, float* dW, float* db, fl
     default: LAUNCH_W(16); break;
   }
 #undef LAUNCH_W
-  const long long n = 27LL * Cin * Cout;
-  k_wgrad_reduce<<<nblocks(n, 256), 256, 0, s>>>(partials, S, n, dW);
-  if (db) k_bias_grad<<<Cout, 256, 0, s>>>(g.p, g.ld, g.off, Mtot, db);
+  nn_wgrad_finish(partials, S, Cin, Cout, dW, g, db, Mtot, s);
 }

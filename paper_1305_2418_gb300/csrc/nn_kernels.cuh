@@ -31,6 +31,9 @@ void nn_conv_dgrad(TView g, int Cout, const __nv_bfloat16* W, FView gx, int Cin,
 void nn_conv_wgrad(TView x, int Cin, TView g, int Cout, float* dW, float* db, float* partials,
                    int B, int lgD, cudaStream_t s);
 long long nn_wgrad_scratch(int Cin, int Cout);
+// dW[i] = sum over the S slices of partials[s][i] (in order), and db
+void nn_wgrad_finish(const float* partials, int S, int Cin, int Cout, float* dW, TView g,
+                     float* db, long long Mtot, cudaStream_t s);
 
 // ---- tensor-core (tcgen05) forward and input-gradient convolutions (nn_tc.cu)
 struct TcArgs {
@@ -57,3 +60,9 @@ void nn_tc_pack(const __nv_bfloat16* W, int Cin, int Cout, int dgrad, __nv_bfloa
                 cudaStream_t s);
 // launch; false if (K, N) is not built
 bool nn_tc_conv(const TcArgs& a, int K, int N, bool dgrad, cudaStream_t s);
+// weight gradient on tcgen05 (same result and arguments as nn_conv_wgrad;
+// partials: nn_tc_wgrad_scratch floats); false if (Cin, Cout) is not built
+bool nn_tc_wgrad_supported(int Cin, int Cout);
+long long nn_tc_wgrad_scratch(int Cin, int Cout);
+bool nn_tc_wgrad(TView x, int Cin, TView g, int Cout, float* dW, float* db, float* partials,
+                 int B, int lgD, int* err, cudaStream_t s);

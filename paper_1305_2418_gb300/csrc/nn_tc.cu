@@ -22,8 +22,17 @@
 // ReLU), stored BF16.  Input gradient: gx[m][ci] = sum_{tap,co}
 // g[m - d_tap][co] W[tap][ci][co], stored (or added) FP32.
 //
+// Weight gradient (k_wgrad_tc): dW[t][ci][co] = sum_v x[v][ci] g[v - d_t][co]
+// as the transposed GEMM rows = (tap, co) (128 / Cout taps per CTA), columns
+// = ci, reduction = voxels.  Both operands are then contiguous along their
+// row index in the NDHWC tensors (the channels), so they are staged in the
+// MN-major canonical layout (core matrices of 8 voxels x 16 bytes of
+// channels) by 16-byte cp.async copies, without a transpose.  The voxels are
+// split over CTAs; each CTA writes its partial dW, reduced in a fixed order.
+//
 // Every wait on an mbarrier is bounded; a wait that runs out sets *err and the
 // CTA leaves through the normal exit (TMEM freed).
+#include <algorithm>
 #include <cstdint>
 
 #include "nn_kernels.cuh"
@@ -100,6 +109,19 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
+}
+
+// MN-major operands without swizzle: the field at bits 32-45 (SBO) holds the
+// stride between core matrices along M (or N), the field at bits 16-29 (LBO)
+// the stride between core matrices along K
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, uint32_t mn_stride,
+                                             uint32_t k_stride) {
+  return sdesc(saddr, k_stride, mn_stride);
+}
+
+// instruction descriptor: BF16 x BF16 -> FP32, A and B MN-major (bits 15, 16)
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N) {
+  return idesc_bf16(M, N) | (1u << 15) | (1u << 16);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
@@ -295,6 +317,184 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(
                  : "memory");
 }
 
+// ---- weight gradient ------------------------------------------------------
+constexpr int WG_KC = 64;     // voxels per stage (4 MMAs of K = 16)
+constexpr int WG_STAGES = 3;  // stages in flight
+constexpr int WG_CTAS = 608;  // target CTAs of a launch (4 per SM)
+
+// CI input channels (MMA N), CO output channels (128 / CO taps per CTA).
+// blockIdx.x: tap group; blockIdx.y: voxel range [q chunk, (q + 1) chunk).
+template <int CI, int CO>
+__global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(
+    const __nv_bfloat16* __restrict__ x, int ldx, int offx, const __nv_bfloat16* __restrict__ g,
+    int ldg, int offg, int lgD, long long Mtot, long long chunk, float* __restrict__ part,
+    int tmem_cols, int* __restrict__ err) {
+  constexpr int TPM = TC_M / CO;                 // taps per CTA
+  constexpr int A_BYTES = TC_M * WG_KC * 2;      // 16 KB
+  constexpr int B_BYTES = CI * WG_KC * 2;
+  constexpr int ST_BYTES = A_BYTES + B_BYTES;
+  constexpr uint32_t A_KSTR = (TC_M / 8) * 128;  // bytes between 8-voxel groups
+  constexpr uint32_t B_KSTR = (CI / 8) * 128;
+  constexpr uint32_t IDESC = idesc_bf16_mn(TC_M, CI);
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* done = reinterpret_cast<uint64_t*>(smem + WG_STAGES * ST_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + WG_STAGES);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tile = blockIdx.x;
+  const long long v0 = (long long)blockIdx.y * chunk;
+  const long long v1 = v0 + chunk < Mtot ? v0 + chunk : Mtot;
+  const int nk = v1 > v0 ? (int)((v1 - v0 + WG_KC - 1) / WG_KC) : 0;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int q = 0; q < WG_STAGES; ++q) mbar_init(done + q, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = *tslot;
+  bool ok = true;
+
+  // stage st <- voxels [v0 + k WG_KC, +WG_KC): chunk e of a tile lands at 16 e
+  // (A: e = (8-voxel group, 8-row group, voxel in group); B likewise with the
+  // 8-channel groups of x)
+  auto load = [&](int k, int st) {
+    unsigned char* As = smem + st * ST_BYTES;
+    unsigned char* Bs = As + A_BYTES;
+    const long long vb = v0 + (long long)k * WG_KC;
+    for (int e = tid; e < TC_M * WG_KC / 8; e += TC_THREADS) {
+      const int r8 = e & 7, mg = (e >> 3) & (TC_M / 8 - 1), kg = e >> 7;
+      const int tl = mg / (CO / 8), co8 = mg - tl * (CO / 8);
+      const int t = tile * TPM + tl;
+      const long long v = vb + kg * 8 + r8;
+      const bool ok_e = t < 27 && v < v1;
+      long long src = 0;
+      if (ok_e) {
+        const int dx = t / 9 - 1, dy = (t / 3) % 3 - 1, dz = t % 3 - 1;
+        src = tc_nbr(v, lgD, -dx, -dy, -dz) * ldg + offg + 8 * co8;
+      }
+      cp_async16(As + 16 * e, g + src, ok_e);
+    }
+    for (int e = tid; e < CI * WG_KC / 8; e += TC_THREADS) {
+      const int r8 = e & 7, ng = (e >> 3) % (CI / 8), kg = (e >> 3) / (CI / 8);
+      const long long v = vb + kg * 8 + r8;
+      const bool ok_e = v < v1;
+      cp_async16(Bs + 16 * e, x + (ok_e ? v * ldx + offx + 8 * ng : 0), ok_e);
+    }
+  };
+
+  int commits[WG_STAGES] = {}, last_commit = -1;
+  for (int k = 0; k < WG_STAGES - 1; ++k) {
+    if (k < nk) load(k, k);
+    cp_async_commit();
+  }
+  for (int k = 0; k < nk; ++k) {
+    const int st = k % WG_STAGES;
+    const int kn = k + WG_STAGES - 1;
+    if (kn < nk) {
+      const int sn = kn % WG_STAGES;  // last read by the MMAs of chunk k - 1
+      if (k >= 1 && tid == 0 &&
+          !mbar_wait(done + sn, (uint32_t)(((k - 1) / WG_STAGES) & 1), err))
+        ok = false;
+      ok = __syncthreads_and(ok);
+      if (!ok) break;
+      load(kn, sn);
+    }
+    cp_async_commit();
+    cp_async_wait<WG_STAGES - 1>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(smem + st * ST_BYTES), b0 = a0 + A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < WG_KC / 16; ++kk) {
+        const uint64_t ad = sdesc_mn(a0 + 2 * kk * A_KSTR, 128, A_KSTR);
+        const uint64_t bd = sdesc_mn(b0 + 2 * kk * B_KSTR, 128, B_KSTR);
+        mma_bf16(tbase, ad, bd, IDESC, (k > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(done + st);
+      ++commits[st];
+      last_commit = st;
+    }
+  }
+  ok = __syncthreads_and(ok);
+  if (ok && nk > 0 && tid == 0 &&
+      !mbar_wait(done + (nk - 1) % WG_STAGES, (uint32_t)(((nk - 1) / WG_STAGES) & 1), err))
+    ok = false;
+  ok = __syncthreads_and(ok);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    // row = (tap in group, co); its CI accumulators go to part[q][t][ci][co]
+    const int row = warp * 32 + (tid & 31);
+    const int tl = row / CO, co = row - tl * CO, t = tile * TPM + tl;
+    const long long base = ((long long)blockIdx.y * 27 + (t < 27 ? t : 0)) * CI * CO + co;
+    const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int n0 = 0; n0 < CI; n0 += 16) {
+      float v[16];
+      tmem_ld16(lane_addr + n0, v);
+      if (t < 27) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) part[base + (long long)(n0 + i) * CO] = nk > 0 ? v[i] : 0.f;
+      }
+    }
+  } else {
+    // a wait ran out: let the copies and MMAs in flight finish (bounded)
+    cp_async_wait<0>();
+    if (tid == 0 && last_commit >= 0)
+      mbar_wait(done + last_commit, (uint32_t)((commits[last_commit] - 1) & 1), err);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                 "r"(tmem_cols)
+                 : "memory");
+}
+
+// splits of the voxel range: about WG_CTAS CTAs in all, none empty
+void wgrad_split(int Cout, long long Mtot, int* S, long long* chunk) {
+  const int nt = (27 + TC_M / Cout - 1) / (TC_M / Cout);
+  const long long nch = (Mtot + WG_KC - 1) / WG_KC;
+  long long s = std::max(1, WG_CTAS / nt);
+  if (s > nch) s = nch;
+  const long long per = (nch + s - 1) / s;
+  *S = (int)((nch + per - 1) / per);
+  *chunk = per * WG_KC;
+}
+
+template <int CI, int CO>
+void launch_wgrad(TView x, TView g, int lgD, long long Mtot, float* part, int* err, int* S_out,
+                  cudaStream_t s) {
+  constexpr int ST_BYTES = TC_M * WG_KC * 2 + CI * WG_KC * 2;
+  const int cols = CI <= 32 ? 32 : (CI <= 64 ? 64 : (CI <= 128 ? 128 : 256));
+  const size_t need = (size_t)WG_STAGES * ST_BYTES + WG_STAGES * 8 + 16;
+  const int k = 512 / cols;
+  const size_t cap = 233472 / (k + 1) - 1024 + 16;
+  const size_t smem = need > cap ? need : cap;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_wgrad_tc<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    attr = true;
+  }
+  int S;
+  long long chunk;
+  wgrad_split(CO, Mtot, &S, &chunk);
+  const int nt = (27 + TC_M / CO - 1) / (TC_M / CO);
+  k_wgrad_tc<CI, CO><<<dim3(nt, S), TC_THREADS, smem, s>>>(x.p, x.ld, x.off, g.p, g.ld, g.off,
+                                                           lgD, Mtot, chunk, part, cols, err);
+  *S_out = S;
+}
+
 // Packed weight slices.  Forward (N = Cout, K = Cin):
 //   Wp[t][c][n][k8] = W[t][8c + k8][n]
 // Input gradient (N = Cin, K = Cout):
@@ -371,4 +571,34 @@ bool nn_tc_conv(const TcArgs& a, int K, int N, bool dgrad, cudaStream_t s) {
   TC_CASE(16, 48)
 #undef TC_CASE
   return false;
+}
+
+// (Cin, Cout) pairs of the network's weight gradients
+bool nn_tc_wgrad_supported(int Cin, int Cout) {
+  static const int p[][2] = {{16, 16}, {16, 32}, {32, 32}, {32, 64}, {64, 64},
+                             {64, 128}, {128, 128}, {192, 64}, {96, 32}, {48, 16}};
+  for (auto& q : p)
+    if (q[0] == Cin && q[1] == Cout) return true;
+  return false;
+}
+
+long long nn_tc_wgrad_scratch(int Cin, int Cout) {
+  const int nt = (27 + TC_M / Cout - 1) / (TC_M / Cout);
+  return (long long)std::max(1, WG_CTAS / nt) * 27 * Cin * Cout;
+}
+
+bool nn_tc_wgrad(TView x, int Cin, TView g, int Cout, float* dW, float* db, float* partials,
+                 int B, int lgD, int* err, cudaStream_t s) {
+  const long long Mtot = (long long)B << (3 * lgD);
+  int S = 0;
+#define WG_CASE(CI, CO)                                                  \
+  if (Cin == CI && Cout == CO) {                                         \
+    launch_wgrad<CI, CO>(x, g, lgD, Mtot, partials, err, &S, s);         \
+  } else
+  WG_CASE(16, 16) WG_CASE(16, 32) WG_CASE(32, 32) WG_CASE(32, 64) WG_CASE(64, 64)
+  WG_CASE(64, 128) WG_CASE(128, 128) WG_CASE(192, 64) WG_CASE(96, 32) WG_CASE(48, 16)
+  return false;
+#undef WG_CASE
+  nn_wgrad_finish(partials, S, Cin, Cout, dW, g, db, Mtot, s);
+  return true;
 }

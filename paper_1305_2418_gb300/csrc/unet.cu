@@ -332,7 +332,9 @@ static mgfr_status unet_alloc(mgfr_ctx* c, UNet* U, int B, int lgD) {
   U->G_D1a = f(M0 * 16);
   U->G_D1b = f(M0 * 16);
   long long wn = 0;
-  for (const ConvSpec& cs : kConvs) wn = std::max(wn, nn_wgrad_scratch(cs.cin, cs.cout));
+  for (const ConvSpec& cs : kConvs)
+    wn = std::max(wn, std::max(nn_wgrad_scratch(cs.cin, cs.cout),
+                               nn_tc_wgrad_scratch(cs.cin, cs.cout)));
   U->wpart_n = wn;
   U->wpart = f(std::max(wn, 17LL * 1024));
   void* p = nullptr;
@@ -445,8 +447,10 @@ static void conv_bwd(mgfr_ctx* c, UNet* U, int i, const LayerIO& L, int acc_in) 
   const long long M = (long long)U->B << (3 * L.lgD);
   k_relu_bwd<<<nblocks(M * s.cout, BS), BS, 0, c->s>>>(L.gy, L.y, s.cout, M, U->Gpre);
   const TView g = tv(U->Gpre, s.cout);
-  nn_conv_wgrad(L.x, s.cin, g, s.cout, U->G + U->woff[i], U->G + U->boff[i], U->wpart, U->B, L.lgD,
-                c->s);
+  if (!nn_tc_wgrad(L.x, s.cin, g, s.cout, U->G + U->woff[i], U->G + U->boff[i], U->wpart, U->B,
+                   L.lgD, U->tc_err, c->s))
+    nn_conv_wgrad(L.x, s.cin, g, s.cout, U->G + U->woff[i], U->G + U->boff[i], U->wpart, U->B,
+                  L.lgD, c->s);
   if (L.gx.p) {
     if (nn_tc_supported(s.cout, s.cin)) {
       TcArgs a{};
@@ -817,13 +821,26 @@ mgfr_status mgfr_nn_conv3d(int op, int B, int D, int Cin, int Cout, const void* 
     nn_conv_dgrad(TView{(__nv_bfloat16*)g_bf16, Cout, 0}, Cout, (const __nv_bfloat16*)w_bf16,
                   FView{(float*)out, Cin, 0}, Cin, 0, B, lgD, s);
   } else if (op == 2) {
+    const bool tcw = nn_tc_wgrad_supported(Cin, Cout);
     float* part = nullptr;
-    if (cudaMalloc(&part, sizeof(float) * (size_t)nn_wgrad_scratch(Cin, Cout)) != cudaSuccess)
+    int* err = nullptr;
+    const long long np = tcw ? nn_tc_wgrad_scratch(Cin, Cout) : nn_wgrad_scratch(Cin, Cout);
+    if (cudaMalloc(&part, sizeof(float) * (size_t)np) != cudaSuccess) return MGFR_E_OOM;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+      cudaFree(part);
       return MGFR_E_OOM;
-    nn_conv_wgrad(TView{(__nv_bfloat16*)x_bf16, Cin, 0}, Cin, TView{(__nv_bfloat16*)g_bf16, Cout, 0},
-                  Cout, (float*)out, db, part, B, lgD, s);
-    cudaStreamSynchronize(s);
+    }
+    cudaMemsetAsync(err, 0, sizeof(int), s);
+    const TView xv{(__nv_bfloat16*)x_bf16, Cin, 0}, gv{(__nv_bfloat16*)g_bf16, Cout, 0};
+    if (!tcw || !nn_tc_wgrad(xv, Cin, gv, Cout, (float*)out, db, part, B, lgD, err, s))
+      nn_conv_wgrad(xv, Cin, gv, Cout, (float*)out, db, part, B, lgD, s);
+    int e = 0;
+    const bool okc = cudaStreamSynchronize(s) == cudaSuccess &&
+                     cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
     cudaFree(part);
+    cudaFree(err);
+    if (!okc || cudaGetLastError() != cudaSuccess) return MGFR_E_CUDA;
+    if (e) return MGFR_E_TIMEOUT;
   } else {
     return MGFR_E_INVALID;
   }
