@@ -65,9 +65,9 @@ FAMILY_BOUND = {0: "hbm", 1: "hbm", 2: "alu", 3: "hbm", 4: "hbm"}
 # DRAM bytes per cell (dram__bytes_read.sum + dram__bytes_write.sum over the
 # launch's cells), from ncu on the half-density 256^3-base sample of the same
 # workload (same cell size, sigma_g, levels and |fR0|); scaled to a full
-# launch by its cells (family 3: 343.4 MB over the 24.8 M cells of a level-1
+# launch by its cells (family 3: 343.6 MB over the 24.8 M cells of a level-1
 # launch of that sample, 12124 x 256 threads, one per oct).
-TRAFFIC_PER_CELL = {3: 343.39e6 / (12124 * 256 * 8)}
+TRAFFIC_PER_CELL = {3: 343.59e6 / (12124 * 256 * 8)}
 KERNEL_NAMES = {0: "k_sweep32 (FP32 NGS half-sweep, base level)",
                 1: "k_lin_sweep (FP32 linear GS half-sweep, base level)",
                 2: "k_resid_df / k_oresid_df (FP64-accurate residual in double-float)",
