@@ -362,7 +362,7 @@ def learned_extra(mgfr, learned, torch, dev, local):
     s.unet_init(seed=1)
     steps, B = 1500, 4
     t0 = time.perf_counter()
-    losses = learned.train(s, deltas, fr0s, us, steps=steps, batch=B, lr=2e-3, seed=2)
+    losses = learned.train(s, deltas, fr0s, us, steps=steps, batch=B, lr=1e-3, seed=2)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del deltas, us

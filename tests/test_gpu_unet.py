@@ -133,7 +133,12 @@ def test_unet_training_and_learned_start(dev):
     s = mgfr.Solver(0, precision=mgfr.PREC_MIXED)
     deltas, fr0s, us = learned.make_training_set(s, 256, 32, 12.5, seed=11)
     s.unet_init(seed=3)
-    losses = learned.train(s, deltas, fr0s, us, steps=2000, batch=4, lr=2e-3, seed=5)
+    # lr 1e-3: at 2e-3 the loss spikes (once to 94 times its first value) and
+    # whether training recovers depends on the mini-batch seed and on FP32
+    # summation order (two weight-gradient kernels that agree to 1e-6, seeds 5
+    # and 6: two of the four runs ended above the bound below); at 1e-3 both
+    # kernels reach 0.015-0.017 from 0.11-0.12
+    losses = learned.train(s, deltas, fr0s, us, steps=2000, batch=4, lr=1e-3, seed=5)
     first, last = float(np.mean(losses[:20])), float(np.mean(losses[-20:]))
     # the output layer starts at zero, so the first losses are those of the
     # zero prediction; a quarter of them is half its RMS error in v, the same
