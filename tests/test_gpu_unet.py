@@ -126,10 +126,10 @@ def test_unet_training_and_learned_start(dev):
     cell size from the prediction.  The polished answer must not depend on the
     start.  What the network must deliver: over the fields, a start closer to
     the solution (RMS in u, summed) than the zero start by a factor 2, at a
-    cost of at most one more V-cycle per field.  It does not save V-cycles or
+    cost of at most one more V-cycle per field.  It saves few V-cycles and no
     time to 1e-8 (measured and reported by bench.py): the first V-cycle from
-    zero already brings the residual to a few per cent, below what the
-    network's error reaches."""
+    zero already brings the residual to a few per cent, and the prediction
+    costs more than the cycles it saves."""
     s = mgfr.Solver(0, precision=mgfr.PREC_MIXED)
     deltas, fr0s, us = learned.make_training_set(s, 256, 32, 12.5, seed=11)
     s.unet_init(seed=3)
