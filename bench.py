@@ -404,7 +404,8 @@ def time_stepped_extra(mgfr, torch, dev, local, net_path, steps=8):
     (force of Eq. (30) on the base PM grid, leapfrog; the fastest particle
     moves about one base cell over the run): per step the V-cycles of all
     levels and the solve time from a zero start, from the previous step's
-    solution, and from the learned start."""
+    solution on the base level (the paper's step list) and on every level
+    where the octs persist, and from the learned start."""
     from paper_1305_2418_gb300 import pmloop
     w = W256
     d = synth.lognormal_delta(w["N"], w["box"], w["sigma_g"], w["seed"])
@@ -414,7 +415,7 @@ def time_stepped_extra(mgfr, torch, dev, local, net_path, steps=8):
     out = {"workload": "particles256 moved through %d toy PM steps (force of Eq. (30), "
                        "leapfrog, about one base cell in all)" % steps,
            "max_rel_diff_fr": max(r["max_rel_diff_fr"] for r in rows)}
-    for k in ("zero", "previous", "learned"):
+    for k in ("zero", "previous", "previous_all", "learned"):
         if k in rows[0]:
             later = rows[1:]
             out[k] = {"cycles_mean": float(np.mean([r[k]["cycles"] for r in later])),

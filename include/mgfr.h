@@ -109,12 +109,25 @@ typedef struct {
  *                      previous step's u, kept in the context: no copy);
  *                      u_init must be NULL; MGFR_E_INVALID if there is none
  *                      (first solve, another size or precision since).  Not
- *                      for batches. */
+ *                      for batches.
+ *   MGFR_START_PREVIOUS_ALL  as MGFR_START_PREVIOUS on the base level, and in
+ *                      a particle solve also on the refined levels: every oct
+ *                      that the context's previous particle solve (same base
+ *                      grid and box, made in this mode) also had starts from
+ *                      that solve's u there; the other octs start from the
+ *                      prolonged coarser solution (Sec. 3.3).  The paper's
+ *                      step list starts only the base level from the previous
+ *                      step; this carries the previous solution to the
+ *                      refined levels too, an accelerator that leaves the
+ *                      answer unchanged.  When nothing of a previous solve is
+ *                      held (first solve of the context) it is the zero
+ *                      start; u_init must be NULL; not for batches. */
 typedef enum {
   MGFR_START_ZERO = 0,
   MGFR_START_USER = 1,
   MGFR_START_LEARNED = 2,
-  MGFR_START_PREVIOUS = 3
+  MGFR_START_PREVIOUS = 3,
+  MGFR_START_PREVIOUS_ALL = 4
 } mgfr_start;
 
 typedef struct {

@@ -884,8 +884,52 @@ void amr_free(mgfr_ctx* c) {
   if (A->rec_idx) cudaFree(A->rec_idx);
   if (A->split_list) cudaFree(A->split_list);
   if (A->d_split) cudaFree(A->d_split);
+  for (int l = 0; l < AMR_MAXL; ++l) {
+    if (A->prev_key[l]) cudaFree(A->prev_key[l]);
+    if (A->prev_u[l]) cudaFree(A->prev_u[l]);
+  }
   delete A;
   c->amr = nullptr;
+}
+
+// Morton keys of the octs' parent cells (parent coordinates at level l - 1)
+__global__ void k_oct_keys(const int4* __restrict__ opos, long long n_oct,
+                           unsigned long long* __restrict__ key) {
+  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (o >= n_oct) return;
+  const int4 p = opos[o];
+  key[o] = morton3((unsigned)p.x, (unsigned)p.y, (unsigned)p.z);
+}
+
+mgfr_status amr_keep_previous(mgfr_ctx* c, AmrWork* A, bool keep) {
+  A->prev_nlev = 0;
+  if (!keep) return MGFR_OK;
+  // 21 bits per coordinate in the keys: parents of level l have coordinates
+  // below N0 2^(l-1)
+  if ((long long)A->N0 << (A->nlev > 1 ? A->nlev - 2 : 0) > (1LL << 21)) return MGFR_OK;
+  for (int l = 1; l < A->nlev; ++l) {
+    const AmrLevel& L = A->L[l];
+    if (L.n_oct > A->prev_cap[l]) {
+      if (A->prev_key[l]) cudaFree(A->prev_key[l]);
+      if (A->prev_u[l]) cudaFree(A->prev_u[l]);
+      A->prev_key[l] = nullptr;
+      A->prev_u[l] = nullptr;
+      A->prev_cap[l] = 0;
+      MG_CK(c, cudaMalloc(&A->prev_key[l], sizeof(unsigned long long) * (size_t)L.n_oct));
+      MG_CK(c, cudaMalloc(&A->prev_u[l], sizeof(double) * 8 * (size_t)L.n_oct));
+      A->prev_cap[l] = L.n_oct;
+    }
+    A->prev_noct[l] = L.n_oct;
+    if (L.n_oct == 0) continue;
+    k_oct_keys<<<nblocks(L.n_oct, BS), BS, 0, c->s>>>(L.opos, L.n_oct, A->prev_key[l]);
+    MG_CK(c, cudaMemcpyAsync(A->prev_u[l], L.u, sizeof(double) * 8 * (size_t)L.n_oct,
+                             cudaMemcpyDeviceToDevice, c->s));
+    c->launches += 1;
+  }
+  A->prev_nlev = A->nlev;
+  A->prev_N0 = A->N0;
+  A->prev_box = A->box;
+  return MGFR_OK;
 }
 
 void amr_invalidate(mgfr_ctx* c) {
@@ -1227,6 +1271,7 @@ static mgfr_status solve_particles(mgfr_ctx* c, const double* pos, long long Np,
     if (ls != MGFR_OK && ls != MGFR_E_NOCONVERGE) return ls;
     if (ls != MGFR_OK) worst = ls;
   }
+  TRY(amr_keep_previous(c, A, g.start == MGFR_START_PREVIOUS_ALL));
   MG_CK(c, cudaEventRecord(c->t1, c->s));
   // force per level, then at the particles
   f64::force(L0, m, A->fr0, A->acc0, c->s);

@@ -126,7 +126,31 @@ struct AmrWork {
   bool rec_on = false;                            // the last deposit recorded
   long long cap_cells[AMR_MAXL] = {}; // allocated capacity per level (cells)
   long long cap_oct[AMR_MAXL] = {};
+  // the refined levels of the previous particle solve made with start =
+  // MGFR_START_PREVIOUS_ALL: per level, the Morton keys of the octs' parent
+  // cells (increasing: the storage order) and the converged u of their cells
+  int prev_nlev = 0, prev_N0 = 0;
+  double prev_box = 0.0;
+  unsigned long long* prev_key[AMR_MAXL] = {};
+  double* prev_u[AMR_MAXL] = {};
+  long long prev_noct[AMR_MAXL] = {}, prev_cap[AMR_MAXL] = {};
 };
+
+// Morton key of cell (i, j, k) (21 bits each): the bits of i, j and k
+// interleaved with i's the most significant of each triple, the order in
+// which the base level's flag scan visits cells and every level stores octs.
+__host__ __device__ inline unsigned long long morton3(unsigned i, unsigned j, unsigned k) {
+  unsigned long long m = 0;
+  for (int b = 0; b < 21; ++b)
+    m |= ((unsigned long long)((i >> b) & 1u) << (3 * b + 2)) |
+         ((unsigned long long)((j >> b) & 1u) << (3 * b + 1)) |
+         ((unsigned long long)((k >> b) & 1u) << (3 * b));
+  return m;
+}
+
+// Keep the refined levels of this particle solve for the next one (start =
+// MGFR_START_PREVIOUS_ALL), or forget them (any other start).
+mgfr_status amr_keep_previous(mgfr_ctx* c, AmrWork* A, bool keep);
 
 void amr_free(mgfr_ctx* c);
 // Forget the hierarchy of the last particle solve (its level-0 arrays live in

@@ -1296,6 +1296,39 @@ __global__ void k_init_level(long long ncell, const int* __restrict__ pcell,
   wE[c] = exp(v);
 }
 
+// Start of level L from the previous particle solve where its octs persist
+// (start = MGFR_START_PREVIOUS_ALL): the oct whose parent cell has the same
+// Morton key, found by binary search in the previous solve's keys (increasing,
+// the storage order), lends its eight converged values; the other octs keep
+// the prolonged guess of k_init_level.
+__global__ void k_warm_level(const int4* __restrict__ opos, long long n_oct,
+                             const unsigned long long* __restrict__ pkey, long long pn,
+                             const double* __restrict__ pu, double* __restrict__ w,
+                             double* __restrict__ wE, float* __restrict__ w32) {
+  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (o >= n_oct) return;
+  const int4 p = opos[o];
+  const unsigned long long key = morton3((unsigned)p.x, (unsigned)p.y, (unsigned)p.z);
+  long long lo = 0, hi = pn;
+  while (lo < hi) {
+    const long long mid = (lo + hi) >> 1;
+    if (pkey[mid] < key)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  if (lo >= pn || pkey[lo] != key) return;
+  for (int ch = 0; ch < 8; ++ch) {
+    const double v = pu[8 * lo + ch];
+    if (w32) {
+      w32[pidx(8 * o + ch, n_oct)] = f_from_double_bits(v);
+    } else {
+      w[8 * o + ch] = v;
+      wE[8 * o + ch] = exp(v);
+    }
+  }
+}
+
 // Ghost values on the faces of level-l octs that have no neighbouring oct
 // (Sec. 3.3), one thread per ghost value: slot s = t / 4 (its face 6 o + d
 // from gface), qi = t % 4 the face cell.  The face's four outside cells are
@@ -1949,6 +1982,13 @@ mgfr_status amr_solve_level(mgfr_ctx* c, AmrWork* A, int Lv, const Model& m, mgf
   k_init_level<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.ncell, F.pcell, F.pnbr, up,
                                                       g.prolong_linear, F.w, F.wE,
                                                       mixed ? F.w32 : nullptr, F.n_oct);
+  if (g.start == MGFR_START_PREVIOUS_ALL && Lv < A->prev_nlev && A->prev_N0 == A->N0 &&
+      A->prev_box == A->box && A->prev_noct[Lv] > 0 && F.n_oct > 0) {
+    k_warm_level<<<nblocks(F.n_oct, BS), BS, 0, c->s>>>(F.opos, F.n_oct, A->prev_key[Lv],
+                                                         A->prev_noct[Lv], A->prev_u[Lv], F.w,
+                                                         F.wE, mixed ? F.w32 : nullptr);
+    c->launches += 1;
+  }
   if (mixed) {
     k_d2df<<<nblocks(F.ncell, BS), BS, 0, c->s>>>(F.f, reinterpret_cast<dfl*>(F.wf), F.ncell);
   } else {

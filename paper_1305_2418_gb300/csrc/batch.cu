@@ -784,7 +784,7 @@ mgfr_status mgfr_batch_solve(mgfr_ctx* c, int nsolves, const mgfr_batch_item* it
       return set_err(c, MGFR_E_INVALID, "invalid batch item");
     if (g.start == MGFR_START_USER && !it.u_init_dev)
       return set_err(c, MGFR_E_INVALID, "start = user needs u_init_dev on every batch item");
-    if (g.start == MGFR_START_PREVIOUS)
+    if (g.start == MGFR_START_PREVIOUS || g.start == MGFR_START_PREVIOUS_ALL)
       return set_err(c, MGFR_E_INVALID, "start = previous is not available for batches");
   }
   auto w0 = std::chrono::steady_clock::now();

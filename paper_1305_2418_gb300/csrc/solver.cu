@@ -156,8 +156,8 @@ bool validate_cfg(const mgfr_config* c, std::string& why) {
   if (c->max_spins < 0) return bad("max_spins must be >= 0");
   if (!(c->mask_thres >= 0.0 && c->mask_thres < 1.0)) return bad("mask_thres in [0, 1)");
   if (c->n_coarse < 0 || c->n_coarse > 16) return bad("n_coarse in [0, 16]");
-  if (c->start < MGFR_START_ZERO || c->start > MGFR_START_PREVIOUS)
-    return bad("start must be 0 (zero), 1 (user), 2 (learned) or 3 (previous)");
+  if (c->start < MGFR_START_ZERO || c->start > MGFR_START_PREVIOUS_ALL)
+    return bad("start must be 0 (zero), 1 (user), 2 (learned), 3 (previous) or 4 (previous, all levels)");
   return true;
 }
 
@@ -166,10 +166,12 @@ mgfr_status start_guess(mgfr_ctx* c, int N, const double* x, double dscale, cons
   *u0 = u_init;
   if (c->cfg.start == MGFR_START_USER && !u_init)
     return set_err(c, MGFR_E_INVALID, "start = user needs u_init");
-  if (c->cfg.start == MGFR_START_PREVIOUS) {
+  if (c->cfg.start == MGFR_START_PREVIOUS || c->cfg.start == MGFR_START_PREVIOUS_ALL) {
     if (u_init) return set_err(c, MGFR_E_INVALID, "start = previous takes no u_init");
-    if (c->u_prev_N != N || c->dh.N != N)
+    if (c->u_prev_N != N || c->dh.N != N) {
+      if (c->cfg.start == MGFR_START_PREVIOUS_ALL) return MGFR_OK;  // nothing held: zero start
       return set_err(c, MGFR_E_INVALID, "start = previous: no solution of this size in the context");
+    }
     *u0 = c->dh.L[0].u;  // kept in place; the initialisation forms e^u from it
     return MGFR_OK;
   }

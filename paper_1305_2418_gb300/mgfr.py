@@ -17,7 +17,7 @@ MGFR_OK, MGFR_E_INVALID, MGFR_E_CUDA, MGFR_E_OOM, MGFR_E_NOCONVERGE, MGFR_E_TIME
     MGFR_E_UNSUPPORTED = range(7)
 STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "NOCONVERGE", "TIMEOUT", "UNSUPPORTED"]
 PREC_FP64, PREC_MIXED = 0, 1
-START_ZERO, START_USER, START_LEARNED, START_PREVIOUS = 0, 1, 2, 3
+START_ZERO, START_USER, START_LEARNED, START_PREVIOUS, START_PREVIOUS_ALL = 0, 1, 2, 3, 4
 PM_EFFECTIVE, PM_MATTER, PM_TOTAL = 0, 1, 2
 FIELD_U, FIELD_FR, FIELD_SOURCE, FIELD_MASS, FIELD_ACC, FIELD_COUNT = range(6)
 

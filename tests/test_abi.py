@@ -70,7 +70,7 @@ def test_default_config_and_validation(lib):
     assert cfg.start == mgfr.START_ZERO
     bad = [dict(fr0_abs=0.0), dict(n=0), dict(tol_rel=2.0), dict(n_pre=0, n_post=0),
            dict(precision=7), dict(omega_m=-1.0), dict(step_cap=0.0), dict(n_coarse=-1),
-           dict(n_coarse=17), dict(mixed_inner=0), dict(mask_thres=1.0), dict(start=4),
+           dict(n_coarse=17), dict(mixed_inner=0), dict(mask_thres=1.0), dict(start=5),
            dict(start=-1)]
     for kw in bad:
         c = mgfr.default_config(**kw)
