@@ -592,7 +592,8 @@ def main():
         e2e_upd += r["stats"]["cell_updates"]
     f1.record()
     torch.cuda.synchronize()
-    e2e_value, _ = D.whole_job_rate(e2e_upd, f0.elapsed_time(f1), dev)
+    e2e_ms = f0.elapsed_time(f1)
+    e2e_value, _ = D.whole_job_rate(e2e_upd, e2e_ms, dev)
     del host_in, host_out
     # ---- potential of matter + effective mass on the base PM grid (Eq. (30)) ----
     pm = {}
@@ -710,7 +711,7 @@ def main():
         "clocks": ck,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * n_part,
-                "d2h_bytes_per_step": 24 * n_part},
+                "d2h_bytes_per_step": 24 * n_part, "ms_per_step": e2e_ms / args.steps},
         "cpu_baseline": cpu,
         "pm_potential": pm,
         **extras,
