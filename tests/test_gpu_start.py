@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1305_2418_gb300 import build, mgfr, synth
 
 pytestmark = pytest.mark.gpu
@@ -74,6 +75,11 @@ def test_learned_start_reaches_the_same_answer(dev):
     out = s.solve_density(d, box)
     assert rel(out["fr"], ref["fr"]) <= 1e-5
     assert out["stats"]["res_l2_final"] <= 1e-8 * out["stats"]["f_l2"]
+    # and against the FP64 oracle directly (the mixed-form tolerance)
+    u_ref, st_ref = oracle.solve_dense(d.cpu().numpy(), box, 1e-5, tol=1e-11, max_vcycles=300)
+    assert st_ref["converged"] == 1.0
+    fr_ref, _ = oracle.force_dense(u_ref, box, 1e-5)
+    assert np.abs(out["fr"].cpu().numpy() / fr_ref - 1.0).max() <= 1e-5
     # particle solve: the base level is predicted from its deposited density
     N0, pbox = 32, 25.0
     pd = synth.lognormal_delta(N0, pbox, 1.5, 12005)
