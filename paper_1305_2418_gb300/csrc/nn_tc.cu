@@ -495,6 +495,177 @@ void launch_wgrad(TView x, TView g, int lgD, long long Mtot, float* part, int* e
   *S_out = S;
 }
 
+// ---- halo-tiled forward and input gradient for the full-resolution layers ---
+// A CTA computes TX x-slices of a 16 (y) x 8 (z) block of output voxels, one
+// M = 128 tile per slice (row m = 8 y + z).  It stages the input once as a
+// (TX + 2) x 18 x 10 voxel block with its one-voxel periodic halo, laid out
+// [8-channel group][x][y][z] with 16 bytes per voxel, and all 27 taps'
+// packed weights by one bulk copy.  The A operand of tap (dx, dy, dz) is then
+// a K-major no-swizzle view of the halo block: core matrices of 8 z-
+// consecutive voxels x 16 bytes, 8-row groups (y) 10 x 16 bytes apart (SBO),
+// 8-channel groups one block-plane apart (LBO), the start shifted by the tap
+// offset.  So the block is read from global memory once instead of 27 times,
+// and a tile costs 27 (KC / 16) MMAs on shared-memory operands.
+template <int KC, int NC, bool DGRAD, int TX>
+__global__ void __launch_bounds__(TC_THREADS) k_conv_halo(
+    const __nv_bfloat16* __restrict__ x, int ldx, int offx, const __nv_bfloat16* __restrict__ Wp,
+    const float* __restrict__ bias, int relu, __nv_bfloat16* __restrict__ y, int ldy, int offy,
+    float* __restrict__ gx, int ldg, int offg, int accumulate, int lgD, int tmem_cols,
+    int* __restrict__ err) {
+  constexpr int HX = TX + 2, HY = 18, HZ = 10, CH = KC / 8;
+  constexpr int PLANE = HX * HY * HZ * 16;  // bytes of one 8-channel group
+  constexpr int H_BYTES = CH * PLANE;
+  constexpr int W_BYTES = 27 * NC * KC * 2;
+  constexpr uint32_t SBO = HZ * 16, B_LBO = NC * 16;
+  constexpr uint32_t IDESC = idesc_bf16(TC_M, NC);
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* Hs = smem;
+  unsigned char* Ws = smem + H_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Ws + W_BYTES);  // weights, MMAs
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int D = 1 << lgD, M = D - 1;
+  // tile coordinates: z blocks of 8, y blocks of 16, x blocks of TX, samples
+  const int nz = D >> 3, ny = D >> 4, nx = D / TX;
+  long long bid = blockIdx.x;
+  const int bz = (int)(bid % nz);
+  bid /= nz;
+  const int by = (int)(bid % ny);
+  bid /= ny;
+  const int bx = (int)(bid % nx);
+  const long long b = bid / nx;
+  const int x0 = bx * TX, y0 = by * 16, z0 = bz * 8;
+  const long long sbase = b << (3 * lgD);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(bars, 1);
+    mbar_init(bars + 1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = *tslot;
+  bool ok = true;
+  if (tid == 0) bulk_load(Ws, Wp, (uint32_t)W_BYTES, bars);
+  // the halo block: chunk e = ((c8 HX + hx) HY + hy) HZ + hz lands at 16 e
+  for (int e = tid; e < CH * HX * HY * HZ; e += TC_THREADS) {
+    int r = e;
+    const int hz = r % HZ;
+    r /= HZ;
+    const int hy = r % HY;
+    r /= HY;
+    const int hx = r % HX;
+    const int c8 = r / HX;
+    const long long v = sbase + ((((long long)((x0 + hx - 1) & M) << lgD) + ((y0 + hy - 1) & M))
+                                 << lgD) +
+                        ((z0 + hz - 1) & M);
+    cp_async16(Hs + 16 * e, x + v * ldx + offx + 8 * c8, true);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  bool issued = false;
+  if (tid == 0) {
+    if (!mbar_wait(bars, 0, err)) {
+      ok = false;
+    } else {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t h0 = smem_u32(Hs), w0 = smem_u32(Ws);
+      const int sg = DGRAD ? -1 : 1;
+#pragma unroll 1
+      for (int t = 0; t < 27; ++t) {
+        const int dx = sg * (t / 9 - 1), dy = sg * ((t / 3) % 3 - 1), dz = sg * (t % 3 - 1);
+#pragma unroll 1
+        for (int tx = 0; tx < TX; ++tx) {
+          const uint32_t a_off = (uint32_t)((((tx + dx + 1) * HY + (dy + 1)) * HZ + (dz + 1)) * 16);
+#pragma unroll
+          for (int kk = 0; kk < KC / 16; ++kk) {
+            const uint64_t ad = sdesc(h0 + a_off + 2 * kk * PLANE, PLANE, SBO);
+            const uint64_t bd = sdesc(w0 + t * (NC * KC * 2) + 2 * kk * B_LBO, B_LBO, 128);
+            mma_bf16(tbase + tx * NC, ad, bd, IDESC, (t > 0 || kk > 0) ? 1u : 0u);
+          }
+        }
+      }
+      mma_commit(bars + 1);
+      issued = true;
+    }
+  }
+  ok = __syncthreads_and(ok);
+  if (ok && tid == 0 && !mbar_wait(bars + 1, 0, err)) ok = false;
+  ok = __syncthreads_and(ok);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int row = warp * 32 + (tid & 31);
+    const int yy = row >> 3, zz = row & 7;
+    const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int tx = 0; tx < TX; ++tx) {
+      const long long m = sbase + ((((long long)(x0 + tx) << lgD) + (y0 + yy)) << lgD) + (z0 + zz);
+#pragma unroll 1
+      for (int n0 = 0; n0 < NC; n0 += 16) {
+        float v[16];
+        tmem_ld16(lane_addr + tx * NC + n0, v);
+        if (!DGRAD) {
+          __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            float a = v[i] + (bias ? bias[n0 + i] : 0.f);
+            if (relu) a = fmaxf(a, 0.f);
+            o[i] = __float2bfloat16(a);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(y + m * ldy + offy + n0);
+          dst[0] = reinterpret_cast<const uint4*>(o)[0];
+          dst[1] = reinterpret_cast<const uint4*>(o)[1];
+        } else {
+          float* q = gx + m * ldg + offg + n0;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) q[i] = accumulate ? q[i] + v[i] : v[i];
+        }
+      }
+    }
+  } else if (tid == 0) {
+    // a wait ran out: the weights' copy and the MMAs in flight (each bounded)
+    if (issued) mbar_wait(bars + 1, 0, err);
+    else mbar_wait(bars, 0, err);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                 "r"(tmem_cols)
+                 : "memory");
+}
+
+template <int KC, int NC, bool DG, int TX>
+void launch_halo(const TcArgs& a, cudaStream_t s) {
+  constexpr int H_BYTES = (KC / 8) * (TX + 2) * 18 * 10 * 16, W_BYTES = 27 * NC * KC * 2;
+  const int cols0 = TX * NC;
+  const int cols = cols0 <= 32 ? 32 : (cols0 <= 64 ? 64 : (cols0 <= 128 ? 128 : 256));
+  const size_t need = (size_t)H_BYTES + W_BYTES + 2 * 8 + 16;
+  const int k = 512 / cols;
+  const size_t cap = 233472 / (k + 1) - 1024 + 16;
+  const size_t smem = need > cap ? need : cap;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_conv_halo<KC, NC, DG, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    attr = true;
+  }
+  const long long tiles = a.Mtot / (TX * 16 * 8);
+  k_conv_halo<KC, NC, DG, TX><<<(unsigned)tiles, TC_THREADS, smem, s>>>(
+      a.x, a.ldx, a.offx, a.Wp, a.bias, a.relu, a.y, a.ldy, a.offy, a.gx, a.ldg, a.offg,
+      a.accumulate, a.lgD, cols, a.err);
+}
+
 // Packed weight slices.  Forward (N = Cout, K = Cin):
 //   Wp[t][c][n][k8] = W[t][8c + k8][n]
 // Input gradient (N = Cin, K = Cout):
@@ -560,6 +731,22 @@ bool nn_tc_supported(int K, int N) {
 }
 
 bool nn_tc_conv(const TcArgs& a, int K, int N, bool dgrad, cudaStream_t s) {
+  // the full-resolution layers (16 input channels of the A rows, or 48 of the
+  // skip concatenation) on the halo-tiled kernel when the grid holds its tiles
+  if (a.lgD >= 4 && a.lgD <= 10) {
+    if (K == 16 && N == 16) {
+      if (dgrad) launch_halo<16, 16, true, 4>(a, s); else launch_halo<16, 16, false, 4>(a, s);
+      return true;
+    }
+    if (!dgrad && K == 48 && N == 16) {
+      launch_halo<48, 16, false, 2>(a, s);
+      return true;
+    }
+    if (dgrad && K == 16 && N == 48) {
+      launch_halo<16, 48, true, 2>(a, s);
+      return true;
+    }
+  }
 #define TC_CASE(KK, NN)                                              \
   if (K == KK && N == NN) {                                          \
     if (dgrad) launch_tc<KK, NN, true>(a, s); else launch_tc<KK, NN, false>(a, s); \
