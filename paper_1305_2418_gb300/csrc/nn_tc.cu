@@ -731,13 +731,18 @@ bool nn_tc_supported(int K, int N) {
 }
 
 bool nn_tc_conv(const TcArgs& a, int K, int N, bool dgrad, cudaStream_t s) {
-  // the full-resolution layers (16 input channels of the A rows, or 48 of the
-  // skip concatenation) on the halo-tiled kernel when the grid holds its tiles
+  // the layers of the two finest levels whose input block and 27 weight
+  // slices fit one CTA's shared memory run on the halo-tiled kernel when the
+  // grid holds its tiles (16^3 and more)
   if (a.lgD >= 4 && a.lgD <= 10) {
-    if (K == 16 && N == 16) {
-      if (dgrad) launch_halo<16, 16, true, 4>(a, s); else launch_halo<16, 16, false, 4>(a, s);
-      return true;
-    }
+#define HALO_CASE(KK, NN, TXF, TXD)                                                       \
+  if (K == KK && N == NN) {                                                             \
+    if (dgrad) launch_halo<KK, NN, true, TXD>(a, s); else launch_halo<KK, NN, false, TXF>(a, s); \
+    return true;                                                                        \
+  }
+    HALO_CASE(16, 16, 4, 4) HALO_CASE(16, 32, 4, 4) HALO_CASE(32, 32, 2, 2)
+    HALO_CASE(32, 16, 2, 2)
+#undef HALO_CASE
     if (!dgrad && K == 48 && N == 16) {
       launch_halo<48, 16, false, 2>(a, s);
       return true;

@@ -31,7 +31,8 @@ def bf(a, dev):
                                           (1, 4, 64, 128), (1, 8, 96, 32), (2, 4, 128, 128),
                                           (2, 16, 32, 64), (4, 16, 16, 32),
                                           # the halo-tiled full-resolution kernels
-                                          (1, 16, 16, 16), (2, 16, 48, 16), (1, 32, 16, 16)])
+                                          (1, 16, 16, 16), (2, 16, 48, 16), (1, 32, 16, 16),
+                                          (1, 16, 16, 32), (2, 16, 32, 32), (1, 16, 32, 16)])
 def test_conv_kernels_match_oracle(dev, B, D, Cin, Cout):
     rng = np.random.default_rng(B * 1000 + D * 10 + Cin + Cout)
     x = rng.standard_normal((B, D, D, D, Cin)).astype(np.float32)
