@@ -666,6 +666,189 @@ void launch_halo(const TcArgs& a, cudaStream_t s) {
       a.accumulate, a.lgD, cols, a.err);
 }
 
+// The same halo-tiled form for layers whose 27 weight slices do not fit beside
+// the input block: the block stays resident while the taps' weight slices
+// stream through two shared-memory stages (one bulk copy each).  Thread 0
+// alone loads the slices and issues the MMAs, so the loop over taps has no
+// block-wide synchronisation.
+template <int KC, int NC, bool DGRAD, int TX>
+__global__ void __launch_bounds__(TC_THREADS) k_conv_halo_s(
+    const __nv_bfloat16* __restrict__ x, int ldx, int offx, const __nv_bfloat16* __restrict__ Wp,
+    const float* __restrict__ bias, int relu, __nv_bfloat16* __restrict__ y, int ldy, int offy,
+    float* __restrict__ gx, int ldg, int offg, int accumulate, int lgD, int tmem_cols,
+    int* __restrict__ err) {
+  constexpr int HX = TX + 2, HY = 18, HZ = 10, CH = KC / 8;
+  constexpr int PLANE = HX * HY * HZ * 16;
+  constexpr int H_BYTES = CH * PLANE;
+  constexpr int T_BYTES = NC * KC * 2;  // one tap's weight slice
+  constexpr uint32_t SBO = HZ * 16, B_LBO = NC * 16;
+  constexpr uint32_t IDESC = idesc_bf16(TC_M, NC);
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* Hs = smem;
+  unsigned char* Ws = smem + H_BYTES;  // [2][T_BYTES]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Ws + 2 * T_BYTES);  // full[2], done[2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int D = 1 << lgD, M = D - 1;
+  const int nz = D >> 3, ny = D >> 4, nx = D / TX;
+  long long bid = blockIdx.x;
+  const int bz = (int)(bid % nz);
+  bid /= nz;
+  const int by = (int)(bid % ny);
+  bid /= ny;
+  const int bx = (int)(bid % nx);
+  const long long b = bid / nx;
+  const int x0 = bx * TX, y0 = by * 16, z0 = bz * 8;
+  const long long sbase = b << (3 * lgD);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int q = 0; q < 4; ++q) mbar_init(bars + q, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = *tslot;
+  // thread 0's account of the copies and MMAs in flight
+  int issued[2] = {0, 0}, landed[2] = {0, 0}, commits[2] = {0, 0}, last_commit = -1;
+  if (tid == 0) {
+    bulk_load(Ws, Wp, (uint32_t)T_BYTES, bars);
+    ++issued[0];
+  }
+  for (int e = tid; e < CH * HX * HY * HZ; e += TC_THREADS) {
+    int r = e;
+    const int hz = r % HZ;
+    r /= HZ;
+    const int hy = r % HY;
+    r /= HY;
+    const int hx = r % HX;
+    const int c8 = r / HX;
+    const long long v = sbase + ((((long long)((x0 + hx - 1) & M) << lgD) + ((y0 + hy - 1) & M))
+                                 << lgD) +
+                        ((z0 + hz - 1) & M);
+    cp_async16(Hs + 16 * e, x + v * ldx + offx + 8 * c8, true);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  bool ok = true;
+  if (tid == 0) {
+    const uint32_t h0 = smem_u32(Hs), w0 = smem_u32(Ws);
+    const int sg = DGRAD ? -1 : 1;
+    for (int t = 0; t < 27 && ok; ++t) {
+      const int st = t & 1;
+      if (t + 1 < 27) {
+        const int s1 = (t + 1) & 1;  // last read by the MMAs of tap t - 1
+        if (t >= 1 && !mbar_wait(bars + 2 + s1, ((t - 1) >> 1) & 1, err)) {
+          ok = false;
+          break;
+        }
+        bulk_load(Ws + s1 * T_BYTES, Wp + (long long)(t + 1) * NC * KC, (uint32_t)T_BYTES,
+                  bars + s1);
+        ++issued[s1];
+      }
+      if (!mbar_wait(bars + st, (t >> 1) & 1, err)) {
+        ok = false;
+        break;
+      }
+      ++landed[st];
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int dx = sg * (t / 9 - 1), dy = sg * ((t / 3) % 3 - 1), dz = sg * (t % 3 - 1);
+#pragma unroll 1
+      for (int tx = 0; tx < TX; ++tx) {
+        const uint32_t a_off = (uint32_t)((((tx + dx + 1) * HY + (dy + 1)) * HZ + (dz + 1)) * 16);
+#pragma unroll
+        for (int kk = 0; kk < KC / 16; ++kk) {
+          const uint64_t ad = sdesc(h0 + a_off + 2 * kk * PLANE, PLANE, SBO);
+          const uint64_t bd = sdesc(w0 + st * T_BYTES + 2 * kk * B_LBO, B_LBO, 128);
+          mma_bf16(tbase + tx * NC, ad, bd, IDESC, (t > 0 || kk > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(bars + 2 + st);
+      ++commits[st];
+      last_commit = st;
+    }
+    if (ok && !mbar_wait(bars + 2 + (26 & 1), (26 >> 1) & 1, err)) ok = false;
+    if (!ok) {
+      // a wait ran out: the copies and MMAs in flight (each wait bounded)
+      for (int q = 0; q < 2; ++q)
+        while (landed[q] < issued[q]) {
+          if (!mbar_wait(bars + q, (uint32_t)(landed[q] & 1), err)) break;
+          ++landed[q];
+        }
+      if (last_commit >= 0)
+        mbar_wait(bars + 2 + last_commit, (uint32_t)((commits[last_commit] - 1) & 1), err);
+    }
+  }
+  ok = __syncthreads_and(ok);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int row = warp * 32 + (tid & 31);
+    const int yy = row >> 3, zz = row & 7;
+    const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int tx = 0; tx < TX; ++tx) {
+      const long long m = sbase + ((((long long)(x0 + tx) << lgD) + (y0 + yy)) << lgD) + (z0 + zz);
+#pragma unroll 1
+      for (int n0 = 0; n0 < NC; n0 += 16) {
+        float v[16];
+        tmem_ld16(lane_addr + tx * NC + n0, v);
+        if (!DGRAD) {
+          __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            float a = v[i] + (bias ? bias[n0 + i] : 0.f);
+            if (relu) a = fmaxf(a, 0.f);
+            o[i] = __float2bfloat16(a);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(y + m * ldy + offy + n0);
+          dst[0] = reinterpret_cast<const uint4*>(o)[0];
+          dst[1] = reinterpret_cast<const uint4*>(o)[1];
+        } else {
+          float* q = gx + m * ldg + offg + n0;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) q[i] = accumulate ? q[i] + v[i] : v[i];
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                 "r"(tmem_cols)
+                 : "memory");
+}
+
+template <int KC, int NC, bool DG, int TX>
+void launch_halo_s(const TcArgs& a, cudaStream_t s) {
+  constexpr int H_BYTES = (KC / 8) * (TX + 2) * 18 * 10 * 16, T_BYTES = NC * KC * 2;
+  const int cols0 = TX * NC;
+  const int cols = cols0 <= 32 ? 32 : (cols0 <= 64 ? 64 : (cols0 <= 128 ? 128 : 256));
+  const size_t need = (size_t)H_BYTES + 2 * T_BYTES + 4 * 8 + 16;
+  const int k = 512 / cols;
+  const size_t cap = 233472 / (k + 1) - 1024 + 16;
+  const size_t smem = need > cap ? need : cap;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_conv_halo_s<KC, NC, DG, TX>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
+  }
+  const long long tiles = a.Mtot / (TX * 16 * 8);
+  k_conv_halo_s<KC, NC, DG, TX><<<(unsigned)tiles, TC_THREADS, smem, s>>>(
+      a.x, a.ldx, a.offx, a.Wp, a.bias, a.relu, a.y, a.ldy, a.offy, a.gx, a.ldg, a.offg,
+      a.accumulate, a.lgD, cols, a.err);
+}
+
 // Packed weight slices.  Forward (N = Cout, K = Cin):
 //   Wp[t][c][n][k8] = W[t][8c + k8][n]
 // Input gradient (N = Cin, K = Cout):
@@ -743,6 +926,17 @@ bool nn_tc_conv(const TcArgs& a, int K, int N, bool dgrad, cudaStream_t s) {
     HALO_CASE(16, 16, 4, 4) HALO_CASE(16, 32, 4, 4) HALO_CASE(32, 32, 2, 2)
     HALO_CASE(32, 16, 2, 2)
 #undef HALO_CASE
+    // larger channel counts: the weight slices stream beside the resident block
+#define HALO_S(KK, NN, TXX, DGR)                           \
+  if (K == KK && N == NN && dgrad == DGR) {                \
+    launch_halo_s<KK, NN, DGR, TXX>(a, s);                  \
+    return true;                                            \
+  }
+    HALO_S(96, 32, 2, false) HALO_S(32, 96, 2, true) HALO_S(32, 64, 2, false)
+    HALO_S(64, 32, 2, true) HALO_S(64, 64, 2, false) HALO_S(64, 64, 2, true)
+    HALO_S(64, 128, 2, false) HALO_S(128, 64, 1, true) HALO_S(128, 128, 1, false)
+    HALO_S(128, 128, 1, true) HALO_S(64, 192, 1, true)
+#undef HALO_S
     if (!dgrad && K == 48 && N == 16) {
       launch_halo<48, 16, false, 2>(a, s);
       return true;

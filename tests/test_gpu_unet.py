@@ -32,7 +32,10 @@ def bf(a, dev):
                                           (2, 16, 32, 64), (4, 16, 16, 32),
                                           # the halo-tiled full-resolution kernels
                                           (1, 16, 16, 16), (2, 16, 48, 16), (1, 32, 16, 16),
-                                          (1, 16, 16, 32), (2, 16, 32, 32), (1, 16, 32, 16)])
+                                          (1, 16, 16, 32), (2, 16, 32, 32), (1, 16, 32, 16),
+                                          # the streamed-weight halo kernels
+                                          (1, 16, 96, 32), (1, 16, 32, 64), (1, 16, 64, 64),
+                                          (1, 16, 64, 128), (1, 16, 128, 128), (1, 16, 192, 64)])
 def test_conv_kernels_match_oracle(dev, B, D, Cin, Cout):
     rng = np.random.default_rng(B * 1000 + D * 10 + Cin + Cout)
     x = rng.standard_normal((B, D, D, D, Cin)).astype(np.float32)
