@@ -491,6 +491,57 @@ def family_table(kern_ms, kern_n, kern_cells, steps, peak):
     return fams
 
 
+# Layers of the learned start's network for profiler captures of its
+# convolution kernels: (fields, grid size, Cin, Cout, ops); op 0 forward, 1
+# input gradient, 2 weight gradient.  16 -> 16 is the full-resolution layer
+# (halo-tiled kernel), 64 -> 64 a third-level layer of a 256^3 field and
+# 96 -> 32 the second level's concatenation (streamed-weight halo kernel),
+# 192 -> 64 the third level's concatenation (per-tap kernel).
+CONV_CASE = ((1, 128, 16, 16, (0, 1, 2)), (1, 64, 64, 64, (0, 1, 2)),
+             (1, 128, 96, 32, (0,)), (1, 64, 192, 64, (0,)))
+
+
+def conv_case(dev):
+    """Every op of CONV_CASE once as a warm-up, once more (the launches to
+    capture: the 8 matching `k_conv_|k_wgrad_tc` after the first 8), then 5
+    timed repetitions of each op with CUDA events; one JSON line per op."""
+    import torch
+    from paper_1305_2418_gb300 import mgfr
+
+    layers = []
+    for i, (B, D, ci, co, ops) in enumerate(CONV_CASE):
+        g = torch.Generator(device=dev).manual_seed(100 + i)
+        x = (torch.randn((B, D, D, D, ci), device=dev, generator=g) * 0.5).to(torch.bfloat16)
+        w = (torch.randn((27, ci, co), device=dev, generator=g) * 0.1).to(torch.bfloat16)
+        gy = (torch.randn((B, D, D, D, co), device=dev, generator=g) * 0.5).to(torch.bfloat16)
+        bias = torch.zeros(co, device=dev, dtype=torch.float32)
+        db = torch.zeros(co, device=dev, dtype=torch.float32)
+        for op in ops:
+            if op == 0:
+                f = (lambda x=x, w=w, b=bias: mgfr.conv3d(0, x, w, b, relu=True))
+            elif op == 1:
+                f = (lambda x=x, w=w, gy=gy: mgfr.conv3d(1, x, w, g=gy))
+            else:
+                f = (lambda x=x, w=w, gy=gy, db=db: mgfr.conv3d(2, x, w, g=gy, db=db))
+            layers.append((B, D, ci, co, op, f))
+    for _ in range(2):
+        for *_, f in layers:
+            f()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for B, D, ci, co, op, f in layers:
+        e0.record()
+        for _ in range(5):
+            f()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        flop = 2.0 * 27 * ci * co * B * D ** 3
+        print(json.dumps({"fields": B, "D": D, "cin": ci, "cout": co,
+                          "op": ("forward", "input_grad", "weight_grad")[op],
+                          "ms": round(ms, 4), "tflops": round(flop / ms / 1e9, 1)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -505,6 +556,9 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="a smaller sample of the workload for full-metric profiler captures: "
                          "256^3 base in a 50 Mpc/h box (same cell size), nbar 0.5")
+    ap.add_argument("--conv-case", action="store_true",
+                    help="only the network's convolution layers (for profiler captures of "
+                         "the convolution kernels)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -528,6 +582,10 @@ def main():
     def barrier():
         if world > 1:
             dist.barrier()
+
+    if args.conv_case:
+        conv_case(dev)
+        return
 
     w = dict(WORKLOAD)
     if args.profile_case:

@@ -194,21 +194,46 @@ __global__ void k_wgrad_reduce(const float* __restrict__ partials, int S, long l
   dW[i] = s;
 }
 
-// db[c] = sum over voxels of g[m][c] (one block per channel)
-__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ g, int ldg, int offg, long long Mtot,
-                            float* __restrict__ db) {
-  __shared__ float red[256];
-  const int c = blockIdx.x;
+// db[c] = sum over voxels of g[m][c].  The additions follow one fixed order:
+// for each slot t < 256 the voxels m = t, t + 256, t + 512, ... in turn, then
+// a pairwise tree over the 256 slot sums (stride 128, 64, ..., 1).  Stage 1
+// gives every (slot, channel) pair its own thread (consecutive threads take
+// consecutive channels of one voxel, so a warp's loads are contiguous) and
+// keeps 32 loads of the chain in flight; stage 2 runs the tree, one block
+// per channel.
+constexpr int BG_SLOTS = 256;
+
+__global__ void __launch_bounds__(128) k_bias_slots(const __nv_bfloat16* __restrict__ g, int ldg,
+                                                    int offg, long long Mtot, int Cout,
+                                                    float* __restrict__ part) {
+  const long long T = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (T >= (long long)BG_SLOTS * Cout) return;
+  const int c = (int)(T % Cout), t = (int)(T / Cout);
+  constexpr int U = 32;
   float s = 0.f;
-  for (long long m = threadIdx.x; m < Mtot; m += blockDim.x)
-    s += __bfloat162float(g[m * ldg + offg + c]);
-  red[threadIdx.x] = s;
+  long long m = t;
+  for (; m + (U - 1) * (long long)BG_SLOTS < Mtot; m += U * (long long)BG_SLOTS) {
+    float v[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) v[q] = __bfloat162float(g[(m + q * BG_SLOTS) * ldg + offg + c]);
+#pragma unroll
+    for (int q = 0; q < U; ++q) s += v[q];
+  }
+  for (; m < Mtot; m += BG_SLOTS) s += __bfloat162float(g[m * ldg + offg + c]);
+  part[(long long)t * Cout + c] = s;
+}
+
+__global__ void __launch_bounds__(BG_SLOTS) k_bias_tree(const float* __restrict__ part, int Cout,
+                                                        float* __restrict__ db) {
+  __shared__ float red[BG_SLOTS];
+  const int c = blockIdx.x, t = threadIdx.x;
+  red[t] = part[(long long)t * Cout + c];
   __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+  for (int w = BG_SLOTS / 2; w > 0; w >>= 1) {
+    if (t < w) red[t] += red[t + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) db[c] = red[0];
+  if (t == 0) db[c] = red[0];
 }
 
 constexpr int WG_S_TARGET = 608;  // about 4 blocks per SM of partial tiles
@@ -243,11 +268,16 @@ void nn_conv_dgrad(TView g, int Cout, const __nv_bfloat16* W, FView gx, int Cin,
 #undef LAUNCH_D
 }
 
-void nn_wgrad_finish(const float* partials, int S, int Cin, int Cout, float* dW, TView g,
+void nn_wgrad_finish(float* partials, int S, int Cin, int Cout, float* dW, TView g,
                      float* db, long long Mtot, cudaStream_t s) {
   const long long n = 27LL * Cin * Cout;
   k_wgrad_reduce<<<nblocks(n, 256), 256, 0, s>>>(partials, S, n, dW);
-  if (db) k_bias_grad<<<Cout, 256, 0, s>>>(g.p, g.ld, g.off, Mtot, db);
+  if (!db) return;
+  // the bias stages reuse the partials (read by k_wgrad_reduce before them on
+  // this stream); they hold S * 27 * Cin * Cout >= 432 * Cout floats (Cin >= 16)
+  const long long nt = (long long)BG_SLOTS * Cout;
+  k_bias_slots<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(g.p, g.ld, g.off, Mtot, Cout, partials);
+  k_bias_tree<<<Cout, BG_SLOTS, 0, s>>>(partials, Cout, db);
 }
 
 long long nn_wgrad_scratch(int Cin, int Cout) {

@@ -31,8 +31,9 @@ void nn_conv_dgrad(TView g, int Cout, const __nv_bfloat16* W, FView gx, int Cin,
 void nn_conv_wgrad(TView x, int Cin, TView g, int Cout, float* dW, float* db, float* partials,
                    int B, int lgD, cudaStream_t s);
 long long nn_wgrad_scratch(int Cin, int Cout);
-// dW[i] = sum over the S slices of partials[s][i] (in order), and db
-void nn_wgrad_finish(const float* partials, int S, int Cin, int Cout, float* dW, TView g,
+// dW[i] = sum over the S slices of partials[s][i] (in order), then db (the
+// bias stages reuse `partials` as their scratch: Cin >= 16, S >= 1)
+void nn_wgrad_finish(float* partials, int S, int Cin, int Cout, float* dW, TView g,
                      float* db, long long Mtot, cudaStream_t s);
 
 // ---- tensor-core (tcgen05) forward and input-gradient convolutions (nn_tc.cu)

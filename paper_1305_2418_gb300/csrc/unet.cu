@@ -631,6 +631,9 @@ mgfr_status mgfr_unet_train_step(mgfr_ctx* c, int B, int D, const double* delta_
   mgfr_status rs = unet_alloc(c, U, B, lg_of(D));
   if (rs != MGFR_OK) return rs;
   const long long M0 = (long long)B * D * D * D;
+  // the batch and targets come from work on the caller's stream
+  MG_CK(c, cudaEventRecord(c->ev_in, c->user));
+  MG_CK(c, cudaStreamWaitEvent(c->s, c->ev_in, 0));
   MG_CK(c, cudaMemcpyAsync(U->fr0d, fr0_host, sizeof(double) * B, cudaMemcpyHostToDevice, c->s));
   const Model mm = make_model(c->cfg, 1.0);
   k_features<<<nblocks(M0, BS), BS, 0, c->s>>>(delta_dev, U->fr0d, (long long)D * D * D, M0, U->X0,
