@@ -379,8 +379,8 @@ mgfr_status mgfr_batch_autotune(mgfr_ctx* ctx, int nsolves, const mgfr_batch_ite
  * at a = 1, see mgfr_unet_params) to u; the multigrid then drives the
  * residual to the same tolerance from that start (pass it as u_init or use
  * MGFR_START_LEARNED).  Training and inference run on this library's own
- * tensor-core kernels (tcgen05 for the forward and input-gradient
- * convolutions, mma.sync for the weight gradient).  D (box cells per side) must be
+ * tensor-core kernels (tcgen05 with TMEM accumulators for the forward,
+ * input-gradient and weight-gradient convolutions).  D (box cells per side) must be
  * a power of two in [32, 512]; the network applies at the cell size it was
  * trained at.
  */

@@ -10,6 +10,9 @@
 // transposed weight slice.  The weight gradient is a GEMM over voxels with
 // both operands staged transposed (voxel index contiguous) in shared memory;
 // per-chunk partial sums are reduced by a second kernel (deterministic).
+// The network's own channel pairs run on the tcgen05 kernels of nn_tc.cu;
+// these serve the others.  nn_wgrad_finish (the reduction of the partial dW
+// and the bias gradient) serves both.
 #include <algorithm>
 
 #include "nn_kernels.cuh"
