@@ -1,6 +1,10 @@
-// nn_tc.cu -- the network's 3^3 convolutions (forward and input gradient) on
-// the fifth-generation tensor cores: tcgen05.mma with the FP32 accumulator in
-// tensor memory (TMEM), BF16 operands in shared memory.
+// nn_tc.cu -- the network's 3^3 convolutions (forward, input gradient and
+// weight gradient) on the fifth-generation tensor cores: tcgen05.mma with the
+// FP32 accumulator in tensor memory (TMEM), BF16 operands in shared memory.
+// Three forms: the per-tap kernel (k_conv_tc, below), the halo-tiled kernels
+// of the full- and second-resolution layers (k_conv_halo, k_conv_halo_s: the
+// input block with its one-voxel halo staged once per CTA, each tap a shifted
+// descriptor into it) and the weight gradient (k_wgrad_tc).
 //
 // Implicit GEMM per CTA (128 threads): rows = an M tile of 128 consecutive
 // voxels, columns = all N output channels (N <= 256), reduction = 27 taps x

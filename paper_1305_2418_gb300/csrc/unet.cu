@@ -1,18 +1,20 @@
 // unet.cu -- learned initial guess for the field solve: a 4-level 3D U-Net
 // (16/32/64/128 channels, 3^3 kernels, circular padding) with BF16 weights
 // and activations and FP32 accumulation, trained and evaluated on the GPU by
-// this library's own kernels (nn_conv.cu and the elementwise kernels here).
+// this library's own kernels (the tcgen05 convolutions of nn_tc.cu, the
+// mma.sync ones of nn_conv.cu for other channel pairs, the elementwise
+// kernels here).
 //
 // Input features per voxel: ln(1 + delta), log10|fR0| + 5, 1 and the local
 // screening value -(n+1) ln(1 + Om delta / Rt) (padded to 16 channels; the
-// boxes are at a = 1).  Output: v = asinh(u / 0.01) (FP32), u = 0.01 sinh(v).  Encoder: two conv+ReLU per level, 2^3
-// average pooling.  Decoder: nearest upsampling, concatenation with the
-// encoder output of the same level, two conv+ReLU.  Head: 1x1x1 conv to 1
-// channel.  Loss: mean squared error in u.  Optimiser: Adam on FP32 master
+// boxes are at a = 1).  Output: v = asinh(u / 0.01) (FP32), u = 0.01 sinh(v).
+// Encoder: two conv+ReLU per level, 2^3 average pooling.  Decoder: nearest
+// upsampling, concatenation with the encoder output of the same level, two
+// conv+ReLU.  Head: 1x1x1 conv to 1 channel.  Loss: mean squared error in v.  Optimiser: Adam on FP32 master
 // weights, BF16 copies used by the convolutions.
 //
 // The network is fully convolutional, so it applies to any power-of-two box
-// >= 8 cells at the cell size it was trained on.
+// of 32 to 512 cells per side at the cell size it was trained on.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
