@@ -10,8 +10,9 @@
 // boxes are at a = 1).  Output: v = asinh(u / 0.01) (FP32), u = 0.01 sinh(v).
 // Encoder: two conv+ReLU per level, 2^3 average pooling.  Decoder: nearest
 // upsampling, concatenation with the encoder output of the same level, two
-// conv+ReLU.  Head: 1x1x1 conv to 1 channel.  Loss: mean squared error in v.  Optimiser: Adam on FP32 master
-// weights, BF16 copies used by the convolutions.
+// conv+ReLU.  Head: 1x1x1 conv to 1 channel.  Loss: mean squared error in v.
+// Optimiser: Adam on FP32 master weights, BF16 copies used by the
+// convolutions.
 //
 // The network is fully convolutional, so it applies to any power-of-two box
 // of 32 to 512 cells per side at the cell size it was trained on.
