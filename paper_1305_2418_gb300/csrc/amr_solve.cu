@@ -11,10 +11,12 @@
 // coarse solutions themselves are never modified.
 //
 // Kernels are templated on the working precision T.  The FP64 form runs FP64
-// V-cycles to the tolerance.  The mixed form first runs FP32 V-cycles (e^u
-// stored in FP32, SFU exponentials) until the FP32 residual reaches
-// mixed_switch or stalls, then finishes with FP64 V-cycles from that iterate;
-// the stopping test is always the FP64 residual.
+// V-cycles to the tolerance.  The mixed form first runs FP32 V-cycles (u in
+// FP32, e^u recomputed by the SFU) until the FP32 residual reaches
+// mixed_switch or stalls (phase A), then corrects the defect (phase B): the
+// residual r = f - L(u) of the level in double-float (FP64-accurate, on the
+// FP32 pipes), FP32 linear masked V-cycles on J(u) e = r, u += e in
+// double-float; the stopping test is always that FP64-accurate residual.
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
