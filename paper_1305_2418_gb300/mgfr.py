@@ -1,8 +1,9 @@
 """Thin ctypes binding of libmgfr.so (the C ABI declared in include/mgfr.h).
 
 Argument marshalling only: every step of the solve runs in the library's CUDA
-kernels.  Inputs and outputs are torch CUDA tensors (FP64, contiguous); the
-work is ordered on torch's current stream.  There is no CPU fallback: if the
+kernels.  Inputs and outputs are torch CUDA tensors (FP64, contiguous); a
+Solver's work is ordered after the stream it was created on (torch's current
+stream at that time, unless one is passed).  There is no CPU fallback: if the
 library is missing, loading it raises.
 """
 from __future__ import annotations
@@ -151,7 +152,8 @@ def _ptr(t):
 
 
 class Solver:
-    """A library context bound to one device and torch's current stream."""
+    """A library context bound to one device and one stream (torch's current
+    stream when the Solver is created, unless `stream` is given)."""
 
     def __init__(self, device: int = 0, stream=None, **cfg):
         import torch
